@@ -1,0 +1,184 @@
+/*
+ * lbfmm: GB300-native fast integral-equation solver for the Laplace-Beltrami
+ * Dirichlet problem on the unit sphere with M islands
+ * (Kropinski & Nigam, "Fast integral equation methods for the Laplace-Beltrami
+ * equation on the sphere").
+ *
+ * The method (Sec. 3-5): project the island curves stereographically to the
+ * plane, discretise the double-layer second-kind equation with the trapezoidal
+ * rule (Nystrom), border it with one point source per island (Eq. u_multi,
+ * sum_ak, constraints), and solve the bordered system (Eq. matrix_eqns) with
+ * GMRES preconditioned by the block matrix [[I, E], [F, D]] (Eq.
+ * matrix_eqns_c), computing each matvec with a 2D fast multipole method.
+ *
+ * Conventions
+ *   - Every call returns an int status: 0 = LBF_OK, > 0 = soft (the result is
+ *     usable), < 0 = hard error (outputs undefined).  No exception or exit
+ *     crosses this interface.
+ *   - Array arguments are DEVICE pointers unless marked "host"; the caller owns
+ *     them.  Arrays are contiguous, double precision, row-major.
+ *   - Calls are asynchronous on the given stream unless marked "synchronous".
+ *     Device-side errors (a node at the projection pole, ...) are recorded in a
+ *     status word that lbf_sync_status() returns.
+ *   - Node ordering: nodes are grouped by island through the CSR array
+ *     island_ptr[M+1] (host, int64): island k owns nodes
+ *     island_ptr[k] .. island_ptr[k+1]-1, equispaced in the curve parameter
+ *     alpha in [0, 2 pi) (h_k = 2 pi / N_k, Sec. 5), curve oriented
+ *     counter-clockwise about the island seen from outside the sphere.  Island 0
+ *     plays the role of C_1 (the curve that encircles the north pole, Sec. 3)
+ *     and is exempt from the density constraint (Eq. disc_constr).
+ *   - Unknown vector of the bordered system: [sigma (N); a (M)] (Eq. matrix_eqns),
+ *     right-hand side [2 g; 0] (the paper's doubled scaling, Eq. disc_sphere).
+ */
+#ifndef LBFMM_H
+#define LBFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lbf_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+typedef struct lbf_plan lbf_plan;
+
+/* status codes */
+#define LBF_OK 0
+#define LBF_NOCONV 1        /* GMRES hit maxit before tol; outputs are the last iterate */
+#define LBF_EINVAL (-1)     /* bad argument (null pointer, size, option out of range) */
+#define LBF_EPOLE (-2)      /* a node lies at the projection pole: 1 - x3 < 1e-12 */
+#define LBF_EDEPTH (-3)     /* reserved: the tree needs more than max_depth levels */
+#define LBF_EWORKSPACE (-4) /* workspace too small; see lbf_plan_create */
+#define LBF_ECUDA (-5)      /* a CUDA runtime call failed */
+#define LBF_ETIMEOUT (-6)   /* a bounded device wait gave up */
+#define LBF_ENOTBUILT (-7)  /* the plan was created without the parts this call needs */
+
+/* matvec choice */
+#define LBF_MATVEC_FMM 0
+#define LBF_MATVEC_DIRECT 1
+
+/* operators for lbf_apply */
+#define LBF_OP_FULL 0           /* bordered matrix A = [[I+K, E],[F, D]], in/out N+M */
+#define LBF_OP_K_ONLY 1         /* density block (I + K) sigma, in/out N   */
+#define LBF_OP_PRECONDITIONED 2 /* P^-1 A with P = [[I, E],[F, D]], in/out N+M */
+
+/* Solver and FMM options.  Defaults (lbf_default_options) follow Sec. 6:
+ * GMRES restart 50; tolerance 1e-12 (the paper uses 1e-11); FMM accurate to
+ * about 1e-12 relative. */
+typedef struct lbf_options {
+    double tol;           /* GMRES stop: ||P^-1 (b - A x)|| <= tol ||P^-1 b|| */
+    int restart;          /* GMRES restart length m (1..200) */
+    int maxit;            /* maximum GMRES iterations in total */
+    int p;                /* FMM expansion order: terms 0..p (4..63) */
+    int leaf_size;        /* a quadtree box is split while it holds more nodes (1..1024) */
+    int max_depth;        /* quadtree depth limit D (1..30) */
+    int matvec;           /* LBF_MATVEC_FMM or LBF_MATVEC_DIRECT */
+    int border;           /* 1: build E, F, D and the Schur complement (needed by
+                             LBF_OP_FULL, LBF_OP_PRECONDITIONED, gmres and a-terms
+                             of evaluate); 0: density block only */
+    int64_t box_capacity; /* quadtree boxes reserved in the workspace; 0 = estimate */
+} lbf_options;
+
+int lbf_default_options(lbf_options *opt /* host */);
+
+/* Human-readable name of a status code (static string). */
+const char *lbf_status_string(int status);
+
+/* Bytes of device workspace a plan over these islands needs (synchronous, host
+ * only).  The quadtree part is an estimate from N and leaf_size unless
+ * opt->box_capacity is set; lbf_plan_create reports the exact need if the
+ * estimate was short. */
+int lbf_workspace_size(int M, const int64_t *island_ptr /* host, M+1 */, const lbf_options *opt,
+                       size_t *bytes /* host out */);
+
+/* Build a plan: project the nodes to the plane (Sec. 3), precompute the
+ * trapezoidal weights w_j = h xi'_j, the self terms and the rank-one sphere
+ * correction (Sec. 5, Eq. disc_sphere with Eq. cont_kern), build the Morton
+ * quadtree and its interaction lists, and (opt->border) form E, F, D and
+ * factor the Schur complement S = D - F E (Sec. 5, Eq. matrix_eqns_c).
+ *
+ *   x, dx, d2x : N x 3 nodes on the unit sphere and their first and second
+ *                derivatives with respect to alpha (device)
+ *   centres    : M x 3 points c_k inside island k carrying the multiplier
+ *                sources A_k G(x, c_k) (Eq. u_multi) (device)
+ *   pole_rotation : host 3x3 row-major rotation applied to every point before
+ *                projection, or NULL for none (Sec. 3 "without loss of generality")
+ *   workspace, bytes : device memory owned by the caller, >= lbf_workspace_size;
+ *                it must stay allocated and untouched until lbf_plan_destroy.
+ *   box_capacity_needed : host out (nullable): on LBF_EWORKSPACE, the
+ *                box_capacity to retry with (then query lbf_workspace_size again).
+ * Synchronous: returns after the plan is built.  The library allocates a few KB
+ * of pinned host memory here and no device memory anywhere. */
+int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const double *x,
+                    const double *dx, const double *d2x, const double *centres,
+                    const double *pole_rotation, const lbf_options *opt, void *workspace,
+                    size_t bytes, int64_t *box_capacity_needed, lbf_stream_t stream);
+
+int lbf_plan_destroy(lbf_plan *plan);
+
+/* Plan facts (host out, all nullable): total nodes, islands, quadtree boxes,
+ * leaves, deepest level, expansion order. */
+int lbf_plan_info(const lbf_plan *plan, int64_t *N, int *M, int64_t *nbox, int64_t *nleaf,
+                  int *depth, int *p);
+
+/* Projected geometry in the caller's node order (all nullable, device out):
+ *   xi     : N x 2, the stereographic image (x1 + i x2)/(1 - x3) (Sec. 3)
+ *   normal : N x 2, unit normal into the island in the plane, -i xi'/|xi'|
+ *   weight : N x 2, complex trapezoidal weight h_k xi'_j
+ *   arc_weight : N, h_k |xi'_j| */
+int lbf_geometry_out(const lbf_plan *plan, double *xi, double *normal, double *weight,
+                     double *arc_weight, lbf_stream_t stream);
+
+/* out = op(in) for one of LBF_OP_* (device in/out, caller's node order).
+ * LBF_OP_K_ONLY needs N entries in and out; the others N + M. */
+int lbf_apply(lbf_plan *plan, int op, const double *in, double *out, lbf_stream_t stream);
+
+/* Solve [[I+K, E],[F, D]] [sigma; a] = [2 g; 0] with restarted GMRES on the
+ * left-preconditioned system (Eq. matrix_eqns_c).  g: N boundary values
+ * (device); sigma (N), a (M): device out; x0: initial guess [sigma; a] (N+M,
+ * device, nullable = zero).  iters, rel_res: host out (nullable): iterations
+ * done and the final preconditioned relative residual.  Synchronous.
+ * Returns LBF_NOCONV (> 0) when maxit is reached before tol. */
+int lbf_gmres_solve(lbf_plan *plan, const double *g, double *sigma, double *a, const double *x0,
+                    int *iters, double *rel_res, lbf_stream_t stream);
+
+/* u at T points t (T x 3 on the sphere, off the curves, device) from the
+ * representation formula (Eq. u_multi): the double layer of sigma plus
+ * sum_m a_m G(t, c_m).  a may be NULL (no multiplier sources). */
+int lbf_evaluate(lbf_plan *plan, const double *sigma, const double *a, int64_t T,
+                 const double *targets, double *u, lbf_stream_t stream);
+
+/* out_q = sum_s gamma_s G(t_q, p_s), G the generalized fundamental solution
+ * (Sec. 1.1, Eq. greens_func): Dirichlet data of point sources or vortices
+ * (Sec. 6, Example 2).  t: T x 3, p: S x 3, gamma: S, out: T (device). */
+int lbf_green_sum(int64_t T, const double *t, int64_t S, const double *p, const double *gamma,
+                  double *out, lbf_stream_t stream);
+
+/* The quadtree of a plan (Sec. 6, Example 3), for inspection and tests
+ * (device out, synchronous, all nullable):
+ *   perm  : N entries, perm[i] = caller index of the i-th node in Morton order
+ *   boxes : nbox x 8 int32 rows {level, ix, iy, parent, first_child, nchild,
+ *           begin, end}; boxes are numbered level by level, in Morton order
+ *           within a level; [begin, end) indexes the Morton-ordered nodes.
+ * The integer specification of keys and splitting is given in lbf_tree.cu. */
+int lbf_tree_export(const lbf_plan *plan, int32_t *perm, int32_t *boxes, lbf_stream_t stream);
+
+/* One interaction list of the adaptive FMM in CSR form over boxes
+ * (kind 0..3 = U, V, W, X; device out, synchronous).  ptr: nbox + 1 entries;
+ * idx: *len entries (pass idx = NULL to query *len, host out). */
+int lbf_list_export(const lbf_plan *plan, int kind, int32_t *ptr, int32_t *idx, int64_t *len,
+                    lbf_stream_t stream);
+
+/* Wait for the stream and return the first device-side error recorded by
+ * this plan's kernels (LBF_OK if none).  Synchronous. */
+int lbf_sync_status(lbf_plan *plan, lbf_stream_t stream);
+
+/* Number of kernels this library has launched in this process (a kernel
+ * replayed inside a CUDA graph counts once per replay). */
+int64_t lbf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBFMM_H */

@@ -1,0 +1,454 @@
+// C ABI of liblbfmm (include/lbfmm.h): options, workspace layout, plan life
+// cycle and the public calls.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbf_internal.cuh"
+
+std::atomic<int64_t> g_lbf_launches{0};
+
+int lbf_gmres_kernels_smem(int m);
+int lbf_gmres_blocks();
+int lbf_fmm_init_attrs();
+int lbf_krylov_init_attrs();
+
+namespace {
+
+struct GmresStateBytes {
+    char b[128];
+};
+
+int64_t box_capacity_estimate(int64_t N, const lbf_options &o)
+{
+    if (o.box_capacity > 0) return o.box_capacity;
+    return 8 * N / std::max(1, o.leaf_size) + 64 * o.max_depth + 1024;
+}
+
+bool valid(const lbf_options &o)
+{
+    return o.tol > 0 && o.restart >= 1 && o.restart <= 200 && o.maxit >= 1 && o.p >= 4 &&
+           o.p + 1 <= LBF_MAX_TERMS && o.leaf_size >= 1 && o.leaf_size <= 1024 &&
+           o.max_depth >= 1 && o.max_depth <= 30 &&
+           (o.matvec == LBF_MATVEC_FMM || o.matvec == LBF_MATVEC_DIRECT) &&
+           (o.border == 0 || o.border == 1);
+}
+
+// host tables of the translation operators (scaled expansions, see lbf_fmm.cu)
+void make_tables(std::vector<double> &binom, std::vector<double2> &m2m,
+                 std::vector<double2> &l2l, std::vector<double2> &tpow)
+{
+    const int T = LBF_MAX_TERMS;
+    binom.assign(2 * T * T, 0.0);
+    // Pascal rows n = 0 .. 2T-1, kept for k < T
+    std::vector<double> row(2 * T + 1, 0.0), nxt(2 * T + 1, 0.0);
+    row[0] = 1.0;
+    for (int n = 0; n < 2 * T; n++) {
+        for (int k = 0; k < T; k++) binom[n * T + k] = k <= n ? row[k] : 0.0;
+        nxt[0] = 1.0;
+        for (int k = 1; k <= n + 1; k++) nxt[k] = row[k - 1] + (k <= n ? row[k] : 0.0);
+        row.swap(nxt);
+    }
+    auto C = [&](int n, int k) { return binom[n * T + k]; };
+    m2m.assign(4 * T * T, make_double2(0, 0));
+    l2l.assign(4 * T * T, make_double2(0, 0));
+    for (int d = 0; d < 4; d++) {
+        std::complex<double> dv(((d & 1) ? 0.5 : -0.5), ((d >> 1) ? 0.5 : -0.5));
+        std::vector<std::complex<double>> pw(T);
+        pw[0] = 1.0;
+        for (int k = 1; k < T; k++) pw[k] = pw[k - 1] * dv;
+        for (int l = 0; l < T; l++)
+            for (int k = 0; k < T; k++) {
+                if (k <= l) {  // multipole shift: C(l,k) d^(l-k) 2^-k
+                    std::complex<double> v = C(l, k) * pw[l - k] * std::ldexp(1.0, -k);
+                    m2m[(d * T + l) * T + k] = make_double2(v.real(), v.imag());
+                }
+                if (k >= l) {  // local shift: 2^-l C(k,l) d^(k-l)
+                    std::complex<double> v = std::ldexp(1.0, -l) * C(k, l) * pw[k - l];
+                    l2l[(d * T + l) * T + k] = make_double2(v.real(), v.imag());
+                }
+            }
+    }
+    tpow.assign(49 * (T + 1), make_double2(0, 0));
+    for (int dx = -3; dx <= 3; dx++)
+        for (int dy = -3; dy <= 3; dy++) {
+            if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+            std::complex<double> t = 1.0 / (2.0 * std::complex<double>(dx, dy));
+            std::complex<double> p = 1.0;
+            int o = (dx + 3) * 7 + (dy + 3);
+            for (int k = 0; k <= T; k++) {
+                tpow[o * (T + 1) + k] = make_double2(p.real(), p.imag());
+                p *= t;
+            }
+        }
+}
+
+}  // namespace
+
+// Lay out every array of a plan over the arena (base == nullptr only sizes it).
+void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t cap)
+{
+    Arena &A = pl->arena;
+    const int T = LBF_MAX_TERMS;
+    int P = o.p + 1;
+    int64_t n = N + M;
+    pl->island_ptr = A.get<int64_t>(M + 1);
+    pl->xi = A.get<double2>(N);
+    pl->w = A.get<double2>(N);
+    pl->dself = A.get<double>(N);
+    pl->beta = A.get<double>(N);
+    pl->perm = A.get<int32_t>(N);
+    pl->rank = A.get<int32_t>(N);
+    pl->centres = A.get<double>(3 * (int64_t)M);
+    pl->rot_d = A.get<double>(9);
+    pl->tab_binom = A.get<double>(2 * T * T);
+    pl->tab_m2m = A.get<double2>(4 * T * T);
+    pl->tab_l2l = A.get<double2>(4 * T * T);
+    pl->tab_tpow = A.get<double2>(49 * (T + 1));
+    Tree &t = pl->tree;
+    t.cap = cap;
+    t.level = A.get<int32_t>(cap);
+    t.ix = A.get<int32_t>(cap);
+    t.iy = A.get<int32_t>(cap);
+    t.parent = A.get<int32_t>(cap);
+    t.child0 = A.get<int32_t>(cap);
+    t.nchild = A.get<int32_t>(cap);
+    t.begin = A.get<int32_t>(cap);
+    t.end = A.get<int32_t>(cap);
+    t.leaves = A.get<int32_t>(cap);
+    t.coll = A.get<int32_t>(9 * cap);
+    t.vlist = A.get<int32_t>(27 * cap);
+    t.nv = A.get<int32_t>(cap);
+    t.coarse = A.get<int32_t>(8 * cap);
+    t.ncoarse = A.get<int32_t>(cap);
+    t.xlist = A.get<int32_t>(16 * cap);
+    t.nx = A.get<int32_t>(cap);
+    t.u_cap = 24 * cap;
+    t.w_cap = 16 * cap;
+    t.u_ptr = A.get<int32_t>(cap + 1);
+    t.u_idx = A.get<int32_t>(t.u_cap);
+    t.w_ptr = A.get<int32_t>(cap + 1);
+    t.w_idx = A.get<int32_t>(t.w_cap);
+    pl->q = A.get<double2>(N);
+    if (o.matvec == LBF_MATVEC_FMM) {
+        pl->mpole = A.get<double2>(cap * P);
+        pl->local = A.get<double2>(cap * P);
+    }
+    pl->v = A.get<double>(N);
+    pl->bsig = A.get<double>(4);
+    pl->red = A.get<double>(1024);
+    pl->red_count = A.get<unsigned>(4);
+    pl->dev_status = A.get<int>(1);
+    pl->fvec = A.get<double>(M);
+    pl->yvec = A.get<double>(M);
+    pl->tin = A.get<double>(n);
+    pl->tout = A.get<double>(n);
+    if (o.border) {
+        pl->E = A.get<double>((int64_t)M * N);
+        pl->Sinv = A.get<double>((int64_t)M * M);
+    }
+    int m = o.restart;
+    pl->ldv = (n + 31) / 32 * 32;
+    pl->mdot_blocks = lbf_gmres_blocks();
+    if (o.border) {
+        pl->H = A.get<double>((int64_t)(m + 1) * m + 2 * (m + 1) + 2 * m + 2 * (m + 1) + m);
+        pl->gw = A.get<double>(n);
+        pl->gx = A.get<double>(n);
+        pl->gb = A.get<double>(n);
+        pl->gpart = A.get<double>((int64_t)pl->mdot_blocks * (m + 2));
+        pl->gs = (GmresState *)A.take(sizeof(GmresStateBytes));
+    }
+    // Region shared by the basis V (solves) and the plan-creation temporaries.
+    size_t vbytes = o.border ? sizeof(double) * (size_t)pl->ldv * (m + 1) : 0;
+    int64_t nunits = lbf_cdiv(N, 1024);
+    size_t tmp = 0;
+    auto add = [&](size_t b) { tmp = ((tmp + 255) & ~size_t(255)) + b; };
+    add(sizeof(double2) * N);      // xi_o
+    add(sizeof(double) * 3 * N);   // x3_o
+    add(sizeof(double2) * N);      // w_o
+    add(sizeof(double) * N);       // d_o
+    add(sizeof(double) * N);       // b_o
+    add(sizeof(uint64_t) * N);     // keys
+    add(sizeof(uint64_t) * N);     // keys_alt
+    add(sizeof(int32_t) * N);      // perm_alt
+    int64_t iscr = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + N / 512 + 8192;
+    add(sizeof(int32_t) * iscr);   // integer scratch (scans, histograms, flags)
+    add(sizeof(double) * 2 * (size_t)M * M + 64);  // Gauss-Jordan block
+    size_t big = std::max(vbytes, tmp);
+    pl->region = (char *)A.take(big);
+    pl->V = o.border ? (double *)pl->region : nullptr;
+}
+
+namespace {
+struct Temps {
+    double2 *xi_o, *w_o;
+    double *x3_o, *d_o, *b_o;
+    uint64_t *keys, *keys_alt;
+    int32_t *perm_alt, *iscr;
+    int64_t iscr_len;
+    double *gj;
+};
+
+Temps temps(lbf_plan *pl, char *region, int64_t N, int M, int64_t cap)
+{
+    Temps t;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        off = (off + 255) & ~size_t(255);
+        void *p = region + off;
+        off += b;
+        return p;
+    };
+    t.xi_o = (double2 *)take(sizeof(double2) * N);
+    t.x3_o = (double *)take(sizeof(double) * 3 * N);
+    t.w_o = (double2 *)take(sizeof(double2) * N);
+    t.d_o = (double *)take(sizeof(double) * N);
+    t.b_o = (double *)take(sizeof(double) * N);
+    t.keys = (uint64_t *)take(sizeof(uint64_t) * N);
+    t.keys_alt = (uint64_t *)take(sizeof(uint64_t) * N);
+    t.perm_alt = (int32_t *)take(sizeof(int32_t) * N);
+    int64_t nunits = lbf_cdiv(N, 1024);
+    t.iscr_len = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + N / 512 + 8192;
+    t.iscr = (int32_t *)take(sizeof(int32_t) * t.iscr_len);
+    t.gj = (double *)take(sizeof(double) * 2 * (size_t)M * M + 64);
+    return t;
+}
+}  // namespace
+
+extern "C" {
+
+int lbf_default_options(lbf_options *o)
+{
+    if (!o) return LBF_EINVAL;
+    o->tol = 1e-12;
+    o->restart = 50;
+    o->maxit = 2000;
+    o->p = 40;
+    o->leaf_size = 48;
+    o->max_depth = 30;
+    o->matvec = LBF_MATVEC_FMM;
+    o->border = 1;
+    o->box_capacity = 0;
+    return LBF_OK;
+}
+
+const char *lbf_status_string(int s)
+{
+    switch (s) {
+    case LBF_OK: return "ok";
+    case LBF_NOCONV: return "GMRES reached maxit before tol";
+    case LBF_EINVAL: return "invalid argument";
+    case LBF_EPOLE: return "a node lies at the projection pole";
+    case LBF_EDEPTH: return "quadtree deeper than supported";
+    case LBF_EWORKSPACE: return "workspace too small";
+    case LBF_ECUDA: return "CUDA runtime error";
+    case LBF_ETIMEOUT: return "a bounded device wait gave up";
+    case LBF_ENOTBUILT: return "the plan was created without the parts this call needs";
+    default: return "unknown status";
+    }
+}
+
+static int check_islands(int M, const int64_t *ptr, int64_t *N)
+{
+    if (M < 1 || !ptr || ptr[0] != 0) return LBF_EINVAL;
+    for (int k = 0; k < M; k++)
+        if (ptr[k + 1] - ptr[k] < 3) return LBF_EINVAL;
+    if (ptr[M] >= (int64_t)1 << 31) return LBF_EINVAL;
+    *N = ptr[M];
+    return LBF_OK;
+}
+
+int lbf_workspace_size(int M, const int64_t *island_ptr, const lbf_options *opt, size_t *bytes)
+{
+    if (!opt || !bytes || !valid(*opt)) return LBF_EINVAL;
+    int64_t N;
+    int rc = check_islands(M, island_ptr, &N);
+    if (rc) return rc;
+    lbf_plan tmp;
+    tmp.arena.base = nullptr;
+    tmp.arena.cap = ~size_t(0);
+    lbf_layout(&tmp, N, M, *opt, box_capacity_estimate(N, *opt));
+    *bytes = tmp.arena.off + 256;
+    return LBF_OK;
+}
+
+int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const double *x,
+                    const double *dx, const double *d2x, const double *centres,
+                    const double *pole_rotation, const lbf_options *opt, void *workspace,
+                    size_t bytes, int64_t *box_needed, lbf_stream_t stream)
+{
+    if (!plan || !x || !dx || !d2x || !centres || !opt || !workspace || !valid(*opt))
+        return LBF_EINVAL;
+    *plan = nullptr;
+    int64_t N;
+    int rc = check_islands(M, island_ptr, &N);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = lbf_fmm_init_attrs()) || (rc = lbf_krylov_init_attrs())) return rc;
+    if (M > 28000) return LBF_EINVAL;  // E-sum keeps the M coefficients in shared memory
+    lbf_plan *pl = new (std::nothrow) lbf_plan();
+    if (!pl) return LBF_EINVAL;
+    pl->N = N;
+    pl->M = M;
+    pl->n = N + M;
+    pl->opt = *opt;
+    pl->P = opt->p + 1;
+    int64_t cap = box_capacity_estimate(N, *opt);
+    pl->arena.base = (char *)workspace;
+    pl->arena.cap = bytes;
+    lbf_layout(pl, N, M, *opt, cap);
+    if (pl->arena.overflow) {
+        delete pl;
+        if (box_needed) *box_needed = cap;
+        return LBF_EWORKSPACE;
+    }
+    auto fail = [&](int code) {
+        if (pl->host_status) cudaFreeHost(pl->host_status);
+        if (pl->host_scalars) cudaFreeHost(pl->host_scalars);
+        delete[] pl->island_ptr_h;
+        delete pl;
+        return code;
+    };
+    if (cudaHostAlloc((void **)&pl->host_status, 64, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&pl->host_scalars, 256, cudaHostAllocDefault) != cudaSuccess)
+        return fail(LBF_ECUDA);
+    pl->island_ptr_h = new int64_t[M + 1];
+    memcpy(pl->island_ptr_h, island_ptr, sizeof(int64_t) * (M + 1));
+    if (pole_rotation) {
+        pl->has_rot = 1;
+        memcpy(pl->rot, pole_rotation, sizeof(pl->rot));
+    } else {
+        pl->has_rot = 0;
+        for (int i = 0; i < 9; i++) pl->rot[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    }
+    std::vector<double> binom;
+    std::vector<double2> m2m, l2l, tpow;
+    make_tables(binom, m2m, l2l, tpow);
+#define CK(call) do { if ((call) != cudaSuccess) return fail(LBF_ECUDA); } while (0)
+    CK(cudaMemcpyAsync(pl->island_ptr, island_ptr, sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->rot_d, pl->rot, sizeof(pl->rot), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->tab_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->tab_m2m, m2m.data(), sizeof(double2) * m2m.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->tab_l2l, l2l.data(), sizeof(double2) * l2l.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->tab_tpow, tpow.data(), sizeof(double2) * tpow.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(pl->dev_status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(pl->red_count, 0, 4 * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(pl->bsig, 0, 4 * sizeof(double), s));
+    // plan-creation temporaries overlay the region of the GMRES basis
+    Temps tt = temps(pl, pl->region, N, M, cap);
+    rc = lbf_geometry_build(pl, x, dx, d2x, centres, s, tt.xi_o, tt.x3_o, tt.w_o, tt.d_o, tt.b_o);
+    if (rc) return fail(rc);
+    {
+        int64_t need = 0;
+        rc = lbf_tree_build(pl, s, tt.xi_o, tt.keys, tt.keys_alt, tt.perm_alt, tt.iscr, tt.iscr_len, &need);
+        if (rc == LBF_OK && opt->matvec == LBF_MATVEC_FMM)
+            rc = lbf_lists_build(pl, s, tt.iscr, tt.iscr_len, &need);
+        if (rc == LBF_EWORKSPACE && box_needed) *box_needed = need;
+        if (rc) return fail(rc);
+    }
+    rc = lbf_geometry_gather(pl, s, tt.xi_o, tt.w_o, tt.d_o, tt.b_o);
+    if (rc) return fail(rc);
+    if (opt->border) {
+        rc = lbf_border_build(pl, s, tt.x3_o, tt.gj);
+        if (rc) return fail(rc);
+    }
+    CK(cudaMemcpyAsync(pl->host_status, pl->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+#undef CK
+    int st = *pl->host_status;
+    if (st & LBF_DEV_POLE) return fail(LBF_EPOLE);
+    if (st & 4) return fail(LBF_EINVAL);   // singular Schur complement
+    if (st & 8) return fail(LBF_EDEPTH);   // list overflow
+    *plan = pl;
+    return LBF_OK;
+}
+
+int lbf_plan_destroy(lbf_plan *pl)
+{
+    if (!pl) return LBF_EINVAL;
+    if (pl->host_status) cudaFreeHost(pl->host_status);
+    if (pl->host_scalars) cudaFreeHost(pl->host_scalars);
+    delete[] pl->island_ptr_h;
+    delete pl;
+    return LBF_OK;
+}
+
+int lbf_plan_info(const lbf_plan *pl, int64_t *N, int *M, int64_t *nbox, int64_t *nleaf, int *depth,
+                  int *p)
+{
+    if (!pl) return LBF_EINVAL;
+    if (N) *N = pl->N;
+    if (M) *M = pl->M;
+    if (nbox) *nbox = pl->tree.nbox;
+    if (nleaf) *nleaf = pl->tree.nleaf;
+    if (depth) *depth = pl->tree.nlev - 1;
+    if (p) *p = pl->P - 1;
+    return LBF_OK;
+}
+
+int lbf_geometry_out(const lbf_plan *pl, double *xi, double *normal, double *weight,
+                     double *arc_weight, lbf_stream_t stream)
+{
+    if (!pl) return LBF_EINVAL;
+    return lbf_geometry_out_impl(pl, xi, normal, weight, arc_weight, (cudaStream_t)stream);
+}
+
+int lbf_apply(lbf_plan *pl, int op, const double *in, double *out, lbf_stream_t stream)
+{
+    if (!pl || !in || !out || op < 0 || op > 2) return LBF_EINVAL;
+    if (op != LBF_OP_K_ONLY && !pl->opt.border) return LBF_ENOTBUILT;
+    cudaStream_t s = (cudaStream_t)stream;
+    int with_a = op != LBF_OP_K_ONLY;
+    int rc = lbf_permute_in(pl, in, pl->tin, with_a, s);
+    if (rc) return rc;
+    rc = lbf_apply_op_sorted(pl, op, pl->tin, pl->tout, nullptr, s);
+    if (rc) return rc;
+    return lbf_permute_out(pl, pl->tout, out, with_a, s);
+}
+
+int lbf_gmres_solve(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
+                    int *iters, double *rel_res, lbf_stream_t stream)
+{
+    if (!pl || !g || !sigma) return LBF_EINVAL;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    return lbf_gmres_impl(pl, g, sigma, a, x0, iters, rel_res, (cudaStream_t)stream);
+}
+
+int lbf_evaluate(lbf_plan *pl, const double *sigma, const double *a, int64_t T,
+                 const double *targets, double *u, lbf_stream_t stream)
+{
+    if (!pl || !sigma || T < 0 || (T > 0 && (!targets || !u))) return LBF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = lbf_permute_in(pl, sigma, pl->tin, 0, s);
+    if (rc) return rc;
+    return lbf_evaluate_impl(pl, pl->tin, a, T, targets, u, s);
+}
+
+int lbf_green_sum(int64_t T, const double *t, int64_t S, const double *p, const double *gamma,
+                  double *out, lbf_stream_t stream)
+{
+    if (T < 0 || S < 0 || (T > 0 && (!t || !out)) || (S > 0 && (!p || !gamma))) return LBF_EINVAL;
+    return lbf_green_sum_impl(T, t, S, p, gamma, out, (cudaStream_t)stream);
+}
+
+int lbf_sync_status(lbf_plan *pl, lbf_stream_t stream)
+{
+    if (!pl) return LBF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(pl->host_status, pl->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LBF_ECUDA;
+    int st = *pl->host_status;
+    if (st & LBF_DEV_POLE) return LBF_EPOLE;
+    if (st & LBF_DEV_TIMEOUT) return LBF_ETIMEOUT;
+    if (st & 8) return LBF_EDEPTH;
+    return LBF_OK;
+}
+
+int64_t lbf_launch_count(void) { return g_lbf_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// Internal declarations of liblbfmm (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/lbfmm.h"
+
+#define LBF_PI 3.14159265358979323846
+#define LBF_MAX_TERMS 64  // expansion terms p + 1 supported by the kernels
+#define LBF_MAX_LEVELS 31
+
+// Per-process launch counter (lbf_launch_count).
+extern std::atomic<int64_t> g_lbf_launches;
+
+#define LBF_LAUNCH(kernel, grid, block, smem, stream, ...)                 \
+    do {                                                                   \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);        \
+        g_lbf_launches.fetch_add(1, std::memory_order_relaxed);            \
+    } while (0)
+
+#define LBF_CUDA(call)                                                     \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return LBF_ECUDA;                           \
+    } while (0)
+
+#define LBF_CHECK_LAUNCH() LBF_CUDA(cudaGetLastError())
+
+// Device status word bits (lbf_sync_status).
+#define LBF_DEV_POLE 1
+#define LBF_DEV_TIMEOUT 2
+
+__host__ __device__ static inline int64_t lbf_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Bump allocator over the caller's workspace (256-byte aligned slices).
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, off = 0;
+    bool overflow = false;
+    void *take(size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        if (off > cap) overflow = true;
+        return overflow ? nullptr : p;
+    }
+    template <class T> T *get(int64_t n) { return (T *)take(sizeof(T) * (size_t)(n > 0 ? n : 1)); }
+};
+
+// Adaptive quadtree (boxes numbered level by level, Morton order within a level).
+struct Tree {
+    int64_t cap = 0, nbox = 0, nleaf = 0;
+    int nlev = 0;
+    int64_t lev_start[LBF_MAX_LEVELS + 2] = {};
+    double xmin = 0, ymin = 0, L = 1;  // bounding square
+    int32_t *level, *ix, *iy, *parent, *child0, *nchild, *begin, *end;
+    int32_t *leaves;                    // ids of the leaves, ascending
+    // interaction lists
+    int32_t *coll;                      // 9 colleagues per box (-1 = none)
+    int32_t *vlist, *nv;                // V: up to 27 per box
+    int32_t *coarse, *ncoarse;          // shallower leaves touching the box: up to 8
+    int32_t *xlist, *nx;                // X: up to 16 per box
+    int32_t *u_ptr, *u_idx;             // U (leaves only), CSR over boxes
+    int32_t *w_ptr, *w_idx;             // W (leaves only), CSR over boxes
+    int64_t u_cap = 0, w_cap = 0, u_len = 0, w_len = 0;
+};
+
+struct GmresState;  // device-side scalars (lbf_krylov.cu)
+
+struct lbf_plan {
+    int64_t N = 0;
+    int M = 0;
+    int64_t n = 0;  // unknowns of the bordered system, N + M
+    lbf_options opt{};
+    int P = 0;      // expansion terms p + 1
+    Arena arena;
+    int64_t *island_ptr_h = nullptr;  // host copy
+    int64_t *island_ptr = nullptr;    // device copy
+    // per node, sorted (Morton) order
+    double2 *xi = nullptr, *w = nullptr;
+    double *dself = nullptr, *beta = nullptr;
+    int32_t *perm = nullptr;  // sorted -> caller index
+    int32_t *rank = nullptr;  // caller index -> sorted
+    double *centres = nullptr;  // M x 3 after rotation
+    double rot[9];
+    int has_rot = 0;
+    double *rot_d = nullptr;  // device copy of rot
+    // translation-operator tables (filled on the host at plan time)
+    double *tab_binom = nullptr;   // C(n, k), n < 2*LBF_MAX_TERMS, k < LBF_MAX_TERMS
+    double2 *tab_m2m = nullptr;    // 4 child offsets x LBF_MAX_TERMS^2
+    double2 *tab_l2l = nullptr;    // 4 child offsets x LBF_MAX_TERMS^2
+    double2 *tab_tpow = nullptr;   // 49 same-level offsets x (LBF_MAX_TERMS + 1) powers
+    Tree tree;
+    // FMM work
+    double2 *q = nullptr, *mpole = nullptr, *local = nullptr;
+    double *v = nullptr;        // (I + K - I) sigma = K sigma, doubled scaling
+    double *bsig = nullptr;     // scalar beta . sigma
+    double *red = nullptr;      // reduction partials
+    unsigned int *red_count = nullptr;
+    // border
+    double *E = nullptr;        // M x N, E[m*N + i] = 2 G(x_i, c_m), rows in sorted order
+    double *Sinv = nullptr;     // M x M inverse Schur complement
+    double *fvec = nullptr, *yvec = nullptr;  // M-vectors
+    // generic N+M vectors for lbf_apply / gmres
+    double *tin = nullptr, *tout = nullptr;
+    // gmres
+    double *V = nullptr, *H = nullptr, *gw = nullptr, *gx = nullptr, *gb = nullptr;
+    double *gpart = nullptr;
+    GmresState *gs = nullptr;
+    int64_t ldv = 0;  // stride between basis vectors
+    int mdot_blocks = 0;
+    char *region = nullptr;      // GMRES basis, or plan-creation temporaries
+    int *dev_status = nullptr;
+    int *host_status = nullptr;  // pinned
+    double *host_scalars = nullptr;  // pinned
+};
+
+// ---- layout ------------------------------------------------------------------
+void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &opt, int64_t box_cap);
+
+// ---- geometry (lbf_geometry.cu) ----------------------------------------------
+int lbf_geometry_build(lbf_plan *pl, const double *x, const double *dx, const double *d2x,
+                       const double *centres, cudaStream_t s, double2 *xi_o, double *x3_o,
+                       double2 *w_o, double *d_o, double *b_o);
+int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const double2 *w_o,
+                        const double *d_o, const double *b_o);
+int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double *x3_o, double *scratch);
+int lbf_geometry_out_impl(const lbf_plan *pl, double *xi, double *normal, double *weight,
+                          double *arc, cudaStream_t s);
+
+// ---- tree (lbf_tree.cu) --------------------------------------------------------
+int lbf_tree_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, uint64_t *keys,
+                   uint64_t *keys_alt, int32_t *perm_alt, int32_t *scratch, int64_t scratch_len,
+                   int64_t *box_needed);
+int lbf_lists_build(lbf_plan *pl, cudaStream_t s, int32_t *scratch, int64_t scratch_len,
+                    int64_t *box_needed);
+int lbf_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *scratch, int64_t scratch_len,
+                 cudaStream_t s);  // exclusive scan, out may alias in
+
+// ---- FMM / direct operator (lbf_fmm.cu) -----------------------------------------
+// v = 2 [ (1/2pi) Im sum_{j!=i} q_j/(xi_j - xi_i) + d_i sigma_i + beta.sigma ]   (sorted order)
+int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s);
+int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,
+                      const double *t, double *u, cudaStream_t s);
+int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p,
+                       const double *gamma, double *out, cudaStream_t s);
+
+// ---- border / krylov (lbf_krylov.cu) -----------------------------------------------
+int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, const int *gate,
+                        cudaStream_t s);
+int lbf_precondition_rhs(lbf_plan *pl, const double *g2_sorted, double *out, cudaStream_t s);
+int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
+                   int *iters, double *rel_res, cudaStream_t s);
+int lbf_dot(lbf_plan *pl, const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
+int lbf_permute_in(lbf_plan *pl, const double *in_caller, double *out_sorted, int with_a,
+                   cudaStream_t s);
+int lbf_permute_out(lbf_plan *pl, const double *in_sorted, double *out_caller, int with_a,
+                    cudaStream_t s);

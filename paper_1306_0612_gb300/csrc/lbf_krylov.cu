@@ -1,0 +1,553 @@
+// Bordered operator, block preconditioner and device-resident restarted GMRES
+// (Sec. 5, Eq. matrix_eqns and matrix_eqns_c).
+//
+// Unknowns live in the plan's sorted (Morton) node order: x = [sigma (N); a (M)].
+//   A x       = [sigma + v + E a ; F sigma + D a],   v = K sigma (lbf_apply_K)
+//   P         = [[I, E], [F, D]],  S = D - F E
+//   P^-1 r    : z_a = S^-1 (r_a - F r_sigma),  z_sigma = r_sigma - E z_a
+// The preconditioned operator is applied in the algebraically equal form
+//   P^-1 A x  = x + P^-1 [v; 0] = [sigma + v + E y ; a - y],  y = S^-1 F v,
+// which needs one pass over E per matvec instead of two.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "lbf_internal.cuh"
+
+struct GmresState {
+    int go;         // 1 while Arnoldi steps of the current cycle may run (kernel gate)
+    int j;          // Arnoldi columns completed in the current cycle
+    int it;         // iterations completed in total
+    int converged;  // 1 once the preconditioned residual reached tol
+    int maxit, m;
+    double tol, bnorm, beta, resid, inv;
+};
+
+namespace {
+
+constexpr int kRowsPerChunk = 1024;
+constexpr int kDotBlocks = 152 * 2;
+
+__device__ __forceinline__ bool gate_closed(const int *gate) { return gate && *gate == 0; }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void k_permute_in(int64_t N, int M, const int32_t *__restrict__ perm,
+                             const double *__restrict__ in, double *__restrict__ out, int with_a)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) out[i] = in[perm[i]];
+    else if (with_a && i < N + M) out[i] = in[i];
+}
+
+__global__ void k_permute_out(int64_t N, int M, const int32_t *__restrict__ perm,
+                              const double *__restrict__ in, double *__restrict__ out, int with_a)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) out[perm[i]] = in[i];
+    else if (with_a && i < N + M) out[i] = in[i];
+}
+
+// F u: the unweighted constraint sums over islands 1..M-1 (Eq. disc_constr), in a
+// fixed order (caller order within the island).  Row M-1 of F is zero.
+__global__ void k_island_sums(int M, const int64_t *__restrict__ ptr, const int32_t *__restrict__ rank,
+                              const double *__restrict__ u, double scale, double *__restrict__ out,
+                              const int *gate)
+{
+    if (gate_closed(gate)) return;
+    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= M) return;
+    double s = 0.0;
+    if (r < M - 1)
+        for (int64_t j = ptr[r + 1] + lane; j < ptr[r + 2]; j += 32) s += u[rank[j]];
+    s = warp_sum(s);
+    if (lane == 0) out[r] = scale * s;
+}
+
+// y = alpha S^-1 f (one warp per row)
+__global__ void k_small_gemv(int M, const double *__restrict__ A, const double *__restrict__ f,
+                             double alpha, double *__restrict__ y, const int *gate)
+{
+    if (gate_closed(gate)) return;
+    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= M) return;
+    double s = 0.0;
+    for (int m = lane; m < M; m += 32) s = fma(A[(int64_t)r * M + m], f[m], s);
+    s = warp_sum(s);
+    if (lane == 0) y[r] = alpha * s;
+}
+
+// out_i = x_i + v_i + s * sum_m E[m][i] c_m   (v nullable)
+__global__ void k_esum(int64_t N, int M, const double *__restrict__ E, const double *__restrict__ x,
+                       const double *__restrict__ v, const double *__restrict__ c, double s,
+                       double *__restrict__ out, const int *gate)
+{
+    if (gate_closed(gate)) return;
+    extern __shared__ double sc[];
+    for (int m = threadIdx.x; m < M; m += blockDim.x) sc[m] = c[m];
+    __syncthreads();
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double acc = 0.0;
+    for (int m = 0; m < M; m++) acc = fma(E[(int64_t)m * N + i], sc[m], acc);
+    out[i] = x[i] + (v ? v[i] : 0.0) + s * acc;
+}
+
+__global__ void k_add(int64_t n, const double *__restrict__ x, const double *__restrict__ v,
+                      double *__restrict__ out, const int *gate)
+{
+    if (gate_closed(gate)) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = x[i] + v[i];
+}
+
+// a-rows of the bordered operator.
+//   mode 0 (A x):      out_r = f_r (r < M-1), out_{M-1} = sum_m a_m
+//   mode 1 (P^-1 A x): out_m = a_m - y_m
+__global__ void k_arows(int M, int mode, const double *__restrict__ a, const double *__restrict__ f,
+                        double *__restrict__ out, const int *gate)
+{
+    if (gate_closed(gate)) return;
+    int m = threadIdx.x;
+    if (mode == 0) {
+        if (m < M - 1) {
+            for (int r = m; r < M - 1; r += blockDim.x) out[r] = f[r];
+        }
+        if (m == 0) {
+            double s = 0.0;
+            for (int k = 0; k < M; k++) s += a[k];
+            out[M - 1] = s;
+        }
+    } else {
+        for (int r = m; r < M; r += blockDim.x) out[r] = a[r] - f[r];
+    }
+}
+
+// ---- GMRES kernels --------------------------------------------------------------------
+
+// Partial dot products of w with V[0..nv) over one block's row chunk; the last block
+// to finish sums the partials in block order into h.
+__device__ void dots_phase(const double *V, int64_t ldv, int nv, const double *ws, int rows,
+                           int64_t row0, double *acc)
+{
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = wid; k < nv; k += nw) {
+        const double *vk = V + (int64_t)k * ldv + row0;
+        double s = 0.0;
+        for (int r = lane; r < rows; r += 32) s = fma(vk[r], ws[r], s);
+        s = warp_sum(s);
+        if (lane == 0) acc[k] += s;
+    }
+}
+
+__device__ bool finish_block(unsigned *count)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(count, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return last;
+}
+
+// mode 0: h = V^T w (columns 0..j)
+// mode 1: w -= V h;  h2 = V^T w
+// mode 2: w -= V h2; ||w||^2 -> Hessenberg column j, Givens rotation, convergence test
+__global__ void k_arnoldi(int64_t n, const double *__restrict__ V, int64_t ldv, double *w,
+                          double *part, unsigned *count, double *hbuf, double *H, double *cs,
+                          double *sn, double *gv, GmresState *st, int mode)
+{
+    if (st->go == 0) return;
+    extern __shared__ double sh[];
+    int m = st->m;
+    int j = st->j;
+    int nv = j + 1;
+    double *ws = sh;                   // kRowsPerChunk
+    double *acc = sh + kRowsPerChunk;  // m + 2
+    double *hc = acc + (m + 2);        // m + 1 (coefficients for the update)
+    for (int k = threadIdx.x; k < m + 2; k += blockDim.x) acc[k] = 0.0;
+    const double *hin = (mode == 1) ? hbuf : hbuf + (m + 1);
+    if (mode >= 1)
+        for (int k = threadIdx.x; k < nv; k += blockDim.x) hc[k] = hin[k];
+    __syncthreads();
+    int64_t per = lbf_cdiv(n, gridDim.x);
+    int64_t r0 = blockIdx.x * per, r1 = std::min<int64_t>(n, r0 + per);
+    double nrm = 0.0;
+    for (int64_t c0 = r0; c0 < r1; c0 += kRowsPerChunk) {
+        int rows = (int)std::min<int64_t>(kRowsPerChunk, r1 - c0);
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            double x = w[c0 + r];
+            if (mode >= 1) {
+                for (int k = 0; k < nv; k++) x = fma(-hc[k], V[(int64_t)k * ldv + c0 + r], x);
+                w[c0 + r] = x;
+            }
+            ws[r] = x;
+            nrm = fma(x, x, nrm);
+        }
+        __syncthreads();
+        if (mode <= 1) dots_phase(V, ldv, nv, ws, rows, c0, acc);
+        __syncthreads();
+    }
+    if (mode == 2) {
+        nrm = warp_sum(nrm);
+        __shared__ double wsum[32];
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += wsum[k];
+            acc[0] = t;
+        }
+        __syncthreads();
+    }
+    int nout = (mode == 2) ? 1 : nv;
+    for (int k = threadIdx.x; k < nout; k += blockDim.x) part[(int64_t)blockIdx.x * (m + 2) + k] = acc[k];
+    if (!finish_block(count)) return;
+    // last block: fixed-order reduction over blocks
+    for (int k = threadIdx.x; k < nout; k += blockDim.x) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; b++) s += ((volatile double *)part)[(int64_t)b * (m + 2) + k];
+        if (mode == 0) hbuf[k] = s;
+        else if (mode == 1) hbuf[(m + 1) + k] = s;
+        else acc[0] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *count = 0u;
+        if (mode == 2) {
+            // Hessenberg column j: h = h1 + h2, H[j+1][j] = ||w||
+            double *Hj = H + (int64_t)j * (m + 1);
+            for (int k = 0; k <= j; k++) Hj[k] = hbuf[k] + hbuf[(m + 1) + k];
+            double hn = sqrt(acc[0]);
+            Hj[j + 1] = hn;
+            // apply the previous Givens rotations, then a new one zeroing H[j+1][j]
+            for (int k = 0; k < j; k++) {
+                double a = Hj[k], b = Hj[k + 1];
+                Hj[k] = cs[k] * a + sn[k] * b;
+                Hj[k + 1] = -sn[k] * a + cs[k] * b;
+            }
+            double a = Hj[j], b = Hj[j + 1];
+            double rr = hypot(a, b);
+            double c = rr > 0.0 ? a / rr : 1.0, s = rr > 0.0 ? b / rr : 0.0;
+            cs[j] = c;
+            sn[j] = s;
+            Hj[j] = rr;
+            Hj[j + 1] = 0.0;
+            gv[j + 1] = -s * gv[j];
+            gv[j] = c * gv[j];
+            st->resid = fabs(gv[j + 1]);
+            st->it += 1;
+            st->j = j + 1;
+            st->inv = hn > 0.0 ? 1.0 / hn : 0.0;
+            bool conv = st->resid <= st->tol * st->bnorm;
+            if (conv) st->converged = 1;
+            if (conv || st->it >= st->maxit || j + 1 >= m || !(hn > 0.0)) st->go = 0;
+        }
+    }
+}
+
+// V[j] = w * inv (j = st->j after the Arnoldi step)
+__global__ void k_scale_next(int64_t n, const double *__restrict__ w, double *V, int64_t ldv,
+                             const GmresState *st)
+{
+    if (st->go == 0) return;
+    int j = st->j;
+    double inv = st->inv;
+    double *vj = V + (int64_t)j * ldv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        vj[i] = w[i] * inv;
+}
+
+// end of a cycle: y = H^-1 g (upper triangular, j columns), x += V y
+__global__ void k_solve_y(const double *H, const double *gv, double *y, GmresState *st)
+{
+    if (threadIdx.x != 0) return;
+    int m = st->m, j = st->j;
+    for (int i = j - 1; i >= 0; i--) {
+        double s = gv[i];
+        for (int k = i + 1; k < j; k++) s -= H[(int64_t)k * (m + 1) + i] * y[k];
+        y[i] = s / H[(int64_t)i * (m + 1) + i];
+    }
+}
+
+__global__ void k_xupdate(int64_t n, const double *__restrict__ V, int64_t ldv,
+                          const double *__restrict__ y, const GmresState *st, double *x)
+{
+    int j = st->j;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = x[i];
+        for (int k = 0; k < j; k++) s = fma(y[k], V[(int64_t)k * ldv + i], s);
+        x[i] = s;
+    }
+}
+
+// r = b - Ax (Ax nullable = 0) into V[0], ||r||^2 partials; the last block starts a
+// new cycle: beta = ||r||, g = (beta, 0, ...), j = 0, go = (beta > tol ||b||).
+// With init != 0 it also records ||b|| (the first call, x = 0 or the initial guess).
+__global__ void k_restart(int64_t n, const double *__restrict__ b, const double *__restrict__ Ax,
+                          double *V, double *part, unsigned *count, double *gv, GmresState *st,
+                          int init, const double *__restrict__ bn)
+{
+    __shared__ double wsum[32];
+    double nrm = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double r = b[i] - (Ax ? Ax[i] : 0.0);
+        V[i] = r;
+        nrm = fma(r, r, nrm);
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += wsum[k];
+        part[blockIdx.x] = t;
+    }
+    if (!finish_block(count)) return;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (unsigned k = 0; k < gridDim.x; k++) s += ((volatile double *)part)[k];
+        *count = 0u;
+        double beta = sqrt(s);
+        if (init) st->bnorm = *bn;
+        st->beta = beta;
+        st->resid = beta;
+        st->j = 0;
+        st->inv = beta > 0.0 ? 1.0 / beta : 0.0;
+        for (int k = 0; k <= st->m; k++) gv[k] = 0.0;
+        gv[0] = beta;
+        bool conv = beta <= st->tol * st->bnorm;
+        st->converged = conv ? 1 : 0;
+        st->go = (!conv && st->it < st->maxit) ? 1 : 0;
+    }
+}
+
+__global__ void k_scale_first(int64_t n, double *V, const GmresState *st)
+{
+    double inv = st->inv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        V[i] *= inv;
+}
+
+// ||v||^2 with a fixed-order reduction (single block)
+__global__ void k_norm2(int64_t n, const double *__restrict__ v, double *out)
+{
+    __shared__ double wsum[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(v[i], v[i], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += wsum[k];
+        *out = sqrt(t);
+    }
+}
+
+__global__ void k_init_state(GmresState *st, int m, int maxit, double tol)
+{
+    st->go = 0; st->j = 0; st->it = 0; st->converged = 0;
+    st->m = m; st->maxit = maxit; st->tol = tol;
+    st->bnorm = 0; st->beta = 0; st->resid = 0; st->inv = 0;
+}
+
+__global__ void k_scale(int64_t n, double alpha, double *p)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] *= alpha;
+}
+
+__global__ void k_fill(double *p, int64_t n, double v)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+int lbf_permute_in(lbf_plan *pl, const double *in_caller, double *out_sorted, int with_a,
+                   cudaStream_t s)
+{
+    int64_t n = pl->N + (with_a ? pl->M : 0);
+    LBF_LAUNCH(k_permute_in, lbf_cdiv(n, 256), 256, 0, s, pl->N, pl->M, pl->perm, in_caller,
+               out_sorted, with_a);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+int lbf_permute_out(lbf_plan *pl, const double *in_sorted, double *out_caller, int with_a,
+                    cudaStream_t s)
+{
+    int64_t n = pl->N + (with_a ? pl->M : 0);
+    LBF_LAUNCH(k_permute_out, lbf_cdiv(n, 256), 256, 0, s, pl->N, pl->M, pl->perm, in_sorted,
+               out_caller, with_a);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+int lbf_krylov_init_attrs()
+{
+    LBF_CUDA(cudaFuncSetAttribute(k_esum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    return LBF_OK;
+}
+
+static int esum(lbf_plan *pl, const double *x, const double *v, const double *c, double sc,
+                double *out, const int *gate, cudaStream_t s)
+{
+    size_t smem = sizeof(double) * (size_t)pl->M;
+    LBF_LAUNCH(k_esum, lbf_cdiv(pl->N, 256), 256, smem, s, pl->N, pl->M, pl->E, x, v, c, sc, out,
+               gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+static int island_sums(lbf_plan *pl, const double *u, double scale, double *out, const int *gate,
+                       cudaStream_t s)
+{
+    LBF_LAUNCH(k_island_sums, lbf_cdiv((int64_t)pl->M * 32, 256), 256, 0, s, pl->M, pl->island_ptr,
+               pl->rank, u, scale, out, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+static int small_gemv(lbf_plan *pl, const double *f, double alpha, double *y, const int *gate,
+                      cudaStream_t s)
+{
+    LBF_LAUNCH(k_small_gemv, lbf_cdiv((int64_t)pl->M * 32, 256), 256, 0, s, pl->M, pl->Sinv, f,
+               alpha, y, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, const int *gate,
+                        cudaStream_t s)
+{
+    int64_t N = pl->N;
+    int M = pl->M;
+    int rc = lbf_apply_K(pl, in, pl->v, gate, s);
+    if (rc) return rc;
+    if (op == LBF_OP_K_ONLY) {
+        LBF_LAUNCH(k_add, lbf_cdiv(N, 256), 256, 0, s, N, in, pl->v, out, gate);
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    }
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    if (op == LBF_OP_FULL) {
+        if ((rc = island_sums(pl, in, 1.0, pl->fvec, gate, s))) return rc;
+        if ((rc = esum(pl, in, pl->v, in + N, 1.0, out, gate, s))) return rc;
+        LBF_LAUNCH(k_arows, 1, 256, 0, s, M, 0, in + N, pl->fvec, out + N, gate);
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    }
+    // preconditioned: y = S^-1 F v; out = [sigma + v + E y ; a - y]
+    if ((rc = island_sums(pl, pl->v, 1.0, pl->fvec, gate, s))) return rc;
+    if ((rc = small_gemv(pl, pl->fvec, 1.0, pl->yvec, gate, s))) return rc;
+    if ((rc = esum(pl, in, pl->v, pl->yvec, 1.0, out, gate, s))) return rc;
+    LBF_LAUNCH(k_arows, 1, 256, 0, s, M, 1, in + N, pl->yvec, out + N, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// out = P^-1 [g2; 0]:  z_a = -S^-1 F g2,  z_sigma = g2 - E z_a
+int lbf_precondition_rhs(lbf_plan *pl, const double *g2_sorted, double *out, cudaStream_t s)
+{
+    int rc;
+    if ((rc = island_sums(pl, g2_sorted, 1.0, pl->fvec, nullptr, s))) return rc;
+    if ((rc = small_gemv(pl, pl->fvec, -1.0, out + pl->N, nullptr, s))) return rc;
+    if ((rc = esum(pl, g2_sorted, nullptr, out + pl->N, -1.0, out, nullptr, s))) return rc;
+    return LBF_OK;
+}
+
+static int read_state(lbf_plan *pl, GmresState *h, cudaStream_t s)
+{
+    LBF_CUDA(cudaMemcpyAsync(pl->host_scalars, pl->gs, sizeof(GmresState), cudaMemcpyDeviceToHost, s));
+    LBF_CUDA(cudaStreamSynchronize(s));
+    memcpy(h, pl->host_scalars, sizeof(GmresState));
+    return LBF_OK;
+}
+
+int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
+                   int *iters, double *rel_res, cudaStream_t s)
+{
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    int64_t N = pl->N, n = pl->n;
+    int m = pl->opt.restart;
+    int rc;
+    double *b = pl->gb, *x = pl->gx, *w = pl->gw, *V = pl->V;
+    int64_t ldv = pl->ldv;
+    int nblk = pl->mdot_blocks;
+    double *hbuf = pl->H + (int64_t)(m + 1) * m;   // 2 (m + 1)
+    double *cs = hbuf + 2 * (m + 1), *sn = cs + m, *gv = sn + m, *y = gv + (m + 1);
+    unsigned *count = pl->red_count + 1;
+    // b = P^-1 [2 g; 0] in sorted order (tin holds the permuted data)
+    if ((rc = lbf_permute_in(pl, g, pl->tin, 0, s))) return rc;
+    // the doubled right-hand side 2 g of Eq. disc_sphere
+    LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, pl->tin);
+    LBF_CHECK_LAUNCH();
+    if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
+    LBF_LAUNCH(k_init_state, 1, 1, 0, s, pl->gs, m, pl->opt.maxit, pl->opt.tol);
+    LBF_LAUNCH(k_norm2, 1, 1024, 0, s, n, b, pl->bsig + 1);
+    LBF_CHECK_LAUNCH();
+    const double *Ax = nullptr;
+    if (x0) {
+        if ((rc = lbf_permute_in(pl, x0, x, 1, s))) return rc;
+        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s))) return rc;
+        Ax = w;
+    } else {
+        LBF_LAUNCH(k_fill, lbf_cdiv(n, 256), 256, 0, s, x, n, 0.0);
+        LBF_CHECK_LAUNCH();
+    }
+    LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1, pl->bsig + 1);
+    LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
+    LBF_CHECK_LAUNCH();
+    size_t smem = sizeof(double) * (size_t)(kRowsPerChunk + 2 * (m + 2));
+    GmresState hs;
+    for (;;) {
+        if ((rc = read_state(pl, &hs, s))) return rc;
+        if (hs.converged || hs.it >= hs.maxit || hs.go == 0) break;
+        int steps = std::min(m, hs.maxit - hs.it);
+        for (int k = 0; k < steps; k++) {
+            // w = P^-1 A v_j  (j read on the device)
+            // the operator reads V[j]: use the pointer of column k (j == k within a cycle)
+            const double *vj = V + (int64_t)k * ldv;
+            if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, vj, w, &pl->gs->go, s))) return rc;
+            for (int mode = 0; mode < 3; mode++)
+                LBF_LAUNCH(k_arnoldi, nblk, 256, smem, s, n, V, ldv, w, pl->gpart, count, hbuf,
+                           pl->H, cs, sn, gv, pl->gs, mode);
+            LBF_LAUNCH(k_scale_next, nblk, 256, 0, s, n, w, V, ldv, pl->gs);
+            LBF_CHECK_LAUNCH();
+        }
+        // cycle end: x += V y
+        LBF_LAUNCH(k_solve_y, 1, 32, 0, s, pl->H, gv, y, pl->gs);
+        LBF_LAUNCH(k_xupdate, nblk, 256, 0, s, n, V, ldv, y, pl->gs, x);
+        LBF_CHECK_LAUNCH();
+        if ((rc = read_state(pl, &hs, s))) return rc;
+        if (hs.converged || hs.it >= hs.maxit) break;
+        // restart from the true preconditioned residual
+        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s))) return rc;
+        LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0, pl->bsig + 1);
+        LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
+        LBF_CHECK_LAUNCH();
+    }
+    if ((rc = read_state(pl, &hs, s))) return rc;
+    // outputs in the caller's order
+    LBF_LAUNCH(k_permute_out, lbf_cdiv(N, 256), 256, 0, s, N, pl->M, pl->perm, x, sigma, 0);
+    LBF_CHECK_LAUNCH();
+    if (a) LBF_CUDA(cudaMemcpyAsync(a, x + N, sizeof(double) * pl->M, cudaMemcpyDeviceToDevice, s));
+    LBF_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = hs.it;
+    if (rel_res) *rel_res = hs.bnorm > 0 ? hs.resid / hs.bnorm : 0.0;
+    return hs.converged ? LBF_OK : LBF_NOCONV;
+}
+
+int lbf_gmres_kernels_smem(int m) { return (int)(sizeof(double) * (kRowsPerChunk + 2 * (m + 2))); }
+int lbf_gmres_blocks() { return kDotBlocks; }

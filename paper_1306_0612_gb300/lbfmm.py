@@ -1,0 +1,275 @@
+"""Thin Python binding of liblbfmm (include/lbfmm.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors (float64, contiguous); PyTorch
+supplies device memory and the current stream.  The functions keep the C
+names.  If the compiled library is missing, loading fails loudly: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from .build import LIB
+
+LBF_OK = 0
+LBF_NOCONV = 1
+LBF_EINVAL = -1
+LBF_EPOLE = -2
+LBF_EDEPTH = -3
+LBF_EWORKSPACE = -4
+LBF_ECUDA = -5
+LBF_ETIMEOUT = -6
+LBF_ENOTBUILT = -7
+
+LBF_MATVEC_FMM = 0
+LBF_MATVEC_DIRECT = 1
+LBF_OP_FULL = 0
+LBF_OP_K_ONLY = 1
+LBF_OP_PRECONDITIONED = 2
+
+
+class lbf_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("p", C.c_int),
+                ("leaf_size", C.c_int), ("max_depth", C.c_int), ("matvec", C.c_int),
+                ("border", C.c_int), ("box_capacity", C.c_int64)]
+
+
+class LbfError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {lbf_status_string(status)} ({status})")
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def load():
+    """Load the in-tree liblbfmm.so (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"liblbfmm is not built ({LIB}); run __graft_entry__.build()")
+        lib = C.CDLL(LIB)
+        i64 = C.c_int64
+        sig = {
+            "lbf_default_options": (C.c_int, [C.POINTER(lbf_options)]),
+            "lbf_status_string": (C.c_char_p, [C.c_int]),
+            "lbf_workspace_size": (C.c_int, [C.c_int, _P, C.POINTER(lbf_options), C.POINTER(C.c_size_t)]),
+            "lbf_plan_create": (C.c_int, [C.POINTER(_P), C.c_int, _P, _P, _P, _P, _P, _P,
+                                          C.POINTER(lbf_options), _P, C.c_size_t,
+                                          C.POINTER(i64), _P]),
+            "lbf_plan_destroy": (C.c_int, [_P]),
+            "lbf_plan_info": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+            "lbf_geometry_out": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+            "lbf_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+            "lbf_gmres_solve": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+            "lbf_evaluate": (C.c_int, [_P, _P, _P, i64, _P, _P, _P]),
+            "lbf_green_sum": (C.c_int, [i64, _P, i64, _P, _P, _P, _P]),
+            "lbf_tree_export": (C.c_int, [_P, _P, _P, _P]),
+            "lbf_list_export": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(i64), _P]),
+            "lbf_sync_status": (C.c_int, [_P, _P]),
+            "lbf_launch_count": (i64, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return ["lbf_default_options", "lbf_status_string", "lbf_workspace_size", "lbf_plan_create",
+            "lbf_plan_destroy", "lbf_plan_info", "lbf_geometry_out", "lbf_apply",
+            "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
+            "lbf_list_export", "lbf_sync_status", "lbf_launch_count"]
+
+
+def lbf_status_string(status: int) -> str:
+    try:
+        return load().lbf_status_string(int(status)).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return str(status)
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        raise LbfError(rc, what)
+    return rc
+
+
+def _dptr(t: torch.Tensor | None, n: int | None = None, name: str = "array"):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name}: need a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name}: expected {n} entries, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def lbf_default_options(**kw) -> lbf_options:
+    o = lbf_options()
+    _check(load().lbf_default_options(C.byref(o)), "lbf_default_options")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def lbf_workspace_size(island_ptr: np.ndarray, opt: lbf_options) -> int:
+    ptr = np.ascontiguousarray(island_ptr, dtype=np.int64)
+    out = C.c_size_t(0)
+    _check(load().lbf_workspace_size(len(ptr) - 1, ptr.ctypes.data_as(_P), C.byref(opt),
+                                     C.byref(out)), "lbf_workspace_size")
+    return int(out.value)
+
+
+class Plan:
+    """A plan and the torch-owned workspace it lives in."""
+
+    def __init__(self, handle, workspace, N, M, opt):
+        self.handle = handle
+        self.workspace = workspace
+        self.N, self.M, self.opt = N, M, opt
+
+    def info(self):
+        return lbf_plan_info(self)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.lbf_plan_destroy(self.handle)
+            self.handle = None
+
+
+def lbf_plan_create(island_ptr, x, dx, d2x, centres, pole_rotation=None, opt=None, stream=None,
+                    device=None) -> Plan:
+    """Build a plan (synchronous).  Retries with a larger box capacity when the
+    quadtree outgrows the first workspace estimate."""
+    lib = load()
+    opt = opt or lbf_default_options()
+    ptr = np.ascontiguousarray(island_ptr, dtype=np.int64)
+    M = len(ptr) - 1
+    N = int(ptr[-1])
+    rot = None if pole_rotation is None else np.ascontiguousarray(pole_rotation, dtype=np.float64)
+    dev = x.device if device is None else device
+    for _ in range(6):
+        nbytes = lbf_workspace_size(ptr, opt)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        h = C.c_void_p()
+        need = C.c_int64(0)
+        rc = lib.lbf_plan_create(C.byref(h), M, ptr.ctypes.data_as(_P), _dptr(x, 3 * N, "x"),
+                                 _dptr(dx, 3 * N, "dx"), _dptr(d2x, 3 * N, "d2x"),
+                                 _dptr(centres, 3 * M, "centres"),
+                                 None if rot is None else rot.ctypes.data_as(_P), C.byref(opt),
+                                 C.c_void_p(ws.data_ptr()), C.c_size_t(nbytes), C.byref(need),
+                                 _stream(stream))
+        if rc == LBF_EWORKSPACE and need.value > opt.box_capacity:
+            opt = lbf_options.from_buffer_copy(opt)
+            opt.box_capacity = int(need.value)
+            del ws
+            continue
+        _check(rc, "lbf_plan_create")
+        return Plan(h, ws, N, M, opt)
+    raise LbfError(LBF_EWORKSPACE, "lbf_plan_create")
+
+
+def lbf_plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(load().lbf_plan_destroy(plan.handle), "lbf_plan_destroy")
+        plan.handle = None
+
+
+def lbf_plan_info(plan: Plan) -> dict:
+    N, M, nb, nl, dep, p = (C.c_int64(), C.c_int(), C.c_int64(), C.c_int64(), C.c_int(), C.c_int())
+    _check(load().lbf_plan_info(plan.handle, C.byref(N), C.byref(M), C.byref(nb), C.byref(nl),
+                                C.byref(dep), C.byref(p)), "lbf_plan_info")
+    return dict(N=N.value, M=M.value, nbox=nb.value, nleaf=nl.value, depth=dep.value, p=p.value)
+
+
+def lbf_geometry_out(plan: Plan, xi=None, normal=None, weight=None, arc_weight=None, stream=None):
+    N = plan.N
+    _check(load().lbf_geometry_out(plan.handle, _dptr(xi, 2 * N, "xi"), _dptr(normal, 2 * N, "normal"),
+                                   _dptr(weight, 2 * N, "weight"), _dptr(arc_weight, N, "arc_weight"),
+                                   _stream(stream)), "lbf_geometry_out")
+
+
+def lbf_apply(plan: Plan, op: int, inp: torch.Tensor, out: torch.Tensor, stream=None):
+    n = plan.N if op == LBF_OP_K_ONLY else plan.N + plan.M
+    _check(load().lbf_apply(plan.handle, int(op), _dptr(inp, n, "in"), _dptr(out, n, "out"),
+                            _stream(stream)), "lbf_apply")
+
+
+def lbf_gmres_solve(plan: Plan, g: torch.Tensor, sigma: torch.Tensor, a: torch.Tensor | None = None,
+                    x0: torch.Tensor | None = None, stream=None):
+    """Returns (status, iterations, relative residual); status LBF_NOCONV (> 0) if maxit hit."""
+    it, rr = C.c_int(0), C.c_double(0.0)
+    rc = load().lbf_gmres_solve(plan.handle, _dptr(g, plan.N, "g"), _dptr(sigma, plan.N, "sigma"),
+                                _dptr(a, plan.M, "a"), _dptr(x0, plan.N + plan.M, "x0"),
+                                C.byref(it), C.byref(rr), _stream(stream))
+    _check(rc, "lbf_gmres_solve")
+    return rc, it.value, rr.value
+
+
+def lbf_evaluate(plan: Plan, sigma: torch.Tensor, a: torch.Tensor | None, targets: torch.Tensor,
+                 u: torch.Tensor, stream=None):
+    T = targets.numel() // 3
+    _check(load().lbf_evaluate(plan.handle, _dptr(sigma, plan.N, "sigma"), _dptr(a, plan.M, "a"),
+                               T, _dptr(targets, 3 * T, "targets"), _dptr(u, T, "u"),
+                               _stream(stream)), "lbf_evaluate")
+
+
+def lbf_green_sum(t: torch.Tensor, p: torch.Tensor, gamma: torch.Tensor, out: torch.Tensor,
+                  stream=None):
+    T, S = t.numel() // 3, p.numel() // 3
+    _check(load().lbf_green_sum(T, _dptr(t, 3 * T, "t"), S, _dptr(p, 3 * S, "p"),
+                                _dptr(gamma, S, "gamma"), _dptr(out, T, "out"), _stream(stream)),
+           "lbf_green_sum")
+
+
+def lbf_tree_export(plan: Plan, stream=None):
+    """(perm, boxes) as int32 CUDA tensors; boxes rows are
+    (level, ix, iy, parent, first_child, nchild, begin, end)."""
+    nbox = lbf_plan_info(plan)["nbox"]
+    dev = plan.workspace.device
+    perm = torch.empty(plan.N, dtype=torch.int32, device=dev)
+    boxes = torch.empty((nbox, 8), dtype=torch.int32, device=dev)
+    _check(load().lbf_tree_export(plan.handle, C.c_void_p(perm.data_ptr()),
+                                  C.c_void_p(boxes.data_ptr()), _stream(stream)), "lbf_tree_export")
+    return perm, boxes
+
+
+def lbf_list_export(plan: Plan, kind: int, stream=None):
+    """(ptr, idx) of list kind 0..3 = U, V, W, X as int32 CUDA tensors."""
+    nbox = lbf_plan_info(plan)["nbox"]
+    dev = plan.workspace.device
+    ptr = torch.empty(nbox + 1, dtype=torch.int32, device=dev)
+    n = C.c_int64(0)
+    lib = load()
+    _check(lib.lbf_list_export(plan.handle, int(kind), C.c_void_p(ptr.data_ptr()), None,
+                               C.byref(n), _stream(stream)), "lbf_list_export")
+    idx = torch.empty(max(1, n.value), dtype=torch.int32, device=dev)
+    _check(lib.lbf_list_export(plan.handle, int(kind), C.c_void_p(ptr.data_ptr()),
+                               C.c_void_p(idx.data_ptr()), C.byref(n), _stream(stream)),
+           "lbf_list_export")
+    return ptr, idx[: n.value]
+
+
+def lbf_sync_status(plan: Plan, stream=None) -> int:
+    return load().lbf_sync_status(plan.handle, _stream(stream))
+
+
+def lbf_launch_count() -> int:
+    return int(load().lbf_launch_count())

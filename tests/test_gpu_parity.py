@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Tolerances: the FP64 matvec within rel-l2 1e-10 of the oracle's direct
+matvec, solutions within 1e-9 of the exact data and of the oracle's dense LU,
+integer tree and permutation work bit-exact.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import workloads as wl  # noqa: E402
+from gpu_util import DEV, dev, host, plan_for, rel_l2, zeros  # noqa: E402
+from paper_1306_0612_gb300 import lbfmm as L  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MATVEC_TOL = 1e-10
+SOLVE_TOL = 1e-9
+
+
+def _ragged(seed=31):
+    # islands of very different node counts (ragged CSR), pole in island 0
+    return wl.star_caps(seed, 5, [96, 33, 250, 64, 17], r0=[0.3, 0.15, 0.35, 0.2, 0.1],
+                        amp=[0.2, 0.1, 0.25, 0.0, 0.15], kfreq=[3, 2, 5, 4, 2])
+
+
+# ---- geometry -----------------------------------------------------------------
+
+def test_projection_bits_and_weights():
+    g = wl.config_geometry("C2", nodes=64)
+    p = plan_for(g)
+    N = g.N
+    xi, nrm, w, arc = zeros(2 * N), zeros(2 * N), zeros(2 * N), zeros(N)
+    L.lbf_geometry_out(p, xi, nrm, w, arc)
+    xi_o = oracle.project(g.x)
+    assert np.array_equal(host(xi).reshape(N, 2), xi_o)  # same IEEE ops: bit-exact
+    # weights h xi' against the chain rule written out in numpy
+    X, DX = g.x, g.dx
+    wz = 1 - X[:, 2]
+    z = X[:, 0] + 1j * X[:, 1]
+    xip = (DX[:, 0] + 1j * DX[:, 1]) / wz + z * DX[:, 2] / wz ** 2
+    h = np.repeat(2 * np.pi / g.nodes_per_island, g.nodes_per_island)
+    wc = host(w).reshape(N, 2)
+    assert np.max(np.abs(wc[:, 0] + 1j * wc[:, 1] - h * xip)) < 1e-13 * np.max(np.abs(h * xip))
+    nn = host(nrm).reshape(N, 2)
+    assert np.allclose(np.hypot(nn[:, 0], nn[:, 1]), 1.0, atol=1e-14)
+    assert np.max(np.abs(nn[:, 0] * wc[:, 0] + nn[:, 1] * wc[:, 1])) < 1e-12 * np.max(np.abs(wc))
+    assert np.allclose(host(arc), np.hypot(wc[:, 0], wc[:, 1]), rtol=1e-14)
+
+
+# ---- quadtree: bit-exact against the oracle -------------------------------------
+
+def _tree_case(g, leaf, depth=30):
+    p = plan_for(g, leaf_size=leaf, max_depth=depth)
+    perm, boxes = L.lbf_tree_export(p)
+    ref = oracle.tree(oracle.project(g.x), leaf=leaf, depth=depth)
+    assert np.array_equal(host(perm).astype(np.int64), ref.perm)
+    b = host(boxes).astype(np.int64)
+    assert len(b) == ref.nbox
+    fc = np.where(ref.nchild > 0, ref.first_child, -1)
+    want = np.stack([ref.level, ref.ix, ref.iy, ref.parent, fc, ref.nchild, ref.begin, ref.end], 1)
+    assert np.array_equal(b, want)
+    return p, ref
+
+
+@pytest.mark.parametrize("name,leaf,depth", [("C1", 8, 30), ("C2", 48, 30), ("C2", 4, 30),
+                                             ("ragged", 16, 30), ("C2", 16, 5)])
+def test_tree_bit_exact(name, leaf, depth):
+    g = _ragged() if name == "ragged" else wl.config_geometry(name)
+    _tree_case(g, leaf, depth)
+
+
+def test_tree_root_leaf():
+    g = wl.config_geometry("C1", nodes=40)
+    p, ref = _tree_case(g, 64)
+    assert ref.nbox == 1
+
+
+def test_lists_match_brute_force():
+    g = wl.star_caps(4, 3, 48, r0=[0.3, 0.2, 0.25], amp=[0.2, 0.3, 0.1], kfreq=[3, 5, 2])
+    p, _ = _tree_case(g, 4)
+    ref = oracle.tree(oracle.project(g.x), leaf=4, lists=True)
+    for kind, name in enumerate("UVWX"):
+        ptr, idx = L.lbf_list_export(p, kind)
+        ptr, idx = host(ptr), host(idx)
+        rp, ri = getattr(ref, name + "_ptr"), getattr(ref, name + "_idx")
+        for b in range(ref.nbox):
+            got = sorted(idx[ptr[b]:ptr[b + 1]].tolist())
+            assert got == ri[rp[b]:rp[b + 1]].tolist(), (name, b)
+
+
+# ---- operator ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("matvec", [L.LBF_MATVEC_DIRECT, L.LBF_MATVEC_FMM])
+def test_apply_all_ops_small(matvec):
+    g = _ragged()
+    p = plan_for(g, matvec=matvec, leaf_size=8)
+    A = oracle.matrix(g)
+    Pm = oracle.preconditioner_matrix(A, g.N)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(g.N + g.M)
+    N = g.N
+    out = zeros(N + g.M)
+    L.lbf_apply(p, L.LBF_OP_FULL, dev(v), out)
+    assert rel_l2(host(out), A @ v) < MATVEC_TOL
+    L.lbf_apply(p, L.LBF_OP_PRECONDITIONED, dev(v), out)
+    assert rel_l2(host(out), np.linalg.solve(Pm, A @ v)) < MATVEC_TOL
+    o2 = zeros(N)
+    L.lbf_apply(p, L.LBF_OP_K_ONLY, dev(v[:N]), o2)
+    assert rel_l2(host(o2), A[:N, :N] @ v[:N]) < MATVEC_TOL
+
+
+def test_fmm_matvec_c2_full_size():
+    g = wl.config_geometry("C2")
+    p = plan_for(g)
+    v = np.random.default_rng(2).standard_normal(g.N + g.M)
+    out = zeros(g.N + g.M)
+    L.lbf_apply(p, L.LBF_OP_FULL, dev(v), out)
+    ref = oracle.apply(g, v, 0)
+    assert rel_l2(host(out), ref) < MATVEC_TOL
+    info = p.info()
+    assert info["depth"] >= 8
+
+
+def test_fmm_matvec_c3_sampled_rows():
+    """N = 1,048,576 (1024 islands x 1024 nodes): sampled rows against the oracle."""
+    g = wl.config_geometry("C3", M=1024)
+    p = plan_for(g, border=0)
+    sig = wl.random_density(g.N, 3)
+    out = zeros(g.N)
+    L.lbf_apply(p, L.LBF_OP_K_ONLY, dev(sig), out)
+    rows = np.sort(np.random.default_rng(5).choice(g.N, 48, replace=False))
+    ref = oracle.apply_rows(g, sig, rows, op=1)
+    got = host(out)[rows]
+    assert rel_l2(got, ref) < MATVEC_TOL
+
+
+# ---- solve and evaluate ---------------------------------------------------------------
+
+def _solve_check(g, src, gam, **opt):
+    data = oracle.green_sum(g.x, src, gam)
+    p = plan_for(g, tol=1e-12, **opt)
+    sig, a = zeros(g.N), zeros(g.M)
+    rc, its, rr = L.lbf_gmres_solve(p, dev(data), sig, a)
+    assert rc == L.LBF_OK and rr <= 1e-12
+    s_ref, a_ref = oracle.solve(g, data)
+    assert rel_l2(host(sig), s_ref) < SOLVE_TOL
+    assert np.max(np.abs(host(a) - a_ref)) < SOLVE_TOL
+    tg = wl.targets_off_islands(g, 64, seed=77)
+    u = zeros(64)
+    L.lbf_evaluate(p, sig, a, dev(tg), u)
+    uex = oracle.green_sum(tg, src, gam)
+    err = np.max(np.abs(host(u) - uex)) / np.max(np.abs(uex))
+    assert err < SOLVE_TOL
+    # the device evaluation agrees with the oracle's representation formula
+    uo = oracle.evaluate(g, host(sig), host(a), tg)
+    assert np.max(np.abs(host(u) - uo)) < 1e-12 * np.max(np.abs(uo))
+    return its, err
+
+
+def test_solve_c1_direct():
+    g = wl.config_geometry("C1")
+    src, gam, _ = wl.pair_sources(g, 0)
+    _solve_check(g, src, gam, matvec=L.LBF_MATVEC_DIRECT)
+
+
+def test_solve_c2_fmm():
+    g = wl.config_geometry("C2")
+    src, gam, _ = wl.pair_sources(g, 0, 1)
+    its, err = _solve_check(g, src, gam)
+    assert its < 200
+
+
+def test_solve_ragged_fmm_restarts():
+    g = _ragged()
+    src, gam, _ = wl.pair_sources(g, 2, 4)
+    _solve_check(g, src, gam, restart=5, leaf_size=8)
+
+
+def test_solve_with_initial_guess():
+    g = wl.config_geometry("C1")
+    src, gam, _ = wl.pair_sources(g, 0)
+    data = oracle.green_sum(g.x, src, gam)
+    s_ref, a_ref = oracle.solve(g, data)
+    p = plan_for(g, matvec=L.LBF_MATVEC_DIRECT)
+    sig, a = zeros(g.N), zeros(g.M)
+    x0 = dev(np.concatenate([s_ref, a_ref]))
+    rc, its, rr = L.lbf_gmres_solve(p, dev(data), sig, a, x0=x0)
+    assert rc == L.LBF_OK and its <= 2
+
+
+def test_noconv_reports_soft_status():
+    g = wl.config_geometry("C2", nodes=64)
+    src, gam, _ = wl.pair_sources(g, 0, 1)
+    p = plan_for(g, maxit=3, tol=1e-14)
+    sig, a = zeros(g.N), zeros(g.M)
+    rc, its, rr = L.lbf_gmres_solve(p, dev(oracle.green_sum(g.x, src, gam)), sig, a)
+    assert rc == L.LBF_NOCONV and its == 3 and rr > 1e-14
+
+
+def test_green_sum_matches_oracle():
+    rng = np.random.default_rng(8)
+    t = rng.standard_normal((300, 3)); t /= np.linalg.norm(t, axis=1)[:, None]
+    s = rng.standard_normal((7, 3)); s /= np.linalg.norm(s, axis=1)[:, None]
+    gm = rng.standard_normal(7)
+    out = zeros(300)
+    L.lbf_green_sum(dev(t), dev(s), dev(gm), out)
+    ref = oracle.green_sum(t, s, gm)
+    assert np.max(np.abs(host(out) - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_pole_rotation_argument_matches_prerotated_input():
+    g0 = wl.star_caps(9, 2, 96, r0=[0.3, 0.2], amp=[0.2, 0.1], kfreq=[4, 2], pole=None)
+    R = wl.rotation_to_pole(g0.centres[0])
+    g1 = wl.rotated(g0, R)
+    src, gam, _ = wl.pair_sources(g0, 0, 1)
+    data = oracle.green_sum(g0.x, src, gam)
+    out = []
+    for g, rot in ((g0, R), (g1, None)):
+        p = plan_for(g, rotation=rot, matvec=L.LBF_MATVEC_DIRECT)
+        sig, a = zeros(g.N), zeros(g.M)
+        L.lbf_gmres_solve(p, dev(data), sig, a)
+        out.append((host(sig), host(a)))
+    assert rel_l2(out[0][0], out[1][0]) < 1e-11
+
+
+# ---- edge cases ----------------------------------------------------------------------
+
+def test_node_at_pole_is_an_error():
+    g = wl.config_geometry("C1", nodes=16, pole=None)
+    x = g.x.copy()
+    x[3] = [0.0, 0.0, 1.0]
+    with pytest.raises(L.LbfError) as e:
+        L.lbf_plan_create(g.island_ptr, dev(x), dev(g.dx), dev(g.d2x), dev(g.centres))
+    assert e.value.status == L.LBF_EPOLE
+
+
+def test_zero_targets_and_not_built():
+    g = wl.config_geometry("C1", nodes=64)
+    p = plan_for(g, border=0)
+    u = zeros(1)
+    L.lbf_evaluate(p, zeros(g.N), None, zeros(3)[:0], u[:0])
+    with pytest.raises(L.LbfError) as e:
+        L.lbf_apply(p, L.LBF_OP_FULL, zeros(g.N + 1), zeros(g.N + 1))
+    assert e.value.status == L.LBF_ENOTBUILT
+
+
+def test_small_box_capacity_is_retried():
+    g = wl.config_geometry("C2", nodes=128)
+    p = plan_for(g, box_capacity=64, leaf_size=8)
+    assert p.info()["nbox"] > 64
+    _tree_case(g, 8)
