@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the method's hot path on one GB300 (or N replicas under torchrun).
+
+One step = one pass of the whole path on one geometry with inputs resident in
+HBM: plan creation (stereographic projection and per-node precompute, Morton
+quadtree and interaction lists, border E and inverse Schur complement), the
+left-preconditioned GMRES(50) solve to a 1e-10 relative residual whose every
+iteration applies the FP64 FMM operator, and the evaluation of u at off-curve
+targets.  The headline value is the FMM-operator throughput inside the solve:
+N x (operator applications) / step time, in Mpts/s.
+
+Workload (default): 1024 star-cap islands x 1024 nodes (N = 1,048,576), seed 3,
+Green's-function pair data with sources in islands 0 and 1, 256 targets.
+
+--impl reference times the oracle (plain FP64 C, host cores) on a bounded
+sample of rows of the same operator, in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvec Mpts/s and GMRES solve time at 1e-10 rel err; fraction of FP64 peak"
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of one GB300 (recipe table)
+WORKLOADS = {
+    "C3-1024": dict(M=1024, nodes=1024),
+    "C3-2048": dict(M=2048, nodes=1024),
+    "C2": dict(M=16, nodes=512),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="C3-1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--targets", type=int, default=256)
+    return ap.parse_args()
+
+
+def make_inputs(name):
+    import numpy as np
+    import workloads as wl
+
+    w = WORKLOADS[name]
+    if name.startswith("C3"):
+        g = wl.star_caps(3, w["M"], w["nodes"])
+    else:
+        g = wl.config_geometry("C2")
+    src, gam, _ = wl.pair_sources(g, 0, 1)
+    return g, src, gam, np
+
+
+def workload_config(name, g, T, tol):
+    w = WORKLOADS[name]
+    return {"workload": f"{name}: {w['M']} star-cap islands x {w['nodes']} nodes "
+                        f"(N={g.N}), Green's-pair data, GMRES(50) tol {tol:g}, {T} targets",
+            "islands": g.M, "nodes": g.N, "targets": T, "l2": "inputs larger than L2 (E block "
+            f"{g.N * g.M * 8 / 1e9:.1f} GB, FMM arrays)", "precision": "fp64"}
+
+
+# ---- clocks -------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        except OSError:
+            rows = []
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = max(mx, float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for nme, v in zip(names, r[2:6]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nme)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- oracle baseline (host cores) -------------------------------------------------
+
+def oracle_rate(g, np, rows=256, seed=11):
+    """The oracle's direct matvec (entries computed on the fly, OpenMP rows) on a
+    sample of rows; returns (Mpts/s of a full N-row matvec, seconds, threads)."""
+    import oracle
+
+    oracle.build()
+    sig = np.random.default_rng(seed).standard_normal(g.N)
+    idx = np.sort(np.random.default_rng(seed + 1).choice(g.N, rows, replace=False))
+    t0 = time.perf_counter()
+    oracle.apply_rows(g, sig, idx, op=1)
+    dt = time.perf_counter() - t0
+    full = dt * g.N / rows
+    return g.N / full / 1e6, dt, oracle.num_threads(), rows
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g, src, gam, np = make_inputs(args.workload)
+    rows = 512 if g.N > 100000 else 64
+    for _ in range(args.warmup):
+        oracle_rate(g, np, rows)
+    vals, dts = [], []
+    for _ in range(args.steps):
+        v, dt, cores, rows = oracle_rate(g, np, rows)
+        vals.append(v)
+        dts.append(dt)
+    val = statistics.median(vals)
+    sample = f"{rows} rows of the N={g.N} density block (I+K), entries computed on the fly"
+    line = {"metric": METRIC, "value": val, "unit": "Mpts/s", "impl": "reference", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(dts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.workload, g, args.targets, args.tol),
+            "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---- our arm ---------------------------------------------------------------------------
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1306_0612_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_flops(name, c, P, N, M):
+    """Algorithmic work per the FMM's operation counts (one apply)."""
+    if name == "leaf":
+        return 11 * c["p2p_pairs"] + 8 * P * N + 8 * P * c["w_pairs"] + 10 * N
+    if name == "m2l":
+        return 8 * P * P * c["m2l"] + 8 * P * c["x_pairs"]
+    if name == "p2m":
+        return 8 * P * N
+    if name == "m2m":
+        return 8 * P * P * c["m2m"]
+    if name == "l2l":
+        return 8 * P * P * c["l2l"]
+    if name == "direct":
+        return 11 * N * (N - 1)
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1306_0612_gb300 import lbfmm as L
+    import __graft_entry__
+
+    __graft_entry__.build()
+    g, src, gam, np = make_inputs(args.workload)
+    import workloads as wl
+
+    T = args.targets
+    tg = wl.targets_off_islands(g, T, seed=17)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).to(dev)
+    x, dx, d2x, cen, tgt = t(g.x), t(g.dx), t(g.d2x), t(g.centres), t(tg)
+    srcd, gamd = t(src), t(gam)
+    data = torch.empty(g.N, dtype=torch.float64, device=dev)
+    L.lbf_green_sum(x, srcd, gamd, data)
+    uex = torch.empty(T, dtype=torch.float64, device=dev)
+    L.lbf_green_sum(tgt, srcd, gamd, uex)
+    kw = dict(tol=args.tol)
+    if args.p:
+        kw["p"] = args.p
+    if args.leaf:
+        kw["leaf_size"] = args.leaf
+    opt = L.lbf_default_options(**kw)
+    sig = torch.empty(g.N, dtype=torch.float64, device=dev)
+    a = torch.empty(g.M, dtype=torch.float64, device=dev)
+    u = torch.empty(T, dtype=torch.float64, device=dev)
+    holder = {}
+
+    def step():
+        plan = L.lbf_plan_create(g.island_ptr, x, dx, d2x, cen, opt=opt)
+        rc, its, rr = L.lbf_gmres_solve(plan, data, sig, a)
+        L.lbf_evaluate(plan, sig, a, tgt, u)
+        holder["plan"] = plan
+        return rc, its, rr
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    L.lbf_profile_reset()
+    L.lbf_profile_enable(True)
+    n0 = L.lbf_launch_count()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its_total = 0
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            rc, its, rr = step()
+            its_total += its
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    L.lbf_profile_enable(False)
+    launches = L.lbf_launch_count() - n0
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    clocks = clk.summary()
+    plan = holder["plan"]
+    info = plan.info()
+    counts = L.lbf_plan_counts(plan)
+    P = info["p"] + 1
+    # per-kernel device time over the timed region (CUDA events on the launch stream)
+    prof = {}
+    for kid, name in enumerate(L.KERNEL_NAMES):
+        n, tms = L.lbf_profile_read(kid)
+        if n:
+            prof[name] = {"launches": n, "ms": tms}
+    L.lbf_profile_reset()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    # the leaf (or direct) kernel runs exactly once per operator application
+    apply_key = "leaf" if "leaf" in prof else "direct"
+    n_applies = prof[apply_key]["launches"]
+    applies = n_applies / args.steps
+    fl = kernel_flops(dom, counts, P, g.N, g.M)
+    roofline = None
+    if fl is not None:
+        # algorithmic flops of the kernel over the timed region / its summed device time
+        ach = fl * n_applies / (prof[dom]["ms"] / 1e3) / 1e12
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tp):
+            tj = json.load(open(tp))
+            if tj.get("src_hash") == src_hash() and dom in tj.get("kernels", {}):
+                traffic = tj["kernels"][dom].get("bytes_per_launch")
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
+                    "peak_source": "nominal FP64 (recipe table; not in MEASURED_PEAKS.json)"}
+    # accuracy of the last step
+    err = float((u - uex).abs().max() / uex.abs().max())
+    # pure operator throughput (FMM K-block apply), device-resident
+    vin = torch.randn(g.N, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+    vout = torch.empty_like(vin)
+    for _ in range(2):
+        L.lbf_apply(plan, L.LBF_OP_K_ONLY, vin, vout)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nrep = 5
+    for _ in range(nrep):
+        L.lbf_apply(plan, L.LBF_OP_K_ONLY, vin, vout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    matvec_ms = e0.elapsed_time(e1) / nrep
+    value = g.N * applies * world / (ms / args.steps / 1e3) / 1e6
+
+    # end to end through the public API, host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).pin_memory()
+        hx, hdx, hd2x, hc, ht = pin(g.x), pin(g.dx), pin(g.d2x), pin(g.centres), pin(tg)
+        hg = data.cpu().pin_memory()
+        hu = torch.empty(T, dtype=torch.float64).pin_memory()
+        bi = 8 * (hx.numel() + hdx.numel() + hd2x.numel() + hc.numel() + ht.numel() + hg.numel())
+        bo = 8 * T
+
+        def e2e_step():
+            dx_ = hx.to(dev, non_blocking=True)
+            ddx = hdx.to(dev, non_blocking=True)
+            dd2 = hd2x.to(dev, non_blocking=True)
+            dc = hc.to(dev, non_blocking=True)
+            dt_ = ht.to(dev, non_blocking=True)
+            dg = hg.to(dev, non_blocking=True)
+            plan = L.lbf_plan_create(g.island_ptr, dx_, ddx, dd2, dc, opt=opt)
+            s_ = torch.empty(g.N, dtype=torch.float64, device=dev)
+            a_ = torch.empty(g.M, dtype=torch.float64, device=dev)
+            u_ = torch.empty(T, dtype=torch.float64, device=dev)
+            rc, its, rr = L.lbf_gmres_solve(plan, dg, s_, a_)
+            L.lbf_evaluate(plan, s_, a_, dt_, u_)
+            hu.copy_(u_, non_blocking=True)
+            return its
+
+        e2e_step()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        its_e = 0
+        for _ in range(args.steps):
+            its_e += e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1) / args.steps
+        e2e = {"value": g.N * (its_e / args.steps + 1) * world / (ems / 1e3) / 1e6, "unit": "Mpts/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ems}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        v, dt, cores, rows = oracle_rate(g, np, 512 if g.N > 100000 else 64)
+        cpu = {"value": v, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
+               "sample": f"{rows} rows of the N={g.N} density block (I+K), {dt:.1f} s wall"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload_config(args.workload, g, T, args.tol),
+                "solve": {"gmres_iterations": its_total / args.steps, "rel_residual": rr,
+                          "solution_max_rel_err": err, "step_ms": ms / args.steps,
+                          "fmm_apply_ms": matvec_ms, "fmm_apply_mpts": g.N / matvec_ms / 1e3,
+                          "tree": info, "counts": counts},
+                "kernels_ms": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -170,6 +170,29 @@ int lbf_tree_export(const lbf_plan *plan, int32_t *perm, int32_t *boxes, lbf_str
 int lbf_list_export(const lbf_plan *plan, int kind, int32_t *ptr, int32_t *idx, int64_t *len,
                     lbf_stream_t stream);
 
+/* Work counts of a plan's FMM (host out, synchronous), for algorithmic-FLOP
+ * accounting: counts[0] N, [1] near-field pairs (P2P, self excluded),
+ * [2] M2M shifts, [3] M2L translations (V lists), [4] L2L shifts,
+ * [5] (target node, W box) pairs, [6] (source node, X box) pairs, [7] leaves. */
+int lbf_plan_counts(const lbf_plan *plan, int64_t counts[8], lbf_stream_t stream);
+
+/* Tracing: while enabled, every launch of the kernels below is bracketed by a
+ * pair of CUDA events recorded on the stream it is launched on.  Host calls;
+ * lbf_profile_read synchronizes on the recorded events and returns, per kernel,
+ * the launches and their summed device time. */
+#define LBF_KERNEL_P2M 0
+#define LBF_KERNEL_M2M 1
+#define LBF_KERNEL_M2L 2
+#define LBF_KERNEL_L2L 3
+#define LBF_KERNEL_LEAF 4   /* L2P + M2P + P2P + combine */
+#define LBF_KERNEL_DIRECT 5
+#define LBF_KERNEL_ARNOLDI 6
+#define LBF_KERNEL_ESUM 7   /* E-block pass of the bordered operator */
+#define LBF_KERNEL_COUNT 8
+int lbf_profile_enable(int on);
+int lbf_profile_reset(void);
+int lbf_profile_read(int kernel, int64_t *launches /* host out */, double *total_ms /* host out */);
+
 /* Wait for the stream and return the first device-side error recorded by
  * this plan's kernels (LBF_OK if none).  Synchronous. */
 int lbf_sync_status(lbf_plan *plan, lbf_stream_t stream);

@@ -511,7 +511,7 @@ int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, c
     if (rc) return rc;
     int64_t N = pl->N;
     if (pl->opt.matvec == LBF_MATVEC_DIRECT) {
-        LBF_LAUNCH(k_direct, lbf_cdiv(N, 256), 256, 0, s, N, pl->xi, pl->q, sigma, pl->dself,
+        LBF_LAUNCH_P(LBF_KERNEL_DIRECT, k_direct, lbf_cdiv(N, 256), 256, 0, s, N, pl->xi, pl->q, sigma, pl->dself,
                    pl->bsig, v, gate);
         LBF_CHECK_LAUNCH();
         return LBF_OK;
@@ -523,7 +523,7 @@ int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, c
     {
         int wpb = 2;
         size_t smem = (size_t)wpb * P * 32 * sizeof(double2);
-        LBF_LAUNCH(k_p2m, lbf_cdiv(T.nleaf, wpb), 32 * wpb, smem, s, T.nleaf, T.leaves, T.level,
+        LBF_LAUNCH_P(LBF_KERNEL_P2M, k_p2m, lbf_cdiv(T.nleaf, wpb), 32 * wpb, smem, s, T.nleaf, T.leaves, T.level,
                    T.ix, T.iy, T.begin, T.end, g, P, pl->xi, pl->q, pl->mpole, gate);
         LBF_CHECK_LAUNCH();
     }
@@ -532,12 +532,12 @@ int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, c
     for (int l = T.nlev - 2; l >= 2; l--) {
         int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
         if (le <= ls) continue;
-        LBF_LAUNCH(k_m2m, lbf_cdiv(le - ls, wpb), 32 * wpb, smemP, s, ls, le, T.child0, T.nchild,
+        LBF_LAUNCH_P(LBF_KERNEL_M2M, k_m2m, lbf_cdiv(le - ls, wpb), 32 * wpb, smemP, s, ls, le, T.child0, T.nchild,
                    T.ix, T.iy, P, pl->tab_m2m, pl->mpole, gate);
         LBF_CHECK_LAUNCH();
     }
     // interaction lists into local expansions
-    LBF_LAUNCH(k_m2l, lbf_cdiv(T.nbox, wpb), 32 * wpb, smemP, s, T.nbox, T.level, T.ix, T.iy,
+    LBF_LAUNCH_P(LBF_KERNEL_M2L, k_m2l, lbf_cdiv(T.nbox, wpb), 32 * wpb, smemP, s, T.nbox, T.level, T.ix, T.iy,
                T.vlist, T.nv, T.xlist, T.nx, T.begin, T.end, g, P, pl->tab_binom,
                pl->tab_tpow, pl->xi, pl->q, pl->mpole, pl->local, gate);
     LBF_CHECK_LAUNCH();
@@ -545,11 +545,11 @@ int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, c
     for (int l = 3; l < T.nlev; l++) {
         int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
         if (le <= ls) continue;
-        LBF_LAUNCH(k_l2l, lbf_cdiv(le - ls, wpb), 32 * wpb, smemP, s, ls, le, T.parent, T.ix, T.iy,
+        LBF_LAUNCH_P(LBF_KERNEL_L2L, k_l2l, lbf_cdiv(le - ls, wpb), 32 * wpb, smemP, s, ls, le, T.parent, T.ix, T.iy,
                    P, pl->tab_l2l, pl->local, gate);
         LBF_CHECK_LAUNCH();
     }
-    LBF_LAUNCH(k_leaf, lbf_cdiv(T.nleaf, kLeafWarps), 32 * kLeafWarps, 0, s, T.nleaf, T.leaves,
+    LBF_LAUNCH_P(LBF_KERNEL_LEAF, k_leaf, lbf_cdiv(T.nleaf, kLeafWarps), 32 * kLeafWarps, 0, s, T.nleaf, T.leaves,
                T.level, T.ix, T.iy, T.begin, T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P,
                pl->xi, pl->q, pl->mpole, pl->local, sigma, pl->dself, pl->bsig, v, gate);
     LBF_CHECK_LAUNCH();

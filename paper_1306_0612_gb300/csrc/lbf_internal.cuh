@@ -21,6 +21,15 @@ extern std::atomic<int64_t> g_lbf_launches;
         g_lbf_launches.fetch_add(1, std::memory_order_relaxed);            \
     } while (0)
 
+// Tracing: event pair around a launch when lbf_profile_enable(1) is on.
+void lbf_prof_mark(int id, int begin, cudaStream_t s);
+#define LBF_LAUNCH_P(id, kernel, grid, block, smem, stream, ...)           \
+    do {                                                                   \
+        lbf_prof_mark((id), 1, (stream));                                  \
+        LBF_LAUNCH(kernel, grid, block, smem, stream, __VA_ARGS__);        \
+        lbf_prof_mark((id), 0, (stream));                                  \
+    } while (0)
+
 #define LBF_CUDA(call)                                                     \
     do {                                                                   \
         cudaError_t e_ = (call);                                           \

@@ -404,7 +404,7 @@ static int esum(lbf_plan *pl, const double *x, const double *v, const double *c,
                 double *out, const int *gate, cudaStream_t s)
 {
     size_t smem = sizeof(double) * (size_t)pl->M;
-    LBF_LAUNCH(k_esum, lbf_cdiv(pl->N, 256), 256, smem, s, pl->N, pl->M, pl->E, x, v, c, sc, out,
+    LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_esum, lbf_cdiv(pl->N, 256), 256, smem, s, pl->N, pl->M, pl->E, x, v, c, sc, out,
                gate);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
@@ -521,7 +521,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
             const double *vj = V + (int64_t)k * ldv;
             if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, vj, w, &pl->gs->go, s))) return rc;
             for (int mode = 0; mode < 3; mode++)
-                LBF_LAUNCH(k_arnoldi, nblk, 256, smem, s, n, V, ldv, w, pl->gpart, count, hbuf,
+                LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w, pl->gpart, count, hbuf,
                            pl->H, cs, sn, gv, pl->gs, mode);
             LBF_LAUNCH(k_scale_next, nblk, 256, 0, s, n, w, V, ldv, pl->gs);
             LBF_CHECK_LAUNCH();

@@ -73,6 +73,10 @@ def load():
             "lbf_green_sum": (C.c_int, [i64, _P, i64, _P, _P, _P, _P]),
             "lbf_tree_export": (C.c_int, [_P, _P, _P, _P]),
             "lbf_list_export": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(i64), _P]),
+            "lbf_plan_counts": (C.c_int, [_P, _P, _P]),
+            "lbf_profile_enable": (C.c_int, [C.c_int]),
+            "lbf_profile_reset": (C.c_int, []),
+            "lbf_profile_read": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(C.c_double)]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
             "lbf_launch_count": (i64, []),
         }
@@ -88,7 +92,8 @@ def exported_symbols():
     return ["lbf_default_options", "lbf_status_string", "lbf_workspace_size", "lbf_plan_create",
             "lbf_plan_destroy", "lbf_plan_info", "lbf_geometry_out", "lbf_apply",
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
-            "lbf_list_export", "lbf_sync_status", "lbf_launch_count"]
+            "lbf_list_export", "lbf_plan_counts", "lbf_profile_enable", "lbf_profile_reset",
+            "lbf_profile_read", "lbf_sync_status", "lbf_launch_count"]
 
 
 def lbf_status_string(status: int) -> str:
@@ -265,6 +270,33 @@ def lbf_list_export(plan: Plan, kind: int, stream=None):
                                C.c_void_p(idx.data_ptr()), C.byref(n), _stream(stream)),
            "lbf_list_export")
     return ptr, idx[: n.value]
+
+
+LBF_KERNEL_P2M, LBF_KERNEL_M2M, LBF_KERNEL_M2L, LBF_KERNEL_L2L = 0, 1, 2, 3
+LBF_KERNEL_LEAF, LBF_KERNEL_DIRECT, LBF_KERNEL_ARNOLDI, LBF_KERNEL_ESUM = 4, 5, 6, 7
+KERNEL_NAMES = ["p2m", "m2m", "m2l", "l2l", "leaf", "direct", "arnoldi", "esum"]
+
+
+def lbf_plan_counts(plan: Plan, stream=None) -> dict:
+    c = (C.c_int64 * 8)()
+    _check(load().lbf_plan_counts(plan.handle, C.cast(c, _P), _stream(stream)), "lbf_plan_counts")
+    keys = ["N", "p2p_pairs", "m2m", "m2l", "l2l", "w_pairs", "x_pairs", "leaves"]
+    return dict(zip(keys, [int(v) for v in c]))
+
+
+def lbf_profile_enable(on: bool = True):
+    _check(load().lbf_profile_enable(1 if on else 0), "lbf_profile_enable")
+
+
+def lbf_profile_reset():
+    _check(load().lbf_profile_reset(), "lbf_profile_reset")
+
+
+def lbf_profile_read(kernel: int):
+    """(launches, total device ms) of one traced kernel."""
+    n, t = C.c_int64(0), C.c_double(0.0)
+    _check(load().lbf_profile_read(int(kernel), C.byref(n), C.byref(t)), "lbf_profile_read")
+    return int(n.value), float(t.value)
 
 
 def lbf_sync_status(plan: Plan, stream=None) -> int:
