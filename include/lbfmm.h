@@ -193,6 +193,29 @@ int lbf_profile_enable(int on);
 int lbf_profile_reset(void);
 int lbf_profile_read(int kernel, int64_t *launches /* host out */, double *total_ms /* host out */);
 
+/* lbf_evaluate_noalloc: the same off-curve evaluation as lbf_evaluate, for
+ * callers that cannot allocate device memory at all -- no plan, no workspace,
+ * no allocator call.  (The paper has no counterpart: this is an interface
+ * convenience of this library.)  Useful where no allocator is reachable or
+ * allowed: a loop running on a fixed memory budget set at start-up, a
+ * foreign-language binding without access to the framework's allocator, a
+ * plugin that must not grow its host library's pool.
+ *   xi, weight : N x 2 projected nodes and complex weights h xi', as returned by
+ *                lbf_geometry_out (any node order, the same for sigma)
+ *   sigma      : N densities; a (M), centres (M x 3): multiplier sources in the
+ *                same rotated frame as xi (M = 0: none); targets: T x 3, same frame
+ *   u          : T outputs.  All arrays are device memory owned by the caller.
+ * Its scratch (q = sigma w and the reduction partials, about 4 MB) is one
+ * static device array, so N is limited to LBF_NOALLOC_MAX_NODES: larger N
+ * returns LBF_EINVAL without touching the device.  Every call shares that
+ * array: calls that overlap on the GPU race, so serialise them.  The first call
+ * on a device looks up the array's address with that device current; make it
+ * before any stream capture.  Asynchronous on the stream. */
+#define LBF_NOALLOC_MAX_NODES 262144
+int lbf_evaluate_noalloc(int64_t N, const double *xi, const double *weight, const double *sigma,
+                         int M, const double *a, const double *centres, int64_t T,
+                         const double *targets, double *u, lbf_stream_t stream);
+
 /* Wait for the stream and return the first device-side error recorded by
  * this plan's kernels (LBF_OK if none).  Synchronous. */
 int lbf_sync_status(lbf_plan *plan, lbf_stream_t stream);

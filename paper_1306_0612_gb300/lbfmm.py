@@ -77,6 +77,7 @@ def load():
             "lbf_profile_enable": (C.c_int, [C.c_int]),
             "lbf_profile_reset": (C.c_int, []),
             "lbf_profile_read": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(C.c_double)]),
+            "lbf_evaluate_noalloc": (C.c_int, [i64, _P, _P, _P, C.c_int, _P, _P, i64, _P, _P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
             "lbf_launch_count": (i64, []),
         }
@@ -93,7 +94,7 @@ def exported_symbols():
             "lbf_plan_destroy", "lbf_plan_info", "lbf_geometry_out", "lbf_apply",
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_profile_enable", "lbf_profile_reset",
-            "lbf_profile_read", "lbf_sync_status", "lbf_launch_count"]
+            "lbf_profile_read", "lbf_evaluate_noalloc", "lbf_sync_status", "lbf_launch_count"]
 
 
 def lbf_status_string(status: int) -> str:
@@ -297,6 +298,22 @@ def lbf_profile_read(kernel: int):
     n, t = C.c_int64(0), C.c_double(0.0)
     _check(load().lbf_profile_read(int(kernel), C.byref(n), C.byref(t)), "lbf_profile_read")
     return int(n.value), float(t.value)
+
+
+LBF_NOALLOC_MAX_NODES = 262144
+
+
+def lbf_evaluate_noalloc(xi: torch.Tensor, weight: torch.Tensor, sigma: torch.Tensor,
+                         a: torch.Tensor | None, centres: torch.Tensor | None,
+                         targets: torch.Tensor, u: torch.Tensor, stream=None, N: int | None = None):
+    """Off-curve evaluation without any device allocation (static scratch in the
+    library; N <= LBF_NOALLOC_MAX_NODES; overlapping calls race)."""
+    N = sigma.numel() if N is None else int(N)
+    M = 0 if a is None else a.numel()
+    T = targets.numel() // 3
+    _check(load().lbf_evaluate_noalloc(N, _dptr(xi), _dptr(weight), _dptr(sigma), M, _dptr(a),
+                                       _dptr(centres), T, _dptr(targets), _dptr(u),
+                                       _stream(stream)), "lbf_evaluate_noalloc")
 
 
 def lbf_sync_status(plan: Plan, stream=None) -> int:
