@@ -184,14 +184,10 @@ def kernel_flops(name, c, P, N, M):
     """Algorithmic work per the FMM's operation counts (one apply)."""
     if name == "leaf":
         return 11 * c["p2p_pairs"] + 8 * P * N + 8 * P * c["w_pairs"] + 10 * N
-    if name == "m2l":
-        return 8 * P * P * c["m2l"] + 8 * P * c["x_pairs"]
-    if name == "p2m":
-        return 8 * P * N
-    if name == "m2m":
-        return 8 * P * P * c["m2m"]
-    if name == "l2l":
-        return 8 * P * P * c["l2l"]
+    if name == "down":  # L2L + M2L + P2L
+        return 8 * P * P * (c["m2l"] + c["l2l"]) + 8 * P * c["x_pairs"]
+    if name == "up":  # P2M + M2M
+        return 8 * P * N + 8 * P * P * c["m2m"]
     if name == "direct":
         return 11 * N * (N - 1)
     return None

@@ -180,15 +180,13 @@ int lbf_plan_counts(const lbf_plan *plan, int64_t counts[8], lbf_stream_t stream
  * pair of CUDA events recorded on the stream it is launched on.  Host calls;
  * lbf_profile_read synchronizes on the recorded events and returns, per kernel,
  * the launches and their summed device time. */
-#define LBF_KERNEL_P2M 0
-#define LBF_KERNEL_M2M 1
-#define LBF_KERNEL_M2L 2
-#define LBF_KERNEL_L2L 3
-#define LBF_KERNEL_LEAF 4   /* L2P + M2P + P2P + combine */
-#define LBF_KERNEL_DIRECT 5
-#define LBF_KERNEL_ARNOLDI 6
-#define LBF_KERNEL_ESUM 7   /* E-block pass of the bordered operator */
-#define LBF_KERNEL_COUNT 8
+#define LBF_KERNEL_UP 0     /* upward pass: P2M + M2M, one launch */
+#define LBF_KERNEL_DOWN 1   /* downward pass: L2L + M2L + P2L, one launch per level */
+#define LBF_KERNEL_LEAF 2   /* L2P + M2P + P2P + combine */
+#define LBF_KERNEL_DIRECT 3
+#define LBF_KERNEL_ARNOLDI 4
+#define LBF_KERNEL_ESUM 5   /* E-block pass of the bordered operator */
+#define LBF_KERNEL_COUNT 6
 int lbf_profile_enable(int on);
 int lbf_profile_reset(void);
 int lbf_profile_read(int kernel, int64_t *launches /* host out */, double *total_ms /* host out */);

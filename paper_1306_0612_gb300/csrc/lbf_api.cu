@@ -38,8 +38,8 @@ bool valid(const lbf_options &o)
 }
 
 // host tables of the translation operators (scaled expansions, see lbf_fmm.cu)
-void make_tables(std::vector<double> &binom, std::vector<double2> &m2m,
-                 std::vector<double2> &l2l, std::vector<double2> &tpow)
+void make_tables(std::vector<double> &binom, std::vector<double2> &dshift,
+                 std::vector<double2> &tpow)
 {
     const int T = LBF_MAX_TERMS;
     binom.assign(2 * T * T, 0.0);
@@ -52,25 +52,18 @@ void make_tables(std::vector<double> &binom, std::vector<double2> &m2m,
         for (int k = 1; k <= n + 1; k++) nxt[k] = row[k - 1] + (k <= n ? row[k] : 0.0);
         row.swap(nxt);
     }
-    auto C = [&](int n, int k) { return binom[n * T + k]; };
-    m2m.assign(4 * T * T, make_double2(0, 0));
-    l2l.assign(4 * T * T, make_double2(0, 0));
-    for (int d = 0; d < 4; d++) {
-        std::complex<double> dv(((d & 1) ? 0.5 : -0.5), ((d >> 1) ? 0.5 : -0.5));
-        std::vector<std::complex<double>> pw(T);
-        pw[0] = 1.0;
-        for (int k = 1; k < T; k++) pw[k] = pw[k - 1] * dv;
-        for (int l = 0; l < T; l++)
-            for (int k = 0; k < T; k++) {
-                if (k <= l) {  // multipole shift: C(l,k) d^(l-k) 2^-k
-                    std::complex<double> v = C(l, k) * pw[l - k] * std::ldexp(1.0, -k);
-                    m2m[(d * T + l) * T + k] = make_double2(v.real(), v.imag());
-                }
-                if (k >= l) {  // local shift: 2^-l C(k,l) d^(k-l)
-                    std::complex<double> v = std::ldexp(1.0, -l) * C(k, l) * pw[k - l];
-                    l2l[(d * T + l) * T + k] = make_double2(v.real(), v.imag());
-                }
-            }
+    // child offsets d = ((2dx-1) + i (2dy-1))/2 over the parent half-width:
+    // dshift[c][k] = d^k, dshift[4 + c][k] = (2d)^-k
+    dshift.assign(8 * (T + 1), make_double2(0, 0));
+    for (int c = 0; c < 4; c++) {
+        std::complex<double> d(((c & 1) ? 0.5 : -0.5), ((c >> 1) ? 0.5 : -0.5));
+        std::complex<double> p = 1.0, pinv = 1.0, inv2d = 1.0 / (2.0 * d);
+        for (int k = 0; k <= T; k++) {
+            dshift[c * (T + 1) + k] = make_double2(p.real(), p.imag());
+            dshift[(4 + c) * (T + 1) + k] = make_double2(pinv.real(), pinv.imag());
+            p *= d;
+            pinv *= inv2d;
+        }
     }
     tpow.assign(49 * (T + 1), make_double2(0, 0));
     for (int dx = -3; dx <= 3; dx++)
@@ -105,8 +98,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     pl->centres = A.get<double>(3 * (int64_t)M);
     pl->rot_d = A.get<double>(9);
     pl->tab_binom = A.get<double>(2 * T * T);
-    pl->tab_m2m = A.get<double2>(4 * T * T);
-    pl->tab_l2l = A.get<double2>(4 * T * T);
+    pl->tab_dshift = A.get<double2>(8 * (T + 1));
     pl->tab_tpow = A.get<double2>(49 * (T + 1));
     Tree &t = pl->tree;
     t.cap = cap;
@@ -136,6 +128,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     if (o.matvec == LBF_MATVEC_FMM) {
         pl->mpole = A.get<double2>(cap * P);
         pl->local = A.get<double2>(cap * P);
+        pl->upcnt = A.get<int32_t>(cap);
     }
     pl->v = A.get<double>(N);
     pl->bsig = A.get<double>(4);
@@ -226,7 +219,7 @@ int lbf_default_options(lbf_options *o)
     o->tol = 1e-12;
     o->restart = 50;
     o->maxit = 2000;
-    o->p = 40;
+    o->p = 26;
     o->leaf_size = 48;
     o->max_depth = 30;
     o->matvec = LBF_MATVEC_FMM;
@@ -306,6 +299,8 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
         return LBF_EWORKSPACE;
     }
     auto fail = [&](int code) {
+        for (auto &e : pl->ev)
+            if (e) cudaEventDestroy(e);
         if (pl->host_status) cudaFreeHost(pl->host_status);
         if (pl->host_scalars) cudaFreeHost(pl->host_scalars);
         delete[] pl->island_ptr_h;
@@ -315,6 +310,8 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     if (cudaHostAlloc((void **)&pl->host_status, 64, cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void **)&pl->host_scalars, 256, cudaHostAllocDefault) != cudaSuccess)
         return fail(LBF_ECUDA);
+    for (auto &e : pl->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LBF_ECUDA);
     pl->island_ptr_h = new int64_t[M + 1];
     memcpy(pl->island_ptr_h, island_ptr, sizeof(int64_t) * (M + 1));
     if (pole_rotation) {
@@ -325,14 +322,14 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
         for (int i = 0; i < 9; i++) pl->rot[i] = (i % 4 == 0) ? 1.0 : 0.0;
     }
     std::vector<double> binom;
-    std::vector<double2> m2m, l2l, tpow;
-    make_tables(binom, m2m, l2l, tpow);
+    std::vector<double2> dshift, tpow;
+    make_tables(binom, dshift, tpow);
 #define CK(call) do { if ((call) != cudaSuccess) return fail(LBF_ECUDA); } while (0)
     CK(cudaMemcpyAsync(pl->island_ptr, island_ptr, sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(pl->rot_d, pl->rot, sizeof(pl->rot), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(pl->tab_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(pl->tab_m2m, m2m.data(), sizeof(double2) * m2m.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(pl->tab_l2l, l2l.data(), sizeof(double2) * l2l.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->tab_dshift, dshift.data(), sizeof(double2) * dshift.size(), cudaMemcpyHostToDevice, s));
+    if (pl->upcnt) CK(cudaMemsetAsync(pl->upcnt, 0, sizeof(int32_t) * cap, s));
     CK(cudaMemcpyAsync(pl->tab_tpow, tpow.data(), sizeof(double2) * tpow.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(pl->dev_status, 0, sizeof(int), s));
     CK(cudaMemsetAsync(pl->red_count, 0, 4 * sizeof(unsigned), s));
@@ -369,6 +366,8 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
 int lbf_plan_destroy(lbf_plan *pl)
 {
     if (!pl) return LBF_EINVAL;
+    for (auto &e : pl->ev)
+        if (e) cudaEventDestroy(e);
     if (pl->host_status) cudaFreeHost(pl->host_status);
     if (pl->host_scalars) cudaFreeHost(pl->host_scalars);
     delete[] pl->island_ptr_h;

@@ -109,112 +109,202 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
     }
 }
 
-// P2M: a_k = sum_j q_j ((xi_j - c)/r)^k for every leaf.  One warp per leaf;
-// lanes take nodes, write their terms to shared memory, then lanes take
-// coefficients and sum the terms in node order.
-__global__ void k_p2m(int64_t nleaf, const int32_t *__restrict__ leaves,
-                      const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
-                      const int32_t *__restrict__ iy, const int32_t *__restrict__ bg,
-                      const int32_t *__restrict__ en, BoxGeo g, int P,
-                      const double2 *__restrict__ xi, const double2 *__restrict__ q,
-                      double2 *__restrict__ mp, const int *gate)
+// Shift tables of the scaled expansions for the four child positions c = dx + 2 dy,
+// d = ((2dx-1) + i (2dy-1))/2 (child centre minus parent centre over the parent
+// half-width): dtab[c][k] = d^k and dtab[4 + c][k] = (2d)^-k, k <= LBF_MAX_TERMS.
+__device__ __forceinline__ const double2 *dpow(const double2 *dtab, int c)
+{
+    return dtab + (size_t)c * (LBF_MAX_TERMS + 1);
+}
+__device__ __forceinline__ const double2 *d2inv(const double2 *dtab, int c)
+{
+    return dtab + (size_t)(4 + c) * (LBF_MAX_TERMS + 1);
+}
+
+// Upward pass in one launch.  Every warp takes a leaf and forms its multipole
+// (P2M, a_k = sum_j q_j ((xi_j - c)/r)^k: lanes take nodes, terms go through
+// shared memory, lanes then take coefficients and sum in node order).  Then the
+// warp that completes the last child of a box (a per-box arrival counter) forms
+// that box's multipole from all its children, in child order, and climbs on:
+//   M2M  a_l = d^l sum_{k<=l} C(l,k) (2d)^-k a'_k   (= sum_k C(l,k) d^(l-k) 2^-k a'_k).
+// No warp waits for another; the summation order does not depend on arrival order.
+__global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
+                     const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
+                     const int32_t *__restrict__ iy, const int32_t *__restrict__ bg,
+                     const int32_t *__restrict__ en, const int32_t *__restrict__ parent,
+                     const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
+                     BoxGeo g, int P, const double *__restrict__ binom,
+                     const double2 *__restrict__ dtab, const double2 *__restrict__ xi,
+                     const double2 *__restrict__ q, double2 *mp, int *cnt, const int *gate)
 {
     if (gate_closed(gate)) return;
-    extern __shared__ double2 sm[];
+    extern __shared__ double sm_up[];
+    const int nw = blockDim.x >> 5;
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2 *T = sm + (size_t)wid * P * 32;
-    int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
+    const int cl_len = (P * P + 1) & ~1;                  // keep the double2 region 16-byte aligned
+    double *Cl = sm_up;                                   // P x P, Cl[k*P + l] = C(l, k) (0 for k > l)
+    double2 *T = (double2 *)(sm_up + cl_len) + (size_t)wid * P * 32;
+    double2 *A = (double2 *)(sm_up + cl_len) + (size_t)nw * P * 32 + (size_t)wid * P;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        int k = e / P, l = e % P;
+        Cl[e] = k <= l ? binom[l * LBF_MAX_TERMS + k] : 0.0;
+    }
+    __syncthreads();
+    int64_t t = blockIdx.x * (int64_t)nw + wid;
     if (t >= nleaf) return;
     int b = leaves[t];
-    double cx, cy, r;
-    box_centre(g, level[b], ix[b], iy[b], cx, cy, r);
-    double ir = 1.0 / r;
-    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
-    for (int base = bg[b]; base < en[b]; base += 32) {
-        int j = base + lane;
-        double2 z = make_double2(0, 0), term = make_double2(0, 0);
-        if (j < en[b]) {
-            double2 x = xi[j];
-            z = make_double2((x.x - cx) * ir, (x.y - cy) * ir);
-            term = q[j];
-        }
-        for (int k = 0; k < P; k++) {
-            T[k * 32 + lane] = term;
-            term = cmul(term, z);
-        }
-        __syncwarp();
-        for (int k = lane; k < P; k += 32) {
-            double2 s = make_double2(0, 0);
-            for (int m = 0; m < 32; m++) {
-                double2 v = T[k * 32 + m];
-                s.x += v.x;
-                s.y += v.y;
+    {
+        double cx, cy, r;
+        box_centre(g, level[b], ix[b], iy[b], cx, cy, r);
+        double ir = 1.0 / r;
+        double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
+        for (int base = bg[b]; base < en[b]; base += 32) {
+            int j = base + lane;
+            double2 z = make_double2(0, 0), term = make_double2(0, 0);
+            if (j < en[b]) {
+                double2 x = xi[j];
+                z = make_double2((x.x - cx) * ir, (x.y - cy) * ir);
+                term = q[j];
             }
-            if (k < 32) { acc0.x += s.x; acc0.y += s.y; }
-            else { acc1.x += s.x; acc1.y += s.y; }
+            for (int k = 0; k < P; k++) {
+                T[k * 32 + lane] = term;
+                term = cmul(term, z);
+            }
+            __syncwarp();
+            for (int k = lane; k < P; k += 32) {
+                double2 s = make_double2(0, 0);
+                for (int m = 0; m < 32; m++) {
+                    double2 v = T[k * 32 + m];
+                    s.x += v.x;
+                    s.y += v.y;
+                }
+                if (k < 32) { acc0.x += s.x; acc0.y += s.y; }
+                else { acc1.x += s.x; acc1.y += s.y; }
+            }
+            __syncwarp();
         }
-        __syncwarp();
+        if (lane < P) mp[(int64_t)b * P + lane] = acc0;
+        if (lane + 32 < P) mp[(int64_t)b * P + lane + 32] = acc1;
     }
-    if (lane < P) mp[(int64_t)b * P + lane] = acc0;
-    if (lane + 32 < P) mp[(int64_t)b * P + lane + 32] = acc1;
+    int cur = b;
+    for (;;) {
+        int p = parent[cur];
+        if (p < 0) break;
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            int old = atomicAdd(&cnt[p], 1);
+            last = old == nchild[p] - 1;
+            if (last) cnt[p] = 0;  // ready for the next application
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) break;
+        __threadfence();
+        int l0 = lane, l1 = lane + 32;
+        double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
+        for (int c = child0[p]; c < child0[p] + nchild[p]; c++) {
+            int d = (ix[c] & 1) + 2 * (iy[c] & 1);
+            const double2 *inv = d2inv(dtab, d);
+            for (int k = lane; k < P; k += 32) A[k] = cmul(__ldcg(&mp[(int64_t)c * P + k]), inv[k]);
+            __syncwarp();
+            double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+            for (int k = 0; k < P; k++) {
+                double2 a = A[k];
+                double c0 = Cl[k * P + (l0 < P ? l0 : 0)];
+                s0.x = fma(c0, a.x, s0.x);
+                s0.y = fma(c0, a.y, s0.y);
+                if (l1 < P) {
+                    double c1 = Cl[k * P + l1];
+                    s1.x = fma(c1, a.x, s1.x);
+                    s1.y = fma(c1, a.y, s1.y);
+                }
+            }
+            const double2 *dp = dpow(dtab, d);
+            acc0 = cfma(dp[l0], s0, acc0);
+            if (l1 < P) acc1 = cfma(dp[l1], s1, acc1);
+            __syncwarp();
+        }
+        if (l0 < P) mp[(int64_t)p * P + l0] = acc0;
+        if (l1 < P) mp[(int64_t)p * P + l1] = acc1;
+        cur = p;
+    }
 }
 
-// M2M for the non-leaf boxes of one level: a_l = sum_children sum_{k<=l} S_d[l][k] a'_k,
-// S_d[l][k] = C(l,k) d^(l-k) 2^-k, d = (child centre - parent centre)/r.
-__global__ void k_m2m(int64_t ls, int64_t le, const int32_t *__restrict__ child0,
-                      const int32_t *__restrict__ nchild, const int32_t *__restrict__ ix,
-                      const int32_t *__restrict__ iy, int P, const double2 *__restrict__ S,
-                      double2 *__restrict__ mp, const int *gate)
+__device__ __forceinline__ double2 warp_sum2(double2 v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// Downward pass for the boxes of one level: the local expansion of box b is
+//   L2L from its parent:  b'_l = (2d)^-l sum_{k>=l} C(k,l) d^k b_k
+// plus, scaled by 1/r,
+//   M2L over V(b):  (-1)^l t^(l+1) sum_k C(k+l, l) t^k a_k,  t = 1/(2 (dx + i dy))
+//   P2L over X(b):  (-1)^l sum_j q_j tau_j^(l+1),  tau_j = r / (c - xi_j).
+// Warp per box, lane per coefficient; the binomial tables sit in shared memory
+// with lanes on consecutive entries.  For P2L the lanes take source nodes and
+// run the power recurrence; each coefficient is summed across the warp.
+__global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level,
+                       const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
+                       const int32_t *__restrict__ parent, const int32_t *__restrict__ vlist,
+                       const int32_t *__restrict__ nv, const int32_t *__restrict__ xlist,
+                       const int32_t *__restrict__ nx, const int32_t *__restrict__ bg,
+                       const int32_t *__restrict__ en, BoxGeo g, int P,
+                       const double *__restrict__ binom, const double2 *__restrict__ tpow,
+                       const double2 *__restrict__ dtab, const double2 *__restrict__ xi,
+                       const double2 *__restrict__ q, const double2 *__restrict__ mp,
+                       double2 *__restrict__ loc, const int *gate)
 {
     if (gate_closed(gate)) return;
-    extern __shared__ double2 sm[];
+    extern __shared__ double sm_dn[];
+    const int nw = blockDim.x >> 5;
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2 *A = sm + (size_t)wid * P;
-    int64_t b = ls + blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
-    if (b >= le || nchild[b] == 0) return;
-    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
-    for (int c = child0[b]; c < child0[b] + nchild[b]; c++) {
-        int d = (ix[c] & 1) + 2 * (iy[c] & 1);
-        for (int k = lane; k < P; k += 32) A[k] = mp[(int64_t)c * P + k];
+    double *Cm = sm_dn;             // Cm[k*P + l] = C(k+l, l)
+    double *Cd = sm_dn + P * P;     // Cd[k*P + l] = C(k, l) (0 for k < l)
+    double2 *A = (double2 *)(sm_dn + 2 * P * P) + (size_t)wid * P;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        int k = e / P, l = e % P;
+        Cm[e] = binom[(k + l) * LBF_MAX_TERMS + l];
+        Cd[e] = k >= l ? binom[k * LBF_MAX_TERMS + l] : 0.0;
+    }
+    __syncthreads();
+    int64_t b = ls + blockIdx.x * (int64_t)nw + wid;
+    if (b >= le) return;
+    const int l0 = lane, l1 = lane + 32;
+    const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
+    int bx = ix[b], by = iy[b];
+    double2 accL0 = make_double2(0, 0), accL1 = make_double2(0, 0);
+    // L2L (the parent's local is complete: it belongs to the previous level's launch)
+    if (level[b] >= 3) {
+        int p = parent[b];
+        int d = (bx & 1) + 2 * (by & 1);
+        const double2 *dp = dpow(dtab, d);
+        for (int k = lane; k < P; k += 32) A[k] = cmul(loc[(int64_t)p * P + k], dp[k]);
         __syncwarp();
-        const double2 *Sd = S + (size_t)d * LBF_MAX_TERMS * LBF_MAX_TERMS;
-        int l0 = lane, l1 = lane + 32;
+        double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
         for (int k = 0; k < P; k++) {
             double2 a = A[k];
-            if (k <= l0 && l0 < P) acc0 = cfma(Sd[l0 * LBF_MAX_TERMS + k], a, acc0);
-            if (k <= l1 && l1 < P) acc1 = cfma(Sd[l1 * LBF_MAX_TERMS + k], a, acc1);
+            double c0 = Cd[k * P + lc0];
+            s0.x = fma(c0, a.x, s0.x);
+            s0.y = fma(c0, a.y, s0.y);
+            if (l1 < P) {
+                double c1 = Cd[k * P + lc1];
+                s1.x = fma(c1, a.x, s1.x);
+                s1.y = fma(c1, a.y, s1.y);
+            }
         }
+        const double2 *inv = d2inv(dtab, d);
+        accL0 = cmul(inv[l0], s0);
+        if (l1 < P) accL1 = cmul(inv[l1], s1);
         __syncwarp();
     }
-    if (lane < P) mp[b * P + lane] = acc0;
-    if (lane + 32 < P) mp[b * P + lane + 32] = acc1;
-}
-
-// M2L over V(b) and P2L over X(b) for every box; writes the box's local
-// expansion (zero where both lists are empty).
-//   M2L: b_l = (1/r) (-1)^l t^(l+1) sum_k C(k+l, l) t^k a_k,  t = r / (c_t - c_s)
-//        = 1 / (2 (dx + i dy)) for a same-level offset (dx, dy) in box widths.
-//   P2L: b_l = (1/r) (-1)^l sum_j q_j tau_j^(l+1),  tau_j = r / (c - xi_j).
-__global__ void k_m2l(int64_t nbox, const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
-                      const int32_t *__restrict__ iy, const int32_t *__restrict__ vlist,
-                      const int32_t *__restrict__ nv, const int32_t *__restrict__ xlist,
-                      const int32_t *__restrict__ nx, const int32_t *__restrict__ bg,
-                      const int32_t *__restrict__ en, BoxGeo g, int P,
-                      const double *__restrict__ binom, const double2 *__restrict__ tpow,
-                      const double2 *__restrict__ xi, const double2 *__restrict__ q,
-                      const double2 *__restrict__ mp, double2 *__restrict__ loc, const int *gate)
-{
-    if (gate_closed(gate)) return;
-    extern __shared__ double2 sm[];
-    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2 *A = sm + (size_t)wid * P;
-    int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
-    if (b >= nbox) return;
-    int l0 = lane, l1 = lane + 32;
-    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
-    int bx = ix[b], by = iy[b];
-    for (int v = 0; v < nv[b]; v++) {
-        int s = vlist[b * 27 + v];
+    double2 accF0 = make_double2(0, 0), accF1 = make_double2(0, 0);
+    for (int vq = 0; vq < nv[b]; vq++) {
+        int s = vlist[b * 27 + vq];
         int o = (bx - ix[s] + 3) * 7 + (by - iy[s] + 3);
         const double2 *tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
         for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
@@ -222,83 +312,53 @@ __global__ void k_m2l(int64_t nbox, const int32_t *__restrict__ level, const int
         double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
         for (int k = 0; k < P; k++) {
             double2 a = A[k];
-            double c0 = binom[(k + l0) * LBF_MAX_TERMS + l0];
+            double c0 = Cm[k * P + lc0];
             s0.x = fma(c0, a.x, s0.x);
             s0.y = fma(c0, a.y, s0.y);
             if (l1 < P) {
-                double c1 = binom[(k + l1) * LBF_MAX_TERMS + l1];
+                double c1 = Cm[k * P + lc1];
                 s1.x = fma(c1, a.x, s1.x);
                 s1.y = fma(c1, a.y, s1.y);
             }
         }
         double2 f0 = tp[l0 + 1];
         if (l0 & 1) { f0.x = -f0.x; f0.y = -f0.y; }
-        acc0 = cfma(f0, s0, acc0);
+        accF0 = cfma(f0, s0, accF0);
         if (l1 < P) {
             double2 f1 = tp[l1 + 1];
             if (l1 & 1) { f1.x = -f1.x; f1.y = -f1.y; }
-            acc1 = cfma(f1, s1, acc1);
+            accF1 = cfma(f1, s1, accF1);
         }
         __syncwarp();
     }
     double cx, cy, r;
     box_centre(g, level[b], bx, by, cx, cy, r);
+    double ir = 1.0 / r;
     for (int xq = 0; xq < nx[b]; xq++) {
         int s = xlist[b * 16 + xq];
-        for (int j = bg[s]; j < en[s]; j++) {
-            double2 z = xi[j];
-            double2 tau = crcp(make_double2((cx - z.x) / r, (cy - z.y) / r));
-            double2 qq = q[j];
-            // tau^(l+1) by repeated squaring, l = lane
-            double2 pw = make_double2(1, 0), base = tau;
-            int e = l0 + 1;
-            while (e) {
-                if (e & 1) pw = cmul(pw, base);
-                base = cmul(base, base);
-                e >>= 1;
+        for (int base = bg[s]; base < en[s]; base += 32) {
+            int j = base + lane;
+            double2 tau = make_double2(0, 0), term = make_double2(0, 0);
+            if (j < en[s]) {
+                double2 z = xi[j];
+                tau = crcp(make_double2((cx - z.x) * ir, (cy - z.y) * ir));
+                term = cmul(q[j], tau);  // q tau^(l+1) at l = 0
             }
-            double2 t0 = cmul(qq, pw);
-            if (l0 & 1) { t0.x = -t0.x; t0.y = -t0.y; }
-            acc0.x += t0.x; acc0.y += t0.y;
-            if (l1 < P) {
-                double2 t32 = tau;
-                for (int m = 0; m < 5; m++) t32 = cmul(t32, t32);  // tau^32
-                double2 t1 = cmul(t0, t32);
-                acc1.x += t1.x; acc1.y += t1.y;  // (-1)^(l+32) = (-1)^l
+            for (int l = 0; l < P; l++) {
+                double2 v = warp_sum2(term);
+                if (l & 1) { v.x = -v.x; v.y = -v.y; }
+                if (lane == (l & 31)) {
+                    if (l < 32) { accF0.x += v.x; accF0.y += v.y; }
+                    else { accF1.x += v.x; accF1.y += v.y; }
+                }
+                term = cmul(term, tau);
             }
         }
     }
-    double ir = 1.0 / r;
-    if (l0 < P) loc[b * P + l0] = make_double2(acc0.x * ir, acc0.y * ir);
-    if (l1 < P) loc[b * P + l1] = make_double2(acc1.x * ir, acc1.y * ir);
-}
-
-// L2L into the boxes of one level: b'_l += sum_{k>=l} T_d[l][k] b_k,
-// T_d[l][k] = 2^-l C(k,l) d^(k-l), d = (child centre - parent centre)/r.
-__global__ void k_l2l(int64_t ls, int64_t le, const int32_t *__restrict__ parent,
-                      const int32_t *__restrict__ ix, const int32_t *__restrict__ iy, int P,
-                      const double2 *__restrict__ Tm, double2 *__restrict__ loc, const int *gate)
-{
-    if (gate_closed(gate)) return;
-    extern __shared__ double2 sm[];
-    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2 *B = sm + (size_t)wid * P;
-    int64_t c = ls + blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
-    if (c >= le) return;
-    int p = parent[c];
-    int d = (ix[c] & 1) + 2 * (iy[c] & 1);
-    for (int k = lane; k < P; k += 32) B[k] = loc[(int64_t)p * P + k];
-    __syncwarp();
-    const double2 *Td = Tm + (size_t)d * LBF_MAX_TERMS * LBF_MAX_TERMS;
-    int l0 = lane, l1 = lane + 32;
-    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
-    for (int k = 0; k < P; k++) {
-        double2 a = B[k];
-        if (k >= l0 && l0 < P) acc0 = cfma(Td[l0 * LBF_MAX_TERMS + k], a, acc0);
-        if (k >= l1 && l1 < P) acc1 = cfma(Td[l1 * LBF_MAX_TERMS + k], a, acc1);
-    }
-    if (l0 < P) { double2 o = loc[c * P + l0]; loc[c * P + l0] = make_double2(o.x + acc0.x, o.y + acc0.y); }
-    if (l1 < P) { double2 o = loc[c * P + l1]; loc[c * P + l1] = make_double2(o.x + acc1.x, o.y + acc1.y); }
+    if (l0 < P)
+        loc[b * P + l0] = make_double2(accL0.x + accF0.x * ir, accL0.y + accF0.y * ir);
+    if (l1 < P)
+        loc[b * P + l1] = make_double2(accL1.x + accF1.x * ir, accL1.y + accF1.y * ir);
 }
 
 constexpr int kLeafWarps = 4;
@@ -440,7 +500,10 @@ __global__ void k_evaluate(int64_t N, int M, const double2 *__restrict__ xi,
                            int64_t T, const double *__restrict__ t, int rot_on, const double *rot,
                            double *__restrict__ u)
 {
-    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    // one block per target; threads stride over the nodes, fixed-order block reduction
+    __shared__ double red[32];
+    int64_t wid = blockIdx.x;
+    int lane = threadIdx.x & 31;
     if (wid >= T) return;
     double p[3] = {t[3 * wid], t[3 * wid + 1], t[3 * wid + 2]};
     if (rot_on) {
@@ -453,14 +516,19 @@ __global__ void k_evaluate(int64_t N, int M, const double2 *__restrict__ xi,
     double acc = 0.0;
     if (w > 0.0) {  // a target at the pole sees no Cauchy term (xi = infinity)
         double zx = p[0] / w, zy = p[1] / w;
-        for (int64_t j = lane; j < N; j += 32) {
+        for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
             double dr = xi[j].x - zx, di = xi[j].y - zy;
             double2 qq = q[j];
-            acc += (qq.y * dr - qq.x * di) / (dr * dr + di * di);
+            acc = fma(fma(qq.y, dr, -qq.x * di), rcp_nr(fma(dr, dr, di * di)), acc);
         }
     }
-    acc = warp_sum(acc) * (1.0 / (2.0 * LBF_PI));
-    if (lane == 0) {
+    acc = warp_sum(acc);
+    if (lane == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        acc = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) acc += red[k];
+        acc *= 1.0 / (2.0 * LBF_PI);
         double s = acc + *bsig;
         if (a) {
             for (int m = 0; m < M; m++) {
@@ -492,7 +560,8 @@ __global__ void k_green_sum(int64_t T, const double *__restrict__ t, int64_t S,
 
 int lbf_fmm_init_attrs()
 {
-    LBF_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    LBF_CUDA(cudaFuncSetAttribute(k_up, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    LBF_CUDA(cudaFuncSetAttribute(k_down, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     return LBF_OK;
 }
 
@@ -519,35 +588,27 @@ int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, c
     Tree &T = pl->tree;
     BoxGeo g{T.xmin, T.ymin, T.L};
     int P = pl->P;
-    // upward pass
-    {
-        int wpb = 2;
-        size_t smem = (size_t)wpb * P * 32 * sizeof(double2);
-        LBF_LAUNCH_P(LBF_KERNEL_P2M, k_p2m, lbf_cdiv(T.nleaf, wpb), 32 * wpb, smem, s, T.nleaf, T.leaves, T.level,
-                   T.ix, T.iy, T.begin, T.end, g, P, pl->xi, pl->q, pl->mpole, gate);
+    {   // upward pass: P2M and every M2M level in one launch
+        const int wpb = 2;
+        size_t smem = sizeof(double) * ((P * P + 1) & ~1) + sizeof(double2) * (size_t)wpb * P * 33;
+        LBF_LAUNCH_P(LBF_KERNEL_UP, k_up, lbf_cdiv(T.nleaf, wpb), 32 * wpb, smem, s, T.nleaf,
+                     T.leaves, T.level, T.ix, T.iy, T.begin, T.end, T.parent, T.child0, T.nchild,
+                     g, P, pl->tab_binom, pl->tab_dshift, pl->xi, pl->q, pl->mpole, pl->upcnt,
+                     gate);
         LBF_CHECK_LAUNCH();
     }
-    const int wpb = 4;
-    size_t smemP = (size_t)wpb * P * sizeof(double2);
-    for (int l = T.nlev - 2; l >= 2; l--) {
-        int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
-        if (le <= ls) continue;
-        LBF_LAUNCH_P(LBF_KERNEL_M2M, k_m2m, lbf_cdiv(le - ls, wpb), 32 * wpb, smemP, s, ls, le, T.child0, T.nchild,
-                   T.ix, T.iy, P, pl->tab_m2m, pl->mpole, gate);
-        LBF_CHECK_LAUNCH();
-    }
-    // interaction lists into local expansions
-    LBF_LAUNCH_P(LBF_KERNEL_M2L, k_m2l, lbf_cdiv(T.nbox, wpb), 32 * wpb, smemP, s, T.nbox, T.level, T.ix, T.iy,
-               T.vlist, T.nv, T.xlist, T.nx, T.begin, T.end, g, P, pl->tab_binom,
-               pl->tab_tpow, pl->xi, pl->q, pl->mpole, pl->local, gate);
-    LBF_CHECK_LAUNCH();
-    // downward pass
-    for (int l = 3; l < T.nlev; l++) {
-        int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
-        if (le <= ls) continue;
-        LBF_LAUNCH_P(LBF_KERNEL_L2L, k_l2l, lbf_cdiv(le - ls, wpb), 32 * wpb, smemP, s, ls, le, T.parent, T.ix, T.iy,
-                   P, pl->tab_l2l, pl->local, gate);
-        LBF_CHECK_LAUNCH();
+    {   // downward pass, level by level: L2L + M2L + P2L into the local expansions
+        const int wpb = 8;
+        size_t smem = sizeof(double) * 2 * P * P + sizeof(double2) * (size_t)wpb * P;
+        for (int l = 0; l < T.nlev; l++) {
+            int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
+            if (le <= ls) continue;
+            LBF_LAUNCH_P(LBF_KERNEL_DOWN, k_down, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s, ls, le,
+                         T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin,
+                         T.end, g, P, pl->tab_binom, pl->tab_tpow, pl->tab_dshift, pl->xi, pl->q,
+                         pl->mpole, pl->local, gate);
+            LBF_CHECK_LAUNCH();
+        }
     }
     LBF_LAUNCH_P(LBF_KERNEL_LEAF, k_leaf, lbf_cdiv(T.nleaf, kLeafWarps), 32 * kLeafWarps, 0, s, T.nleaf, T.leaves,
                T.level, T.ix, T.iy, T.begin, T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P,
@@ -562,7 +623,7 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
     int rc = prep(pl, sigma_sorted, nullptr, s);
     if (rc) return rc;
     if (T <= 0) return LBF_OK;
-    LBF_LAUNCH(k_evaluate, lbf_cdiv(T * 32, 256), 256, 0, s, pl->N, pl->M, pl->xi, pl->q,
+    LBF_LAUNCH(k_evaluate, T, 256, 0, s, pl->N, pl->M, pl->xi, pl->q,
                pl->bsig, a, pl->centres, T, t, pl->has_rot, pl->rot_d, u);
     LBF_CHECK_LAUNCH();
     return LBF_OK;

@@ -130,22 +130,22 @@ __global__ void k_build_E(int64_t N, int M, const int32_t *__restrict__ perm,
 // island r+1 (the unweighted constraint rows, Eq. disc_constr); the last row is
 // D's row of ones (Eq. sum_ak).  Stored in the left half of an M x 2M block
 // [S | I] for Gauss-Jordan inversion.  One warp per entry, fixed summation order.
-__global__ void k_schur(int M, const int64_t *__restrict__ ptr, const double *__restrict__ x3_o,
-                        const double *__restrict__ c, double *__restrict__ G)
+__global__ void k_schur(int64_t N, int M, const int64_t *__restrict__ ptr,
+                        const int32_t *__restrict__ rank, const double *__restrict__ E,
+                        double *__restrict__ G)
 {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
-    if (warp >= M * M) return;
-    int r = warp / M, m = warp % M;
+    if (warp >= (int64_t)M * M) return;
+    int r = (int)(warp / M), m = (int)(warp % M);
     double v;
     if (r == M - 1) {
         v = 1.0;
     } else {
+        // entries of E (rows in Morton order) gathered over island r+1 in the caller's order
+        const double *Em = E + (int64_t)m * N;
         double s = 0.0;
-        for (int64_t j = ptr[r + 1] + lane; j < ptr[r + 2]; j += 32) {
-            double xv[3] = {x3_o[3 * j], x3_o[3 * j + 1], x3_o[3 * j + 2]};
-            s += two_green(xv, &c[3 * m]);
-        }
+        for (int64_t j = ptr[r + 1] + lane; j < ptr[r + 2]; j += 32) s += Em[rank[j]];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         v = -s;
     }
@@ -271,8 +271,8 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double *x3_o, double *s
     LBF_CHECK_LAUNCH();
     double *G = scratch;  // M x 2M
     int64_t warps = (int64_t)M * M;
-    LBF_LAUNCH(k_schur, lbf_cdiv(warps * 32, 256), 256, 0, s, M, pl->island_ptr, x3_o,
-               pl->centres, G);
+    LBF_LAUNCH(k_schur, lbf_cdiv(warps * 32, 256), 256, 0, s, N, M, pl->island_ptr, pl->rank,
+               pl->E, G);
     LBF_CHECK_LAUNCH();
     for (int k = 0; k < M; k++) {
         LBF_LAUNCH(k_gj_pivot, 1, 1024, 0, s, M, k, G, pl->dev_status);

@@ -99,12 +99,12 @@ struct lbf_plan {
     double *rot_d = nullptr;  // device copy of rot
     // translation-operator tables (filled on the host at plan time)
     double *tab_binom = nullptr;   // C(n, k), n < 2*LBF_MAX_TERMS, k < LBF_MAX_TERMS
-    double2 *tab_m2m = nullptr;    // 4 child offsets x LBF_MAX_TERMS^2
-    double2 *tab_l2l = nullptr;    // 4 child offsets x LBF_MAX_TERMS^2
+    double2 *tab_dshift = nullptr; // d^k and (2d)^-k for the 4 child offsets, 8 x (LBF_MAX_TERMS + 1)
     double2 *tab_tpow = nullptr;   // 49 same-level offsets x (LBF_MAX_TERMS + 1) powers
     Tree tree;
     // FMM work
     double2 *q = nullptr, *mpole = nullptr, *local = nullptr;
+    int32_t *upcnt = nullptr;   // per-box child arrival counters of the upward pass (kept at 0)
     double *v = nullptr;        // (I + K - I) sigma = K sigma, doubled scaling
     double *bsig = nullptr;     // scalar beta . sigma
     double *red = nullptr;      // reduction partials
@@ -124,6 +124,7 @@ struct lbf_plan {
     char *region = nullptr;      // GMRES basis, or plan-creation temporaries
     int *dev_status = nullptr;
     int *host_status = nullptr;  // pinned
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // GMRES chunk markers (no device memory)
     double *host_scalars = nullptr;  // pinned
 };
 

@@ -515,16 +515,34 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         if ((rc = read_state(pl, &hs, s))) return rc;
         if (hs.converged || hs.it >= hs.maxit || hs.go == 0) break;
         int steps = std::min(m, hs.maxit - hs.it);
-        for (int k = 0; k < steps; k++) {
-            // w = P^-1 A v_j  (j read on the device)
-            // the operator reads V[j]: use the pointer of column k (j == k within a cycle)
-            const double *vj = V + (int64_t)k * ldv;
-            if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, vj, w, &pl->gs->go, s))) return rc;
-            for (int mode = 0; mode < 3; mode++)
-                LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w, pl->gpart, count, hbuf,
-                           pl->H, cs, sn, gv, pl->gs, mode);
-            LBF_LAUNCH(k_scale_next, nblk, 256, 0, s, n, w, V, ldv, pl->gs);
-            LBF_CHECK_LAUNCH();
+        // Arnoldi steps are queued in chunks; before queueing a chunk the host looks
+        // at the state copied after the chunk before last (double-buffered pinned
+        // copy + event), so at most two chunks run past convergence, and those
+        // return at once on the device gate.
+        const int chunk = 4;
+        for (int c = 0, k0 = 0; k0 < steps; c++) {
+            const int slot = c & 1;
+            if (c >= 2) {  // the state recorded after chunk c-2 (chunk c-1 keeps the GPU busy)
+                LBF_CUDA(cudaEventSynchronize(pl->ev[slot]));
+                GmresState chk;
+                memcpy(&chk, (char *)pl->host_scalars + 64 * (1 + slot), sizeof(GmresState));
+                if (chk.go == 0) break;
+            }
+            int k1 = std::min(steps, k0 + chunk);
+            for (int k = k0; k < k1; k++) {
+                // w = P^-1 A v_j: within a cycle the device's j equals the host's k
+                const double *vj = V + (int64_t)k * ldv;
+                if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, vj, w, &pl->gs->go, s))) return rc;
+                for (int mode = 0; mode < 3; mode++)
+                    LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w,
+                                 pl->gpart, count, hbuf, pl->H, cs, sn, gv, pl->gs, mode);
+                LBF_LAUNCH(k_scale_next, nblk, 256, 0, s, n, w, V, ldv, pl->gs);
+                LBF_CHECK_LAUNCH();
+            }
+            k0 = k1;
+            LBF_CUDA(cudaMemcpyAsync((char *)pl->host_scalars + 64 * (1 + slot), pl->gs,
+                                     sizeof(GmresState), cudaMemcpyDeviceToHost, s));
+            LBF_CUDA(cudaEventRecord(pl->ev[slot], s));
         }
         // cycle end: x += V y
         LBF_LAUNCH(k_solve_y, 1, 32, 0, s, pl->H, gv, y, pl->gs);

@@ -39,10 +39,8 @@ __global__ void k_counts(int64_t nbox, const int32_t *__restrict__ level,
         atomicAdd(&c[5], nb * (unsigned long long)(wptr[b + 1] - wptr[b]));
         atomicAdd(&c[7], 1ull);
     }
-    if (level[b] >= 3) {
-        atomicAdd(&c[2], 1ull);
-        atomicAdd(&c[4], 1ull);
-    }
+    if (level[b] >= 1) atomicAdd(&c[2], 1ull);  // every non-root box shifts into its parent
+    if (level[b] >= 3) atomicAdd(&c[4], 1ull);  // locals are non-zero from level 2 down
     atomicAdd(&c[3], (unsigned long long)nv[b]);
     unsigned long long sx = 0;
     for (int q = 0; q < nx[b]; q++) {

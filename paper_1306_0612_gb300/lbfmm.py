@@ -273,9 +273,9 @@ def lbf_list_export(plan: Plan, kind: int, stream=None):
     return ptr, idx[: n.value]
 
 
-LBF_KERNEL_P2M, LBF_KERNEL_M2M, LBF_KERNEL_M2L, LBF_KERNEL_L2L = 0, 1, 2, 3
-LBF_KERNEL_LEAF, LBF_KERNEL_DIRECT, LBF_KERNEL_ARNOLDI, LBF_KERNEL_ESUM = 4, 5, 6, 7
-KERNEL_NAMES = ["p2m", "m2m", "m2l", "l2l", "leaf", "direct", "arnoldi", "esum"]
+LBF_KERNEL_UP, LBF_KERNEL_DOWN, LBF_KERNEL_LEAF = 0, 1, 2
+LBF_KERNEL_DIRECT, LBF_KERNEL_ARNOLDI, LBF_KERNEL_ESUM = 3, 4, 5
+KERNEL_NAMES = ["up", "down", "leaf", "direct", "arnoldi", "esum"]
 
 
 def lbf_plan_counts(plan: Plan, stream=None) -> dict:
