@@ -4,10 +4,11 @@
 One step = one pass of the whole path on one geometry with inputs resident in
 HBM: plan creation (stereographic projection and per-node precompute, Morton
 quadtree and interaction lists, border E and inverse Schur complement), the
-left-preconditioned GMRES(50) solve to a 1e-10 relative residual whose every
-iteration applies the FP64 FMM operator, and the evaluation of u at off-curve
-targets.  The headline value is the FMM-operator throughput inside the solve:
-N x (operator applications) / step time, in Mpts/s.
+left-preconditioned GMRES solve to a 1e-10 relative residual (by default with
+FP32-FMM inner solves and FP64 iterative refinement of the residual; --precision
+fp64 applies the FP64 FMM in every iteration), and the evaluation of u at
+off-curve targets.  The headline value is the operator throughput inside the
+solve: N x (operator applications, both precisions) / step time, in Mpts/s.
 
 Workload (default): 1024 star-cap islands x 1024 nodes (N = 1,048,576), seed 3,
 Green's-function pair data with sources in islands 0 and 1, 256 targets.
@@ -31,7 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FMM matvec Mpts/s and GMRES solve time at 1e-10 rel err; fraction of FP64 peak"
-FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of one GB300 (recipe table)
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of one GB300 (recipe table)
+FP32_PEAK_TFLOPS = 80.6   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 WORKLOADS = {
     "C3-256": dict(M=256, nodes=1024),
     "C3-1024": dict(M=1024, nodes=1024),
@@ -47,9 +49,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="C3-1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32r", choices=["fp64", "fp32r"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--p32", type=int, default=None)
     ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--inner-tol", type=float, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--targets", type=int, default=256)
@@ -69,12 +74,12 @@ def make_inputs(name):
     return g, src, gam, np
 
 
-def workload_config(name, g, T, tol):
+def workload_config(name, g, T, tol, precision):
     w = WORKLOADS[name]
     return {"workload": f"{name}: {w['M']} star-cap islands x {w['nodes']} nodes "
                         f"(N={g.N}), Green's-pair data, GMRES(50) tol {tol:g}, {T} targets",
-            "islands": g.M, "nodes": g.N, "targets": T, "l2": "inputs larger than L2 (E block "
-            f"{g.N * g.M * 8 / 1e9:.1f} GB, FMM arrays)", "precision": "fp64"}
+            "islands": g.M, "nodes": g.N, "targets": T, "precision": precision,
+            "l2": f"inputs larger than L2 (E block {g.N * g.M * 8 / 1e9:.1f} GB, FMM arrays)"}
 
 
 # ---- clocks -------------------------------------------------------------------------
@@ -131,7 +136,7 @@ class Clocks:
 
 def oracle_rate(g, np, rows=256, seed=11):
     """The oracle's direct matvec (entries computed on the fly, OpenMP rows) on a
-    sample of rows; returns (Mpts/s of a full N-row matvec, seconds, threads)."""
+    sample of rows; returns (Mpts/s of a full N-row matvec, seconds, threads, rows)."""
     import oracle
 
     oracle.build()
@@ -162,7 +167,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": val, "unit": "Mpts/s", "impl": "reference", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(dts),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, g, args.targets, args.tol),
+            "data": "synthetic",
+            "config": workload_config(args.workload, g, args.targets, args.tol, "fp64"),
             "cpu_baseline": {"value": val, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -180,17 +186,32 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_flops(name, c, P, N, M):
-    """Algorithmic work per the FMM's operation counts (one apply)."""
-    if name == "leaf":
-        return 11 * c["p2p_pairs"] + 8 * P * N + 8 * P * c["w_pairs"] + 10 * N
-    if name == "down":  # L2L + M2L + P2L
-        return 8 * P * P * (c["m2l"] + c["l2l"]) + 8 * P * c["x_pairs"]
-    if name == "up":  # P2M + M2M
-        return 8 * P * N + 8 * P * P * c["m2m"]
-    if name == "direct":
-        return 11 * N * (N - 1)
-    return None
+def kernel_work(name, c, P, P32, N, M):
+    """(algorithmic work of one operator application, unit) per the FMM's
+    operation counts: 11 flops per near pair, 8(p+1) per node for P2M and L2P and
+    per (node, box) for M2P/P2L, 8(p+1)^2 per translation, 10 per node to combine;
+    the E pass streams 8 N M bytes."""
+    base = name[:-2] if name.endswith("32") else name
+    Q = P32 if name.endswith("32") else P
+    if base == "leaf":
+        return 11 * c["p2p_pairs"] + 8 * Q * N + 8 * Q * c["w_pairs"] + 10 * N, "TFLOP/s"
+    if base == "down":
+        return 8 * Q * Q * (c["m2l"] + c["l2l"]) + 8 * Q * c["x_pairs"], "TFLOP/s"
+    if base == "up":
+        return 8 * Q * N + 8 * Q * Q * c["m2m"], "TFLOP/s"
+    if base == "direct":
+        return 11 * N * (N - 1), "TFLOP/s"
+    if base == "esum":
+        return 8 * N * M, "GB/s"
+    return None, None
+
+
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def run_ours(args):
@@ -223,10 +244,11 @@ def run_ours(args):
     uex = torch.empty(T, dtype=torch.float64, device=dev)
     L.lbf_green_sum(tgt, srcd, gamd, uex)
     kw = dict(tol=args.tol)
-    if args.p:
-        kw["p"] = args.p
-    if args.leaf:
-        kw["leaf_size"] = args.leaf
+    if args.precision == "fp32r":
+        kw["precision"] = L.LBF_PRECISION_FP32_REFINE
+    for k, v in (("p", args.p), ("p32", args.p32), ("leaf_size", args.leaf), ("inner_tol", args.inner_tol)):
+        if v:
+            kw[k] = v
     opt = L.lbf_default_options(**kw)
     sig = torch.empty(g.N, dtype=torch.float64, device=dev)
     a = torch.empty(g.M, dtype=torch.float64, device=dev)
@@ -238,7 +260,7 @@ def run_ours(args):
         rc, its, rr = L.lbf_gmres_solve(plan, data, sig, a)
         L.lbf_evaluate(plan, sig, a, tgt, u)
         holder["plan"] = plan
-        return rc, its, rr
+        return rc, its, rr, L.lbf_solve_stats(plan)
 
     for _ in range(args.warmup):
         step()
@@ -250,13 +272,16 @@ def run_ours(args):
     n0 = L.lbf_launch_count()
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    its_total = 0
+    tot = dict(arnoldi=0, fp64_applies=0, fp32_applies=0, refine_steps=0)
+    rcs = []
     with Clocks(local) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            rc, its, rr = step()
-            its_total += its
+            rc, its, rr, st = step()
+            rcs.append(rc)
+            for k in tot:
+                tot[k] += st[k]
         ev1.record(stream)
         torch.cuda.synchronize()
     L.lbf_profile_enable(False)
@@ -270,7 +295,7 @@ def run_ours(args):
     plan = holder["plan"]
     info = plan.info()
     counts = L.lbf_plan_counts(plan)
-    P = info["p"] + 1
+    P, P32 = info["p"] + 1, opt.p32 + 1
     # per-kernel device time over the timed region (CUDA events on the launch stream)
     prof = {}
     for kid, name in enumerate(L.KERNEL_NAMES):
@@ -279,48 +304,63 @@ def run_ours(args):
             prof[name] = {"launches": n, "ms": tms}
     L.lbf_profile_reset()
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    # operator applications that did work: one per Arnoldi step plus one true
-    # residual per restart (launches queued past convergence return at once)
-    m = opt.restart
-    its_step = its_total / args.steps
-    applies = its_step + max(0, -(-int(its_step) // m) - 1)
-    n_applies = applies * args.steps
-    fl = kernel_flops(dom, counts, P, g.N, g.M)
+    # applications that did work (launches queued past convergence return at once)
+    n64, n32 = tot["fp64_applies"], tot["fp32_applies"]
+    applies = (n64 + n32) / args.steps
+    work, unit = kernel_work(dom, counts, P, P32, g.N, g.M)
     roofline = None
-    if fl is not None:
-        # algorithmic flops of the kernel over the timed region / its summed device time
-        ach = fl * n_applies / (prof[dom]["ms"] / 1e3) / 1e12
+    if work is not None:
+        n_app = n32 if dom.endswith("32") else n64
+        if dom == "esum":
+            n_app = n64 + n32
+        rate = work * n_app / (prof[dom]["ms"] / 1e3)
+        if unit == "GB/s":
+            peak, src_p = measured_hbm()
+            ach, bound = rate / 1e9, "hbm"
+        else:
+            f32 = dom.endswith("32")
+            peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+            src_p = ("FP32 derived from unit counts and the 2.07 GHz clock" if f32 else
+                     "nominal FP64 (recipe table; MEASURED_PEAKS.json has no FP64 entry)")
+            ach, bound = rate / 1e12, "alu"
         traffic = None
         tp = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tp):
             tj = json.load(open(tp))
             if tj.get("src_hash") == src_hash() and dom in tj.get("kernels", {}):
                 traffic = tj["kernels"][dom].get("bytes_per_launch")
-        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
-                    "peak_source": "nominal FP64 (recipe table; not in MEASURED_PEAKS.json)"}
-    # accuracy of the last step
+        roofline = {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": unit,
+                    "frac": ach / peak, "traffic": traffic, "peak_source": src_p}
     err = float((u - uex).abs().max() / uex.abs().max())
-    # pure operator throughput (FMM K-block apply), device-resident
-    vin = torch.randn(g.N, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+    # pure operator throughput of the FMM K-block apply in both precisions
+    vin = torch.randn(g.N, dtype=torch.float64, device=dev,
+                      generator=torch.Generator(device=dev).manual_seed(1))
     vout = torch.empty_like(vin)
-    for _ in range(2):
-        L.lbf_apply(plan, L.LBF_OP_K_ONLY, vin, vout)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    nrep = 5
-    for _ in range(nrep):
-        L.lbf_apply(plan, L.LBF_OP_K_ONLY, vin, vout)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    matvec_ms = e0.elapsed_time(e1) / nrep
+    apply_ms = {}
+    ops = [("fp64", L.LBF_OP_K_ONLY)]
+    if args.precision == "fp32r":
+        ops.append(("fp32", L.LBF_OP_K_ONLY | L.LBF_OP_FP32))
+    ref64 = torch.empty_like(vin)
+    L.lbf_apply(plan, L.LBF_OP_K_ONLY, vin, ref64)
+    apply_err = {}
+    for nm, op in ops:
+        for _ in range(2):
+            L.lbf_apply(plan, op, vin, vout)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            L.lbf_apply(plan, op, vin, vout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        apply_ms[nm] = e0.elapsed_time(e1) / 5
+        apply_err[nm] = float((vout - ref64).norm() / ref64.norm())
     value = g.N * applies * world / (ms / args.steps / 1e3) / 1e6
 
     # end to end through the public API, host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).pin_memory()
+        pin = lambda a_: torch.from_numpy(np.ascontiguousarray(a_, dtype=np.float64).reshape(-1)).pin_memory()
         hx, hdx, hd2x, hc, ht = pin(g.x), pin(g.dx), pin(g.d2x), pin(g.centres), pin(tg)
         hg = data.cpu().pin_memory()
         hu = torch.empty(T, dtype=torch.float64).pin_memory()
@@ -334,28 +374,27 @@ def run_ours(args):
             dc = hc.to(dev, non_blocking=True)
             dt_ = ht.to(dev, non_blocking=True)
             dg = hg.to(dev, non_blocking=True)
-            plan = L.lbf_plan_create(g.island_ptr, dx_, ddx, dd2, dc, opt=opt)
+            pl = L.lbf_plan_create(g.island_ptr, dx_, ddx, dd2, dc, opt=opt)
             s_ = torch.empty(g.N, dtype=torch.float64, device=dev)
             a_ = torch.empty(g.M, dtype=torch.float64, device=dev)
             u_ = torch.empty(T, dtype=torch.float64, device=dev)
-            rc, its, rr = L.lbf_gmres_solve(plan, dg, s_, a_)
-            L.lbf_evaluate(plan, s_, a_, dt_, u_)
+            L.lbf_gmres_solve(pl, dg, s_, a_)
+            L.lbf_evaluate(pl, s_, a_, dt_, u_)
             hu.copy_(u_, non_blocking=True)
-            return its
+            st = L.lbf_solve_stats(pl)
+            return st["fp64_applies"] + st["fp32_applies"]
 
         e2e_step()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        its_e = 0
+        ap_e = 0
         for _ in range(args.steps):
-            its_e += e2e_step()
+            ap_e += e2e_step()
         f1.record(stream)
         torch.cuda.synchronize()
         ems = f0.elapsed_time(f1) / args.steps
-        ie = its_e / args.steps
-        ae = ie + max(0, -(-int(ie) // opt.restart) - 1)
-        e2e = {"value": g.N * ae * world / (ems / 1e3) / 1e6, "unit": "Mpts/s",
+        e2e = {"value": g.N * (ap_e / args.steps) * world / (ems / 1e3) / 1e6, "unit": "Mpts/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ems}
 
     cpu = None
@@ -366,11 +405,16 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": workload_config(args.workload, g, T, args.tol),
-                "solve": {"gmres_iterations": its_total / args.steps, "rel_residual": rr,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": workload_config(args.workload, g, T, args.tol, args.precision),
+                "solve": {"status": rcs, "applies_per_step": applies,
+                          "fp64_applies": n64 / args.steps, "fp32_applies": n32 / args.steps,
+                          "refine_steps": tot["refine_steps"] / args.steps, "rel_residual": rr,
                           "solution_max_rel_err": err, "step_ms": ms / args.steps,
-                          "fmm_apply_ms": matvec_ms, "fmm_apply_mpts": g.N / matvec_ms / 1e3,
+                          "apply_ms": apply_ms, "apply_rel_err_vs_fp64": apply_err,
+                          "apply_mpts": {k: g.N / v / 1e3 for k, v in apply_ms.items()},
                           "tree": info, "counts": counts},
                 "kernels_ms": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

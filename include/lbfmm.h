@@ -78,7 +78,26 @@ typedef struct lbf_options {
                              LBF_OP_FULL, LBF_OP_PRECONDITIONED, gmres and a-terms
                              of evaluate); 0: density block only */
     int64_t box_capacity; /* quadtree boxes reserved in the workspace; 0 = estimate */
+    int precision;        /* LBF_PRECISION_FP64 or LBF_PRECISION_FP32_REFINE */
+    int p32;              /* expansion order of the FP32 FMM (4..31) */
+    double inner_tol;     /* FP32_REFINE: relative tolerance of each inner solve */
+    int max_refine;       /* FP32_REFINE: maximum refinement steps */
 } lbf_options;
+
+/* precision of gmres_solve:
+ *   FP64:        every operator application in double;
+ *   FP32_REFINE: iterative refinement (GMRES-IR): the FP64 residual
+ *                r = P^-1 ([2g; 0] - A x) is formed with the double FMM, the
+ *                correction solves P^-1 A d = r with GMRES whose operator runs
+ *                the FMM in float (expansions, translations and near field;
+ *                node offsets, self terms, the sphere correction, the border
+ *                blocks, the Arnoldi basis and the Givens rotations stay in
+ *                double), and x += d until ||r|| <= tol ||P^-1 [2g; 0]||. */
+#define LBF_PRECISION_FP64 0
+#define LBF_PRECISION_FP32_REFINE 1
+/* lbf_apply: OR this into op to run the FMM part in float (plans built with
+ * LBF_PRECISION_FP32_REFINE) */
+#define LBF_OP_FP32 16
 
 int lbf_default_options(lbf_options *opt /* host */);
 
@@ -143,6 +162,11 @@ int lbf_apply(lbf_plan *plan, int op, const double *in, double *out, lbf_stream_
 int lbf_gmres_solve(lbf_plan *plan, const double *g, double *sigma, double *a, const double *x0,
                     int *iters, double *rel_res, lbf_stream_t stream);
 
+/* Work of the plan's last lbf_gmres_solve (host out): stats[0] Arnoldi steps,
+ * [1] FP64 operator applications, [2] FP32 operator applications,
+ * [3] refinement steps (0 for LBF_PRECISION_FP64). */
+int lbf_solve_stats(const lbf_plan *plan, int64_t stats[4]);
+
 /* u at T points t (T x 3 on the sphere, off the curves, device) from the
  * representation formula (Eq. u_multi): the double layer of sigma plus
  * sum_m a_m G(t, c_m).  a may be NULL (no multiplier sources). */
@@ -186,7 +210,10 @@ int lbf_plan_counts(const lbf_plan *plan, int64_t counts[8], lbf_stream_t stream
 #define LBF_KERNEL_DIRECT 3
 #define LBF_KERNEL_ARNOLDI 4
 #define LBF_KERNEL_ESUM 5   /* E-block pass of the bordered operator */
-#define LBF_KERNEL_COUNT 6
+#define LBF_KERNEL_UP32 6   /* the three FMM passes of the float operator */
+#define LBF_KERNEL_DOWN32 7
+#define LBF_KERNEL_LEAF32 8
+#define LBF_KERNEL_COUNT 9
 int lbf_profile_enable(int on);
 int lbf_profile_reset(void);
 int lbf_profile_read(int kernel, int64_t *launches /* host out */, double *total_ms /* host out */);

@@ -34,7 +34,10 @@ bool valid(const lbf_options &o)
            o.p + 1 <= LBF_MAX_TERMS && o.leaf_size >= 1 && o.leaf_size <= 1024 &&
            o.max_depth >= 1 && o.max_depth <= 30 &&
            (o.matvec == LBF_MATVEC_FMM || o.matvec == LBF_MATVEC_DIRECT) &&
-           (o.border == 0 || o.border == 1);
+           (o.border == 0 || o.border == 1) &&
+           (o.precision == LBF_PRECISION_FP64 || o.precision == LBF_PRECISION_FP32_REFINE) &&
+           o.p32 >= 4 && o.p32 + 1 <= 32 && o.inner_tol > 0 && o.inner_tol < 1 &&
+           o.max_refine >= 1;
 }
 
 // host tables of the translation operators (scaled expansions, see lbf_fmm.cu)
@@ -129,6 +132,22 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         pl->mpole = A.get<double2>(cap * P);
         pl->local = A.get<double2>(cap * P);
         pl->upcnt = A.get<int32_t>(cap);
+    }
+    if (o.precision == LBF_PRECISION_FP32_REFINE) {
+        int P32 = o.p32 + 1;
+        pl->P32 = P32;
+        pl->q32 = A.get<float2>(N);
+        if (o.matvec == LBF_MATVEC_FMM) {
+            pl->mpole32 = A.get<float2>(cap * P32);
+            pl->local32 = A.get<float2>(cap * P32);
+        }
+        pl->tab32_binom = A.get<float>(2 * T * T);
+        pl->tab32_tpow = A.get<float2>(49 * (T + 1));
+        pl->tab32_dshift = A.get<float2>(8 * (T + 1));
+        if (o.border) {
+            pl->gr = A.get<double>(n);
+            pl->gd = A.get<double>(n);
+        }
     }
     pl->v = A.get<double>(N);
     pl->bsig = A.get<double>(4);
@@ -225,6 +244,10 @@ int lbf_default_options(lbf_options *o)
     o->matvec = LBF_MATVEC_FMM;
     o->border = 1;
     o->box_capacity = 0;
+    o->precision = LBF_PRECISION_FP64;
+    o->p32 = 12;
+    o->inner_tol = 1e-4;
+    o->max_refine = 20;
     return LBF_OK;
 }
 
@@ -329,6 +352,15 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     CK(cudaMemcpyAsync(pl->rot_d, pl->rot, sizeof(pl->rot), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(pl->tab_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(pl->tab_dshift, dshift.data(), sizeof(double2) * dshift.size(), cudaMemcpyHostToDevice, s));
+    if (pl->tab32_binom) {  // the same tables rounded to float
+        std::vector<float> b32(binom.begin(), binom.end());
+        std::vector<float2> t32(tpow.size()), d32(dshift.size());
+        for (size_t i = 0; i < tpow.size(); i++) t32[i] = make_float2((float)tpow[i].x, (float)tpow[i].y);
+        for (size_t i = 0; i < dshift.size(); i++) d32[i] = make_float2((float)dshift[i].x, (float)dshift[i].y);
+        CK(cudaMemcpyAsync(pl->tab32_binom, b32.data(), sizeof(float) * b32.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(pl->tab32_tpow, t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(pl->tab32_dshift, d32.data(), sizeof(float2) * d32.size(), cudaMemcpyHostToDevice, s));
+    }
     if (pl->upcnt) CK(cudaMemsetAsync(pl->upcnt, 0, sizeof(int32_t) * cap, s));
     CK(cudaMemcpyAsync(pl->tab_tpow, tpow.data(), sizeof(double2) * tpow.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(pl->dev_status, 0, sizeof(int), s));
@@ -397,13 +429,16 @@ int lbf_geometry_out(const lbf_plan *pl, double *xi, double *normal, double *wei
 
 int lbf_apply(lbf_plan *pl, int op, const double *in, double *out, lbf_stream_t stream)
 {
+    int prec = (op & LBF_OP_FP32) ? LBF_PREC_FP32 : LBF_PREC_FP64;
+    op &= ~LBF_OP_FP32;
     if (!pl || !in || !out || op < 0 || op > 2) return LBF_EINVAL;
     if (op != LBF_OP_K_ONLY && !pl->opt.border) return LBF_ENOTBUILT;
+    if (prec == LBF_PREC_FP32 && !pl->q32) return LBF_ENOTBUILT;
     cudaStream_t s = (cudaStream_t)stream;
     int with_a = op != LBF_OP_K_ONLY;
     int rc = lbf_permute_in(pl, in, pl->tin, with_a, s);
     if (rc) return rc;
-    rc = lbf_apply_op_sorted(pl, op, pl->tin, pl->tout, nullptr, s);
+    rc = lbf_apply_op_sorted(pl, op, pl->tin, pl->tout, nullptr, s, prec);
     if (rc) return rc;
     return lbf_permute_out(pl, pl->tout, out, with_a, s);
 }
@@ -414,6 +449,13 @@ int lbf_gmres_solve(lbf_plan *pl, const double *g, double *sigma, double *a, con
     if (!pl || !g || !sigma) return LBF_EINVAL;
     if (!pl->opt.border) return LBF_ENOTBUILT;
     return lbf_gmres_impl(pl, g, sigma, a, x0, iters, rel_res, (cudaStream_t)stream);
+}
+
+int lbf_solve_stats(const lbf_plan *pl, int64_t stats[4])
+{
+    if (!pl || !stats) return LBF_EINVAL;
+    for (int k = 0; k < 4; k++) stats[k] = pl->stats[k];
+    return LBF_OK;
 }
 
 int lbf_evaluate(lbf_plan *pl, const double *sigma, const double *a, int64_t T,

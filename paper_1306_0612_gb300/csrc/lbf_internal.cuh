@@ -104,6 +104,14 @@ struct lbf_plan {
     Tree tree;
     // FMM work
     double2 *q = nullptr, *mpole = nullptr, *local = nullptr;
+    // float FMM (precision FP32_REFINE)
+    int P32 = 0;
+    float2 *q32 = nullptr, *mpole32 = nullptr, *local32 = nullptr;
+    float *tab32_binom = nullptr;
+    float2 *tab32_tpow = nullptr, *tab32_dshift = nullptr;
+    double *gr = nullptr, *gd = nullptr;  // refinement residual and correction
+    // last solve: Arnoldi steps, FP64 applications, FP32 applications, refinement steps
+    int64_t stats[4] = {0, 0, 0, 0};
     int32_t *upcnt = nullptr;   // per-box child arrival counters of the upward pass (kept at 0)
     double *v = nullptr;        // (I + K - I) sigma = K sigma, doubled scaling
     double *bsig = nullptr;     // scalar beta . sigma
@@ -152,7 +160,10 @@ int lbf_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *scratch, i
 
 // ---- FMM / direct operator (lbf_fmm.cu) -----------------------------------------
 // v = 2 [ (1/2pi) Im sum_{j!=i} q_j/(xi_j - xi_i) + d_i sigma_i + beta.sigma ]   (sorted order)
-int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s);
+#define LBF_PREC_FP64 0
+#define LBF_PREC_FP32 1
+int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s,
+                int prec);
 int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,
                       const double *t, double *u, cudaStream_t s);
 int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p,
@@ -160,7 +171,7 @@ int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p,
 
 // ---- border / krylov (lbf_krylov.cu) -----------------------------------------------
 int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, const int *gate,
-                        cudaStream_t s);
+                        cudaStream_t s, int prec = LBF_PREC_FP64);
 int lbf_precondition_rhs(lbf_plan *pl, const double *g2_sorted, double *out, cudaStream_t s);
 int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
                    int *iters, double *rel_res, cudaStream_t s);

@@ -366,6 +366,14 @@ __global__ void k_scale(int64_t n, double alpha, double *p)
     if (i < n) p[i] *= alpha;
 }
 
+// out = alpha x + beta y (out may alias x or y)
+__global__ void k_axpby(int64_t n, double alpha, const double *x, double beta, const double *y,
+                        double *out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = alpha * x[i] + beta * y[i];
+}
+
 __global__ void k_fill(double *p, int64_t n, double v)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -429,11 +437,11 @@ static int small_gemv(lbf_plan *pl, const double *f, double alpha, double *y, co
 }
 
 int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, const int *gate,
-                        cudaStream_t s)
+                        cudaStream_t s, int prec)
 {
     int64_t N = pl->N;
     int M = pl->M;
-    int rc = lbf_apply_K(pl, in, pl->v, gate, s);
+    int rc = lbf_apply_K(pl, in, pl->v, gate, s, prec);
     if (rc) return rc;
     if (op == LBF_OP_K_ONLY) {
         LBF_LAUNCH(k_add, lbf_cdiv(N, 256), 256, 0, s, N, in, pl->v, out, gate);
@@ -475,38 +483,35 @@ static int read_state(lbf_plan *pl, GmresState *h, cudaStream_t s)
     return LBF_OK;
 }
 
-int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
-                   int *iters, double *rel_res, cudaStream_t s)
+// Restarted GMRES on P^-1 A x = b (sorted order, n unknowns) from x (x_given) or
+// from 0, with the operator in precision prec, stopping at ||b - P^-1 A x|| <=
+// tol * (*bnorm_dev).  Counts operator applications in pl->stats.
+static int gmres_core(lbf_plan *pl, const double *b, const double *bnorm_dev, double *x,
+                      bool x_given, double tol, int maxit, int prec, cudaStream_t s,
+                      GmresState *out)
 {
-    if (!pl->opt.border) return LBF_ENOTBUILT;
-    int64_t N = pl->N, n = pl->n;
+    int64_t n = pl->n;
     int m = pl->opt.restart;
     int rc;
-    double *b = pl->gb, *x = pl->gx, *w = pl->gw, *V = pl->V;
+    double *w = pl->gw, *V = pl->V;
     int64_t ldv = pl->ldv;
     int nblk = pl->mdot_blocks;
     double *hbuf = pl->H + (int64_t)(m + 1) * m;   // 2 (m + 1)
     double *cs = hbuf + 2 * (m + 1), *sn = cs + m, *gv = sn + m, *y = gv + (m + 1);
     unsigned *count = pl->red_count + 1;
-    // b = P^-1 [2 g; 0] in sorted order (tin holds the permuted data)
-    if ((rc = lbf_permute_in(pl, g, pl->tin, 0, s))) return rc;
-    // the doubled right-hand side 2 g of Eq. disc_sphere
-    LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, pl->tin);
-    LBF_CHECK_LAUNCH();
-    if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
-    LBF_LAUNCH(k_init_state, 1, 1, 0, s, pl->gs, m, pl->opt.maxit, pl->opt.tol);
-    LBF_LAUNCH(k_norm2, 1, 1024, 0, s, n, b, pl->bsig + 1);
+    int64_t *applies = prec == LBF_PREC_FP32 ? &pl->stats[2] : &pl->stats[1];
+    LBF_LAUNCH(k_init_state, 1, 1, 0, s, pl->gs, m, maxit, tol);
     LBF_CHECK_LAUNCH();
     const double *Ax = nullptr;
-    if (x0) {
-        if ((rc = lbf_permute_in(pl, x0, x, 1, s))) return rc;
-        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s))) return rc;
+    if (x_given) {
+        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s, prec))) return rc;
+        (*applies)++;
         Ax = w;
     } else {
         LBF_LAUNCH(k_fill, lbf_cdiv(n, 256), 256, 0, s, x, n, 0.0);
         LBF_CHECK_LAUNCH();
     }
-    LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1, pl->bsig + 1);
+    LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1, bnorm_dev);
     LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
     LBF_CHECK_LAUNCH();
     size_t smem = sizeof(double) * (size_t)(kRowsPerChunk + 2 * (m + 2));
@@ -532,7 +537,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
             for (int k = k0; k < k1; k++) {
                 // w = P^-1 A v_j: within a cycle the device's j equals the host's k
                 const double *vj = V + (int64_t)k * ldv;
-                if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, vj, w, &pl->gs->go, s))) return rc;
+                if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, vj, w, &pl->gs->go, s, prec))) return rc;
                 for (int mode = 0; mode < 3; mode++)
                     LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w,
                                  pl->gpart, count, hbuf, pl->H, cs, sn, gv, pl->gs, mode);
@@ -551,20 +556,91 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         if ((rc = read_state(pl, &hs, s))) return rc;
         if (hs.converged || hs.it >= hs.maxit) break;
         // restart from the true preconditioned residual
-        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s))) return rc;
-        LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0, pl->bsig + 1);
+        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s, prec))) return rc;
+        (*applies)++;
+        LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0, bnorm_dev);
         LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
         LBF_CHECK_LAUNCH();
     }
     if ((rc = read_state(pl, &hs, s))) return rc;
+    *applies += hs.it;
+    pl->stats[0] += hs.it;
+    *out = hs;
+    return LBF_OK;
+}
+
+int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
+                   int *iters, double *rel_res, cudaStream_t s)
+{
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    int64_t N = pl->N, n = pl->n;
+    int rc;
+    double *b = pl->gb, *x = pl->gx;
+    for (auto &v : pl->stats) v = 0;
+    // b = P^-1 [2 g; 0] in sorted order (tin holds the permuted data)
+    if ((rc = lbf_permute_in(pl, g, pl->tin, 0, s))) return rc;
+    // the doubled right-hand side 2 g of Eq. disc_sphere
+    LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, pl->tin);
+    LBF_CHECK_LAUNCH();
+    if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
+    double *bn = pl->bsig + 1, *rn = pl->bsig + 2;
+    LBF_LAUNCH(k_norm2, 1, 1024, 0, s, n, b, bn);
+    LBF_CHECK_LAUNCH();
+    if (x0 && (rc = lbf_permute_in(pl, x0, x, 1, s))) return rc;
+    GmresState hs{};
+    bool converged = false;
+    double rel = 0.0;
+    int its = 0;
+    if (pl->opt.precision == LBF_PRECISION_FP64 || !pl->q32) {
+        if ((rc = gmres_core(pl, b, bn, x, x0 != nullptr, pl->opt.tol, pl->opt.maxit, LBF_PREC_FP64, s,
+                             &hs)))
+            return rc;
+        converged = hs.converged;
+        its = hs.it;
+        rel = hs.bnorm > 0 ? hs.resid / hs.bnorm : 0.0;
+    } else {
+        // iterative refinement: FP64 residual, FP32-operator GMRES correction
+        double *r = pl->gr, *d = pl->gd;
+        if (!x0) {
+            LBF_LAUNCH(k_fill, lbf_cdiv(n, 256), 256, 0, s, x, n, 0.0);
+            LBF_CHECK_LAUNCH();
+        }
+        double hb[3];
+        for (int k = 0;; k++) {
+            if (k == 0 && !x0) {
+                LBF_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            } else {
+                if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, pl->gw, nullptr, s,
+                                              LBF_PREC_FP64)))
+                    return rc;
+                pl->stats[1]++;
+                LBF_LAUNCH(k_axpby, lbf_cdiv(n, 256), 256, 0, s, n, 1.0, b, -1.0, pl->gw, r);
+                LBF_CHECK_LAUNCH();
+            }
+            LBF_LAUNCH(k_norm2, 1, 1024, 0, s, n, r, rn);
+            LBF_CHECK_LAUNCH();
+            LBF_CUDA(cudaMemcpyAsync(hb, pl->bsig, sizeof(hb), cudaMemcpyDeviceToHost, s));
+            LBF_CUDA(cudaStreamSynchronize(s));
+            rel = hb[1] > 0 ? hb[2] / hb[1] : 0.0;
+            if (rel <= pl->opt.tol) { converged = true; break; }
+            if (k >= pl->opt.max_refine || its >= pl->opt.maxit) break;
+            pl->stats[3]++;
+            if ((rc = gmres_core(pl, r, rn, d, false, pl->opt.inner_tol, pl->opt.maxit - its,
+                                 LBF_PREC_FP32, s, &hs)))
+                return rc;
+            its += hs.it;
+            LBF_LAUNCH(k_axpby, lbf_cdiv(n, 256), 256, 0, s, n, 1.0, x, 1.0, d, x);
+            LBF_CHECK_LAUNCH();
+        }
+    }
     // outputs in the caller's order
     LBF_LAUNCH(k_permute_out, lbf_cdiv(N, 256), 256, 0, s, N, pl->M, pl->perm, x, sigma, 0);
     LBF_CHECK_LAUNCH();
     if (a) LBF_CUDA(cudaMemcpyAsync(a, x + N, sizeof(double) * pl->M, cudaMemcpyDeviceToDevice, s));
     LBF_CUDA(cudaStreamSynchronize(s));
-    if (iters) *iters = hs.it;
-    if (rel_res) *rel_res = hs.bnorm > 0 ? hs.resid / hs.bnorm : 0.0;
-    return hs.converged ? LBF_OK : LBF_NOCONV;
+    if (iters) *iters = its;
+    if (rel_res) *rel_res = rel;
+    return converged ? LBF_OK : LBF_NOCONV;
 }
 
 int lbf_gmres_kernels_smem(int m) { return (int)(sizeof(double) * (kRowsPerChunk + 2 * (m + 2))); }

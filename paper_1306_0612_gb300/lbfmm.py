@@ -31,12 +31,16 @@ LBF_MATVEC_DIRECT = 1
 LBF_OP_FULL = 0
 LBF_OP_K_ONLY = 1
 LBF_OP_PRECONDITIONED = 2
+LBF_OP_FP32 = 16
+LBF_PRECISION_FP64 = 0
+LBF_PRECISION_FP32_REFINE = 1
 
 
 class lbf_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("p", C.c_int),
                 ("leaf_size", C.c_int), ("max_depth", C.c_int), ("matvec", C.c_int),
-                ("border", C.c_int), ("box_capacity", C.c_int64)]
+                ("border", C.c_int), ("box_capacity", C.c_int64), ("precision", C.c_int),
+                ("p32", C.c_int), ("inner_tol", C.c_double), ("max_refine", C.c_int)]
 
 
 class LbfError(RuntimeError):
@@ -78,6 +82,7 @@ def load():
             "lbf_profile_reset": (C.c_int, []),
             "lbf_profile_read": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(C.c_double)]),
             "lbf_evaluate_noalloc": (C.c_int, [i64, _P, _P, _P, C.c_int, _P, _P, i64, _P, _P, _P]),
+            "lbf_solve_stats": (C.c_int, [_P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
             "lbf_launch_count": (i64, []),
         }
@@ -94,7 +99,8 @@ def exported_symbols():
             "lbf_plan_destroy", "lbf_plan_info", "lbf_geometry_out", "lbf_apply",
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_profile_enable", "lbf_profile_reset",
-            "lbf_profile_read", "lbf_evaluate_noalloc", "lbf_sync_status", "lbf_launch_count"]
+            "lbf_profile_read", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
+            "lbf_launch_count"]
 
 
 def lbf_status_string(status: int) -> str:
@@ -212,8 +218,15 @@ def lbf_geometry_out(plan: Plan, xi=None, normal=None, weight=None, arc_weight=N
                                    _stream(stream)), "lbf_geometry_out")
 
 
+def lbf_solve_stats(plan: Plan) -> dict:
+    st = (C.c_int64 * 4)()
+    _check(load().lbf_solve_stats(plan.handle, C.cast(st, _P)), "lbf_solve_stats")
+    return dict(arnoldi=int(st[0]), fp64_applies=int(st[1]), fp32_applies=int(st[2]),
+                refine_steps=int(st[3]))
+
+
 def lbf_apply(plan: Plan, op: int, inp: torch.Tensor, out: torch.Tensor, stream=None):
-    n = plan.N if op == LBF_OP_K_ONLY else plan.N + plan.M
+    n = plan.N if (op & ~LBF_OP_FP32) == LBF_OP_K_ONLY else plan.N + plan.M
     _check(load().lbf_apply(plan.handle, int(op), _dptr(inp, n, "in"), _dptr(out, n, "out"),
                             _stream(stream)), "lbf_apply")
 
@@ -275,7 +288,7 @@ def lbf_list_export(plan: Plan, kind: int, stream=None):
 
 LBF_KERNEL_UP, LBF_KERNEL_DOWN, LBF_KERNEL_LEAF = 0, 1, 2
 LBF_KERNEL_DIRECT, LBF_KERNEL_ARNOLDI, LBF_KERNEL_ESUM = 3, 4, 5
-KERNEL_NAMES = ["up", "down", "leaf", "direct", "arnoldi", "esum"]
+KERNEL_NAMES = ["up", "down", "leaf", "direct", "arnoldi", "esum", "up32", "down32", "leaf32"]
 
 
 def lbf_plan_counts(plan: Plan, stream=None) -> dict:

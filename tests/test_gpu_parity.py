@@ -256,3 +256,41 @@ def test_small_box_capacity_is_retried():
     p = plan_for(g, box_capacity=64, leaf_size=8)
     assert p.info()["nbox"] > 64
     _tree_case(g, 8)
+
+
+# ---- FP32 operator and iterative refinement ----------------------------------------------
+
+def test_fp32_operator_error_against_fp64_and_oracle():
+    """The float FMM operator, with its self terms and sphere correction in double,
+    stays within single-precision accuracy of the FP64 operator and the oracle."""
+    g = wl.config_geometry("C2")
+    p = plan_for(g, precision=L.LBF_PRECISION_FP32_REFINE)
+    v = np.random.default_rng(21).standard_normal(g.N)
+    o64, o32 = zeros(g.N), zeros(g.N)
+    L.lbf_apply(p, L.LBF_OP_K_ONLY, dev(v), o64)
+    L.lbf_apply(p, L.LBF_OP_K_ONLY | L.LBF_OP_FP32, dev(v), o32)
+    ref = oracle.apply(g, v, 1)
+    assert rel_l2(host(o64), ref) < MATVEC_TOL
+    e32 = rel_l2(host(o32), ref)
+    assert 1e-12 < e32 < 1e-5, e32
+
+
+def test_refinement_solve_c2_matches_oracle():
+    g = wl.config_geometry("C2")
+    src, gam, _ = wl.pair_sources(g, 0, 1)
+    _solve_check(g, src, gam, precision=L.LBF_PRECISION_FP32_REFINE)
+
+
+def test_refinement_solve_ragged_restarts_and_counts():
+    g = _ragged()
+    src, gam, _ = wl.pair_sources(g, 2, 4)
+    data = oracle.green_sum(g.x, src, gam)
+    p = plan_for(g, tol=1e-12, precision=L.LBF_PRECISION_FP32_REFINE, restart=6, leaf_size=8)
+    sig, a = zeros(g.N), zeros(g.M)
+    rc, its, rr = L.lbf_gmres_solve(p, dev(data), sig, a)
+    assert rc == L.LBF_OK and rr <= 1e-12
+    st = L.lbf_solve_stats(p)
+    assert st["refine_steps"] >= 2 and st["fp64_applies"] == st["refine_steps"]
+    assert st["fp32_applies"] >= its
+    s_ref, a_ref = oracle.solve(g, data)
+    assert rel_l2(host(sig), s_ref) < SOLVE_TOL
