@@ -53,6 +53,7 @@ typedef struct lbf_plan lbf_plan;
 #define LBF_ECUDA (-5)      /* a CUDA runtime call failed */
 #define LBF_ETIMEOUT (-6)   /* a bounded device wait gave up */
 #define LBF_ENOTBUILT (-7)  /* the plan was created without the parts this call needs */
+#define LBF_ESINGULAR (-8)  /* the Schur complement S = D - F E of the border is singular */
 
 /* matvec choice */
 #define LBF_MATVEC_FMM 0

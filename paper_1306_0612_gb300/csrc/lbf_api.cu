@@ -14,7 +14,7 @@ std::atomic<int64_t> g_lbf_launches{0};
 int lbf_gmres_kernels_smem(int m);
 int lbf_gmres_blocks();
 int lbf_fmm_init_attrs();
-int lbf_krylov_init_attrs();
+int lbf_border_init_attrs();
 
 namespace {
 
@@ -159,7 +159,34 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     pl->tin = A.get<double>(n);
     pl->tout = A.get<double>(n);
     if (o.border) {
-        pl->E = A.get<double>((int64_t)M * N);
+        Border &B = pl->bd;
+        B.P = 36;   // (sqrt2/3)^36 / 36 ~ 1e-13 worst-case truncation of P2L + L2P
+        B.P32 = 16;
+        B.pair_cap = (int64_t)M * 27 * (o.max_depth + 1);
+        B.leaf_of = A.get<int32_t>(N);
+        B.ell = A.get<double>(N);
+        B.xc = A.get<double2>(M);
+        B.kind = A.get<int32_t>(M);
+        B.cell = A.get<int32_t>(2 * (int64_t)M);
+        B.lam = A.get<double>(M);
+        B.glob = A.get<int32_t>(M);
+        B.nglob = A.get<int32_t>(1);
+        B.pairs_a = A.get<int32_t>(B.pair_cap);
+        B.pairs_b = A.get<int32_t>(B.pair_cap);
+        B.p2l_ptr = A.get<int32_t>(cap + 1);
+        B.p2l_src = A.get<int32_t>(B.pair_cap);
+        B.near_ptr = A.get<int32_t>(cap + 1);
+        B.near_src = A.get<int32_t>(B.pair_cap);
+        B.loc = A.get<double2>(cap * B.P);
+        if (o.precision == LBF_PRECISION_FP32_REFINE) B.loc32 = A.get<float2>(cap * B.P32);
+        B.zc = A.get<double2>(M);
+        B.Rk = A.get<double>(M);
+        B.rk = A.get<double>(M);
+        B.slog = A.get<double>(M);
+        B.sell = A.get<double>(M);
+        B.mu = A.get<double2>((int64_t)M * B.P);
+        B.nu = A.get<double2>((int64_t)M * B.P);
+        B.sums = A.get<double>(4);
         pl->Sinv = A.get<double>((int64_t)M * M);
     }
     int m = o.restart;
@@ -186,7 +213,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     add(sizeof(uint64_t) * N);     // keys
     add(sizeof(uint64_t) * N);     // keys_alt
     add(sizeof(int32_t) * N);      // perm_alt
-    int64_t iscr = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + N / 512 + 8192;
+    int64_t iscr = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     add(sizeof(int32_t) * iscr);   // integer scratch (scans, histograms, flags)
     add(sizeof(double) * 2 * (size_t)M * M + 64);  // Gauss-Jordan block
     size_t big = std::max(vbytes, tmp);
@@ -223,7 +250,7 @@ Temps temps(lbf_plan *pl, char *region, int64_t N, int M, int64_t cap)
     t.keys_alt = (uint64_t *)take(sizeof(uint64_t) * N);
     t.perm_alt = (int32_t *)take(sizeof(int32_t) * N);
     int64_t nunits = lbf_cdiv(N, 1024);
-    t.iscr_len = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + N / 512 + 8192;
+    t.iscr_len = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     t.iscr = (int32_t *)take(sizeof(int32_t) * t.iscr_len);
     t.gj = (double *)take(sizeof(double) * 2 * (size_t)M * M + 64);
     return t;
@@ -263,6 +290,7 @@ const char *lbf_status_string(int s)
     case LBF_ECUDA: return "CUDA runtime error";
     case LBF_ETIMEOUT: return "a bounded device wait gave up";
     case LBF_ENOTBUILT: return "the plan was created without the parts this call needs";
+    case LBF_ESINGULAR: return "the Schur complement of the border is singular";
     default: return "unknown status";
     }
 }
@@ -303,8 +331,7 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     int rc = check_islands(M, island_ptr, &N);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((rc = lbf_fmm_init_attrs()) || (rc = lbf_krylov_init_attrs())) return rc;
-    if (M > 28000) return LBF_EINVAL;  // E-sum keeps the M coefficients in shared memory
+    if ((rc = lbf_fmm_init_attrs()) || (rc = lbf_border_init_attrs())) return rc;
     lbf_plan *pl = new (std::nothrow) lbf_plan();
     if (!pl) return LBF_EINVAL;
     pl->N = N;
@@ -381,7 +408,7 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     rc = lbf_geometry_gather(pl, s, tt.xi_o, tt.w_o, tt.d_o, tt.b_o);
     if (rc) return fail(rc);
     if (opt->border) {
-        rc = lbf_border_build(pl, s, tt.x3_o, tt.gj);
+        rc = lbf_border_build(pl, s, tt.xi_o, tt.gj, tt.iscr, tt.iscr_len);
         if (rc) return fail(rc);
     }
     CK(cudaMemcpyAsync(pl->host_status, pl->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -389,8 +416,9 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
 #undef CK
     int st = *pl->host_status;
     if (st & LBF_DEV_POLE) return fail(LBF_EPOLE);
-    if (st & 4) return fail(LBF_EINVAL);   // singular Schur complement
-    if (st & 8) return fail(LBF_EDEPTH);   // list overflow
+    if (st & 4) return fail(LBF_ESINGULAR);   // singular Schur complement
+    if (st & 8) return fail(LBF_EDEPTH);      // list overflow
+    if (st & 16) return fail(LBF_EWORKSPACE); // more near centres per island than the border holds
     *plan = pl;
     return LBF_OK;
 }

@@ -1,0 +1,714 @@
+// The multiplier potential of the bordered system (Sec. 4.1, Eq. u_multi;
+// Sec. 5, Eq. matrix_eqns): (E y)_i = sum_m y_m 2 G(x_i, c_m) at every node, and
+// the Schur complement S = D - F E of the block preconditioner (Eq. matrix_eqns_c),
+// without forming the N x M block E (the paper notes E a could be evaluated by
+// the FMM, Sec. 5).
+//
+// In the stereographic plane (Sec. 3, Eq. fundC), for a centre with finite image
+// xi_m and for the centre at the pole,
+//   2 G(x, c_m)   = (1/2pi) [ l(x) - log 2 + lam_m - 2 log|xi - xi_m| ],
+//   2 G(x, pole)  = (1/2pi) [ l(x) - log 2 ],
+// with l(x) = log(1 + |xi|^2), lam_m = log(1 + |xi_m|^2).  So
+//   (E y)_i = (1/2pi) [ (l_i - log 2) Y + Lam - 2 sum_{m finite} y_m log|xi_i - xi_m| ],
+// Y = sum_m y_m, Lam = sum_{m finite} y_m lam_m.
+//
+// The log sum runs on the nodes' quadtree: every finite centre is a point source
+// that, level by level, enters the local expansion of each box that first
+// becomes well separated from the centre's cell (P2L into boxes whose parent
+// touches the cell of the parent level but which do not touch the centre's own
+// cell); local expansions are shifted down (L2L) and evaluated at the nodes
+// (L2P); a leaf that still touches the centre's cell at its own level sums that
+// centre directly.  Every (node, centre) pair is counted exactly once.
+//
+// S needs sum_j log|xi_j - xi_m| over the nodes j of island k for every (k, m);
+// it uses moments of the island's nodes about their mean z_k (radius R_k, inner
+// radius rho_k): the multipole of the island where |xi_m - z_k| >= 3 R_k, its
+// inner expansion where |xi_m - z_k| <= rho_k / 3, and a direct sum otherwise.
+#include <algorithm>
+
+#include "lbf_internal.cuh"
+
+namespace {
+
+constexpr double kEta = 3.0;
+constexpr int kMaxLevelsWalk = LBF_MAX_LEVELS + 1;
+
+template <typename R> struct __align__(2 * sizeof(R)) cz {
+    R x, y;
+};
+__device__ __forceinline__ double fmr(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmr(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <typename R> __device__ __forceinline__ cz<R> zmul(cz<R> a, cz<R> b)
+{
+    return cz<R>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R> __device__ __forceinline__ cz<R> zfma(cz<R> a, cz<R> b, cz<R> c)
+{
+    return cz<R>{fmr(a.x, b.x, fmr(-a.y, b.y, c.x)), fmr(a.x, b.y, fmr(a.y, b.x, c.y))};
+}
+__device__ __forceinline__ cz<double> zinv(cz<double> a)
+{
+    double d = 1.0 / (a.x * a.x + a.y * a.y);
+    return cz<double>{a.x * d, -a.y * d};
+}
+__device__ __forceinline__ double rlog(double v) { return log(v); }
+__device__ __forceinline__ float rlog(float v) { return __logf(v); }
+
+template <typename R> __device__ __forceinline__ R wsum(R v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct Geo {
+    double xmin, ymin, L;
+};
+__device__ __forceinline__ void centre_of(const Geo &g, int l, int ix, int iy, double &cx,
+                                          double &cy, double &r)
+{
+    double w = ldexp(g.L, -l);
+    r = 0.5 * w;
+    cx = g.xmin + (ix + 0.5) * w;
+    cy = g.ymin + (iy + 0.5) * w;
+}
+
+// ---- plan time ------------------------------------------------------------------------
+
+__global__ void k_mp_nodes(int64_t N, const double2 *__restrict__ xi, double *__restrict__ ell)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double2 z = xi[i];
+    ell[i] = log1p(z.x * z.x + z.y * z.y);
+}
+
+__global__ void k_mp_leaf_of(int64_t nleaf, const int32_t *__restrict__ leaves,
+                             const int32_t *__restrict__ bg, const int32_t *__restrict__ en,
+                             int32_t *__restrict__ leaf_of)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nleaf) return;
+    int b = leaves[t];
+    for (int i = bg[b]; i < en[b]; i++) leaf_of[i] = b;
+}
+
+// per centre: planar image, lam_m, and its cell at the finest level of the tree
+// (kind 0: at the pole; 1: inside the tree's square; 2: outside it -> summed directly)
+__global__ void k_mp_centres(int M, const double *__restrict__ c, Geo g, int D,
+                             double2 *__restrict__ xc, int32_t *__restrict__ kind,
+                             double *__restrict__ lam, int32_t *__restrict__ cell)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double w = 1.0 - c[3 * m + 2];
+    if (w < 1e-12) {
+        kind[m] = 0;
+        xc[m] = make_double2(0, 0);
+        lam[m] = 0;
+        cell[2 * m] = cell[2 * m + 1] = 0;
+        return;
+    }
+    double2 z = make_double2(c[3 * m] / w, c[3 * m + 1] / w);
+    xc[m] = z;
+    lam[m] = log1p(z.x * z.x + z.y * z.y);
+    double fx = floor((z.x - g.xmin) / g.L * ldexp(1.0, D));
+    double fy = floor((z.y - g.ymin) / g.L * ldexp(1.0, D));
+    double cmax = ldexp(1.0, D) - 1.0;
+    bool in = fx >= 0 && fy >= 0 && fx <= cmax && fy <= cmax;
+    kind[m] = in ? 1 : 2;
+    cell[2 * m] = in ? (int32_t)fx : 0;
+    cell[2 * m + 1] = in ? (int32_t)fy : 0;
+}
+
+struct TView {
+    const int32_t *level, *ix, *iy, *child0, *nchild;
+};
+
+// Walk one centre down the tree.  A holds the boxes of the current level that
+// touch the centre's cell there (at most 9; every box of level 1 touches it).
+// Children of A that do not touch the centre's cell at their level get a P2L;
+// leaves that touch it sum the centre directly.  fill == 0 counts, fill == 1
+// writes (box, centre) pairs at the centre's offsets.
+__global__ void k_mp_walk(int M, const int32_t *__restrict__ kind, const int32_t *__restrict__ cell,
+                          int D, TView T, int fill, int32_t *__restrict__ np2l,
+                          int32_t *__restrict__ nnear, const int32_t *__restrict__ op2l,
+                          const int32_t *__restrict__ onear, int32_t *__restrict__ p2l_box,
+                          int32_t *__restrict__ near_box, int *__restrict__ status)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int cp = 0, cn = 0;
+    int32_t *pb = fill ? p2l_box + op2l[m] : nullptr;
+    int32_t *nb = fill ? near_box + onear[m] : nullptr;
+    if (kind[m] == 1) {
+        int cx = cell[2 * m], cy = cell[2 * m + 1];
+        int A[9], nA = 0, An[9];
+        if (T.nchild[0] == 0) {
+            if (fill) nb[cn] = 0;
+            cn++;
+        } else {
+            for (int c = T.child0[0]; c < T.child0[0] + T.nchild[0]; c++) A[nA++] = c;
+        }
+        for (int l = 1; nA > 0 && l < kMaxLevelsWalk; l++) {
+            int nn = 0;
+            for (int q = 0; q < nA; q++) {
+                int b = A[q];
+                if (T.nchild[b] == 0) {  // a leaf touching the centre's cell: direct
+                    if (fill) nb[cn] = b;
+                    cn++;
+                    continue;
+                }
+                int lx = cx >> (D - l - 1), ly = cy >> (D - l - 1);
+                for (int c = T.child0[b]; c < T.child0[b] + T.nchild[b]; c++) {
+                    if (abs(T.ix[c] - lx) <= 1 && abs(T.iy[c] - ly) <= 1) {
+                        if (nn < 9) An[nn] = c;
+                        nn++;
+                    } else {
+                        if (fill) pb[cp] = c;
+                        cp++;
+                    }
+                }
+            }
+            if (nn > 9) atomicOr(status, 8);
+            nA = nn < 9 ? nn : 9;
+            for (int q = 0; q < nA; q++) A[q] = An[q];
+        }
+    }
+    if (!fill) {
+        np2l[m] = cp;
+        nnear[m] = cn;
+    }
+}
+
+// transpose (box, centre) pairs, generated centre by centre, into lists per box
+__global__ void k_pairs_count(int M, const int32_t *__restrict__ off, const int32_t *__restrict__ cnt,
+                              const int32_t *__restrict__ box, int32_t *__restrict__ per_box)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    for (int q = off[m]; q < off[m] + cnt[m]; q++) atomicAdd(&per_box[box[q]], 1);
+}
+
+__global__ void k_pairs_fill(int M, const int32_t *__restrict__ off, const int32_t *__restrict__ cnt,
+                             const int32_t *__restrict__ box, const int32_t *__restrict__ ptr,
+                             int32_t *__restrict__ cursor, int32_t *__restrict__ src)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    for (int q = off[m]; q < off[m] + cnt[m]; q++) {
+        int b = box[q];
+        src[ptr[b] + atomicAdd(&cursor[b], 1)] = m;
+    }
+}
+
+// each box's list in ascending centre order (deterministic sums)
+__global__ void k_sort_segments(int64_t nbox, const int32_t *__restrict__ ptr, int32_t *__restrict__ v)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    for (int i = ptr[b] + 1; i < ptr[b + 1]; i++) {
+        int x = v[i], j = i - 1;
+        while (j >= ptr[b] && v[j] > x) { v[j + 1] = v[j]; j--; }
+        v[j + 1] = x;
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = wsum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
+    __syncthreads();
+    return t;
+}
+__device__ __forceinline__ double block_max(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = sh[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); k++) t = fmax(t, sh[k]);
+    __syncthreads();
+    return t;
+}
+
+// Per island (block of 256): node mean z_k, radii R_k (max) and rho_k (min),
+// sum of log|xi_j - z_k|, sum of (l_j - log 2), and the scaled moments
+//   mu_l = sum_j ((xi_j - z_k)/R_k)^l,   nu_l = sum_j (rho_k/(xi_j - z_k))^l,  l = 1..P-1.
+__global__ void k_mp_islands(int M, int P, const int64_t *__restrict__ ptr,
+                             const double2 *__restrict__ xi_o, double2 *__restrict__ zc,
+                             double *__restrict__ Rk, double *__restrict__ rk,
+                             double *__restrict__ slog, double *__restrict__ sell,
+                             double2 *__restrict__ mu, double2 *__restrict__ nu)
+{
+    __shared__ double sh[32];
+    __shared__ double2 smu[8][LBF_MAX_TERMS], snu[8][LBF_MAX_TERMS];
+    int k = blockIdx.x;
+    int64_t b = ptr[k], e = ptr[k + 1];
+    double sx = 0, sy = 0;
+    for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) { sx += xi_o[j].x; sy += xi_o[j].y; }
+    double n = (double)(e - b);
+    double cx = block_sum(sx, sh) / n, cy = block_sum(sy, sh) / n;
+    double dmax = 0, dmin = -INFINITY, sl = 0, se = 0;
+    for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+        double dx = xi_o[j].x - cx, dy = xi_o[j].y - cy;
+        double d2 = dx * dx + dy * dy;
+        dmax = fmax(dmax, d2);
+        dmin = fmax(dmin, -d2);
+        sl += 0.5 * log(d2);
+        double2 z = xi_o[j];
+        se += log1p(z.x * z.x + z.y * z.y) - LBF_LN2;
+    }
+    double R = sqrt(block_max(dmax, sh));
+    double rho = sqrt(-block_max(dmin, sh));
+    double slv = block_sum(sl, sh), sev = block_sum(se, sh);
+    if (threadIdx.x == 0) {
+        zc[k] = make_double2(cx, cy);
+        Rk[k] = R;
+        rk[k] = rho;
+        slog[k] = slv;
+        sell[k] = sev;
+    }
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2 am0 = make_double2(0, 0), am1 = am0, an0 = am0, an1 = am0;
+    for (int64_t base = b + wid * 32; base < e; base += blockDim.x) {
+        int64_t j = base + lane;
+        cz<double> u{0, 0}, v{0, 0};
+        if (j < e) {
+            cz<double> d{xi_o[j].x - cx, xi_o[j].y - cy};
+            u = cz<double>{d.x / R, d.y / R};
+            v = zinv(cz<double>{d.x / rho, d.y / rho});
+        }
+        cz<double> pu = u, pv = v;
+        for (int l = 1; l < P; l++) {
+            double mx = wsum(pu.x), my = wsum(pu.y), nx = wsum(pv.x), ny = wsum(pv.y);
+            if (lane == (l & 31)) {
+                if (l < 32) { am0.x += mx; am0.y += my; an0.x += nx; an0.y += ny; }
+                else { am1.x += mx; am1.y += my; an1.x += nx; an1.y += ny; }
+            }
+            pu = zmul(pu, u);
+            pv = zmul(pv, v);
+        }
+    }
+    smu[wid][lane] = am0;
+    snu[wid][lane] = an0;
+    smu[wid][lane + 32] = am1;
+    snu[wid][lane + 32] = an1;
+    __syncthreads();
+    for (int l = threadIdx.x; l < P; l += blockDim.x) {
+        double2 a = make_double2(0, 0), c = a;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            a.x += smu[w][l].x; a.y += smu[w][l].y;
+            c.x += snu[w][l].x; c.y += snu[w][l].y;
+        }
+        mu[(int64_t)k * P + l] = l ? a : make_double2(n, 0);
+        nu[(int64_t)k * P + l] = l ? c : make_double2(n, 0);
+    }
+}
+
+// sum_j log|xi_j - xi_m| over the nodes j of island k
+__device__ double island_logsum(int k, int P, const int64_t *ptr, const double2 *xi_o, double2 xm,
+                                double2 z, double R, double rho, const double2 *mu,
+                                const double2 *nu, double slog)
+{
+    cz<double> d{xm.x - z.x, xm.y - z.y};
+    double dd = sqrt(d.x * d.x + d.y * d.y);
+    if (dd >= kEta * R) {
+        // N_k log|xi_m - z_k| - Re sum_l mu_l (R/(xi_m - z_k))^l / l
+        cz<double> t = zinv(cz<double>{d.x / R, d.y / R}), pw = t;
+        double s = 0.0;
+        for (int l = 1; l < P; l++) {
+            double2 c = mu[(int64_t)k * P + l];
+            s += (c.x * pw.x - c.y * pw.y) / l;
+            pw = zmul(pw, t);
+        }
+        return mu[(int64_t)k * P].x * log(dd) - s;
+    }
+    if (dd * kEta <= rho) {
+        // sum_j log|xi_j - z_k| - Re sum_l nu_l ((xi_m - z_k)/rho)^l / l
+        cz<double> t{d.x / rho, d.y / rho}, pw = t;
+        double s = 0.0;
+        for (int l = 1; l < P; l++) {
+            double2 c = nu[(int64_t)k * P + l];
+            s += (c.x * pw.x - c.y * pw.y) / l;
+            pw = zmul(pw, t);
+        }
+        return slog - s;
+    }
+    double s = 0.0;
+    for (int64_t j = ptr[k]; j < ptr[k + 1]; j++) {
+        double dx = xi_o[j].x - xm.x, dy = xi_o[j].y - xm.y;
+        s += 0.5 * log(dx * dx + dy * dy);
+    }
+    return s;
+}
+
+// S = D - F E into the left half of [S | I] (M x 2M): row r < M-1 is minus the sum
+// of E over island r+1 (Eq. disc_constr), the last row is D's row of ones (Eq. sum_ak).
+__global__ void k_mp_schur(int M, int P, const int64_t *__restrict__ ptr,
+                           const double2 *__restrict__ xi_o, const double2 *__restrict__ xc,
+                           const int32_t *__restrict__ kind, const double *__restrict__ lam,
+                           const double2 *__restrict__ zc, const double *__restrict__ Rk,
+                           const double *__restrict__ rk, const double *__restrict__ slog,
+                           const double *__restrict__ sell, const double2 *__restrict__ mu,
+                           const double2 *__restrict__ nu, double *__restrict__ G)
+{
+    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M * M) return;
+    int r = (int)(id / M), m = (int)(id % M);
+    double v;
+    if (r == M - 1) {
+        v = 1.0;
+    } else {
+        int k = r + 1;
+        double fe = sell[k];  // sum_j (l_j - log 2)
+        if (kind[m] != 0) {
+            double ls = island_logsum(k, P, ptr, xi_o, xc[m], zc[k], Rk[k], rk[k], mu, nu, slog[k]);
+            fe += (double)(ptr[k + 1] - ptr[k]) * lam[m] - 2.0 * ls;
+        }
+        v = -fe / (2.0 * LBF_PI);
+    }
+    G[(int64_t)r * 2 * M + m] = v;
+    G[(int64_t)r * 2 * M + M + m] = (r == m) ? 1.0 : 0.0;
+}
+
+// ---- per application ---------------------------------------------------------------
+
+// P2L of the log sources into every box (warp per box; lanes take centres, terms pass
+// through shared memory, lanes then take coefficients and sum in centre order):
+//   b_0 = sum y_m log|c - xi_m|,  b_l = sum y_m (-1)^(l+1) tau_m^l / l,  tau_m = r/(c - xi_m).
+// The warp of box 0 also forms Y = sum_m y_m and Lam = sum_{m finite} y_m lam_m.
+template <typename R>
+__global__ void k_mp_p2l(int64_t nbox, int P, int M, const int32_t *__restrict__ ptr,
+                         const int32_t *__restrict__ src, const int32_t *__restrict__ level,
+                         const int32_t *__restrict__ ix, const int32_t *__restrict__ iy, Geo g,
+                         const double2 *__restrict__ xc, const int32_t *__restrict__ kind,
+                         const double *__restrict__ lam, const double *__restrict__ y,
+                         cz<R> *__restrict__ loc, double *__restrict__ sums, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smr[];
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cz<R> *T = (cz<R> *)smr + (size_t)wid * P * 32;
+    int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
+    if (b >= nbox) return;
+    if (b == 0) {
+        double Y = 0.0, Lam = 0.0;
+        for (int m = lane; m < M; m += 32) {
+            Y += y[m];
+            if (kind[m]) Lam += y[m] * lam[m];
+        }
+        Y = wsum(Y);
+        Lam = wsum(Lam);
+        if (lane == 0) { sums[0] = Y; sums[1] = Lam; }
+    }
+    double cx, cy, r;
+    centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
+    double b0 = 0.0;
+    cz<R> a0{0, 0}, a1{0, 0};
+    for (int base = ptr[b]; base < ptr[b + 1]; base += 32) {
+        int q = base + lane;
+        cz<R> tau{0, 0};
+        R ym = 0;
+        if (q < ptr[b + 1]) {
+            int m = src[q];
+            double2 xm = xc[m];
+            double dx = cx - xm.x, dy = cy - xm.y;
+            b0 += y[m] * 0.5 * log(dx * dx + dy * dy);
+            cz<double> t = zinv(cz<double>{dx / r, dy / r});
+            tau = cz<R>{(R)t.x, (R)t.y};
+            ym = (R)y[m];
+        }
+        cz<R> pw{ym * tau.x, ym * tau.y};  // y tau^l, l = 1
+        for (int l = 1; l < P; l++) {
+            T[l * 32 + lane] = pw;
+            pw = zmul(pw, tau);
+        }
+        __syncwarp();
+        for (int l = lane; l < P; l += 32) {
+            if (l == 0) continue;
+            cz<R> s{0, 0};
+            for (int k = 0; k < 32; k++) { s.x += T[l * 32 + k].x; s.y += T[l * 32 + k].y; }
+            if (l < 32) { a0.x += s.x; a0.y += s.y; }
+            else { a1.x += s.x; a1.y += s.y; }
+        }
+        __syncwarp();
+    }
+    b0 = wsum(b0);
+    for (int l = lane; l < P; l += 32) {
+        cz<R> a = l < 32 ? a0 : a1;
+        R f = ((l & 1) ? (R)1 : (R)-1) / (R)l;
+        loc[b * P + l] = l == 0 ? cz<R>{(R)b0, 0} : cz<R>{a.x * f, a.y * f};
+    }
+}
+
+// L2L into the boxes of one level: b'_l += (2d)^-l sum_{k>=l} C(k,l) d^k b_k
+template <typename R>
+__global__ void k_mp_l2l(int64_t ls, int64_t le, int P, const int32_t *__restrict__ parent,
+                         const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
+                         const R *__restrict__ binom, const cz<R> *__restrict__ dtab,
+                         cz<R> *__restrict__ loc, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smr[];
+    const int nw = blockDim.x >> 5;
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tl = (P * P * (int)sizeof(R) + 15) / 16 * 16;
+    R *Cd = (R *)smr;  // Cd[k*P + l] = C(k, l) (0 for k < l)
+    cz<R> *A = (cz<R> *)(smr + tl) + (size_t)wid * P;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        int k = e / P, l = e % P;
+        Cd[e] = k >= l ? binom[k * LBF_MAX_TERMS + l] : R(0);
+    }
+    __syncthreads();
+    int64_t b = ls + blockIdx.x * (int64_t)nw + wid;
+    if (b >= le) return;
+    int p = parent[b];
+    int d = (ix[b] & 1) + 2 * (iy[b] & 1);
+    const cz<R> *dp = dtab + (size_t)d * (LBF_MAX_TERMS + 1);
+    const cz<R> *inv = dtab + (size_t)(4 + d) * (LBF_MAX_TERMS + 1);
+    for (int k = lane; k < P; k += 32) A[k] = zmul(loc[(int64_t)p * P + k], dp[k]);
+    __syncwarp();
+    const int l0 = lane, l1 = lane + 32;
+    const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
+    cz<R> s0{0, 0}, s1{0, 0};
+    for (int k = 0; k < P; k++) {
+        cz<R> a = A[k];
+        R c0 = Cd[k * P + lc0];
+        s0.x = fmr(c0, a.x, s0.x);
+        s0.y = fmr(c0, a.y, s0.y);
+        if (l1 < P) {
+            R c1 = Cd[k * P + lc1];
+            s1.x = fmr(c1, a.x, s1.x);
+            s1.y = fmr(c1, a.y, s1.y);
+        }
+    }
+    if (l0 < P) {
+        cz<R> o = loc[b * P + l0], t = zmul(inv[l0], s0);
+        loc[b * P + l0] = cz<R>{o.x + t.x, o.y + t.y};
+    }
+    if (l1 < P) {
+        cz<R> o = loc[b * P + l1], t = zmul(inv[l1], s1);
+        loc[b * P + l1] = cz<R>{o.x + t.x, o.y + t.y};
+    }
+}
+
+// out_i = x_i + v_i + s (E y)_i at every node (Morton order), v nullable: L2P of the
+// node's leaf, its direct centres, and the centres summed directly everywhere.
+template <typename R>
+__global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
+                          const int32_t *__restrict__ leaf_of, const int32_t *__restrict__ level,
+                          const int32_t *__restrict__ ix, const int32_t *__restrict__ iy, Geo g,
+                          const cz<R> *__restrict__ loc, const int32_t *__restrict__ nptr,
+                          const int32_t *__restrict__ nsrc, const int32_t *__restrict__ glob,
+                          int nglob, const double2 *__restrict__ xc, const double *__restrict__ y,
+                          const double *__restrict__ ell, const double *__restrict__ sums,
+                          const double *__restrict__ x, const double *__restrict__ v, double s,
+                          double *__restrict__ out, const int *gate,
+                          const int32_t *__restrict__ parent, int walk)
+{
+    if (gate && *gate == 0) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int b = leaf_of[i];
+    double2 zi = xi[i];
+    double cx, cy, r;
+    centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
+    cz<R> u{(R)((zi.x - cx) / r), (R)((zi.y - cy) / r)};
+    double lsum = 0.0;
+    if (!walk) {
+        const cz<R> *lb = loc + (int64_t)b * P;
+        cz<R> acc = lb[P - 1];
+        for (int l = P - 2; l >= 0; l--) acc = zfma(acc, u, lb[l]);
+        lsum = (double)acc.x;
+    } else {
+        // every ancestor's own expansion at the node (no L2L chain), offsets from the
+        // integer box coordinates: (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s
+        const int lv = level[b];
+        for (int a = b; a >= 0 && level[a] >= 2; a = parent[a]) {
+            const int sh = lv - level[a];
+            const R sc = (R)ldexp(1.0, -sh);
+            const int dxi = ix[b] - (ix[a] << sh), dyi = iy[b] - (iy[a] << sh);
+            cz<R> ua{(R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + u.x * sc,
+                     (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + u.y * sc};
+            const cz<R> *la = loc + (int64_t)a * P;
+            cz<R> t = la[P - 1];
+            for (int l = P - 2; l >= 0; l--) t = zfma(t, ua, la[l]);
+            lsum += (double)t.x;
+        }
+    }
+    for (int q = nptr[b]; q < nptr[b + 1]; q++) {
+        int m = nsrc[q];
+        double ex = zi.x - xc[m].x, ey = zi.y - xc[m].y;
+        lsum += y[m] * 0.5 * (double)rlog((R)(ex * ex + ey * ey));
+    }
+    for (int q = 0; q < nglob; q++) {
+        int m = glob[q];
+        double ex = zi.x - xc[m].x, ey = zi.y - xc[m].y;
+        lsum += y[m] * 0.5 * log(ex * ex + ey * ey);
+    }
+    double phi = ((ell[i] - LBF_LN2) * sums[0] + sums[1] - 2.0 * lsum) * (1.0 / (2.0 * LBF_PI));
+    out[i] = x[i] + (v ? v[i] : 0.0) + s * phi;
+}
+
+__global__ void k_mp_glob(int M, const int32_t *__restrict__ kind, int32_t *__restrict__ glob,
+                          int32_t *__restrict__ nglob)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int n = 0;
+    for (int m = 0; m < M; m++)
+        if (kind[m] == 2) glob[n++] = m;
+    *nglob = n;
+}
+
+__global__ void k_zero_i32(int32_t *p, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0;
+}
+
+template <typename R> size_t l2l_smem(int P, int wpb)
+{
+    return (P * P * sizeof(R) + 15) / 16 * 16 + sizeof(cz<R>) * (size_t)wpb * P;
+}
+
+}  // namespace
+
+int lbf_border_init_attrs()
+{
+    const int cap = 200 * 1024;
+    LBF_CUDA(cudaFuncSetAttribute(k_mp_p2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    LBF_CUDA(cudaFuncSetAttribute(k_mp_p2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    LBF_CUDA(cudaFuncSetAttribute(k_mp_l2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    LBF_CUDA(cudaFuncSetAttribute(k_mp_l2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    return LBF_OK;
+}
+
+static int read_i32(const int32_t *d, int32_t *h, cudaStream_t s)
+{
+    LBF_CUDA(cudaMemcpyAsync(h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LBF_CUDA(cudaStreamSynchronize(s));
+    return LBF_OK;
+}
+
+// (box, centre) pairs of one kind -> per-box lists in ascending centre order
+static int pairs_to_boxes(lbf_plan *pl, cudaStream_t s, const int32_t *off, const int32_t *cnt,
+                          const int32_t *box, int32_t *ptr, int32_t *src, int32_t *work,
+                          int64_t work_len)
+{
+    int64_t nb = pl->tree.nbox;
+    int M = pl->M;
+    LBF_LAUNCH(k_zero_i32, lbf_cdiv(2 * nb, 256), 256, 0, s, work, 2 * nb);
+    LBF_LAUNCH(k_pairs_count, lbf_cdiv(M, 128), 128, 0, s, M, off, cnt, box, work);
+    LBF_CHECK_LAUNCH();
+    int rc = lbf_scan_i32(work, ptr, nb, work + 2 * nb, work_len - 2 * nb, s);
+    if (rc) return rc;
+    int32_t a = 0, b = 0;
+    if ((rc = read_i32(ptr + nb - 1, &a, s)) || (rc = read_i32(work + nb - 1, &b, s))) return rc;
+    int32_t tot = a + b;
+    LBF_CUDA(cudaMemcpyAsync(ptr + nb, &tot, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    LBF_LAUNCH(k_pairs_fill, lbf_cdiv(M, 128), 128, 0, s, M, off, cnt, box, ptr, work + nb, src);
+    LBF_LAUNCH(k_sort_segments, lbf_cdiv(nb, 128), 128, 0, s, nb, ptr, src);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// Plan time: node and centre data, the centres' walks down the tree (P2L and
+// direct lists per box), island moments, and S into G (M x 2M, identity on the right).
+int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
+                 int64_t work_len)
+{
+    int64_t N = pl->N;
+    int M = pl->M;
+    Border &B = pl->bd;
+    Tree &T = pl->tree;
+    Geo g{T.xmin, T.ymin, T.L};
+    int D = pl->opt.max_depth;
+    LBF_LAUNCH(k_mp_nodes, lbf_cdiv(N, 256), 256, 0, s, N, pl->xi, B.ell);
+    LBF_LAUNCH(k_mp_leaf_of, lbf_cdiv(T.nleaf, 128), 128, 0, s, T.nleaf, T.leaves, T.begin, T.end,
+               B.leaf_of);
+    LBF_LAUNCH(k_mp_centres, lbf_cdiv(M, 128), 128, 0, s, M, pl->centres, g, D, B.xc, B.kind, B.lam,
+               B.cell);
+    LBF_LAUNCH(k_mp_glob, 1, 32, 0, s, M, B.kind, B.glob, B.nglob);
+    LBF_LAUNCH(k_mp_islands, M, 256, 0, s, M, B.P, pl->island_ptr, xi_o, B.zc, B.Rk, B.rk, B.slog,
+               B.sell, B.mu, B.nu);
+    LBF_CHECK_LAUNCH();
+    LBF_CUDA(cudaMemcpyAsync(&B.nglob_h, B.nglob, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    // walks: count, offsets, fill
+    TView tv{T.level, T.ix, T.iy, T.child0, T.nchild};
+    int32_t *np2l = work, *nnear = work + M, *op2l = work + 2 * M, *onear = work + 3 * M;
+    int32_t *w2 = work + 4 * M;
+    int64_t w2_len = work_len - 4 * M;
+    LBF_LAUNCH(k_mp_walk, lbf_cdiv(M, 128), 128, 0, s, M, B.kind, B.cell, D, tv, 0, np2l, nnear,
+               (const int32_t *)nullptr, (const int32_t *)nullptr, (int32_t *)nullptr,
+               (int32_t *)nullptr, pl->dev_status);
+    LBF_CHECK_LAUNCH();
+    int rc = lbf_scan_i32(np2l, op2l, M, w2, w2_len, s);
+    if (!rc) rc = lbf_scan_i32(nnear, onear, M, w2, w2_len, s);
+    if (rc) return rc;
+    int32_t a = 0, b = 0, c = 0, d = 0;
+    if ((rc = read_i32(op2l + M - 1, &a, s)) || (rc = read_i32(np2l + M - 1, &b, s)) ||
+        (rc = read_i32(onear + M - 1, &c, s)) || (rc = read_i32(nnear + M - 1, &d, s)))
+        return rc;
+    int64_t n_p2l = (int64_t)a + b, n_near = (int64_t)c + d;
+    if (n_p2l > B.pair_cap || n_near > B.pair_cap) return LBF_EWORKSPACE;
+    LBF_LAUNCH(k_mp_walk, lbf_cdiv(M, 128), 128, 0, s, M, B.kind, B.cell, D, tv, 1, np2l, nnear,
+               op2l, onear, B.pairs_a, B.pairs_b, pl->dev_status);
+    LBF_CHECK_LAUNCH();
+    if ((rc = pairs_to_boxes(pl, s, op2l, np2l, B.pairs_a, B.p2l_ptr, B.p2l_src, w2, w2_len))) return rc;
+    if ((rc = pairs_to_boxes(pl, s, onear, nnear, B.pairs_b, B.near_ptr, B.near_src, w2, w2_len)))
+        return rc;
+    B.n_p2l = n_p2l;
+    B.n_near = n_near;
+    LBF_LAUNCH(k_mp_schur, lbf_cdiv((int64_t)M * M, 128), 128, 0, s, M, B.P, pl->island_ptr, xi_o,
+               B.xc, B.kind, B.lam, B.zc, B.Rk, B.rk, B.slog, B.sell, B.mu, B.nu, G);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// out = x + v + s E y (Morton order; v nullable) in precision prec.
+int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v, double sc,
+                 double *out, const int *gate, cudaStream_t s, int prec)
+{
+    Border &B = pl->bd;
+    Tree &T = pl->tree;
+    Geo g{T.xmin, T.ymin, T.L};
+    int M = pl->M;
+    const int wpb = 4;
+    bool f32 = prec == LBF_PREC_FP32 && B.loc32;
+    if (f32) {
+        int P = B.P32;
+        size_t smem = sizeof(cz<float>) * (size_t)wpb * P * 32;
+        LBF_LAUNCH(k_mp_p2l<float>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
+                   B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
+                   (cz<float> *)B.loc32, B.sums, gate);
+        // float: no L2L chain, the evaluation walks each node's ancestors
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<float>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
+                     pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<float> *)B.loc32,
+                     B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
+                     out, gate, T.parent, 1);
+    } else {
+        int P = B.P;
+        size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
+        LBF_LAUNCH(k_mp_p2l<double>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
+                   B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
+                   (cz<double> *)B.loc, B.sums, gate);
+        for (int l = 3; l < T.nlev; l++) {
+            int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
+            if (le <= ls) continue;
+            LBF_LAUNCH(k_mp_l2l<double>, lbf_cdiv(le - ls, 8), 256, l2l_smem<double>(P, 8), s, ls,
+                       le, P, T.parent, T.ix, T.iy, pl->tab_binom,
+                       (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, gate);
+        }
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<double>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N,
+                     P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<double> *)B.loc,
+                     B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
+                     out, gate, T.parent, 0);
+    }
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}

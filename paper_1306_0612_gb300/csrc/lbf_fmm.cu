@@ -211,22 +211,34 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                      pl->upcnt, gate);
         LBF_CHECK_LAUNCH();
     }
+    // In double the downward pass runs level by level (L2L + M2L + P2L).  In float
+    // every box's M2L + P2L runs in one launch and the leaf kernel evaluates each
+    // ancestor's expansion at the targets instead of shifting them down: float
+    // arithmetic is cheap on this GPU, launches are not.
+    const int walk = dbl ? 0 : 1;
     {
         const int wpb = down_warps<R>(P);
         const size_t smem = down_smem<R>(P, wpb);
-        for (int l = 0; l < T.nlev; l++) {
-            int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
-            if (le <= ls) continue;
-            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s,
-                         ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx,
-                         T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, q, mp, loc, gate);
+        if (walk) {
+            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s,
+                         (int64_t)0, T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist,
+                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, q, mp, loc, gate, 0);
             LBF_CHECK_LAUNCH();
+        } else {
+            for (int l = 0; l < T.nlev; l++) {
+                int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
+                if (le <= ls) continue;
+                LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s,
+                             ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx,
+                             T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, q, mp, loc, gate, 1);
+                LBF_CHECK_LAUNCH();
+            }
         }
     }
     LBF_LAUNCH_P(kid_leaf, fmm::k_leaf<R>, lbf_cdiv(T.nleaf, fmm::kLeafWarps),
                  32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, q, mp, loc, sigma,
-                 pl->dself, pl->bsig, v, gate);
+                 pl->dself, pl->bsig, v, gate, T.parent, walk);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }

@@ -215,7 +215,7 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                        const R *__restrict__ binom, const cx<R> *__restrict__ tpow,
                        const cx<R> *__restrict__ dtab, const double2 *__restrict__ xi,
                        const cx<R> *__restrict__ q, const cx<R> *__restrict__ mp,
-                       cx<R> *__restrict__ loc, const int *gate)
+                       cx<R> *__restrict__ loc, const int *gate, int with_l2l)
 {
     if (gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -238,8 +238,9 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
     int bx = ix[b], by = iy[b];
     cx<R> accL0 = mk<R>(0, 0), accL1 = mk<R>(0, 0);
-    // L2L: b'_l = (2d)^-l sum_{k>=l} C(k,l) d^k b_k (the parent belongs to the previous launch)
-    if (level[b] >= 3) {
+    // L2L: b'_l = (2d)^-l sum_{k>=l} C(k,l) d^k b_k (the parent belongs to the previous launch);
+    // skipped when the leaf kernel evaluates every ancestor's expansion itself (with_l2l == 0)
+    if (with_l2l && level[b] >= 3) {
         int p = parent[b];
         int d = (bx & 1) + 2 * (by & 1);
         const cx<R> *dp = dpow(dtab, d);
@@ -347,7 +348,8 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const double2 *__restrict__ xi, const cx<R> *__restrict__ q,
                        const cx<R> *__restrict__ mp, const cx<R> *__restrict__ loc,
                        const double *__restrict__ sigma, const double *__restrict__ dself,
-                       const double *__restrict__ bsig, double *__restrict__ v, const int *gate)
+                       const double *__restrict__ bsig, double *__restrict__ v, const int *gate,
+                       const int32_t *__restrict__ parent, int walk)
 {
     if (gate_closed(gate)) return;
     __shared__ cx<R> sx[kLeafWarps][kSrcChunk];
@@ -372,8 +374,27 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             double2 zi = xi[i];
             sz[wid][lane] = mk<R>((R)(zi.x - cxd), (R)(zi.y - cyd));
             cx<R> u = mk<R>((R)((zi.x - cxd) * ir), (R)((zi.y - cyd) * ir));
-            cx<R> phi = lb[P - 1];
-            for (int l = P - 2; l >= 0; l--) phi = cfma(phi, u, lb[l]);
+            cx<R> phi = mk<R>(0, 0);
+            if (!walk) {
+                phi = lb[P - 1];
+                for (int l = P - 2; l >= 0; l--) phi = cfma(phi, u, lb[l]);
+            } else {
+                // every ancestor's own local expansion at the target (no L2L chain):
+                // (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s, s = depth gap
+                const int lv = level[b];
+                for (int a = b; a >= 0 && level[a] >= 2; a = parent[a]) {
+                    const int sh = lv - level[a];
+                    const R sc = (R)ldexp(1.0, -sh);
+                    const int dxi = ix[b] - (ix[a] << sh), dyi = iy[b] - (iy[a] << sh);
+                    cx<R> ua = mk<R>((R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + u.x * sc,
+                                     (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + u.y * sc);
+                    const cx<R> *la = loc + (int64_t)a * P;
+                    cx<R> t = la[P - 1];
+                    for (int l = P - 2; l >= 0; l--) t = cfma(t, ua, la[l]);
+                    phi.x += t.x;
+                    phi.y += t.y;
+                }
+            }
             for (int wq = wptr[b]; wq < wptr[b + 1]; wq++) {
                 int s = widx[wq];
                 double sxd, syd, sr;

@@ -1,5 +1,5 @@
-// Per-node precompute (Sec. 3 and Sec. 5) and the bordering blocks E, F, D with
-// the inverse Schur complement of the block preconditioner (Sec. 5).
+// Per-node precompute (Sec. 3 and Sec. 5) and the inverse Schur complement of
+// the block preconditioner (Sec. 5).
 #include "lbf_internal.cuh"
 
 namespace {
@@ -104,55 +104,6 @@ __global__ void k_rotate_centres(int M, const double *__restrict__ c, Rot R, dou
     out[3 * m] = v[0];
     out[3 * m + 1] = v[1];
     out[3 * m + 2] = v[2];
-}
-
-// 2 G(x, c) = (1/2pi) log(2 / |x - c|^2)  (Sec. 1.1, Eq. greens_func, doubled as in Eq. disc_sphere)
-__device__ __forceinline__ double two_green(const double *x, const double *c)
-{
-    double a = x[0] - c[0], b = x[1] - c[1], d = x[2] - c[2];
-    return (1.0 / (2.0 * LBF_PI)) * log(2.0 / (a * a + b * b + d * d));
-}
-
-// E[m*N + i] = 2 G(x_{perm[i]}, c_m): the bordering column block (Sec. 5, Eq. matrix_eqns).
-__global__ void k_build_E(int64_t N, int M, const int32_t *__restrict__ perm,
-                          const double *__restrict__ x3_o, const double *__restrict__ c,
-                          double *__restrict__ E)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int m = blockIdx.y;
-    if (i >= N) return;
-    int32_t j = perm[i];
-    double xv[3] = {x3_o[3 * j], x3_o[3 * j + 1], x3_o[3 * j + 2]};
-    E[(int64_t)m * N + i] = two_green(xv, &c[3 * m]);
-}
-
-// Schur complement S = D - F E (Sec. 5): row r < M-1 is minus the sum of E over
-// island r+1 (the unweighted constraint rows, Eq. disc_constr); the last row is
-// D's row of ones (Eq. sum_ak).  Stored in the left half of an M x 2M block
-// [S | I] for Gauss-Jordan inversion.  One warp per entry, fixed summation order.
-__global__ void k_schur(int64_t N, int M, const int64_t *__restrict__ ptr,
-                        const int32_t *__restrict__ rank, const double *__restrict__ E,
-                        double *__restrict__ G)
-{
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= (int64_t)M * M) return;
-    int r = (int)(warp / M), m = (int)(warp % M);
-    double v;
-    if (r == M - 1) {
-        v = 1.0;
-    } else {
-        // entries of E (rows in Morton order) gathered over island r+1 in the caller's order
-        const double *Em = E + (int64_t)m * N;
-        double s = 0.0;
-        for (int64_t j = ptr[r + 1] + lane; j < ptr[r + 2]; j += 32) s += Em[rank[j]];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        v = -s;
-    }
-    if (lane == 0) {
-        G[(int64_t)r * 2 * M + m] = v;
-        G[(int64_t)r * 2 * M + M + m] = (r == m) ? 1.0 : 0.0;
-    }
 }
 
 // Gauss-Jordan step k on [S | I] (M x 2M, row-major): partial pivoting on column
@@ -262,18 +213,15 @@ int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const
     return LBF_OK;
 }
 
-int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double *x3_o, double *scratch)
+// S = D - F E from the island expansions of the multiplier potential, then its
+// inverse by Gauss-Jordan elimination with partial pivoting.
+int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
+                     int32_t *work, int64_t work_len)
 {
-    int64_t N = pl->N;
     int M = pl->M;
-    dim3 grid((unsigned)lbf_cdiv(N, 256), (unsigned)M);
-    LBF_LAUNCH(k_build_E, grid, 256, 0, s, N, M, pl->perm, x3_o, pl->centres, pl->E);
-    LBF_CHECK_LAUNCH();
     double *G = scratch;  // M x 2M
-    int64_t warps = (int64_t)M * M;
-    LBF_LAUNCH(k_schur, lbf_cdiv(warps * 32, 256), 256, 0, s, N, M, pl->island_ptr, pl->rank,
-               pl->E, G);
-    LBF_CHECK_LAUNCH();
+    int rc = lbf_mp_build(pl, s, xi_o, G, work, work_len);
+    if (rc) return rc;
     for (int k = 0; k < M; k++) {
         LBF_LAUNCH(k_gj_pivot, 1, 1024, 0, s, M, k, G, pl->dev_status);
         int64_t work = (int64_t)M * (2 * M - (k + 1));

@@ -77,6 +77,32 @@ struct Tree {
     int64_t u_cap = 0, w_cap = 0, u_len = 0, w_len = 0;
 };
 
+#define LBF_LN2 0.69314718055994530942
+
+// Multiplier potential E y on the node quadtree, Schur complement from island
+// moments (lbf_border.cu).
+struct Border {
+    int P = 0, P32 = 0;              // expansion terms (double, float)
+    int64_t pair_cap = 0, n_p2l = 0, n_near = 0;
+    int32_t *leaf_of = nullptr;      // leaf box of each node (Morton order)
+    double *ell = nullptr;           // log(1 + |xi_i|^2)
+    double2 *xc = nullptr;           // planar centres
+    int32_t *kind = nullptr;         // 0 pole, 1 inside the tree's square, 2 outside
+    int32_t *cell = nullptr;         // finest-level cell of each centre (2 per centre)
+    double *lam = nullptr;           // log(1 + |xi_m|^2)
+    int32_t *glob = nullptr, *nglob = nullptr;  // centres summed directly at every node
+    int nglob_h = 0;
+    int32_t *pairs_a = nullptr, *pairs_b = nullptr;  // staging of (box, centre) pairs
+    int32_t *p2l_ptr = nullptr, *p2l_src = nullptr;  // P2L centres per box (CSR)
+    int32_t *near_ptr = nullptr, *near_src = nullptr;  // direct centres per leaf (CSR)
+    double2 *loc = nullptr;          // local expansions of the log potential, box x P
+    float2 *loc32 = nullptr;         // box x P32
+    double2 *zc = nullptr;           // island node means
+    double *Rk = nullptr, *rk = nullptr, *slog = nullptr, *sell = nullptr;
+    double2 *mu = nullptr, *nu = nullptr;  // island moments, M x P
+    double *sums = nullptr;          // Y, Lam
+};
+
 struct GmresState;  // device-side scalars (lbf_krylov.cu)
 
 struct lbf_plan {
@@ -118,7 +144,7 @@ struct lbf_plan {
     double *red = nullptr;      // reduction partials
     unsigned int *red_count = nullptr;
     // border
-    double *E = nullptr;        // M x N, E[m*N + i] = 2 G(x_i, c_m), rows in sorted order
+    Border bd;                  // E y by island expansions (E itself is never formed)
     double *Sinv = nullptr;     // M x M inverse Schur complement
     double *fvec = nullptr, *yvec = nullptr;  // M-vectors
     // generic N+M vectors for lbf_apply / gmres
@@ -145,7 +171,13 @@ int lbf_geometry_build(lbf_plan *pl, const double *x, const double *dx, const do
                        double2 *w_o, double *d_o, double *b_o);
 int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const double2 *w_o,
                         const double *d_o, const double *b_o);
-int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double *x3_o, double *scratch);
+int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
+                     int32_t *work, int64_t work_len);
+// ---- multiplier potential (lbf_border.cu) -------------------------------------
+int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
+                 int64_t work_len);
+int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v, double sc,
+                 double *out, const int *gate, cudaStream_t s, int prec);
 int lbf_geometry_out_impl(const lbf_plan *pl, double *xi, double *normal, double *weight,
                           double *arc, cudaStream_t s);
 

@@ -81,22 +81,6 @@ __global__ void k_small_gemv(int M, const double *__restrict__ A, const double *
     if (lane == 0) y[r] = alpha * s;
 }
 
-// out_i = x_i + v_i + s * sum_m E[m][i] c_m   (v nullable)
-__global__ void k_esum(int64_t N, int M, const double *__restrict__ E, const double *__restrict__ x,
-                       const double *__restrict__ v, const double *__restrict__ c, double s,
-                       double *__restrict__ out, const int *gate)
-{
-    if (gate_closed(gate)) return;
-    extern __shared__ double sc[];
-    for (int m = threadIdx.x; m < M; m += blockDim.x) sc[m] = c[m];
-    __syncthreads();
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double acc = 0.0;
-    for (int m = 0; m < M; m++) acc = fma(E[(int64_t)m * N + i], sc[m], acc);
-    out[i] = x[i] + (v ? v[i] : 0.0) + s * acc;
-}
-
 __global__ void k_add(int64_t n, const double *__restrict__ x, const double *__restrict__ v,
                       double *__restrict__ out, const int *gate)
 {
@@ -402,20 +386,11 @@ int lbf_permute_out(lbf_plan *pl, const double *in_sorted, double *out_caller, i
     return LBF_OK;
 }
 
-int lbf_krylov_init_attrs()
-{
-    LBF_CUDA(cudaFuncSetAttribute(k_esum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    return LBF_OK;
-}
-
+// out = x + v + sc E c (the multiplier potential of the centres' strengths c)
 static int esum(lbf_plan *pl, const double *x, const double *v, const double *c, double sc,
-                double *out, const int *gate, cudaStream_t s)
+                double *out, const int *gate, cudaStream_t s, int prec = LBF_PREC_FP64)
 {
-    size_t smem = sizeof(double) * (size_t)pl->M;
-    LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_esum, lbf_cdiv(pl->N, 256), 256, smem, s, pl->N, pl->M, pl->E, x, v, c, sc, out,
-               gate);
-    LBF_CHECK_LAUNCH();
-    return LBF_OK;
+    return lbf_mp_apply(pl, c, x, v, sc, out, gate, s, prec);
 }
 
 static int island_sums(lbf_plan *pl, const double *u, double scale, double *out, const int *gate,
@@ -459,7 +434,7 @@ int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, con
     // preconditioned: y = S^-1 F v; out = [sigma + v + E y ; a - y]
     if ((rc = island_sums(pl, pl->v, 1.0, pl->fvec, gate, s))) return rc;
     if ((rc = small_gemv(pl, pl->fvec, 1.0, pl->yvec, gate, s))) return rc;
-    if ((rc = esum(pl, in, pl->v, pl->yvec, 1.0, out, gate, s))) return rc;
+    if ((rc = esum(pl, in, pl->v, pl->yvec, 1.0, out, gate, s, prec))) return rc;
     LBF_LAUNCH(k_arows, 1, 256, 0, s, M, 1, in + N, pl->yvec, out + N, gate);
     LBF_CHECK_LAUNCH();
     return LBF_OK;

@@ -25,6 +25,7 @@ LBF_EWORKSPACE = -4
 LBF_ECUDA = -5
 LBF_ETIMEOUT = -6
 LBF_ENOTBUILT = -7
+LBF_ESINGULAR = -8
 
 LBF_MATVEC_FMM = 0
 LBF_MATVEC_DIRECT = 1
