@@ -201,20 +201,36 @@ int lbf_list_export(const lbf_plan *plan, int kind, int32_t *ptr, int32_t *idx, 
  * [5] (target node, W box) pairs, [6] (source node, X box) pairs, [7] leaves. */
 int lbf_plan_counts(const lbf_plan *plan, int64_t counts[8], lbf_stream_t stream);
 
+/* Work counts of the multiplier potential E y (Sec. 4.1, Eq. u_multi; the FMM
+ * evaluation of E a suggested in Sec. 5), host out, synchronous:
+ * counts[0] (box, centre) P2L pairs, [1] (node, centre) pairs summed directly
+ * (adjacent leaves), [2] centres summed directly at every node (outside the
+ * tree's square), [3] sum over nodes of the local expansions evaluated by the
+ * float operator (tree levels >= 2 on the path from the node's leaf to the
+ * root), [4] terms of its double local expansions, [5] terms of its float
+ * local expansions.  LBF_ENOTBUILT without the border. */
+int lbf_border_counts(const lbf_plan *plan, int64_t counts[6], lbf_stream_t stream);
+
 /* Tracing: while enabled, every launch of the kernels below is bracketed by a
  * pair of CUDA events recorded on the stream it is launched on.  Host calls;
  * lbf_profile_read synchronizes on the recorded events and returns, per kernel,
  * the launches and their summed device time. */
 #define LBF_KERNEL_UP 0     /* upward pass: P2M + M2M, one launch */
 #define LBF_KERNEL_DOWN 1   /* downward pass: L2L + M2L + P2L, one launch per level */
+                            /* (the float pass: M2L + P2L, one launch, no L2L) */
 #define LBF_KERNEL_LEAF 2   /* L2P + M2P + P2P + combine */
 #define LBF_KERNEL_DIRECT 3
 #define LBF_KERNEL_ARNOLDI 4
-#define LBF_KERNEL_ESUM 5   /* E-block pass of the bordered operator */
+#define LBF_KERNEL_ESUM 5   /* multiplier potential E y at the nodes: L2P + direct centres */
 #define LBF_KERNEL_UP32 6   /* the three FMM passes of the float operator */
 #define LBF_KERNEL_DOWN32 7
 #define LBF_KERNEL_LEAF32 8
-#define LBF_KERNEL_COUNT 9
+#define LBF_KERNEL_ESUM32 9 /* the multiplier potential of the float operator */
+/* stages of lbf_plan_create (every launch of the stage between one event pair) */
+#define LBF_STAGE_GEOMETRY 10 /* projection, quadtree, interaction lists, gather */
+#define LBF_STAGE_BORDER 11   /* multiplier-potential lists and the Schur complement */
+#define LBF_STAGE_INVERSE 12  /* Gauss-Jordan inverse of the Schur complement */
+#define LBF_KERNEL_COUNT 13
 int lbf_profile_enable(int on);
 int lbf_profile_reset(void);
 int lbf_profile_read(int kernel, int64_t *launches /* host out */, double *total_ms /* host out */);

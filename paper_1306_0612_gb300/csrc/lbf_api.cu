@@ -137,6 +137,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         int P32 = o.p32 + 1;
         pl->P32 = P32;
         pl->q32 = A.get<float2>(N);
+        pl->u32 = A.get<float2>(N);
         if (o.matvec == LBF_MATVEC_FMM) {
             pl->mpole32 = A.get<float2>(cap * P32);
             pl->local32 = A.get<float2>(cap * P32);
@@ -395,6 +396,7 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     CK(cudaMemsetAsync(pl->bsig, 0, 4 * sizeof(double), s));
     // plan-creation temporaries overlay the region of the GMRES basis
     Temps tt = temps(pl, pl->region, N, M, cap);
+    lbf_prof_mark(LBF_STAGE_GEOMETRY, 1, s);
     rc = lbf_geometry_build(pl, x, dx, d2x, centres, s, tt.xi_o, tt.x3_o, tt.w_o, tt.d_o, tt.b_o);
     if (rc) return fail(rc);
     {
@@ -407,6 +409,8 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     }
     rc = lbf_geometry_gather(pl, s, tt.xi_o, tt.w_o, tt.d_o, tt.b_o);
     if (rc) return fail(rc);
+    if ((rc = lbf_fmm_prepare(pl, s))) return fail(rc);
+    lbf_prof_mark(LBF_STAGE_GEOMETRY, 0, s);
     if (opt->border) {
         rc = lbf_border_build(pl, s, tt.xi_o, tt.gj, tt.iscr, tt.iscr_len);
         if (rc) return fail(rc);

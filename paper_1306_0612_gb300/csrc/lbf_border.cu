@@ -509,37 +509,41 @@ __global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
                           const double *__restrict__ ell, const double *__restrict__ sums,
                           const double *__restrict__ x, const double *__restrict__ v, double s,
                           double *__restrict__ out, const int *gate,
-                          const int32_t *__restrict__ parent, int walk)
+                          const int32_t *__restrict__ parent, const float2 *__restrict__ u32,
+                          int walk)
 {
     if (gate && *gate == 0) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     int b = leaf_of[i];
     double2 zi = xi[i];
-    double cx, cy, r;
-    centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
-    cz<R> u{(R)((zi.x - cx) / r), (R)((zi.y - cy) / r)};
     double lsum = 0.0;
     if (!walk) {
+        double cx, cy, r;
+        centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
+        cz<R> u{(R)((zi.x - cx) / r), (R)((zi.y - cy) / r)};
         const cz<R> *lb = loc + (int64_t)b * P;
         cz<R> acc = lb[P - 1];
         for (int l = P - 2; l >= 0; l--) acc = zfma(acc, u, lb[l]);
         lsum = (double)acc.x;
     } else {
-        // every ancestor's own expansion at the node (no L2L chain), offsets from the
-        // integer box coordinates: (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s
+        // float: every ancestor's own expansion at the node (no L2L chain), from the
+        // node's leaf-local coordinate u: (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s
+        const float2 uu = u32[i];
         const int lv = level[b];
+        R acc = 0;
         for (int a = b; a >= 0 && level[a] >= 2; a = parent[a]) {
             const int sh = lv - level[a];
-            const R sc = (R)ldexp(1.0, -sh);
+            const R sc = (R)__int_as_float((127 - sh) << 23);  // 2^-sh
             const int dxi = ix[b] - (ix[a] << sh), dyi = iy[b] - (iy[a] << sh);
-            cz<R> ua{(R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + u.x * sc,
-                     (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + u.y * sc};
+            cz<R> ua{(R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + (R)uu.x * sc,
+                     (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + (R)uu.y * sc};
             const cz<R> *la = loc + (int64_t)a * P;
             cz<R> t = la[P - 1];
             for (int l = P - 2; l >= 0; l--) t = zfma(t, ua, la[l]);
-            lsum += (double)t.x;
+            acc += t.x;
         }
+        lsum = (double)acc;
     }
     for (int q = nptr[b]; q < nptr[b + 1]; q++) {
         int m = nsrc[q];
@@ -687,10 +691,10 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
                    (cz<float> *)B.loc32, B.sums, gate);
         // float: no L2L chain, the evaluation walks each node's ancestors
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<float>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_eval<float>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
                      pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<float> *)B.loc32,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, T.parent, 1);
+                     out, gate, T.parent, pl->u32, 1);
     } else {
         int P = B.P;
         size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
@@ -707,8 +711,48 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
         LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<double>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N,
                      P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<double> *)B.loc,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, T.parent, 0);
+                     out, gate, T.parent, (const float2 *)nullptr, 0);
     }
     LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+namespace {
+__global__ void k_mp_counts(int64_t nleaf, const int32_t *__restrict__ leaves,
+                            const int32_t *__restrict__ level, const int32_t *__restrict__ bg,
+                            const int32_t *__restrict__ en, const int32_t *__restrict__ nptr,
+                            unsigned long long *__restrict__ c)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nleaf) return;
+    int b = leaves[t];
+    unsigned long long nb = (unsigned long long)(en[b] - bg[b]);
+    atomicAdd(&c[0], nb * (unsigned long long)(nptr[b + 1] - nptr[b]));
+    if (level[b] >= 2) atomicAdd(&c[1], nb * (unsigned long long)(level[b] - 1));
+}
+}  // namespace
+
+extern "C" int lbf_border_counts(const lbf_plan *pl, int64_t counts[6], lbf_stream_t stream)
+{
+    if (!pl || !counts) return LBF_EINVAL;
+    for (int k = 0; k < 6; k++) counts[k] = 0;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Tree &T = pl->tree;
+    const Border &B = pl->bd;
+    unsigned long long *c = (unsigned long long *)pl->red;  // counters in the reduction scratch
+    LBF_CUDA(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), s));
+    LBF_LAUNCH(k_mp_counts, lbf_cdiv(T.nleaf, 256), 256, 0, s, T.nleaf, T.leaves, T.level, T.begin,
+               T.end, B.near_ptr, c);
+    LBF_CHECK_LAUNCH();
+    unsigned long long h[2];
+    LBF_CUDA(cudaMemcpyAsync(h, c, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LBF_CUDA(cudaStreamSynchronize(s));
+    counts[0] = B.n_p2l;
+    counts[1] = (int64_t)h[0];
+    counts[2] = B.nglob_h;
+    counts[3] = (int64_t)h[1];
+    counts[4] = B.P;
+    counts[5] = B.P32;
     return LBF_OK;
 }

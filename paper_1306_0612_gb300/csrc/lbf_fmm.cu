@@ -163,6 +163,27 @@ __global__ void k_green_sum(int64_t T, const double *__restrict__ t, int64_t S,
     out[q] = s;
 }
 
+// per node: (xi - c)/r about its leaf's centre c and half-width r, rounded to
+// float once per geometry (warp per leaf)
+__global__ void k_local_coords(int64_t nleaf, const int32_t *__restrict__ leaves,
+                               const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
+                               const int32_t *__restrict__ iy, const int32_t *__restrict__ bg,
+                               const int32_t *__restrict__ en, fmm::BoxGeo g,
+                               const double2 *__restrict__ xi, float2 *__restrict__ u32)
+{
+    int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (t >= nleaf) return;
+    int b = leaves[t];
+    double cx_, cy_, r;
+    fmm::box_centre(g, level[b], ix[b], iy[b], cx_, cy_, r);
+    double ir = 1.0 / r;
+    for (int i = bg[b] + lane; i < en[b]; i += 32) {
+        double2 z = xi[i];
+        u32[i] = make_float2((float)((z.x - cx_) * ir), (float)((z.y - cy_) * ir));
+    }
+}
+
 // shared-memory bytes of the two FMM pass kernels
 template <typename R> size_t up_smem(int P, int wpb)
 {
@@ -170,7 +191,7 @@ template <typename R> size_t up_smem(int P, int wpb)
 }
 template <typename R> size_t down_smem(int P, int wpb)
 {
-    return (2 * P * P * sizeof(R) + 15) / 16 * 16 + sizeof(cx<R>) * (size_t)wpb * P * 33;
+    return (2 * P * P * sizeof(R) + 15) / 16 * 16 + sizeof(cx<R>) * (size_t)wpb * P * 34;
 }
 constexpr size_t kSmemCap = 200 * 1024;
 
@@ -207,8 +228,8 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
         const int wpb = 2;
         LBF_LAUNCH_P(kid_up, fmm::k_up<R>, lbf_cdiv(T.nleaf, wpb), 32 * wpb,
                      up_smem<R>(P, wpb), s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
-                     T.end, T.parent, T.child0, T.nchild, g, P, binom, dsh, pl->xi, q, mp,
-                     pl->upcnt, gate);
+                     T.end, T.parent, T.child0, T.nchild, g, P, binom, dsh, pl->xi, pl->u32, q,
+                     mp, pl->upcnt, gate);
         LBF_CHECK_LAUNCH();
     }
     // In double the downward pass runs level by level (L2L + M2L + P2L).  In float
@@ -222,7 +243,8 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
         if (walk) {
             LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s,
                          (int64_t)0, T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist,
-                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, q, mp, loc, gate, 0);
+                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, pl->u32, q, mp, loc,
+                         gate, 0);
             LBF_CHECK_LAUNCH();
         } else {
             for (int l = 0; l < T.nlev; l++) {
@@ -230,15 +252,16 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                 if (le <= ls) continue;
                 LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s,
                              ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx,
-                             T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, q, mp, loc, gate, 1);
+                             T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, pl->u32, q, mp, loc,
+                             gate, 1);
                 LBF_CHECK_LAUNCH();
             }
         }
     }
     LBF_LAUNCH_P(kid_leaf, fmm::k_leaf<R>, lbf_cdiv(T.nleaf, fmm::kLeafWarps),
                  32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
-                 T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, q, mp, loc, sigma,
-                 pl->dself, pl->bsig, v, gate, T.parent, walk);
+                 T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, pl->u32, q, mp, loc,
+                 sigma, pl->dself, pl->bsig, v, gate, T.parent, walk);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -286,6 +309,17 @@ int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, c
     }
     FmmArrays a{pl->P, pl->q, pl->mpole, pl->local, pl->tab_binom, pl->tab_tpow, pl->tab_dshift};
     return fmm_apply<double>(pl, a, sigma, v, gate, s);
+}
+
+int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
+{
+    if (!pl->u32) return LBF_OK;
+    Tree &T = pl->tree;
+    fmm::BoxGeo g{T.xmin, T.ymin, T.L};
+    LBF_LAUNCH(k_local_coords, lbf_cdiv(T.nleaf, 8), 256, 0, s, T.nleaf, T.leaves, T.level, T.ix,
+               T.iy, T.begin, T.end, g, pl->xi, pl->u32);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
 }
 
 int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,

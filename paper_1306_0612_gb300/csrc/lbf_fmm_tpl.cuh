@@ -1,7 +1,10 @@
 // FMM kernels templated on the real type R (double: the accurate operator;
-// float: the inner operator of iterative refinement).  Box geometry, node
-// offsets from box centres and the final combine are formed in double; the
-// expansions, translations and near-field pair sums run in R.
+// float: the inner operator of iterative refinement).  The expansions,
+// translations and near-field pair sums run in R; the final combine in double.
+// The float path reads each node's coordinate relative to its own leaf (formed
+// in double once per geometry) and moves it between box frames by powers of two
+// and exact integer centre offsets, so its inner loops issue no double
+// arithmetic (this GPU runs double at 1/64 of the float rate).
 //
 // Scaled expansions about a box centre c with half-width r:
 //   multipole  phi(z) = sum_k a_k r^k / (z - c)^(k+1),  a_k = sum_j q_j ((xi_j - c)/r)^k
@@ -73,6 +76,37 @@ __device__ __forceinline__ void box_centre(const BoxGeo &g, int l, int ix, int i
     cy_ = g.ymin + (iy + 0.5) * w;
 }
 
+// 2^e from the exponent bits (|e| well inside the normal range)
+template <typename R> __device__ __forceinline__ R pow2(int e);
+template <> __device__ __forceinline__ float pow2<float>(int e) { return __int_as_float((127 + e) << 23); }
+template <> __device__ __forceinline__ double pow2<double>(int e)
+{
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// (c_a - c_b) / r_b for box a (level la) and box b (level lb), per axis
+// (2 a + 1) 2^(lb - la) - (2 b + 1), formed in integers at the finer level and
+// scaled once, so the float path needs no double arithmetic for box offsets
+__device__ __forceinline__ float2 centre_offset(int la, int ax, int ay, int lb, int bx, int by)
+{
+    if (la >= lb) {
+        const int sh = la - lb;
+        const long long dx = (2LL * ax + 1) - ((2LL * bx + 1) << sh);
+        const long long dy = (2LL * ay + 1) - ((2LL * by + 1) << sh);
+        const float f = pow2<float>(-sh);
+        return make_float2((float)(int)dx * f, (float)(int)dy * f);
+    }
+    const int sh = lb - la;
+    const long long dx = ((2LL * ax + 1) << sh) - (2LL * bx + 1);
+    const long long dy = ((2LL * ay + 1) << sh) - (2LL * by + 1);
+    return make_float2((float)(int)dx, (float)(int)dy);
+}
+
+// Largest level gap over which the float path rescales a node's leaf-local
+// coordinate into another box's frame (the rounding of the leaf-local value grows
+// by 2 per level); wider gaps form the offset from the double node position.
+constexpr int kMaxGapF32 = 3;
+
 // shift tables for the four child positions: d^k and (2d)^-k, k <= LBF_MAX_TERMS
 template <typename R> __device__ __forceinline__ const cx<R> *dpow(const cx<R> *dtab, int c)
 {
@@ -92,8 +126,8 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
                      const int32_t *__restrict__ en, const int32_t *__restrict__ parent,
                      const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
                      BoxGeo g, int P, const R *__restrict__ binom, const cx<R> *__restrict__ dtab,
-                     const double2 *__restrict__ xi, const cx<R> *__restrict__ q, cx<R> *mp,
-                     int *cnt, const int *gate)
+                     const double2 *__restrict__ xi, const float2 *__restrict__ u32,
+                     const cx<R> *__restrict__ q, cx<R> *mp, int *cnt, const int *gate)
 {
     if (gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -120,8 +154,13 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
             int j = base + lane;
             cx<R> z = mk<R>(0, 0), term = mk<R>(0, 0);
             if (j < en[b]) {
-                double2 x = xi[j];
-                z = mk<R>((R)((x.x - cxd) * ir), (R)((x.y - cyd) * ir));
+                if constexpr (sizeof(R) == 4) {
+                    float2 uu = u32[j];
+                    z = mk<R>(uu.x, uu.y);
+                } else {
+                    double2 x = xi[j];
+                    z = mk<R>((R)((x.x - cxd) * ir), (R)((x.y - cyd) * ir));
+                }
                 term = q[j];
             }
             for (int k = 0; k < P; k++) {
@@ -214,8 +253,9 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                        const int32_t *__restrict__ en, BoxGeo g, int P,
                        const R *__restrict__ binom, const cx<R> *__restrict__ tpow,
                        const cx<R> *__restrict__ dtab, const double2 *__restrict__ xi,
-                       const cx<R> *__restrict__ q, const cx<R> *__restrict__ mp,
-                       cx<R> *__restrict__ loc, const int *gate, int with_l2l)
+                       const float2 *__restrict__ u32, const cx<R> *__restrict__ q,
+                       const cx<R> *__restrict__ mp, cx<R> *__restrict__ loc, const int *gate,
+                       int with_l2l)
 {
     if (gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -224,8 +264,8 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     const int tl = (2 * P * P * (int)sizeof(R) + 15) / 16 * 16;
     R *Cm = (R *)sm_raw;          // Cm[k*P + l] = C(k+l, l)
     R *Cd = Cm + P * P;           // Cd[k*P + l] = C(k, l) (0 for k < l)
-    cx<R> *A = (cx<R> *)(sm_raw + tl) + (size_t)wid * P;
-    cx<R> *T = (cx<R> *)(sm_raw + tl) + (size_t)nw * P + (size_t)wid * P * 32;
+    cx<R> *A = (cx<R> *)(sm_raw + tl) + (size_t)wid * 2 * P;
+    cx<R> *T = (cx<R> *)(sm_raw + tl) + (size_t)nw * 2 * P + (size_t)wid * P * 32;
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
         int k = e / P, l = e % P;
         Cm[e] = binom[(k + l) * LBF_MAX_TERMS + l];
@@ -265,46 +305,100 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     }
     // M2L: (-1)^l t^(l+1) sum_k C(k+l, l) t^k a_k,  t = 1/(2 (dx + i dy))  (times 1/r below)
     cx<R> accF0 = mk<R>(0, 0), accF1 = mk<R>(0, 0);
-    for (int vq = 0; vq < nv[b]; vq++) {
-        int s = vlist[b * 27 + vq];
-        int o = (bx - ix[s] + 3) * 7 + (by - iy[s] + 3);
-        const cx<R> *tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
-        for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
-        __syncwarp();
-        cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
-        for (int k = 0; k < P; k++) {
-            cx<R> a = A[k];
-            R c0 = Cm[k * P + lc0];
-            s0.x = fm(c0, a.x, s0.x);
-            s0.y = fm(c0, a.y, s0.y);
-            if (l1 < P) {
-                R c1 = Cm[k * P + lc1];
-                s1.x = fm(c1, a.x, s1.x);
-                s1.y = fm(c1, a.y, s1.y);
+    if (P <= 16) {
+        // two half-warps take two V-list boxes at a time; lane gl of a half-warp owns
+        // coefficient gl, and the halves are summed at the end
+        const int grp = lane >> 4, gl = lane & 15;
+        const int glc = gl < P ? gl : 0;
+        cx<R> *Ag = A + grp * P;
+        for (int v0 = 0; v0 < nv[b]; v0 += 2) {
+            const int vq = v0 + grp;
+            const bool on = vq < nv[b];
+            const cx<R> *tp = tpow;
+            if (on) {
+                int s = vlist[b * 27 + vq];
+                int o = (bx - ix[s] + 3) * 7 + (by - iy[s] + 3);
+                tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
+                if (gl < P) Ag[gl] = cmul(mp[(int64_t)s * P + gl], tp[gl]);
             }
+            __syncwarp();
+            if (on && gl < P) {
+                cx<R> s0 = mk<R>(0, 0);
+                for (int k = 0; k < P; k++) {
+                    cx<R> a = Ag[k];
+                    R c0 = Cm[k * P + glc];
+                    s0.x = fm(c0, a.x, s0.x);
+                    s0.y = fm(c0, a.y, s0.y);
+                }
+                cx<R> f0 = tp[gl + 1];
+                if (gl & 1) { f0.x = -f0.x; f0.y = -f0.y; }
+                accF0 = cfma(f0, s0, accF0);
+            }
+            __syncwarp();
         }
-        cx<R> f0 = tp[l0 + 1];
-        if (l0 & 1) { f0.x = -f0.x; f0.y = -f0.y; }
-        accF0 = cfma(f0, s0, accF0);
-        if (l1 < P) {
-            cx<R> f1 = tp[l1 + 1];
-            if (l1 & 1) { f1.x = -f1.x; f1.y = -f1.y; }
-            accF1 = cfma(f1, s1, accF1);
+        accF0.x += __shfl_down_sync(0xffffffffu, accF0.x, 16);
+        accF0.y += __shfl_down_sync(0xffffffffu, accF0.y, 16);
+        if (lane >= 16) accF0 = mk<R>(0, 0);
+    } else {
+        for (int vq = 0; vq < nv[b]; vq++) {
+            int s = vlist[b * 27 + vq];
+            int o = (bx - ix[s] + 3) * 7 + (by - iy[s] + 3);
+            const cx<R> *tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
+            for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
+            __syncwarp();
+            cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+            for (int k = 0; k < P; k++) {
+                cx<R> a = A[k];
+                R c0 = Cm[k * P + lc0];
+                s0.x = fm(c0, a.x, s0.x);
+                s0.y = fm(c0, a.y, s0.y);
+                if (l1 < P) {
+                    R c1 = Cm[k * P + lc1];
+                    s1.x = fm(c1, a.x, s1.x);
+                    s1.y = fm(c1, a.y, s1.y);
+                }
+            }
+            cx<R> f0 = tp[l0 + 1];
+            if (l0 & 1) { f0.x = -f0.x; f0.y = -f0.y; }
+            accF0 = cfma(f0, s0, accF0);
+            if (l1 < P) {
+                cx<R> f1 = tp[l1 + 1];
+                if (l1 & 1) { f1.x = -f1.x; f1.y = -f1.y; }
+                accF1 = cfma(f1, s1, accF1);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     // P2L: (-1)^l sum_j q_j tau_j^(l+1), tau_j = r / (c - xi_j)  (times 1/r below)
+    const int lb = level[b];
     double cxd, cyd, r;
-    box_centre(g, level[b], bx, by, cxd, cyd, r);
+    box_centre(g, lb, bx, by, cxd, cyd, r);
     double ir = 1.0 / r;
     for (int xq = 0; xq < nx[b]; xq++) {
         int s = xlist[b * 16 + xq];
+        // float: the source's leaf-local coordinate rescaled into this box's frame
+        bool local = false;
+        float fs = 0.f;
+        float2 os = make_float2(0.f, 0.f);
+        if constexpr (sizeof(R) == 4) {
+            const int ls = level[s];
+            local = lb >= ls && lb - ls <= kMaxGapF32;
+            if (local) {
+                fs = pow2<float>(lb - ls);
+                os = centre_offset(ls, ix[s], iy[s], lb, bx, by);
+            }
+        }
         for (int base = bg[s]; base < en[s]; base += 32) {
             int j = base + lane;
             cx<R> tau = mk<R>(0, 0), term = mk<R>(0, 0);
             if (j < en[s]) {
-                double2 z = xi[j];
-                tau = crcp(mk<R>((R)((cxd - z.x) * ir), (R)((cyd - z.y) * ir)));
+                if (local) {
+                    float2 uu = u32[j];
+                    tau = crcp(mk<R>(-fmaf(uu.x, fs, os.x), -fmaf(uu.y, fs, os.y)));
+                } else {
+                    double2 z = xi[j];
+                    tau = crcp(mk<R>((R)((cxd - z.x) * ir), (R)((cyd - z.y) * ir)));
+                }
                 term = cmul(q[j], tau);  // l = 0
             }
             for (int l = 0; l < P; l++) {
@@ -334,10 +428,13 @@ constexpr int kLeafWarps = 4;
 constexpr int kSrcChunk = 256;
 
 // Per leaf: far field (L2P of the leaf's local expansion and M2P from W(b)),
-// near field (P2P over U(b), self excluded) in coordinates relative to the leaf
-// centre (formed in double, so the cancellation of close nodes happens before
-// any rounding to R), and the combine into v in double:
+// near field (P2P over U(b), self excluded) and the combine into v in double:
 //   v_i = 2 [ (1/2pi) c_i + dself_i sigma_i + beta.sigma ].
+// Near-field positions are taken relative to the leaf centre in units of its
+// half-width r, so close nodes cancel before any rounding to R: in double from
+// the node positions, in float from each node's own leaf-local coordinate
+// rescaled by a power of two and shifted by the exact offset between box
+// centres (double positions only where a source box is much coarser).
 template <typename R>
 __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
@@ -345,13 +442,15 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const int32_t *__restrict__ en, const int32_t *__restrict__ uptr,
                        const int32_t *__restrict__ uidx, const int32_t *__restrict__ wptr,
                        const int32_t *__restrict__ widx, BoxGeo g, int P,
-                       const double2 *__restrict__ xi, const cx<R> *__restrict__ q,
-                       const cx<R> *__restrict__ mp, const cx<R> *__restrict__ loc,
-                       const double *__restrict__ sigma, const double *__restrict__ dself,
-                       const double *__restrict__ bsig, double *__restrict__ v, const int *gate,
-                       const int32_t *__restrict__ parent, int walk)
+                       const double2 *__restrict__ xi, const float2 *__restrict__ u32,
+                       const cx<R> *__restrict__ q, const cx<R> *__restrict__ mp,
+                       const cx<R> *__restrict__ loc, const double *__restrict__ sigma,
+                       const double *__restrict__ dself, const double *__restrict__ bsig,
+                       double *__restrict__ v, const int *gate, const int32_t *__restrict__ parent,
+                       int walk)
 {
     if (gate_closed(gate)) return;
+    constexpr bool kF32 = sizeof(R) == 4;
     __shared__ cx<R> sx[kLeafWarps][kSrcChunk];
     __shared__ cx<R> sq[kLeafWarps][kSrcChunk];
     __shared__ int32_t sj[kLeafWarps][kSrcChunk];
@@ -360,10 +459,12 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t t = blockIdx.x * (int64_t)kLeafWarps + wid;
     if (t >= nleaf) return;
-    int b = leaves[t];
+    const int b = leaves[t];
+    const int lt = level[b], tx = ix[b], ty = iy[b];
     double cxd, cyd, r;
-    box_centre(g, level[b], ix[b], iy[b], cxd, cyd, r);
-    double ir = 1.0 / r;
+    box_centre(g, lt, tx, ty, cxd, cyd, r);
+    const double ir = 1.0 / r;
+    const R irr = (R)ir;
     const cx<R> *lb = loc + (int64_t)b * P;
     double bs = *bsig;
     for (int tb = bg[b]; tb < en[b]; tb += 32) {
@@ -371,9 +472,15 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         int i = tb + lane;
         R cfar = 0;
         if (lane < nt) {
-            double2 zi = xi[i];
-            sz[wid][lane] = mk<R>((R)(zi.x - cxd), (R)(zi.y - cyd));
-            cx<R> u = mk<R>((R)((zi.x - cxd) * ir), (R)((zi.y - cyd) * ir));
+            cx<R> u;  // (z - c)/r
+            if constexpr (kF32) {
+                float2 uu = u32[i];
+                u = mk<R>(uu.x, uu.y);
+            } else {
+                double2 zi = xi[i];
+                u = mk<R>((zi.x - cxd) * ir, (zi.y - cyd) * ir);
+            }
+            sz[wid][lane] = u;
             cx<R> phi = mk<R>(0, 0);
             if (!walk) {
                 phi = lb[P - 1];
@@ -381,32 +488,49 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             } else {
                 // every ancestor's own local expansion at the target (no L2L chain):
                 // (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s, s = depth gap
-                const int lv = level[b];
                 for (int a = b; a >= 0 && level[a] >= 2; a = parent[a]) {
-                    const int sh = lv - level[a];
-                    const R sc = (R)ldexp(1.0, -sh);
-                    const int dxi = ix[b] - (ix[a] << sh), dyi = iy[b] - (iy[a] << sh);
+                    const int sh = lt - level[a];
+                    const R sc = pow2<R>(-sh);
+                    const int dxi = tx - (ix[a] << sh), dyi = ty - (iy[a] << sh);
                     cx<R> ua = mk<R>((R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + u.x * sc,
                                      (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + u.y * sc);
                     const cx<R> *la = loc + (int64_t)a * P;
-                    cx<R> t = la[P - 1];
-                    for (int l = P - 2; l >= 0; l--) t = cfma(t, ua, la[l]);
-                    phi.x += t.x;
-                    phi.y += t.y;
+                    cx<R> tt = la[P - 1];
+                    for (int l = P - 2; l >= 0; l--) tt = cfma(tt, ua, la[l]);
+                    phi.x += tt.x;
+                    phi.y += tt.y;
                 }
             }
             for (int wq = wptr[b]; wq < wptr[b + 1]; wq++) {
-                int s = widx[wq];
-                double sxd, syd, sr;
-                box_centre(g, level[s], ix[s], iy[s], sxd, syd, sr);
-                double isr = 1.0 / sr;
-                cx<R> rho = crcp(mk<R>((R)((zi.x - sxd) * isr), (R)((zi.y - syd) * isr)));
+                const int s = widx[wq];
+                const int ls = level[s];
+                cx<R> zs;  // (z - c_s)/r_s
+                R isr;
+                bool local = false;
+                if constexpr (kF32) {
+                    local = ls >= lt && ls - lt <= kMaxGapF32;
+                    if (local) {
+                        const float f = pow2<float>(ls - lt);
+                        const float2 o = centre_offset(lt, tx, ty, ls, ix[s], iy[s]);
+                        zs = mk<R>(fmaf(u.x, f, o.x), fmaf(u.y, f, o.y));
+                        isr = irr * f;
+                    }
+                }
+                if (!local) {
+                    double2 zi = xi[i];
+                    double sxd, syd, sr;
+                    box_centre(g, ls, ix[s], iy[s], sxd, syd, sr);
+                    const double isd = 1.0 / sr;
+                    zs = mk<R>((R)((zi.x - sxd) * isd), (R)((zi.y - syd) * isd));
+                    isr = (R)isd;
+                }
+                cx<R> rho = crcp(zs);
                 const cx<R> *a = mp + (int64_t)s * P;
                 cx<R> ps = a[P - 1];
                 for (int k = P - 2; k >= 0; k--) ps = cfma(ps, rho, a[k]);
                 ps = cmul(ps, rho);
-                phi.x += ps.x * (R)isr;
-                phi.y += ps.y * (R)isr;
+                phi.x += ps.x * isr;
+                phi.y += ps.y * isr;
             }
             cfar = -phi.y;
         }
@@ -434,13 +558,31 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             fill = 0;
         };
         for (int uq = uptr[b]; uq < uptr[b + 1]; uq++) {
-            int s = uidx[uq];
+            const int s = uidx[uq];
             int sb = bg[s], se = en[s];
+            bool local = false;
+            float fs = 0.f;
+            float2 os = make_float2(0.f, 0.f);
+            if constexpr (kF32) {
+                const int ls = level[s];
+                local = ls >= lt && ls - lt <= 16;
+                if (local) {
+                    fs = pow2<float>(lt - ls);
+                    os = centre_offset(ls, ix[s], iy[s], lt, tx, ty);
+                }
+            }
             while (sb < se) {
                 int take = min(se - sb, kSrcChunk - fill);
                 for (int m = lane; m < take; m += 32) {
-                    double2 zs = xi[sb + m];
-                    sx[wid][fill + m] = mk<R>((R)(zs.x - cxd), (R)(zs.y - cyd));
+                    cx<R> zr;  // (z_j - c)/r
+                    if (local) {
+                        float2 uu = u32[sb + m];
+                        zr = mk<R>(fmaf(uu.x, fs, os.x), fmaf(uu.y, fs, os.y));
+                    } else {
+                        double2 zs = xi[sb + m];
+                        zr = mk<R>((R)((zs.x - cxd) * ir), (R)((zs.y - cyd) * ir));
+                    }
+                    sx[wid][fill + m] = zr;
                     sq[wid][fill + m] = q[sb + m];
                     sj[wid][fill + m] = sb + m;
                 }
@@ -452,7 +594,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         if (fill > 0) process();
         __syncwarp();
         if (lane < nt) {
-            double c = (double)cfar + (double)cn[wid][lane];
+            double c = (double)cfar + (double)(cn[wid][lane] * irr);
             v[i] = 2.0 * (c * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + bs);
         }
         __syncwarp();

@@ -220,8 +220,11 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *
 {
     int M = pl->M;
     double *G = scratch;  // M x 2M
+    lbf_prof_mark(LBF_STAGE_BORDER, 1, s);
     int rc = lbf_mp_build(pl, s, xi_o, G, work, work_len);
+    lbf_prof_mark(LBF_STAGE_BORDER, 0, s);
     if (rc) return rc;
+    lbf_prof_mark(LBF_STAGE_INVERSE, 1, s);
     for (int k = 0; k < M; k++) {
         LBF_LAUNCH(k_gj_pivot, 1, 1024, 0, s, M, k, G, pl->dev_status);
         int64_t work = (int64_t)M * (2 * M - (k + 1));
@@ -230,6 +233,7 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *
     LBF_CHECK_LAUNCH();
     LBF_LAUNCH(k_copy_inverse, lbf_cdiv((int64_t)M * M, 256), 256, 0, s, M, G, pl->Sinv);
     LBF_CHECK_LAUNCH();
+    lbf_prof_mark(LBF_STAGE_INVERSE, 0, s);
     return LBF_OK;
 }
 

@@ -133,6 +133,7 @@ struct lbf_plan {
     // float FMM (precision FP32_REFINE)
     int P32 = 0;
     float2 *q32 = nullptr, *mpole32 = nullptr, *local32 = nullptr;
+    float2 *u32 = nullptr;  // per node: (xi - c)/r about the centre c, half-width r of its leaf
     float *tab32_binom = nullptr;
     float2 *tab32_tpow = nullptr, *tab32_dshift = nullptr;
     double *gr = nullptr, *gd = nullptr;  // refinement residual and correction
@@ -196,6 +197,7 @@ int lbf_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *scratch, i
 #define LBF_PREC_FP32 1
 int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s,
                 int prec);
+int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s);  // plan time, after the tree and the gather
 int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,
                       const double *t, double *u, cudaStream_t s);
 int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p,

@@ -79,6 +79,7 @@ def load():
             "lbf_tree_export": (C.c_int, [_P, _P, _P, _P]),
             "lbf_list_export": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(i64), _P]),
             "lbf_plan_counts": (C.c_int, [_P, _P, _P]),
+            "lbf_border_counts": (C.c_int, [_P, _P, _P]),
             "lbf_profile_enable": (C.c_int, [C.c_int]),
             "lbf_profile_reset": (C.c_int, []),
             "lbf_profile_read": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(C.c_double)]),
@@ -99,8 +100,8 @@ def exported_symbols():
     return ["lbf_default_options", "lbf_status_string", "lbf_workspace_size", "lbf_plan_create",
             "lbf_plan_destroy", "lbf_plan_info", "lbf_geometry_out", "lbf_apply",
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
-            "lbf_list_export", "lbf_plan_counts", "lbf_profile_enable", "lbf_profile_reset",
-            "lbf_profile_read", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
+            "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
+            "lbf_profile_reset", "lbf_profile_read", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
             "lbf_launch_count"]
 
 
@@ -289,13 +290,21 @@ def lbf_list_export(plan: Plan, kind: int, stream=None):
 
 LBF_KERNEL_UP, LBF_KERNEL_DOWN, LBF_KERNEL_LEAF = 0, 1, 2
 LBF_KERNEL_DIRECT, LBF_KERNEL_ARNOLDI, LBF_KERNEL_ESUM = 3, 4, 5
-KERNEL_NAMES = ["up", "down", "leaf", "direct", "arnoldi", "esum", "up32", "down32", "leaf32"]
+KERNEL_NAMES = ["up", "down", "leaf", "direct", "arnoldi", "esum", "up32", "down32", "leaf32",
+                "esum32", "plan_geometry", "plan_border", "plan_inverse"]
 
 
 def lbf_plan_counts(plan: Plan, stream=None) -> dict:
     c = (C.c_int64 * 8)()
     _check(load().lbf_plan_counts(plan.handle, C.cast(c, _P), _stream(stream)), "lbf_plan_counts")
     keys = ["N", "p2p_pairs", "m2m", "m2l", "l2l", "w_pairs", "x_pairs", "leaves"]
+    return dict(zip(keys, [int(v) for v in c]))
+
+
+def lbf_border_counts(plan: Plan, stream=None) -> dict:
+    c = (C.c_int64 * 6)()
+    _check(load().lbf_border_counts(plan.handle, C.cast(c, _P), _stream(stream)), "lbf_border_counts")
+    keys = ["p2l_pairs", "direct_pairs", "global_centres", "walk_expansions", "terms", "terms32"]
     return dict(zip(keys, [int(v) for v in c]))
 
 
