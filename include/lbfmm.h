@@ -99,6 +99,9 @@ typedef struct lbf_options {
 /* lbf_apply: OR this into op to run the FMM part in float (plans built with
  * LBF_PRECISION_FP32_REFINE) */
 #define LBF_OP_FP32 16
+/* lbf_apply: OR this into op to apply the transposed operator instead (the
+ * adjoint system): K_ONLY -> (I + 2K)^T, FULL -> A^T, PRECONDITIONED -> P^-T A^T */
+#define LBF_OP_TRANSPOSE 32
 
 int lbf_default_options(lbf_options *opt /* host */);
 
@@ -115,8 +118,9 @@ int lbf_workspace_size(int M, const int64_t *island_ptr /* host, M+1 */, const l
 /* Build a plan: project the nodes to the plane (Sec. 3), precompute the
  * trapezoidal weights w_j = h xi'_j, the self terms and the rank-one sphere
  * correction (Sec. 5, Eq. disc_sphere with Eq. cont_kern), build the Morton
- * quadtree and its interaction lists, and (opt->border) form E, F, D and
- * factor the Schur complement S = D - F E (Sec. 5, Eq. matrix_eqns_c).
+ * quadtree and its interaction lists, and (opt->border) build the lists of the
+ * multiplier potential E y (evaluated on the quadtree, E is never formed) and
+ * invert the Schur complement S = D - F E (Sec. 5, Eq. matrix_eqns_c).
  *
  *   x, dx, d2x : N x 3 nodes on the unit sphere and their first and second
  *                derivatives with respect to alpha (device)
@@ -134,6 +138,19 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
                     const double *dx, const double *d2x, const double *centres,
                     const double *pole_rotation, const lbf_options *opt, void *workspace,
                     size_t bytes, int64_t *box_capacity_needed, lbf_stream_t stream);
+
+/* The same plan from nodes given in the stereographic plane (Sec. 3), for
+ * callers whose variables are the planar node positions (derivatives with
+ * respect to xi_j, with xi'_j and xi''_j held fixed, use this form):
+ *   xi, dxi, d2xi : N x 2 (re, im) planar nodes and their first and second
+ *                   derivatives with respect to alpha (device)
+ *   centres       : M x 3 multiplier sites on the unit sphere (device)
+ * No pole rotation (the plane is the caller's); everything else as
+ * lbf_plan_create. */
+int lbf_plan_create_planar(lbf_plan **plan, int M, const int64_t *island_ptr, const double *xi,
+                           const double *dxi, const double *d2xi, const double *centres,
+                           const lbf_options *opt, void *workspace, size_t bytes,
+                           int64_t *box_capacity_needed, lbf_stream_t stream);
 
 int lbf_plan_destroy(lbf_plan *plan);
 
@@ -162,6 +179,38 @@ int lbf_apply(lbf_plan *plan, int op, const double *in, double *out, lbf_stream_
  * Returns LBF_NOCONV (> 0) when maxit is reached before tol. */
 int lbf_gmres_solve(lbf_plan *plan, const double *g, double *sigma, double *a, const double *x0,
                     int *iters, double *rel_res, lbf_stream_t stream);
+
+/* The adjoint system (Sec. 5, the bordered Eq. matrix_eqns transposed): solve
+ * A^T lam = r by GMRES on P^-T A^T (left preconditioning with P^T, the same
+ * tolerance, restart, precision and refinement options as lbf_gmres_solve).
+ *   r, lam : N + M device vectors in caller order (node part, then one entry per
+ *            constraint row, the last one the row of Eq. sum_ak); x0 nullable.
+ * Synchronous; LBF_NOCONV (soft) when maxit is reached. */
+int lbf_gmres_solve_transpose(lbf_plan *plan, const double *r, double *lam, const double *x0,
+                              int *iters, double *rel_res, lbf_stream_t stream);
+
+/* Transposed evaluation (adjoint of lbf_evaluate, Eq. u_multi): for u = C [sigma; a]
+ * at the targets, [sbar; abar] = C^T ubar, i.e.
+ *   sbar_j = sum_t ubar_t ( (1/2pi) Im(w_j / (xi_j - xi_t)) + beta_j ),
+ *   abar_m = sum_t ubar_t G(t, c_m).
+ *   targets : T x 3 on the unit sphere; ubar : T; sbar : N; abar : M (nullable);
+ *   device, caller order.  Asynchronous; needs the border.  LBF_EWORKSPACE when
+ *   the plan's basis region (restart + 1 vectors) holds fewer than 4 N doubles. */
+int lbf_evaluate_transpose(lbf_plan *plan, int64_t T, const double *targets, const double *ubar,
+                           double *sbar, double *abar, lbf_stream_t stream);
+
+/* Gradient of a target functional L(u) with respect to the planar node positions
+ * (d/dRe xi_j, d/dIm xi_j; xi'_j and xi''_j held fixed, so the weights and the
+ * diagonal-limit terms are constant):
+ *   dL/dxi_j = d/dxi_j (ubar^T C z) - lam^T (dA/dxi_j) z,   A^T lam = C^T ubar,
+ * for the solution z = [sigma; a] of lbf_gmres_solve, ubar = dL/du at the targets
+ * and lam from lbf_gmres_solve_transpose (r = C^T ubar from lbf_evaluate_transpose).
+ * dL/dg_j = 2 lam_j needs no call.  sigma (N), a (M), lam (N + M), ubar (T),
+ * targets (T x 3), grad (N x 2 out): device, caller order.  Asynchronous, FP64;
+ * LBF_EWORKSPACE when the basis region holds fewer than 12 N doubles. */
+int lbf_gradient_nodes(lbf_plan *plan, const double *sigma, const double *a, const double *lam,
+                       int64_t T, const double *targets, const double *ubar, double *grad,
+                       lbf_stream_t stream);
 
 /* Work of the plan's last lbf_gmres_solve (host out): stats[0] Arnoldi steps,
  * [1] FP64 operator applications, [2] FP32 operator applications,

@@ -131,8 +131,8 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     if (o.matvec == LBF_MATVEC_FMM) {
         pl->mpole = A.get<double2>(cap * P);
         pl->local = A.get<double2>(cap * P);
-        pl->upcnt = A.get<int32_t>(cap);
     }
+    if (o.matvec == LBF_MATVEC_FMM || o.border) pl->upcnt = A.get<int32_t>(cap);
     if (o.precision == LBF_PRECISION_FP32_REFINE) {
         int P32 = o.p32 + 1;
         pl->P32 = P32;
@@ -178,6 +178,8 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         B.p2l_src = A.get<int32_t>(B.pair_cap);
         B.near_ptr = A.get<int32_t>(cap + 1);
         B.near_src = A.get<int32_t>(B.pair_cap);
+        B.cp2l = A.get<int32_t>((int64_t)M + 1);
+        B.cnear = A.get<int32_t>((int64_t)M + 1);
         B.loc = A.get<double2>(cap * B.P);
         if (o.precision == LBF_PRECISION_FP32_REFINE) B.loc32 = A.get<float2>(cap * B.P32);
         B.zc = A.get<double2>(M);
@@ -207,25 +209,26 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     size_t tmp = 0;
     auto add = [&](size_t b) { tmp = ((tmp + 255) & ~size_t(255)) + b; };
     add(sizeof(double2) * N);      // xi_o
-    add(sizeof(double) * 3 * N);   // x3_o
     add(sizeof(double2) * N);      // w_o
     add(sizeof(double) * N);       // d_o
     add(sizeof(double) * N);       // b_o
-    add(sizeof(uint64_t) * N);     // keys
-    add(sizeof(uint64_t) * N);     // keys_alt
-    add(sizeof(int32_t) * N);      // perm_alt
+    const int64_t nk = std::max<int64_t>(N, o.border ? pl->bd.pair_cap : 0);  // tree and pair sorts
+    add(sizeof(uint64_t) * nk);    // keys
+    add(sizeof(uint64_t) * nk);    // keys_alt
+    add(sizeof(int32_t) * nk);     // perm_alt
     int64_t iscr = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     add(sizeof(int32_t) * iscr);   // integer scratch (scans, histograms, flags)
-    add(sizeof(double) * 2 * (size_t)M * M + 64);  // Gauss-Jordan block
+    add(sizeof(double) * lbf_gj_scratch_doubles(M));  // Gauss-Jordan pivot rows and partials
     size_t big = std::max(vbytes, tmp);
     pl->region = (char *)A.take(big);
+    pl->region_bytes = big;
     pl->V = o.border ? (double *)pl->region : nullptr;
 }
 
 namespace {
 struct Temps {
     double2 *xi_o, *w_o;
-    double *x3_o, *d_o, *b_o;
+    double *d_o, *b_o;
     uint64_t *keys, *keys_alt;
     int32_t *perm_alt, *iscr;
     int64_t iscr_len;
@@ -243,17 +246,17 @@ Temps temps(lbf_plan *pl, char *region, int64_t N, int M, int64_t cap)
         return p;
     };
     t.xi_o = (double2 *)take(sizeof(double2) * N);
-    t.x3_o = (double *)take(sizeof(double) * 3 * N);
     t.w_o = (double2 *)take(sizeof(double2) * N);
     t.d_o = (double *)take(sizeof(double) * N);
     t.b_o = (double *)take(sizeof(double) * N);
-    t.keys = (uint64_t *)take(sizeof(uint64_t) * N);
-    t.keys_alt = (uint64_t *)take(sizeof(uint64_t) * N);
-    t.perm_alt = (int32_t *)take(sizeof(int32_t) * N);
+    const int64_t nk = std::max<int64_t>(N, pl->opt.border ? pl->bd.pair_cap : 0);
+    t.keys = (uint64_t *)take(sizeof(uint64_t) * nk);
+    t.keys_alt = (uint64_t *)take(sizeof(uint64_t) * nk);
+    t.perm_alt = (int32_t *)take(sizeof(int32_t) * nk);
     int64_t nunits = lbf_cdiv(N, 1024);
     t.iscr_len = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     t.iscr = (int32_t *)take(sizeof(int32_t) * t.iscr_len);
-    t.gj = (double *)take(sizeof(double) * 2 * (size_t)M * M + 64);
+    t.gj = (double *)take(sizeof(double) * lbf_gj_scratch_doubles(M));
     return t;
 }
 }  // namespace
@@ -320,10 +323,10 @@ int lbf_workspace_size(int M, const int64_t *island_ptr, const lbf_options *opt,
     return LBF_OK;
 }
 
-int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const double *x,
-                    const double *dx, const double *d2x, const double *centres,
-                    const double *pole_rotation, const lbf_options *opt, void *workspace,
-                    size_t bytes, int64_t *box_needed, lbf_stream_t stream)
+static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const double *x,
+                       const double *dx, const double *d2x, const double *centres,
+                       const double *pole_rotation, int planar, const lbf_options *opt,
+                       void *workspace, size_t bytes, int64_t *box_needed, lbf_stream_t stream)
 {
     if (!plan || !x || !dx || !d2x || !centres || !opt || !workspace || !valid(*opt))
         return LBF_EINVAL;
@@ -397,7 +400,7 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     // plan-creation temporaries overlay the region of the GMRES basis
     Temps tt = temps(pl, pl->region, N, M, cap);
     lbf_prof_mark(LBF_STAGE_GEOMETRY, 1, s);
-    rc = lbf_geometry_build(pl, x, dx, d2x, centres, s, tt.xi_o, tt.x3_o, tt.w_o, tt.d_o, tt.b_o);
+    rc = lbf_geometry_build(pl, x, dx, d2x, centres, planar, s, tt.xi_o, tt.w_o, tt.d_o, tt.b_o);
     if (rc) return fail(rc);
     {
         int64_t need = 0;
@@ -412,7 +415,8 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
     if ((rc = lbf_fmm_prepare(pl, s))) return fail(rc);
     lbf_prof_mark(LBF_STAGE_GEOMETRY, 0, s);
     if (opt->border) {
-        rc = lbf_border_build(pl, s, tt.xi_o, tt.gj, tt.iscr, tt.iscr_len);
+        SortBufs sb{tt.keys, tt.keys_alt, tt.perm_alt};
+        rc = lbf_border_build(pl, s, tt.xi_o, tt.gj, tt.iscr, tt.iscr_len, sb);
         if (rc) return fail(rc);
     }
     CK(cudaMemcpyAsync(pl->host_status, pl->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -420,11 +424,30 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
 #undef CK
     int st = *pl->host_status;
     if (st & LBF_DEV_POLE) return fail(LBF_EPOLE);
+    if (st & LBF_DEV_TIMEOUT) return fail(LBF_ETIMEOUT);  // a grid barrier of the inverse gave up
     if (st & 4) return fail(LBF_ESINGULAR);   // singular Schur complement
     if (st & 8) return fail(LBF_EDEPTH);      // list overflow
     if (st & 16) return fail(LBF_EWORKSPACE); // more near centres per island than the border holds
     *plan = pl;
     return LBF_OK;
+}
+
+int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const double *x,
+                    const double *dx, const double *d2x, const double *centres,
+                    const double *pole_rotation, const lbf_options *opt, void *workspace,
+                    size_t bytes, int64_t *box_needed, lbf_stream_t stream)
+{
+    return plan_create(plan, M, island_ptr, x, dx, d2x, centres, pole_rotation, 0, opt, workspace,
+                       bytes, box_needed, stream);
+}
+
+int lbf_plan_create_planar(lbf_plan **plan, int M, const int64_t *island_ptr, const double *xi,
+                           const double *dxi, const double *d2xi, const double *centres,
+                           const lbf_options *opt, void *workspace, size_t bytes,
+                           int64_t *box_needed, lbf_stream_t stream)
+{
+    return plan_create(plan, M, island_ptr, xi, dxi, d2xi, centres, nullptr, 1, opt, workspace,
+                       bytes, box_needed, stream);
 }
 
 int lbf_plan_destroy(lbf_plan *pl)
@@ -462,7 +485,8 @@ int lbf_geometry_out(const lbf_plan *pl, double *xi, double *normal, double *wei
 int lbf_apply(lbf_plan *pl, int op, const double *in, double *out, lbf_stream_t stream)
 {
     int prec = (op & LBF_OP_FP32) ? LBF_PREC_FP32 : LBF_PREC_FP64;
-    op &= ~LBF_OP_FP32;
+    const int tr = op & LBF_OP_TRANSPOSE;
+    op &= ~(LBF_OP_FP32 | LBF_OP_TRANSPOSE);
     if (!pl || !in || !out || op < 0 || op > 2) return LBF_EINVAL;
     if (op != LBF_OP_K_ONLY && !pl->opt.border) return LBF_ENOTBUILT;
     if (prec == LBF_PREC_FP32 && !pl->q32) return LBF_ENOTBUILT;
@@ -470,7 +494,7 @@ int lbf_apply(lbf_plan *pl, int op, const double *in, double *out, lbf_stream_t 
     int with_a = op != LBF_OP_K_ONLY;
     int rc = lbf_permute_in(pl, in, pl->tin, with_a, s);
     if (rc) return rc;
-    rc = lbf_apply_op_sorted(pl, op, pl->tin, pl->tout, nullptr, s, prec);
+    rc = lbf_apply_op_sorted(pl, op | tr, pl->tin, pl->tout, nullptr, s, prec);
     if (rc) return rc;
     return lbf_permute_out(pl, pl->tout, out, with_a, s);
 }
@@ -480,7 +504,35 @@ int lbf_gmres_solve(lbf_plan *pl, const double *g, double *sigma, double *a, con
 {
     if (!pl || !g || !sigma) return LBF_EINVAL;
     if (!pl->opt.border) return LBF_ENOTBUILT;
-    return lbf_gmres_impl(pl, g, sigma, a, x0, iters, rel_res, (cudaStream_t)stream);
+    return lbf_gmres_impl(pl, g, sigma, a, x0, iters, rel_res, (cudaStream_t)stream, 0);
+}
+
+int lbf_gmres_solve_transpose(lbf_plan *pl, const double *r, double *lam, const double *x0,
+                              int *iters, double *rel_res, lbf_stream_t stream)
+{
+    if (!pl || !r || !lam) return LBF_EINVAL;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    return lbf_gmres_impl(pl, r, lam, nullptr, x0, iters, rel_res, (cudaStream_t)stream, 1);
+}
+
+int lbf_evaluate_transpose(lbf_plan *pl, int64_t T, const double *targets, const double *ubar,
+                           double *sbar, double *abar, lbf_stream_t stream)
+{
+    if (!pl || T < 0 || !sbar || (T > 0 && (!targets || !ubar))) return LBF_EINVAL;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    if (pl->region_bytes < sizeof(double) * (4 * (size_t)pl->N + 8)) return LBF_EWORKSPACE;
+    return lbf_evaluate_transpose_impl(pl, T, targets, ubar, sbar, abar, (cudaStream_t)stream);
+}
+
+int lbf_gradient_nodes(lbf_plan *pl, const double *sigma, const double *a, const double *lam,
+                       int64_t T, const double *targets, const double *ubar, double *grad,
+                       lbf_stream_t stream)
+{
+    if (!pl || !sigma || !a || !lam || !grad || T < 0 || (T > 0 && (!targets || !ubar)))
+        return LBF_EINVAL;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    if (pl->region_bytes < sizeof(double) * (12 * (size_t)pl->N + 8)) return LBF_EWORKSPACE;
+    return lbf_gradient_nodes_impl(pl, sigma, a, lam, T, targets, ubar, grad, (cudaStream_t)stream);
 }
 
 int lbf_solve_stats(const lbf_plan *pl, int64_t stats[4])

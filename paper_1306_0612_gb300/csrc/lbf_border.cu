@@ -189,30 +189,6 @@ __global__ void k_pairs_count(int M, const int32_t *__restrict__ off, const int3
     for (int q = off[m]; q < off[m] + cnt[m]; q++) atomicAdd(&per_box[box[q]], 1);
 }
 
-__global__ void k_pairs_fill(int M, const int32_t *__restrict__ off, const int32_t *__restrict__ cnt,
-                             const int32_t *__restrict__ box, const int32_t *__restrict__ ptr,
-                             int32_t *__restrict__ cursor, int32_t *__restrict__ src)
-{
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= M) return;
-    for (int q = off[m]; q < off[m] + cnt[m]; q++) {
-        int b = box[q];
-        src[ptr[b] + atomicAdd(&cursor[b], 1)] = m;
-    }
-}
-
-// each box's list in ascending centre order (deterministic sums)
-__global__ void k_sort_segments(int64_t nbox, const int32_t *__restrict__ ptr, int32_t *__restrict__ v)
-{
-    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    for (int i = ptr[b] + 1; i < ptr[b + 1]; i++) {
-        int x = v[i], j = i - 1;
-        while (j >= ptr[b] && v[j] > x) { v[j + 1] = v[j]; j--; }
-        v[j + 1] = x;
-    }
-}
-
 __device__ __forceinline__ double block_sum(double v, double *sh)
 {
     v = wsum(v);
@@ -310,10 +286,10 @@ __global__ void k_mp_islands(int M, int P, const int64_t *__restrict__ ptr,
     }
 }
 
-// sum_j log|xi_j - xi_m| over the nodes j of island k
-__device__ double island_logsum(int k, int P, const int64_t *ptr, const double2 *xi_o, double2 xm,
-                                double2 z, double R, double rho, const double2 *mu,
-                                const double2 *nu, double slog)
+// sum_j log|xi_j - xi_m| over the nodes j of island k by the island's expansions;
+// false where xi_m is neither far from nor deep inside the island (direct sum needed)
+__device__ bool island_logsum(int k, int P, double2 xm, double2 z, double R, double rho,
+                              const double2 *mu, const double2 *nu, double slog, double &out)
 {
     cz<double> d{xm.x - z.x, xm.y - z.y};
     double dd = sqrt(d.x * d.x + d.y * d.y);
@@ -326,7 +302,8 @@ __device__ double island_logsum(int k, int P, const int64_t *ptr, const double2 
             s += (c.x * pw.x - c.y * pw.y) / l;
             pw = zmul(pw, t);
         }
-        return mu[(int64_t)k * P].x * log(dd) - s;
+        out = mu[(int64_t)k * P].x * log(dd) - s;
+        return true;
     }
     if (dd * kEta <= rho) {
         // sum_j log|xi_j - z_k| - Re sum_l nu_l ((xi_m - z_k)/rho)^l / l
@@ -337,43 +314,81 @@ __device__ double island_logsum(int k, int P, const int64_t *ptr, const double2 
             s += (c.x * pw.x - c.y * pw.y) / l;
             pw = zmul(pw, t);
         }
-        return slog - s;
+        out = slog - s;
+        return true;
     }
-    double s = 0.0;
-    for (int64_t j = ptr[k]; j < ptr[k + 1]; j++) {
-        double dx = xi_o[j].x - xm.x, dy = xi_o[j].y - xm.y;
-        s += 0.5 * log(dx * dx + dy * dy);
-    }
-    return s;
+    return false;
 }
 
-// S = D - F E into the left half of [S | I] (M x 2M): row r < M-1 is minus the sum
+__device__ __forceinline__ double schur_entry(int M, int r, int m, const int64_t *ptr,
+                                              const int32_t *kind, const double *lam,
+                                              const double *sell, double ls)
+{
+    if (r == M - 1) return 1.0;
+    const int k = r + 1;
+    double fe = sell[k];  // sum_j (l_j - log 2)
+    if (kind[m] != 0) fe += (double)(ptr[k + 1] - ptr[k]) * lam[m] - 2.0 * ls;
+    return -fe / (2.0 * LBF_PI);
+}
+
+// S = D - F E into G (M x M, row-major): row r < M-1 is minus the sum
 // of E over island r+1 (Eq. disc_constr), the last row is D's row of ones (Eq. sum_ak).
+// Entries that need a direct sum over the island's nodes are listed for
+// k_mp_schur_direct (a warp per entry) instead of looping in one lane.
 __global__ void k_mp_schur(int M, int P, const int64_t *__restrict__ ptr,
                            const double2 *__restrict__ xi_o, const double2 *__restrict__ xc,
                            const int32_t *__restrict__ kind, const double *__restrict__ lam,
                            const double2 *__restrict__ zc, const double *__restrict__ Rk,
                            const double *__restrict__ rk, const double *__restrict__ slog,
                            const double *__restrict__ sell, const double2 *__restrict__ mu,
-                           const double2 *__restrict__ nu, double *__restrict__ G)
+                           const double2 *__restrict__ nu, double *__restrict__ G,
+                           int32_t *__restrict__ dcount, int32_t *__restrict__ dlist, int dcap)
 {
     int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (id >= (int64_t)M * M) return;
     int r = (int)(id / M), m = (int)(id % M);
-    double v;
-    if (r == M - 1) {
-        v = 1.0;
-    } else {
-        int k = r + 1;
-        double fe = sell[k];  // sum_j (l_j - log 2)
-        if (kind[m] != 0) {
-            double ls = island_logsum(k, P, ptr, xi_o, xc[m], zc[k], Rk[k], rk[k], mu, nu, slog[k]);
-            fe += (double)(ptr[k + 1] - ptr[k]) * lam[m] - 2.0 * ls;
+    double ls = 0.0;
+    bool listed = false;
+    if (r < M - 1 && kind[m] != 0) {
+        const int k = r + 1;
+        if (!island_logsum(k, P, xc[m], zc[k], Rk[k], rk[k], mu, nu, slog[k], ls)) {
+            int q = atomicAdd(dcount, 1);
+            if (q < dcap) {
+                dlist[q] = (int32_t)id;
+                listed = true;
+            } else {  // list full: sum here
+                ls = 0.0;
+                for (int64_t j = ptr[k]; j < ptr[k + 1]; j++) {
+                    double dx = xi_o[j].x - xc[m].x, dy = xi_o[j].y - xc[m].y;
+                    ls += 0.5 * log(dx * dx + dy * dy);
+                }
+            }
         }
-        v = -fe / (2.0 * LBF_PI);
     }
-    G[(int64_t)r * 2 * M + m] = v;
-    G[(int64_t)r * 2 * M + M + m] = (r == m) ? 1.0 : 0.0;
+    if (!listed) G[(int64_t)r * M + m] = schur_entry(M, r, m, ptr, kind, lam, sell, ls);
+}
+
+__global__ void k_mp_schur_direct(int M, const int64_t *__restrict__ ptr,
+                                  const double2 *__restrict__ xi_o, const double2 *__restrict__ xc,
+                                  const int32_t *__restrict__ kind, const double *__restrict__ lam,
+                                  const double *__restrict__ sell, const int32_t *__restrict__ dcount,
+                                  const int32_t *__restrict__ dlist, int dcap, double *__restrict__ G)
+{
+    const int n = min(*dcount, dcap);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < n; q += nwarps) {
+        const int64_t id = dlist[q];
+        const int r = (int)(id / M), m = (int)(id % M), k = r + 1;
+        const double2 xm = xc[m];
+        double ls = 0.0;
+        for (int64_t j = ptr[k] + lane; j < ptr[k + 1]; j += 32) {
+            double dx = xi_o[j].x - xm.x, dy = xi_o[j].y - xm.y;
+            ls += 0.5 * log(dx * dx + dy * dy);
+        }
+        ls = wsum(ls);
+        if (lane == 0) G[(int64_t)r * M + m] = schur_entry(M, r, m, ptr, kind, lam, sell, ls);
+    }
 }
 
 // ---- per application ---------------------------------------------------------------
@@ -600,31 +615,48 @@ static int read_i32(const int32_t *d, int32_t *h, cudaStream_t s)
 }
 
 // (box, centre) pairs of one kind -> per-box lists in ascending centre order
+// per pair of a centre-major list: sort key = the box, value = the centre
+__global__ void k_pair_keys(int M, const int32_t *__restrict__ off, const int32_t *__restrict__ cnt,
+                            const int32_t *__restrict__ box, uint64_t *__restrict__ key,
+                            int32_t *__restrict__ centre)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    for (int q = off[m]; q < off[m] + cnt[m]; q++) {
+        key[q] = (uint64_t)box[q];
+        centre[q] = m;
+    }
+}
+
+// (box, centre) pairs generated centre by centre -> per-box lists in ascending
+// centre order (CSR ptr/src): a stable radix sort by box of the centre-major
+// pairs keeps every box's centres in generation (= centre) order.
 static int pairs_to_boxes(lbf_plan *pl, cudaStream_t s, const int32_t *off, const int32_t *cnt,
-                          const int32_t *box, int32_t *ptr, int32_t *src, int32_t *work,
-                          int64_t work_len)
+                          const int32_t *box, int64_t npairs, int32_t *ptr, int32_t *src,
+                          const SortBufs &sb, int32_t *work, int64_t work_len)
 {
     int64_t nb = pl->tree.nbox;
     int M = pl->M;
-    LBF_LAUNCH(k_zero_i32, lbf_cdiv(2 * nb, 256), 256, 0, s, work, 2 * nb);
+    LBF_LAUNCH(k_zero_i32, lbf_cdiv(nb, 256), 256, 0, s, work, nb);
     LBF_LAUNCH(k_pairs_count, lbf_cdiv(M, 128), 128, 0, s, M, off, cnt, box, work);
     LBF_CHECK_LAUNCH();
-    int rc = lbf_scan_i32(work, ptr, nb, work + 2 * nb, work_len - 2 * nb, s);
+    int rc = lbf_scan_i32(work, ptr, nb, work + nb, work_len - nb, s);
     if (rc) return rc;
-    int32_t a = 0, b = 0;
-    if ((rc = read_i32(ptr + nb - 1, &a, s)) || (rc = read_i32(work + nb - 1, &b, s))) return rc;
-    int32_t tot = a + b;
+    int32_t tot = (int32_t)npairs;
     LBF_CUDA(cudaMemcpyAsync(ptr + nb, &tot, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    LBF_LAUNCH(k_pairs_fill, lbf_cdiv(M, 128), 128, 0, s, M, off, cnt, box, ptr, work + nb, src);
-    LBF_LAUNCH(k_sort_segments, lbf_cdiv(nb, 128), 128, 0, s, nb, ptr, src);
+    LBF_CUDA(cudaStreamSynchronize(s));  // tot is a host local
+    if (npairs == 0) return LBF_OK;
+    LBF_LAUNCH(k_pair_keys, lbf_cdiv(M, 128), 128, 0, s, M, off, cnt, box, sb.key, src);
     LBF_CHECK_LAUNCH();
-    return LBF_OK;
+    int bits = 1;
+    while (((int64_t)1 << bits) < nb) bits++;
+    return lbf_radix_sort(sb.key, sb.key_alt, src, sb.val_alt, npairs, bits, work, work_len, s);
 }
 
 // Plan time: node and centre data, the centres' walks down the tree (P2L and
-// direct lists per box), island moments, and S into G (M x 2M, identity on the right).
+// direct lists per box), island moments, and S into G (M x M).
 int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
-                 int64_t work_len)
+                 int64_t work_len, const SortBufs &sb)
 {
     int64_t N = pl->N;
     int M = pl->M;
@@ -663,13 +695,32 @@ int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, i
     LBF_LAUNCH(k_mp_walk, lbf_cdiv(M, 128), 128, 0, s, M, B.kind, B.cell, D, tv, 1, np2l, nnear,
                op2l, onear, B.pairs_a, B.pairs_b, pl->dev_status);
     LBF_CHECK_LAUNCH();
-    if ((rc = pairs_to_boxes(pl, s, op2l, np2l, B.pairs_a, B.p2l_ptr, B.p2l_src, w2, w2_len))) return rc;
-    if ((rc = pairs_to_boxes(pl, s, onear, nnear, B.pairs_b, B.near_ptr, B.near_src, w2, w2_len)))
+    if ((rc = pairs_to_boxes(pl, s, op2l, np2l, B.pairs_a, n_p2l, B.p2l_ptr, B.p2l_src, sb, w2,
+                             w2_len)))
         return rc;
+    if ((rc = pairs_to_boxes(pl, s, onear, nnear, B.pairs_b, n_near, B.near_ptr, B.near_src, sb, w2,
+                             w2_len)))
+        return rc;
+    // the centre-major lists stay: offsets per centre for the transposed potential
+    LBF_CUDA(cudaMemcpyAsync(B.cp2l, op2l, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, s));
+    LBF_CUDA(cudaMemcpyAsync(B.cnear, onear, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, s));
+    {
+        int32_t tail[2] = {(int32_t)n_p2l, (int32_t)n_near};
+        LBF_CUDA(cudaMemcpyAsync(B.cp2l + M, &tail[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        LBF_CUDA(cudaMemcpyAsync(B.cnear + M, &tail[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        LBF_CUDA(cudaStreamSynchronize(s));  // tail is a host local
+    }
     B.n_p2l = n_p2l;
     B.n_near = n_near;
+    // the walk and pair scratch is free again: a counter and the list of direct entries
+    int32_t *dcount = w2, *dlist = w2 + 1;
+    const int dcap = (int)std::min<int64_t>(w2_len - 1, INT32_MAX);
+    LBF_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int32_t), s));
     LBF_LAUNCH(k_mp_schur, lbf_cdiv((int64_t)M * M, 128), 128, 0, s, M, B.P, pl->island_ptr, xi_o,
-               B.xc, B.kind, B.lam, B.zc, B.Rk, B.rk, B.slog, B.sell, B.mu, B.nu, G);
+               B.xc, B.kind, B.lam, B.zc, B.Rk, B.rk, B.slog, B.sell, B.mu, B.nu, G, dcount, dlist,
+               dcap);
+    LBF_LAUNCH(k_mp_schur_direct, 152 * 4, 256, 0, s, M, pl->island_ptr, xi_o, B.xc, B.kind, B.lam,
+               B.sell, dcount, dlist, dcap, G);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -754,5 +805,163 @@ extern "C" int lbf_border_counts(const lbf_plan *pl, int64_t counts[6], lbf_stre
     counts[3] = (int64_t)h[1];
     counts[4] = B.P;
     counts[5] = B.P32;
+    return LBF_OK;
+}
+
+// ---- transposed and differentiated multiplier potential (adjoint) -----------------------
+namespace {
+
+// sums[2] = sum_i tau_i (l_i - log 2), one block, fixed order
+__global__ void k_mp_tsum(int64_t N, const double *__restrict__ tau, const double *__restrict__ ell,
+                          double *__restrict__ sums, const int *gate)
+{
+    if (gate && *gate == 0) return;
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) a = fma(tau[i], ell[i] - LBF_LN2, a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) sums[2] = a;
+}
+
+// out_m = add_m + sc (E^T tau)_m, warp per centre (Sec. 4.1, Eq. u_multi, transposed):
+//   (E^T tau)_m = (1/2pi) [ sum_i tau_i (l_i - log 2) + lam_m T - 2 sum_i tau_i log|xi_i - xi_m| ]
+// (no lam and log terms for the centre at the pole), T = sum_i tau_i.  The log sum
+// takes the same (box, centre) pairs as E y, transposed: the multipoles of the
+// boxes the centre's walk entered by P2L (M2P at the centre), the leaves it sums
+// directly, and every node for a centre outside the tree's square.
+__global__ void k_mp_transpose(int M, int P, Geo g, const int32_t *__restrict__ level,
+                               const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
+                               const int32_t *__restrict__ bg, const int32_t *__restrict__ en,
+                               const int32_t *__restrict__ cp2l, const int32_t *__restrict__ pa,
+                               const int32_t *__restrict__ cnear, const int32_t *__restrict__ pb,
+                               const int32_t *__restrict__ kind, const double2 *__restrict__ xc,
+                               const double *__restrict__ lam, int64_t N,
+                               const double2 *__restrict__ xi, const double *__restrict__ tau,
+                               const cz<double> *__restrict__ mp, const double *__restrict__ bsig,
+                               const double *__restrict__ sums, double sc,
+                               const double *__restrict__ add, double *__restrict__ out,
+                               const int *gate)
+{
+    if (gate && *gate == 0) return;
+    const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (m >= M) return;
+    double L = 0.0;
+    if (kind[m] != 0) {
+        const double2 xm = xc[m];
+        for (int q = cp2l[m] + lane; q < cp2l[m + 1]; q += 32) {
+            const int b = pa[q];
+            double cx, cy, r;
+            centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
+            const double dx = xm.x - cx, dy = xm.y - cy;
+            const cz<double> rho = zinv(cz<double>{dx / r, dy / r});  // r / (xi_m - c)
+            const cz<double> *a = mp + (int64_t)b * P;
+            // A_0 log|xi_m - c| - Re sum_{l>=1} A_l rho^l / l
+            cz<double> pw = rho;
+            double s = 0.0;
+            for (int l = 1; l < P; l++) {
+                s += (a[l].x * pw.x - a[l].y * pw.y) / l;
+                pw = zmul(pw, rho);
+            }
+            L += a[0].x * 0.5 * log(dx * dx + dy * dy) - s;
+        }
+        for (int q = cnear[m]; q < cnear[m + 1]; q++) {
+            const int b = pb[q];
+            for (int i = bg[b] + lane; i < en[b]; i += 32) {
+                const double ex = xi[i].x - xm.x, ey = xi[i].y - xm.y;
+                L += tau[i] * 0.5 * log(ex * ex + ey * ey);
+            }
+        }
+        if (kind[m] == 2)
+            for (int64_t i = lane; i < N; i += 32) {
+                const double ex = xi[i].x - xm.x, ey = xi[i].y - xm.y;
+                L += tau[i] * 0.5 * log(ex * ex + ey * ey);
+            }
+    }
+    L = wsum(L);
+    if (lane == 0) {
+        const double e = kind[m] != 0 ? sums[2] + lam[m] * *bsig - 2.0 * L : sums[2];
+        out[m] = (add ? add[m] : 0.0) + sc * e * (1.0 / (2.0 * LBF_PI));
+    }
+}
+
+// grad_i (E y)_i as a 2-vector (d/dRe xi_i, d/dIm xi_i):
+//   (1/2pi) [ Y 2 xi_i/(1 + |xi_i|^2) - 2 (Re Psi', -Im Psi') ],  Psi'(z) = sum_{m finite} y_m/(z - xi_m),
+// Psi' from the derivative of the leaf's local expansion plus the direct centres.
+__global__ void k_mp_grad(int64_t N, int P, const double2 *__restrict__ xi,
+                          const int32_t *__restrict__ leaf_of, const int32_t *__restrict__ level,
+                          const int32_t *__restrict__ ix, const int32_t *__restrict__ iy, Geo g,
+                          const cz<double> *__restrict__ loc, const int32_t *__restrict__ nptr,
+                          const int32_t *__restrict__ nsrc, const int32_t *__restrict__ glob,
+                          int nglob, const double2 *__restrict__ xc, const double *__restrict__ y,
+                          const double *__restrict__ sums, double2 *__restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = leaf_of[i];
+    const double2 zi = xi[i];
+    double cx, cy, r;
+    centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
+    const cz<double> u{(zi.x - cx) / r, (zi.y - cy) / r};
+    const cz<double> *lb = loc + (int64_t)b * P;
+    cz<double> d{(P - 1) * lb[P - 1].x, (P - 1) * lb[P - 1].y};
+    for (int l = P - 2; l >= 1; l--) d = zfma(d, u, cz<double>{l * lb[l].x, l * lb[l].y});
+    double pr = d.x / r, pi = d.y / r;
+    auto direct = [&](int m) {
+        const double ex = zi.x - xc[m].x, ey = zi.y - xc[m].y;
+        const double s = y[m] / (ex * ex + ey * ey);
+        pr += s * ex;
+        pi -= s * ey;
+    };
+    for (int q = nptr[b]; q < nptr[b + 1]; q++) direct(nsrc[q]);
+    for (int q = 0; q < nglob; q++) direct(glob[q]);
+    const double Y = sums[0], den = 1.0 + zi.x * zi.x + zi.y * zi.y;
+    const double k = 1.0 / (2.0 * LBF_PI);
+    out[i] = make_double2(k * (Y * 2.0 * zi.x / den - 2.0 * pr), k * (Y * 2.0 * zi.y / den + 2.0 * pi));
+}
+
+}  // namespace
+
+// out = add + sc E^T tau (M-vectors; tau sorted, N), FP64.  Uses the plan's q, bsig and
+// the double expansion buffer of the multiplier potential as scratch.
+int lbf_mp_apply_transpose(lbf_plan *pl, const double *tau, double sc, const double *add,
+                           double *out, const int *gate, cudaStream_t s)
+{
+    Border &B = pl->bd;
+    Tree &T = pl->tree;
+    Geo g{T.xmin, T.ymin, T.L};
+    int rc = lbf_multipoles(pl, tau, B.P, B.loc, gate, s);
+    if (rc) return rc;
+    LBF_LAUNCH(k_mp_tsum, 1, 1024, 0, s, pl->N, tau, B.ell, B.sums, gate);
+    LBF_LAUNCH(k_mp_transpose, lbf_cdiv(pl->M, 8), 256, 0, s, pl->M, B.P, g, T.level, T.ix, T.iy,
+               T.begin, T.end, B.cp2l, B.pairs_a, B.cnear, B.pairs_b, B.kind, B.xc, B.lam, pl->N,
+               pl->xi, tau, (const cz<double> *)B.loc, pl->bsig, B.sums, sc, add, out, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// out_i = grad_i (E y)_i (sorted order, N double2), FP64
+int lbf_mp_gradient(lbf_plan *pl, const double *y, double2 *out, cudaStream_t s)
+{
+    Border &B = pl->bd;
+    Tree &T = pl->tree;
+    Geo g{T.xmin, T.ymin, T.L};
+    int M = pl->M;
+    int P = B.P;
+    const int wpb = 4;
+    size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
+    LBF_LAUNCH(k_mp_p2l<double>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M, B.p2l_ptr,
+               B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y, (cz<double> *)B.loc,
+               B.sums, (const int *)nullptr);
+    for (int l = 3; l < T.nlev; l++) {
+        int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
+        if (le <= ls) continue;
+        LBF_LAUNCH(k_mp_l2l<double>, lbf_cdiv(le - ls, 8), 256, l2l_smem<double>(P, 8), s, ls, le,
+                   P, T.parent, T.ix, T.iy, pl->tab_binom, (const cz<double> *)pl->tab_dshift,
+                   (cz<double> *)B.loc, (const int *)nullptr);
+    }
+    LBF_LAUNCH(k_mp_grad, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P, pl->xi, B.leaf_of, T.level,
+               T.ix, T.iy, g, (const cz<double> *)B.loc, B.near_ptr, B.near_src, B.glob,
+               B.nglob_h, B.xc, y, B.sums, out);
+    LBF_CHECK_LAUNCH();
     return LBF_OK;
 }

@@ -30,8 +30,10 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// q = sigma w (double, and a float copy for the inner operator) and beta . sigma
-// (fixed-order two-level reduction: the last block sums the block partials in order).
+// Charges and one scalar for an FMM pass: q = sigma w (w given) or q = (sigma, 0)
+// (w null), in double and/or float, and sum_i beta_i sigma_i (beta given) or
+// sum_i sigma_i (beta null), by a fixed-order two-level reduction (the last block
+// sums the block partials in order).
 __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double2 *__restrict__ w,
                        const double *__restrict__ beta, double2 *__restrict__ q,
                        float2 *__restrict__ q32, double *__restrict__ part,
@@ -44,11 +46,14 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         double s = sigma[i];
-        double2 ww = w[i];
-        double2 qq = make_double2(s * ww.x, s * ww.y);
+        double2 qq = make_double2(s, 0.0);
+        if (w) {
+            double2 ww = w[i];
+            qq = make_double2(s * ww.x, s * ww.y);
+        }
         if (q) q[i] = qq;
         if (q32) q32[i] = make_float2((float)qq.x, (float)qq.y);
-        acc = fma(beta[i], s, acc);
+        acc = beta ? fma(beta[i], s, acc) : acc + s;
     }
     acc = warp_sum(acc);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -72,16 +77,19 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
     }
 }
 
-// Direct O(N^2) Cauchy sum with the same combine (tiled through shared memory).
+// Direct O(N^2) Cauchy sums with the same outputs as the leaf kernel's modes
+// (tiled through shared memory).
+template <int MODE>
 __global__ void k_direct(int64_t N, const double2 *__restrict__ xi, const double2 *__restrict__ q,
                          const double *__restrict__ sigma, const double *__restrict__ dself,
+                         const double2 *__restrict__ w, const double *__restrict__ beta,
                          const double *__restrict__ bsig, double *__restrict__ v, const int *gate)
 {
     if (fmm::gate_closed(gate)) return;
     __shared__ double2 sx[256], sq[256];
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double2 z = i < N ? xi[i] : make_double2(0, 0);
-    double acc = 0.0;
+    double accI = 0.0, ar = 0.0, ai = 0.0;
     for (int64_t base = 0; base < N; base += 256) {
         int64_t j = base + threadIdx.x;
         __syncthreads();
@@ -91,12 +99,30 @@ __global__ void k_direct(int64_t N, const double2 *__restrict__ xi, const double
         for (int m = 0; m < n; m++) {
             if (base + m == i) continue;
             double dr = sx[m].x - z.x, di = sx[m].y - z.y;
-            double num = fma(sq[m].y, dr, -sq[m].x * di);
-            double den = fma(dr, dr, di * di);
-            acc = fma(num, fmm::rcp(den), acc);
+            double2 qq = sq[m];
+            double ir2 = fmm::rcp(fma(dr, dr, di * di));
+            if (MODE == fmm::kLeafForward) {
+                accI = fma(fma(qq.y, dr, -qq.x * di), ir2, accI);
+            } else if (MODE == fmm::kLeafTranspose) {
+                ar = fma(fma(qq.x, dr, qq.y * di), ir2, ar);
+                ai = fma(fma(qq.y, dr, -qq.x * di), ir2, ai);
+            } else {
+                double er = (dr * dr - di * di) * ir2 * ir2, ei = -2 * dr * di * ir2 * ir2;
+                ar = fma(qq.x, er, fma(-qq.y, ei, ar));
+                ai = fma(qq.x, ei, fma(qq.y, er, ai));
+            }
         }
     }
-    if (i < N) v[i] = 2.0 * (acc * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + *bsig);
+    if (i >= N) return;
+    if (MODE == fmm::kLeafForward) {
+        v[i] = 2.0 * (accI * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + *bsig);
+    } else if (MODE == fmm::kLeafTranspose) {
+        double2 ww = w[i];
+        double im = -(ww.x * ai + ww.y * ar);
+        v[i] = 2.0 * (im * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + beta[i] * *bsig);
+    } else {
+        ((double2 *)v)[i] = make_double2(-ar, -ai);
+    }
 }
 
 // u(t) at off-curve targets: (1/2pi) Im sum_j q_j/(xi_j - xi_t) + beta.sigma
@@ -209,7 +235,7 @@ struct FmmArrays {
     const void *binom, *tpow, *dshift;
 };
 
-template <typename R>
+template <typename R, int MODE>
 int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, const int *gate,
               cudaStream_t s)
 {
@@ -236,7 +262,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     // every box's M2L + P2L runs in one launch and the leaf kernel evaluates each
     // ancestor's expansion at the targets instead of shifting them down: float
     // arithmetic is cheap on this GPU, launches are not.
-    const int walk = dbl ? 0 : 1;
+    const int walk = dbl || MODE == fmm::kLeafDeriv ? 0 : 1;
     {
         const int wpb = down_warps<R>(P);
         const size_t smem = down_smem<R>(P, wpb);
@@ -258,10 +284,10 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
             }
         }
     }
-    LBF_LAUNCH_P(kid_leaf, fmm::k_leaf<R>, lbf_cdiv(T.nleaf, fmm::kLeafWarps),
+    LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
                  32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, pl->u32, q, mp, loc,
-                 sigma, pl->dself, pl->bsig, v, gate, T.parent, walk);
+                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, T.parent, walk);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -277,10 +303,14 @@ int lbf_fmm_init_attrs()
     return LBF_OK;
 }
 
-static int prep(lbf_plan *pl, const double *sigma, int prec, const int *gate, cudaStream_t s)
+// charges and the scalar of one pass: forward q = w sigma with beta . sigma;
+// transposed and real-charge passes q = (sigma, 0) with sum sigma
+static int prep(lbf_plan *pl, const double *sigma, int prec, bool weighted, const int *gate,
+                cudaStream_t s)
 {
     int nb = (int)std::min<int64_t>(lbf_cdiv(pl->N, 256), 1024);
-    LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma, pl->w, pl->beta,
+    LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma, weighted ? pl->w : (const double2 *)nullptr,
+               weighted ? pl->beta : (const double *)nullptr,
                prec == LBF_PREC_FP32 ? (double2 *)nullptr : pl->q,
                prec == LBF_PREC_FP32 ? pl->q32 : (float2 *)nullptr, pl->red, pl->red_count,
                pl->bsig, gate);
@@ -288,27 +318,62 @@ static int prep(lbf_plan *pl, const double *sigma, int prec, const int *gate, cu
     return LBF_OK;
 }
 
-int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s,
-                int prec)
+template <int MODE>
+static int apply_mode(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s,
+                      int prec, bool weighted)
 {
     if (prec == LBF_PREC_FP32 && !pl->q32) return LBF_ENOTBUILT;
-    if (pl->opt.matvec == LBF_MATVEC_DIRECT) prec = LBF_PREC_FP64;
-    int rc = prep(pl, sigma, prec, gate, s);
+    if (pl->opt.matvec == LBF_MATVEC_DIRECT || MODE == fmm::kLeafDeriv) prec = LBF_PREC_FP64;
+    int rc = prep(pl, sigma, prec, weighted, gate, s);
     if (rc) return rc;
     int64_t N = pl->N;
     if (pl->opt.matvec == LBF_MATVEC_DIRECT) {
-        LBF_LAUNCH_P(LBF_KERNEL_DIRECT, k_direct, lbf_cdiv(N, 256), 256, 0, s, N, pl->xi, pl->q,
-                     sigma, pl->dself, pl->bsig, v, gate);
+        LBF_LAUNCH_P(LBF_KERNEL_DIRECT, k_direct<MODE>, lbf_cdiv(N, 256), 256, 0, s, N, pl->xi,
+                     pl->q, sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate);
         LBF_CHECK_LAUNCH();
         return LBF_OK;
     }
     if (prec == LBF_PREC_FP32) {
         FmmArrays a{pl->P32, pl->q32, pl->mpole32, pl->local32, pl->tab32_binom, pl->tab32_tpow,
                     pl->tab32_dshift};
-        return fmm_apply<float>(pl, a, sigma, v, gate, s);
+        return fmm_apply<float, MODE>(pl, a, sigma, v, gate, s);
     }
     FmmArrays a{pl->P, pl->q, pl->mpole, pl->local, pl->tab_binom, pl->tab_tpow, pl->tab_dshift};
-    return fmm_apply<double>(pl, a, sigma, v, gate, s);
+    return fmm_apply<double, MODE>(pl, a, sigma, v, gate, s);
+}
+
+int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s,
+                int prec)
+{
+    return apply_mode<fmm::kLeafForward>(pl, sigma, v, gate, s, prec, true);
+}
+
+int lbf_apply_KT(lbf_plan *pl, const double *tau, double *v, const int *gate, cudaStream_t s,
+                 int prec)
+{
+    return apply_mode<fmm::kLeafTranspose>(pl, tau, v, gate, s, prec, false);
+}
+
+int lbf_cauchy_deriv(lbf_plan *pl, const double *x, bool weighted, double2 *out, cudaStream_t s)
+{
+    return apply_mode<fmm::kLeafDeriv>(pl, x, (double *)out, nullptr, s, LBF_PREC_FP64, weighted);
+}
+
+int lbf_multipoles(lbf_plan *pl, const double *x, int P, double2 *mp, const int *gate,
+                   cudaStream_t s)
+{
+    if (P > LBF_MAX_TERMS) return LBF_EINVAL;
+    int rc = prep(pl, x, LBF_PREC_FP64, false, gate, s);
+    if (rc) return rc;
+    Tree &T = pl->tree;
+    BoxGeo g{T.xmin, T.ymin, T.L};
+    const int wpb = 2;
+    LBF_LAUNCH(fmm::k_up<double>, lbf_cdiv(T.nleaf, wpb), 32 * wpb, up_smem<double>(P, wpb), s,
+               T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin, T.end, T.parent, T.child0,
+               T.nchild, g, P, pl->tab_binom, (const cx<double> *)pl->tab_dshift, pl->xi,
+               pl->u32, (const cx<double> *)pl->q, (cx<double> *)mp, pl->upcnt, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
 }
 
 int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
@@ -325,7 +390,7 @@ int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
 int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,
                       const double *t, double *u, cudaStream_t s)
 {
-    int rc = prep(pl, sigma_sorted, LBF_PREC_FP64, nullptr, s);
+    int rc = prep(pl, sigma_sorted, LBF_PREC_FP64, true, nullptr, s);
     if (rc) return rc;
     if (T <= 0) return LBF_OK;
     LBF_LAUNCH(k_evaluate, T, 256, 0, s, pl->N, pl->M, pl->xi, pl->q, pl->bsig, a, pl->centres, T,

@@ -427,15 +427,25 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
 constexpr int kLeafWarps = 4;
 constexpr int kSrcChunk = 256;
 
-// Per leaf: far field (L2P of the leaf's local expansion and M2P from W(b)),
-// near field (P2P over U(b), self excluded) and the combine into v in double:
-//   v_i = 2 [ (1/2pi) c_i + dself_i sigma_i + beta.sigma ].
-// Near-field positions are taken relative to the leaf centre in units of its
-// half-width r, so close nodes cancel before any rounding to R: in double from
-// the node positions, in float from each node's own leaf-local coordinate
-// rescaled by a power of two and shifted by the exact offset between box
-// centres (double positions only where a source box is much coarser).
-template <typename R>
+// What the leaf kernel writes for node i (all with the self pair excluded):
+//   kLeafForward   v_i = 2 [ (1/2pi) Im sum_j q_j/(xi_j - xi_i) + dself_i sigma_i + s ],
+//                  the double-layer rows of Eq. disc_sphere (s = beta.sigma);
+//   kLeafTranspose v_i = 2 [ (1/2pi) Im(w_i Phi(xi_i)) + dself_i sigma_i + beta_i s ],
+//                  Phi(z) = sum_j q_j/(z - xi_j) with real charges q_j = tau_j and
+//                  s = sum_j tau_j: the transposed rows (K^T tau)_i;
+//   kLeafDeriv     Phi'(xi_i) = -sum_j q_j/(xi_i - xi_j)^2 as a double2.
+constexpr int kLeafForward = 0, kLeafTranspose = 1, kLeafDeriv = 2;
+
+// Per leaf: far field (L2P of the leaf's local expansion, or of every ancestor's,
+// and M2P from W(b)), near field (P2P over U(b)), then the output above.  A lane
+// owns one target; the sources of U(b) pass through shared memory in chunks and
+// every lane reads each one (broadcast).  Near-field positions are taken relative
+// to the leaf centre in units of its half-width r, so close nodes cancel before
+// any rounding to R: in double from the node positions, in float from each node's
+// own leaf-local coordinate rescaled by a power of two and shifted by the exact
+// offset between box centres (double positions only where a source box is much
+// coarser).
+template <typename R, int MODE>
 __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
                        const int32_t *__restrict__ iy, const int32_t *__restrict__ bg,
@@ -445,7 +455,8 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const double2 *__restrict__ xi, const float2 *__restrict__ u32,
                        const cx<R> *__restrict__ q, const cx<R> *__restrict__ mp,
                        const cx<R> *__restrict__ loc, const double *__restrict__ sigma,
-                       const double *__restrict__ dself, const double *__restrict__ bsig,
+                       const double *__restrict__ dself, const double2 *__restrict__ w,
+                       const double *__restrict__ beta, const double *__restrict__ bsig,
                        double *__restrict__ v, const int *gate, const int32_t *__restrict__ parent,
                        int walk)
 {
@@ -454,8 +465,6 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
     __shared__ cx<R> sx[kLeafWarps][kSrcChunk];
     __shared__ cx<R> sq[kLeafWarps][kSrcChunk];
     __shared__ int32_t sj[kLeafWarps][kSrcChunk];
-    __shared__ R cn[kLeafWarps][32];
-    __shared__ cx<R> sz[kLeafWarps][32];
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t t = blockIdx.x * (int64_t)kLeafWarps + wid;
     if (t >= nleaf) return;
@@ -466,13 +475,13 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
     const double ir = 1.0 / r;
     const R irr = (R)ir;
     const cx<R> *lb = loc + (int64_t)b * P;
-    double bs = *bsig;
     for (int tb = bg[b]; tb < en[b]; tb += 32) {
-        int nt = min(32, en[b] - tb);
-        int i = tb + lane;
-        R cfar = 0;
-        if (lane < nt) {
-            cx<R> u;  // (z - c)/r
+        const int nt = min(32, en[b] - tb);
+        const int i = tb + lane;
+        const bool act = lane < nt;
+        cx<R> u = mk<R>(0, 0);  // (z - c)/r
+        cx<R> phi = mk<R>(0, 0);  // far field: Phi (or Phi' in kLeafDeriv)
+        if (act) {
             if constexpr (kF32) {
                 float2 uu = u32[i];
                 u = mk<R>(uu.x, uu.y);
@@ -480,9 +489,13 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                 double2 zi = xi[i];
                 u = mk<R>((zi.x - cxd) * ir, (zi.y - cyd) * ir);
             }
-            sz[wid][lane] = u;
-            cx<R> phi = mk<R>(0, 0);
-            if (!walk) {
+            if constexpr (MODE == kLeafDeriv) {
+                // d/dz sum_l b_l ((z - c)/r)^l = (1/r) sum_{l>=1} l b_l u^(l-1)
+                cx<R> d = mk<R>((R)(P - 1) * lb[P - 1].x, (R)(P - 1) * lb[P - 1].y);
+                for (int l = P - 2; l >= 1; l--)
+                    d = cfma(d, u, mk<R>((R)l * lb[l].x, (R)l * lb[l].y));
+                phi = mk<R>(d.x * irr, d.y * irr);
+            } else if (!walk) {
                 phi = lb[P - 1];
                 for (int l = P - 2; l >= 0; l--) phi = cfma(phi, u, lb[l]);
             } else {
@@ -524,35 +537,51 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                     zs = mk<R>((R)((zi.x - sxd) * isd), (R)((zi.y - syd) * isd));
                     isr = (R)isd;
                 }
-                cx<R> rho = crcp(zs);
+                const cx<R> rho = crcp(zs);  // r_s / (z - c_s)
                 const cx<R> *a = mp + (int64_t)s * P;
-                cx<R> ps = a[P - 1];
-                for (int k = P - 2; k >= 0; k--) ps = cfma(ps, rho, a[k]);
-                ps = cmul(ps, rho);
-                phi.x += ps.x * isr;
-                phi.y += ps.y * isr;
+                if constexpr (MODE == kLeafDeriv) {
+                    // -(1/r^2) sum_k (k+1) a_k rho^(k+2)
+                    cx<R> ps = mk<R>((R)P * a[P - 1].x, (R)P * a[P - 1].y);
+                    for (int k = P - 2; k >= 0; k--)
+                        ps = cfma(ps, rho, mk<R>((R)(k + 1) * a[k].x, (R)(k + 1) * a[k].y));
+                    ps = cmul(ps, cmul(rho, rho));
+                    phi.x -= ps.x * isr * isr;
+                    phi.y -= ps.y * isr * isr;
+                } else {
+                    cx<R> ps = a[P - 1];
+                    for (int k = P - 2; k >= 0; k--) ps = cfma(ps, rho, a[k]);
+                    ps = cmul(ps, rho);
+                    phi.x += ps.x * isr;
+                    phi.y += ps.y * isr;
+                }
             }
-            cfar = -phi.y;
         }
-        cn[wid][lane] = 0;
-        __syncwarp();
+        // near field, in units of r: sum over sources of q conj(dz)/|dz|^2 (Im part only
+        // in the forward mode) or q conj(dz)^2/|dz|^4, dz = xi_s - z
+        R accI = 0;
+        cx<R> acc = mk<R>(0, 0);
         int fill = 0;
         auto process = [&]() {
             __syncwarp();
-            for (int tt = 0; tt < nt; tt++) {
-                int ti = tb + tt;
-                cx<R> z = sz[wid][tt];
-                R acc = 0;
-                for (int m = lane; m < fill; m += 32) {
-                    if (sj[wid][m] == ti) continue;
-                    R dr = sx[wid][m].x - z.x, di = sx[wid][m].y - z.y;
-                    cx<R> qq = sq[wid][m];
-                    R num = fm(qq.y, dr, -qq.x * di);
-                    R den = fm(dr, dr, di * di);
-                    acc = fm(num, rcp(den), acc);
+            if (act) {
+                for (int m = 0; m < fill; m++) {
+                    if (sj[wid][m] == i) continue;
+                    const cx<R> zs = sx[wid][m];
+                    const cx<R> qq = sq[wid][m];
+                    const R dr = zs.x - u.x, di = zs.y - u.y;
+                    const R ir2 = rcp(fm(dr, dr, di * di));
+                    if constexpr (MODE == kLeafForward) {
+                        accI = fm(fm(qq.y, dr, -qq.x * di), ir2, accI);
+                    } else if constexpr (MODE == kLeafTranspose) {
+                        acc.x = fm(fm(qq.x, dr, qq.y * di), ir2, acc.x);
+                        acc.y = fm(fm(qq.y, dr, -qq.x * di), ir2, acc.y);
+                    } else {
+                        // q conj(dz)^2 / |dz|^4
+                        const R er = (dr * dr - di * di) * ir2 * ir2, ei = -2 * dr * di * ir2 * ir2;
+                        acc.x = fm(qq.x, er, fm(-qq.y, ei, acc.x));
+                        acc.y = fm(qq.x, ei, fm(qq.y, er, acc.y));
+                    }
                 }
-                acc = wsum(acc);
-                if (lane == tt) cn[wid][tt] += acc;
             }
             __syncwarp();
             fill = 0;
@@ -592,10 +621,22 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             }
         }
         if (fill > 0) process();
-        __syncwarp();
-        if (lane < nt) {
-            double c = (double)cfar + (double)(cn[wid][lane] * irr);
-            v[i] = 2.0 * (c * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + bs);
+        if (act) {
+            if constexpr (MODE == kLeafForward) {
+                double c = (double)(-phi.y) + (double)(accI * irr);
+                v[i] = 2.0 * (c * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + *bsig);
+            } else if constexpr (MODE == kLeafTranspose) {
+                // Phi = far - near sum (the near sum above is sum q/(xi_s - z))
+                const double pr = (double)phi.x - (double)(acc.x * irr);
+                const double pi = (double)phi.y - (double)(acc.y * irr);
+                const double2 ww = w[i];
+                const double im = ww.x * pi + ww.y * pr;
+                v[i] = 2.0 * (im * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + beta[i] * *bsig);
+            } else {
+                const double i2 = (double)irr * (double)irr;
+                ((double2 *)v)[i] = make_double2((double)phi.x - (double)acc.x * i2,
+                                                 (double)phi.y - (double)acc.y * i2);
+            }
         }
         __syncwarp();
     }

@@ -37,7 +37,7 @@ __device__ __forceinline__ void rotate(const Rot &R, double *v)
 __global__ void k_project(int64_t N, int M, const int64_t *__restrict__ ptr,
                           const double *__restrict__ x, const double *__restrict__ dx,
                           const double *__restrict__ d2x, Rot R, double2 *__restrict__ xi_o,
-                          double *__restrict__ x3_o, double2 *__restrict__ w_o,
+                          double2 *__restrict__ w_o,
                           double *__restrict__ d_o, double *__restrict__ b_o,
                           int *__restrict__ status)
 {
@@ -51,9 +51,6 @@ __global__ void k_project(int64_t N, int M, const int64_t *__restrict__ ptr,
     rotate(R, p0);
     rotate(R, p1);
     rotate(R, p2);
-    x3_o[3 * j] = p0[0];
-    x3_o[3 * j + 1] = p0[1];
-    x3_o[3 * j + 2] = p0[2];
     double w = __dsub_rn(1.0, p0[2]);
     if (!(w >= 1e-12)) {
         atomicOr(status, LBF_DEV_POLE);
@@ -75,6 +72,26 @@ __global__ void k_project(int64_t N, int M, const int64_t *__restrict__ ptr,
     // Im(xi''/xi') = Im(xi'' conj(xi'))/|xi'|^2
     d_o[j] = (h / (4.0 * LBF_PI)) * (bi * ar - br * ai) / a2;
     // Im(conj(xi) xi') = xr*ai - xim*ar
+    b_o[j] = -(h / (2.0 * LBF_PI)) * (xr * ai - xim * ar) / (1.0 + xr * xr + xim * xim);
+}
+
+// The same per-node data from planar nodes xi, xi', xi'' (caller's plane)
+__global__ void k_planar(int64_t N, int M, const int64_t *__restrict__ ptr,
+                         const double *__restrict__ xi, const double *__restrict__ dxi,
+                         const double *__restrict__ d2xi, double2 *__restrict__ xi_o,
+                         double2 *__restrict__ w_o, double *__restrict__ d_o,
+                         double *__restrict__ b_o)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    int k = island_of(ptr, M, j);
+    double h = 2.0 * LBF_PI / (double)(ptr[k + 1] - ptr[k]);
+    double xr = xi[2 * j], xim = xi[2 * j + 1];
+    double ar = dxi[2 * j], ai = dxi[2 * j + 1];
+    double br = d2xi[2 * j], bi = d2xi[2 * j + 1];
+    xi_o[j] = make_double2(xr, xim);
+    w_o[j] = make_double2(h * ar, h * ai);
+    d_o[j] = (h / (4.0 * LBF_PI)) * (bi * ar - br * ai) / (ar * ar + ai * ai);
     b_o[j] = -(h / (2.0 * LBF_PI)) * (xr * ai - xim * ar) / (1.0 + xr * xr + xim * xim);
 }
 
@@ -108,58 +125,185 @@ __global__ void k_rotate_centres(int M, const double *__restrict__ c, Rot R, dou
 
 // Gauss-Jordan step k on [S | I] (M x 2M, row-major): partial pivoting on column
 // k, swap, scale the pivot row.  One block.
-__global__ void k_gj_pivot(int M, int k, double *__restrict__ G, int *__restrict__ status)
+// ---- inverse of the Schur complement ---------------------------------------------------
+//
+// In-place Gauss-Jordan elimination with partial pivoting (row interchanges), all
+// M steps in one cooperative launch: per step k every block reduces the partial
+// column maxima to the pivot row p, the grid saves the scaled pivot row, the old
+// row k and the multipliers (column k after the interchange), and after a grid
+// barrier every element is updated once:
+//   A_kj <- A_pj / A_pk,  A_ik <- -A_ik / A_pk,  A_ij <- A_ij - A_ik A_pj / A_pk,
+// while the same pass forms the partial maxima of column k + 1.  The interchanges
+// are undone at the end by swapping columns k and p for k = M-1, ..., 0.
+//
+// The grid barrier is a counter and a generation word; every block is resident
+// (cooperative launch), and each wait gives up after kBarrierSpins polls, setting
+// status bit LBF_DEV_TIMEOUT, so the kernel always ends.
+
+constexpr unsigned kBarrierSpins = 1u << 22;
+constexpr int kGjThreads = 256;
+constexpr int kGjMaxBlocks = 2048;
+
+struct GridBarrier {
+    unsigned count, gen;
+};
+
+__device__ bool grid_barrier(GridBarrier *bar, unsigned nb, int *status)
 {
-    __shared__ double sval[1024];
-    __shared__ int sidx[1024];
-    int t = threadIdx.x;
-    double best = -1.0;
-    int bi = M;
-    for (int i = k + t; i < M; i += blockDim.x) {
-        double a = fabs(G[(int64_t)i * 2 * M + k]);
-        if (a > best || (a == best && i < bi)) { best = a; bi = i; }
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = &bar->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == nb - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*vgen == g) {
+                if (++it > kBarrierSpins) {
+                    atomicOr(status, LBF_DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)status & LBF_DEV_TIMEOUT) ok = 0;
     }
-    sval[t] = best;
-    sidx[t] = bi;
+    __syncthreads();
+    return ok != 0;
+}
+
+// block-wide (max |value|, smallest index) reduction; result valid in every thread
+__device__ void block_argmax(double &v, int &idx, double *sv, int *si)
+{
+    const int t = threadIdx.x;
+    sv[t] = v;
+    si[t] = idx;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (t < o) {
-            double a = sval[t + o];
-            int i = sidx[t + o];
-            if (a > sval[t] || (a == sval[t] && i < sidx[t])) { sval[t] = a; sidx[t] = i; }
+            double a = sv[t + o];
+            int i = si[t + o];
+            if (a > sv[t] || (a == sv[t] && i < si[t])) {
+                sv[t] = a;
+                si[t] = i;
+            }
         }
         __syncthreads();
     }
-    int p = sidx[0];
-    double piv = G[(int64_t)p * 2 * M + k];
-    if (t == 0 && !(fabs(piv) > 0.0)) atomicOr(status, 4);
-    double inv = 1.0 / piv;
-    for (int j = t; j < 2 * M; j += blockDim.x) {
-        double a = G[(int64_t)k * 2 * M + j];
-        double b = G[(int64_t)p * 2 * M + j];
-        if (p != k) G[(int64_t)p * 2 * M + j] = a;
-        G[(int64_t)k * 2 * M + j] = b * inv;
+    v = sv[0];
+    idx = si[0];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGjThreads)
+k_gj_coop(int M, double *A, double *rowk, double *oldk, double *colk, double *pval, int *pidx,
+          int *pivrow, GridBarrier *bar, int *status)
+{
+    __shared__ double sv[kGjThreads];
+    __shared__ int si[kGjThreads];
+    const unsigned nb = gridDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)nb * blockDim.x;
+    const int64_t MM = (int64_t)M * M;
+    const int i0 = (int)(tid / M), j0 = (int)(tid % M);
+    const int di = (int)(nthr / M), dj = (int)(nthr % M);
+    // partial maxima of column 0
+    {
+        double best = -1.0;
+        int bi = M;
+        for (int64_t i = tid; i < M; i += nthr) {
+            double a = fabs(__ldcg(&A[i * M]));
+            if (a > best) { best = a; bi = (int)i; }
+        }
+        block_argmax(best, bi, sv, si);
+        if (threadIdx.x == 0) { pval[blockIdx.x] = best; pidx[blockIdx.x] = bi; }
+    }
+    if (!grid_barrier(bar, nb, status)) return;
+    for (int k = 0; k < M; k++) {
+        // pivot row: every block reduces the partial maxima the same way
+        double best = -1.0;
+        int p = M;
+        for (unsigned q = threadIdx.x; q < nb; q += blockDim.x) {
+            double a = __ldcg(&pval[q]);
+            int i = __ldcg(&pidx[q]);
+            if (a > best || (a == best && i < p)) { best = a; p = i; }
+        }
+        block_argmax(best, p, sv, si);
+        if (!(best > 0.0) || p >= M) {  // every block sees the same value: all stop here
+            if (tid == 0) atomicOr(status, 4);
+            return;
+        }
+        const double piv = __ldcg(&A[(int64_t)p * M + k]);
+        const double ipiv = 1.0 / piv;
+        if (tid == 0) pivrow[k] = p;
+        for (int64_t j = tid; j < M; j += nthr) {
+            const double apj = __ldcg(&A[(int64_t)p * M + j]);
+            const double akj = __ldcg(&A[(int64_t)k * M + j]);
+            rowk[j] = (j == k) ? ipiv : apj * ipiv;
+            oldk[j] = akj;
+            // multiplier of row j after the interchange of rows k and p
+            colk[j] = (j == k) ? piv : (j == p ? __ldcg(&A[(int64_t)k * M + k])
+                                               : __ldcg(&A[j * M + k]));
+        }
+        if (!grid_barrier(bar, nb, status)) return;
+        double nbest = -1.0;
+        int ni = M;
+        int i = i0, j = j0;  // (i, j) of element e, advanced without dividing
+        for (int64_t e = tid; e < MM; e += nthr, i += di, j += dj) {
+            if (j >= M) { j -= M; i++; }
+            double val;
+            if (i == k) {
+                val = __ldcg(&rowk[j]);
+            } else {
+                const double f = __ldcg(&colk[i]);
+                if (j == k) {
+                    val = -f * __ldcg(&rowk[k]);
+                } else {
+                    const double a = (i == p) ? __ldcg(&oldk[j]) : __ldcg(&A[e]);
+                    val = fma(-f, __ldcg(&rowk[j]), a);
+                }
+            }
+            A[e] = val;
+            if (j == k + 1 && i > k) {
+                double av = fabs(val);
+                if (av > nbest || (av == nbest && i < ni)) { nbest = av; ni = i; }
+            }
+        }
+        block_argmax(nbest, ni, sv, si);
+        if (threadIdx.x == 0) { pval[blockIdx.x] = nbest; pidx[blockIdx.x] = ni; }
+        if (!grid_barrier(bar, nb, status)) return;
     }
 }
 
-__global__ void k_gj_elim(int M, int k, double *__restrict__ G)
+__global__ void k_gj_init(int M, int *__restrict__ pivrow)
 {
-    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t ncol = 2 * M - (k + 1);
-    if (id >= (int64_t)M * ncol) return;
-    int i = (int)(id / ncol);
-    int j = k + 1 + (int)(id % ncol);
-    if (i == k) return;
-    double f = G[(int64_t)i * 2 * M + k];
-    G[(int64_t)i * 2 * M + j] -= f * G[(int64_t)k * 2 * M + j];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < M) pivrow[k] = k;
 }
 
-__global__ void k_copy_inverse(int M, const double *__restrict__ G, double *__restrict__ Sinv)
+// undo the row interchanges: swap columns k and pivrow[k] for k = M-1, ..., 0 (thread per
+// row).  pivrow starts as the identity, so steps an early stop (a singular pivot or a
+// barrier that gave up) never reached swap nothing.
+__global__ void k_gj_unscramble(int M, double *__restrict__ A, const int *__restrict__ pivrow)
 {
-    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (id >= (int64_t)M * M) return;
-    int i = (int)(id / M), j = (int)(id % M);
-    Sinv[id] = G[(int64_t)i * 2 * M + M + j];
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double *row = A + i * M;
+    for (int k = M - 1; k >= 0; k--) {
+        int p = pivrow[k];
+        if (p != k && p >= 0 && p < M) {
+            double t = row[k];
+            row[k] = row[p];
+            row[p] = t;
+        }
+    }
 }
 
 __global__ void k_geometry_out(int64_t N, const int32_t *__restrict__ rank,
@@ -190,13 +334,17 @@ Rot make_rot(const lbf_plan *pl)
 }  // namespace
 
 int lbf_geometry_build(lbf_plan *pl, const double *x, const double *dx, const double *d2x,
-                       const double *centres, cudaStream_t s, double2 *xi_o, double *x3_o,
+                       const double *centres, int planar, cudaStream_t s, double2 *xi_o,
                        double2 *w_o, double *d_o, double *b_o)
 {
     int64_t N = pl->N;
     Rot R = make_rot(pl);
-    LBF_LAUNCH(k_project, lbf_cdiv(N, 256), 256, 0, s, N, pl->M, pl->island_ptr, x, dx, d2x, R,
-               xi_o, x3_o, w_o, d_o, b_o, pl->dev_status);
+    if (planar)
+        LBF_LAUNCH(k_planar, lbf_cdiv(N, 256), 256, 0, s, N, pl->M, pl->island_ptr, x, dx, d2x,
+                   xi_o, w_o, d_o, b_o);
+    else
+        LBF_LAUNCH(k_project, lbf_cdiv(N, 256), 256, 0, s, N, pl->M, pl->island_ptr, x, dx, d2x,
+                   R, xi_o, w_o, d_o, b_o, pl->dev_status);
     LBF_CHECK_LAUNCH();
     LBF_LAUNCH(k_rotate_centres, lbf_cdiv(pl->M, 128), 128, 0, s, pl->M, centres, R, pl->centres);
     LBF_CHECK_LAUNCH();
@@ -214,24 +362,43 @@ int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const
 }
 
 // S = D - F E from the island expansions of the multiplier potential, then its
-// inverse by Gauss-Jordan elimination with partial pivoting.
+// inverse in place by Gauss-Jordan elimination with partial pivoting.
+size_t lbf_gj_scratch_doubles(int M) { return 3 * (size_t)M + 2 * kGjMaxBlocks + (size_t)M + 64; }
+
 int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
-                     int32_t *work, int64_t work_len)
+                     int32_t *work, int64_t work_len, const SortBufs &sb)
 {
     int M = pl->M;
-    double *G = scratch;  // M x 2M
+    double *S = pl->Sinv;
     lbf_prof_mark(LBF_STAGE_BORDER, 1, s);
-    int rc = lbf_mp_build(pl, s, xi_o, G, work, work_len);
+    int rc = lbf_mp_build(pl, s, xi_o, S, work, work_len, sb);
     lbf_prof_mark(LBF_STAGE_BORDER, 0, s);
     if (rc) return rc;
     lbf_prof_mark(LBF_STAGE_INVERSE, 1, s);
-    for (int k = 0; k < M; k++) {
-        LBF_LAUNCH(k_gj_pivot, 1, 1024, 0, s, M, k, G, pl->dev_status);
-        int64_t work = (int64_t)M * (2 * M - (k + 1));
-        if (work > 0) LBF_LAUNCH(k_gj_elim, lbf_cdiv(work, 256), 256, 0, s, M, k, G);
-    }
-    LBF_CHECK_LAUNCH();
-    LBF_LAUNCH(k_copy_inverse, lbf_cdiv((int64_t)M * M, 256), 256, 0, s, M, G, pl->Sinv);
+    int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+    LBF_CUDA(cudaGetDevice(&dev));
+    LBF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    LBF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    LBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, kGjThreads, 0));
+    if (!coop || per_sm < 1) return LBF_ECUDA;
+    // two blocks per SM: enough to keep every SM's double pipe busy, few enough that the
+    // barrier's single counter stays cheap
+    int64_t want = lbf_cdiv((int64_t)M * M, (int64_t)kGjThreads);
+    int nb = (int)std::min<int64_t>(std::min<int64_t>((int64_t)nsm * std::min(per_sm, 2), kGjMaxBlocks),
+                                    std::max<int64_t>(want, 1));
+    double *rowk = scratch, *oldk = scratch + M, *colk = scratch + 2 * M;
+    double *pval = scratch + 3 * M;
+    int *pidx = (int *)(pval + kGjMaxBlocks);
+    int *pivrow = pidx + kGjMaxBlocks;
+    GridBarrier *bar = (GridBarrier *)(pivrow + M + (M & 1));
+    LBF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+    LBF_LAUNCH(k_gj_init, lbf_cdiv(M, 256), 256, 0, s, M, pivrow);
+    int *status = pl->dev_status;
+    void *args[] = {&M, &S, &rowk, &oldk, &colk, &pval, &pidx, &pivrow, &bar, &status};
+    LBF_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(nb), dim3(kGjThreads), args,
+                                         0, s));
+    g_lbf_launches.fetch_add(1, std::memory_order_relaxed);
+    LBF_LAUNCH(k_gj_unscramble, lbf_cdiv(M, 128), 128, 0, s, M, S, pivrow);
     LBF_CHECK_LAUNCH();
     lbf_prof_mark(LBF_STAGE_INVERSE, 0, s);
     return LBF_OK;

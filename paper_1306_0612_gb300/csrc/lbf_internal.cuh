@@ -95,6 +95,7 @@ struct Border {
     int32_t *pairs_a = nullptr, *pairs_b = nullptr;  // staging of (box, centre) pairs
     int32_t *p2l_ptr = nullptr, *p2l_src = nullptr;  // P2L centres per box (CSR)
     int32_t *near_ptr = nullptr, *near_src = nullptr;  // direct centres per leaf (CSR)
+    int32_t *cp2l = nullptr, *cnear = nullptr;  // per centre: offsets into pairs_a / pairs_b (M + 1)
     double2 *loc = nullptr;          // local expansions of the log potential, box x P
     float2 *loc32 = nullptr;         // box x P32
     double2 *zc = nullptr;           // island node means
@@ -157,6 +158,7 @@ struct lbf_plan {
     int64_t ldv = 0;  // stride between basis vectors
     int mdot_blocks = 0;
     char *region = nullptr;      // GMRES basis, or plan-creation temporaries
+    size_t region_bytes = 0;
     int *dev_status = nullptr;
     int *host_status = nullptr;  // pinned
     cudaEvent_t ev[2] = {nullptr, nullptr};  // GMRES chunk markers (no device memory)
@@ -166,19 +168,30 @@ struct lbf_plan {
 // ---- layout ------------------------------------------------------------------
 void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &opt, int64_t box_cap);
 
+struct SortBufs {  // plan-time scratch of a pair sort (capacity max(N, pair capacity))
+    uint64_t *key, *key_alt;
+    int32_t *val_alt;
+};
+
 // ---- geometry (lbf_geometry.cu) ----------------------------------------------
 int lbf_geometry_build(lbf_plan *pl, const double *x, const double *dx, const double *d2x,
-                       const double *centres, cudaStream_t s, double2 *xi_o, double *x3_o,
+                       const double *centres, int planar, cudaStream_t s, double2 *xi_o,
                        double2 *w_o, double *d_o, double *b_o);
 int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const double2 *w_o,
                         const double *d_o, const double *b_o);
 int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
-                     int32_t *work, int64_t work_len);
+                     int32_t *work, int64_t work_len, const SortBufs &sb);
+size_t lbf_gj_scratch_doubles(int M);  // scratch of lbf_border_build
 // ---- multiplier potential (lbf_border.cu) -------------------------------------
 int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
-                 int64_t work_len);
+                 int64_t work_len, const SortBufs &sb);
 int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v, double sc,
                  double *out, const int *gate, cudaStream_t s, int prec);
+// out = add + sc E^T tau (M-vectors, add nullable; tau sorted), FP64
+int lbf_mp_apply_transpose(lbf_plan *pl, const double *tau, double sc, const double *add,
+                           double *out, const int *gate, cudaStream_t s);
+// out_i = gradient of (E y)_i with respect to (Re xi_i, Im xi_i), sorted order, FP64
+int lbf_mp_gradient(lbf_plan *pl, const double *y, double2 *out, cudaStream_t s);
 int lbf_geometry_out_impl(const lbf_plan *pl, double *xi, double *normal, double *weight,
                           double *arc, cudaStream_t s);
 
@@ -190,6 +203,10 @@ int lbf_lists_build(lbf_plan *pl, cudaStream_t s, int32_t *scratch, int64_t scra
                     int64_t *box_needed);
 int lbf_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *scratch, int64_t scratch_len,
                  cudaStream_t s);  // exclusive scan, out may alias in
+// stable LSD radix sort of (keys, vals) on the low `bits` bits of the keys; the
+// result is in keys/vals, the *_alt arrays are scratch of the same length
+int lbf_radix_sort(uint64_t *keys, uint64_t *keys_alt, int32_t *vals, int32_t *vals_alt, int64_t n,
+                   int bits, int32_t *scratch, int64_t scratch_len, cudaStream_t s);
 
 // ---- FMM / direct operator (lbf_fmm.cu) -----------------------------------------
 // v = 2 [ (1/2pi) Im sum_{j!=i} q_j/(xi_j - xi_i) + d_i sigma_i + beta.sigma ]   (sorted order)
@@ -198,6 +215,16 @@ int lbf_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *scratch, i
 int lbf_apply_K(lbf_plan *pl, const double *sigma, double *v, const int *gate, cudaStream_t s,
                 int prec);
 int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s);  // plan time, after the tree and the gather
+// v = 2 [ (1/2pi) Im(w_i sum_{j!=i} tau_j/(xi_i - xi_j)) + d_i tau_i + beta_i sum_j tau_j ]:
+// the transposed rows (K^T tau)_i, doubled (sorted order)
+int lbf_apply_KT(lbf_plan *pl, const double *tau, double *v, const int *gate, cudaStream_t s,
+                 int prec);
+// out_i = Phi'(xi_i) = -sum_{j!=i} q_j/(xi_i - xi_j)^2, q = w x (weighted) or (x, 0), FP64
+int lbf_cauchy_deriv(lbf_plan *pl, const double *x, bool weighted, double2 *out, cudaStream_t s);
+// scaled multipoles a_k = sum_j x_j ((xi_j - c)/r)^k, k < P, of real charges x on every
+// box (P2M + M2M); also writes q = (x, 0) and *bsig = sum_j x_j
+int lbf_multipoles(lbf_plan *pl, const double *x, int P, double2 *mp, const int *gate,
+                   cudaStream_t s);
 int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,
                       const double *t, double *u, cudaStream_t s);
 int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p,
@@ -207,9 +234,16 @@ int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p,
 int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, const int *gate,
                         cudaStream_t s, int prec = LBF_PREC_FP64);
 int lbf_precondition_rhs(lbf_plan *pl, const double *g2_sorted, double *out, cudaStream_t s);
+int lbf_precondition_rhs_t(lbf_plan *pl, const double *r_sorted, double *out, cudaStream_t s);
 int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
-                   int *iters, double *rel_res, cudaStream_t s);
+                   int *iters, double *rel_res, cudaStream_t s, int transpose);
 int lbf_dot(lbf_plan *pl, const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
+// ---- adjoint (lbf_adjoint.cu) ---------------------------------------------------------
+int lbf_evaluate_transpose_impl(lbf_plan *pl, int64_t T, const double *t, const double *ub,
+                                double *sbar, double *abar, cudaStream_t s);
+int lbf_gradient_nodes_impl(lbf_plan *pl, const double *sigma, const double *a, const double *lam,
+                            int64_t T, const double *t, const double *ub, double *grad,
+                            cudaStream_t s);
 int lbf_permute_in(lbf_plan *pl, const double *in_caller, double *out_sorted, int with_a,
                    cudaStream_t s);
 int lbf_permute_out(lbf_plan *pl, const double *in_sorted, double *out_caller, int with_a,

@@ -111,6 +111,46 @@ __global__ void k_arows(int M, int mode, const double *__restrict__ a, const dou
     }
 }
 
+// out_i = x_i + sc mu_{k-1} for the nodes i of island k >= 1 (F^T mu, Eq. disc_constr
+// transposed), out_i = x_i on island 0; thread per caller index, sorted outputs
+__global__ void k_island_scatter(int64_t N, int M, const int64_t *__restrict__ ptr,
+                                 const int32_t *__restrict__ rank, const double *__restrict__ x,
+                                 const double *__restrict__ mu, double sc, double *__restrict__ out,
+                                 const int *gate)
+{
+    if (gate_closed(gate)) return;
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    int lo = 0, hi = M - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ptr[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    const int i = rank[j];
+    out[i] = x[i] + (lo >= 1 ? sc * mu[lo - 1] : 0.0);
+}
+
+// y = alpha S^-T f (thread per output, coalesced over the rows of S^-1)
+__global__ void k_small_gemv_t(int M, const double *__restrict__ A, const double *__restrict__ f,
+                               double alpha, double *__restrict__ y, const int *gate)
+{
+    if (gate_closed(gate)) return;
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    double s = 0.0;
+    for (int m = 0; m < M; m++) s = fma(A[(int64_t)m * M + r], f[m], s);
+    y[r] = alpha * s;
+}
+
+// out_m += c_{M-1} (D^T c: D is the row of ones of Eq. sum_ak, in row M-1)
+__global__ void k_add_last(int M, const double *__restrict__ c, double *__restrict__ out,
+                           const int *gate)
+{
+    if (gate_closed(gate)) return;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) out[m] += c[M - 1];
+}
+
 // ---- GMRES kernels --------------------------------------------------------------------
 
 // Partial dot products of w with V[0..nv) over one block's row chunk; the last block
@@ -411,9 +451,68 @@ static int small_gemv(lbf_plan *pl, const double *f, double alpha, double *y, co
     return LBF_OK;
 }
 
+static int island_scatter(lbf_plan *pl, const double *x, const double *mu, double sc, double *out,
+                          const int *gate, cudaStream_t s)
+{
+    LBF_LAUNCH(k_island_scatter, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, pl->M, pl->island_ptr,
+               pl->rank, x, mu, sc, out, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+static int small_gemv_t(lbf_plan *pl, const double *f, double alpha, double *y, const int *gate,
+                        cudaStream_t s)
+{
+    LBF_LAUNCH(k_small_gemv_t, lbf_cdiv(pl->M, 128), 128, 0, s, pl->M, pl->Sinv, f, alpha, y, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// Transposed operators (sorted order), in = [tau; mu]:
+//   K_ONLY:         tau + 2 K^T tau
+//   FULL:           A^T in = [tau + 2 K^T tau + F^T mu ; E^T tau + D^T mu]
+//   PRECONDITIONED: P^-T A^T in = in + [v - F^T y ; y],  v = 2 K^T tau,  y = -S^-T E^T v
+// (A^T = P^T + [[2 K^T, 0], [0, 0]], P^T = [[I, F^T], [E^T, D^T]], Sec. 5, Eq. matrix_eqns_c)
+static int apply_op_transposed(lbf_plan *pl, int op, const double *in, double *out,
+                               const int *gate, cudaStream_t s, int prec)
+{
+    int64_t N = pl->N;
+    int M = pl->M;
+    int rc = lbf_apply_KT(pl, in, pl->v, gate, s, prec);
+    if (rc) return rc;
+    LBF_LAUNCH(k_add, lbf_cdiv(N, 256), 256, 0, s, N, in, pl->v, out, gate);
+    LBF_CHECK_LAUNCH();
+    if (op == LBF_OP_K_ONLY) return LBF_OK;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    if (op == LBF_OP_FULL) {
+        if ((rc = island_scatter(pl, out, in + N, 1.0, out, gate, s))) return rc;
+        if ((rc = lbf_mp_apply_transpose(pl, in, 1.0, nullptr, out + N, gate, s))) return rc;
+        LBF_LAUNCH(k_add_last, lbf_cdiv(M, 128), 128, 0, s, M, in + N, out + N, gate);
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    }
+    if ((rc = lbf_mp_apply_transpose(pl, pl->v, 1.0, nullptr, pl->fvec, gate, s))) return rc;
+    if ((rc = small_gemv_t(pl, pl->fvec, -1.0, pl->yvec, gate, s))) return rc;
+    if ((rc = island_scatter(pl, out, pl->yvec, -1.0, out, gate, s))) return rc;
+    LBF_LAUNCH(k_add, lbf_cdiv(M, 128), 128, 0, s, M, in + N, pl->yvec, out + N, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// out = P^-T r:  z_a = S^-T (r_a - E^T r_sigma),  z_sigma = r_sigma - F^T z_a
+int lbf_precondition_rhs_t(lbf_plan *pl, const double *r_sorted, double *out, cudaStream_t s)
+{
+    int64_t N = pl->N;
+    int rc;
+    if ((rc = lbf_mp_apply_transpose(pl, r_sorted, -1.0, r_sorted + N, pl->fvec, nullptr, s))) return rc;
+    if ((rc = small_gemv_t(pl, pl->fvec, 1.0, out + N, nullptr, s))) return rc;
+    return island_scatter(pl, r_sorted, out + N, -1.0, out, nullptr, s);
+}
+
 int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, const int *gate,
                         cudaStream_t s, int prec)
 {
+    if (op & LBF_OP_TRANSPOSE) return apply_op_transposed(pl, op & ~LBF_OP_TRANSPOSE, in, out, gate, s, prec);
     int64_t N = pl->N;
     int M = pl->M;
     int rc = lbf_apply_K(pl, in, pl->v, gate, s, prec);
@@ -461,7 +560,7 @@ static int read_state(lbf_plan *pl, GmresState *h, cudaStream_t s)
 // Restarted GMRES on P^-1 A x = b (sorted order, n unknowns) from x (x_given) or
 // from 0, with the operator in precision prec, stopping at ||b - P^-1 A x|| <=
 // tol * (*bnorm_dev).  Counts operator applications in pl->stats.
-static int gmres_core(lbf_plan *pl, const double *b, const double *bnorm_dev, double *x,
+static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnorm_dev, double *x,
                       bool x_given, double tol, int maxit, int prec, cudaStream_t s,
                       GmresState *out)
 {
@@ -479,7 +578,7 @@ static int gmres_core(lbf_plan *pl, const double *b, const double *bnorm_dev, do
     LBF_CHECK_LAUNCH();
     const double *Ax = nullptr;
     if (x_given) {
-        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s, prec))) return rc;
+        if ((rc = lbf_apply_op_sorted(pl, opc, x, w, nullptr, s, prec))) return rc;
         (*applies)++;
         Ax = w;
     } else {
@@ -512,7 +611,7 @@ static int gmres_core(lbf_plan *pl, const double *b, const double *bnorm_dev, do
             for (int k = k0; k < k1; k++) {
                 // w = P^-1 A v_j: within a cycle the device's j equals the host's k
                 const double *vj = V + (int64_t)k * ldv;
-                if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, vj, w, &pl->gs->go, s, prec))) return rc;
+                if ((rc = lbf_apply_op_sorted(pl, opc, vj, w, &pl->gs->go, s, prec))) return rc;
                 for (int mode = 0; mode < 3; mode++)
                     LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w,
                                  pl->gpart, count, hbuf, pl->H, cs, sn, gv, pl->gs, mode);
@@ -531,7 +630,7 @@ static int gmres_core(lbf_plan *pl, const double *b, const double *bnorm_dev, do
         if ((rc = read_state(pl, &hs, s))) return rc;
         if (hs.converged || hs.it >= hs.maxit) break;
         // restart from the true preconditioned residual
-        if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, w, nullptr, s, prec))) return rc;
+        if ((rc = lbf_apply_op_sorted(pl, opc, x, w, nullptr, s, prec))) return rc;
         (*applies)++;
         LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0, bnorm_dev);
         LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
@@ -544,20 +643,30 @@ static int gmres_core(lbf_plan *pl, const double *b, const double *bnorm_dev, do
     return LBF_OK;
 }
 
+// Forward (transpose == 0): A [sigma; a] = [2 g; 0] from g (N, caller order).
+// Adjoint (transpose == 1): A^T lam = r from r = g (N + M, caller order), lam into
+// sigma (N + M, caller order), a unused.  Left preconditioning by P (P^T).
 int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
-                   int *iters, double *rel_res, cudaStream_t s)
+                   int *iters, double *rel_res, cudaStream_t s, int transpose)
 {
     if (!pl->opt.border) return LBF_ENOTBUILT;
     int64_t N = pl->N, n = pl->n;
     int rc;
     double *b = pl->gb, *x = pl->gx;
+    const int opc = LBF_OP_PRECONDITIONED | (transpose ? LBF_OP_TRANSPOSE : 0);
     for (auto &v : pl->stats) v = 0;
-    // b = P^-1 [2 g; 0] in sorted order (tin holds the permuted data)
-    if ((rc = lbf_permute_in(pl, g, pl->tin, 0, s))) return rc;
-    // the doubled right-hand side 2 g of Eq. disc_sphere
-    LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, pl->tin);
-    LBF_CHECK_LAUNCH();
-    if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
+    if (transpose) {
+        // b = P^-T r
+        if ((rc = lbf_permute_in(pl, g, pl->tin, 1, s))) return rc;
+        if ((rc = lbf_precondition_rhs_t(pl, pl->tin, b, s))) return rc;
+    } else {
+        // b = P^-1 [2 g; 0] in sorted order (tin holds the permuted data), with the
+        // doubled right-hand side 2 g of Eq. disc_sphere
+        if ((rc = lbf_permute_in(pl, g, pl->tin, 0, s))) return rc;
+        LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, pl->tin);
+        LBF_CHECK_LAUNCH();
+        if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
+    }
     double *bn = pl->bsig + 1, *rn = pl->bsig + 2;
     LBF_LAUNCH(k_norm2, 1, 1024, 0, s, n, b, bn);
     LBF_CHECK_LAUNCH();
@@ -567,7 +676,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
     double rel = 0.0;
     int its = 0;
     if (pl->opt.precision == LBF_PRECISION_FP64 || !pl->q32) {
-        if ((rc = gmres_core(pl, b, bn, x, x0 != nullptr, pl->opt.tol, pl->opt.maxit, LBF_PREC_FP64, s,
+        if ((rc = gmres_core(pl, opc, b, bn, x, x0 != nullptr, pl->opt.tol, pl->opt.maxit, LBF_PREC_FP64, s,
                              &hs)))
             return rc;
         converged = hs.converged;
@@ -585,7 +694,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
             if (k == 0 && !x0) {
                 LBF_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             } else {
-                if ((rc = lbf_apply_op_sorted(pl, LBF_OP_PRECONDITIONED, x, pl->gw, nullptr, s,
+                if ((rc = lbf_apply_op_sorted(pl, opc, x, pl->gw, nullptr, s,
                                               LBF_PREC_FP64)))
                     return rc;
                 pl->stats[1]++;
@@ -600,7 +709,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
             if (rel <= pl->opt.tol) { converged = true; break; }
             if (k >= pl->opt.max_refine || its >= pl->opt.maxit) break;
             pl->stats[3]++;
-            if ((rc = gmres_core(pl, r, rn, d, false, pl->opt.inner_tol, pl->opt.maxit - its,
+            if ((rc = gmres_core(pl, opc, r, rn, d, false, pl->opt.inner_tol, pl->opt.maxit - its,
                                  LBF_PREC_FP32, s, &hs)))
                 return rc;
             its += hs.it;
@@ -609,9 +718,11 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         }
     }
     // outputs in the caller's order
-    LBF_LAUNCH(k_permute_out, lbf_cdiv(N, 256), 256, 0, s, N, pl->M, pl->perm, x, sigma, 0);
+    LBF_LAUNCH(k_permute_out, lbf_cdiv(transpose ? n : N, 256), 256, 0, s, N, pl->M, pl->perm, x,
+               sigma, transpose);
     LBF_CHECK_LAUNCH();
-    if (a) LBF_CUDA(cudaMemcpyAsync(a, x + N, sizeof(double) * pl->M, cudaMemcpyDeviceToDevice, s));
+    if (a && !transpose)
+        LBF_CUDA(cudaMemcpyAsync(a, x + N, sizeof(double) * pl->M, cudaMemcpyDeviceToDevice, s));
     LBF_CUDA(cudaStreamSynchronize(s));
     if (iters) *iters = its;
     if (rel_res) *rel_res = rel;

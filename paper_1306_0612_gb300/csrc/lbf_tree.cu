@@ -451,6 +451,37 @@ static int read_i32(const int32_t *d, int32_t *h, cudaStream_t s)
     return LBF_OK;
 }
 
+int lbf_radix_sort(uint64_t *keys, uint64_t *keys_alt, int32_t *vals, int32_t *vals_alt, int64_t n,
+                   int bits, int32_t *scratch, int64_t scratch_len, cudaStream_t s)
+{
+    if (n <= 0) return LBF_OK;
+    int64_t nunits = lbf_cdiv(n, kUnit);
+    int32_t *hist = scratch;
+    int32_t *sc = scratch + 256 * nunits;
+    int64_t sc_len = scratch_len - 256 * nunits;
+    if (sc_len < 0) return LBF_EWORKSPACE;
+    int passes = (int)lbf_cdiv(bits, 8);
+    uint64_t *ka = keys, *kb = keys_alt;
+    int32_t *va = vals, *vb = vals_alt;
+    for (int ps = 0; ps < passes; ps++) {
+        int shift = 8 * ps;
+        LBF_LAUNCH(k_rs_hist, lbf_cdiv(nunits, 8), 256, 0, s, ka, n, shift, hist, nunits);
+        LBF_CHECK_LAUNCH();
+        int rc = lbf_scan_i32(hist, hist, 256 * nunits, sc, sc_len, s);
+        if (rc) return rc;
+        LBF_LAUNCH(k_rs_scatter, lbf_cdiv(nunits, 8), 256, 0, s, ka, va, kb, vb, n, shift, hist,
+                   nunits);
+        LBF_CHECK_LAUNCH();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        LBF_CUDA(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        LBF_CUDA(cudaMemcpyAsync(vals, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return LBF_OK;
+}
+
 int lbf_tree_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, uint64_t *keys,
                    uint64_t *keys_alt, int32_t *perm_alt, int32_t *scratch, int64_t scratch_len,
                    int64_t *box_needed)
@@ -476,30 +507,8 @@ int lbf_tree_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, uint64_t *
     T.L = hb[2];
 
     // radix sort (keys, perm)
-    int64_t nunits = lbf_cdiv(N, kUnit);
-    int32_t *hist = scratch;
-    int32_t *sc = scratch + 256 * nunits;
-    int64_t sc_len = scratch_len - 256 * nunits;
-    if (sc_len < 0) return LBF_EWORKSPACE;
-    int passes = (int)lbf_cdiv(2 * D, 8);
-    uint64_t *ka = keys, *kb = keys_alt;
-    int32_t *va = pl->perm, *vb = perm_alt;
-    for (int ps = 0; ps < passes; ps++) {
-        int shift = 8 * ps;
-        LBF_LAUNCH(k_rs_hist, lbf_cdiv(nunits, 8), 256, 0, s, ka, N, shift, hist, nunits);
-        LBF_CHECK_LAUNCH();
-        int rc = lbf_scan_i32(hist, hist, 256 * nunits, sc, sc_len, s);
-        if (rc) return rc;
-        LBF_LAUNCH(k_rs_scatter, lbf_cdiv(nunits, 8), 256, 0, s, ka, va, kb, vb, N, shift, hist,
-                   nunits);
-        LBF_CHECK_LAUNCH();
-        std::swap(ka, kb);
-        std::swap(va, vb);
-    }
-    if (ka != keys) {
-        LBF_CUDA(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * N, cudaMemcpyDeviceToDevice, s));
-        LBF_CUDA(cudaMemcpyAsync(pl->perm, va, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
-    }
+    int rc = lbf_radix_sort(keys, keys_alt, pl->perm, perm_alt, N, 2 * D, scratch, scratch_len, s);
+    if (rc) return rc;
 
     // root box
     int32_t root[8] = {0, 0, 0, -1, -1, 0, 0, (int32_t)N};
@@ -547,7 +556,7 @@ int lbf_tree_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, uint64_t *
     int32_t *pos = scratch + T.nbox;
     LBF_LAUNCH(k_leaf_flags, lbf_cdiv(T.nbox, 256), 256, 0, s, T.nbox, T.nchild, flags);
     LBF_CHECK_LAUNCH();
-    int rc = lbf_scan_i32(flags, pos, T.nbox, scratch + 2 * T.nbox, scratch_len - 2 * T.nbox, s);
+    rc = lbf_scan_i32(flags, pos, T.nbox, scratch + 2 * T.nbox, scratch_len - 2 * T.nbox, s);
     if (rc) return rc;
     int32_t lp = 0, lf = 0;
     if ((rc = read_i32(pos + T.nbox - 1, &lp, s))) return rc;

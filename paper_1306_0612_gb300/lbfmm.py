@@ -33,6 +33,7 @@ LBF_OP_FULL = 0
 LBF_OP_K_ONLY = 1
 LBF_OP_PRECONDITIONED = 2
 LBF_OP_FP32 = 16
+LBF_OP_TRANSPOSE = 32
 LBF_PRECISION_FP64 = 0
 LBF_PRECISION_FP32_REFINE = 1
 
@@ -69,6 +70,9 @@ def load():
             "lbf_plan_create": (C.c_int, [C.POINTER(_P), C.c_int, _P, _P, _P, _P, _P, _P,
                                           C.POINTER(lbf_options), _P, C.c_size_t,
                                           C.POINTER(i64), _P]),
+            "lbf_plan_create_planar": (C.c_int, [C.POINTER(_P), C.c_int, _P, _P, _P, _P, _P,
+                                                 C.POINTER(lbf_options), _P, C.c_size_t,
+                                                 C.POINTER(i64), _P]),
             "lbf_plan_destroy": (C.c_int, [_P]),
             "lbf_plan_info": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "lbf_geometry_out": (C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -85,6 +89,9 @@ def load():
             "lbf_profile_read": (C.c_int, [C.c_int, C.POINTER(i64), C.POINTER(C.c_double)]),
             "lbf_evaluate_noalloc": (C.c_int, [i64, _P, _P, _P, C.c_int, _P, _P, i64, _P, _P, _P]),
             "lbf_solve_stats": (C.c_int, [_P, _P]),
+            "lbf_gmres_solve_transpose": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+            "lbf_evaluate_transpose": (C.c_int, [_P, i64, _P, _P, _P, _P, _P]),
+            "lbf_gradient_nodes": (C.c_int, [_P, _P, _P, _P, i64, _P, _P, _P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
             "lbf_launch_count": (i64, []),
         }
@@ -98,10 +105,12 @@ def load():
 
 def exported_symbols():
     return ["lbf_default_options", "lbf_status_string", "lbf_workspace_size", "lbf_plan_create",
+            "lbf_plan_create_planar",
             "lbf_plan_destroy", "lbf_plan_info", "lbf_geometry_out", "lbf_apply",
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
-            "lbf_profile_reset", "lbf_profile_read", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
+            "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
+            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
             "lbf_launch_count"]
 
 
@@ -168,36 +177,51 @@ class Plan:
             self.handle = None
 
 
-def lbf_plan_create(island_ptr, x, dx, d2x, centres, pole_rotation=None, opt=None, stream=None,
-                    device=None) -> Plan:
-    """Build a plan (synchronous).  Retries with a larger box capacity when the
-    quadtree outgrows the first workspace estimate."""
+def _create(planar, island_ptr, a, da, d2a, centres, pole_rotation, opt, stream, device):
     lib = load()
     opt = opt or lbf_default_options()
     ptr = np.ascontiguousarray(island_ptr, dtype=np.int64)
     M = len(ptr) - 1
     N = int(ptr[-1])
+    k = 2 if planar else 3
     rot = None if pole_rotation is None else np.ascontiguousarray(pole_rotation, dtype=np.float64)
-    dev = x.device if device is None else device
+    dev = a.device if device is None else device
+    name = "lbf_plan_create_planar" if planar else "lbf_plan_create"
     for _ in range(6):
         nbytes = lbf_workspace_size(ptr, opt)
         ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         h = C.c_void_p()
         need = C.c_int64(0)
-        rc = lib.lbf_plan_create(C.byref(h), M, ptr.ctypes.data_as(_P), _dptr(x, 3 * N, "x"),
-                                 _dptr(dx, 3 * N, "dx"), _dptr(d2x, 3 * N, "d2x"),
-                                 _dptr(centres, 3 * M, "centres"),
-                                 None if rot is None else rot.ctypes.data_as(_P), C.byref(opt),
-                                 C.c_void_p(ws.data_ptr()), C.c_size_t(nbytes), C.byref(need),
-                                 _stream(stream))
+        geo = (_dptr(a, k * N, "nodes"), _dptr(da, k * N, "first derivatives"),
+               _dptr(d2a, k * N, "second derivatives"), _dptr(centres, 3 * M, "centres"))
+        tail = (C.byref(opt), C.c_void_p(ws.data_ptr()), C.c_size_t(nbytes), C.byref(need),
+                _stream(stream))
+        if planar:
+            rc = lib.lbf_plan_create_planar(C.byref(h), M, ptr.ctypes.data_as(_P), *geo, *tail)
+        else:
+            rc = lib.lbf_plan_create(C.byref(h), M, ptr.ctypes.data_as(_P), *geo,
+                                     None if rot is None else rot.ctypes.data_as(_P), *tail)
         if rc == LBF_EWORKSPACE and need.value > opt.box_capacity:
             opt = lbf_options.from_buffer_copy(opt)
             opt.box_capacity = int(need.value)
             del ws
             continue
-        _check(rc, "lbf_plan_create")
+        _check(rc, name)
         return Plan(h, ws, N, M, opt)
-    raise LbfError(LBF_EWORKSPACE, "lbf_plan_create")
+    raise LbfError(LBF_EWORKSPACE, name)
+
+
+def lbf_plan_create(island_ptr, x, dx, d2x, centres, pole_rotation=None, opt=None, stream=None,
+                    device=None) -> Plan:
+    """Build a plan from nodes on the sphere (synchronous).  Retries with a larger
+    box capacity when the quadtree outgrows the first workspace estimate."""
+    return _create(False, island_ptr, x, dx, d2x, centres, pole_rotation, opt, stream, device)
+
+
+def lbf_plan_create_planar(island_ptr, xi, dxi, d2xi, centres, opt=None, stream=None,
+                           device=None) -> Plan:
+    """Build a plan from planar nodes xi, xi', xi'' (N x 2 each, synchronous)."""
+    return _create(True, island_ptr, xi, dxi, d2xi, centres, None, opt, stream, device)
 
 
 def lbf_plan_destroy(plan: Plan):
@@ -228,7 +252,7 @@ def lbf_solve_stats(plan: Plan) -> dict:
 
 
 def lbf_apply(plan: Plan, op: int, inp: torch.Tensor, out: torch.Tensor, stream=None):
-    n = plan.N if (op & ~LBF_OP_FP32) == LBF_OP_K_ONLY else plan.N + plan.M
+    n = plan.N if (op & ~(LBF_OP_FP32 | LBF_OP_TRANSPOSE)) == LBF_OP_K_ONLY else plan.N + plan.M
     _check(load().lbf_apply(plan.handle, int(op), _dptr(inp, n, "in"), _dptr(out, n, "out"),
                             _stream(stream)), "lbf_apply")
 
@@ -250,6 +274,37 @@ def lbf_evaluate(plan: Plan, sigma: torch.Tensor, a: torch.Tensor | None, target
     _check(load().lbf_evaluate(plan.handle, _dptr(sigma, plan.N, "sigma"), _dptr(a, plan.M, "a"),
                                T, _dptr(targets, 3 * T, "targets"), _dptr(u, T, "u"),
                                _stream(stream)), "lbf_evaluate")
+
+
+def lbf_gmres_solve_transpose(plan: Plan, r: torch.Tensor, lam: torch.Tensor,
+                              x0: torch.Tensor | None = None, stream=None):
+    """Adjoint solve A^T lam = r (N + M vectors); returns (status, iterations, residual)."""
+    n = plan.N + plan.M
+    it, rr = C.c_int(0), C.c_double(0.0)
+    rc = load().lbf_gmres_solve_transpose(plan.handle, _dptr(r, n, "r"), _dptr(lam, n, "lam"),
+                                          _dptr(x0, n, "x0"), C.byref(it), C.byref(rr),
+                                          _stream(stream))
+    _check(rc, "lbf_gmres_solve_transpose")
+    return rc, it.value, rr.value
+
+
+def lbf_evaluate_transpose(plan: Plan, targets: torch.Tensor, ubar: torch.Tensor,
+                           sbar: torch.Tensor, abar: torch.Tensor | None = None, stream=None):
+    T = targets.numel() // 3
+    _check(load().lbf_evaluate_transpose(plan.handle, T, _dptr(targets, 3 * T, "targets"),
+                                         _dptr(ubar, T, "ubar"), _dptr(sbar, plan.N, "sbar"),
+                                         _dptr(abar, plan.M, "abar"), _stream(stream)),
+           "lbf_evaluate_transpose")
+
+
+def lbf_gradient_nodes(plan: Plan, sigma: torch.Tensor, a: torch.Tensor, lam: torch.Tensor,
+                       targets: torch.Tensor, ubar: torch.Tensor, grad: torch.Tensor, stream=None):
+    T = targets.numel() // 3
+    _check(load().lbf_gradient_nodes(plan.handle, _dptr(sigma, plan.N, "sigma"),
+                                     _dptr(a, plan.M, "a"), _dptr(lam, plan.N + plan.M, "lam"), T,
+                                     _dptr(targets, 3 * T, "targets"), _dptr(ubar, T, "ubar"),
+                                     _dptr(grad, 2 * plan.N, "grad"), _stream(stream)),
+           "lbf_gradient_nodes")
 
 
 def lbf_green_sum(t: torch.Tensor, p: torch.Tensor, gamma: torch.Tensor, out: torch.Tensor,

@@ -31,3 +31,15 @@ def max_rel(u, ref):
 
 def rel_l2(u, ref):
     return float(np.linalg.norm(np.asarray(u) - np.asarray(ref)) / np.linalg.norm(ref))
+
+
+def planar_nodes(g):
+    """xi, xi', xi'' of the projected nodes by the chain rule of xi = z / (1 - x3)
+    (Sec. 3), as three N x 2 arrays (re, im)."""
+    X, D1, D2 = g.x, g.dx, g.d2x
+    z, z1, z2 = (A[:, 0] + 1j * A[:, 1] for A in (X, D1, D2))
+    w, w1, w2 = 1 - X[:, 2], -D1[:, 2], -D2[:, 2]
+    xi = z / w
+    xi1 = z1 / w - z * w1 / w ** 2
+    xi2 = z2 / w - 2 * z1 * w1 / w ** 2 - z * w2 / w ** 2 + 2 * z * w1 ** 2 / w ** 3
+    return [np.stack([c.real, c.imag], axis=1) for c in (xi, xi1, xi2)]

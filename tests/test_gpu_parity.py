@@ -14,6 +14,7 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import workloads as wl  # noqa: E402
 from gpu_util import DEV, dev, host, plan_for, rel_l2, zeros  # noqa: E402
+from helpers import planar_nodes  # noqa: E402
 from paper_1306_0612_gb300 import lbfmm as L  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -50,6 +51,20 @@ def test_projection_bits_and_weights():
     assert np.allclose(np.hypot(nn[:, 0], nn[:, 1]), 1.0, atol=1e-14)
     assert np.max(np.abs(nn[:, 0] * wc[:, 0] + nn[:, 1] * wc[:, 1])) < 1e-12 * np.max(np.abs(wc))
     assert np.allclose(host(arc), np.hypot(wc[:, 0], wc[:, 1]), rtol=1e-14)
+
+
+def test_planar_plan_matches_sphere_plan():
+    g = wl.config_geometry("C2", nodes=128)
+    xi, xi1, xi2 = planar_nodes(g)
+    ps = plan_for(g)
+    pp = L.lbf_plan_create_planar(g.island_ptr, dev(xi), dev(xi1), dev(xi2), dev(g.centres),
+                                  opt=L.lbf_default_options())
+    v = np.random.default_rng(5).standard_normal(g.N + g.M)
+    for op in (L.LBF_OP_FULL, L.LBF_OP_PRECONDITIONED):
+        a, b = zeros(g.N + g.M), zeros(g.N + g.M)
+        L.lbf_apply(ps, op, dev(v), a)
+        L.lbf_apply(pp, op, dev(v), b)
+        assert rel_l2(host(b), host(a)) < 1e-12
 
 
 # ---- quadtree: bit-exact against the oracle -------------------------------------
@@ -112,6 +127,21 @@ def test_apply_all_ops_small(matvec):
     o2 = zeros(N)
     L.lbf_apply(p, L.LBF_OP_K_ONLY, dev(v[:N]), o2)
     assert rel_l2(host(o2), A[:N, :N] @ v[:N]) < MATVEC_TOL
+
+
+def test_preconditioned_op_many_islands():
+    """200 islands: the inverse Schur complement from the multi-block Gauss-Jordan
+    kernel and the tree-based multiplier potential against the dense P^-1 A."""
+    g = wl.star_caps(41, 200, 8)
+    p = plan_for(g, leaf_size=8)
+    A = oracle.matrix(g)
+    Pm = oracle.preconditioner_matrix(A, g.N)
+    v = np.random.default_rng(4).standard_normal(g.N + g.M)
+    out = zeros(g.N + g.M)
+    L.lbf_apply(p, L.LBF_OP_PRECONDITIONED, dev(v), out)
+    assert rel_l2(host(out), np.linalg.solve(Pm, A @ v)) < MATVEC_TOL
+    L.lbf_apply(p, L.LBF_OP_FULL, dev(v), out)
+    assert rel_l2(host(out), A @ v) < MATVEC_TOL
 
 
 def test_fmm_matvec_c2_full_size():
@@ -239,6 +269,17 @@ def test_node_at_pole_is_an_error():
     with pytest.raises(L.LbfError) as e:
         L.lbf_plan_create(g.island_ptr, dev(x), dev(g.dx), dev(g.d2x), dev(g.centres))
     assert e.value.status == L.LBF_EPOLE
+
+
+def test_shared_multiplier_centre_is_singular():
+    """Two islands given the same multiplier site make two columns of the Schur
+    complement S = D - F E equal (Eq. matrix_eqns_c): plan creation reports it."""
+    g = wl.config_geometry("C2", nodes=64)
+    c = g.centres.copy()
+    c[2] = c[1]
+    with pytest.raises(L.LbfError) as e:
+        L.lbf_plan_create(g.island_ptr, dev(g.x), dev(g.dx), dev(g.d2x), dev(c))
+    assert e.value.status == L.LBF_ESINGULAR
 
 
 def test_zero_targets_and_not_built():
