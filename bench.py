@@ -48,7 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="C3-1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="C3-1024", choices=sorted(WORKLOADS) + ["C4"])
+    ap.add_argument("--instances", type=int, default=512, help="C4: independent geometries")
+    ap.add_argument("--loop-instances", type=int, default=48,
+                    help="C4: instances timed in the plain FP64 loop (a bounded sample)")
+    ap.add_argument("--workers", type=int, default=16, help="C4: scheduler threads/streams")
     ap.add_argument("--precision", default="fp32r", choices=["fp64", "fp32r"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--p", type=int, default=None)
@@ -434,10 +438,113 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """C4: independent geometries of uneven size (1-64 islands, 64-1024 nodes per
+    island, log-uniform), 16 Green's-pair right-hand sides each, solved to 1e-10 and
+    evaluated at off-curve targets.  Batched arm: the native scheduler (worker
+    streams, FP32 FMM with FP64 refinement).  Baseline arm: the plain FP64 loop over
+    instances on one stream (plan, 16 solves, evaluations), on a bounded sample."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1306_0612_gb300 import lbfmm as L
+    import __graft_entry__
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    T = 32
+    inst = []
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).to(dev)
+    for g, pairs in wl.batch_instances(seed=4, count=args.instances, nrhs=16):
+        x = t(g.x)
+        data = torch.empty((len(pairs), g.N), dtype=torch.float64, device=dev)
+        tg = t(wl.targets_off_islands(g, T, seed=5))
+        uex = torch.empty((len(pairs), T), dtype=torch.float64, device=dev)
+        for k, (pp, gam) in enumerate(pairs):
+            L.lbf_green_sum(x, t(pp), t(gam), data[k])
+            L.lbf_green_sum(tg, t(pp), t(gam), uex[k])
+        inst.append(dict(island_ptr=g.island_ptr, x=x, dx=t(g.dx), d2x=t(g.d2x),
+                         centres=t(g.centres), g=data, targets=tg, uex=uex, N=g.N, M=g.M))
+    torch.cuda.synchronize()
+    nsolve = sum(i["g"].shape[0] for i in inst)
+    nodes = sum(i["N"] for i in inst)
+
+    def err(res, sub):
+        e = []
+        for ins, r in zip(sub, res):
+            d = (r["u"] - ins["uex"]).abs().amax(dim=1) / ins["uex"].abs().amax(dim=1)
+            e.extend(d.tolist())
+        return float(np.max(e)), float(np.median(e))
+
+    def batched(precision, sub):
+        opt = L.lbf_default_options(tol=args.tol, precision=precision)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = L.lbf_batch_run(sub, opt=opt, nworkers=args.workers)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = [r["status"] for r in res]
+        return dt, res, st
+
+    # warm-up on a few instances (library load, attributes, allocator)
+    batched(L.LBF_PRECISION_FP32_REFINE, inst[:args.workers])
+    dt32, res32, st32 = batched(L.LBF_PRECISION_FP32_REFINE, inst)
+    e32 = err(res32, inst)
+    dt64b, res64b, st64b = batched(L.LBF_PRECISION_FP64, inst)
+    e64b = err(res64b, inst)
+    # plain FP64 loop over instances, one stream, on a bounded sample
+    sub = inst[:min(args.loop_instances, len(inst))]
+    opt64 = L.lbf_default_options(tol=args.tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nloop = 0
+    loop_err = []
+    for ins in sub:
+        plan = L.lbf_plan_create(ins["island_ptr"], ins["x"], ins["dx"], ins["d2x"], ins["centres"],
+                                 opt=opt64)
+        sig = torch.empty(ins["N"], dtype=torch.float64, device=dev)
+        a = torch.empty(ins["M"], dtype=torch.float64, device=dev)
+        u = torch.empty(T, dtype=torch.float64, device=dev)
+        for k in range(ins["g"].shape[0]):
+            L.lbf_gmres_solve(plan, ins["g"][k], sig, a)
+            L.lbf_evaluate(plan, sig, a, ins["targets"], u)
+            loop_err.append(float((u - ins["uex"][k]).abs().max() / ins["uex"][k].abs().max()))
+            nloop += 1
+        del plan
+    torch.cuda.synchronize()
+    dtl = time.perf_counter() - t0
+    loop_rate = nloop / dtl
+    line = {"metric": "batched uneven solves: solves per second (plan + GMRES to 1e-10 + evaluation)",
+            "value": nsolve / dt32, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic",
+            "config": {"workload": f"C4: {len(inst)} star-cap geometries, 1-64 islands, 64-1024 nodes "
+                                   f"per island (log-uniform), 16 Green's-pair right-hand sides each, "
+                                   f"{T} targets", "instances": len(inst), "solves": nsolve,
+                       "nodes": nodes, "workers": args.workers, "tol": args.tol},
+            "batched_fp32r": {"wall_s": dt32, "solves_per_s": nsolve / dt32,
+                              "statuses_ok": st32.count(0), "solution_err_max": e32[0],
+                              "solution_err_median": e32[1],
+                              "fp32_applies": sum(r["fp32_applies"] for r in res32),
+                              "fp64_applies": sum(r["fp64_applies"] for r in res32)},
+            "batched_fp64": {"wall_s": dt64b, "solves_per_s": nsolve / dt64b,
+                             "statuses_ok": st64b.count(0), "solution_err_max": e64b[0],
+                             "solution_err_median": e64b[1]},
+            "loop_fp64": {"instances": len(sub), "solves": nloop, "wall_s": dtl,
+                          "solves_per_s": loop_rate, "solution_err_max": float(np.max(loop_err)),
+                          "note": "plain FP64 loop over instances on one stream, timed on the "
+                                  "first instances of the same list"},
+            "speedup_vs_loop_fp64": (nsolve / dt32) / loop_rate}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "C4":
+        return run_batch(args)
     return run_ours(args)
 
 

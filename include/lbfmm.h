@@ -212,6 +212,37 @@ int lbf_gradient_nodes(lbf_plan *plan, const double *sigma, const double *a, con
                        int64_t T, const double *targets, const double *ubar, double *grad,
                        lbf_stream_t stream);
 
+/* Batched solves of independent geometries: many instances of the bordered system
+ * of Sec. 5, each with nrhs right-hand sides (the paper solves one instance at a
+ * time; this is an interface of the library).  nworkers host threads, each with its
+ * own CUDA stream, take the items largest first (nodes x right-hand sides); per
+ * item: a plan (lbf_plan_create, no pole rotation), for every right-hand side
+ * lbf_gmres_solve with opt and, when T > 0 and u != NULL, lbf_evaluate at the
+ * targets; then the plan is destroyed.  Synchronous.  Returns LBF_EINVAL for a bad
+ * item, LBF_ECUDA if a worker could not start; each item's own outcome is in its
+ * status (LBF_EWORKSPACE with box_capacity_needed set when its workspace was short). */
+typedef struct lbf_batch_item {
+    /* in */
+    int M;                                  /* islands */
+    const int64_t *island_ptr;              /* host, M + 1 */
+    const double *x, *dx, *d2x, *centres;   /* device, as lbf_plan_create */
+    void *workspace;                        /* device, >= lbf_workspace_size(M, island_ptr, opt) */
+    size_t bytes;
+    int nrhs;                               /* right-hand sides */
+    const double *g;                        /* device, nrhs x N: right-hand side r at g + r N */
+    double *sigma, *a;                      /* device out, nrhs x N and nrhs x M (a nullable) */
+    int64_t T;                              /* targets (0: no evaluation) */
+    const double *targets;                  /* device, T x 3 */
+    double *u;                              /* device out, nrhs x T (nullable) */
+    int64_t box_capacity;                   /* this item's opt->box_capacity (0: estimate) */
+    /* out (host) */
+    int status, iters;                      /* worst status; GMRES iterations over the rhs */
+    int64_t fp64_applies, fp32_applies;     /* operator applications over the rhs */
+    double max_rel_res;                     /* largest final relative residual */
+    int64_t box_capacity_needed;            /* see lbf_plan_create */
+} lbf_batch_item;
+int lbf_batch_run(int nitems, lbf_batch_item *items, const lbf_options *opt, int nworkers);
+
 /* Work of the plan's last lbf_gmres_solve (host out): stats[0] Arnoldi steps,
  * [1] FP64 operator applications, [2] FP32 operator applications,
  * [3] refinement steps (0 for LBF_PRECISION_FP64). */

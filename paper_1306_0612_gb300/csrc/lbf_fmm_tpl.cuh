@@ -478,7 +478,12 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
     for (int tb = bg[b]; tb < en[b]; tb += 32) {
         const int nt = min(32, en[b] - tb);
         const int i = tb + lane;
-        const bool act = lane < nt;
+        const bool act = lane < nt;  // this lane's far field and output
+        // near field: TP >= nt target slots, 32/TP lanes per target splitting the sources
+        const int TP = nt <= 1 ? 1 : 1 << (32 - __clz(nt - 1));
+        const int slot = lane & (TP - 1), grp = lane / TP, G = 32 / TP;
+        const int ti = tb + slot;
+        const bool pact = slot < nt;
         cx<R> u = mk<R>(0, 0);  // (z - c)/r
         cx<R> phi = mk<R>(0, 0);  // far field: Phi (or Phi' in kLeafDeriv)
         if (act) {
@@ -558,17 +563,19 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         }
         // near field, in units of r: sum over sources of q conj(dz)/|dz|^2 (Im part only
         // in the forward mode) or q conj(dz)^2/|dz|^4, dz = xi_s - z
+        const cx<R> ut = mk<R>(__shfl_sync(0xffffffffu, u.x, slot),
+                               __shfl_sync(0xffffffffu, u.y, slot));
         R accI = 0;
         cx<R> acc = mk<R>(0, 0);
         int fill = 0;
         auto process = [&]() {
             __syncwarp();
-            if (act) {
-                for (int m = 0; m < fill; m++) {
-                    if (sj[wid][m] == i) continue;
+            if (pact) {
+                for (int m = grp; m < fill; m += G) {
+                    if (sj[wid][m] == ti) continue;
                     const cx<R> zs = sx[wid][m];
                     const cx<R> qq = sq[wid][m];
-                    const R dr = zs.x - u.x, di = zs.y - u.y;
+                    const R dr = zs.x - ut.x, di = zs.y - ut.y;
                     const R ir2 = rcp(fm(dr, dr, di * di));
                     if constexpr (MODE == kLeafForward) {
                         accI = fm(fm(qq.y, dr, -qq.x * di), ir2, accI);
@@ -621,6 +628,11 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             }
         }
         if (fill > 0) process();
+        for (int o = TP; o < 32; o <<= 1) {  // sum the source groups of each target
+            accI += __shfl_xor_sync(0xffffffffu, accI, o);
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
         if (act) {
             if constexpr (MODE == kLeafForward) {
                 double c = (double)(-phi.y) + (double)(accI * irr);

@@ -127,22 +127,25 @@ __global__ void k_rotate_centres(int M, const double *__restrict__ c, Rot R, dou
 // k, swap, scale the pivot row.  One block.
 // ---- inverse of the Schur complement ---------------------------------------------------
 //
-// In-place Gauss-Jordan elimination with partial pivoting (row interchanges), all
-// M steps in one cooperative launch: per step k every block reduces the partial
-// column maxima to the pivot row p, the grid saves the scaled pivot row, the old
-// row k and the multipliers (column k after the interchange), and after a grid
-// barrier every element is updated once:
-//   A_kj <- A_pj / A_pk,  A_ik <- -A_ik / A_pk,  A_ij <- A_ij - A_ik A_pj / A_pk,
-// while the same pass forms the partial maxima of column k + 1.  The interchanges
-// are undone at the end by swapping columns k and p for k = M-1, ..., 0.
+// Gauss-Jordan elimination with partial pivoting (row interchanges), all M steps in
+// one cooperative launch.  Step k reads matrix A_k and writes A_(k+1) (two buffers
+// in turn), so every block takes the pivot row p, row k and column k straight from
+// A_k and one grid barrier per step suffices:
+//   row k:       A'_kj = A_pj / A_pk                   (A'_kk = 1 / A_pk)
+//   row i != k:  A'_ij = B_ij - B_ik A_pj / A_pk,  A'_ik = -B_ik / A_pk,
+// B being A_k with rows k and p interchanged.  The same pass forms each block's
+// partial maximum of |A'_i,k+1|, i > k (two sets of partials, by step parity, so a
+// block never overwrites values another block is still reducing).  Every block
+// reduces the partials the same way, so all agree on the next pivot.  The
+// interchanges are undone at the end by swapping columns k and p, k = M-1, ..., 0.
 //
 // The grid barrier is a counter and a generation word; every block is resident
 // (cooperative launch), and each wait gives up after kBarrierSpins polls, setting
 // status bit LBF_DEV_TIMEOUT, so the kernel always ends.
 
 constexpr unsigned kBarrierSpins = 1u << 22;
-constexpr int kGjThreads = 256;
-constexpr int kGjMaxBlocks = 2048;
+constexpr int kGjThreads = 512;
+constexpr int kGjMaxBlocks = 1024;
 
 struct GridBarrier {
     unsigned count, gen;
@@ -169,7 +172,6 @@ __device__ bool grid_barrier(GridBarrier *bar, unsigned nb, int *status)
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
@@ -203,8 +205,8 @@ __device__ void block_argmax(double &v, int &idx, double *sv, int *si)
 }
 
 __global__ void __launch_bounds__(kGjThreads)
-k_gj_coop(int M, double *A, double *rowk, double *oldk, double *colk, double *pval, int *pidx,
-          int *pivrow, GridBarrier *bar, int *status)
+k_gj_coop(int M, double *A0, double *A1, double *pval, int *pidx, double *amax, int *pivrow,
+          GridBarrier *bar, int *status)
 {
     __shared__ double sv[kGjThreads];
     __shared__ int si[kGjThreads];
@@ -214,45 +216,48 @@ k_gj_coop(int M, double *A, double *rowk, double *oldk, double *colk, double *pv
     const int64_t MM = (int64_t)M * M;
     const int i0 = (int)(tid / M), j0 = (int)(tid % M);
     const int di = (int)(nthr / M), dj = (int)(nthr % M);
-    // partial maxima of column 0
+    // partial maxima of column 0 (parity 0) and of every |S_ij|
     {
-        double best = -1.0;
-        int bi = M;
+        double best = -1.0, big = 0.0;
+        int bi = M, unused = 0;
         for (int64_t i = tid; i < M; i += nthr) {
-            double a = fabs(__ldcg(&A[i * M]));
+            double a = fabs(A0[i * M]);
             if (a > best) { best = a; bi = (int)i; }
         }
+        for (int64_t e = tid; e < MM; e += nthr) big = fmax(big, fabs(A0[e]));
         block_argmax(best, bi, sv, si);
-        if (threadIdx.x == 0) { pval[blockIdx.x] = best; pidx[blockIdx.x] = bi; }
+        block_argmax(big, unused, sv, si);
+        if (threadIdx.x == 0) {
+            pval[blockIdx.x] = best;
+            pidx[blockIdx.x] = bi;
+            amax[blockIdx.x] = big;
+        }
     }
     if (!grid_barrier(bar, nb, status)) return;
+    // a pivot at or below M 2^-52 max|S_ij| counts as zero: S is singular to double precision
+    double tiny = 0.0;
+    for (unsigned q = 0; q < nb; q++) tiny = fmax(tiny, __ldcg(&amax[q]));
+    tiny *= (double)M * 0x1p-52;
     for (int k = 0; k < M; k++) {
-        // pivot row: every block reduces the partial maxima the same way
+        const double *Ain = (k & 1) ? A1 : A0;
+        double *Aout = (k & 1) ? A0 : A1;
+        const double *pv = pval + (k & 1) * kGjMaxBlocks;
+        const int *pi = pidx + (k & 1) * kGjMaxBlocks;
         double best = -1.0;
         int p = M;
         for (unsigned q = threadIdx.x; q < nb; q += blockDim.x) {
-            double a = __ldcg(&pval[q]);
-            int i = __ldcg(&pidx[q]);
+            double a = __ldcg(&pv[q]);
+            int i = __ldcg(&pi[q]);
             if (a > best || (a == best && i < p)) { best = a; p = i; }
         }
         block_argmax(best, p, sv, si);
-        if (!(best > 0.0) || p >= M) {  // every block sees the same value: all stop here
+        if (!(best > tiny) || p >= M) {  // every block sees the same value: all stop here
             if (tid == 0) atomicOr(status, 4);
             return;
         }
-        const double piv = __ldcg(&A[(int64_t)p * M + k]);
-        const double ipiv = 1.0 / piv;
         if (tid == 0) pivrow[k] = p;
-        for (int64_t j = tid; j < M; j += nthr) {
-            const double apj = __ldcg(&A[(int64_t)p * M + j]);
-            const double akj = __ldcg(&A[(int64_t)k * M + j]);
-            rowk[j] = (j == k) ? ipiv : apj * ipiv;
-            oldk[j] = akj;
-            // multiplier of row j after the interchange of rows k and p
-            colk[j] = (j == k) ? piv : (j == p ? __ldcg(&A[(int64_t)k * M + k])
-                                               : __ldcg(&A[j * M + k]));
-        }
-        if (!grid_barrier(bar, nb, status)) return;
+        const double ipiv = 1.0 / __ldcg(&Ain[(int64_t)p * M + k]);
+        const double *rowp = Ain + (int64_t)p * M;
         double nbest = -1.0;
         int ni = M;
         int i = i0, j = j0;  // (i, j) of element e, advanced without dividing
@@ -260,24 +265,28 @@ k_gj_coop(int M, double *A, double *rowk, double *oldk, double *colk, double *pv
             if (j >= M) { j -= M; i++; }
             double val;
             if (i == k) {
-                val = __ldcg(&rowk[j]);
+                val = (j == k) ? ipiv : __ldcg(&rowp[j]) * ipiv;
             } else {
-                const double f = __ldcg(&colk[i]);
+                const int src = (i == p) ? k : i;  // row i of B
+                const double f = __ldcg(&Ain[(int64_t)src * M + k]);
                 if (j == k) {
-                    val = -f * __ldcg(&rowk[k]);
+                    val = -f * ipiv;
                 } else {
-                    const double a = (i == p) ? __ldcg(&oldk[j]) : __ldcg(&A[e]);
-                    val = fma(-f, __ldcg(&rowk[j]), a);
+                    const double a = __ldcg(&Ain[(int64_t)src * M + j]);
+                    val = fma(-f * ipiv, __ldcg(&rowp[j]), a);
                 }
             }
-            A[e] = val;
+            Aout[e] = val;
             if (j == k + 1 && i > k) {
                 double av = fabs(val);
                 if (av > nbest || (av == nbest && i < ni)) { nbest = av; ni = i; }
             }
         }
         block_argmax(nbest, ni, sv, si);
-        if (threadIdx.x == 0) { pval[blockIdx.x] = nbest; pidx[blockIdx.x] = ni; }
+        if (threadIdx.x == 0) {
+            pval[((k + 1) & 1) * kGjMaxBlocks + blockIdx.x] = nbest;
+            pidx[((k + 1) & 1) * kGjMaxBlocks + blockIdx.x] = ni;
+        }
         if (!grid_barrier(bar, nb, status)) return;
     }
 }
@@ -363,7 +372,10 @@ int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const
 
 // S = D - F E from the island expansions of the multiplier potential, then its
 // inverse in place by Gauss-Jordan elimination with partial pivoting.
-size_t lbf_gj_scratch_doubles(int M) { return 3 * (size_t)M + 2 * kGjMaxBlocks + (size_t)M + 64; }
+size_t lbf_gj_scratch_doubles(int M)
+{
+    return (size_t)M * M + 5 * (size_t)kGjMaxBlocks + (size_t)M + 64;
+}
 
 int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
                      int32_t *work, int64_t work_len, const SortBufs &sb)
@@ -381,23 +393,24 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *
     LBF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     LBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, kGjThreads, 0));
     if (!coop || per_sm < 1) return LBF_ECUDA;
-    // two blocks per SM: enough to keep every SM's double pipe busy, few enough that the
-    // barrier's single counter stays cheap
+    // one block per SM: every SM's double pipe busy, one barrier arrival per SM
     int64_t want = lbf_cdiv((int64_t)M * M, (int64_t)kGjThreads);
-    int nb = (int)std::min<int64_t>(std::min<int64_t>((int64_t)nsm * std::min(per_sm, 2), kGjMaxBlocks),
-                                    std::max<int64_t>(want, 1));
-    double *rowk = scratch, *oldk = scratch + M, *colk = scratch + 2 * M;
-    double *pval = scratch + 3 * M;
-    int *pidx = (int *)(pval + kGjMaxBlocks);
-    int *pivrow = pidx + kGjMaxBlocks;
+    int nb = (int)std::min<int64_t>(std::min<int64_t>(nsm, kGjMaxBlocks), std::max<int64_t>(want, 1));
+    double *S1 = scratch;                         // the second M x M buffer
+    double *pval = scratch + (size_t)M * M;       // 2 x kGjMaxBlocks
+    int *pidx = (int *)(pval + 2 * kGjMaxBlocks); // 2 x kGjMaxBlocks
+    double *amax = (double *)(pidx + 2 * kGjMaxBlocks);  // kGjMaxBlocks
+    int *pivrow = (int *)(amax + kGjMaxBlocks);   // M
     GridBarrier *bar = (GridBarrier *)(pivrow + M + (M & 1));
     LBF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
     LBF_LAUNCH(k_gj_init, lbf_cdiv(M, 256), 256, 0, s, M, pivrow);
     int *status = pl->dev_status;
-    void *args[] = {&M, &S, &rowk, &oldk, &colk, &pval, &pidx, &pivrow, &bar, &status};
+    void *args[] = {&M, &S, &S1, &pval, &pidx, &amax, &pivrow, &bar, &status};
     LBF_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(nb), dim3(kGjThreads), args,
                                          0, s));
     g_lbf_launches.fetch_add(1, std::memory_order_relaxed);
+    // after M steps the result is in the buffer step M wrote
+    if (M & 1) LBF_CUDA(cudaMemcpyAsync(S, S1, sizeof(double) * (size_t)M * M, cudaMemcpyDeviceToDevice, s));
     LBF_LAUNCH(k_gj_unscramble, lbf_cdiv(M, 128), 128, 0, s, M, S, pivrow);
     LBF_CHECK_LAUNCH();
     lbf_prof_mark(LBF_STAGE_INVERSE, 0, s);

@@ -45,6 +45,18 @@ class lbf_options(C.Structure):
                 ("p32", C.c_int), ("inner_tol", C.c_double), ("max_refine", C.c_int)]
 
 
+class lbf_batch_item(C.Structure):
+    """Mirror of the C struct lbf_batch_item (one independent instance of a batch)."""
+    _fields_ = [("M", C.c_int), ("island_ptr", C.c_void_p), ("x", C.c_void_p),
+                ("dx", C.c_void_p), ("d2x", C.c_void_p), ("centres", C.c_void_p),
+                ("workspace", C.c_void_p), ("bytes", C.c_size_t), ("nrhs", C.c_int),
+                ("g", C.c_void_p), ("sigma", C.c_void_p), ("a", C.c_void_p), ("T", C.c_int64),
+                ("targets", C.c_void_p), ("u", C.c_void_p), ("box_capacity", C.c_int64),
+                ("status", C.c_int),
+                ("iters", C.c_int), ("fp64_applies", C.c_int64), ("fp32_applies", C.c_int64),
+                ("max_rel_res", C.c_double), ("box_capacity_needed", C.c_int64)]
+
+
 class LbfError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -90,6 +102,8 @@ def load():
             "lbf_evaluate_noalloc": (C.c_int, [i64, _P, _P, _P, C.c_int, _P, _P, i64, _P, _P, _P]),
             "lbf_solve_stats": (C.c_int, [_P, _P]),
             "lbf_gmres_solve_transpose": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+            "lbf_batch_run": (C.c_int, [C.c_int, C.POINTER(lbf_batch_item), C.POINTER(lbf_options),
+                                        C.c_int]),
             "lbf_evaluate_transpose": (C.c_int, [_P, i64, _P, _P, _P, _P, _P]),
             "lbf_gradient_nodes": (C.c_int, [_P, _P, _P, _P, i64, _P, _P, _P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
@@ -110,7 +124,7 @@ def exported_symbols():
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
             "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
-            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
+            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
             "lbf_launch_count"]
 
 
@@ -305,6 +319,73 @@ def lbf_gradient_nodes(plan: Plan, sigma: torch.Tensor, a: torch.Tensor, lam: to
                                      _dptr(targets, 3 * T, "targets"), _dptr(ubar, T, "ubar"),
                                      _dptr(grad, 2 * plan.N, "grad"), _stream(stream)),
            "lbf_gradient_nodes")
+
+
+def lbf_batch_run(instances, opt=None, nworkers=8):
+    """Solve many independent instances (native scheduler, one CUDA stream per worker).
+
+    instances: list of dicts with keys island_ptr (host int64, M + 1), x, dx, d2x,
+    centres (CUDA float64), g (nrhs x N), and optionally targets (T x 3).  Returns a
+    list of dicts with sigma (nrhs x N), a (nrhs x M), u (nrhs x T or None) and the
+    item's status, iters, fp64_applies, fp32_applies, max_rel_res.  Instances whose
+    quadtree outgrew the workspace estimate are rerun with the size they reported."""
+    lib = load()
+    opt = opt or lbf_default_options()
+    n = len(instances)
+    results = [None] * n
+    todo = list(range(n))
+    caps = [opt.box_capacity] * n
+    for _ in range(4):
+        if not todo:
+            break
+        items = (lbf_batch_item * len(todo))()
+        keep = []
+        for slot, q in enumerate(todo):
+            ins = instances[q]
+            ptr = np.ascontiguousarray(ins["island_ptr"], dtype=np.int64)
+            M, N = len(ptr) - 1, int(ptr[-1])
+            o = lbf_options.from_buffer_copy(opt)
+            o.box_capacity = caps[q]
+            nbytes = lbf_workspace_size(ptr, o)
+            dev = ins["x"].device
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            g = ins["g"].reshape(-1)
+            nrhs = g.numel() // N
+            sigma = torch.empty(nrhs * N, dtype=torch.float64, device=dev)
+            a = torch.empty(nrhs * M, dtype=torch.float64, device=dev)
+            t = ins.get("targets")
+            T = 0 if t is None else t.numel() // 3
+            u = torch.empty(nrhs * T, dtype=torch.float64, device=dev) if T else None
+            it = items[slot]
+            it.M, it.island_ptr = M, ptr.ctypes.data
+            it.x = _dptr(ins["x"], 3 * N, "x").value
+            it.dx = _dptr(ins["dx"], 3 * N, "dx").value
+            it.d2x = _dptr(ins["d2x"], 3 * N, "d2x").value
+            it.centres = _dptr(ins["centres"], 3 * M, "centres").value
+            it.workspace, it.bytes = ws.data_ptr(), nbytes
+            it.nrhs, it.g = nrhs, _dptr(g, nrhs * N, "g").value
+            it.sigma, it.a = sigma.data_ptr(), a.data_ptr()
+            it.T = T
+            it.targets = None if T == 0 else _dptr(t, 3 * T, "targets").value
+            it.u = None if u is None else u.data_ptr()
+            it.box_capacity = caps[q]
+            keep.append((q, ptr, ws, sigma, a, u, nrhs, N, M, T))
+        _check(lib.lbf_batch_run(len(todo), items, C.byref(opt), int(nworkers)), "lbf_batch_run")
+        nxt = []
+        for slot, (q, ptr, ws, sigma, a, u, nrhs, N, M, T) in enumerate(keep):
+            it = items[slot]
+            if it.status == LBF_EWORKSPACE and it.box_capacity_needed > caps[q]:
+                caps[q] = int(it.box_capacity_needed)
+                nxt.append(q)
+                continue
+            results[q] = dict(sigma=sigma.view(nrhs, N), a=a.view(nrhs, M),
+                              u=None if u is None else u.view(nrhs, T), status=it.status,
+                              iters=it.iters, fp64_applies=it.fp64_applies,
+                              fp32_applies=it.fp32_applies, max_rel_res=it.max_rel_res)
+        todo = nxt
+    for q in todo:
+        raise LbfError(LBF_EWORKSPACE, f"lbf_batch_run item {q}")
+    return results
 
 
 def lbf_green_sum(t: torch.Tensor, p: torch.Tensor, gamma: torch.Tensor, out: torch.Tensor,

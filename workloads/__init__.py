@@ -15,4 +15,5 @@ from .star_caps import (  # noqa: F401
     rotation_to_pole,
     apply_rotation,
     rotated,
+    batch_instances,
 )

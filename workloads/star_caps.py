@@ -286,3 +286,25 @@ def config_geometry(name: str, **kw) -> Geometry:
     if name == "C5":
         return star_caps(5, kw.get("M", 256), kw.get("nodes", 512), pole=kw.get("pole", "first"))
     raise KeyError(name)
+
+
+def batch_instances(seed: int = 4, count: int = 512, nrhs: int = 16, max_islands: int = 64,
+                    nodes_range=(64, 1024)):
+    """Independent geometries of uneven size with several source pairs each: per
+    instance M ~ U{1..max_islands}, nodes per island round(exp U(ln a, ln b)) for
+    nodes_range = (a, b), and nrhs +1/-1 source pairs in random islands (both in
+    island 0 when M = 1).  Returns a list of (Geometry, [(points, strengths), ...])."""
+    rng = np.random.default_rng(seed)
+    out = []
+    lo, hi = np.log(nodes_range[0]), np.log(nodes_range[1])
+    for _ in range(count):
+        M = int(rng.integers(1, max_islands + 1))
+        nodes = np.rint(np.exp(rng.uniform(lo, hi, size=M))).astype(np.int64)
+        g = star_caps(int(rng.integers(0, 2**31 - 1)), M, nodes)
+        srng = np.random.default_rng(int(rng.integers(0, 2**31 - 1)))
+        pairs = []
+        for _ in range(nrhs):
+            p, gam, _ = random_pair_sources(g, srng)
+            pairs.append((p, gam))
+        out.append((g, pairs))
+    return out
