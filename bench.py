@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FMM matvec Mpts/s and GMRES solve time at 1e-10 rel err; fraction of FP64 peak"
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of one GB300 (recipe table)
 FP32_PEAK_TFLOPS = 80.6   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+DF64_FLOPS_PER_FLOP = 9.5  # float flops per double-float flop (fma 18/2, mul 10, add 11)
 WORKLOADS = {
     "C3-256": dict(M=256, nodes=1024),
     "C3-1024": dict(M=1024, nodes=1024),
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--loop-instances", type=int, default=48,
                     help="C4: instances timed in the plain FP64 loop (a bounded sample)")
     ap.add_argument("--workers", type=int, default=16, help="C4: scheduler threads/streams")
+    ap.add_argument("--sweep", action="store_true",
+                    help="C3 matvec sweep: one line per island count (K_ONLY operator)")
+    ap.add_argument("--sweep-m", default="64,128,256,1024,2048,4096,8192,16384")
     ap.add_argument("--precision", default="fp32r", choices=["fp64", "fp32r"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--p", type=int, default=None)
@@ -83,6 +87,7 @@ def workload_config(name, g, T, tol, precision):
     return {"workload": f"{name}: {w['M']} star-cap islands x {w['nodes']} nodes "
                         f"(N={g.N}), Green's-pair data, GMRES(50) tol {tol:g}, {T} targets",
             "islands": g.M, "nodes": g.N, "targets": T, "precision": precision,
+            "accurate_operator_arithmetic": "double-float FMM (pairs of floats), double elsewhere",
             "l2": f"working set larger than L2: the Krylov basis alone is 51 x {g.N + g.M} doubles "
                   f"({51 * (g.N + g.M) * 8 / 1e6:.0f} MB), streamed every iteration"}
 
@@ -333,6 +338,10 @@ def run_ours(args):
             peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
             src_p = ("FP32 derived from unit counts and the 2.07 GHz clock" if f32 else
                      "nominal FP64 (recipe table; MEASURED_PEAKS.json has no FP64 entry)")
+            if not f32 and dom in ("up", "down", "leaf") and opt.fmm64:
+                src_p += ("; this kernel runs double-float arithmetic on the FP32 pipes, whose "
+                          f"own ceiling is {FP32_PEAK_TFLOPS / DF64_FLOPS_PER_FLOP:.2f} TFLOP/s of "
+                          "double flops (FP32 peak / 9.5 float flops per double flop)")
             ach, bound = rate / 1e12, "alu"
         traffic = None
         tp = os.path.join(ROOT, "profiles", "traffic.json")
@@ -539,10 +548,90 @@ def run_batch(args):
     return 0
 
 
+def run_sweep(args):
+    """C3 sweep: the density operator (I + 2K) sigma, sigma ~ N(0, 1), on 2^k islands x
+    1024 nodes; FP64 and FP32 FMM applies (median of 5 after 3 warm-ups, CUDA events),
+    per-kernel algorithmic rates, the FP32 error against FP64, and (N <= 262144) the FMM
+    against the GPU's tiled direct sum, with the direct sum's own time."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1306_0612_gb300 import lbfmm as L
+    import __graft_entry__
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).to(dev)
+
+    def timed(plan, op, vin, vout, reps=5):
+        for _ in range(3):
+            L.lbf_apply(plan, op, vin, vout)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.lbf_apply(plan, op, vin, vout)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for M in [int(v) for v in args.sweep_m.split(",")]:
+        g = wl.star_caps(3, M, 1024)
+        x, dx, d2x, cen = t(g.x), t(g.dx), t(g.d2x), t(g.centres)
+        opt = L.lbf_default_options(border=0, precision=L.LBF_PRECISION_FP32_REFINE)
+        plan = L.lbf_plan_create(g.island_ptr, x, dx, d2x, cen, opt=opt)
+        vin = t(wl.random_density(g.N, seed=1))
+        o64, o32 = torch.empty_like(vin), torch.empty_like(vin)
+        ms64 = timed(plan, L.LBF_OP_K_ONLY, vin, o64)
+        ms32 = timed(plan, L.LBF_OP_K_ONLY | L.LBF_OP_FP32, vin, o32)
+        counts = L.lbf_plan_counts(plan)
+        info = plan.info()
+        P, P32 = info["p"] + 1, opt.p32 + 1
+        L.lbf_profile_reset()
+        L.lbf_profile_enable(True)
+        L.lbf_apply(plan, L.LBF_OP_K_ONLY, vin, o64)
+        L.lbf_apply(plan, L.LBF_OP_K_ONLY | L.LBF_OP_FP32, vin, o32)
+        torch.cuda.synchronize()
+        L.lbf_profile_enable(False)
+        kern = {}
+        for kid, name in enumerate(L.KERNEL_NAMES):
+            n, tms = L.lbf_profile_read(kid)
+            if n and name in ("up", "down", "leaf", "up32", "down32", "leaf32"):
+                work, _ = kernel_work(name, counts, None, P, P32, g.N)
+                peak = FP32_PEAK_TFLOPS if name.endswith("32") else FP64_PEAK_TFLOPS
+                ach = work / (tms / 1e3) / 1e12
+                kern[name] = {"ms": round(tms, 3), "tflops": ach, "frac": ach / peak}
+        L.lbf_profile_reset()
+        line = {"sweep": "C3", "islands": M, "N": g.N, "tree": info,
+                "fp64": {"apply_ms": ms64, "mpts": g.N / ms64 / 1e3},
+                "fp32": {"apply_ms": ms32, "mpts": g.N / ms32 / 1e3,
+                         "rel_l2_vs_fp64": float((o32 - o64).norm() / o64.norm())},
+                "kernels": kern}
+        if g.N <= 262144:
+            od = torch.empty_like(vin)
+            pd = L.lbf_plan_create(g.island_ptr, x, dx, d2x, cen,
+                                   opt=L.lbf_default_options(border=0, matvec=L.LBF_MATVEC_DIRECT))
+            msd = timed(pd, L.LBF_OP_K_ONLY, vin, od, reps=3)
+            line["direct"] = {"apply_ms": msd, "mpts": g.N / msd / 1e3,
+                              "pairs_per_s": g.N * (g.N - 1) / (msd / 1e3)}
+            line["fp64"]["rel_l2_vs_direct"] = float((o64 - od).norm() / od.norm())
+            line["fp32"]["rel_l2_vs_direct"] = float((o32 - od).norm() / od.norm())
+            del pd
+        print(json.dumps(line), flush=True)
+        del plan
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.workload == "C4":
         return run_batch(args)
     return run_ours(args)

@@ -83,6 +83,13 @@ typedef struct lbf_options {
     int p32;              /* expansion order of the FP32 FMM (4..31) */
     double inner_tol;     /* FP32_REFINE: relative tolerance of each inner solve */
     int max_refine;       /* FP32_REFINE: maximum refinement steps */
+    int graphs;           /* GMRES steps replayed from a CUDA graph captured once per plan
+                             (stream must not be the legacy default stream): 1 on, 0 off,
+                             -1 automatic (on for N <= 262144, where launches dominate);
+                             per-kernel tracing skips graph-replayed kernels */
+    int fmm64;            /* arithmetic of the accurate (double) FMM operator: 0 double,
+                             1 double-float (pairs of floats, ~48-bit significands; this
+                             GPU issues float 64 times faster than double) */
 } lbf_options;
 
 /* precision of gmres_solve:

@@ -37,7 +37,7 @@ bool valid(const lbf_options &o)
            (o.border == 0 || o.border == 1) &&
            (o.precision == LBF_PRECISION_FP64 || o.precision == LBF_PRECISION_FP32_REFINE) &&
            o.p32 >= 4 && o.p32 + 1 <= 32 && o.inner_tol > 0 && o.inner_tol < 1 &&
-           o.max_refine >= 1;
+           o.max_refine >= 1 && o.graphs >= -1 && o.graphs <= 1 && (o.fmm64 == 0 || o.fmm64 == 1);
 }
 
 // host tables of the translation operators (scaled expansions, see lbf_fmm.cu)
@@ -133,6 +133,13 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         pl->local = A.get<double2>(cap * P);
     }
     if (o.matvec == LBF_MATVEC_FMM || o.border) pl->upcnt = A.get<int32_t>(cap);
+    if (o.matvec == LBF_MATVEC_FMM && o.fmm64) {
+        pl->qdf = A.get<double2>(N);   // cx<df64>: 16 B per node
+        pl->udf = A.get<double2>(N);
+        pl->tabdf_binom = A.get<double>(2 * T * T);
+        pl->tabdf_tpow = A.get<double2>(49 * (T + 1));
+        pl->tabdf_dshift = A.get<double2>(8 * (T + 1));
+    }
     if (o.precision == LBF_PRECISION_FP32_REFINE) {
         int P32 = o.p32 + 1;
         pl->P32 = P32;
@@ -159,6 +166,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     pl->yvec = A.get<double>(M);
     pl->tin = A.get<double>(n);
     pl->tout = A.get<double>(n);
+    if (o.border) pl->vstep = A.get<double>(n);
     if (o.border) {
         Border &B = pl->bd;
         B.P = 36;   // (sqrt2/3)^36 / 36 ~ 1e-13 worst-case truncation of P2L + L2P
@@ -279,6 +287,8 @@ int lbf_default_options(lbf_options *o)
     o->p32 = 12;
     o->inner_tol = 1e-4;
     o->max_refine = 20;
+    o->graphs = -1;
+    o->fmm64 = 1;
     return LBF_OK;
 }
 
@@ -392,6 +402,26 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
         CK(cudaMemcpyAsync(pl->tab32_tpow, t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(pl->tab32_dshift, d32.data(), sizeof(float2) * d32.size(), cudaMemcpyHostToDevice, s));
     }
+    if (pl->tabdf_binom) {  // the same tables as double-floats (hi, lo per real)
+        std::vector<float> b2(2 * binom.size()), t2(4 * tpow.size()), d2(4 * dshift.size());
+        auto split = [](double v, float *o) {
+            o[0] = (float)v;
+            o[1] = (float)(v - (double)o[0]);
+        };
+        for (size_t i = 0; i < binom.size(); i++) split(binom[i], &b2[2 * i]);
+        for (size_t i = 0; i < tpow.size(); i++) {
+            split(tpow[i].x, &t2[4 * i]);
+            split(tpow[i].y, &t2[4 * i + 2]);
+        }
+        for (size_t i = 0; i < dshift.size(); i++) {
+            split(dshift[i].x, &d2[4 * i]);
+            split(dshift[i].y, &d2[4 * i + 2]);
+        }
+        CK(cudaMemcpyAsync(pl->tabdf_binom, b2.data(), sizeof(float) * b2.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(pl->tabdf_tpow, t2.data(), sizeof(float) * t2.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(pl->tabdf_dshift, d2.data(), sizeof(float) * d2.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // the host vectors end with this scope
+    }
     if (pl->upcnt) CK(cudaMemsetAsync(pl->upcnt, 0, sizeof(int32_t) * cap, s));
     CK(cudaMemcpyAsync(pl->tab_tpow, tpow.data(), sizeof(double2) * tpow.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(pl->dev_status, 0, sizeof(int), s));
@@ -453,6 +483,9 @@ int lbf_plan_create_planar(lbf_plan **plan, int M, const int64_t *island_ptr, co
 int lbf_plan_destroy(lbf_plan *pl)
 {
     if (!pl) return LBF_EINVAL;
+    for (auto &row : pl->gexec)
+        for (auto &g : row)
+            if (g) cudaGraphExecDestroy(g);
     for (auto &e : pl->ev)
         if (e) cudaEventDestroy(e);
     if (pl->host_status) cudaFreeHost(pl->host_status);

@@ -36,8 +36,9 @@ __device__ __forceinline__ double warp_sum(double v)
 // sums the block partials in order).
 __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double2 *__restrict__ w,
                        const double *__restrict__ beta, double2 *__restrict__ q,
-                       float2 *__restrict__ q32, double *__restrict__ part,
-                       unsigned *__restrict__ count, double *__restrict__ out, const int *gate)
+                       float2 *__restrict__ q32, cx<df64> *__restrict__ qdf,
+                       double *__restrict__ part, unsigned *__restrict__ count,
+                       double *__restrict__ out, const int *gate)
 {
     if (fmm::gate_closed(gate)) return;
     __shared__ double sh[32];
@@ -53,6 +54,7 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
         }
         if (q) q[i] = qq;
         if (q32) q32[i] = make_float2((float)qq.x, (float)qq.y);
+        if (qdf) qdf[i] = cx<df64>{df64(qq.x), df64(qq.y)};
         acc = beta ? fma(beta[i], s, acc) : acc + s;
     }
     acc = warp_sum(acc);
@@ -195,7 +197,8 @@ __global__ void k_local_coords(int64_t nleaf, const int32_t *__restrict__ leaves
                                const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
                                const int32_t *__restrict__ iy, const int32_t *__restrict__ bg,
                                const int32_t *__restrict__ en, fmm::BoxGeo g,
-                               const double2 *__restrict__ xi, float2 *__restrict__ u32)
+                               const double2 *__restrict__ xi, float2 *__restrict__ u32,
+                               cx<df64> *__restrict__ udf)
 {
     int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -206,7 +209,9 @@ __global__ void k_local_coords(int64_t nleaf, const int32_t *__restrict__ leaves
     double ir = 1.0 / r;
     for (int i = bg[b] + lane; i < en[b]; i += 32) {
         double2 z = xi[i];
-        u32[i] = make_float2((float)((z.x - cx_) * ir), (float)((z.y - cy_) * ir));
+        const double ux = (z.x - cx_) * ir, uy = (z.y - cy_) * ir;
+        if (u32) u32[i] = make_float2((float)ux, (float)uy);
+        if (udf) udf[i] = cx<df64>{df64(ux), df64(uy)};
     }
 }
 
@@ -233,6 +238,7 @@ struct FmmArrays {
     const void *q;
     void *mp, *loc;
     const void *binom, *tpow, *dshift;
+    const void *uloc;  // leaf-local node coordinates (float, double-float), else null
 };
 
 template <typename R, int MODE>
@@ -240,12 +246,13 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
               cudaStream_t s)
 {
     Tree &T = pl->tree;
-    BoxGeo g{T.xmin, T.ymin, T.L};
+    BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
     const int P = a.P;
     const cx<R> *q = (const cx<R> *)a.q;
     cx<R> *mp = (cx<R> *)a.mp, *loc = (cx<R> *)a.loc;
     const R *binom = (const R *)a.binom;
     const cx<R> *tpow = (const cx<R> *)a.tpow, *dsh = (const cx<R> *)a.dshift;
+    const cx<R> *uloc = (const cx<R> *)a.uloc;
     const bool dbl = sizeof(R) == sizeof(double);
     const int kid_up = dbl ? LBF_KERNEL_UP : LBF_KERNEL_UP32;
     const int kid_down = dbl ? LBF_KERNEL_DOWN : LBF_KERNEL_DOWN32;
@@ -254,7 +261,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
         const int wpb = 2;
         LBF_LAUNCH_P(kid_up, fmm::k_up<R>, lbf_cdiv(T.nleaf, wpb), 32 * wpb,
                      up_smem<R>(P, wpb), s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
-                     T.end, T.parent, T.child0, T.nchild, g, P, binom, dsh, pl->xi, pl->u32, q,
+                     T.end, T.parent, T.child0, T.nchild, g, P, binom, dsh, pl->xi, uloc, q,
                      mp, pl->upcnt, gate);
         LBF_CHECK_LAUNCH();
     }
@@ -269,7 +276,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
         if (walk) {
             LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s,
                          (int64_t)0, T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist,
-                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, pl->u32, q, mp, loc,
+                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc,
                          gate, 0);
             LBF_CHECK_LAUNCH();
         } else {
@@ -278,7 +285,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                 if (le <= ls) continue;
                 LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s,
                              ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx,
-                             T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, pl->u32, q, mp, loc,
+                             T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc,
                              gate, 1);
                 LBF_CHECK_LAUNCH();
             }
@@ -286,7 +293,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     }
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
                  32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
-                 T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, pl->u32, q, mp, loc,
+                 T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
                  sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, T.parent, walk);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
@@ -300,20 +307,26 @@ int lbf_fmm_init_attrs()
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_up<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_up<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     return LBF_OK;
 }
 
 // charges and the scalar of one pass: forward q = w sigma with beta . sigma;
 // transposed and real-charge passes q = (sigma, 0) with sum sigma
-static int prep(lbf_plan *pl, const double *sigma, int prec, bool weighted, const int *gate,
+// arithmetic of one pass: float, double, or double-float
+enum class Arith { F32, F64, DF64 };
+
+static int prep(lbf_plan *pl, const double *sigma, Arith ar, bool weighted, const int *gate,
                 cudaStream_t s)
 {
     int nb = (int)std::min<int64_t>(lbf_cdiv(pl->N, 256), 1024);
     LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma, weighted ? pl->w : (const double2 *)nullptr,
                weighted ? pl->beta : (const double *)nullptr,
-               prec == LBF_PREC_FP32 ? (double2 *)nullptr : pl->q,
-               prec == LBF_PREC_FP32 ? pl->q32 : (float2 *)nullptr, pl->red, pl->red_count,
-               pl->bsig, gate);
+               ar == Arith::F64 ? pl->q : (double2 *)nullptr,
+               ar == Arith::F32 ? pl->q32 : (float2 *)nullptr,
+               ar == Arith::DF64 ? (cx<df64> *)pl->qdf : (cx<df64> *)nullptr, pl->red,
+               pl->red_count, pl->bsig, gate);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -324,7 +337,11 @@ static int apply_mode(lbf_plan *pl, const double *sigma, double *v, const int *g
 {
     if (prec == LBF_PREC_FP32 && !pl->q32) return LBF_ENOTBUILT;
     if (pl->opt.matvec == LBF_MATVEC_DIRECT || MODE == fmm::kLeafDeriv) prec = LBF_PREC_FP64;
-    int rc = prep(pl, sigma, prec, weighted, gate, s);
+    const Arith ar = prec == LBF_PREC_FP32 ? Arith::F32
+                     : (pl->qdf && MODE != fmm::kLeafDeriv && pl->opt.matvec == LBF_MATVEC_FMM)
+                         ? Arith::DF64
+                         : Arith::F64;
+    int rc = prep(pl, sigma, ar, weighted, gate, s);
     if (rc) return rc;
     int64_t N = pl->N;
     if (pl->opt.matvec == LBF_MATVEC_DIRECT) {
@@ -333,12 +350,18 @@ static int apply_mode(lbf_plan *pl, const double *sigma, double *v, const int *g
         LBF_CHECK_LAUNCH();
         return LBF_OK;
     }
-    if (prec == LBF_PREC_FP32) {
+    if (ar == Arith::F32) {
         FmmArrays a{pl->P32, pl->q32, pl->mpole32, pl->local32, pl->tab32_binom, pl->tab32_tpow,
-                    pl->tab32_dshift};
+                    pl->tab32_dshift, pl->u32};
         return fmm_apply<float, MODE>(pl, a, sigma, v, gate, s);
     }
-    FmmArrays a{pl->P, pl->q, pl->mpole, pl->local, pl->tab_binom, pl->tab_tpow, pl->tab_dshift};
+    if (ar == Arith::DF64) {
+        FmmArrays a{pl->P, pl->qdf, pl->mpole, pl->local, pl->tabdf_binom, pl->tabdf_tpow,
+                    pl->tabdf_dshift, pl->udf};
+        return fmm_apply<df64, MODE>(pl, a, sigma, v, gate, s);
+    }
+    FmmArrays a{pl->P, pl->q, pl->mpole, pl->local, pl->tab_binom, pl->tab_tpow, pl->tab_dshift,
+                nullptr};
     return fmm_apply<double, MODE>(pl, a, sigma, v, gate, s);
 }
 
@@ -363,26 +386,27 @@ int lbf_multipoles(lbf_plan *pl, const double *x, int P, double2 *mp, const int 
                    cudaStream_t s)
 {
     if (P > LBF_MAX_TERMS) return LBF_EINVAL;
-    int rc = prep(pl, x, LBF_PREC_FP64, false, gate, s);
+    int rc = prep(pl, x, Arith::F64, false, gate, s);
     if (rc) return rc;
     Tree &T = pl->tree;
-    BoxGeo g{T.xmin, T.ymin, T.L};
+    BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
     const int wpb = 2;
     LBF_LAUNCH(fmm::k_up<double>, lbf_cdiv(T.nleaf, wpb), 32 * wpb, up_smem<double>(P, wpb), s,
                T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin, T.end, T.parent, T.child0,
                T.nchild, g, P, pl->tab_binom, (const cx<double> *)pl->tab_dshift, pl->xi,
-               pl->u32, (const cx<double> *)pl->q, (cx<double> *)mp, pl->upcnt, gate);
+               (const cx<double> *)nullptr, (const cx<double> *)pl->q, (cx<double> *)mp,
+               pl->upcnt, gate);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
 
 int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
 {
-    if (!pl->u32) return LBF_OK;
+    if (!pl->u32 && !pl->udf) return LBF_OK;
     Tree &T = pl->tree;
-    fmm::BoxGeo g{T.xmin, T.ymin, T.L};
+    fmm::BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
     LBF_LAUNCH(k_local_coords, lbf_cdiv(T.nleaf, 8), 256, 0, s, T.nleaf, T.leaves, T.level, T.ix,
-               T.iy, T.begin, T.end, g, pl->xi, pl->u32);
+               T.iy, T.begin, T.end, g, pl->xi, pl->u32, (cx<df64> *)pl->udf);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -390,7 +414,7 @@ int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
 int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,
                       const double *t, double *u, cudaStream_t s)
 {
-    int rc = prep(pl, sigma_sorted, LBF_PREC_FP64, true, nullptr, s);
+    int rc = prep(pl, sigma_sorted, Arith::F64, true, nullptr, s);
     if (rc) return rc;
     if (T <= 0) return LBF_OK;
     LBF_LAUNCH(k_evaluate, T, 256, 0, s, pl->N, pl->M, pl->xi, pl->q, pl->bsig, a, pl->centres, T,

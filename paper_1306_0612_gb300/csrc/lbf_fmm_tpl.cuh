@@ -13,6 +13,9 @@
 // c_i = Im sum_{j != i} q_j / (xi_j - xi_i) = -Im phi(xi_i).
 #pragma once
 
+#include <type_traits>
+
+#include "lbf_df64.cuh"
 #include "lbf_internal.cuh"
 
 namespace fmm {
@@ -23,6 +26,15 @@ template <typename R> struct __align__(2 * sizeof(R)) cx {
 
 __device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ df64 fm(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
+
+// float and double-float read each node's leaf-local coordinate (rounded once per
+// geometry) and move it between box frames by powers of two and integer offsets;
+// double forms node offsets from the double positions
+template <typename R> constexpr bool kLocal = !std::is_same<R, double>::value;
+// largest level gap over which a leaf-local coordinate is rescaled into a coarser
+// box's frame (its rounding grows by 2 per level; wider gaps use the positions)
+template <typename R> constexpr int kMaxGap = std::is_same<R, float>::value ? 3 : 12;
 
 template <typename R> __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
 template <typename R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b)
@@ -48,6 +60,7 @@ __device__ __forceinline__ double rcp(double a)
     return fma(x, e, x);
 }
 __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ df64 rcp(df64 a) { return df_rcp(a); }
 
 template <typename R> __device__ __forceinline__ cx<R> crcp(cx<R> a)
 {
@@ -65,6 +78,8 @@ template <typename R> __device__ __forceinline__ R wsum(R v)
 
 struct BoxGeo {
     double xmin, ymin, L;
+    float invLf;  // 1/L rounded to float: 1/r of a level-l box is invLf 2^(l+1)
+    df64 invLd;   // 1/L as a double-float
 };
 
 __device__ __forceinline__ void box_centre(const BoxGeo &g, int l, int ix, int iy, double &cx_,
@@ -82,6 +97,39 @@ template <> __device__ __forceinline__ float pow2<float>(int e) { return __int_a
 template <> __device__ __forceinline__ double pow2<double>(int e)
 {
     return __longlong_as_double((long long)(1023 + e) << 52);
+}
+template <> __device__ __forceinline__ df64 pow2<df64>(int e) { return df64(pow2<float>(e)); }
+
+// 1/r of a level-l box in R without double arithmetic (float, double-float)
+template <typename R> __device__ __forceinline__ R inv_half_width(const BoxGeo &g, int l);
+template <> __device__ __forceinline__ float inv_half_width<float>(const BoxGeo &g, int l)
+{
+    return g.invLf * pow2<float>(l + 1);
+}
+template <> __device__ __forceinline__ df64 inv_half_width<df64>(const BoxGeo &g, int l)
+{
+    return df_ldexp(g.invLd, pow2<float>(l + 1));
+}
+
+// an expansion coefficient written by another block of the same launch (through L2)
+__device__ __forceinline__ cx<double> ldcg_cx(const cx<double> *p)
+{
+    double2 v = __ldcg((const double2 *)p);
+    return cx<double>{v.x, v.y};
+}
+__device__ __forceinline__ cx<float> ldcg_cx(const cx<float> *p)
+{
+    float2 v = __ldcg((const float2 *)p);
+    return cx<float>{v.x, v.y};
+}
+__device__ __forceinline__ cx<df64> ldcg_cx(const cx<df64> *p)
+{
+    float4 v = __ldcg((const float4 *)p);
+    return cx<df64>{df64(v.x, v.y, 0), df64(v.z, v.w, 0)};
+}
+template <typename R> __device__ __forceinline__ cx<R> offset_cx(float2 o)
+{
+    return cx<R>{R(o.x), R(o.y)};
 }
 
 // (c_a - c_b) / r_b for box a (level la) and box b (level lb), per axis
@@ -102,10 +150,6 @@ __device__ __forceinline__ float2 centre_offset(int la, int ax, int ay, int lb, 
     return make_float2((float)(int)dx, (float)(int)dy);
 }
 
-// Largest level gap over which the float path rescales a node's leaf-local
-// coordinate into another box's frame (the rounding of the leaf-local value grows
-// by 2 per level); wider gaps form the offset from the double node position.
-constexpr int kMaxGapF32 = 3;
 
 // shift tables for the four child positions: d^k and (2d)^-k, k <= LBF_MAX_TERMS
 template <typename R> __device__ __forceinline__ const cx<R> *dpow(const cx<R> *dtab, int c)
@@ -126,7 +170,7 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
                      const int32_t *__restrict__ en, const int32_t *__restrict__ parent,
                      const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
                      BoxGeo g, int P, const R *__restrict__ binom, const cx<R> *__restrict__ dtab,
-                     const double2 *__restrict__ xi, const float2 *__restrict__ u32,
+                     const double2 *__restrict__ xi, const cx<R> *__restrict__ uloc,
                      const cx<R> *__restrict__ q, cx<R> *mp, int *cnt, const int *gate)
 {
     if (gate_closed(gate)) return;
@@ -146,17 +190,19 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
     if (t >= nleaf) return;
     int b = leaves[t];
     {
-        double cxd, cyd, r;
-        box_centre(g, level[b], ix[b], iy[b], cxd, cyd, r);
-        double ir = 1.0 / r;
+        double cxd = 0, cyd = 0, ir = 0;
+        if constexpr (!kLocal<R>) {  // float and double-float read leaf-local coordinates
+            double r;
+            box_centre(g, level[b], ix[b], iy[b], cxd, cyd, r);
+            ir = 1.0 / r;
+        }
         cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
         for (int base = bg[b]; base < en[b]; base += 32) {
             int j = base + lane;
             cx<R> z = mk<R>(0, 0), term = mk<R>(0, 0);
             if (j < en[b]) {
-                if constexpr (sizeof(R) == 4) {
-                    float2 uu = u32[j];
-                    z = mk<R>(uu.x, uu.y);
+                if constexpr (kLocal<R>) {
+                    z = uloc[j];
                 } else {
                     double2 x = xi[j];
                     z = mk<R>((R)((x.x - cxd) * ir), (R)((x.y - cyd) * ir));
@@ -205,16 +251,8 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
             int d = (ix[c] & 1) + 2 * (iy[c] & 1);
             const cx<R> *inv = d2inv(dtab, d);
             for (int k = lane; k < P; k += 32) {
-                cx<R> a;
-                const cx<R> *src = &mp[(int64_t)c * P + k];
                 // written by other warps in this launch: read through L2
-                if (sizeof(R) == 8) {
-                    double2 v = __ldcg((const double2 *)src);
-                    a = mk<R>((R)v.x, (R)v.y);
-                } else {
-                    float2 v = __ldcg((const float2 *)src);
-                    a = mk<R>((R)v.x, (R)v.y);
-                }
+                const cx<R> a = ldcg_cx(&mp[(int64_t)c * P + k]);
                 A[k] = cmul(a, inv[k]);
             }
             __syncwarp();
@@ -253,7 +291,7 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                        const int32_t *__restrict__ en, BoxGeo g, int P,
                        const R *__restrict__ binom, const cx<R> *__restrict__ tpow,
                        const cx<R> *__restrict__ dtab, const double2 *__restrict__ xi,
-                       const float2 *__restrict__ u32, const cx<R> *__restrict__ q,
+                       const cx<R> *__restrict__ uloc, const cx<R> *__restrict__ q,
                        const cx<R> *__restrict__ mp, cx<R> *__restrict__ loc, const int *gate,
                        int with_l2l)
 {
@@ -371,21 +409,28 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     }
     // P2L: (-1)^l sum_j q_j tau_j^(l+1), tau_j = r / (c - xi_j)  (times 1/r below)
     const int lb = level[b];
-    double cxd, cyd, r;
-    box_centre(g, lb, bx, by, cxd, cyd, r);
-    double ir = 1.0 / r;
+    double cxd = 0, cyd = 0, ir = 0;
+    bool have_c = false;
+    auto need_centre = [&]() {  // double centre: the double path and float fallbacks only
+        if (have_c) return;
+        double r;
+        box_centre(g, lb, bx, by, cxd, cyd, r);
+        ir = 1.0 / r;
+        have_c = true;
+    };
+    if constexpr (!kLocal<R>) need_centre();
     for (int xq = 0; xq < nx[b]; xq++) {
         int s = xlist[b * 16 + xq];
-        // float: the source's leaf-local coordinate rescaled into this box's frame
+        // float, double-float: the source's leaf-local coordinate rescaled into this box's frame
         bool local = false;
-        float fs = 0.f;
-        float2 os = make_float2(0.f, 0.f);
-        if constexpr (sizeof(R) == 4) {
+        R fs = R(0.0f);
+        cx<R> os = mk<R>(R(0.0f), R(0.0f));
+        if constexpr (kLocal<R>) {
             const int ls = level[s];
-            local = lb >= ls && lb - ls <= kMaxGapF32;
+            local = lb >= ls && lb - ls <= kMaxGap<R>;
             if (local) {
-                fs = pow2<float>(lb - ls);
-                os = centre_offset(ls, ix[s], iy[s], lb, bx, by);
+                fs = R(pow2<float>(lb - ls));
+                os = offset_cx<R>(centre_offset(ls, ix[s], iy[s], lb, bx, by));
             }
         }
         for (int base = bg[s]; base < en[s]; base += 32) {
@@ -393,9 +438,10 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
             cx<R> tau = mk<R>(0, 0), term = mk<R>(0, 0);
             if (j < en[s]) {
                 if (local) {
-                    float2 uu = u32[j];
-                    tau = crcp(mk<R>(-fmaf(uu.x, fs, os.x), -fmaf(uu.y, fs, os.y)));
+                    const cx<R> uu = uloc[j];
+                    tau = crcp(mk<R>(-(uu.x * fs + os.x), -(uu.y * fs + os.y)));
                 } else {
+                    need_centre();
                     double2 z = xi[j];
                     tau = crcp(mk<R>((R)((cxd - z.x) * ir), (R)((cyd - z.y) * ir)));
                 }
@@ -419,7 +465,9 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
             __syncwarp();
         }
     }
-    const R irr = (R)ir;
+    R irr;
+    if constexpr (kLocal<R>) irr = inv_half_width<R>(g, lb);
+    else irr = (R)ir;
     if (l0 < P) loc[b * P + l0] = mk<R>(accL0.x + accF0.x * irr, accL0.y + accF0.y * irr);
     if (l1 < P) loc[b * P + l1] = mk<R>(accL1.x + accF1.x * irr, accL1.y + accF1.y * irr);
 }
@@ -452,7 +500,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const int32_t *__restrict__ en, const int32_t *__restrict__ uptr,
                        const int32_t *__restrict__ uidx, const int32_t *__restrict__ wptr,
                        const int32_t *__restrict__ widx, BoxGeo g, int P,
-                       const double2 *__restrict__ xi, const float2 *__restrict__ u32,
+                       const double2 *__restrict__ xi, const cx<R> *__restrict__ uloc,
                        const cx<R> *__restrict__ q, const cx<R> *__restrict__ mp,
                        const cx<R> *__restrict__ loc, const double *__restrict__ sigma,
                        const double *__restrict__ dself, const double2 *__restrict__ w,
@@ -461,7 +509,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        int walk)
 {
     if (gate_closed(gate)) return;
-    constexpr bool kF32 = sizeof(R) == 4;
+    constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
     __shared__ cx<R> sx[kLeafWarps][kSrcChunk];
     __shared__ cx<R> sq[kLeafWarps][kSrcChunk];
     __shared__ int32_t sj[kLeafWarps][kSrcChunk];
@@ -470,10 +518,22 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
     if (t >= nleaf) return;
     const int b = leaves[t];
     const int lt = level[b], tx = ix[b], ty = iy[b];
-    double cxd, cyd, r;
-    box_centre(g, lt, tx, ty, cxd, cyd, r);
-    const double ir = 1.0 / r;
-    const R irr = (R)ir;
+    double cxd = 0, cyd = 0, ir = 0;
+    bool have_c = false;
+    auto need_centre = [&]() {  // double centre: the double path and float fallbacks only
+        if (have_c) return;
+        double r;
+        box_centre(g, lt, tx, ty, cxd, cyd, r);
+        ir = 1.0 / r;
+        have_c = true;
+    };
+    R irr;
+    if constexpr (kF32) {
+        irr = inv_half_width<R>(g, lt);
+    } else {
+        need_centre();
+        irr = (R)ir;
+    }
     const cx<R> *lb = loc + (int64_t)b * P;
     for (int tb = bg[b]; tb < en[b]; tb += 32) {
         const int nt = min(32, en[b] - tb);
@@ -488,8 +548,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         cx<R> phi = mk<R>(0, 0);  // far field: Phi (or Phi' in kLeafDeriv)
         if (act) {
             if constexpr (kF32) {
-                float2 uu = u32[i];
-                u = mk<R>(uu.x, uu.y);
+                u = uloc[i];
             } else {
                 double2 zi = xi[i];
                 u = mk<R>((zi.x - cxd) * ir, (zi.y - cyd) * ir);
@@ -526,11 +585,11 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                 R isr;
                 bool local = false;
                 if constexpr (kF32) {
-                    local = ls >= lt && ls - lt <= kMaxGapF32;
+                    local = ls >= lt && ls - lt <= kMaxGap<R>;
                     if (local) {
-                        const float f = pow2<float>(ls - lt);
-                        const float2 o = centre_offset(lt, tx, ty, ls, ix[s], iy[s]);
-                        zs = mk<R>(fmaf(u.x, f, o.x), fmaf(u.y, f, o.y));
+                        const R f = R(pow2<float>(ls - lt));
+                        const cx<R> o = offset_cx<R>(centre_offset(lt, tx, ty, ls, ix[s], iy[s]));
+                        zs = mk<R>(u.x * f + o.x, u.y * f + o.y);
                         isr = irr * f;
                     }
                 }
@@ -597,14 +656,14 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             const int s = uidx[uq];
             int sb = bg[s], se = en[s];
             bool local = false;
-            float fs = 0.f;
-            float2 os = make_float2(0.f, 0.f);
+            R fs = R(0.0f);
+            cx<R> os = mk<R>(R(0.0f), R(0.0f));
             if constexpr (kF32) {
                 const int ls = level[s];
                 local = ls >= lt && ls - lt <= 16;
                 if (local) {
-                    fs = pow2<float>(lt - ls);
-                    os = centre_offset(ls, ix[s], iy[s], lt, tx, ty);
+                    fs = R(pow2<float>(lt - ls));
+                    os = offset_cx<R>(centre_offset(ls, ix[s], iy[s], lt, tx, ty));
                 }
             }
             while (sb < se) {
@@ -612,9 +671,10 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                 for (int m = lane; m < take; m += 32) {
                     cx<R> zr;  // (z_j - c)/r
                     if (local) {
-                        float2 uu = u32[sb + m];
-                        zr = mk<R>(fmaf(uu.x, fs, os.x), fmaf(uu.y, fs, os.y));
+                        const cx<R> uu = uloc[sb + m];
+                        zr = mk<R>(uu.x * fs + os.x, uu.y * fs + os.y);
                     } else {
+                        need_centre();
                         double2 zs = xi[sb + m];
                         zr = mk<R>((R)((zs.x - cxd) * ir), (R)((zs.y - cyd) * ir));
                     }

@@ -23,6 +23,7 @@ extern std::atomic<int64_t> g_lbf_launches;
 
 // Tracing: event pair around a launch when lbf_profile_enable(1) is on.
 void lbf_prof_mark(int id, int begin, cudaStream_t s);
+void lbf_prof_capture(bool on);  // this thread is capturing a CUDA graph: no marks
 #define LBF_LAUNCH_P(id, kernel, grid, block, smem, stream, ...)           \
     do {                                                                   \
         lbf_prof_mark((id), 1, (stream));                                  \
@@ -135,6 +136,10 @@ struct lbf_plan {
     int P32 = 0;
     float2 *q32 = nullptr, *mpole32 = nullptr, *local32 = nullptr;
     float2 *u32 = nullptr;  // per node: (xi - c)/r about the centre c, half-width r of its leaf
+    // double-float operator (opt.fmm64): charges, leaf-local coordinates (pairs of
+    // float pairs, 16 B), and the translation tables; expansions reuse mpole/local
+    void *qdf = nullptr, *udf = nullptr;
+    void *tabdf_binom = nullptr, *tabdf_tpow = nullptr, *tabdf_dshift = nullptr;
     float *tab32_binom = nullptr;
     float2 *tab32_tpow = nullptr, *tab32_dshift = nullptr;
     double *gr = nullptr, *gd = nullptr;  // refinement residual and correction
@@ -162,6 +167,9 @@ struct lbf_plan {
     int *dev_status = nullptr;
     int *host_status = nullptr;  // pinned
     cudaEvent_t ev[2] = {nullptr, nullptr};  // GMRES chunk markers (no device memory)
+    double *vstep = nullptr;                  // the Arnoldi input of a graph-replayed step
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [prec][transpose]
+    int64_t gnodes[2][2] = {{0, 0}, {0, 0}};  // kernels per replay
     double *host_scalars = nullptr;  // pinned
 };
 

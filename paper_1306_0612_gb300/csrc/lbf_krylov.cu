@@ -151,6 +151,15 @@ __global__ void k_add_last(int M, const double *__restrict__ c, double *__restri
     if (m < M) out[m] += c[M - 1];
 }
 
+// the Arnoldi input v_j of the current step (j from the device state) into a fixed buffer
+__global__ void k_copy_vj(int64_t n, const double *__restrict__ V, int64_t ldv,
+                          const GmresState *__restrict__ st, double *__restrict__ out)
+{
+    if (st->go == 0) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = V[(int64_t)st->j * ldv + i];
+}
+
 // ---- GMRES kernels --------------------------------------------------------------------
 
 // Partial dot products of w with V[0..nv) over one block's row chunk; the last block
@@ -560,6 +569,66 @@ static int read_state(lbf_plan *pl, GmresState *h, cudaStream_t s)
 // Restarted GMRES on P^-1 A x = b (sorted order, n unknowns) from x (x_given) or
 // from 0, with the operator in precision prec, stopping at ||b - P^-1 A x|| <=
 // tol * (*bnorm_dev).  Counts operator applications in pl->stats.
+// One Arnoldi step on stream s: w = op(v_j), CGS2 against V, Givens update, v_{j+1}.
+// from_state: the input is copied from V by the device's j (graph-replayable);
+// otherwise v_j is addressed from the host's k.
+static int arnoldi_step(lbf_plan *pl, int opc, int prec, int k, bool from_state, cudaStream_t s)
+{
+    int64_t n = pl->n;
+    int m = pl->opt.restart;
+    double *w = pl->gw, *V = pl->V;
+    int64_t ldv = pl->ldv;
+    int nblk = pl->mdot_blocks;
+    double *hbuf = pl->H + (int64_t)(m + 1) * m;
+    double *cs = hbuf + 2 * (m + 1), *sn = cs + m, *gv = sn + m;
+    unsigned *count = pl->red_count + 1;
+    size_t smem = sizeof(double) * (size_t)(kRowsPerChunk + 2 * (m + 2));
+    const double *vj = V + (int64_t)k * ldv;
+    if (from_state) {
+        LBF_LAUNCH(k_copy_vj, lbf_cdiv(n, 256), 256, 0, s, n, V, ldv, pl->gs, pl->vstep);
+        vj = pl->vstep;
+    }
+    int rc = lbf_apply_op_sorted(pl, opc, vj, w, &pl->gs->go, s, prec);
+    if (rc) return rc;
+    for (int mode = 0; mode < 3; mode++)
+        LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w, pl->gpart,
+                     count, hbuf, pl->H, cs, sn, gv, pl->gs, mode);
+    LBF_LAUNCH(k_scale_next, nblk, 256, 0, s, n, w, V, ldv, pl->gs);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// The captured step graph of (prec, transpose), built on first use; null when graphs
+// are off for this plan or the stream cannot capture (the legacy default stream).
+static cudaGraphExec_t step_graph(lbf_plan *pl, int opc, int prec, cudaStream_t s)
+{
+    const int g = pl->opt.graphs;
+    if (g == 0 || (g < 0 && pl->N > (1 << 18)) || s == nullptr || !pl->vstep) return nullptr;
+    const int pi = prec == LBF_PREC_FP32 ? 1 : 0, ti = (opc & LBF_OP_TRANSPOSE) ? 1 : 0;
+    if (pl->gexec[pi][ti]) return pl->gexec[pi][ti];
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    lbf_prof_capture(true);
+    const int64_t n0 = g_lbf_launches.load();
+    int rc = arnoldi_step(pl, opc, prec, 0, true, s);
+    // captured, not launched: count them at every replay instead
+    pl->gnodes[pi][ti] = g_lbf_launches.load() - n0;
+    g_lbf_launches.fetch_sub(pl->gnodes[pi][ti]);
+    lbf_prof_capture(false);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == LBF_OK && e == cudaSuccess && graph &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+        pl->gexec[pi][ti] = exec;
+    else
+        cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return pl->gexec[pi][ti];
+}
+
 static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnorm_dev, double *x,
                       bool x_given, double tol, int maxit, int prec, cudaStream_t s,
                       GmresState *out)
@@ -588,7 +657,9 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
     LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1, bnorm_dev);
     LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
     LBF_CHECK_LAUNCH();
-    size_t smem = sizeof(double) * (size_t)(kRowsPerChunk + 2 * (m + 2));
+    cudaGraphExec_t sg = step_graph(pl, opc, prec, s);
+    const int64_t sg_nodes =
+        pl->gnodes[prec == LBF_PREC_FP32 ? 1 : 0][(opc & LBF_OP_TRANSPOSE) ? 1 : 0];
     GmresState hs;
     for (;;) {
         if ((rc = read_state(pl, &hs, s))) return rc;
@@ -610,13 +681,12 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
             int k1 = std::min(steps, k0 + chunk);
             for (int k = k0; k < k1; k++) {
                 // w = P^-1 A v_j: within a cycle the device's j equals the host's k
-                const double *vj = V + (int64_t)k * ldv;
-                if ((rc = lbf_apply_op_sorted(pl, opc, vj, w, &pl->gs->go, s, prec))) return rc;
-                for (int mode = 0; mode < 3; mode++)
-                    LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w,
-                                 pl->gpart, count, hbuf, pl->H, cs, sn, gv, pl->gs, mode);
-                LBF_LAUNCH(k_scale_next, nblk, 256, 0, s, n, w, V, ldv, pl->gs);
-                LBF_CHECK_LAUNCH();
+                if (sg) {
+                    LBF_CUDA(cudaGraphLaunch(sg, s));
+                    g_lbf_launches.fetch_add(sg_nodes, std::memory_order_relaxed);
+                } else if ((rc = arnoldi_step(pl, opc, prec, k, false, s))) {
+                    return rc;
+                }
             }
             k0 = k1;
             LBF_CUDA(cudaMemcpyAsync((char *)pl->host_scalars + 64 * (1 + slot), pl->gs,

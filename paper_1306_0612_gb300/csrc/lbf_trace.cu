@@ -52,9 +52,15 @@ __global__ void k_counts(int64_t nbox, const int32_t *__restrict__ level,
 
 }  // namespace
 
+namespace {
+thread_local bool t_capturing = false;
+}
+
+void lbf_prof_capture(bool on) { t_capturing = on; }
+
 void lbf_prof_mark(int id, int begin, cudaStream_t s)
 {
-    if (!g_prof.on) return;
+    if (!g_prof.on || t_capturing) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (!g_prof.on || g_prof.next >= g_prof.pool.size()) return;
     cudaEvent_t ev = g_prof.pool[g_prof.next++];

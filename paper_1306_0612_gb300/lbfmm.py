@@ -42,7 +42,8 @@ class lbf_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("p", C.c_int),
                 ("leaf_size", C.c_int), ("max_depth", C.c_int), ("matvec", C.c_int),
                 ("border", C.c_int), ("box_capacity", C.c_int64), ("precision", C.c_int),
-                ("p32", C.c_int), ("inner_tol", C.c_double), ("max_refine", C.c_int)]
+                ("p32", C.c_int), ("inner_tol", C.c_double), ("max_refine", C.c_int),
+                ("graphs", C.c_int), ("fmm64", C.c_int)]
 
 
 class lbf_batch_item(C.Structure):
