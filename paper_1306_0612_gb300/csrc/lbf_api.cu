@@ -145,6 +145,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         pl->P32 = P32;
         pl->q32 = A.get<float2>(N);
         pl->u32 = A.get<float2>(N);
+        pl->anc = A.get<int32_t>(cap * LBF_ANC_STRIDE);
         if (o.matvec == LBF_MATVEC_FMM) {
             pl->mpole32 = A.get<float2>(cap * P32);
             pl->local32 = A.get<float2>(cap * P32);
@@ -186,6 +187,12 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         B.p2l_src = A.get<int32_t>(B.pair_cap);
         B.near_ptr = A.get<int32_t>(cap + 1);
         B.near_src = A.get<int32_t>(B.pair_cap);
+        B.chunk_leaf = A.get<int32_t>(B.pair_cap);
+        B.chunk_k = A.get<int32_t>(B.pair_cap);
+        B.nodebase = A.get<int32_t>(N + 1);
+        // partial sums: sum over leaves of nodes x ceil(direct centres / 32) <= N + 2 pair_cap
+        B.partial_cap = N + 2 * B.pair_cap;
+        B.partial = A.get<double>(B.partial_cap);
         B.cp2l = A.get<int32_t>((int64_t)M + 1);
         B.cnear = A.get<int32_t>((int64_t)M + 1);
         B.loc = A.get<double2>(cap * B.P);

@@ -25,7 +25,9 @@
 // radius rho_k): the multipole of the island where |xi_m - z_k| >= 3 R_k, its
 // inner expansion where |xi_m - z_k| <= rho_k / 3, and a direct sum otherwise.
 #include <algorithm>
+#include <type_traits>
 
+#include "lbf_df64.cuh"
 #include "lbf_internal.cuh"
 
 namespace {
@@ -38,6 +40,7 @@ template <typename R> struct __align__(2 * sizeof(R)) cz {
 };
 __device__ __forceinline__ double fmr(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmr(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ df64 fmr(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
 template <typename R> __device__ __forceinline__ cz<R> zmul(cz<R> a, cz<R> b)
 {
     return cz<R>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
@@ -51,8 +54,6 @@ __device__ __forceinline__ cz<double> zinv(cz<double> a)
     double d = 1.0 / (a.x * a.x + a.y * a.y);
     return cz<double>{a.x * d, -a.y * d};
 }
-__device__ __forceinline__ double rlog(double v) { return log(v); }
-__device__ __forceinline__ float rlog(float v) { return __logf(v); }
 
 template <typename R> __device__ __forceinline__ R wsum(R v)
 {
@@ -391,6 +392,33 @@ __global__ void k_mp_schur_direct(int M, const int64_t *__restrict__ ptr,
     }
 }
 
+// direct centres of each leaf in chunks of 32 (a warp each at application time)
+__global__ void k_chunk_count(int64_t nbox, const int32_t *__restrict__ nptr, int32_t *__restrict__ nch)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b < nbox) nch[b] = (nptr[b + 1] - nptr[b] + 31) / 32;
+}
+
+__global__ void k_chunk_fill(int64_t nbox, const int32_t *__restrict__ nch,
+                             const int32_t *__restrict__ base, int32_t *__restrict__ cleaf,
+                             int32_t *__restrict__ ck)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    for (int k = 0; k < nch[b]; k++) {
+        cleaf[base[b] + k] = (int32_t)b;
+        ck[base[b] + k] = k;
+    }
+}
+
+__global__ void k_node_chunks(int64_t N, const int32_t *__restrict__ leaf_of,
+                              const int32_t *__restrict__ nch, int32_t *__restrict__ cnt)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) cnt[i] = nch[leaf_of[i]];
+    if (i == N) cnt[i] = 0;
+}
+
 // ---- per application ---------------------------------------------------------------
 
 // P2L of the log sources into every box (warp per box; lanes take centres, terms pass
@@ -421,21 +449,34 @@ __global__ void k_mp_p2l(int64_t nbox, int P, int M, const int32_t *__restrict__
         Lam = wsum(Lam);
         if (lane == 0) { sums[0] = Y; sums[1] = Lam; }
     }
+    if (ptr[b] == ptr[b + 1] && b != 0) {  // no centres: a zero expansion
+        for (int l = lane; l < P; l += 32) loc[b * P + l] = cz<R>{R(0), R(0)};
+        return;
+    }
     double cx, cy, r;
     centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
+    const double ir = 1.0 / r;
     double b0 = 0.0;
-    cz<R> a0{0, 0}, a1{0, 0};
+    cz<R> a0{R(0), R(0)}, a1{R(0), R(0)};
     for (int base = ptr[b]; base < ptr[b + 1]; base += 32) {
         int q = base + lane;
-        cz<R> tau{0, 0};
-        R ym = 0;
+        cz<R> tau{R(0), R(0)};
+        R ym = R(0);
         if (q < ptr[b + 1]) {
             int m = src[q];
             double2 xm = xc[m];
             double dx = cx - xm.x, dy = cy - xm.y;
-            b0 += y[m] * 0.5 * log(dx * dx + dy * dy);
-            cz<double> t = zinv(cz<double>{dx / r, dy / r});
-            tau = cz<R>{(R)t.x, (R)t.y};
+            if constexpr (std::is_same<R, float>::value) {
+                // the float operator: the difference in double, the rest in float
+                const float fx = (float)(dx * ir), fy = (float)(dy * ir);
+                const float d2 = fx * fx + fy * fy, id = __fdividef(1.0f, d2);
+                b0 += y[m] * (double)(0.5f * __logf(d2 * (float)(r * r)));
+                tau = cz<R>{fx * id, -fy * id};
+            } else {
+                b0 += y[m] * 0.5 * log(dx * dx + dy * dy);
+                cz<double> t = zinv(cz<double>{dx * ir, dy * ir});
+                tau = cz<R>{(R)t.x, (R)t.y};
+            }
             ym = (R)y[m];
         }
         cz<R> pw{ym * tau.x, ym * tau.y};  // y tau^l, l = 1
@@ -512,6 +553,40 @@ __global__ void k_mp_l2l(int64_t ls, int64_t le, int P, const int32_t *__restric
     }
 }
 
+// The centres a leaf sums directly, 32 per warp: for every node i of the leaf,
+// partial[nodebase[i] + k] = sum over chunk k of y_m log|xi_i - xi_m| (in double; the
+// float operator takes the log in float).  Spreading a long list over many warps keeps
+// one leaf from holding the whole launch.
+template <typename R>
+__global__ void k_mp_near(int64_t nchunks, const int32_t *__restrict__ cleaf,
+                          const int32_t *__restrict__ ck, const int32_t *__restrict__ nptr,
+                          const int32_t *__restrict__ nsrc, const int32_t *__restrict__ bg,
+                          const int32_t *__restrict__ en, const double2 *__restrict__ xi,
+                          const double2 *__restrict__ xc, const double *__restrict__ y,
+                          const int32_t *__restrict__ nodebase, double *__restrict__ partial,
+                          const int *gate)
+{
+    if (gate && *gate == 0) return;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nchunks) return;
+    const int b = cleaf[w], k = ck[w];
+    const int q0 = nptr[b] + 32 * k, q1 = min(nptr[b + 1], q0 + 32);
+    for (int i = bg[b] + lane; i < en[b]; i += 32) {
+        const double2 zi = xi[i];
+        double acc = 0.0;
+        for (int q = q0; q < q1; q++) {
+            const int m = nsrc[q];
+            const double ex = zi.x - xc[m].x, ey = zi.y - xc[m].y;
+            if constexpr (std::is_same<R, float>::value)
+                acc += y[m] * (double)(0.5f * __logf((float)(ex * ex + ey * ey)));
+            else
+                acc += y[m] * 0.5 * log(ex * ex + ey * ey);
+        }
+        partial[nodebase[i] + k] = acc;
+    }
+}
+
 // out_i = x_i + v_i + s (E y)_i at every node (Morton order), v nullable: L2P of the
 // node's leaf, its direct centres, and the centres summed directly everywhere.
 template <typename R>
@@ -525,7 +600,8 @@ __global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
                           const double *__restrict__ x, const double *__restrict__ v, double s,
                           double *__restrict__ out, const int *gate,
                           const int32_t *__restrict__ parent, const float2 *__restrict__ u32,
-                          int walk)
+                          int walk, const cz<R> *__restrict__ uloc,
+                          const int32_t *__restrict__ nodebase, const double *__restrict__ partial)
 {
     if (gate && *gate == 0) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -534,9 +610,15 @@ __global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
     double2 zi = xi[i];
     double lsum = 0.0;
     if (!walk) {
-        double cx, cy, r;
-        centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
-        cz<R> u{(R)((zi.x - cx) / r), (R)((zi.y - cy) / r)};
+        cz<R> u;
+        if (uloc) {  // the leaf-local coordinate of the double-float operator
+            u = uloc[i];
+        } else {
+            double cx, cy, r;
+            centre_of(g, level[b], ix[b], iy[b], cx, cy, r);
+            const double ir = 1.0 / r;
+            u = cz<R>{(R)((zi.x - cx) * ir), (R)((zi.y - cy) * ir)};
+        }
         const cz<R> *lb = loc + (int64_t)b * P;
         cz<R> acc = lb[P - 1];
         for (int l = P - 2; l >= 0; l--) acc = zfma(acc, u, lb[l]);
@@ -545,12 +627,13 @@ __global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
         // float: every ancestor's own expansion at the node (no L2L chain), from the
         // node's leaf-local coordinate u: (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s
         const float2 uu = u32[i];
-        const int lv = level[b];
+        const int lv = level[b], bx = ix[b], by = iy[b];
+        const int32_t *ab = parent + (int64_t)b * LBF_ANC_STRIDE;  // the ancestor table
         R acc = 0;
-        for (int a = b; a >= 0 && level[a] >= 2; a = parent[a]) {
-            const int sh = lv - level[a];
+        for (int sh = 0; sh <= lv - 2; sh++) {
+            const int a = ab[sh];
             const R sc = (R)__int_as_float((127 - sh) << 23);  // 2^-sh
-            const int dxi = ix[b] - (ix[a] << sh), dyi = iy[b] - (iy[a] << sh);
+            const int dxi = bx & ((1 << sh) - 1), dyi = by & ((1 << sh) - 1);
             cz<R> ua{(R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + (R)uu.x * sc,
                      (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + (R)uu.y * sc};
             const cz<R> *la = loc + (int64_t)a * P;
@@ -560,11 +643,7 @@ __global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
         }
         lsum = (double)acc;
     }
-    for (int q = nptr[b]; q < nptr[b + 1]; q++) {
-        int m = nsrc[q];
-        double ex = zi.x - xc[m].x, ey = zi.y - xc[m].y;
-        lsum += y[m] * 0.5 * (double)rlog((R)(ex * ex + ey * ey));
-    }
+    for (int q = nodebase[i]; q < nodebase[i + 1]; q++) lsum += partial[q];  // direct centres
     for (int q = 0; q < nglob; q++) {
         int m = glob[q];
         double ex = zi.x - xc[m].x, ey = zi.y - xc[m].y;
@@ -604,6 +683,8 @@ int lbf_border_init_attrs()
     LBF_CUDA(cudaFuncSetAttribute(k_mp_p2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     LBF_CUDA(cudaFuncSetAttribute(k_mp_l2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     LBF_CUDA(cudaFuncSetAttribute(k_mp_l2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    LBF_CUDA(cudaFuncSetAttribute(k_mp_p2l<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    LBF_CUDA(cudaFuncSetAttribute(k_mp_l2l<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return LBF_OK;
 }
 
@@ -712,6 +793,28 @@ int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, i
     }
     B.n_p2l = n_p2l;
     B.n_near = n_near;
+    {
+        // the direct centres in chunks of 32 per leaf, and per node its partial-sum slots
+        const int64_t nb = T.nbox;
+        int32_t *nch = w2, *cbase = w2 + nb + 1, *sc = w2 + 2 * (nb + 1);
+        const int64_t sc_len = w2_len - 2 * (nb + 1);
+        LBF_LAUNCH(k_chunk_count, lbf_cdiv(nb, 256), 256, 0, s, nb, B.near_ptr, nch);
+        LBF_CHECK_LAUNCH();
+        if ((rc = lbf_scan_i32(nch, cbase, nb, sc, sc_len, s))) return rc;
+        int32_t lastb = 0, lastn = 0;
+        if ((rc = read_i32(cbase + nb - 1, &lastb, s)) || (rc = read_i32(nch + nb - 1, &lastn, s)))
+            return rc;
+        B.nchunks = (int64_t)lastb + lastn;
+        if (B.nchunks > B.pair_cap) return LBF_EWORKSPACE;
+        LBF_LAUNCH(k_chunk_fill, lbf_cdiv(nb, 256), 256, 0, s, nb, nch, cbase, B.chunk_leaf, B.chunk_k);
+        LBF_LAUNCH(k_node_chunks, lbf_cdiv(N + 1, 256), 256, 0, s, N, B.leaf_of, nch, B.nodebase);
+        LBF_CHECK_LAUNCH();
+        if ((rc = lbf_scan_i32(B.nodebase, B.nodebase, N + 1, sc, sc_len, s))) return rc;
+        int32_t np = 0;
+        if ((rc = read_i32(B.nodebase + N, &np, s))) return rc;
+        B.npartial = np;
+        if (B.npartial > B.partial_cap) return LBF_EWORKSPACE;
+    }
     // the walk and pair scratch is free again: a counter and the list of direct entries
     int32_t *dcount = w2, *dlist = w2 + 1;
     const int dcap = (int)std::min<int64_t>(w2_len - 1, INT32_MAX);
@@ -742,10 +845,38 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
                    (cz<float> *)B.loc32, B.sums, gate);
         // float: no L2L chain, the evaluation walks each node's ancestors
+        if (B.nchunks)
+            LBF_LAUNCH(k_mp_near<float>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks, B.chunk_leaf,
+                       B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi, B.xc, y,
+                       B.nodebase, B.partial, gate);
         LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_eval<float>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
                      pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<float> *)B.loc32,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, T.parent, pl->u32, 1);
+                     out, gate, pl->anc, pl->u32, 1, (const cz<float> *)nullptr, B.nodebase,
+                     B.partial);
+    } else if (pl->udf) {
+        // the accurate operator in double-float (P2L terms formed in double)
+        int P = B.P;
+        size_t smem = sizeof(cz<df64>) * (size_t)wpb * P * 32;
+        LBF_LAUNCH(k_mp_p2l<df64>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
+                   B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
+                   (cz<df64> *)B.loc, B.sums, gate);
+        for (int l = 3; l < T.nlev; l++) {
+            int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
+            if (le <= ls) continue;
+            LBF_LAUNCH(k_mp_l2l<df64>, lbf_cdiv(le - ls, 8), 256, l2l_smem<df64>(P, 8), s, ls, le,
+                       P, T.parent, T.ix, T.iy, (const df64 *)pl->tabdf_binom,
+                       (const cz<df64> *)pl->tabdf_dshift, (cz<df64> *)B.loc, gate);
+        }
+        if (B.nchunks)
+            LBF_LAUNCH(k_mp_near<double>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks,
+                       B.chunk_leaf, B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi,
+                       B.xc, y, B.nodebase, B.partial, gate);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<df64>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
+                     pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<df64> *)B.loc,
+                     B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
+                     out, gate, T.parent, (const float2 *)nullptr, 0, (const cz<df64> *)pl->udf,
+                     B.nodebase, B.partial);
     } else {
         int P = B.P;
         size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
@@ -759,10 +890,15 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
                        le, P, T.parent, T.ix, T.iy, pl->tab_binom,
                        (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, gate);
         }
+        if (B.nchunks)
+            LBF_LAUNCH(k_mp_near<double>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks,
+                       B.chunk_leaf, B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi,
+                       B.xc, y, B.nodebase, B.partial, gate);
         LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<double>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N,
                      P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<double> *)B.loc,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, T.parent, (const float2 *)nullptr, 0);
+                     out, gate, T.parent, (const float2 *)nullptr, 0, (const cz<double> *)nullptr,
+                     B.nodebase, B.partial);
     }
     LBF_CHECK_LAUNCH();
     return LBF_OK;

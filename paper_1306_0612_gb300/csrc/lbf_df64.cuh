@@ -15,7 +15,7 @@
 
 struct __align__(8) df64 {
     float hi, lo;
-    __host__ __device__ df64() : hi(0.f), lo(0.f) {}
+    df64() = default;  // trivial: usable in __shared__ arrays
     __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
     __host__ __device__ df64(float f) : hi(f), lo(0.f) {}
     __host__ __device__ df64(int i) : df64((double)i) {}
@@ -80,6 +80,8 @@ __device__ __forceinline__ df64 df_rcp(df64 a)
     df64 r = df_fma(-a, xd, df64(1.0f));
     return df_fma(xd, r, xd);
 }
+
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) { return a * df_rcp(b); }
 
 // exact scaling by a power of two
 __device__ __forceinline__ df64 df_ldexp(df64 a, float p2) { return df64(a.hi * p2, a.lo * p2, 0); }

@@ -215,6 +215,19 @@ __global__ void k_local_coords(int64_t nleaf, const int32_t *__restrict__ leaves
     }
 }
 
+// per leaf: its ancestors at levels >= 2, nearest first (the leaf itself at s = 0)
+__global__ void k_ancestors(int64_t nleaf, const int32_t *__restrict__ leaves,
+                            const int32_t *__restrict__ level, const int32_t *__restrict__ parent,
+                            int32_t *__restrict__ anc)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nleaf) return;
+    const int b = leaves[t];
+    int s = 0;
+    for (int a = b; a >= 0 && level[a] >= 2 && s < LBF_ANC_STRIDE; a = parent[a])
+        anc[(int64_t)b * LBF_ANC_STRIDE + s++] = a;
+}
+
 // shared-memory bytes of the two FMM pass kernels
 template <typename R> size_t up_smem(int P, int wpb)
 {
@@ -291,10 +304,12 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
             }
         }
     }
+    const size_t walk_smem =
+        walk ? sizeof(cx<R>) * (size_t)fmm::kLeafWarps * (LBF_ANC_STRIDE - 1) * P : 0;
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
-                 32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
+                 32 * fmm::kLeafWarps, walk_smem, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
-                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, T.parent, walk);
+                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, pl->anc, walk);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -308,6 +323,10 @@ int lbf_fmm_init_attrs()
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_up<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafForward>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafTranspose>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     return LBF_OK;
 }
@@ -407,6 +426,9 @@ int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
     fmm::BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
     LBF_LAUNCH(k_local_coords, lbf_cdiv(T.nleaf, 8), 256, 0, s, T.nleaf, T.leaves, T.level, T.ix,
                T.iy, T.begin, T.end, g, pl->xi, pl->u32, (cx<df64> *)pl->udf);
+    if (pl->anc)
+        LBF_LAUNCH(k_ancestors, lbf_cdiv(T.nleaf, 256), 256, 0, s, T.nleaf, T.leaves, T.level,
+                   T.parent, pl->anc);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }

@@ -505,7 +505,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const cx<R> *__restrict__ loc, const double *__restrict__ sigma,
                        const double *__restrict__ dself, const double2 *__restrict__ w,
                        const double *__restrict__ beta, const double *__restrict__ bsig,
-                       double *__restrict__ v, const int *gate, const int32_t *__restrict__ parent,
+                       double *__restrict__ v, const int *gate, const int32_t *__restrict__ anc,
                        int walk)
 {
     if (gate_closed(gate)) return;
@@ -518,6 +518,19 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
     if (t >= nleaf) return;
     const int b = leaves[t];
     const int lt = level[b], tx = ix[b], ty = iy[b];
+    // the ancestor walk: every lane evaluates the same ancestors' expansions, so the warp
+    // stages them in shared memory once per leaf (coalesced) and the lanes read broadcasts
+    extern __shared__ __align__(16) unsigned char walk_sm[];
+    cx<R> *sl = (cx<R> *)walk_sm + (size_t)wid * (LBF_ANC_STRIDE - 1) * P;
+    if (walk) {
+        const int32_t *ab = anc + (int64_t)b * LBF_ANC_STRIDE;
+        const int nA = lt - 1 > 0 ? lt - 1 : 0;
+        for (int e = lane; e < nA * P; e += 32) {
+            const int sh = e / P, l = e - sh * P;
+            sl[e] = loc[(int64_t)ab[sh] * P + l];
+        }
+        __syncwarp();
+    }
     double cxd = 0, cyd = 0, ir = 0;
     bool have_c = false;
     auto need_centre = [&]() {  // double centre: the double path and float fallbacks only
@@ -564,14 +577,14 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                 for (int l = P - 2; l >= 0; l--) phi = cfma(phi, u, lb[l]);
             } else {
                 // every ancestor's own local expansion at the target (no L2L chain):
-                // (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s, s = depth gap
-                for (int a = b; a >= 0 && level[a] >= 2; a = parent[a]) {
-                    const int sh = lt - level[a];
+                // (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s, s = depth gap,
+                // ix_b - 2^s ix_a = the low s bits of ix_b; coefficients staged above
+                for (int sh = 0; sh <= lt - 2; sh++) {
                     const R sc = pow2<R>(-sh);
-                    const int dxi = tx - (ix[a] << sh), dyi = ty - (iy[a] << sh);
+                    const int dxi = tx & ((1 << sh) - 1), dyi = ty & ((1 << sh) - 1);
                     cx<R> ua = mk<R>((R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + u.x * sc,
                                      (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + u.y * sc);
-                    const cx<R> *la = loc + (int64_t)a * P;
+                    const cx<R> *la = sl + sh * P;
                     cx<R> tt = la[P - 1];
                     for (int l = P - 2; l >= 0; l--) tt = cfma(tt, ua, la[l]);
                     phi.x += tt.x;

@@ -260,26 +260,41 @@ k_gj_coop(int M, double *A0, double *A1, double *pval, int *pidx, double *amax, 
         const double *rowp = Ain + (int64_t)p * M;
         double nbest = -1.0;
         int ni = M;
-        int i = i0, j = j0;  // (i, j) of element e, advanced without dividing
-        for (int64_t e = tid; e < MM; e += nthr, i += di, j += dj) {
-            if (j >= M) { j -= M; i++; }
-            double val;
-            if (i == k) {
-                val = (j == k) ? ipiv : __ldcg(&rowp[j]) * ipiv;
-            } else {
-                const int src = (i == p) ? k : i;  // row i of B
-                const double f = __ldcg(&Ain[(int64_t)src * M + k]);
-                if (j == k) {
-                    val = -f * ipiv;
-                } else {
-                    const double a = __ldcg(&Ain[(int64_t)src * M + j]);
-                    val = fma(-f * ipiv, __ldcg(&rowp[j]), a);
-                }
+        // four elements per pass, their loads issued before any is used (the loop is
+        // bound by L2 latency); (i, j) of element e advanced without dividing
+        int i = i0, j = j0;
+        for (int64_t e = tid; e < MM; e += 4 * nthr) {
+            int64_t ee[4];
+            int ii[4], jj[4];
+            double fa[4], aa[4], rp[4];
+            for (int u = 0; u < 4; u++) {
+                ee[u] = e + u * nthr;
+                ii[u] = i;
+                jj[u] = j;
+                i += di;
+                j += dj;
+                if (j >= M) { j -= M; i++; }
             }
-            Aout[e] = val;
-            if (j == k + 1 && i > k) {
-                double av = fabs(val);
-                if (av > nbest || (av == nbest && i < ni)) { nbest = av; ni = i; }
+            for (int u = 0; u < 4; u++) {
+                fa[u] = aa[u] = rp[u] = 0.0;
+                if (ee[u] < MM && ii[u] != k) {
+                    const int src = (ii[u] == p) ? k : ii[u];  // row i of B
+                    fa[u] = __ldcg(&Ain[(int64_t)src * M + k]);
+                    if (jj[u] != k) aa[u] = __ldcg(&Ain[(int64_t)src * M + jj[u]]);
+                }
+                if (ee[u] < MM && jj[u] != k) rp[u] = __ldcg(&rowp[jj[u]]);
+            }
+            for (int u = 0; u < 4; u++) {
+                if (ee[u] >= MM) break;
+                double val;
+                if (ii[u] == k) val = (jj[u] == k) ? ipiv : rp[u] * ipiv;
+                else if (jj[u] == k) val = -fa[u] * ipiv;
+                else val = fma(-fa[u] * ipiv, rp[u], aa[u]);
+                Aout[ee[u]] = val;
+                if (jj[u] == k + 1 && ii[u] > k) {
+                    double av = fabs(val);
+                    if (av > nbest || (av == nbest && ii[u] < ni)) { nbest = av; ni = ii[u]; }
+                }
             }
         }
         block_argmax(nbest, ni, sv, si);

@@ -11,6 +11,7 @@
 #define LBF_PI 3.14159265358979323846
 #define LBF_MAX_TERMS 64  // expansion terms p + 1 supported by the kernels
 #define LBF_MAX_LEVELS 31
+#define LBF_ANC_STRIDE 32
 
 // Per-process launch counter (lbf_launch_count).
 extern std::atomic<int64_t> g_lbf_launches;
@@ -85,6 +86,11 @@ struct Tree {
 struct Border {
     int P = 0, P32 = 0;              // expansion terms (double, float)
     int64_t pair_cap = 0, n_p2l = 0, n_near = 0;
+    // direct centres in chunks of 32 per leaf, a warp each: chunk -> (leaf, chunk index),
+    // per node the first of its partial sums (one per chunk of its leaf)
+    int32_t *chunk_leaf = nullptr, *chunk_k = nullptr, *nodebase = nullptr;
+    double *partial = nullptr;
+    int64_t nchunks = 0, npartial = 0, partial_cap = 0;
     int32_t *leaf_of = nullptr;      // leaf box of each node (Morton order)
     double *ell = nullptr;           // log(1 + |xi_i|^2)
     double2 *xc = nullptr;           // planar centres
@@ -136,6 +142,8 @@ struct lbf_plan {
     int P32 = 0;
     float2 *q32 = nullptr, *mpole32 = nullptr, *local32 = nullptr;
     float2 *u32 = nullptr;  // per node: (xi - c)/r about the centre c, half-width r of its leaf
+    int32_t *anc = nullptr;  // per leaf b: anc[b * LBF_ANC_STRIDE + s] = its ancestor s levels up
+                             // (levels >= 2 only), for the float operator's ancestor walk
     // double-float operator (opt.fmm64): charges, leaf-local coordinates (pairs of
     // float pairs, 16 B), and the translation tables; expansions reuse mpole/local
     void *qdf = nullptr, *udf = nullptr;
