@@ -175,6 +175,119 @@ __global__ void k_evaluate(int64_t N, int M, const double2 *__restrict__ xi,
     }
 }
 
+// u(t) with the far field from the quadtree: the same representation formula as
+// k_evaluate, but boxes at least kEvalSep half-widths from the target enter through
+// their multipole expansion (M2P: every node of the box is within sqrt(2) r of its
+// centre, so the series ratio is at most 1/3 and the truncation after P terms is below
+// 3^-P relative), leaves closer than that by the direct sum, other boxes are opened.
+// One warp per target; each level's frontier is written in a fixed order (warp prefix
+// sums), so the sum is reproducible.
+constexpr double kEvalSep = 4.25;  // >= 3 sqrt(2): |(xi - c)/(t - c)| <= 1/3 in the box
+constexpr int kEvalFront = 2048;   // frontier capacity per warp (per level)
+constexpr int kEvalWarps = 4;
+
+__global__ void k_evaluate_tree(int64_t N, int M, const double2 *__restrict__ xi,
+                                const double2 *__restrict__ q, const cx<df64> *__restrict__ mp,
+                                int P, const int32_t *__restrict__ level,
+                                const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
+                                const int32_t *__restrict__ child0,
+                                const int32_t *__restrict__ nchild, const int32_t *__restrict__ bg,
+                                const int32_t *__restrict__ en, BoxGeo g,
+                                const double *__restrict__ bsig, const double *__restrict__ a,
+                                const double *__restrict__ c, int64_t T,
+                                const double *__restrict__ t, int rot_on,
+                                const double *__restrict__ rot, double *__restrict__ u,
+                                int *__restrict__ status)
+{
+    extern __shared__ int32_t front[];  // [warp][2][kEvalFront]
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tq = blockIdx.x * (int64_t)kEvalWarps + wid;
+    if (tq >= T) return;
+    int32_t *fr[2] = {front + (size_t)wid * 2 * kEvalFront, front + (size_t)wid * 2 * kEvalFront + kEvalFront};
+    double p[3] = {t[3 * tq], t[3 * tq + 1], t[3 * tq + 2]};
+    if (rot_on) {
+        double r0 = rot[0] * p[0] + rot[1] * p[1] + rot[2] * p[2];
+        double r1 = rot[3] * p[0] + rot[4] * p[1] + rot[5] * p[2];
+        double r2 = rot[6] * p[0] + rot[7] * p[1] + rot[8] * p[2];
+        p[0] = r0; p[1] = r1; p[2] = r2;
+    }
+    const double w = 1.0 - p[2];
+    double accr = 0.0, acci = 0.0;  // sum over sources of q/(xi - t)
+    if (w > 0.0) {                  // a target at the pole sees no Cauchy term
+        const double zx = p[0] / w, zy = p[1] / w;
+        int cur = 0, n = 1;
+        if (lane == 0) fr[0][0] = 0;
+        __syncwarp();
+        while (n > 0) {
+            int nn = 0;
+            for (int base = 0; base < n; base += 32) {
+                const int e = base + lane;
+                int kids = 0, b = -1;
+                if (e < n) {
+                    b = fr[cur][e];
+                    double cxd, cyd, r;
+                    box_centre(g, level[b], ix[b], iy[b], cxd, cyd, r);
+                    const double dx = zx - cxd, dy = zy - cyd;
+                    if (b != 0 && dx * dx + dy * dy >= kEvalSep * kEvalSep * r * r) {
+                        // M2P: Phi(t) = (1/r) sum_k a_k rho^(k+1), rho = r/(t - c); q/(xi - t) = -Phi
+                        const double id = 1.0 / (dx * dx + dy * dy);
+                        const cx<df64> rho{df64(r * dx * id), df64(-r * dy * id)};
+                        const cx<df64> *ak = mp + (int64_t)b * P;
+                        cx<df64> ps = ak[P - 1];
+                        for (int k = P - 2; k >= 0; k--) ps = fmm::cfma(ps, rho, ak[k]);
+                        ps = fmm::cmul(ps, rho);
+                        const double ir = 1.0 / r;
+                        accr -= (double)ps.x * ir;
+                        acci -= (double)ps.y * ir;
+                    } else if (nchild[b] == 0) {
+                        for (int j = bg[b]; j < en[b]; j++) {
+                            const double dr = xi[j].x - zx, di = xi[j].y - zy;
+                            const double2 qq = q[j];
+                            const double id = 1.0 / (dr * dr + di * di);
+                            accr += (qq.x * dr + qq.y * di) * id;
+                            acci += (qq.y * dr - qq.x * di) * id;
+                        }
+                    } else {
+                        kids = nchild[b];
+                    }
+                }
+                // children in frontier order: exclusive prefix sum of the lanes' counts
+                int incl = kids;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                int pos = nn + incl - kids;
+                for (int k = 0; k < kids; k++, pos++) {
+                    if (pos < kEvalFront) fr[1 - cur][pos] = child0[b] + k;
+                }
+                nn += total;
+            }
+            if (nn > kEvalFront) {
+                if (lane == 0) atomicOr(status, 8);
+                nn = 0;
+            }
+            __syncwarp();
+            cur = 1 - cur;
+            n = nn;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        accr += __shfl_xor_sync(0xffffffffu, accr, o);
+        acci += __shfl_xor_sync(0xffffffffu, acci, o);
+    }
+    double sa = 0.0;
+    if (a) {
+        for (int m = lane; m < M; m += 32) {
+            double d0 = p[0] - c[3 * m], d1 = p[1] - c[3 * m + 1], d2 = p[2] - c[3 * m + 2];
+            sa += a[m] * (1.0 / (4.0 * LBF_PI)) * log(2.0 / (d0 * d0 + d1 * d1 + d2 * d2));
+        }
+        for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    if (lane == 0) u[tq] = acci * (1.0 / (2.0 * LBF_PI)) + *bsig + sa;
+}
+
 __global__ void k_green_sum(int64_t T, const double *__restrict__ t, int64_t S,
                             const double *__restrict__ p, const double *__restrict__ gm,
                             double *__restrict__ out)
@@ -323,6 +436,8 @@ int lbf_fmm_init_attrs()
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_up<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
+    LBF_CUDA(cudaFuncSetAttribute(k_evaluate_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(int32_t) * 2 * kEvalFront * kEvalWarps)));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafForward>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafTranspose>,
@@ -436,6 +551,30 @@ int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
 int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a, int64_t T,
                       const double *t, double *u, cudaStream_t s)
 {
+    if (pl->opt.matvec == LBF_MATVEC_FMM && pl->qdf && T > 0) {
+        // charges in double (direct part) and double-float (multipoles), beta . sigma
+        int nb = (int)std::min<int64_t>(lbf_cdiv(pl->N, 256), 1024);
+        LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma_sorted, pl->w, pl->beta, pl->q,
+                   (float2 *)nullptr, (cx<df64> *)pl->qdf, pl->red, pl->red_count, pl->bsig,
+                   (const int *)nullptr);
+        LBF_CHECK_LAUNCH();
+        Tree &Tr = pl->tree;
+        BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L)};
+        const int P = pl->P, wpb = 2;
+        LBF_LAUNCH(fmm::k_up<df64>, lbf_cdiv(Tr.nleaf, wpb), 32 * wpb, up_smem<df64>(P, wpb), s,
+                   Tr.nleaf, Tr.leaves, Tr.level, Tr.ix, Tr.iy, Tr.begin, Tr.end, Tr.parent,
+                   Tr.child0, Tr.nchild, g, P, (const df64 *)pl->tabdf_binom,
+                   (const cx<df64> *)pl->tabdf_dshift, pl->xi, (const cx<df64> *)pl->udf,
+                   (const cx<df64> *)pl->qdf, (cx<df64> *)pl->mpole, pl->upcnt,
+                   (const int *)nullptr);
+        LBF_LAUNCH(k_evaluate_tree, lbf_cdiv(T, kEvalWarps), 32 * kEvalWarps,
+                   sizeof(int32_t) * 2 * kEvalFront * kEvalWarps, s, pl->N, pl->M, pl->xi, pl->q,
+                   (const cx<df64> *)pl->mpole, P, Tr.level, Tr.ix, Tr.iy, Tr.child0, Tr.nchild,
+                   Tr.begin, Tr.end, g, pl->bsig, a, pl->centres, T, t, pl->has_rot, pl->rot_d, u,
+                   pl->dev_status);
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    }
     int rc = prep(pl, sigma_sorted, Arith::F64, true, nullptr, s);
     if (rc) return rc;
     if (T <= 0) return LBF_OK;

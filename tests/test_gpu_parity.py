@@ -144,6 +144,37 @@ def test_preconditioned_op_many_islands():
     assert rel_l2(host(out), A @ v) < MATVEC_TOL
 
 
+@pytest.mark.parametrize("fmm64", [0, 1])
+def test_accurate_operator_arithmetic(fmm64):
+    """The accurate FMM in native double (fmm64 = 0) and in double-float (fmm64 = 1):
+    both within the FP64 tolerance of the oracle, and within 1e-12 of each other."""
+    g = wl.config_geometry("C2")
+    p = plan_for(g, fmm64=fmm64)
+    v = np.random.default_rng(6).standard_normal(g.N + g.M)
+    out = zeros(g.N + g.M)
+    L.lbf_apply(p, L.LBF_OP_FULL, dev(v), out)
+    assert rel_l2(host(out), oracle.apply(g, v, 0)) < MATVEC_TOL
+    other = plan_for(g, fmm64=1 - fmm64)
+    o2 = zeros(g.N + g.M)
+    L.lbf_apply(other, L.LBF_OP_FULL, dev(v), o2)
+    assert rel_l2(host(out), host(o2)) < 1e-12
+
+
+def test_tree_evaluation_matches_direct_evaluation():
+    """lbf_evaluate on an FMM plan (far field from the quadtree's multipoles) against the
+    direct evaluation of a direct-matvec plan, same density and multipliers."""
+    g = wl.config_geometry("C2")
+    t = wl.targets_off_islands(g, 500, seed=9)
+    rng = np.random.default_rng(13)
+    s_, a_ = dev(rng.standard_normal(g.N)), dev(rng.standard_normal(g.M))
+    uf, ud = zeros(len(t)), zeros(len(t))
+    L.lbf_evaluate(plan_for(g), s_, a_, dev(t), uf)
+    L.lbf_evaluate(plan_for(g, matvec=L.LBF_MATVEC_DIRECT), s_, a_, dev(t), ud)
+    assert rel_l2(host(uf), host(ud)) < 1e-12
+    ref = oracle.evaluate(g, host(s_), host(a_), t)
+    assert rel_l2(host(uf), ref) < 1e-12
+
+
 def test_fmm_matvec_c2_full_size():
     g = wl.config_geometry("C2")
     p = plan_for(g)
