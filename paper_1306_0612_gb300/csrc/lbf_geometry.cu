@@ -1,5 +1,7 @@
 // Per-node precompute (Sec. 3 and Sec. 5) and the inverse Schur complement of
 // the block preconditioner (Sec. 5).
+#include <utility>
+
 #include "lbf_internal.cuh"
 
 namespace {
@@ -123,21 +125,15 @@ __global__ void k_rotate_centres(int M, const double *__restrict__ c, Rot R, dou
     out[3 * m + 2] = v[2];
 }
 
-// Gauss-Jordan step k on [S | I] (M x 2M, row-major): partial pivoting on column
-// k, swap, scale the pivot row.  One block.
 // ---- inverse of the Schur complement ---------------------------------------------------
 //
-// Gauss-Jordan elimination with partial pivoting (row interchanges), all M steps in
-// one cooperative launch.  Step k reads matrix A_k and writes A_(k+1) (two buffers
-// in turn), so every block takes the pivot row p, row k and column k straight from
-// A_k and one grid barrier per step suffices:
-//   row k:       A'_kj = A_pj / A_pk                   (A'_kk = 1 / A_pk)
-//   row i != k:  A'_ij = B_ij - B_ik A_pj / A_pk,  A'_ik = -B_ik / A_pk,
-// B being A_k with rows k and p interchanged.  The same pass forms each block's
-// partial maximum of |A'_i,k+1|, i > k (two sets of partials, by step parity, so a
-// block never overwrites values another block is still reducing).  Every block
-// reduces the partials the same way, so all agree on the next pivot.  The
-// interchanges are undone at the end by swapping columns k and p, k = M-1, ..., 0.
+// Gauss-Jordan elimination with partial pivoting (row interchanges), in place, all M
+// steps in one cooperative launch.  Step k, with B = A after interchanging rows k and
+// p (p the pivot row):
+//   row k:       A'_kj = B_kj / B_kk                  (A'_kk = 1 / B_kk)
+//   row i != k:  A'_ij = B_ij - B_ik A'_kj,   A'_ik = -B_ik / B_kk.
+// The interchanges are undone at the end by swapping columns k and p, k = M-1, ..., 0.
+// A singular S (a pivot at or below M 2^-52 max|S_ij|) sets status bit 4.
 //
 // The grid barrier is a counter and a generation word; every block is resident
 // (cooperative launch), and each wait gives up after kBarrierSpins polls, setting
@@ -181,128 +177,361 @@ __device__ bool grid_barrier(GridBarrier *bar, unsigned nb, int *status)
     return ok != 0;
 }
 
-// block-wide (max |value|, smallest index) reduction; result valid in every thread
-__device__ void block_argmax(double &v, int &idx, double *sv, int *si)
+// Magnitudes are compared as the bit patterns of |x| (for doubles that are not NaN the
+// order of |x| is the unsigned order of its bits), so the pivot searches issue integer
+// instructions only: the double pipe of this GPU is narrow.  A NaN sorts above every
+// number, so a NaN pivot reads as a singular matrix.
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull, kInfBits = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ unsigned long long abs_key(double x)
 {
-    const int t = threadIdx.x;
-    sv[t] = v;
-    si[t] = idx;
+    return (unsigned long long)__double_as_longlong(x) & kAbsMask;
+}
+
+// block-wide (max key, smallest index) reduction, result in every thread: warp
+// shuffles, then one warp over the warps' results.  sk, si hold 33 entries.
+__device__ void block_argmax(unsigned long long &key, int &idx, unsigned long long *sk, int *si)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, key, o);
+        const int i = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (a > key || (a == key && i < idx)) { key = a; idx = i; }
+    }
+    if (lane == 0) { sk[wid] = key; si[wid] = idx; }
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (t < o) {
-            double a = sv[t + o];
-            int i = si[t + o];
-            if (a > sv[t] || (a == sv[t] && i < si[t])) {
-                sv[t] = a;
-                si[t] = i;
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        key = lane < nw ? sk[lane] : 0ull;
+        idx = lane < nw ? si[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, key, o);
+            const int i = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (a > key || (a == key && i < idx)) { key = a; idx = i; }
+        }
+        if (lane == 0) { sk[32] = key; si[32] = idx; }
+    }
+    __syncthreads();
+    key = sk[32];
+    idx = si[32];
+}
+
+// Blocked Gauss-Jordan: the same elimination, kGjPanel pivot steps per round q.
+// Panel P = [k0, k0 + np).  Let B = Pi A_P (the panel's columns after its row
+// interchanges Pi) and B_P its rows at the panel positions.  The panel's elementary
+// transformations multiply to Q = I + (W - I_P) e_P^T with Q B = e_P, so W_P = B_P^-1
+// and W_R = -B_R B_P^-1 on the other rows R.  Every other column j becomes
+//   Q Pi A_j:   rows i in P:  G_j = B_P^-1 (Pi A_j)_P,   rows i in R:  (Pi A_j)_i - B_i G_j,
+// and the panel's own columns become W.
+//
+// Round q reads matrix A_q and writes A_(q+1) (two buffers in turn), so any block may
+// update any part of it.  Block 0 searches the pivots: it runs the panel's steps on
+// rows >= k0 only (the rows above never take part in pivoting, and W on rows >= k0,
+// B_P^-1 included, does not depend on them), in shared memory, and publishes the
+// pivot rows and B_P^-1.  Look-ahead: while blocks 1.. apply panel q to the matrix,
+// block 0 waits only for the columns of panel q + 1 (done first, in row chunks, each
+// chunk signalling a counter) and then searches panel q + 1's pivots, so the serial
+// pivot search overlaps the update and each round costs one grid barrier.
+//
+// Panel steps: a thread owns rows i = k0 + t, k0 + t + 512, ...; the previous step's
+// update already reduced its rows to one pivot candidate, so a step is one block
+// reduction, the new pivot row formed by one warp, and eight fused multiply-adds per
+// row (the pivot column is updated as a column whose entry is zero, which gives
+// -B_ik / B_kk).
+constexpr int kGjPanel = 8;
+
+template <bool STAGE>
+__device__ __forceinline__ double gj_ld(const double *P, int64_t idx)
+{
+    if constexpr (STAGE) return P[idx];
+    else return __ldcg(P + idx);
+}
+
+struct GjShared {
+    unsigned long long sk[33];
+    int si[33];
+    double nk[kGjPanel], rk[kGjPanel];   // new pivot row, old row k
+    int rrow[2 * kGjPanel], rsrc[2 * kGjPanel], nR;
+    double binv[kGjPanel][kGjPanel];    // B_P^-1 of the round's panel
+    double V[kGjPanel][kGjPanel], G[kGjPanel][kGjPanel];
+};
+
+// Pivot search of the panel [k0, k0 + np) of A (one block): rows >= k0 of the panel
+// columns into Pw (column-major, Pw[c M + i]), the steps, then the pivot rows and
+// B_P^-1 (row c at binv + c kGjPanel).  Returns false if S is singular.
+template <bool STAGE>
+__device__ bool gj_panel(int M, const double *A, int k0, int np, unsigned long long tinykey,
+                         double *Pw, int *pivrow, double *binv, GjShared &sh)
+{
+    for (int e = threadIdx.x; e < (M - k0) * np; e += blockDim.x) {
+        const int i = k0 + e / np, c = e % np;
+        Pw[c * M + i] = __ldcg(&A[(int64_t)i * M + k0 + c]);
+    }
+    __syncthreads();
+    unsigned long long ck = 0ull;
+    int ci = M;
+    for (int i = k0 + threadIdx.x; i < M; i += blockDim.x) {
+        const unsigned long long a = abs_key(gj_ld<STAGE>(Pw, i));
+        if (a > ck) { ck = a; ci = i; }
+    }
+    bool ok = true;
+    for (int c = 0; c < np; c++) {
+        const int k = k0 + c;
+        block_argmax(ck, ci, sh.sk, sh.si);
+        if (ck <= tinykey || ck > kInfBits || ci >= M) {  // same values in every thread
+            ok = false;
+            break;
+        }
+        const int p = ci;
+        if (threadIdx.x < np) {
+            const int cc = threadIdx.x;
+            const double ipiv = 1.0 / gj_ld<STAGE>(Pw, c * M + p);
+            sh.rk[cc] = gj_ld<STAGE>(Pw, cc * M + k);
+            sh.nk[cc] = cc == c ? ipiv : gj_ld<STAGE>(Pw, cc * M + p) * ipiv;
+            if (cc == 0) pivrow[k] = p;
+        }
+        __syncthreads();  // rows k and p read before any row is written
+        double nk[kGjPanel], rk[kGjPanel];
+#pragma unroll
+        for (int cc = 0; cc < kGjPanel; cc++) {
+            nk[cc] = cc < np ? sh.nk[cc] : 0.0;
+            rk[cc] = cc < np ? sh.rk[cc] : 0.0;
+        }
+        ck = 0ull;
+        ci = M;
+        for (int i = k0 + threadIdx.x; i < M; i += blockDim.x) {
+            if (i == k) {
+#pragma unroll
+                for (int cc = 0; cc < kGjPanel; cc++)
+                    if (cc < np) Pw[cc * M + k] = nk[cc];
+                continue;
             }
+            double b[kGjPanel], f = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < kGjPanel; cc++) {
+                b[cc] = cc >= np ? 0.0 : (i == p ? rk[cc] : gj_ld<STAGE>(Pw, cc * M + i));
+                if (cc == c) { f = b[cc]; b[cc] = 0.0; }
+            }
+#pragma unroll
+            for (int cc = 0; cc < kGjPanel; cc++) {
+                if (cc >= np) continue;
+                const double v = fma(-f, nk[cc], b[cc]);
+                Pw[cc * M + i] = v;
+                if (cc == c + 1 && i > k) {
+                    const unsigned long long a = abs_key(v);
+                    if (a > ck) { ck = a; ci = i; }  // rows ascending per thread: first wins ties
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (ok)
+        for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+            const int r = e / np, c = e % np;
+            binv[r * kGjPanel + c] = gj_ld<STAGE>(Pw, c * M + k0 + r);
+        }
+    return ok;
+}
+
+// The swap set of the panel [k0, k0 + np): the rows its interchanges move (rrow) and,
+// for each, the row its value comes from (rsrc); slot[row] = entry or -1 (thread 0).
+__device__ void gj_swapset(int k0, int np, const int *pivrow, int *slot, GjShared &sh)
+{
+    int n = 0;
+    for (int k = k0; k < k0 + np; k++) {
+        const int p = __ldcg(&pivrow[k]);
+        int a = -1, b = -1;
+        for (int t = 0; t < n; t++)
+            if (sh.rrow[t] == k) a = t;
+        if (a < 0) { sh.rrow[n] = k; sh.rsrc[n] = k; a = n++; }
+        for (int t = 0; t < n; t++)
+            if (sh.rrow[t] == p) b = t;
+        if (b < 0) { sh.rrow[n] = p; sh.rsrc[n] = p; b = n++; }
+        const int tmp = sh.rsrc[a];
+        sh.rsrc[a] = sh.rsrc[b];
+        sh.rsrc[b] = tmp;
+    }
+    sh.nR = n;
+    for (int t = 0; t < n; t++) slot[sh.rrow[t]] = t;
+}
+
+// One work item of round q (one block): column tile `tile` (kGjPanel columns), rows
+// [r0, r1), read from Aq and written to Aq1.  The panel's own tile gets W.
+__device__ void gj_item(int M, const double *Aq, double *Aq1, int k0, int np, int tile, int r0, int r1,
+                        const int *slot, GjShared &sh)
+{
+    const int jc = threadIdx.x % kGjPanel, rg = threadIdx.x / kGjPanel, nrg = blockDim.x / kGjPanel;
+    const int j = tile * kGjPanel + jc;
+    const bool wtile = tile * kGjPanel == k0;
+    if (!wtile) {
+        // (Pi A_j)_P and G_j = B_P^-1 (Pi A_j)_P for the tile's columns
+        for (int e = threadIdx.x; e < np * kGjPanel; e += blockDim.x) {
+            const int m = e / kGjPanel, c = e % kGjPanel, jj = tile * kGjPanel + c;
+            const int src = sh.rsrc[slot[k0 + m]];
+            sh.V[m][c] = jj < M ? __ldcg(&Aq[(int64_t)src * M + jj]) : 0.0;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < np * kGjPanel; e += blockDim.x) {
+            const int m = e / kGjPanel, c = e % kGjPanel;
+            double g = 0.0;
+            for (int l = 0; l < np; l++) g = fma(sh.binv[m][l], sh.V[l][c], g);
+            sh.G[m][c] = g;
         }
         __syncthreads();
     }
-    v = sv[0];
-    idx = si[0];
-    __syncthreads();
+    if (j < M && (!wtile || jc < np)) {
+        double g[kGjPanel];
+#pragma unroll
+        for (int m = 0; m < kGjPanel; m++) g[m] = m < np ? (wtile ? sh.binv[m][jc] : sh.G[m][jc]) : 0.0;
+        for (int i0 = r0 + rg; i0 < r1; i0 += 4 * nrg) {
+            double x[4], b[4][kGjPanel];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u * nrg;
+                x[u] = 0.0;
+#pragma unroll
+                for (int m = 0; m < kGjPanel; m++) b[u][m] = 0.0;
+                if (i < r1 && (i < k0 || i >= k0 + np)) {
+                    const int sl = slot[i];
+                    const int64_t src = (int64_t)(sl >= 0 ? sh.rsrc[sl] : i) * M;
+                    if (!wtile) x[u] = __ldcg(&Aq[src + j]);
+#pragma unroll
+                    for (int m = 0; m < kGjPanel; m++)
+                        if (m < np) b[u][m] = __ldcg(&Aq[src + k0 + m]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u * nrg;
+                if (i >= r1) break;
+                double out = x[u];
+                if (i >= k0 && i < k0 + np) {
+#pragma unroll
+                    for (int m = 0; m < kGjPanel; m++)
+                        if (i == k0 + m) out = wtile ? sh.binv[m][jc] : sh.G[m][jc];
+                } else {
+#pragma unroll
+                    for (int m = 0; m < kGjPanel; m++) out = fma(-b[u][m], g[m], out);
+                }
+                Aq1[(int64_t)i * M + j] = out;
+            }
+        }
+    }
+    __syncthreads();  // V, G reused by the next item
 }
 
-__global__ void __launch_bounds__(kGjThreads)
-k_gj_coop(int M, double *A0, double *A1, double *pval, int *pidx, double *amax, int *pivrow,
-          GridBarrier *bar, int *status)
+// Bounded wait of block 0 for `target` finished chunks; false (status set) on time-out.
+__device__ bool gj_wait(unsigned *done, unsigned target, int *status)
 {
-    __shared__ double sv[kGjThreads];
-    __shared__ int si[kGjThreads];
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        unsigned it = 0;
+        while (*(volatile unsigned *)done < target)
+            if (++it > kBarrierSpins) {
+                atomicOr(status, LBF_DEV_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <bool STAGE>
+__global__ void __launch_bounds__(kGjThreads)
+k_gj_blocked(int M, double *A0, double *A1, double *amax, int *pivrow, double *binv, unsigned *done,
+             GridBarrier *bar, int *status, double *Pg)
+{
+    extern __shared__ __align__(16) unsigned char gsm[];
+    int *slot = (int *)gsm;                                     // M: swap-set entry of a row, or -1
+    double *Pw = STAGE ? (double *)(slot + M + (M & 1)) : Pg;   // block 0's panel, Pw[c M + i]
+    __shared__ GjShared sh;
     const unsigned nb = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)nb * blockDim.x;
     const int64_t MM = (int64_t)M * M;
-    const int i0 = (int)(tid / M), j0 = (int)(tid % M);
-    const int di = (int)(nthr / M), dj = (int)(nthr % M);
-    // partial maxima of column 0 (parity 0) and of every |S_ij|
+    unsigned long long *akey = (unsigned long long *)amax;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) slot[i] = -1;
     {
-        double best = -1.0, big = 0.0;
-        int bi = M, unused = 0;
-        for (int64_t i = tid; i < M; i += nthr) {
-            double a = fabs(A0[i * M]);
-            if (a > best) { best = a; bi = (int)i; }
-        }
-        for (int64_t e = tid; e < MM; e += nthr) big = fmax(big, fabs(A0[e]));
-        block_argmax(best, bi, sv, si);
-        block_argmax(big, unused, sv, si);
-        if (threadIdx.x == 0) {
-            pval[blockIdx.x] = best;
-            pidx[blockIdx.x] = bi;
-            amax[blockIdx.x] = big;
-        }
+        unsigned long long big = 0ull;
+        int unused = 0;
+        for (int64_t e = tid; e < MM; e += nthr) big = max(big, abs_key(A0[e]));
+        block_argmax(big, unused, sh.sk, sh.si);
+        if (threadIdx.x == 0) akey[blockIdx.x] = big;
     }
     if (!grid_barrier(bar, nb, status)) return;
     // a pivot at or below M 2^-52 max|S_ij| counts as zero: S is singular to double precision
-    double tiny = 0.0;
-    for (unsigned q = 0; q < nb; q++) tiny = fmax(tiny, __ldcg(&amax[q]));
-    tiny *= (double)M * 0x1p-52;
-    for (int k = 0; k < M; k++) {
-        const double *Ain = (k & 1) ? A1 : A0;
-        double *Aout = (k & 1) ? A0 : A1;
-        const double *pv = pval + (k & 1) * kGjMaxBlocks;
-        const int *pi = pidx + (k & 1) * kGjMaxBlocks;
-        double best = -1.0;
-        int p = M;
-        for (unsigned q = threadIdx.x; q < nb; q += blockDim.x) {
-            double a = __ldcg(&pv[q]);
-            int i = __ldcg(&pi[q]);
-            if (a > best || (a == best && i < p)) { best = a; p = i; }
-        }
-        block_argmax(best, p, sv, si);
-        if (!(best > tiny) || p >= M) {  // every block sees the same value: all stop here
-            if (tid == 0) atomicOr(status, 4);
-            return;
-        }
-        if (tid == 0) pivrow[k] = p;
-        const double ipiv = 1.0 / __ldcg(&Ain[(int64_t)p * M + k]);
-        const double *rowp = Ain + (int64_t)p * M;
-        double nbest = -1.0;
-        int ni = M;
-        // four elements per pass, their loads issued before any is used (the loop is
-        // bound by L2 latency); (i, j) of element e advanced without dividing
-        int i = i0, j = j0;
-        for (int64_t e = tid; e < MM; e += 4 * nthr) {
-            int64_t ee[4];
-            int ii[4], jj[4];
-            double fa[4], aa[4], rp[4];
-            for (int u = 0; u < 4; u++) {
-                ee[u] = e + u * nthr;
-                ii[u] = i;
-                jj[u] = j;
-                i += di;
-                j += dj;
-                if (j >= M) { j -= M; i++; }
-            }
-            for (int u = 0; u < 4; u++) {
-                fa[u] = aa[u] = rp[u] = 0.0;
-                if (ee[u] < MM && ii[u] != k) {
-                    const int src = (ii[u] == p) ? k : ii[u];  // row i of B
-                    fa[u] = __ldcg(&Ain[(int64_t)src * M + k]);
-                    if (jj[u] != k) aa[u] = __ldcg(&Ain[(int64_t)src * M + jj[u]]);
-                }
-                if (ee[u] < MM && jj[u] != k) rp[u] = __ldcg(&rowp[jj[u]]);
-            }
-            for (int u = 0; u < 4; u++) {
-                if (ee[u] >= MM) break;
-                double val;
-                if (ii[u] == k) val = (jj[u] == k) ? ipiv : rp[u] * ipiv;
-                else if (jj[u] == k) val = -fa[u] * ipiv;
-                else val = fma(-fa[u] * ipiv, rp[u], aa[u]);
-                Aout[ee[u]] = val;
-                if (jj[u] == k + 1 && ii[u] > k) {
-                    double av = fabs(val);
-                    if (av > nbest || (av == nbest && ii[u] < ni)) { nbest = av; ni = ii[u]; }
-                }
-            }
-        }
-        block_argmax(nbest, ni, sv, si);
-        if (threadIdx.x == 0) {
-            pval[((k + 1) & 1) * kGjMaxBlocks + blockIdx.x] = nbest;
-            pidx[((k + 1) & 1) * kGjMaxBlocks + blockIdx.x] = ni;
-        }
+    unsigned long long big = 0ull;
+    for (unsigned q = 0; q < nb; q++) big = max(big, __ldcg(&akey[q]));
+    const unsigned long long tinykey =
+        big > kInfBits ? kInfBits : abs_key(__longlong_as_double((long long)big) * (double)M * 0x1p-52);
+    const int ntile = (M + kGjPanel - 1) / kGjPanel;
+    // row chunks of the next panel's tile and of the panel's own tile
+    const int hc = max(64, (((M + 7) / 8 + 63) / 64) * 64), nch = (M + hc - 1) / hc;
+    const bool lone = nb == 1;  // a single block does everything itself
+    const int nwk = lone ? 1 : (int)nb - 1, wk = lone ? 0 : (int)blockIdx.x - 1;
+    if (blockIdx.x == 0 &&
+        !gj_panel<STAGE>(M, A0, 0, min(M, kGjPanel), tinykey, Pw, pivrow, binv, sh) && threadIdx.x == 0)
+        atomicOr(status, 4);
+    unsigned waited = 0;
+    for (int k0 = 0, q = 0; k0 < M; k0 += kGjPanel, q++) {
+        const int np = min(M - k0, kGjPanel), n0 = k0 + kGjPanel;
+        const double *Aq = (q & 1) ? A1 : A0;
+        double *Aq1 = (q & 1) ? A0 : A1;
         if (!grid_barrier(bar, nb, status)) return;
+        if (*(volatile int *)status & 4) return;  // singular: every block stops here
+        if (threadIdx.x == 0) gj_swapset(k0, np, pivrow, slot, sh);
+        for (int e = threadIdx.x; e < kGjPanel * kGjPanel; e += blockDim.x)
+            sh.binv[e / kGjPanel][e % kGjPanel] = __ldcg(&binv[(q & 1) * kGjPanel * kGjPanel + e]);
+        __syncthreads();
+        const int tp = k0 / kGjPanel, tn = n0 < M ? tp + 1 : -1;
+        const int cn = tn >= 0 ? nch : 0;  // chunk items of the next panel's tile
+        const int nitems = cn + nch + (ntile - 1 - (tn >= 0 ? 1 : 0));
+        double *binv1 = binv + ((q + 1) & 1) * kGjPanel * kGjPanel;
+        if (blockIdx.x == 0 && !lone) {
+            if (tn >= 0) {
+                waited += cn;
+                if (!gj_wait(done, waited, status)) return;
+                if (!gj_panel<STAGE>(M, Aq1, n0, min(M - n0, kGjPanel), tinykey, Pw, pivrow, binv1, sh) &&
+                    threadIdx.x == 0)
+                    atomicOr(status, 4);
+            }
+        } else {
+            for (int w = wk; w < nitems; w += nwk) {
+                int tile, r0 = 0, r1 = M;
+                if (w < cn) {
+                    tile = tn;
+                    r0 = w * hc;
+                    r1 = min(M, r0 + hc);
+                } else if (w < cn + nch) {
+                    tile = tp;
+                    r0 = (w - cn) * hc;
+                    r1 = min(M, r0 + hc);
+                } else {  // the other tiles in order, skipping tp and tn
+                    tile = w - cn - nch;
+                    const int lo = tn >= 0 ? min(tp, tn) : tp, hi = tn >= 0 ? max(tp, tn) : INT_MAX;
+                    if (tile >= lo) tile++;
+                    if (tile >= hi) tile++;
+                }
+                gj_item(M, Aq, Aq1, k0, np, tile, r0, r1, slot, sh);
+                if (w < cn) {  // the chunk's rows visible device-wide, then counted
+                    __threadfence();
+                    __syncthreads();
+                    if (threadIdx.x == 0) atomicAdd(done, 1u);
+                    if (lone && w == cn - 1 &&
+                        !gj_panel<STAGE>(M, Aq1, n0, min(M - n0, kGjPanel), tinykey, Pw, pivrow, binv1, sh) &&
+                        threadIdx.x == 0)
+                        atomicOr(status, 4);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int t = 0; t < sh.nR; t++) slot[sh.rrow[t]] = -1;
     }
 }
 
@@ -312,22 +541,30 @@ __global__ void k_gj_init(int M, int *__restrict__ pivrow)
     if (k < M) pivrow[k] = k;
 }
 
-// undo the row interchanges: swap columns k and pivrow[k] for k = M-1, ..., 0 (thread per
-// row).  pivrow starts as the identity, so steps an early stop (a singular pivot or a
-// barrier that gave up) never reached swap nothing.
-__global__ void k_gj_unscramble(int M, double *__restrict__ A, const int *__restrict__ pivrow)
+// Undo the row interchanges: swapping columns k and pivrow[k] for k = M-1, ..., 0 is
+// the column permutation out_j = in_perm[j]; one thread composes it.  pivrow starts
+// as the identity, so steps an early stop (a singular pivot or a barrier that gave up)
+// never reached swap nothing.
+__global__ void k_gj_perm(int M, const int *__restrict__ pivrow, int *__restrict__ perm)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= M) return;
-    double *row = A + i * M;
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int j = 0; j < M; j++) perm[j] = j;
     for (int k = M - 1; k >= 0; k--) {
-        int p = pivrow[k];
+        const int p = pivrow[k];
         if (p != k && p >= 0 && p < M) {
-            double t = row[k];
-            row[k] = row[p];
-            row[p] = t;
+            const int t = perm[k];
+            perm[k] = perm[p];
+            perm[p] = t;
         }
     }
+}
+
+// out[i][j] = in[i][perm[j]] (block per row)
+__global__ void k_gj_gather(int M, const double *__restrict__ in, const int *__restrict__ perm,
+                            double *__restrict__ out)
+{
+    const int64_t i = blockIdx.x;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) out[i * M + j] = __ldg(&in[i * M + perm[j]]);
 }
 
 __global__ void k_geometry_out(int64_t N, const int32_t *__restrict__ rank,
@@ -387,9 +624,14 @@ int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const
 
 // S = D - F E from the island expansions of the multiplier potential, then its
 // inverse in place by Gauss-Jordan elimination with partial pivoting.
+constexpr size_t kGjSmemCap = 200 * 1024;
+
+// scratch of lbf_border_build: the second matrix buffer, block 0's panel (when it
+// does not fit in shared memory), the partial maxima, pivot rows, permutation, B_P^-1
+// twice, the chunk counter and the grid barrier
 size_t lbf_gj_scratch_doubles(int M)
 {
-    return (size_t)M * M + 5 * (size_t)kGjMaxBlocks + (size_t)M + 64;
+    return (size_t)M * M + (size_t)M * kGjPanel + kGjMaxBlocks + (size_t)M + 2 * kGjPanel * kGjPanel + 64;
 }
 
 int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
@@ -406,27 +648,41 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *
     LBF_CUDA(cudaGetDevice(&dev));
     LBF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     LBF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    LBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, kGjThreads, 0));
+    // shared memory: the row slots (M), block 0's panel if it fits
+    const size_t sm_base = sizeof(int) * (size_t)(M + 1);
+    const size_t sm_w = sizeof(double) * (size_t)M * kGjPanel;
+    const bool stage = sm_base + sm_w <= kGjSmemCap;
+    const size_t smem = sm_base + (stage ? sm_w : 0);
+    if (smem > kGjSmemCap) return LBF_EINVAL;  // M above ~51,000
+    const void *fn = stage ? (const void *)k_gj_blocked<true> : (const void *)k_gj_blocked<false>;
+    LBF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmemCap));
+    LBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGjThreads, smem));
     if (!coop || per_sm < 1) return LBF_ECUDA;
     // one block per SM: every SM's double pipe busy, one barrier arrival per SM
-    int64_t want = lbf_cdiv((int64_t)M * M, (int64_t)kGjThreads);
-    int nb = (int)std::min<int64_t>(std::min<int64_t>(nsm, kGjMaxBlocks), std::max<int64_t>(want, 1));
-    double *S1 = scratch;                         // the second M x M buffer
-    double *pval = scratch + (size_t)M * M;       // 2 x kGjMaxBlocks
-    int *pidx = (int *)(pval + 2 * kGjMaxBlocks); // 2 x kGjMaxBlocks
-    double *amax = (double *)(pidx + 2 * kGjMaxBlocks);  // kGjMaxBlocks
-    int *pivrow = (int *)(amax + kGjMaxBlocks);   // M
-    GridBarrier *bar = (GridBarrier *)(pivrow + M + (M & 1));
-    LBF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+    int nb = (int)std::min<int64_t>(nsm, kGjMaxBlocks);
+    double *S1 = scratch;                                        // M x M
+    double *Pg = S1 + (size_t)M * M;                             // M x kGjPanel
+    double *amax = Pg + (size_t)M * kGjPanel;                    // kGjMaxBlocks
+    double *binv = amax + kGjMaxBlocks;                          // 2 x kGjPanel^2
+    int *pivrow = (int *)(binv + 2 * kGjPanel * kGjPanel);       // M
+    int *perm = pivrow + M;                                      // M
+    unsigned *done = (unsigned *)(perm + M);                     // 1
+    GridBarrier *bar = (GridBarrier *)(done + 2);
+    LBF_CUDA(cudaMemsetAsync(done, 0, 2 * sizeof(unsigned) + sizeof(GridBarrier), s));
     LBF_LAUNCH(k_gj_init, lbf_cdiv(M, 256), 256, 0, s, M, pivrow);
+    // round q reads A_q and writes A_(q+1); start so that the result lands in S1
+    const int rounds = (M + kGjPanel - 1) / kGjPanel;
+    double *A0 = S, *A1 = S1;
+    if (!(rounds & 1)) {
+        LBF_CUDA(cudaMemcpyAsync(S1, S, sizeof(double) * (size_t)M * M, cudaMemcpyDeviceToDevice, s));
+        std::swap(A0, A1);
+    }
     int *status = pl->dev_status;
-    void *args[] = {&M, &S, &S1, &pval, &pidx, &amax, &pivrow, &bar, &status};
-    LBF_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(nb), dim3(kGjThreads), args,
-                                         0, s));
+    void *args[] = {&M, &A0, &A1, &amax, &pivrow, &binv, &done, &bar, &status, &Pg};
+    LBF_CUDA(cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kGjThreads), args, smem, s));
     g_lbf_launches.fetch_add(1, std::memory_order_relaxed);
-    // after M steps the result is in the buffer step M wrote
-    if (M & 1) LBF_CUDA(cudaMemcpyAsync(S, S1, sizeof(double) * (size_t)M * M, cudaMemcpyDeviceToDevice, s));
-    LBF_LAUNCH(k_gj_unscramble, lbf_cdiv(M, 128), 128, 0, s, M, S, pivrow);
+    LBF_LAUNCH(k_gj_perm, 1, 32, 0, s, M, pivrow, perm);
+    LBF_LAUNCH(k_gj_gather, M, 256, 0, s, M, S1, perm, S);
     LBF_CHECK_LAUNCH();
     lbf_prof_mark(LBF_STAGE_INVERSE, 0, s);
     return LBF_OK;
