@@ -253,7 +253,7 @@ struct GjShared {
     unsigned long long sk[33];
     int si[33];
     double nk[kGjPanel], rk[kGjPanel];   // new pivot row, old row k
-    int rrow[2 * kGjPanel], rsrc[2 * kGjPanel], nR;
+    int rrow[2 * kGjPanel], rsrc[2 * kGjPanel], nR, pv[kGjPanel];
     double binv[kGjPanel][kGjPanel];    // B_P^-1 of the round's panel
     double V[kGjPanel][kGjPanel], G[kGjPanel][kGjPanel];
 };
@@ -277,22 +277,46 @@ __device__ bool gj_panel(int M, const double *A, int k0, int np, unsigned long l
         if (a > ck) { ck = a; ci = i; }
     }
     bool ok = true;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = 0; c < np; c++) {
         const int k = k0 + c;
-        block_argmax(ck, ci, sh.sk, sh.si);
+        // pivot: the block's (max |B_ik|, smallest i) over i >= k; warp 0 then forms the
+        // new pivot row and keeps the old row k, all before the second barrier
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, ck, o);
+            const int i = __shfl_xor_sync(0xffffffffu, ci, o);
+            if (a > ck || (a == ck && i < ci)) { ck = a; ci = i; }
+        }
+        if (lane == 0) { sh.sk[wid] = ck; sh.si[wid] = ci; }
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = blockDim.x >> 5;
+            ck = lane < nw ? sh.sk[lane] : 0ull;
+            ci = lane < nw ? sh.si[lane] : INT_MAX;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, ck, o);
+                const int i = __shfl_xor_sync(0xffffffffu, ci, o);
+                if (a > ck || (a == ck && i < ci)) { ck = a; ci = i; }
+            }
+            if (lane == 0) { sh.sk[32] = ck; sh.si[32] = ci; }
+            if (ck > tinykey && ck <= kInfBits && ci < M && lane < np) {
+                const int p = ci;
+                const double ipiv = 1.0 / gj_ld<STAGE>(Pw, c * M + p);
+                sh.rk[lane] = gj_ld<STAGE>(Pw, lane * M + k);
+                sh.nk[lane] = lane == c ? ipiv : gj_ld<STAGE>(Pw, lane * M + p) * ipiv;
+                if (lane == 0) pivrow[k] = p;
+            }
+        }
+        __syncthreads();  // rows k and p read before any row is written
+        ck = sh.sk[32];
+        ci = sh.si[32];
         if (ck <= tinykey || ck > kInfBits || ci >= M) {  // same values in every thread
             ok = false;
             break;
         }
         const int p = ci;
-        if (threadIdx.x < np) {
-            const int cc = threadIdx.x;
-            const double ipiv = 1.0 / gj_ld<STAGE>(Pw, c * M + p);
-            sh.rk[cc] = gj_ld<STAGE>(Pw, cc * M + k);
-            sh.nk[cc] = cc == c ? ipiv : gj_ld<STAGE>(Pw, cc * M + p) * ipiv;
-            if (cc == 0) pivrow[k] = p;
-        }
-        __syncthreads();  // rows k and p read before any row is written
         double nk[kGjPanel], rk[kGjPanel];
 #pragma unroll
         for (int cc = 0; cc < kGjPanel; cc++) {
@@ -336,12 +360,13 @@ __device__ bool gj_panel(int M, const double *A, int k0, int np, unsigned long l
 }
 
 // The swap set of the panel [k0, k0 + np): the rows its interchanges move (rrow) and,
-// for each, the row its value comes from (rsrc); slot[row] = entry or -1 (thread 0).
-__device__ void gj_swapset(int k0, int np, const int *pivrow, int *slot, GjShared &sh)
+// for each, the row its value comes from (rsrc); slot[row] = entry or -1 (thread 0,
+// from the pivot rows in sh.pv).
+__device__ void gj_swapset(int k0, int np, int *slot, GjShared &sh)
 {
     int n = 0;
     for (int k = k0; k < k0 + np; k++) {
-        const int p = __ldcg(&pivrow[k]);
+        const int p = sh.pv[k - k0];
         int a = -1, b = -1;
         for (int t = 0; t < n; t++)
             if (sh.rrow[t] == k) a = t;
@@ -471,7 +496,7 @@ k_gj_blocked(int M, double *A0, double *A1, double *amax, int *pivrow, double *b
         big > kInfBits ? kInfBits : abs_key(__longlong_as_double((long long)big) * (double)M * 0x1p-52);
     const int ntile = (M + kGjPanel - 1) / kGjPanel;
     // row chunks of the next panel's tile and of the panel's own tile
-    const int hc = max(64, (((M + 7) / 8 + 63) / 64) * 64), nch = (M + hc - 1) / hc;
+    const int hc = max(64, (((M + 15) / 16 + 63) / 64) * 64), nch = (M + hc - 1) / hc;
     const bool lone = nb == 1;  // a single block does everything itself
     const int nwk = lone ? 1 : (int)nb - 1, wk = lone ? 0 : (int)blockIdx.x - 1;
     if (blockIdx.x == 0 &&
@@ -484,10 +509,15 @@ k_gj_blocked(int M, double *A0, double *A1, double *amax, int *pivrow, double *b
         double *Aq1 = (q & 1) ? A0 : A1;
         if (!grid_barrier(bar, nb, status)) return;
         if (*(volatile int *)status & 4) return;  // singular: every block stops here
-        if (threadIdx.x == 0) gj_swapset(k0, np, pivrow, slot, sh);
-        for (int e = threadIdx.x; e < kGjPanel * kGjPanel; e += blockDim.x)
-            sh.binv[e / kGjPanel][e % kGjPanel] = __ldcg(&binv[(q & 1) * kGjPanel * kGjPanel + e]);
-        __syncthreads();
+        const bool worker = blockIdx.x != 0 || lone;
+        if (worker) {
+            for (int e = threadIdx.x; e < kGjPanel * kGjPanel; e += blockDim.x)
+                sh.binv[e / kGjPanel][e % kGjPanel] = __ldcg(&binv[(q & 1) * kGjPanel * kGjPanel + e]);
+            if (threadIdx.x < np) sh.pv[threadIdx.x] = __ldcg(&pivrow[k0 + threadIdx.x]);
+            __syncthreads();
+            if (threadIdx.x == 0) gj_swapset(k0, np, slot, sh);
+            __syncthreads();
+        }
         const int tp = k0 / kGjPanel, tn = n0 < M ? tp + 1 : -1;
         const int cn = tn >= 0 ? nch : 0;  // chunk items of the next panel's tile
         const int nitems = cn + nch + (ntile - 1 - (tn >= 0 ? 1 : 0));
@@ -530,7 +560,7 @@ k_gj_blocked(int M, double *A0, double *A1, double *amax, int *pivrow, double *b
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0)
+        if (worker && threadIdx.x == 0)
             for (int t = 0; t < sh.nR; t++) slot[sh.rrow[t]] = -1;
     }
 }
