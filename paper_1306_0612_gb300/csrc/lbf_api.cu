@@ -149,6 +149,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         if (o.matvec == LBF_MATVEC_FMM) {
             pl->mpole32 = A.get<float2>(cap * P32);
             pl->local32 = A.get<float2>(cap * P32);
+            pl->pull = A.get<uint32_t>(2 * cap + 4);
         }
         pl->tab32_binom = A.get<float>(2 * T * T);
         pl->tab32_tpow = A.get<float2>(49 * (T + 1));
@@ -360,6 +361,14 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
     pl->n = N + M;
     pl->opt = *opt;
     pl->P = opt->p + 1;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            delete pl;
+            return LBF_ECUDA;
+        }
+    }
     int64_t cap = box_capacity_estimate(N, *opt);
     pl->arena.base = (char *)workspace;
     pl->arena.cap = bytes;
@@ -430,6 +439,7 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
         CK(cudaStreamSynchronize(s));  // the host vectors end with this scope
     }
     if (pl->upcnt) CK(cudaMemsetAsync(pl->upcnt, 0, sizeof(int32_t) * cap, s));
+    if (pl->pull) CK(cudaMemsetAsync(pl->pull, 0, sizeof(uint32_t) * (2 * cap + 4), s));
     CK(cudaMemcpyAsync(pl->tab_tpow, tpow.data(), sizeof(double2) * tpow.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(pl->dev_status, 0, sizeof(int), s));
     CK(cudaMemsetAsync(pl->red_count, 0, 4 * sizeof(unsigned), s));

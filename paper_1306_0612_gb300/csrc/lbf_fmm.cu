@@ -391,19 +391,20 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                      mp, pl->upcnt, gate);
         LBF_CHECK_LAUNCH();
     }
-    // In double the downward pass runs level by level (L2L + M2L + P2L).  In float
-    // every box's M2L + P2L runs in one launch and the leaf kernel evaluates each
-    // ancestor's expansion at the targets instead of shifting them down: float
-    // arithmetic is cheap on this GPU, launches are not.
-    const int walk = dbl || MODE == fmm::kLeafDeriv ? 0 : 1;
+    // In double (and double-float) the downward pass runs level by level (L2L + M2L +
+    // P2L).  In float every box runs in one launch, taking the boxes in index order and
+    // shifting its parent's full expansion down once the parent is done, so the leaf
+    // kernel evaluates one expansion per target.
     {
         const int wpb = down_warps<R>(P);
         const size_t smem = down_smem<R>(P, wpb);
-        if (walk) {
-            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s,
-                         (int64_t)0, T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist,
-                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc,
-                         gate, 0);
+        if (!dbl) {
+            if (!pl->pull) return LBF_EINVAL;
+            const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, wpb), 4 * (int64_t)std::max(pl->nsm, 1));
+            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, grid, 32 * wpb, smem, s, (int64_t)0, T.nbox,
+                         T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin, T.end,
+                         g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate, 2, pl->pull,
+                         pl->dev_status);
             LBF_CHECK_LAUNCH();
         } else {
             for (int l = 0; l < T.nlev; l++) {
@@ -412,17 +413,15 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                 LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s,
                              ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx,
                              T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc,
-                             gate, 1);
+                             gate, 1, (unsigned *)nullptr, pl->dev_status);
                 LBF_CHECK_LAUNCH();
             }
         }
     }
-    const size_t walk_smem =
-        walk ? sizeof(cx<R>) * (size_t)fmm::kLeafWarps * (LBF_ANC_STRIDE - 1) * P : 0;
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
-                 32 * fmm::kLeafWarps, walk_smem, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
+                 32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
-                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, pl->anc, walk);
+                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -438,10 +437,6 @@ int lbf_fmm_init_attrs()
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_up<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(k_evaluate_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(int32_t) * 2 * kEvalFront * kEvalWarps)));
-    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafForward>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafTranspose>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     return LBF_OK;
 }

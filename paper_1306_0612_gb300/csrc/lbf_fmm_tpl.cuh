@@ -279,6 +279,9 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
     }
 }
 
+constexpr unsigned kPullSpins = 1u << 24;
+constexpr unsigned kGrab = 1;
+
 // Downward pass for one level (see lbf_fmm.cu): L2L + M2L (V) + P2L (X).
 // P2L lanes take source nodes and run the power recurrence; their terms go
 // through shared memory and lanes then take coefficients and sum in node order.
@@ -293,7 +296,7 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                        const cx<R> *__restrict__ dtab, const double2 *__restrict__ xi,
                        const cx<R> *__restrict__ uloc, const cx<R> *__restrict__ q,
                        const cx<R> *__restrict__ mp, cx<R> *__restrict__ loc, const int *gate,
-                       int with_l2l)
+                       int with_l2l, unsigned *pull, int *status)
 {
     if (gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -310,19 +313,46 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         Cd[e] = k >= l ? binom[k * LBF_MAX_TERMS + l] : R(0);
     }
     __syncthreads();
-    int64_t b = ls + blockIdx.x * (int64_t)nw + wid;
-    if (b >= le) return;
     const int l0 = lane, l1 = lane + 32;
     const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
+    // with_l2l == 2: every box in one launch, in two phases.  Phase 1 takes runs of
+    // boxes from a counter and writes each one's M2L + P2L part; phase 2 takes them
+    // again in increasing index order (level by level) and adds the parent's full expansion
+    // shifted down (L2L), once the parent is done.  Every box a warp waits for was
+    // taken earlier by a running warp, so each wait ends.  The last warp to finish
+    // resets the counters and advances the epoch that marks a box done.
+    // pull: [0] phase-1 counter, [1] finished warps, [2] epoch, [3] phase-2 counter,
+    // then per box the epoch of its phase-1 part and of its full expansion.
+    unsigned *part = pull + 4, *done = pull + 4 + (le - ls);
+    unsigned epoch = 0;
+    if (with_l2l == 2) {
+        if (lane == 0) epoch = *(volatile unsigned *)&pull[2];
+        epoch = __shfl_sync(0xffffffffu, epoch, 0);
+    }
+    unsigned cb = 0, ce = 0;  // the warp's current run of boxes (kGrab at a time)
+    for (int64_t it = 0;; it++) {
+    int64_t b;
+    if (with_l2l == 2) {
+        if (cb == ce) {
+            unsigned bi = 0;
+            if (lane == 0) bi = atomicAdd(&pull[0], kGrab);
+            cb = __shfl_sync(0xffffffffu, bi, 0);
+            ce = cb + kGrab;
+        }
+        b = ls + (int64_t)cb++;
+    } else {
+        b = it == 0 ? ls + blockIdx.x * (int64_t)nw + wid : le;
+    }
+    if (b >= le) break;
     int bx = ix[b], by = iy[b];
     cx<R> accL0 = mk<R>(0, 0), accL1 = mk<R>(0, 0);
-    // L2L: b'_l = (2d)^-l sum_{k>=l} C(k,l) d^k b_k (the parent belongs to the previous launch);
-    // skipped when the leaf kernel evaluates every ancestor's expansion itself (with_l2l == 0)
-    if (with_l2l && level[b] >= 3) {
+    // L2L: b'_l = (2d)^-l sum_{k>=l} C(k,l) d^k b_k, from the parent's full local expansion
+    // (with_l2l == 1: written by the previous launch; 2: by another warp of this launch)
+    auto l2l = [&]() {
         int p = parent[b];
         int d = (bx & 1) + 2 * (by & 1);
         const cx<R> *dp = dpow(dtab, d);
-        for (int k = lane; k < P; k += 32) A[k] = cmul(loc[(int64_t)p * P + k], dp[k]);
+        for (int k = lane; k < P; k += 32) A[k] = cmul(ldcg_cx(&loc[(int64_t)p * P + k]), dp[k]);
         __syncwarp();
         cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
         for (int k = 0; k < P; k++) {
@@ -340,7 +370,8 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         accL0 = cmul(inv[l0], s0);
         if (l1 < P) accL1 = cmul(inv[l1], s1);
         __syncwarp();
-    }
+    };
+    if (with_l2l == 1 && level[b] >= 3) l2l();
     // M2L: (-1)^l t^(l+1) sum_k C(k+l, l) t^k a_k,  t = 1/(2 (dx + i dy))  (times 1/r below)
     cx<R> accF0 = mk<R>(0, 0), accF1 = mk<R>(0, 0);
     if (P <= 16) {
@@ -470,10 +501,91 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     else irr = (R)ir;
     if (l0 < P) loc[b * P + l0] = mk<R>(accL0.x + accF0.x * irr, accL0.y + accF0.y * irr);
     if (l1 < P) loc[b * P + l1] = mk<R>(accL1.x + accF1.x * irr, accL1.y + accF1.y * irr);
+    if (with_l2l == 2) {
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicExch(&part[b - ls], epoch + 1u);
+    }
+    }  // boxes
+    if (with_l2l != 2) return;
+    // phase 2: full expansions, top down
+    auto wait_for = [&](const unsigned *flag) {
+        if (lane == 0) {
+            unsigned spins = 0;
+            while (*(volatile const unsigned *)flag != epoch + 1u)
+                if (++spins > kPullSpins) {
+                    atomicOr(status, LBF_DEV_TIMEOUT);
+                    break;
+                }
+        }
+        __syncwarp();
+        __threadfence();
+    };
+    cb = ce = 0;
+    for (;;) {
+        if (cb == ce) {
+            unsigned bi = 0;
+            if (lane == 0) bi = atomicAdd(&pull[3], kGrab);
+            cb = __shfl_sync(0xffffffffu, bi, 0);
+            ce = cb + kGrab;
+        }
+        const int64_t b = ls + (int64_t)cb++;
+        if (b >= le) break;
+        wait_for(&part[b - ls]);
+        if (level[b] >= 3) {
+            const int p = parent[b];
+            wait_for(&done[p - ls]);
+            const int bx = ix[b], by = iy[b], d = (bx & 1) + 2 * (by & 1);
+            const cx<R> *dp = dpow(dtab, d);
+            for (int k = lane; k < P; k += 32) A[k] = cmul(ldcg_cx(&loc[(int64_t)p * P + k]), dp[k]);
+            __syncwarp();
+            cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+            for (int k = 0; k < P; k++) {
+                cx<R> a = A[k];
+                R c0 = Cd[k * P + lc0];
+                s0.x = fm(c0, a.x, s0.x);
+                s0.y = fm(c0, a.y, s0.y);
+                if (l1 < P) {
+                    R c1 = Cd[k * P + lc1];
+                    s1.x = fm(c1, a.x, s1.x);
+                    s1.y = fm(c1, a.y, s1.y);
+                }
+            }
+            const cx<R> *inv = d2inv(dtab, d);
+            if (l0 < P) {
+                const cx<R> own = ldcg_cx(&loc[b * P + l0]);
+                loc[b * P + l0] = cfma(inv[l0], s0, own);
+            }
+            if (l1 < P) {
+                const cx<R> own = ldcg_cx(&loc[b * P + l1]);
+                loc[b * P + l1] = cfma(inv[l1], s1, own);
+            }
+            __threadfence();
+            __syncwarp();
+        }
+        if (lane == 0) atomicExch(&done[b - ls], epoch + 1u);
+    }
+    if (lane == 0) {
+        const unsigned total = gridDim.x * (unsigned)nw;
+        if (atomicAdd(&pull[1], 1u) == total - 1u) {
+            pull[0] = 0u;
+            pull[1] = 0u;
+            pull[3] = 0u;
+            __threadfence();
+            atomicExch(&pull[2], epoch + 1u);
+        }
+    }
 }
 
 constexpr int kLeafWarps = 4;
 constexpr int kSrcChunk = 256;
+
+template <typename R> struct LeafSrc {
+    cx<R> z, q;
+};
+__device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool positive(double x) { return x > 0.0; }
+__device__ __forceinline__ bool positive(df64 x) { return x.hi > 0.0f; }
 
 // What the leaf kernel writes for node i (all with the self pair excluded):
 //   kLeafForward   v_i = 2 [ (1/2pi) Im sum_j q_j/(xi_j - xi_i) + dself_i sigma_i + s ],
@@ -484,8 +596,8 @@ constexpr int kSrcChunk = 256;
 //   kLeafDeriv     Phi'(xi_i) = -sum_j q_j/(xi_i - xi_j)^2 as a double2.
 constexpr int kLeafForward = 0, kLeafTranspose = 1, kLeafDeriv = 2;
 
-// Per leaf: far field (L2P of the leaf's local expansion, or of every ancestor's,
-// and M2P from W(b)), near field (P2P over U(b)), then the output above.  A lane
+// Per leaf: far field (L2P of the leaf's full local expansion and M2P from W(b)),
+// near field (P2P over U(b)), then the output above.  A lane
 // owns one target; the sources of U(b) pass through shared memory in chunks and
 // every lane reads each one (broadcast).  Near-field positions are taken relative
 // to the leaf centre in units of its half-width r, so close nodes cancel before
@@ -505,32 +617,16 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const cx<R> *__restrict__ loc, const double *__restrict__ sigma,
                        const double *__restrict__ dself, const double2 *__restrict__ w,
                        const double *__restrict__ beta, const double *__restrict__ bsig,
-                       double *__restrict__ v, const int *gate, const int32_t *__restrict__ anc,
-                       int walk)
+                       double *__restrict__ v, const int *gate)
 {
     if (gate_closed(gate)) return;
     constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
-    __shared__ cx<R> sx[kLeafWarps][kSrcChunk];
-    __shared__ cx<R> sq[kLeafWarps][kSrcChunk];
-    __shared__ int32_t sj[kLeafWarps][kSrcChunk];
+    __shared__ LeafSrc<R> ss[kLeafWarps][kSrcChunk];  // (position in units of r, charge)
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t t = blockIdx.x * (int64_t)kLeafWarps + wid;
     if (t >= nleaf) return;
     const int b = leaves[t];
     const int lt = level[b], tx = ix[b], ty = iy[b];
-    // the ancestor walk: every lane evaluates the same ancestors' expansions, so the warp
-    // stages them in shared memory once per leaf (coalesced) and the lanes read broadcasts
-    extern __shared__ __align__(16) unsigned char walk_sm[];
-    cx<R> *sl = (cx<R> *)walk_sm + (size_t)wid * (LBF_ANC_STRIDE - 1) * P;
-    if (walk) {
-        const int32_t *ab = anc + (int64_t)b * LBF_ANC_STRIDE;
-        const int nA = lt - 1 > 0 ? lt - 1 : 0;
-        for (int e = lane; e < nA * P; e += 32) {
-            const int sh = e / P, l = e - sh * P;
-            sl[e] = loc[(int64_t)ab[sh] * P + l];
-        }
-        __syncwarp();
-    }
     double cxd = 0, cyd = 0, ir = 0;
     bool have_c = false;
     auto need_centre = [&]() {  // double centre: the double path and float fallbacks only
@@ -555,7 +651,6 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         // near field: TP >= nt target slots, 32/TP lanes per target splitting the sources
         const int TP = nt <= 1 ? 1 : 1 << (32 - __clz(nt - 1));
         const int slot = lane & (TP - 1), grp = lane / TP, G = 32 / TP;
-        const int ti = tb + slot;
         const bool pact = slot < nt;
         cx<R> u = mk<R>(0, 0);  // (z - c)/r
         cx<R> phi = mk<R>(0, 0);  // far field: Phi (or Phi' in kLeafDeriv)
@@ -572,24 +667,9 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                 for (int l = P - 2; l >= 1; l--)
                     d = cfma(d, u, mk<R>((R)l * lb[l].x, (R)l * lb[l].y));
                 phi = mk<R>(d.x * irr, d.y * irr);
-            } else if (!walk) {
+            } else {
                 phi = lb[P - 1];
                 for (int l = P - 2; l >= 0; l--) phi = cfma(phi, u, lb[l]);
-            } else {
-                // every ancestor's own local expansion at the target (no L2L chain):
-                // (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s, s = depth gap,
-                // ix_b - 2^s ix_a = the low s bits of ix_b; coefficients staged above
-                for (int sh = 0; sh <= lt - 2; sh++) {
-                    const R sc = pow2<R>(-sh);
-                    const int dxi = tx & ((1 << sh) - 1), dyi = ty & ((1 << sh) - 1);
-                    cx<R> ua = mk<R>((R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + u.x * sc,
-                                     (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + u.y * sc);
-                    const cx<R> *la = sl + sh * P;
-                    cx<R> tt = la[P - 1];
-                    for (int l = P - 2; l >= 0; l--) tt = cfma(tt, ua, la[l]);
-                    phi.x += tt.x;
-                    phi.y += tt.y;
-                }
             }
             for (int wq = wptr[b]; wq < wptr[b + 1]; wq++) {
                 const int s = widx[wq];
@@ -643,12 +723,14 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         auto process = [&]() {
             __syncwarp();
             if (pact) {
+#pragma unroll 4
                 for (int m = grp; m < fill; m += G) {
-                    if (sj[wid][m] == ti) continue;
-                    const cx<R> zs = sx[wid][m];
-                    const cx<R> qq = sq[wid][m];
+                    const LeafSrc<R> sm = ss[wid][m];
+                    const cx<R> zs = sm.z, qq = sm.q;
                     const R dr = zs.x - ut.x, di = zs.y - ut.y;
-                    const R ir2 = rcp(fm(dr, dr, di * di));
+                    // the target itself (the only source at distance 0) adds nothing
+                    const R d2 = fm(dr, dr, di * di);
+                    const R ir2 = positive(d2) ? rcp(d2) : R(0.0f);
                     if constexpr (MODE == kLeafForward) {
                         accI = fm(fm(qq.y, dr, -qq.x * di), ir2, accI);
                     } else if constexpr (MODE == kLeafTranspose) {
@@ -691,9 +773,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                         double2 zs = xi[sb + m];
                         zr = mk<R>((R)((zs.x - cxd) * ir), (R)((zs.y - cyd) * ir));
                     }
-                    sx[wid][fill + m] = zr;
-                    sq[wid][fill + m] = q[sb + m];
-                    sj[wid][fill + m] = sb + m;
+                    ss[wid][fill + m] = LeafSrc<R>{zr, q[sb + m]};
                 }
                 fill += take;
                 sb += take;

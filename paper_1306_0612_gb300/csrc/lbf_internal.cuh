@@ -154,6 +154,11 @@ struct lbf_plan {
     // last solve: Arnoldi steps, FP64 applications, FP32 applications, refinement steps
     int64_t stats[4] = {0, 0, 0, 0};
     int32_t *upcnt = nullptr;   // per-box child arrival counters of the upward pass (kept at 0)
+    // float downward pass: [0], [3] box counters of its two phases, [1] finished warps,
+    // [2] epoch, then per box the epochs in which its M2L + P2L part and its full local
+    // expansion were written (nbox each)
+    uint32_t *pull = nullptr;
+    int nsm = 0;                // streaming multiprocessors of the plan's device
     double *v = nullptr;        // (I + K - I) sigma = K sigma, doubled scaling
     double *bsig = nullptr;     // scalar beta . sigma
     double *red = nullptr;      // reduction partials
