@@ -210,8 +210,7 @@ def kernel_work(name, c, bc, P, P32, N):
     if base == "leaf":
         return 11 * c["p2p_pairs"] + 8 * Q * N + 8 * Q * c["w_pairs"] + 10 * N, "TFLOP/s"
     if base == "down":
-        l2l = 0 if f32 else c["l2l"]
-        return 8 * Q * Q * (c["m2l"] + l2l) + 8 * Q * c["x_pairs"], "TFLOP/s"
+        return 8 * Q * Q * (c["m2l"] + c["l2l"]) + 8 * Q * c["x_pairs"], "TFLOP/s"
     if base == "up":
         return 8 * Q * N + 8 * Q * Q * c["m2m"], "TFLOP/s"
     if base == "direct":

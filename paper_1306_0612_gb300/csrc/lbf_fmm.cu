@@ -352,11 +352,18 @@ template <typename R> size_t down_smem(int P, int wpb)
 }
 constexpr size_t kSmemCap = 200 * 1024;
 
+// warps per block of the downward pass: the most resident warps per SM that its
+// shared memory allows (228 KB per SM, 1 KB of it reserved per block)
 template <typename R> int down_warps(int P)
 {
-    int w = 8;
-    while (w > 1 && down_smem<R>(P, w) > kSmemCap) w >>= 1;
-    return w;
+    int best = 1, most = 0;
+    for (int w = 8; w >= 1; w--) {
+        const size_t sm = down_smem<R>(P, w);
+        if (sm > kSmemCap) continue;
+        const int resident = w * (int)((228 * 1024) / (sm + 1024));
+        if (resident > most) { most = resident; best = w; }
+    }
+    return best;
 }
 
 struct FmmArrays {
