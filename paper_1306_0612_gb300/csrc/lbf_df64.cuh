@@ -83,6 +83,9 @@ __device__ __forceinline__ df64 df_rcp(df64 a)
 
 __device__ __forceinline__ df64 operator/(df64 a, df64 b) { return a * df_rcp(b); }
 
+// the float nearest to hi + lo
+__device__ __forceinline__ float df_round(df64 a) { return __fadd_rn(a.hi, a.lo); }
+
 // exact scaling by a power of two
 __device__ __forceinline__ df64 df_ldexp(df64 a, float p2) { return df64(a.hi * p2, a.lo * p2, 0); }
 

@@ -386,6 +386,8 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     const R *binom = (const R *)a.binom;
     const cx<R> *tpow = (const cx<R> *)a.tpow, *dsh = (const cx<R> *)a.dshift;
     const cx<R> *uloc = (const cx<R> *)a.uloc;
+    // the float passes form coordinates across large level gaps in double-float
+    const cx<df64> *udf = sizeof(R) == sizeof(float) ? (const cx<df64> *)pl->udf : nullptr;
     const bool dbl = sizeof(R) == sizeof(double);
     const int kid_up = dbl ? LBF_KERNEL_UP : LBF_KERNEL_UP32;
     const int kid_down = dbl ? LBF_KERNEL_DOWN : LBF_KERNEL_DOWN32;
@@ -411,7 +413,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
             LBF_LAUNCH_P(kid_down, fmm::k_down<R>, grid, 32 * wpb, smem, s, (int64_t)0, T.nbox,
                          T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin, T.end,
                          g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate, 2, pl->pull,
-                         pl->dev_status);
+                         pl->dev_status, udf);
             LBF_CHECK_LAUNCH();
         } else {
             for (int l = 0; l < T.nlev; l++) {
@@ -420,7 +422,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                 LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s,
                              ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx,
                              T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc,
-                             gate, 1, (unsigned *)nullptr, pl->dev_status);
+                             gate, 1, (unsigned *)nullptr, pl->dev_status, udf);
                 LBF_CHECK_LAUNCH();
             }
         }
@@ -428,7 +430,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
                  32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
-                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate);
+                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }

@@ -35,6 +35,11 @@ template <typename R> constexpr bool kLocal = !std::is_same<R, double>::value;
 // largest level gap over which a leaf-local coordinate is rescaled into a coarser
 // box's frame (its rounding grows by 2 per level; wider gaps use the positions)
 template <typename R> constexpr int kMaxGap = std::is_same<R, float>::value ? 3 : 12;
+// float: level gaps beyond kMaxGap (up to kDfGap, where box offsets stay exact in float)
+// form the coordinate in double-float from the node's double-float leaf-local
+// coordinate, so the cancellation between a large rescaled coordinate and the box
+// offset happens in ~48 bits, then round it to float
+constexpr int kDfGap = 20;
 
 template <typename R> __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
 template <typename R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b)
@@ -296,7 +301,7 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                        const cx<R> *__restrict__ dtab, const double2 *__restrict__ xi,
                        const cx<R> *__restrict__ uloc, const cx<R> *__restrict__ q,
                        const cx<R> *__restrict__ mp, cx<R> *__restrict__ loc, const int *gate,
-                       int with_l2l, unsigned *pull, int *status)
+                       int with_l2l, unsigned *pull, int *status, const cx<df64> *__restrict__ udf)
 {
     if (gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -453,13 +458,15 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     for (int xq = 0; xq < nx[b]; xq++) {
         int s = xlist[b * 16 + xq];
         // float, double-float: the source's leaf-local coordinate rescaled into this box's frame
-        bool local = false;
+        bool local = false, dfp = false;
         R fs = R(0.0f);
         cx<R> os = mk<R>(R(0.0f), R(0.0f));
         if constexpr (kLocal<R>) {
             const int ls = level[s];
             local = lb >= ls && lb - ls <= kMaxGap<R>;
-            if (local) {
+            if constexpr (std::is_same<R, float>::value)
+                dfp = !local && udf && lb >= ls && lb - ls <= kDfGap;
+            if (local || dfp) {
                 fs = R(pow2<float>(lb - ls));
                 os = offset_cx<R>(centre_offset(ls, ix[s], iy[s], lb, bx, by));
             }
@@ -471,6 +478,12 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                 if (local) {
                     const cx<R> uu = uloc[j];
                     tau = crcp(mk<R>(-(uu.x * fs + os.x), -(uu.y * fs + os.y)));
+                } else if (dfp) {
+                    if constexpr (std::is_same<R, float>::value) {
+                        const cx<df64> ud = udf[j];
+                        tau = crcp(mk<R>(-df_round(df_ldexp(ud.x, fs) + df64(os.x)),
+                                         -df_round(df_ldexp(ud.y, fs) + df64(os.y))));
+                    }
                 } else {
                     need_centre();
                     double2 z = xi[j];
@@ -617,7 +630,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const cx<R> *__restrict__ loc, const double *__restrict__ sigma,
                        const double *__restrict__ dself, const double2 *__restrict__ w,
                        const double *__restrict__ beta, const double *__restrict__ bsig,
-                       double *__restrict__ v, const int *gate)
+                       double *__restrict__ v, const int *gate, const cx<df64> *__restrict__ udf)
 {
     if (gate_closed(gate)) return;
     constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
@@ -685,6 +698,17 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                         zs = mk<R>(u.x * f + o.x, u.y * f + o.y);
                         isr = irr * f;
                     }
+                    if constexpr (std::is_same<R, float>::value) {
+                        if (!local && udf && ls >= lt && ls - lt <= kDfGap) {
+                            const float f = pow2<float>(ls - lt);
+                            const float2 o = centre_offset(lt, tx, ty, ls, ix[s], iy[s]);
+                            const cx<df64> ud = udf[i];
+                            zs = mk<R>(df_round(df_ldexp(ud.x, f) + df64(o.x)),
+                                       df_round(df_ldexp(ud.y, f) + df64(o.y)));
+                            isr = irr * f;
+                            local = true;
+                        }
+                    }
                 }
                 if (!local) {
                     double2 zi = xi[i];
@@ -750,13 +774,15 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         for (int uq = uptr[b]; uq < uptr[b + 1]; uq++) {
             const int s = uidx[uq];
             int sb = bg[s], se = en[s];
-            bool local = false;
+            bool local = false, dfp = false;
             R fs = R(0.0f);
             cx<R> os = mk<R>(R(0.0f), R(0.0f));
             if constexpr (kF32) {
                 const int ls = level[s];
                 local = ls >= lt && ls - lt <= 16;
-                if (local) {
+                if constexpr (std::is_same<R, float>::value)
+                    dfp = !local && udf && ls < lt && lt - ls <= kDfGap;  // a coarser source leaf
+                if (local || dfp) {
                     fs = R(pow2<float>(lt - ls));
                     os = offset_cx<R>(centre_offset(ls, ix[s], iy[s], lt, tx, ty));
                 }
@@ -768,6 +794,12 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                     if (local) {
                         const cx<R> uu = uloc[sb + m];
                         zr = mk<R>(uu.x * fs + os.x, uu.y * fs + os.y);
+                    } else if (dfp) {
+                        if constexpr (std::is_same<R, float>::value) {
+                            const cx<df64> ud = udf[sb + m];
+                            zr = mk<R>(df_round(df_ldexp(ud.x, fs) + df64(os.x)),
+                                       df_round(df_ldexp(ud.y, fs) + df64(os.y)));
+                        }
                     } else {
                         need_centre();
                         double2 zs = xi[sb + m];
