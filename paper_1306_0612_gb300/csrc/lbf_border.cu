@@ -55,6 +55,13 @@ __device__ __forceinline__ cz<double> zinv(cz<double> a)
     return cz<double>{a.x * d, -a.y * d};
 }
 
+// an expansion coefficient written by another warp of the same launch (through L2)
+__device__ __forceinline__ cz<float> ldcg_cz(const cz<float> *p)
+{
+    const float2 v = __ldcg((const float2 *)p);
+    return cz<float>{v.x, v.y};
+}
+
 template <typename R> __device__ __forceinline__ R wsum(R v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -553,6 +560,100 @@ __global__ void k_mp_l2l(int64_t ls, int64_t le, int P, const int32_t *__restric
     }
 }
 
+// The float operator's L2L chain in one launch: warps take the boxes in index order
+// (level by level) from a counter and add the parent's full expansion shifted down once
+// the parent is marked done (a per-box epoch word; the parent was taken earlier by a
+// running warp, so every wait ends; each wait is bounded and reports a time-out).  The
+// last warp to finish resets the counters and advances the epoch.  pull: [1] finished
+// warps, [2] epoch, [3] box counter, then nbox words unused here and nbox done epochs.
+constexpr unsigned kChainSpins = 1u << 24;
+
+template <typename R>
+__global__ void k_mp_chain(int64_t nbox, int P, const int32_t *__restrict__ parent,
+                           const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
+                           const int32_t *__restrict__ iy, const R *__restrict__ binom,
+                           const cz<R> *__restrict__ dtab, cz<R> *loc, unsigned *pull, int *status,
+                           const int *gate)
+{
+    if (gate && *gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smr[];
+    const int nw = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tl = (P * P * (int)sizeof(R) + 15) / 16 * 16;
+    R *Cd = (R *)smr;  // Cd[k*P + l] = C(k, l) (0 for k < l)
+    cz<R> *A = (cz<R> *)(smr + tl) + (size_t)wid * P;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        const int k = e / P, l = e % P;
+        Cd[e] = k >= l ? binom[k * LBF_MAX_TERMS + l] : R(0);
+    }
+    __syncthreads();
+    unsigned *done = pull + 4 + nbox;
+    unsigned epoch = 0;
+    if (lane == 0) epoch = *(volatile unsigned *)&pull[2];
+    epoch = __shfl_sync(0xffffffffu, epoch, 0);
+    const int l0 = lane, l1 = lane + 32;
+    const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
+    for (;;) {
+        unsigned bi = 0;
+        if (lane == 0) bi = atomicAdd(&pull[3], 1u);
+        const int64_t b = (int64_t)__shfl_sync(0xffffffffu, bi, 0);
+        if (b >= nbox) break;
+        if (level[b] >= 3) {
+            const int p = parent[b];
+            if (lane == 0) {
+                unsigned spins = 0;
+                while (*(volatile unsigned *)&done[p] != epoch + 1u)
+                    if (++spins > kChainSpins) {
+                        atomicOr(status, LBF_DEV_TIMEOUT);
+                        break;
+                    }
+            }
+            __syncwarp();
+            __threadfence();
+            const int d = (ix[b] & 1) + 2 * (iy[b] & 1);
+            const cz<R> *dp = dtab + (size_t)d * (LBF_MAX_TERMS + 1);
+            const cz<R> *inv = dtab + (size_t)(4 + d) * (LBF_MAX_TERMS + 1);
+            for (int k = lane; k < P; k += 32) {
+                const cz<R> pk = ldcg_cz(&loc[(int64_t)p * P + k]);
+                A[k] = zmul(pk, dp[k]);
+            }
+            __syncwarp();
+            cz<R> s0{0, 0}, s1{0, 0};
+            for (int k = 0; k < P; k++) {
+                const cz<R> a = A[k];
+                const R c0 = Cd[k * P + lc0];
+                s0.x = fmr(c0, a.x, s0.x);
+                s0.y = fmr(c0, a.y, s0.y);
+                if (l1 < P) {
+                    const R c1 = Cd[k * P + lc1];
+                    s1.x = fmr(c1, a.x, s1.x);
+                    s1.y = fmr(c1, a.y, s1.y);
+                }
+            }
+            if (l0 < P) {
+                const cz<R> o = loc[b * P + l0], t = zmul(inv[l0], s0);
+                loc[b * P + l0] = cz<R>{o.x + t.x, o.y + t.y};
+            }
+            if (l1 < P) {
+                const cz<R> o = loc[b * P + l1], t = zmul(inv[l1], s1);
+                loc[b * P + l1] = cz<R>{o.x + t.x, o.y + t.y};
+            }
+            __threadfence();
+            __syncwarp();
+        }
+        if (lane == 0) atomicExch(&done[b], epoch + 1u);
+    }
+    if (lane == 0) {
+        const unsigned total = gridDim.x * (unsigned)nw;
+        if (atomicAdd(&pull[1], 1u) == total - 1u) {
+            pull[1] = 0u;
+            pull[3] = 0u;
+            __threadfence();
+            atomicExch(&pull[2], epoch + 1u);
+        }
+    }
+}
+
 // The centres a leaf sums directly, 32 per warp: for every node i of the leaf,
 // partial[nodebase[i] + k] = sum over chunk k of y_m log|xi_i - xi_m| (in double; the
 // float operator takes the log in float).  Spreading a long list over many warps keeps
@@ -844,7 +945,17 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
         LBF_LAUNCH(k_mp_p2l<float>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
                    (cz<float> *)B.loc32, B.sums, gate);
-        // float: no L2L chain, the evaluation walks each node's ancestors
+        // float: the L2L chain in one launch (with the float FMM's counters and tables),
+        // else the evaluation walks each node's ancestors
+        const bool chain = pl->pull != nullptr;
+        if (chain) {
+            const int cw = 8;
+            const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_chain<float>, grid, 32 * cw, l2l_smem<float>(P, cw), s,
+                         T.nbox, P, T.parent, T.level, T.ix, T.iy, pl->tab32_binom,
+                         (const cz<float> *)pl->tab32_dshift, (cz<float> *)B.loc32, pl->pull,
+                         pl->dev_status, gate);
+        }
         if (B.nchunks)
             LBF_LAUNCH(k_mp_near<float>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks, B.chunk_leaf,
                        B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi, B.xc, y,
@@ -852,7 +963,8 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
         LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_eval<float>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
                      pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<float> *)B.loc32,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, pl->anc, pl->u32, 1, (const cz<float> *)nullptr, B.nodebase,
+                     out, gate, pl->anc, pl->u32, chain ? 0 : 1,
+                     chain ? (const cz<float> *)pl->u32 : (const cz<float> *)nullptr, B.nodebase,
                      B.partial);
     } else if (pl->udf) {
         // the accurate operator in double-float (P2L terms formed in double)

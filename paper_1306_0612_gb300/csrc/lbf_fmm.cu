@@ -70,11 +70,18 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
         last = (c == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double t = 0.0;
-        for (unsigned b = 0; b < gridDim.x; b++) t += ((volatile double *)part)[b];
-        *out = t;
+    if (!last) return;
+    // the last block sums the block partials in a fixed order (strided, then by warps)
+    __threadfence();
+    double t = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(&part[b]);
+    t = warp_sum(t);
+    if (lane == 0) sh[wid] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) u += sh[k];
+        *out = u;
         *count = 0u;
     }
 }
