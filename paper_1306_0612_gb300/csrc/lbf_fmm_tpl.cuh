@@ -382,19 +382,31 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     if (P <= 16) {
         // two half-warps take two V-list boxes at a time; lane gl of a half-warp owns
         // coefficient gl, and the halves are summed at the end
+        // the V list's boxes and offset indices are loaded once, a lane per entry (at most
+        // 27), and the next pair's multipole coefficients are fetched one step ahead
         const int grp = lane >> 4, gl = lane & 15;
         const int glc = gl < P ? gl : 0;
         cx<R> *Ag = A + grp * P;
-        for (int v0 = 0; v0 < nv[b]; v0 += 2) {
+        const int nvb = nv[b];
+        int vs = 0, vo = 0;
+        if (lane < nvb) {
+            vs = vlist[b * 27 + lane];
+            vo = (bx - ix[vs] + 3) * 7 + (by - iy[vs] + 3);
+        }
+        cx<R> mnext = mk<R>(0, 0);
+        {
+            const int s0 = __shfl_sync(0xffffffffu, vs, grp);
+            if (grp < nvb && gl < P) mnext = mp[(int64_t)s0 * P + gl];
+        }
+        for (int v0 = 0; v0 < nvb; v0 += 2) {
             const int vq = v0 + grp;
-            const bool on = vq < nv[b];
-            const cx<R> *tp = tpow;
-            if (on) {
-                int s = vlist[b * 27 + vq];
-                int o = (bx - ix[s] + 3) * 7 + (by - iy[s] + 3);
-                tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
-                if (gl < P) Ag[gl] = cmul(mp[(int64_t)s * P + gl], tp[gl]);
-            }
+            const bool on = vq < nvb;
+            const int o = __shfl_sync(0xffffffffu, vo, vq & 31);
+            const int sn = __shfl_sync(0xffffffffu, vs, (vq + 2) & 31);
+            const cx<R> mcur = mnext;
+            if (vq + 2 < nvb && gl < P) mnext = mp[(int64_t)sn * P + gl];
+            const cx<R> *tp = tpow + (size_t)(on ? o : 0) * (LBF_MAX_TERMS + 1);
+            if (on && gl < P) Ag[gl] = cmul(mcur, tp[gl]);
             __syncwarp();
             if (on && gl < P) {
                 cx<R> s0 = mk<R>(0, 0);
@@ -414,11 +426,29 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         accF0.y += __shfl_down_sync(0xffffffffu, accF0.y, 16);
         if (lane >= 16) accF0 = mk<R>(0, 0);
     } else {
-        for (int vq = 0; vq < nv[b]; vq++) {
-            int s = vlist[b * 27 + vq];
-            int o = (bx - ix[s] + 3) * 7 + (by - iy[s] + 3);
+        // V-list records loaded once (a lane per entry); with P <= 32 the next box's
+        // coefficients are fetched one step ahead
+        const int nvb = nv[b];
+        int vs = 0, vo = 0;
+        if (lane < nvb) {
+            vs = vlist[b * 27 + lane];
+            vo = (bx - ix[vs] + 3) * 7 + (by - iy[vs] + 3);
+        }
+        cx<R> mnext = mk<R>(0, 0);
+        const int sfirst = __shfl_sync(0xffffffffu, vs, 0);
+        if (P <= 32 && nvb > 0 && lane < P) mnext = mp[(int64_t)sfirst * P + lane];
+        for (int vq = 0; vq < nvb; vq++) {
+            const int s = __shfl_sync(0xffffffffu, vs, vq);
+            const int o = __shfl_sync(0xffffffffu, vo, vq);
+            const int sn = __shfl_sync(0xffffffffu, vs, (vq + 1) & 31);
             const cx<R> *tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
-            for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
+            if (P <= 32) {
+                const cx<R> mcur = mnext;
+                if (vq + 1 < nvb && lane < P) mnext = mp[(int64_t)sn * P + lane];
+                if (lane < P) A[lane] = cmul(mcur, tp[lane]);
+            } else {
+                for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
+            }
             __syncwarp();
             cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
             for (int k = 0; k < P; k++) {
@@ -455,26 +485,38 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         have_c = true;
     };
     if constexpr (!kLocal<R>) need_centre();
-    for (int xq = 0; xq < nx[b]; xq++) {
-        int s = xlist[b * 16 + xq];
+    // the X list's box records (at most 16), a lane per box, then broadcast
+    const int nxb = nx[b];
+    int xr_s = 0, xr_l = 0, xr_x = 0, xr_y = 0, xr_b = 0, xr_e = 0;
+    if (lane < nxb) {
+        xr_s = xlist[b * 16 + lane];
+        xr_l = level[xr_s];
+        xr_x = ix[xr_s];
+        xr_y = iy[xr_s];
+        xr_b = bg[xr_s];
+        xr_e = en[xr_s];
+    }
+    for (int xq = 0; xq < nxb; xq++) {
+        const int ls = __shfl_sync(0xffffffffu, xr_l, xq);
+        const int sx_ = __shfl_sync(0xffffffffu, xr_x, xq), sy_ = __shfl_sync(0xffffffffu, xr_y, xq);
+        const int sbg = __shfl_sync(0xffffffffu, xr_b, xq), sen = __shfl_sync(0xffffffffu, xr_e, xq);
         // float, double-float: the source's leaf-local coordinate rescaled into this box's frame
         bool local = false, dfp = false;
         R fs = R(0.0f);
         cx<R> os = mk<R>(R(0.0f), R(0.0f));
         if constexpr (kLocal<R>) {
-            const int ls = level[s];
             local = lb >= ls && lb - ls <= kMaxGap<R>;
             if constexpr (std::is_same<R, float>::value)
                 dfp = !local && udf && lb >= ls && lb - ls <= kDfGap;
             if (local || dfp) {
                 fs = R(pow2<float>(lb - ls));
-                os = offset_cx<R>(centre_offset(ls, ix[s], iy[s], lb, bx, by));
+                os = offset_cx<R>(centre_offset(ls, sx_, sy_, lb, bx, by));
             }
         }
-        for (int base = bg[s]; base < en[s]; base += 32) {
+        for (int base = sbg; base < sen; base += 32) {
             int j = base + lane;
             cx<R> tau = mk<R>(0, 0), term = mk<R>(0, 0);
-            if (j < en[s]) {
+            if (j < sen) {
                 if (local) {
                     const cx<R> uu = uloc[j];
                     tau = crcp(mk<R>(-(uu.x * fs + os.x), -(uu.y * fs + os.y)));
