@@ -370,19 +370,37 @@ __global__ void k_scale_first(int64_t n, double *V, const GmresState *st)
         V[i] *= inv;
 }
 
-// ||v||^2 with a fixed-order reduction (single block)
-__global__ void k_norm2(int64_t n, const double *__restrict__ v, double *out)
+// ||v|| with a fixed-order reduction: block partials, then the last block to finish
+// sums them (strided, then by warps) and resets the counter
+__global__ void k_norm2(int64_t n, const double *__restrict__ v, double *part, unsigned *count,
+                        double *out)
 {
     __shared__ double wsum[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(v[i], v[i], s);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s = fma(v[i], v[i], s);
     s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    if (lane == 0) wsum[wid] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += wsum[k];
-        *out = sqrt(t);
+        for (int k = 0; k < nw; k++) t += wsum[k];
+        part[blockIdx.x] = t;
+    }
+    if (!finish_block(count)) return;
+    double t = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(&part[b]);
+    t = warp_sum(t);
+    __syncthreads();
+    if (lane == 0) wsum[wid] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < nw; k++) u += wsum[k];
+        *out = sqrt(u);
+        *count = 0u;
     }
 }
 
@@ -738,7 +756,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
     }
     double *bn = pl->bsig + 1, *rn = pl->bsig + 2;
-    LBF_LAUNCH(k_norm2, 1, 1024, 0, s, n, b, bn);
+    LBF_LAUNCH(k_norm2, pl->mdot_blocks, 256, 0, s, n, b, pl->gpart, pl->red_count + 2, bn);
     LBF_CHECK_LAUNCH();
     if (x0 && (rc = lbf_permute_in(pl, x0, x, 1, s))) return rc;
     GmresState hs{};
@@ -771,7 +789,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
                 LBF_LAUNCH(k_axpby, lbf_cdiv(n, 256), 256, 0, s, n, 1.0, b, -1.0, pl->gw, r);
                 LBF_CHECK_LAUNCH();
             }
-            LBF_LAUNCH(k_norm2, 1, 1024, 0, s, n, r, rn);
+            LBF_LAUNCH(k_norm2, pl->mdot_blocks, 256, 0, s, n, r, pl->gpart, pl->red_count + 2, rn);
             LBF_CHECK_LAUNCH();
             LBF_CUDA(cudaMemcpyAsync(hb, pl->bsig, sizeof(hb), cudaMemcpyDeviceToHost, s));
             LBF_CUDA(cudaStreamSynchronize(s));
