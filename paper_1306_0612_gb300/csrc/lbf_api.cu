@@ -132,7 +132,10 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         pl->mpole = A.get<double2>(cap * P);
         pl->local = A.get<double2>(cap * P);
     }
-    if (o.matvec == LBF_MATVEC_FMM || o.border) pl->upcnt = A.get<int32_t>(cap);
+    if (o.matvec == LBF_MATVEC_FMM || o.border) {
+        pl->upcnt = A.get<int32_t>(cap);
+        pl->pull = A.get<uint32_t>(2 * cap + 4);
+    }
     if (o.matvec == LBF_MATVEC_FMM && o.fmm64) {
         pl->qdf = A.get<double2>(N);   // cx<df64>: 16 B per node
         pl->udf = A.get<double2>(N);
@@ -149,7 +152,6 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         if (o.matvec == LBF_MATVEC_FMM) {
             pl->mpole32 = A.get<float2>(cap * P32);
             pl->local32 = A.get<float2>(cap * P32);
-            pl->pull = A.get<uint32_t>(2 * cap + 4);
         }
         pl->tab32_binom = A.get<float>(2 * T * T);
         pl->tab32_tpow = A.get<float2>(49 * (T + 1));
