@@ -61,6 +61,11 @@ __device__ __forceinline__ cz<float> ldcg_cz(const cz<float> *p)
     const float2 v = __ldcg((const float2 *)p);
     return cz<float>{v.x, v.y};
 }
+__device__ __forceinline__ cz<double> ldcg_cz(const cz<double> *p)
+{
+    const double2 v = __ldcg((const double2 *)p);
+    return cz<double>{v.x, v.y};
+}
 __device__ __forceinline__ cz<df64> ldcg_cz(const cz<df64> *p)
 {
     const float4 v = __ldcg((const float4 *)p);
@@ -1009,12 +1014,21 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
         LBF_LAUNCH(k_mp_p2l<double>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
                    (cz<double> *)B.loc, B.sums, gate);
-        for (int l = 3; l < T.nlev; l++) {
-            int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
-            if (le <= ls) continue;
-            LBF_LAUNCH(k_mp_l2l<double>, lbf_cdiv(le - ls, 8), 256, l2l_smem<double>(P, 8), s, ls,
-                       le, P, T.parent, T.ix, T.iy, pl->tab_binom,
-                       (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, gate);
+        if (pl->pull) {  // the L2L chain in one launch
+            const int cw = 8;
+            const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
+            LBF_LAUNCH(k_mp_chain<double>, grid, 32 * cw, l2l_smem<double>(P, cw), s, T.nbox, P,
+                       T.parent, T.level, T.ix, T.iy, pl->tab_binom,
+                       (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, pl->pull,
+                       pl->dev_status, gate);
+        } else {
+            for (int l = 3; l < T.nlev; l++) {
+                int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
+                if (le <= ls) continue;
+                LBF_LAUNCH(k_mp_l2l<double>, lbf_cdiv(le - ls, 8), 256, l2l_smem<double>(P, 8), s, ls,
+                           le, P, T.parent, T.ix, T.iy, pl->tab_binom,
+                           (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, gate);
+            }
         }
         if (B.nchunks)
             LBF_LAUNCH(k_mp_near<double>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks,

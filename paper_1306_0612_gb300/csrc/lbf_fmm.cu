@@ -407,16 +407,14 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                      mp, pl->upcnt, gate);
         LBF_CHECK_LAUNCH();
     }
-    // Float and double-float: every box runs in one launch, taking the boxes in index
-    // order and shifting its parent's full expansion down once the parent is done, so
-    // the leaf kernel evaluates one expansion per target.  Native double (the fallback
-    // accurate operator) runs level by level (L2L + M2L + P2L).
+    // Every box runs in one launch, taking the boxes in index order and shifting its
+    // parent's full expansion down once the parent is done, so the leaf kernel
+    // evaluates one expansion per target (level by level only if the plan has no
+    // counters for it).
     {
         const int wpb = down_warps<R>(P);
         const size_t smem = down_smem<R>(P, wpb);
-        constexpr bool kPullMode = !std::is_same<R, double>::value;  // float, double-float
-        if (kPullMode) {
-            if (!pl->pull) return LBF_EINVAL;
+        if (pl->pull) {
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, wpb), 4 * (int64_t)std::max(pl->nsm, 1));
             LBF_LAUNCH_P(kid_down, fmm::k_down<R>, grid, 32 * wpb, smem, s, (int64_t)0, T.nbox,
                          T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin, T.end,
