@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "lbf_internal.cuh"
 
@@ -31,6 +32,11 @@ constexpr int kDotBlocks = 152 * 2;
 __device__ __forceinline__ bool gate_closed(const int *gate) { return gate && *gate == 0; }
 
 __device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -152,28 +158,30 @@ __global__ void k_add_last(int M, const double *__restrict__ c, double *__restri
 }
 
 // the Arnoldi input v_j of the current step (j from the device state) into a fixed buffer
-__global__ void k_copy_vj(int64_t n, const double *__restrict__ V, int64_t ldv,
+template <typename T>
+__global__ void k_copy_vj(int64_t n, const T *__restrict__ V, int64_t ldv,
                           const GmresState *__restrict__ st, double *__restrict__ out)
 {
     if (st->go == 0) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = V[(int64_t)st->j * ldv + i];
+    if (i < n) out[i] = (double)V[(int64_t)st->j * ldv + i];
 }
 
 // ---- GMRES kernels --------------------------------------------------------------------
 
 // Partial dot products of w with V[0..nv) over one block's row chunk; the last block
 // to finish sums the partials in block order into h.
-__device__ void dots_phase(const double *V, int64_t ldv, int nv, const double *ws, int rows,
+template <typename T>
+__device__ void dots_phase(const T *V, int64_t ldv, int nv, const T *ws, int rows,
                            int64_t row0, double *acc)
 {
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = wid; k < nv; k += nw) {
-        const double *vk = V + (int64_t)k * ldv + row0;
-        double s = 0.0;
+        const T *vk = V + (int64_t)k * ldv + row0;
+        T s = T(0);
         for (int r = lane; r < rows; r += 32) s = fma(vk[r], ws[r], s);
         s = warp_sum(s);
-        if (lane == 0) acc[k] += s;
+        if (lane == 0) acc[k] += (double)s;
     }
 }
 
@@ -190,33 +198,42 @@ __device__ bool finish_block(unsigned *count)
 // mode 0: h = V^T w (columns 0..j)
 // mode 1: w -= V h;  h2 = V^T w
 // mode 2: w -= V h2; ||w||^2 -> Hessenberg column j, Givens rotation, convergence test
-__global__ void k_arnoldi(int64_t n, const double *__restrict__ V, int64_t ldv, double *w,
-                          double *part, unsigned *count, double *hbuf, double *H, double *cs,
-                          double *sn, double *gv, GmresState *st, int mode)
+// T: the storage and arithmetic of the basis.  double: w is both the operator's output
+// and the working vector.  float (the inner solves of the refinement, whose operator is
+// float too): mode 0 rounds the operator's output w into the float working vector wt;
+// dot products accumulate in float per thread and in double across threads and blocks.
+template <typename T>
+__global__ void k_arnoldi(int64_t n, const T *__restrict__ V, int64_t ldv, const double *w,
+                          T *wt, double *part, unsigned *count, double *hbuf, double *H,
+                          double *cs, double *sn, double *gv, GmresState *st, int mode)
 {
     if (st->go == 0) return;
     extern __shared__ double sh[];
     int m = st->m;
     int j = st->j;
     int nv = j + 1;
-    double *ws = sh;                   // kRowsPerChunk
+    T *ws = (T *)sh;                   // kRowsPerChunk
     double *acc = sh + kRowsPerChunk;  // m + 2
-    double *hc = acc + (m + 2);        // m + 1 (coefficients for the update)
+    T *hc = (T *)(acc + (m + 2));      // m + 1 (coefficients for the update)
     for (int k = threadIdx.x; k < m + 2; k += blockDim.x) acc[k] = 0.0;
     const double *hin = (mode == 1) ? hbuf : hbuf + (m + 1);
     if (mode >= 1)
-        for (int k = threadIdx.x; k < nv; k += blockDim.x) hc[k] = hin[k];
+        for (int k = threadIdx.x; k < nv; k += blockDim.x) hc[k] = (T)hin[k];
     __syncthreads();
     int64_t per = lbf_cdiv(n, gridDim.x);
     int64_t r0 = blockIdx.x * per, r1 = std::min<int64_t>(n, r0 + per);
-    double nrm = 0.0;
+    T nrm = T(0);
     for (int64_t c0 = r0; c0 < r1; c0 += kRowsPerChunk) {
         int rows = (int)std::min<int64_t>(kRowsPerChunk, r1 - c0);
         for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-            double x = w[c0 + r];
-            if (mode >= 1) {
+            T x;
+            if (mode == 0) {
+                x = (T)w[c0 + r];
+                if constexpr (!std::is_same<T, double>::value) wt[c0 + r] = x;
+            } else {
+                x = wt[c0 + r];
                 for (int k = 0; k < nv; k++) x = fma(-hc[k], V[(int64_t)k * ldv + c0 + r], x);
-                w[c0 + r] = x;
+                wt[c0 + r] = x;
             }
             ws[r] = x;
             nrm = fma(x, x, nrm);
@@ -228,7 +245,7 @@ __global__ void k_arnoldi(int64_t n, const double *__restrict__ V, int64_t ldv, 
     if (mode == 2) {
         nrm = warp_sum(nrm);
         __shared__ double wsum[32];
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = nrm;
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (double)nrm;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
@@ -240,13 +257,20 @@ __global__ void k_arnoldi(int64_t n, const double *__restrict__ V, int64_t ldv, 
     int nout = (mode == 2) ? 1 : nv;
     for (int k = threadIdx.x; k < nout; k += blockDim.x) part[(int64_t)blockIdx.x * (m + 2) + k] = acc[k];
     if (!finish_block(count)) return;
-    // last block: fixed-order reduction over blocks
-    for (int k = threadIdx.x; k < nout; k += blockDim.x) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; b++) s += ((volatile double *)part)[(int64_t)b * (m + 2) + k];
-        if (mode == 0) hbuf[k] = s;
-        else if (mode == 1) hbuf[(m + 1) + k] = s;
-        else acc[0] = s;
+    // last block: fixed-order reduction over blocks, a warp per output (lanes strided
+    // over the blocks, then a warp sum)
+    {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int k = wid; k < nout; k += nw) {
+            double s = 0.0;
+            for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(&part[(int64_t)b * (m + 2) + k]);
+            s = warp_sum(s);
+            if (lane == 0) {
+                if (mode == 0) hbuf[k] = s;
+                else if (mode == 1) hbuf[(m + 1) + k] = s;
+                else acc[0] = s;
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -284,13 +308,14 @@ __global__ void k_arnoldi(int64_t n, const double *__restrict__ V, int64_t ldv, 
 }
 
 // V[j] = w * inv (j = st->j after the Arnoldi step)
-__global__ void k_scale_next(int64_t n, const double *__restrict__ w, double *V, int64_t ldv,
+template <typename T>
+__global__ void k_scale_next(int64_t n, const T *__restrict__ w, T *V, int64_t ldv,
                              const GmresState *st)
 {
     if (st->go == 0) return;
     int j = st->j;
-    double inv = st->inv;
-    double *vj = V + (int64_t)j * ldv;
+    const T inv = (T)st->inv;
+    T *vj = V + (int64_t)j * ldv;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         vj[i] = w[i] * inv;
@@ -308,23 +333,25 @@ __global__ void k_solve_y(const double *H, const double *gv, double *y, GmresSta
     }
 }
 
-__global__ void k_xupdate(int64_t n, const double *__restrict__ V, int64_t ldv,
+template <typename T>
+__global__ void k_xupdate(int64_t n, const T *__restrict__ V, int64_t ldv,
                           const double *__restrict__ y, const GmresState *st, double *x)
 {
     int j = st->j;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double s = x[i];
-        for (int k = 0; k < j; k++) s = fma(y[k], V[(int64_t)k * ldv + i], s);
-        x[i] = s;
+        T s = T(0);
+        for (int k = 0; k < j; k++) s = fma((T)y[k], V[(int64_t)k * ldv + i], s);
+        x[i] += (double)s;
     }
 }
 
 // r = b - Ax (Ax nullable = 0) into V[0], ||r||^2 partials; the last block starts a
 // new cycle: beta = ||r||, g = (beta, 0, ...), j = 0, go = (beta > tol ||b||).
 // With init != 0 it also records ||b|| (the first call, x = 0 or the initial guess).
+template <typename T>
 __global__ void k_restart(int64_t n, const double *__restrict__ b, const double *__restrict__ Ax,
-                          double *V, double *part, unsigned *count, double *gv, GmresState *st,
+                          T *V, double *part, unsigned *count, double *gv, GmresState *st,
                           int init, const double *__restrict__ bn)
 {
     __shared__ double wsum[32];
@@ -332,7 +359,7 @@ __global__ void k_restart(int64_t n, const double *__restrict__ b, const double 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double r = b[i] - (Ax ? Ax[i] : 0.0);
-        V[i] = r;
+        V[i] = (T)r;
         nrm = fma(r, r, nrm);
     }
     nrm = warp_sum(nrm);
@@ -344,9 +371,12 @@ __global__ void k_restart(int64_t n, const double *__restrict__ b, const double 
         part[blockIdx.x] = t;
     }
     if (!finish_block(count)) return;
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += 32) s += __ldcg(&part[k]);
+        s = warp_sum(s);
+    }
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (unsigned k = 0; k < gridDim.x; k++) s += ((volatile double *)part)[k];
         *count = 0u;
         double beta = sqrt(s);
         if (init) st->bnorm = *bn;
@@ -362,9 +392,10 @@ __global__ void k_restart(int64_t n, const double *__restrict__ b, const double 
     }
 }
 
-__global__ void k_scale_first(int64_t n, double *V, const GmresState *st)
+template <typename T>
+__global__ void k_scale_first(int64_t n, T *V, const GmresState *st)
 {
-    double inv = st->inv;
+    const T inv = (T)st->inv;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         V[i] *= inv;
@@ -423,6 +454,12 @@ __global__ void k_axpby(int64_t n, double alpha, const double *x, double beta, c
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = alpha * x[i] + beta * y[i];
+}
+
+__global__ void k_widen(int64_t n, const float *__restrict__ in, double *__restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
 }
 
 __global__ void k_fill(double *p, int64_t n, double v)
@@ -590,30 +627,53 @@ static int read_state(lbf_plan *pl, GmresState *h, cudaStream_t s)
 // One Arnoldi step on stream s: w = op(v_j), CGS2 against V, Givens update, v_{j+1}.
 // from_state: the input is copied from V by the device's j (graph-replayable);
 // otherwise v_j is addressed from the host's k.
-static int arnoldi_step(lbf_plan *pl, int opc, int prec, int k, bool from_state, cudaStream_t s)
+// The float basis of the inner solves of the refinement: the first (m + 1) ldv floats of
+// the basis region, then the float working vector.
+static float *basis32(lbf_plan *pl) { return (float *)pl->V; }
+static float *work32(lbf_plan *pl) { return (float *)pl->V + (int64_t)(pl->opt.restart + 1) * pl->ldv; }
+
+template <typename T>
+static int arnoldi_step_t(lbf_plan *pl, int opc, int prec, int k, bool from_state, T *V, T *wt,
+                          cudaStream_t s)
 {
     int64_t n = pl->n;
     int m = pl->opt.restart;
-    double *w = pl->gw, *V = pl->V;
+    double *w = pl->gw;
     int64_t ldv = pl->ldv;
     int nblk = pl->mdot_blocks;
     double *hbuf = pl->H + (int64_t)(m + 1) * m;
     double *cs = hbuf + 2 * (m + 1), *sn = cs + m, *gv = sn + m;
     unsigned *count = pl->red_count + 1;
     size_t smem = sizeof(double) * (size_t)(kRowsPerChunk + 2 * (m + 2));
-    const double *vj = V + (int64_t)k * ldv;
-    if (from_state) {
-        LBF_LAUNCH(k_copy_vj, lbf_cdiv(n, 256), 256, 0, s, n, V, ldv, pl->gs, pl->vstep);
+    const double *vj = std::is_same<T, double>::value ? (const double *)(V + (int64_t)k * ldv) : nullptr;
+    if (from_state || !vj) {
+        // the operator reads v_j in double: from the device's j (graph-replayable), or a
+        // float basis vector widened
+        if (from_state) {
+            LBF_LAUNCH(k_copy_vj<T>, lbf_cdiv(n, 256), 256, 0, s, n, V, ldv, pl->gs, pl->vstep);
+        } else {
+            LBF_LAUNCH(k_widen, lbf_cdiv(n, 256), 256, 0, s, n, (const float *)(V + (int64_t)k * ldv),
+                       pl->vstep);
+        }
         vj = pl->vstep;
     }
     int rc = lbf_apply_op_sorted(pl, opc, vj, w, &pl->gs->go, s, prec);
     if (rc) return rc;
     for (int mode = 0; mode < 3; mode++)
-        LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi, nblk, 256, smem, s, n, V, ldv, w, pl->gpart,
+        LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi<T>, nblk, 256, smem, s, n, V, ldv, w, wt, pl->gpart,
                      count, hbuf, pl->H, cs, sn, gv, pl->gs, mode);
-    LBF_LAUNCH(k_scale_next, nblk, 256, 0, s, n, w, V, ldv, pl->gs);
+    LBF_LAUNCH(k_scale_next<T>, nblk, 256, 0, s, n, wt, V, ldv, pl->gs);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
+}
+
+// The float operator's solves keep their basis in float (the inner solves of the
+// refinement need ~1e-4; the accurate operator's solves keep double).
+static int arnoldi_step(lbf_plan *pl, int opc, int prec, int k, bool from_state, cudaStream_t s)
+{
+    if (prec == LBF_PREC_FP32)
+        return arnoldi_step_t<float>(pl, opc, prec, k, from_state, basis32(pl), work32(pl), s);
+    return arnoldi_step_t<double>(pl, opc, prec, k, from_state, pl->V, pl->gw, s);
 }
 
 // The captured step graph of (prec, transpose), built on first use; null when graphs
@@ -672,8 +732,17 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
         LBF_LAUNCH(k_fill, lbf_cdiv(n, 256), 256, 0, s, x, n, 0.0);
         LBF_CHECK_LAUNCH();
     }
-    LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1, bnorm_dev);
-    LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
+    const bool f32 = prec == LBF_PREC_FP32;
+    float *V32 = basis32(pl);
+    if (f32) {
+        LBF_LAUNCH(k_restart<float>, nblk, 256, 0, s, n, b, Ax, V32, pl->gpart, count, gv, pl->gs, 1,
+                   bnorm_dev);
+        LBF_LAUNCH(k_scale_first<float>, nblk, 256, 0, s, n, V32, pl->gs);
+    } else {
+        LBF_LAUNCH(k_restart<double>, nblk, 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1,
+                   bnorm_dev);
+        LBF_LAUNCH(k_scale_first<double>, nblk, 256, 0, s, n, V, pl->gs);
+    }
     LBF_CHECK_LAUNCH();
     cudaGraphExec_t sg = step_graph(pl, opc, prec, s);
     const int64_t sg_nodes =
@@ -713,15 +782,23 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
         }
         // cycle end: x += V y
         LBF_LAUNCH(k_solve_y, 1, 32, 0, s, pl->H, gv, y, pl->gs);
-        LBF_LAUNCH(k_xupdate, nblk, 256, 0, s, n, V, ldv, y, pl->gs, x);
+        if (f32) LBF_LAUNCH(k_xupdate<float>, nblk, 256, 0, s, n, V32, ldv, y, pl->gs, x);
+        else LBF_LAUNCH(k_xupdate<double>, nblk, 256, 0, s, n, V, ldv, y, pl->gs, x);
         LBF_CHECK_LAUNCH();
         if ((rc = read_state(pl, &hs, s))) return rc;
         if (hs.converged || hs.it >= hs.maxit) break;
         // restart from the true preconditioned residual
         if ((rc = lbf_apply_op_sorted(pl, opc, x, w, nullptr, s, prec))) return rc;
         (*applies)++;
-        LBF_LAUNCH(k_restart, nblk, 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0, bnorm_dev);
-        LBF_LAUNCH(k_scale_first, nblk, 256, 0, s, n, V, pl->gs);
+        if (f32) {
+            LBF_LAUNCH(k_restart<float>, nblk, 256, 0, s, n, b, w, V32, pl->gpart, count, gv, pl->gs, 0,
+                       bnorm_dev);
+            LBF_LAUNCH(k_scale_first<float>, nblk, 256, 0, s, n, V32, pl->gs);
+        } else {
+            LBF_LAUNCH(k_restart<double>, nblk, 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0,
+                       bnorm_dev);
+            LBF_LAUNCH(k_scale_first<double>, nblk, 256, 0, s, n, V, pl->gs);
+        }
         LBF_CHECK_LAUNCH();
     }
     if ((rc = read_state(pl, &hs, s))) return rc;
