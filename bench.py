@@ -201,7 +201,7 @@ def kernel_work(name, c, bc, P, P32, N):
     operation counts: 11 flops per near pair, 8(p+1) per node for P2M and L2P and
     per (node, box) for M2P/P2L, 8(p+1)^2 per translation, 10 per node to combine.
     Multiplier potential: 8 flops per local-expansion term evaluated at a node
-    (one expansion per node),
+    (one expansion per node in double, one per ancestor level >= 2 in float),
     8 per (node, centre) pair summed directly (log counted as one flop, like the
     division of P2P), 10 per node to combine."""
     f32 = name.endswith("32")
@@ -216,7 +216,7 @@ def kernel_work(name, c, bc, P, P32, N):
     if base == "direct":
         return 11 * N * (N - 1), "TFLOP/s"
     if base == "esum" and bc:
-        terms = 8 * (bc["terms32"] if f32 else bc["terms"]) * N
+        terms = 8 * bc["terms32"] * bc["walk_expansions"] if f32 else 8 * bc["terms"] * N
         return (terms + 8 * bc["direct_pairs"] + 8 * bc["global_centres"] * N + 10 * N,
                 "TFLOP/s")
     return None, None

@@ -955,9 +955,9 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
         LBF_LAUNCH(k_mp_p2l<float>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
                    (cz<float> *)B.loc32, B.sums, gate);
-        // float: the L2L chain in one launch (with the float FMM's counters and tables),
-        // else the evaluation walks each node's ancestors
-        const bool chain = pl->pull != nullptr;
+        // float: the evaluation walks each node's ancestors (cheaper here than the L2L
+        // chain, which is serial along each path while the walk is parallel over nodes)
+        const bool chain = false;
         if (chain) {
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
