@@ -407,6 +407,9 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                      mp, pl->upcnt, gate);
         LBF_CHECK_LAUNCH();
     }
+    // float forward rows: no chain, the far field comes from the per-node walk below
+    const bool walk = sizeof(R) == sizeof(float) && MODE == fmm::kLeafForward && pl->anc &&
+                      pl->bd.leaf_of;
     // Every box runs in one launch, taking the boxes in index order and shifting its
     // parent's full expansion down once the parent is done, so the leaf kernel
     // evaluates one expansion per target (level by level only if the plan has no
@@ -414,7 +417,13 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     {
         const int wpb = down_warps<R>(P);
         const size_t smem = down_smem<R>(P, wpb);
-        if (pl->pull) {
+        if (walk) {  // every box's own M2L + P2L, a warp per box, no chain
+            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, (int64_t)0,
+                         T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin,
+                         T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate, 0,
+                         (unsigned *)nullptr, pl->dev_status, udf);
+            LBF_CHECK_LAUNCH();
+        } else if (pl->pull) {
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, wpb), 4 * (int64_t)std::max(pl->nsm, 1));
             LBF_LAUNCH_P(kid_down, fmm::k_down<R>, grid, 32 * wpb, smem, s, (int64_t)0, T.nbox,
                          T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin, T.end,
@@ -436,7 +445,12 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
                  32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
-                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf);
+                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf, walk ? 0 : 1);
+    if (walk) {
+        LBF_LAUNCH_P(kid_leaf, fmm::k_l2p_walk, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
+                     pl->bd.leaf_of, T.level, T.ix, T.iy, pl->anc, (const float2 *)uloc,
+                     (const cx<float> *)loc, v, gate);
+    }
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }

@@ -672,7 +672,8 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const cx<R> *__restrict__ loc, const double *__restrict__ sigma,
                        const double *__restrict__ dself, const double2 *__restrict__ w,
                        const double *__restrict__ beta, const double *__restrict__ bsig,
-                       double *__restrict__ v, const int *gate, const cx<df64> *__restrict__ udf)
+                       double *__restrict__ v, const int *gate, const cx<df64> *__restrict__ udf,
+                       int l2p)
 {
     if (gate_closed(gate)) return;
     constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
@@ -722,7 +723,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                 for (int l = P - 2; l >= 1; l--)
                     d = cfma(d, u, mk<R>((R)l * lb[l].x, (R)l * lb[l].y));
                 phi = mk<R>(d.x * irr, d.y * irr);
-            } else {
+            } else if (l2p) {
                 phi = lb[P - 1];
                 for (int l = P - 2; l >= 0; l--) phi = cfma(phi, u, lb[l]);
             }
@@ -879,6 +880,40 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         }
         __syncwarp();
     }
+}
+
+// The far field of the float operator's forward rows, a thread per node: every
+// ancestor's own local expansion (levels >= 2, the leaf included) at the node, from its
+// leaf-local coordinate u: (z - c_a)/r_a = 2((ix_b - 2^s ix_a + 1/2) 2^-s - 1/2) + u 2^-s
+// for a depth gap s (ix_b - 2^s ix_a = the low s bits of ix_b).  Adds the far-field
+// term of the forward rows, 2 (1/2pi) (-Im Phi), to v (the leaf kernel wrote the rest).
+// A parallel alternative to shifting the expansions down the tree (L2L): no serial
+// chain, and the nodes of a leaf share their ancestors' coefficients in L1.
+__global__ void k_l2p_walk(int64_t N, int P, const int32_t *__restrict__ leaf_of,
+                           const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
+                           const int32_t *__restrict__ iy, const int32_t *__restrict__ anc,
+                           const float2 *__restrict__ u32, const cx<float> *__restrict__ loc,
+                           double *__restrict__ v, const int *gate)
+{
+    if (gate_closed(gate)) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = leaf_of[i];
+    const float2 uu = u32[i];
+    const int lv = level[b], bx = ix[b], by = iy[b];
+    const int32_t *ab = anc + (int64_t)b * LBF_ANC_STRIDE;
+    float acc = 0.0f;
+    for (int sh = 0; sh <= lv - 2; sh++) {
+        const cx<float> *la = loc + (int64_t)ab[sh] * P;
+        const float sc = pow2<float>(-sh);
+        const int dxi = bx & ((1 << sh) - 1), dyi = by & ((1 << sh) - 1);
+        const cx<float> ua = mk<float>(2.0f * (((float)dxi + 0.5f) * sc - 0.5f) + uu.x * sc,
+                                       2.0f * (((float)dyi + 0.5f) * sc - 0.5f) + uu.y * sc);
+        cx<float> t = la[P - 1];
+        for (int l = P - 2; l >= 0; l--) t = cfma(t, ua, la[l]);
+        acc += t.y;
+    }
+    v[i] += 2.0 * (-(double)acc * (1.0 / (2.0 * LBF_PI)));
 }
 
 }  // namespace fmm
