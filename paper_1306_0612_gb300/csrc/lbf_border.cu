@@ -740,14 +740,29 @@ __global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
         const float2 uu = u32[i];
         const int lv = level[b], bx = ix[b], by = iy[b];
         const int32_t *ab = parent + (int64_t)b * LBF_ANC_STRIDE;  // the ancestor table
-        R acc = 0;
-        for (int sh = 0; sh <= lv - 2; sh++) {
-            const int a = ab[sh];
+        auto at = [&](int sh) {
             const R sc = (R)__int_as_float((127 - sh) << 23);  // 2^-sh
             const int dxi = bx & ((1 << sh) - 1), dyi = by & ((1 << sh) - 1);
-            cz<R> ua{(R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + (R)uu.x * sc,
-                     (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + (R)uu.y * sc};
-            const cz<R> *la = loc + (int64_t)a * P;
+            return cz<R>{(R)2 * (((R)dxi + (R)0.5) * sc - (R)0.5) + (R)uu.x * sc,
+                         (R)2 * (((R)dyi + (R)0.5) * sc - (R)0.5) + (R)uu.y * sc};
+        };
+        // two ancestors at a time: two independent Horner chains
+        R acc = 0;
+        const int na = lv - 1;
+        int sh = 0;
+        for (; sh + 1 < na; sh += 2) {
+            const cz<R> *la = loc + (int64_t)ab[sh] * P, *lb = loc + (int64_t)ab[sh + 1] * P;
+            const cz<R> ua = at(sh), ub = at(sh + 1);
+            cz<R> ta = la[P - 1], tb = lb[P - 1];
+            for (int l = P - 2; l >= 0; l--) {
+                ta = zfma(ta, ua, la[l]);
+                tb = zfma(tb, ub, lb[l]);
+            }
+            acc += ta.x + tb.x;
+        }
+        if (sh < na) {
+            const cz<R> *la = loc + (int64_t)ab[sh] * P;
+            const cz<R> ua = at(sh);
             cz<R> t = la[P - 1];
             for (int l = P - 2; l >= 0; l--) t = zfma(t, ua, la[l]);
             acc += t.x;

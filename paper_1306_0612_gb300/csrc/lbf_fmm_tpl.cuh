@@ -902,13 +902,29 @@ __global__ void k_l2p_walk(int64_t N, int P, const int32_t *__restrict__ leaf_of
     const float2 uu = u32[i];
     const int lv = level[b], bx = ix[b], by = iy[b];
     const int32_t *ab = anc + (int64_t)b * LBF_ANC_STRIDE;
-    float acc = 0.0f;
-    for (int sh = 0; sh <= lv - 2; sh++) {
-        const cx<float> *la = loc + (int64_t)ab[sh] * P;
+    auto at = [&](int sh) {  // the node in ancestor sh's frame, and its coefficients
         const float sc = pow2<float>(-sh);
         const int dxi = bx & ((1 << sh) - 1), dyi = by & ((1 << sh) - 1);
-        const cx<float> ua = mk<float>(2.0f * (((float)dxi + 0.5f) * sc - 0.5f) + uu.x * sc,
-                                       2.0f * (((float)dyi + 0.5f) * sc - 0.5f) + uu.y * sc);
+        return mk<float>(2.0f * (((float)dxi + 0.5f) * sc - 0.5f) + uu.x * sc,
+                         2.0f * (((float)dyi + 0.5f) * sc - 0.5f) + uu.y * sc);
+    };
+    // two ancestors at a time: two independent Horner chains
+    float acc = 0.0f;
+    const int na = lv - 1;
+    int sh = 0;
+    for (; sh + 1 < na; sh += 2) {
+        const cx<float> *la = loc + (int64_t)ab[sh] * P, *lb = loc + (int64_t)ab[sh + 1] * P;
+        const cx<float> ua = at(sh), ub = at(sh + 1);
+        cx<float> ta = la[P - 1], tb = lb[P - 1];
+        for (int l = P - 2; l >= 0; l--) {
+            ta = cfma(ta, ua, la[l]);
+            tb = cfma(tb, ub, lb[l]);
+        }
+        acc += ta.y + tb.y;
+    }
+    if (sh < na) {
+        const cx<float> *la = loc + (int64_t)ab[sh] * P;
+        const cx<float> ua = at(sh);
         cx<float> t = la[P - 1];
         for (int l = P - 2; l >= 0; l--) t = cfma(t, ua, la[l]);
         acc += t.y;
