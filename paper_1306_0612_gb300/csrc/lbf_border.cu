@@ -267,19 +267,26 @@ __global__ void k_mp_islands(int M, int P, const int64_t *__restrict__ ptr,
         slog[k] = slv;
         sell[k] = sev;
     }
+    // the moments sum_j u_j^l and sum_j v_j^l in double-float (pairs of floats, ~48 bits):
+    // this GPU issues float arithmetic 64 times faster than double, and the powers and
+    // warp sums are the whole cost of this kernel
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double2 am0 = make_double2(0, 0), am1 = am0, an0 = am0, an1 = am0;
+    using D = df64;
+    const D zero(0.0f);
+    cz<D> am0{zero, zero}, am1 = am0, an0 = am0, an1 = am0;
+    const double iR = 1.0 / R;
     for (int64_t base = b + wid * 32; base < e; base += blockDim.x) {
         int64_t j = base + lane;
-        cz<double> u{0, 0}, v{0, 0};
+        cz<D> u{zero, zero}, v{zero, zero};
         if (j < e) {
             cz<double> d{xi_o[j].x - cx, xi_o[j].y - cy};
-            u = cz<double>{d.x / R, d.y / R};
-            v = zinv(cz<double>{d.x / rho, d.y / rho});
+            cz<double> vd = zinv(cz<double>{d.x / rho, d.y / rho});
+            u = cz<D>{D(d.x * iR), D(d.y * iR)};
+            v = cz<D>{D(vd.x), D(vd.y)};
         }
-        cz<double> pu = u, pv = v;
+        cz<D> pu = u, pv = v;
         for (int l = 1; l < P; l++) {
-            double mx = wsum(pu.x), my = wsum(pu.y), nx = wsum(pv.x), ny = wsum(pv.y);
+            D mx = wsum(pu.x), my = wsum(pu.y), nx = wsum(pv.x), ny = wsum(pv.y);
             if (lane == (l & 31)) {
                 if (l < 32) { am0.x += mx; am0.y += my; an0.x += nx; an0.y += ny; }
                 else { am1.x += mx; am1.y += my; an1.x += nx; an1.y += ny; }
@@ -288,10 +295,11 @@ __global__ void k_mp_islands(int M, int P, const int64_t *__restrict__ ptr,
             pv = zmul(pv, v);
         }
     }
-    smu[wid][lane] = am0;
-    snu[wid][lane] = an0;
-    smu[wid][lane + 32] = am1;
-    snu[wid][lane + 32] = an1;
+    auto dd = [](cz<D> a) { return make_double2((double)a.x, (double)a.y); };
+    smu[wid][lane] = dd(am0);
+    snu[wid][lane] = dd(an0);
+    smu[wid][lane + 32] = dd(am1);
+    snu[wid][lane + 32] = dd(an1);
     __syncthreads();
     for (int l = threadIdx.x; l < P; l += blockDim.x) {
         double2 a = make_double2(0, 0), c = a;

@@ -57,14 +57,24 @@ __global__ void k_bbox_partial(int64_t N, const double2 *__restrict__ xi, double
     if (t < 4) part[4 * blockIdx.x + t] = s[t][0];
 }
 
+// one warp: lanes strided over the block partials, then shuffles (min and max are
+// exact, so the result does not depend on the order)
 __global__ void k_bbox_final(int nb, const double *__restrict__ part, double *__restrict__ bbox)
 {
-    if (threadIdx.x != 0) return;
-    double mnx = part[0], mxx = part[1], mny = part[2], mxy = part[3];
-    for (int b = 1; b < nb; b++) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    double mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+    for (int b = lane; b < nb; b += 32) {
         mnx = fmin(mnx, part[4 * b]); mxx = fmax(mxx, part[4 * b + 1]);
         mny = fmin(mny, part[4 * b + 2]); mxy = fmax(mxy, part[4 * b + 3]);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fmin(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mxx = fmax(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mny = fmin(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxy = fmax(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    if (lane != 0) return;
     double ex = __dsub_rn(mxx, mnx), ey = __dsub_rn(mxy, mny);
     double L = __dmul_rn(ex > ey ? ex : ey, 1.0 + 0x1p-20);
     if (!(L > 0.0)) L = 1.0;
