@@ -641,6 +641,12 @@ template <typename R> struct LeafSrc {
 __device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
 __device__ __forceinline__ bool positive(double x) { return x > 0.0; }
 __device__ __forceinline__ bool positive(df64 x) { return x.hi > 0.0f; }
+// far below any squared distance between distinct nodes in units of a leaf half-width,
+// and its reciprocal stays finite in R
+template <typename R> __device__ __forceinline__ R tiny_sq();
+template <> __device__ __forceinline__ float tiny_sq<float>() { return 1e-30f; }
+template <> __device__ __forceinline__ double tiny_sq<double>() { return 1e-30; }
+template <> __device__ __forceinline__ df64 tiny_sq<df64>() { return df64(1e-30f); }
 
 // What the leaf kernel writes for node i (all with the self pair excluded):
 //   kLeafForward   v_i = 2 [ (1/2pi) Im sum_j q_j/(xi_j - xi_i) + dself_i sigma_i + s ],
@@ -795,9 +801,13 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                     const LeafSrc<R> sm = ss[wid][m];
                     const cx<R> zs = sm.z, qq = sm.q;
                     const R dr = zs.x - ut.x, di = zs.y - ut.y;
-                    // the target itself (the only source at distance 0) adds nothing
+                    // the target itself (the only source at distance 0) adds nothing: with a
+                    // tiny shift of |dz|^2 its term is 0 x (finite), so the forward and
+                    // transposed rows need no test; the derivative rows (|dz|^-4) test
                     const R d2 = fm(dr, dr, di * di);
-                    const R ir2 = positive(d2) ? rcp(d2) : R(0.0f);
+                    R ir2;
+                    if constexpr (MODE == kLeafDeriv) ir2 = positive(d2) ? rcp(d2) : R(0.0f);
+                    else ir2 = rcp(d2 + tiny_sq<R>());
                     if constexpr (MODE == kLeafForward) {
                         accI = fm(fm(qq.y, dr, -qq.x * di), ir2, accI);
                     } else if constexpr (MODE == kLeafTranspose) {
