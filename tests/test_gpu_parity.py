@@ -347,6 +347,20 @@ def test_fp32_operator_error_against_fp64_and_oracle():
     assert 1e-12 < e32 < 1e-5, e32
 
 
+def test_fp32_operator_c3_sampled_rows():
+    """N = 1,048,576 (the bench's geometry, tree depth 20): the float operator of the
+    refinement (per-node far-field walk, double-float coordinates across level gaps)
+    against sampled oracle rows, within single-precision accuracy."""
+    g = wl.config_geometry("C3", M=1024)
+    p = plan_for(g, precision=L.LBF_PRECISION_FP32_REFINE)
+    sig = wl.random_density(g.N, 3)
+    o32 = zeros(g.N)
+    L.lbf_apply(p, L.LBF_OP_K_ONLY | L.LBF_OP_FP32, dev(sig), o32)
+    rows = np.sort(np.random.default_rng(6).choice(g.N, 48, replace=False))
+    ref = oracle.apply_rows(g, sig, rows, op=1)
+    assert rel_l2(host(o32)[rows], ref) < 2e-6
+
+
 def test_refinement_solve_c2_matches_oracle():
     g = wl.config_geometry("C2")
     src, gam, _ = wl.pair_sources(g, 0, 1)
