@@ -149,6 +149,9 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         pl->q32 = A.get<float2>(N);
         pl->u32 = A.get<float2>(N);
         pl->anc = A.get<int32_t>(cap * LBF_ANC_STRIDE);
+        pl->isl = A.get<int32_t>(N);
+        pl->imean = A.get<double>((int64_t)M + 8);
+        pl->iacoef = A.get<double>(M);
         if (o.matvec == LBF_MATVEC_FMM) {
             pl->mpole32 = A.get<float2>(cap * P32);
             pl->local32 = A.get<float2>(cap * P32);
@@ -180,6 +183,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         B.ell = A.get<double>(N);
         B.xc = A.get<double2>(M);
         B.kind = A.get<int32_t>(M);
+        B.live = A.get<int32_t>(M);
         B.cell = A.get<int32_t>(2 * (int64_t)M);
         B.lam = A.get<double>(M);
         B.glob = A.get<int32_t>(M);
@@ -381,6 +385,7 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
         return LBF_EWORKSPACE;
     }
     auto fail = [&](int code) {
+        lbf_border_end(pl);  // waits for the side stream's work first
         for (auto &e : pl->ev)
             if (e) cudaEventDestroy(e);
         if (pl->host_status) cudaFreeHost(pl->host_status);
@@ -451,6 +456,9 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
     lbf_prof_mark(LBF_STAGE_GEOMETRY, 1, s);
     rc = lbf_geometry_build(pl, x, dx, d2x, centres, planar, s, tt.xi_o, tt.w_o, tt.d_o, tt.b_o);
     if (rc) return fail(rc);
+    // S and its inverse need only the planar nodes and the centres: they run on a side
+    // stream while this one builds the tree
+    if (opt->border && (rc = lbf_border_start(pl, s, tt.xi_o, tt.gj))) return fail(rc);
     {
         int64_t need = 0;
         rc = lbf_tree_build(pl, s, tt.xi_o, tt.keys, tt.keys_alt, tt.perm_alt, tt.iscr, tt.iscr_len, &need);
@@ -465,11 +473,12 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
     lbf_prof_mark(LBF_STAGE_GEOMETRY, 0, s);
     if (opt->border) {
         SortBufs sb{tt.keys, tt.keys_alt, tt.perm_alt};
-        rc = lbf_border_build(pl, s, tt.xi_o, tt.gj, tt.iscr, tt.iscr_len, sb);
+        rc = lbf_border_build(pl, s, tt.iscr, tt.iscr_len, sb);
         if (rc) return fail(rc);
     }
     CK(cudaMemcpyAsync(pl->host_status, pl->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    lbf_border_end(pl);
 #undef CK
     int st = *pl->host_status;
     if (st & LBF_DEV_POLE) return fail(LBF_EPOLE);

@@ -110,25 +110,39 @@ __global__ void k_mp_leaf_of(int64_t nleaf, const int32_t *__restrict__ leaves,
     for (int i = bg[b]; i < en[b]; i++) leaf_of[i] = b;
 }
 
-// per centre: planar image, lam_m, and its cell at the finest level of the tree
-// (kind 0: at the pole; 1: inside the tree's square; 2: outside it -> summed directly)
+// per centre: planar image and lam_m (live 0 at the pole)
+__global__ void k_mp_centres_plane(int M, const double *__restrict__ c, double2 *__restrict__ xc,
+                                   double *__restrict__ lam, int32_t *__restrict__ live)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double w = 1.0 - c[3 * m + 2];
+    if (w < 1e-12) {
+        live[m] = 0;
+        xc[m] = make_double2(0, 0);
+        lam[m] = 0;
+        return;
+    }
+    double2 z = make_double2(c[3 * m] / w, c[3 * m + 1] / w);
+    xc[m] = z;
+    lam[m] = log1p(z.x * z.x + z.y * z.y);
+    live[m] = 1;
+}
+
+// per centre: its cell at the finest level of the tree (kind 0: at the pole; 1: inside
+// the tree's square; 2: outside it -> summed directly); the planar image as above
 __global__ void k_mp_centres(int M, const double *__restrict__ c, Geo g, int D,
-                             double2 *__restrict__ xc, int32_t *__restrict__ kind,
-                             double *__restrict__ lam, int32_t *__restrict__ cell)
+                             int32_t *__restrict__ kind, int32_t *__restrict__ cell)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     double w = 1.0 - c[3 * m + 2];
     if (w < 1e-12) {
         kind[m] = 0;
-        xc[m] = make_double2(0, 0);
-        lam[m] = 0;
         cell[2 * m] = cell[2 * m + 1] = 0;
         return;
     }
     double2 z = make_double2(c[3 * m] / w, c[3 * m + 1] / w);
-    xc[m] = z;
-    lam[m] = log1p(z.x * z.x + z.y * z.y);
     double fx = floor((z.x - g.xmin) / g.L * ldexp(1.0, D));
     double fy = floor((z.y - g.ymin) / g.L * ldexp(1.0, D));
     double cmax = ldexp(1.0, D) - 1.0;
@@ -232,7 +246,8 @@ __device__ __forceinline__ double block_max(double v, double *sh)
 
 // Per island (block of 256): node mean z_k, radii R_k (max) and rho_k (min),
 // sum of log|xi_j - z_k|, sum of (l_j - log 2), and the scaled moments
-//   mu_l = sum_j ((xi_j - z_k)/R_k)^l,   nu_l = sum_j (rho_k/(xi_j - z_k))^l,  l = 1..P-1.
+//   mu_l = (1/l) sum_j ((xi_j - z_k)/R_k)^l,   nu_l = (1/l) sum_j (rho_k/(xi_j - z_k))^l,
+// l = 1..P-1 (the 1/l of the log expansions applied once here), mu_0 = nu_0 = N_k.
 __global__ void k_mp_islands(int M, int P, const int64_t *__restrict__ ptr,
                              const double2 *__restrict__ xi_o, double2 *__restrict__ zc,
                              double *__restrict__ Rk, double *__restrict__ rk,
@@ -307,8 +322,9 @@ __global__ void k_mp_islands(int M, int P, const int64_t *__restrict__ ptr,
             a.x += smu[w][l].x; a.y += smu[w][l].y;
             c.x += snu[w][l].x; c.y += snu[w][l].y;
         }
-        mu[(int64_t)k * P + l] = l ? a : make_double2(n, 0);
-        nu[(int64_t)k * P + l] = l ? c : make_double2(n, 0);
+        const double il = l ? 1.0 / l : 0.0;
+        mu[(int64_t)k * P + l] = l ? make_double2(a.x * il, a.y * il) : make_double2(n, 0);
+        nu[(int64_t)k * P + l] = l ? make_double2(c.x * il, c.y * il) : make_double2(n, 0);
     }
 }
 
@@ -319,41 +335,38 @@ __device__ bool island_logsum(int k, int P, double2 xm, double2 z, double R, dou
 {
     cz<double> d{xm.x - z.x, xm.y - z.y};
     double dd = sqrt(d.x * d.x + d.y * d.y);
-    if (dd >= kEta * R) {
-        // N_k log|xi_m - z_k| - Re sum_l mu_l (R/(xi_m - z_k))^l / l
-        cz<double> t = zinv(cz<double>{d.x / R, d.y / R}), pw = t;
-        double s = 0.0;
-        for (int l = 1; l < P; l++) {
-            double2 c = mu[(int64_t)k * P + l];
-            s += (c.x * pw.x - c.y * pw.y) / l;
-            pw = zmul(pw, t);
+    // Re sum_{l>=1} c_l t^l by Horner's rule (c = the moments with their 1/l)
+    auto series = [&](const double2 *c, cz<double> t) {
+        cz<double> a{c[P - 1].x, c[P - 1].y};
+        for (int l = P - 2; l >= 1; l--) {
+            const double2 cl = c[l];
+            a = cz<double>{fma(a.x, t.x, fma(-a.y, t.y, cl.x)), fma(a.x, t.y, fma(a.y, t.x, cl.y))};
         }
-        out = mu[(int64_t)k * P].x * log(dd) - s;
+        return a.x * t.x - a.y * t.y;
+    };
+    if (dd >= kEta * R) {
+        // N_k log|xi_m - z_k| - Re sum_l mu_l (R/(xi_m - z_k))^l
+        const cz<double> t = zinv(cz<double>{d.x / R, d.y / R});
+        out = mu[(int64_t)k * P].x * log(dd) - series(mu + (int64_t)k * P, t);
         return true;
     }
     if (dd * kEta <= rho) {
-        // sum_j log|xi_j - z_k| - Re sum_l nu_l ((xi_m - z_k)/rho)^l / l
-        cz<double> t{d.x / rho, d.y / rho}, pw = t;
-        double s = 0.0;
-        for (int l = 1; l < P; l++) {
-            double2 c = nu[(int64_t)k * P + l];
-            s += (c.x * pw.x - c.y * pw.y) / l;
-            pw = zmul(pw, t);
-        }
-        out = slog - s;
+        // sum_j log|xi_j - z_k| - Re sum_l nu_l ((xi_m - z_k)/rho)^l
+        const cz<double> t{d.x / rho, d.y / rho};
+        out = slog - series(nu + (int64_t)k * P, t);
         return true;
     }
     return false;
 }
 
 __device__ __forceinline__ double schur_entry(int M, int r, int m, const int64_t *ptr,
-                                              const int32_t *kind, const double *lam,
+                                              const int32_t *live, const double *lam,
                                               const double *sell, double ls)
 {
     if (r == M - 1) return 1.0;
     const int k = r + 1;
     double fe = sell[k];  // sum_j (l_j - log 2)
-    if (kind[m] != 0) fe += (double)(ptr[k + 1] - ptr[k]) * lam[m] - 2.0 * ls;
+    if (live[m] != 0) fe += (double)(ptr[k + 1] - ptr[k]) * lam[m] - 2.0 * ls;
     return -fe / (2.0 * LBF_PI);
 }
 
@@ -363,7 +376,7 @@ __device__ __forceinline__ double schur_entry(int M, int r, int m, const int64_t
 // k_mp_schur_direct (a warp per entry) instead of looping in one lane.
 __global__ void k_mp_schur(int M, int P, const int64_t *__restrict__ ptr,
                            const double2 *__restrict__ xi_o, const double2 *__restrict__ xc,
-                           const int32_t *__restrict__ kind, const double *__restrict__ lam,
+                           const int32_t *__restrict__ live, const double *__restrict__ lam,
                            const double2 *__restrict__ zc, const double *__restrict__ Rk,
                            const double *__restrict__ rk, const double *__restrict__ slog,
                            const double *__restrict__ sell, const double2 *__restrict__ mu,
@@ -375,7 +388,7 @@ __global__ void k_mp_schur(int M, int P, const int64_t *__restrict__ ptr,
     int r = (int)(id / M), m = (int)(id % M);
     double ls = 0.0;
     bool listed = false;
-    if (r < M - 1 && kind[m] != 0) {
+    if (r < M - 1 && live[m] != 0) {
         const int k = r + 1;
         if (!island_logsum(k, P, xc[m], zc[k], Rk[k], rk[k], mu, nu, slog[k], ls)) {
             int q = atomicAdd(dcount, 1);
@@ -391,12 +404,12 @@ __global__ void k_mp_schur(int M, int P, const int64_t *__restrict__ ptr,
             }
         }
     }
-    if (!listed) G[(int64_t)r * M + m] = schur_entry(M, r, m, ptr, kind, lam, sell, ls);
+    if (!listed) G[(int64_t)r * M + m] = schur_entry(M, r, m, ptr, live, lam, sell, ls);
 }
 
 __global__ void k_mp_schur_direct(int M, const int64_t *__restrict__ ptr,
                                   const double2 *__restrict__ xi_o, const double2 *__restrict__ xc,
-                                  const int32_t *__restrict__ kind, const double *__restrict__ lam,
+                                  const int32_t *__restrict__ live, const double *__restrict__ lam,
                                   const double *__restrict__ sell, const int32_t *__restrict__ dcount,
                                   const int32_t *__restrict__ dlist, int dcap, double *__restrict__ G)
 {
@@ -413,7 +426,7 @@ __global__ void k_mp_schur_direct(int M, const int64_t *__restrict__ ptr,
             ls += 0.5 * log(dx * dx + dy * dy);
         }
         ls = wsum(ls);
-        if (lane == 0) G[(int64_t)r * M + m] = schur_entry(M, r, m, ptr, kind, lam, sell, ls);
+        if (lane == 0) G[(int64_t)r * M + m] = schur_entry(M, r, m, ptr, live, lam, sell, ls);
     }
 }
 
@@ -868,10 +881,31 @@ static int pairs_to_boxes(lbf_plan *pl, cudaStream_t s, const int32_t *off, cons
     return lbf_radix_sort(sb.key, sb.key_alt, src, sb.val_alt, npairs, bits, work, work_len, s);
 }
 
-// Plan time: node and centre data, the centres' walks down the tree (P2L and
-// direct lists per box), island moments, and S into G (M x M).
-int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
-                 int64_t work_len, const SortBufs &sb)
+// Plan time, without the tree: the centres' planar images, the island moments and
+// S = D - F E into G (M x M).  work holds a counter and the entries summed directly.
+int lbf_schur_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
+                    int64_t work_len)
+{
+    const int M = pl->M;
+    Border &B = pl->bd;
+    LBF_LAUNCH(k_mp_centres_plane, lbf_cdiv(M, 128), 128, 0, s, M, pl->centres, B.xc, B.lam, B.live);
+    LBF_LAUNCH(k_mp_islands, M, 256, 0, s, M, B.P, pl->island_ptr, xi_o, B.zc, B.Rk, B.rk, B.slog,
+               B.sell, B.mu, B.nu);
+    int32_t *dcount = work, *dlist = work + 1;
+    const int dcap = (int)std::min<int64_t>(work_len - 1, INT32_MAX);
+    LBF_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int32_t), s));
+    LBF_LAUNCH(k_mp_schur, lbf_cdiv((int64_t)M * M, 128), 128, 0, s, M, B.P, pl->island_ptr, xi_o,
+               B.xc, B.live, B.lam, B.zc, B.Rk, B.rk, B.slog, B.sell, B.mu, B.nu, G, dcount, dlist,
+               dcap);
+    LBF_LAUNCH(k_mp_schur_direct, 152 * 4, 256, 0, s, M, pl->island_ptr, xi_o, B.xc, B.live, B.lam,
+               B.sell, dcount, dlist, dcap, G);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// Plan time, with the tree: node data, the centres' cells and walks down the tree (P2L
+// and direct lists per box).
+int lbf_mp_build(lbf_plan *pl, cudaStream_t s, int32_t *work, int64_t work_len, const SortBufs &sb)
 {
     int64_t N = pl->N;
     int M = pl->M;
@@ -882,11 +916,8 @@ int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, i
     LBF_LAUNCH(k_mp_nodes, lbf_cdiv(N, 256), 256, 0, s, N, pl->xi, B.ell);
     LBF_LAUNCH(k_mp_leaf_of, lbf_cdiv(T.nleaf, 128), 128, 0, s, T.nleaf, T.leaves, T.begin, T.end,
                B.leaf_of);
-    LBF_LAUNCH(k_mp_centres, lbf_cdiv(M, 128), 128, 0, s, M, pl->centres, g, D, B.xc, B.kind, B.lam,
-               B.cell);
+    LBF_LAUNCH(k_mp_centres, lbf_cdiv(M, 128), 128, 0, s, M, pl->centres, g, D, B.kind, B.cell);
     LBF_LAUNCH(k_mp_glob, 1, 32, 0, s, M, B.kind, B.glob, B.nglob);
-    LBF_LAUNCH(k_mp_islands, M, 256, 0, s, M, B.P, pl->island_ptr, xi_o, B.zc, B.Rk, B.rk, B.slog,
-               B.sell, B.mu, B.nu);
     LBF_CHECK_LAUNCH();
     LBF_CUDA(cudaMemcpyAsync(&B.nglob_h, B.nglob, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     // walks: count, offsets, fill
@@ -949,16 +980,6 @@ int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, i
         B.npartial = np;
         if (B.npartial > B.partial_cap) return LBF_EWORKSPACE;
     }
-    // the walk and pair scratch is free again: a counter and the list of direct entries
-    int32_t *dcount = w2, *dlist = w2 + 1;
-    const int dcap = (int)std::min<int64_t>(w2_len - 1, INT32_MAX);
-    LBF_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int32_t), s));
-    LBF_LAUNCH(k_mp_schur, lbf_cdiv((int64_t)M * M, 128), 128, 0, s, M, B.P, pl->island_ptr, xi_o,
-               B.xc, B.kind, B.lam, B.zc, B.Rk, B.rk, B.slog, B.sell, B.mu, B.nu, G, dcount, dlist,
-               dcap);
-    LBF_LAUNCH(k_mp_schur_direct, 152 * 4, 256, 0, s, M, pl->island_ptr, xi_o, B.xc, B.kind, B.lam,
-               B.sell, dcount, dlist, dcap, G);
-    LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
 

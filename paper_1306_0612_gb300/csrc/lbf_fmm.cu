@@ -38,7 +38,8 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
                        const double *__restrict__ beta, double2 *__restrict__ q,
                        float2 *__restrict__ q32, cx<df64> *__restrict__ qdf,
                        double *__restrict__ part, unsigned *__restrict__ count,
-                       double *__restrict__ out, const int *gate)
+                       double *__restrict__ out, const int *gate,
+                       const int32_t *__restrict__ isl, const double *__restrict__ mean)
 {
     if (fmm::gate_closed(gate)) return;
     __shared__ double sh[32];
@@ -47,10 +48,11 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         double s = sigma[i];
-        double2 qq = make_double2(s, 0.0);
+        const double sc = isl ? s - mean[isl[i]] : s;  // the charges of sigma less its island means
+        double2 qq = make_double2(sc, 0.0);
         if (w) {
             double2 ww = w[i];
-            qq = make_double2(s * ww.x, s * ww.y);
+            qq = make_double2(sc * ww.x, sc * ww.y);
         }
         if (q) q[i] = qq;
         if (q32) q32[i] = make_float2((float)qq.x, (float)qq.y);
@@ -84,6 +86,98 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
         *out = u;
         *count = 0u;
     }
+}
+
+// island of each node (sorted order), a warp per island
+__global__ void k_island_ids(int M, const int64_t *__restrict__ ptr, const int32_t *__restrict__ rank,
+                             int32_t *__restrict__ isl)
+{
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wg >= M) return;
+    for (int64_t j = ptr[wg] + lane; j < ptr[wg + 1]; j += 32) isl[rank[j]] = (int32_t)wg;
+}
+
+// The rows of a density constant on one island.  With the planar double layer
+// P(u)_i = (1/2pi) Im sum_{j != i} w_j u_j/(xi_j - xi_i) + dself_i u_i, the discrete form
+// of Gauss' theorem (Sec. 3) gives, for the indicator 1_k of island k's nodes,
+//   P(1_k) = (o_k/2) 1_k + n_k (1 - 1_k)
+// with o_k = +-1 the curve's orientation and n_k its winding number about the other
+// islands (0, or +-1 for the one island whose planar image encloses all the others).
+// So 2 K 1_k = 2 P(1_k) + 2 (beta . 1_k) 1 = (o_k - 2 n_k) 1_k + (2 n_k + 2 beta . 1_k) 1.
+// A warp per island evaluates o_k/2 at its first node and n_k at two nodes of the next
+// island, rounds them, and flags the split off if a value is not near its rounding or
+// more than one island encloses others.
+__global__ void k_island_modes(int M, const int64_t *__restrict__ ptr, const int32_t *__restrict__ rank,
+                               const double2 *__restrict__ xi, const double2 *__restrict__ w,
+                               const double *__restrict__ dself, double *__restrict__ acoef,
+                               double *__restrict__ scal, unsigned *__restrict__ flags)
+{
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= M) return;
+    const int64_t b = ptr[k], e = ptr[k + 1];
+    const int64_t k1 = (k + 1) % M;
+    const double2 z0 = xi[rank[b]];
+    const double2 z1 = xi[rank[ptr[k1]]], z2 = xi[rank[(ptr[k1] + ptr[k1 + 1]) / 2]];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    auto term = [](double2 wj, double2 zj, double2 z) {  // Im(w_j / (xi_j - z))
+        const double dx = zj.x - z.x, dy = zj.y - z.y;
+        return (wj.y * dx - wj.x * dy) / (dx * dx + dy * dy);
+    };
+    for (int64_t j = b + lane; j < e; j += 32) {
+        const int32_t r = rank[j];
+        const double2 wj = w[r], zj = xi[r];
+        if (j != b) s0 += term(wj, zj, z0);
+        if (M > 1) {
+            s1 += term(wj, zj, z1);
+            s2 += term(wj, zj, z2);
+        }
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane != 0) return;
+    const double on = s0 / (2.0 * LBF_PI) + dself[rank[b]];
+    const double n1 = s1 / (2.0 * LBF_PI), n2 = s2 / (2.0 * LBF_PI);
+    const double o = on > 0.0 ? 1.0 : -1.0, n = rint(n1);
+    const bool good = fabs(2.0 * on - o) < 0.02 && fabs(n1 - n) < 0.01 && fabs(n2 - n) < 0.01 &&
+                      fabs(n) <= 1.0;
+    acoef[k] = o - 2.0 * n;
+    if (!good) atomicOr(&flags[0], 1u);
+    if (n != 0.0) {
+        atomicAdd(&flags[1], 1u);
+        scal[1] = (double)k;
+        scal[2] = 2.0 * n;
+    }
+}
+
+__global__ void k_island_modes_end(double *__restrict__ scal, unsigned *__restrict__ flags)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const bool ok = flags[0] == 0u && flags[1] <= 1u;
+    scal[0] = ok ? 1.0 : 0.0;
+    if (!ok || flags[1] == 0u) {
+        scal[1] = -1.0;
+        scal[2] = 0.0;
+    }
+}
+
+// mean of sigma (sorted order) over each island's nodes, a warp per island, fixed order
+// (0 where the split is off)
+__global__ void k_island_means(int M, const int64_t *__restrict__ ptr, const int32_t *__restrict__ rank,
+                               const double *__restrict__ sigma, double *__restrict__ mean,
+                               const int *gate)
+{
+    if (fmm::gate_closed(gate)) return;
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wg >= M) return;
+    const int64_t b = ptr[wg], e = ptr[wg + 1];
+    double acc = 0.0;
+    for (int64_t j = b + lane; j < e; j += 32) acc += sigma[rank[j]];
+    acc = warp_sum(acc);
+    if (lane == 0) mean[wg] = (e > b && mean[M] != 0.0) ? acc / (double)(e - b) : 0.0;
 }
 
 // Direct O(N^2) Cauchy sums with the same outputs as the leaf kernel's modes
@@ -381,9 +475,14 @@ struct FmmArrays {
     const void *uloc;  // leaf-local node coordinates (float, double-float), else null
 };
 
+// split (float forward rows): the passes see sigma less its island means m_k, and the
+// leaf kernel adds the means' rows exactly (k_island_modes): for islands traversed with
+// the land on one side, (I + 2K) 1_k is a constant vector, far smaller than 1_k, so the
+// float passes never form the near-cancelling sum of a mean density, which is what the
+// corrections of the refinement are made of.
 template <typename R, int MODE>
 int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, const int *gate,
-              cudaStream_t s)
+              cudaStream_t s, bool split = false)
 {
     Tree &T = pl->tree;
     BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
@@ -445,7 +544,10 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
                  32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
-                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf, walk ? 0 : 1);
+                 sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf, walk ? 0 : 1,
+                 split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
+                 split ? (const double *)pl->imean : (const double *)nullptr,
+                 split ? (const double *)pl->iacoef : (const double *)nullptr, pl->M);
     if (walk) {
         LBF_LAUNCH_P(kid_leaf, fmm::k_l2p_walk, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
                      pl->bd.leaf_of, T.level, T.ix, T.iy, pl->anc, (const float2 *)uloc,
@@ -475,16 +577,22 @@ int lbf_fmm_init_attrs()
 // arithmetic of one pass: float, double, or double-float
 enum class Arith { F32, F64, DF64 };
 
+// split: the charges of sigma less its island means (the float forward pass; the leaf
+// kernel adds the means' part back exactly)
 static int prep(lbf_plan *pl, const double *sigma, Arith ar, bool weighted, const int *gate,
-                cudaStream_t s)
+                cudaStream_t s, bool split = false)
 {
     int nb = (int)std::min<int64_t>(lbf_cdiv(pl->N, 256), 1024);
+    if (split)
+        LBF_LAUNCH(k_island_means, lbf_cdiv((int64_t)pl->M * 32, 256), 256, 0, s, pl->M,
+                   pl->island_ptr, pl->rank, sigma, pl->imean, gate);
     LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma, weighted ? pl->w : (const double2 *)nullptr,
                weighted ? pl->beta : (const double *)nullptr,
                ar == Arith::F64 ? pl->q : (double2 *)nullptr,
                ar == Arith::F32 ? pl->q32 : (float2 *)nullptr,
                ar == Arith::DF64 ? (cx<df64> *)pl->qdf : (cx<df64> *)nullptr, pl->red,
-               pl->red_count, pl->bsig, gate);
+               pl->red_count, pl->bsig, gate, split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
+               split ? (const double *)pl->imean : (const double *)nullptr);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -499,7 +607,9 @@ static int apply_mode(lbf_plan *pl, const double *sigma, double *v, const int *g
                      : (pl->qdf && MODE != fmm::kLeafDeriv && pl->opt.matvec == LBF_MATVEC_FMM)
                          ? Arith::DF64
                          : Arith::F64;
-    int rc = prep(pl, sigma, ar, weighted, gate, s);
+    // the float forward rows split off each island's mean density (see fmm_apply)
+    const bool split = ar == Arith::F32 && MODE == fmm::kLeafForward && weighted && pl->isl;
+    int rc = prep(pl, sigma, ar, weighted, gate, s, split);
     if (rc) return rc;
     int64_t N = pl->N;
     if (pl->opt.matvec == LBF_MATVEC_DIRECT) {
@@ -511,7 +621,7 @@ static int apply_mode(lbf_plan *pl, const double *sigma, double *v, const int *g
     if (ar == Arith::F32) {
         FmmArrays a{pl->P32, pl->q32, pl->mpole32, pl->local32, pl->tab32_binom, pl->tab32_tpow,
                     pl->tab32_dshift, pl->u32};
-        return fmm_apply<float, MODE>(pl, a, sigma, v, gate, s);
+        return fmm_apply<float, MODE>(pl, a, sigma, v, gate, s, split);
     }
     if (ar == Arith::DF64) {
         FmmArrays a{pl->P, pl->qdf, pl->mpole, pl->local, pl->tabdf_binom, pl->tabdf_tpow,
@@ -560,6 +670,16 @@ int lbf_multipoles(lbf_plan *pl, const double *x, int P, double2 *mp, const int 
 
 int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
 {
+    if (pl->isl) {
+        const int M = pl->M;
+        unsigned *flags = (unsigned *)(pl->imean + M + 4);
+        LBF_CUDA(cudaMemsetAsync(pl->imean, 0, sizeof(double) * ((size_t)M + 8), s));
+        LBF_LAUNCH(k_island_ids, lbf_cdiv((int64_t)M * 32, 256), 256, 0, s, M, pl->island_ptr,
+                   pl->rank, pl->isl);
+        LBF_LAUNCH(k_island_modes, lbf_cdiv((int64_t)M * 32, 256), 256, 0, s, M, pl->island_ptr,
+                   pl->rank, pl->xi, pl->w, pl->dself, pl->iacoef, pl->imean + M, flags);
+        LBF_LAUNCH(k_island_modes_end, 1, 32, 0, s, pl->imean + M, flags);
+    }
     if (!pl->u32 && !pl->udf) return LBF_OK;
     Tree &T = pl->tree;
     fmm::BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
@@ -580,7 +700,7 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
         int nb = (int)std::min<int64_t>(lbf_cdiv(pl->N, 256), 1024);
         LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma_sorted, pl->w, pl->beta, pl->q,
                    (float2 *)nullptr, (cx<df64> *)pl->qdf, pl->red, pl->red_count, pl->bsig,
-                   (const int *)nullptr);
+                   (const int *)nullptr, (const int32_t *)nullptr, (const double *)nullptr);
         LBF_CHECK_LAUNCH();
         Tree &Tr = pl->tree;
         BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L)};

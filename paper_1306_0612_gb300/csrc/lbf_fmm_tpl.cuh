@@ -679,7 +679,8 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const double *__restrict__ dself, const double2 *__restrict__ w,
                        const double *__restrict__ beta, const double *__restrict__ bsig,
                        double *__restrict__ v, const int *gate, const cx<df64> *__restrict__ udf,
-                       int l2p)
+                       int l2p, const int32_t *__restrict__ isl, const double *__restrict__ imean,
+                       const double *__restrict__ iacoef, int M)
 {
     if (gate_closed(gate)) return;
     constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
@@ -874,7 +875,17 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         if (act) {
             if constexpr (MODE == kLeafForward) {
                 double c = (double)(-phi.y) + (double)(accI * irr);
-                v[i] = 2.0 * (c * (1.0 / (2.0 * LBF_PI)) + dself[i] * sigma[i] + *bsig);
+                // with island means m split off (isl given): the sums saw sigma - m; the
+                // means' rows are a_k m_k + 2 n m_(enclosing island) (the beta . m part is
+                // in bsig, formed from sigma)
+                double mk = 0.0, mrow = 0.0;
+                if (isl) {
+                    const int k = isl[i];
+                    mk = imean[k];
+                    const int ke = (int)imean[M + 1];
+                    mrow = iacoef[k] * mk + (ke >= 0 ? imean[M + 2] * imean[ke] : 0.0);
+                }
+                v[i] = 2.0 * (c * (1.0 / (2.0 * LBF_PI)) + dself[i] * (sigma[i] - mk) + *bsig) + mrow;
             } else if constexpr (MODE == kLeafTranspose) {
                 // Phi = far - near sum (the near sum above is sum q/(xi_s - z))
                 const double pr = (double)phi.x - (double)(acc.x * irr);

@@ -656,7 +656,7 @@ int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const
 // inverse in place by Gauss-Jordan elimination with partial pivoting.
 constexpr size_t kGjSmemCap = 200 * 1024;
 
-// scratch of lbf_border_build: the second matrix buffer, block 0's panel (when it
+// scratch of lbf_border_start: the second matrix buffer, block 0's panel (when it
 // does not fit in shared memory), the partial maxima, pivot rows, permutation, B_P^-1
 // twice, the chunk counter and the grid barrier
 size_t lbf_gj_scratch_doubles(int M)
@@ -664,16 +664,25 @@ size_t lbf_gj_scratch_doubles(int M)
     return (size_t)M * M + (size_t)M * kGjPanel + kGjMaxBlocks + (size_t)M + 2 * kGjPanel * kGjPanel + 64;
 }
 
-int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
-                     int32_t *work, int64_t work_len, const SortBufs &sb)
+// S and S^-1 need the planar nodes and the centres only, not the tree: they run on a
+// side stream (highest priority) that forks from s here, and the inverse takes part of
+// the SMs so that the tree build on s proceeds beside it.
+int lbf_border_start(lbf_plan *pl, cudaStream_t s0, const double2 *xi_o, double *scratch)
 {
     int M = pl->M;
     double *S = pl->Sinv;
-    lbf_prof_mark(LBF_STAGE_BORDER, 1, s);
-    int rc = lbf_mp_build(pl, s, xi_o, S, work, work_len, sb);
-    lbf_prof_mark(LBF_STAGE_BORDER, 0, s);
-    if (rc) return rc;
+    int lo = 0, hi = 0;
+    LBF_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    LBF_CUDA(cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, hi));
+    for (auto &e : pl->fork) LBF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    LBF_CUDA(cudaEventRecord(pl->fork[0], s0));
+    const cudaStream_t s = pl->side;
+    LBF_CUDA(cudaStreamWaitEvent(s, pl->fork[0], 0));
     lbf_prof_mark(LBF_STAGE_INVERSE, 1, s);
+    // until the inverse starts, the first M^2 doubles of its scratch hold the list of
+    // Schur entries summed directly (at most M^2 - M of them)
+    int rc = lbf_schur_build(pl, s, xi_o, S, (int32_t *)scratch, 2 * (int64_t)M * M);
+    if (rc) return rc;
     int dev = 0, nsm = 0, per_sm = 0, coop = 0;
     LBF_CUDA(cudaGetDevice(&dev));
     LBF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -688,8 +697,9 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *
     LBF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmemCap));
     LBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGjThreads, smem));
     if (!coop || per_sm < 1) return LBF_ECUDA;
-    // one block per SM: every SM's double pipe busy, one barrier arrival per SM
-    int nb = (int)std::min<int64_t>(nsm, kGjMaxBlocks);
+    // one block per SM, on half of the SMs: the pivot search of one block bounds each
+    // round, and the other half builds the tree meanwhile
+    const int nb = (int)std::min<int64_t>(std::max(2, nsm / 2), kGjMaxBlocks);
     double *S1 = scratch;                                        // M x M
     double *Pg = S1 + (size_t)M * M;                             // M x kGjPanel
     double *amax = Pg + (size_t)M * kGjPanel;                    // kGjMaxBlocks
@@ -715,7 +725,34 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *
     LBF_LAUNCH(k_gj_gather, M, 256, 0, s, M, S1, perm, S);
     LBF_CHECK_LAUNCH();
     lbf_prof_mark(LBF_STAGE_INVERSE, 0, s);
+    LBF_CUDA(cudaEventRecord(pl->fork[1], s));
     return LBF_OK;
+}
+
+int lbf_border_build(lbf_plan *pl, cudaStream_t s, int32_t *work, int64_t work_len,
+                     const SortBufs &sb)
+{
+    lbf_prof_mark(LBF_STAGE_BORDER, 1, s);
+    int rc = lbf_mp_build(pl, s, work, work_len, sb);
+    lbf_prof_mark(LBF_STAGE_BORDER, 0, s);
+    if (rc) return rc;
+    // join: later work on s sees S^-1
+    LBF_CUDA(cudaStreamWaitEvent(s, pl->fork[1], 0));
+    return LBF_OK;
+}
+
+void lbf_border_end(lbf_plan *pl)
+{
+    if (pl->side) {
+        cudaStreamSynchronize(pl->side);
+        cudaStreamDestroy(pl->side);
+        pl->side = nullptr;
+    }
+    for (auto &e : pl->fork)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
 }
 
 int lbf_geometry_out_impl(const lbf_plan *pl, double *xi, double *normal, double *weight,

@@ -95,6 +95,7 @@ struct Border {
     double *ell = nullptr;           // log(1 + |xi_i|^2)
     double2 *xc = nullptr;           // planar centres
     int32_t *kind = nullptr;         // 0 pole, 1 inside the tree's square, 2 outside
+    int32_t *live = nullptr;         // 1 unless at the pole (kind != 0, without the tree)
     int32_t *cell = nullptr;         // finest-level cell of each centre (2 per centre)
     double *lam = nullptr;           // log(1 + |xi_m|^2)
     int32_t *glob = nullptr, *nglob = nullptr;  // centres summed directly at every node
@@ -144,6 +145,12 @@ struct lbf_plan {
     float2 *u32 = nullptr;  // per node: (xi - c)/r about the centre c, half-width r of its leaf
     int32_t *anc = nullptr;  // per leaf b: anc[b * LBF_ANC_STRIDE + s] = its ancestor s levels up
                              // (levels >= 2 only), for the float operator's ancestor walk
+    int32_t *isl = nullptr;  // per node (sorted order): its island
+    // the float forward pass's island split: per island its mean density (M), then
+    // [M] 1 if the split is on, [M+1] the island whose planar curve encloses the others
+    // (-1: none), [M+2] twice its winding number there; iacoef: the coefficient of an
+    // island's own mean in its rows
+    double *imean = nullptr, *iacoef = nullptr;
     // double-float operator (opt.fmm64): charges, leaf-local coordinates (pairs of
     // float pairs, 16 B), and the translation tables; expansions reuse mpole/local
     void *qdf = nullptr, *udf = nullptr;
@@ -184,6 +191,10 @@ struct lbf_plan {
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [prec][transpose]
     int64_t gnodes[2][2] = {{0, 0}, {0, 0}};  // kernels per replay
     double *host_scalars = nullptr;  // pinned
+    // plan creation only: the stream of the Schur complement and its inverse (beside the
+    // tree build), and its fork and join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork[2] = {nullptr, nullptr};
 };
 
 // ---- layout ------------------------------------------------------------------
@@ -200,12 +211,19 @@ int lbf_geometry_build(lbf_plan *pl, const double *x, const double *dx, const do
                        double2 *w_o, double *d_o, double *b_o);
 int lbf_geometry_gather(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, const double2 *w_o,
                         const double *d_o, const double *b_o);
-int lbf_border_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch,
-                     int32_t *work, int64_t work_len, const SortBufs &sb);
-size_t lbf_gj_scratch_doubles(int M);  // scratch of lbf_border_build
+// S and S^-1 on the side stream (forked from s after the planar nodes exist)
+int lbf_border_start(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *scratch);
+// the tree-dependent part of the border on s, then s waits for S^-1
+int lbf_border_build(lbf_plan *pl, cudaStream_t s, int32_t *work, int64_t work_len,
+                     const SortBufs &sb);
+void lbf_border_end(lbf_plan *pl);     // releases the side stream and events
+size_t lbf_gj_scratch_doubles(int M);  // scratch of lbf_border_start
 // ---- multiplier potential (lbf_border.cu) -------------------------------------
-int lbf_mp_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
-                 int64_t work_len, const SortBufs &sb);
+// S = D - F E into G (M x M) from the planar nodes and centres alone; work holds the
+// list of entries summed directly
+int lbf_schur_build(lbf_plan *pl, cudaStream_t s, const double2 *xi_o, double *G, int32_t *work,
+                    int64_t work_len);
+int lbf_mp_build(lbf_plan *pl, cudaStream_t s, int32_t *work, int64_t work_len, const SortBufs &sb);
 int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v, double sc,
                  double *out, const int *gate, cudaStream_t s, int prec);
 // out = add + sc E^T tau (M-vectors, add nullable; tau sorted), FP64

@@ -347,6 +347,24 @@ def test_fp32_operator_error_against_fp64_and_oracle():
     assert 1e-12 < e32 < 1e-5, e32
 
 
+def test_fp32_operator_island_constant_densities():
+    """Densities nearly constant on each island (what the refinement's corrections are
+    made of) map to outputs far smaller than themselves: (I + 2K) 1_k = 2 (beta . 1_k) 1.
+    The float rows split off the island means, so their error stays relative to the
+    output instead of to the density."""
+    g = wl.config_geometry("C2")
+    p = plan_for(g, precision=L.LBF_PRECISION_FP32_REFINE)
+    rng = np.random.default_rng(23)
+    m = rng.standard_normal(g.M)
+    v = np.repeat(m, np.diff(np.asarray(g.island_ptr))) + 1e-3 * rng.standard_normal(g.N)
+    o32 = zeros(g.N)
+    L.lbf_apply(p, L.LBF_OP_K_ONLY | L.LBF_OP_FP32, dev(v), o32)
+    ref = oracle.apply(g, v, 1)
+    assert np.linalg.norm(ref) < 0.05 * np.linalg.norm(v)  # the near-cancelling regime
+    e32 = rel_l2(host(o32), ref)
+    assert 1e-12 < e32 < 1e-6, e32
+
+
 def test_fp32_operator_c3_sampled_rows():
     """N = 1,048,576 (the bench's geometry, tree depth 20): the float operator of the
     refinement (per-node far-field walk, double-float coordinates across level gaps)
