@@ -486,7 +486,8 @@ def run_batch(args):
         return float(np.max(e)), float(np.median(e))
 
     def batched(precision, sub):
-        opt = L.lbf_default_options(tol=args.tol, precision=precision)
+        kw = dict(inner_tol=args.inner_tol) if args.inner_tol else {}
+        opt = L.lbf_default_options(tol=args.tol, precision=precision, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = L.lbf_batch_run(sub, opt=opt, nworkers=args.workers)

@@ -299,7 +299,7 @@ int lbf_default_options(lbf_options *o)
     o->box_capacity = 0;
     o->precision = LBF_PRECISION_FP64;
     o->p32 = 12;
-    o->inner_tol = 1e-4;
+    o->inner_tol = 3e-4;
     o->max_refine = 20;
     o->graphs = -1;
     o->fmm64 = 1;
