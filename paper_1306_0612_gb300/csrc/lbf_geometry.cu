@@ -243,37 +243,48 @@ __device__ void block_argmax(unsigned long long &key, int &idx, unsigned long lo
 constexpr int kGjPanel = 8;
 
 template <bool STAGE>
-__device__ __forceinline__ double gj_ld(const double *P, int64_t idx)
+__device__ __forceinline__ float gj_ldf(const float *P, int64_t idx)
 {
     if constexpr (STAGE) return P[idx];
     else return __ldcg(P + idx);
 }
 
+// |x| of a float as the unsigned order of its bits; a NaN sorts above infinity
+__device__ __forceinline__ unsigned fkey(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+constexpr unsigned kFInfBits = 0x7f800000u;
+
 struct GjShared {
     unsigned long long sk[33];
     int si[33];
-    double nk[kGjPanel], rk[kGjPanel];   // new pivot row, old row k
+    float nk[kGjPanel], rk[kGjPanel];   // new pivot row, old row k (the search, in float)
     int rrow[2 * kGjPanel], rsrc[2 * kGjPanel], nR, pv[kGjPanel];
+    int bsrc[kGjPanel], okB;             // source rows of B_P; its inverse succeeded
     double binv[kGjPanel][kGjPanel];    // B_P^-1 of the round's panel
     double V[kGjPanel][kGjPanel], G[kGjPanel][kGjPanel];
+    double B[kGjPanel][kGjPanel];       // B_P, then B_P^-1 (block 0)
 };
 
-// Pivot search of the panel [k0, k0 + np) of A (one block): rows >= k0 of the panel
-// columns into Pw (column-major, Pw[c M + i]), the steps, then the pivot rows and
-// B_P^-1 (row c at binv + c kGjPanel).  Returns false if S is singular.
+// Pivot search of the panel [k0, k0 + np) of A (one block), then B_P^-1 (row c at
+// binv + c kGjPanel).  The search only chooses the pivot rows, so it runs the panel's
+// steps in float (the narrow double pipe made it the serial part of every round):
+// rows >= k0 of the panel columns, rounded to float, into Pw (column-major,
+// Pw[c M + i]).  B_P (the chosen rows of the panel, in their order, from the double
+// matrix) is then inverted in double by one warp without further pivoting -- the
+// elimination the double search would have done on those rows -- and a pivot at or
+// below tinykey there means S is singular.  Returns false if S is singular.
 template <bool STAGE>
 __device__ bool gj_panel(int M, const double *A, int k0, int np, unsigned long long tinykey,
-                         double *Pw, int *pivrow, double *binv, GjShared &sh)
+                         float *Pw, int *pivrow, double *binv, GjShared &sh)
 {
     for (int e = threadIdx.x; e < (M - k0) * np; e += blockDim.x) {
         const int i = k0 + e / np, c = e % np;
-        Pw[c * M + i] = __ldcg(&A[(int64_t)i * M + k0 + c]);
+        Pw[c * M + i] = (float)__ldcg(&A[(int64_t)i * M + k0 + c]);
     }
     __syncthreads();
     unsigned long long ck = 0ull;
     int ci = M;
     for (int i = k0 + threadIdx.x; i < M; i += blockDim.x) {
-        const unsigned long long a = abs_key(gj_ld<STAGE>(Pw, i));
+        const unsigned long long a = fkey(gj_ldf<STAGE>(Pw, i));
         if (a > ck) { ck = a; ci = i; }
     }
     bool ok = true;
@@ -301,27 +312,27 @@ __device__ bool gj_panel(int M, const double *A, int k0, int np, unsigned long l
                 if (a > ck || (a == ck && i < ci)) { ck = a; ci = i; }
             }
             if (lane == 0) { sh.sk[32] = ck; sh.si[32] = ci; }
-            if (ck > tinykey && ck <= kInfBits && ci < M && lane < np) {
+            if (ck > 0ull && ck <= kFInfBits && ci < M && lane < np) {
                 const int p = ci;
-                const double ipiv = 1.0 / gj_ld<STAGE>(Pw, c * M + p);
-                sh.rk[lane] = gj_ld<STAGE>(Pw, lane * M + k);
-                sh.nk[lane] = lane == c ? ipiv : gj_ld<STAGE>(Pw, lane * M + p) * ipiv;
-                if (lane == 0) pivrow[k] = p;
+                const float ipiv = 1.0f / gj_ldf<STAGE>(Pw, c * M + p);
+                sh.rk[lane] = gj_ldf<STAGE>(Pw, lane * M + k);
+                sh.nk[lane] = lane == c ? ipiv : gj_ldf<STAGE>(Pw, lane * M + p) * ipiv;
+                if (lane == 0) sh.pv[c] = p;
             }
         }
         __syncthreads();  // rows k and p read before any row is written
         ck = sh.sk[32];
         ci = sh.si[32];
-        if (ck <= tinykey || ck > kInfBits || ci >= M) {  // same values in every thread
+        if (ck == 0ull || ck > kFInfBits || ci >= M) {  // same values in every thread
             ok = false;
             break;
         }
         const int p = ci;
-        double nk[kGjPanel], rk[kGjPanel];
+        float nk[kGjPanel], rk[kGjPanel];
 #pragma unroll
         for (int cc = 0; cc < kGjPanel; cc++) {
-            nk[cc] = cc < np ? sh.nk[cc] : 0.0;
-            rk[cc] = cc < np ? sh.rk[cc] : 0.0;
+            nk[cc] = cc < np ? sh.nk[cc] : 0.0f;
+            rk[cc] = cc < np ? sh.rk[cc] : 0.0f;
         }
         ck = 0ull;
         ci = M;
@@ -332,31 +343,85 @@ __device__ bool gj_panel(int M, const double *A, int k0, int np, unsigned long l
                     if (cc < np) Pw[cc * M + k] = nk[cc];
                 continue;
             }
-            double b[kGjPanel], f = 0.0;
+            float b[kGjPanel], f = 0.0f;
 #pragma unroll
             for (int cc = 0; cc < kGjPanel; cc++) {
-                b[cc] = cc >= np ? 0.0 : (i == p ? rk[cc] : gj_ld<STAGE>(Pw, cc * M + i));
-                if (cc == c) { f = b[cc]; b[cc] = 0.0; }
+                b[cc] = cc >= np ? 0.0f : (i == p ? rk[cc] : gj_ldf<STAGE>(Pw, cc * M + i));
+                if (cc == c) { f = b[cc]; b[cc] = 0.0f; }
             }
 #pragma unroll
             for (int cc = 0; cc < kGjPanel; cc++) {
                 if (cc >= np) continue;
-                const double v = fma(-f, nk[cc], b[cc]);
+                const float v = fmaf(-f, nk[cc], b[cc]);
                 Pw[cc * M + i] = v;
                 if (cc == c + 1 && i > k) {
-                    const unsigned long long a = abs_key(v);
+                    const unsigned long long a = fkey(v);
                     if (a > ck) { ck = a; ci = i; }  // rows ascending per thread: first wins ties
                 }
             }
         }
     }
     __syncthreads();
-    if (ok)
-        for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
-            const int r = e / np, c = e % np;
-            binv[r * kGjPanel + c] = gj_ld<STAGE>(Pw, c * M + k0 + r);
+    if (!ok) return false;
+    // the rows that the interchanges bring to positions k0 .. k0 + np - 1
+    if (threadIdx.x == 0) {
+        int pos[2 * kGjPanel], src[2 * kGjPanel], n = 0;
+        auto find = [&](int r) {
+            for (int t = 0; t < n; t++)
+                if (pos[t] == r) return t;
+            pos[n] = r;
+            src[n] = r;
+            return n++;
+        };
+        for (int c = 0; c < np; c++) {
+            pivrow[k0 + c] = sh.pv[c];
+            const int ta = find(k0 + c), tb = find(sh.pv[c]);
+            const int t = src[ta];
+            src[ta] = src[tb];
+            src[tb] = t;
         }
-    return ok;
+        for (int m = 0; m < np; m++) sh.bsrc[m] = src[find(k0 + m)];
+    }
+    __syncthreads();
+    // B_P^-1 in double by warp 0: Gauss-Jordan in the chosen order (entries lane, lane + 32)
+    if (wid == 0) {
+        for (int e = lane; e < kGjPanel * kGjPanel; e += 32) {
+            const int r = e / kGjPanel, c = e % kGjPanel;
+            sh.B[r][c] = (r < np && c < np) ? __ldcg(&A[(int64_t)sh.bsrc[r] * M + k0 + c])
+                                            : (r == c ? 1.0 : 0.0);
+        }
+        __syncwarp();
+        bool good = true;
+        for (int c = 0; c < np; c++) {
+            const double piv = sh.B[c][c];
+            const unsigned long long pk = abs_key(piv);
+            if (pk <= tinykey || pk > kInfBits) { good = false; break; }  // same in every lane
+            const double ip = 1.0 / piv;
+            double nv[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int e = lane + 32 * h, r = e / kGjPanel, j = e % kGjPanel;
+                const double bc = sh.B[c][j], f = sh.B[r][c];
+                if (r == c) nv[h] = j == c ? ip : bc * ip;
+                else nv[h] = j == c ? -f * ip : fma(-f, bc * ip, sh.B[r][j]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int e = lane + 32 * h;
+                sh.B[e / kGjPanel][e % kGjPanel] = nv[h];
+            }
+            __syncwarp();
+        }
+        if (lane == 0) sh.okB = good ? 1 : 0;
+    }
+    __syncthreads();
+    if (!sh.okB) return false;
+    for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
+        const int r = e / np, c = e % np;
+        binv[r * kGjPanel + c] = sh.B[r][c];
+    }
+    return true;
 }
 
 // The swap set of the panel [k0, k0 + np): the rows its interchanges move (rrow) and,
@@ -473,7 +538,7 @@ k_gj_blocked(int M, double *A0, double *A1, double *amax, int *pivrow, double *b
 {
     extern __shared__ __align__(16) unsigned char gsm[];
     int *slot = (int *)gsm;                                     // M: swap-set entry of a row, or -1
-    double *Pw = STAGE ? (double *)(slot + M + (M & 1)) : Pg;   // block 0's panel, Pw[c M + i]
+    float *Pw = STAGE ? (float *)(slot + M) : (float *)Pg;      // block 0's panel, Pw[c M + i]
     __shared__ GjShared sh;
     const unsigned nb = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -689,7 +754,7 @@ int lbf_border_start(lbf_plan *pl, cudaStream_t s0, const double2 *xi_o, double 
     LBF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     // shared memory: the row slots (M), block 0's panel if it fits
     const size_t sm_base = sizeof(int) * (size_t)(M + 1);
-    const size_t sm_w = sizeof(double) * (size_t)M * kGjPanel;
+    const size_t sm_w = sizeof(float) * (size_t)M * kGjPanel;
     const bool stage = sm_base + sm_w <= kGjSmemCap;
     const size_t smem = sm_base + (stage ? sm_w : 0);
     if (smem > kGjSmemCap) return LBF_EINVAL;  // M above ~51,000
@@ -697,9 +762,10 @@ int lbf_border_start(lbf_plan *pl, cudaStream_t s0, const double2 *xi_o, double 
     LBF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmemCap));
     LBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGjThreads, smem));
     if (!coop || per_sm < 1) return LBF_ECUDA;
-    // one block per SM, on half of the SMs: the pivot search of one block bounds each
-    // round, and the other half builds the tree meanwhile
-    const int nb = (int)std::min<int64_t>(std::max(2, nsm / 2), kGjMaxBlocks);
+    // one block per SM, on two thirds of the SMs: the rest build the tree meanwhile
+    // (measured at M = 1024: half, two thirds and four fifths within 1 % of each other
+    // over the whole step; all SMs stall the tree build)
+    const int nb = (int)std::min<int64_t>(std::max(2, 2 * nsm / 3), kGjMaxBlocks);
     double *S1 = scratch;                                        // M x M
     double *Pg = S1 + (size_t)M * M;                             // M x kGjPanel
     double *amax = Pg + (size_t)M * kGjPanel;                    // kGjMaxBlocks
