@@ -4,6 +4,8 @@ Tolerances: the FP64 matvec within rel-l2 1e-10 of the oracle's direct
 matvec, solutions within 1e-9 of the exact data and of the oracle's dense LU,
 integer tree and permutation work bit-exact.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -362,6 +364,25 @@ def test_fp32_operator_island_constant_densities():
     ref = oracle.apply(g, v, 1)
     assert np.linalg.norm(ref) < 0.05 * np.linalg.norm(v)  # the near-cancelling regime
     e32 = rel_l2(host(o32), ref)
+    assert 1e-12 < e32 < 1e-6, e32
+
+
+def test_fp32_operator_island_split_reversed_orientation():
+    """The same islands traversed the other way (nodes reversed, x' negated): the
+    split's per-island coefficients come from each curve's measured orientation and
+    winding number, so the float rows still match the oracle."""
+    g = wl.config_geometry("C2")
+    ptr = np.asarray(g.island_ptr)
+    N = g.N
+    idx = np.concatenate([np.arange(ptr[k], ptr[k + 1])[::-1] for k in range(g.M)])
+    x, dx, d2x = (np.asarray(a).reshape(N, 3) for a in (g.x, g.dx, g.d2x))
+    gr = dataclasses.replace(g, x=x[idx].copy(), dx=-dx[idx], d2x=d2x[idx].copy())
+    p = plan_for(gr, precision=L.LBF_PRECISION_FP32_REFINE)
+    rng = np.random.default_rng(24)
+    v = np.repeat(rng.standard_normal(g.M), np.diff(ptr)) + 1e-3 * rng.standard_normal(N)
+    o32 = zeros(N)
+    L.lbf_apply(p, L.LBF_OP_K_ONLY | L.LBF_OP_FP32, dev(v), o32)
+    e32 = rel_l2(host(o32), oracle.apply(gr, v, 1))
     assert 1e-12 < e32 < 1e-6, e32
 
 
