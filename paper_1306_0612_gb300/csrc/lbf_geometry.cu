@@ -585,7 +585,10 @@ k_gj_blocked(int M, double *A0, double *A1, double *amax, int *pivrow, double *b
         }
         const int tp = k0 / kGjPanel, tn = n0 < M ? tp + 1 : -1;
         const int cn = tn >= 0 ? nch : 0;  // chunk items of the next panel's tile
-        const int nitems = cn + nch + (ntile - 1 - (tn >= 0 ? 1 : 0));
+        // the other tiles in R row parts when there are more tiles than blocks to take them
+        const int nother = ntile - 1 - (tn >= 0 ? 1 : 0);
+        const int R = (nwk < cn + nch + nother && M >= 256) ? 2 : 1, hr = (M + R - 1) / R;
+        const int nitems = cn + nch + R * nother;
         double *binv1 = binv + ((q + 1) & 1) * kGjPanel * kGjPanel;
         if (blockIdx.x == 0 && !lone) {
             if (tn >= 0) {
@@ -606,8 +609,11 @@ k_gj_blocked(int M, double *A0, double *A1, double *amax, int *pivrow, double *b
                     tile = tp;
                     r0 = (w - cn) * hc;
                     r1 = min(M, r0 + hc);
-                } else {  // the other tiles in order, skipping tp and tn
-                    tile = w - cn - nch;
+                } else {  // the other tiles in order, skipping tp and tn, in R row parts
+                    const int t = w - cn - nch;
+                    tile = t / R;
+                    r0 = (t % R) * hr;
+                    r1 = min(M, r0 + hr);
                     const int lo = tn >= 0 ? min(tp, tn) : tp, hi = tn >= 0 ? max(tp, tn) : INT_MAX;
                     if (tile >= lo) tile++;
                     if (tile >= hi) tile++;
