@@ -8,7 +8,8 @@ a wrong sign, factor or index, a transposed operand) fails it:
 * the constant-density identity (I + 2K) zeta_k = 2 area(Omega_k)/(4 pi) at
   every node (Sec. 4.1 read with the jump relation Eq. jump and Green's
   identity, Eq. green2) - pins the kernel's sign, its 1/2pi, its diagonal and
-  the row/column orientation, against an independent closed-form area;
+  the row/column orientation, against an independent closed-form area; with the
+  islands traversed the other way it becomes 2 zeta_k - 2 area(Omega_k)/(4 pi);
 * the diagonal entry equals the limit of the off-diagonal kernel (Appendix A);
 * the planar Cauchy form (Sec. 3, Eq. dlpC and cont_kern, sign of the Cauchy
   term corrected) agrees entry by entry with the 3D form;
@@ -100,6 +101,24 @@ def test_constant_density_identity_other_pole(oracle):
         y = A[:g.N, :g.N] @ (isl == k).astype(float)
         ak = cap_area(g.r0[k], g.amp[k], g.kfreq[k]) / (4 * np.pi)
         assert np.max(np.abs(y - 2 * ak)) < 1e-10
+
+
+def test_constant_density_identity_reversed_orientation(oracle):
+    """Islands traversed the other way flip the double layer's normal, so
+    (I + 2K) zeta_k = 2 zeta_k - 2 area(Omega_k)/(4 pi): the island-constant rows the
+    float operator adds exactly (orientation o_k = +1 there) are pinned here."""
+    import dataclasses
+    g = _three_islands(128)
+    ptr = np.asarray(g.island_ptr)
+    idx = np.concatenate([np.arange(ptr[k], ptr[k + 1])[::-1] for k in range(g.M)])
+    x, dx, d2x = (np.asarray(a).reshape(g.N, 3) for a in (g.x, g.dx, g.d2x))
+    gr = dataclasses.replace(g, x=x[idx].copy(), dx=-dx[idx], d2x=d2x[idx].copy())
+    K2 = oracle.matrix(gr)[:g.N, :g.N]
+    isl = g.island_of_node()
+    for k in range(g.M):
+        zeta = (isl == k).astype(float)
+        ak = cap_area(g.r0[k], g.amp[k], g.kfreq[k]) / (4 * np.pi)
+        assert np.max(np.abs(K2 @ zeta - (2 * zeta - 2 * ak))) < 1e-11, k
 
 
 def test_diagonal_is_limit_of_kernel(oracle):
