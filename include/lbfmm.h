@@ -81,7 +81,8 @@ typedef struct lbf_options {
     int64_t box_capacity; /* quadtree boxes reserved in the workspace; 0 = estimate */
     int precision;        /* LBF_PRECISION_FP64 or LBF_PRECISION_FP32_REFINE */
     int p32;              /* expansion order of the FP32 FMM (4..31) */
-    double inner_tol;     /* FP32_REFINE: relative tolerance of each inner solve */
+    double inner_tol;     /* FP32_REFINE: relative tolerance of each inner solve
+                             (default 3e-4) */
     int max_refine;       /* FP32_REFINE: maximum refinement steps */
     int graphs;           /* GMRES steps replayed from a CUDA graph captured once per plan
                              (stream must not be the legacy default stream): 1 on, 0 off,
@@ -99,8 +100,11 @@ typedef struct lbf_options {
  *                correction solves P^-1 A d = r with GMRES whose operator runs
  *                the FMM in float (expansions, translations and near field;
  *                node offsets, self terms, the sphere correction, the border
- *                blocks, the Arnoldi basis and the Givens rotations stay in
- *                double), and x += d until ||r|| <= tol ||P^-1 [2g; 0]||. */
+ *                blocks, the rows of each island's mean density -- added
+ *                exactly from the discrete Gauss identity -- and the Hessenberg
+ *                matrix and Givens rotations stay in double; the Krylov basis
+ *                of these inner solves is stored in float, its dot products
+ *                summed in double), and x += d until ||r|| <= tol ||P^-1 [2g; 0]||. */
 #define LBF_PRECISION_FP64 0
 #define LBF_PRECISION_FP32_REFINE 1
 /* lbf_apply: OR this into op to run the FMM part in float (plans built with
