@@ -771,7 +771,13 @@ int lbf_border_start(lbf_plan *pl, cudaStream_t s0, const double2 *xi_o, double 
     // one block per SM, on two thirds of the SMs: the rest build the tree meanwhile
     // (measured at M = 1024: half, two thirds and four fifths within 1 % of each other
     // over the whole step; all SMs stall the tree build)
-    const int nb = (int)std::min<int64_t>(std::max(2, 2 * nsm / 3), kGjMaxBlocks);
+    // and no more blocks than a round has work items (block 0 and, per round, the chunks
+    // of two tiles and the other tiles): each block holds a whole SM, so a small S must
+    // not take the GPU from other streams' work
+    const int ntile = (M + kGjPanel - 1) / kGjPanel;
+    const int hc = std::max(64, (((M + 15) / 16 + 63) / 64) * 64), nch = (M + hc - 1) / hc;
+    const int nb = (int)std::min<int64_t>(std::min(std::max(2, 2 * nsm / 3), 1 + 2 * nch + ntile),
+                                          kGjMaxBlocks);
     double *S1 = scratch;                                        // M x M
     double *Pg = S1 + (size_t)M * M;                             // M x kGjPanel
     double *amax = Pg + (size_t)M * kGjPanel;                    // kGjMaxBlocks
