@@ -10,6 +10,9 @@ a wrong sign, factor or index, a transposed operand) fails it:
   identity, Eq. green2) - pins the kernel's sign, its 1/2pi, its diagonal and
   the row/column orientation, against an independent closed-form area; with the
   islands traversed the other way it becomes 2 zeta_k - 2 area(Omega_k)/(4 pi);
+* the rows of an island-constant density from each curve's orientation and winding
+  number (the planar form of the same identity, both orientations, the island around
+  the pole included) - pins the exact rows the float operator adds;
 * the diagonal entry equals the limit of the off-diagonal kernel (Appendix A);
 * the planar Cauchy form (Sec. 3, Eq. dlpC and cont_kern, sign of the Cauchy
   term corrected) agrees entry by entry with the 3D form;
@@ -172,6 +175,58 @@ def test_planar_cauchy_form_agrees(oracle):
     Kbad = (1 / TWO_PI) * np.imag((h * xip)[None, :] / (-dz)) + beta[None, :]
     np.fill_diagonal(Kbad, np.diag(Kp))
     assert np.max(np.abs(K - Kbad)) > 1e-3
+
+
+def _planar(g):
+    """xi, xi', xi'' (Sec. 3), the weights h, dself_i = (h/4pi) Im(xi''/xi') and beta."""
+    h = np.repeat(TWO_PI / g.nodes_per_island, g.nodes_per_island)
+    X, DX, D2X = (np.asarray(a).reshape(g.N, 3) for a in (g.x, g.dx, g.d2x))
+    w = 1 - X[:, 2]
+    z, zp, zpp = (A[:, 0] + 1j * A[:, 1] for A in (X, DX, D2X))
+    wp, wpp = -DX[:, 2], -D2X[:, 2]
+    xi = z / w
+    xip = zp / w - z * wp / w ** 2
+    xipp = zpp / w - 2 * zp * wp / w ** 2 - z * wpp / w ** 2 + 2 * z * wp ** 2 / w ** 3
+    dself = (h / (4 * np.pi)) * np.imag(xipp / xip)
+    beta = -(h / TWO_PI) * np.imag(np.conj(xi) * xip / (1 + np.abs(xi) ** 2))
+    return h, xi, xip, dself, beta
+
+
+@pytest.mark.parametrize("reverse", [False, True])
+def test_island_constant_rows_from_orientation_and_winding(oracle, reverse):
+    """The rows the float operator adds exactly for a density constant on island k:
+    with o_k = 2 x (the planar double layer of 1_k at one of its own nodes) and n_k =
+    (its value at a node of another island), rounded, 2K 1_k = (o_k - 2 n_k) 1_k +
+    (2 n_k + 2 beta . 1_k) 1 -- for the island around the pole (n_k != 0) too, and with
+    the islands traversed the other way."""
+    import dataclasses
+    g = _three_islands(128)
+    if reverse:
+        ptr = np.asarray(g.island_ptr)
+        idx = np.concatenate([np.arange(ptr[k], ptr[k + 1])[::-1] for k in range(g.M)])
+        x, dx, d2x = (np.asarray(a).reshape(g.N, 3) for a in (g.x, g.dx, g.d2x))
+        g = dataclasses.replace(g, x=x[idx].copy(), dx=-dx[idx], d2x=d2x[idx].copy())
+    ptr = np.asarray(g.island_ptr)
+    h, xi, xip, dself, beta = _planar(g)
+    K2 = oracle.matrix(g)[:g.N, :g.N] - np.eye(g.N)  # 2K
+    enclosing = 0
+    for k in range(g.M):
+        sl = slice(ptr[k], ptr[k + 1])
+        i0, i1 = ptr[k], ptr[(k + 1) % g.M]
+        d0 = xi[sl] - xi[i0]
+        d0[0] = 1.0
+        t0 = (h * xip)[sl] / d0
+        t0[0] = 0.0
+        on = np.imag(t0.sum()) / TWO_PI + dself[i0]
+        off = np.imag(((h * xip)[sl] / (xi[sl] - xi[i1])).sum()) / TWO_PI
+        o, n = np.sign(on), np.rint(off)
+        assert abs(2 * on - o) < 1e-9 and abs(off - n) < 1e-9
+        enclosing += n != 0
+        one = np.zeros(g.N)
+        one[sl] = 1.0
+        ref = (o - 2 * n) * one + (2 * n + 2 * beta[sl].sum())
+        assert np.max(np.abs(K2 @ one - ref)) < 1e-10, k
+    assert enclosing == 1  # the island around the pole (c_1 at the north pole)
 
 
 # ---- the bordered system ------------------------------------------------------
