@@ -230,6 +230,20 @@ def measured_hbm():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def aggregate(ms, units, world, device):
+    """Whole-job numbers of one timed region over the ranks: the slowest rank's time and
+    the units every rank processed (each rank runs its own replica)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -303,10 +317,7 @@ def run_ours(args):
     L.lbf_profile_enable(False)
     launches = L.lbf_launch_count() - n0
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, units = aggregate(ms, float(g.N * (tot["fp64_applies"] + tot["fp32_applies"])), world, dev)
     clocks = clk.summary()
     plan = holder["plan"]
     info = plan.info()
@@ -374,7 +385,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         apply_ms[nm] = e0.elapsed_time(e1) / 5
         apply_err[nm] = float((vout - ref64).norm() / ref64.norm())
-    value = g.N * applies * world / (ms / args.steps / 1e3) / 1e6
+    value = units / (ms / 1e3) / 1e6
 
     # end to end through the public API, host buffers, copies inside the timed region
     e2e = None
@@ -405,6 +416,9 @@ def run_ours(args):
 
         e2e_step()
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         ap_e = 0
@@ -412,9 +426,9 @@ def run_ours(args):
             ap_e += e2e_step()
         f1.record(stream)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1) / args.steps
-        e2e = {"value": g.N * (ap_e / args.steps) * world / (ems / 1e3) / 1e6, "unit": "Mpts/s",
-               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ems}
+        ems, units_e = aggregate(f0.elapsed_time(f1), float(g.N * ap_e), world, dev)
+        e2e = {"value": units_e / (ems / 1e3) / 1e6, "unit": "Mpts/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": ems / args.steps}
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
