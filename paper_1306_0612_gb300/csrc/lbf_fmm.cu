@@ -143,7 +143,7 @@ __global__ void k_island_modes(int M, const int64_t *__restrict__ ptr, const int
     const double o = on > 0.0 ? 1.0 : -1.0, n = rint(n1);
     const bool good = fabs(2.0 * on - o) < 0.02 && fabs(n1 - n) < 0.01 && fabs(n2 - n) < 0.01 &&
                       fabs(n) <= 1.0;
-    acoef[k] = o - 2.0 * n;
+    acoef[k] = good ? o - 2.0 * n : 0.0;  // finite even where a sum was not (the split is off then)
     if (!good) atomicOr(&flags[0], 1u);
     if (n != 0.0) {
         atomicAdd(&flags[1], 1u);
