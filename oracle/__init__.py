@@ -150,6 +150,14 @@ def evaluate(g, sigma, a, targets) -> np.ndarray:
     return u
 
 
+def point_vortices(g, vortices, gamma, targets, A=None) -> np.ndarray:
+    """psi at off-curve targets for point vortices in the ocean with psi = 0 on every
+    curve (Sec. 6, Example 2): psi = psi* + sum_j Gamma_j G(., v_j), where psi* solves the
+    Dirichlet problem with data -sum_j Gamma_j G(x, v_j) on the curves."""
+    sigma, a = solve(g, -green_sum(g.x, vortices, gamma), A)
+    return evaluate(g, sigma, a, targets) + green_sum(targets, vortices, gamma)
+
+
 def project(x) -> np.ndarray:
     """Stereographic projection xi = (x1 + i x2)/(1 - x3) (Sec. 3), as an N x 2 array."""
     x = _f64(x)

@@ -19,6 +19,8 @@ a wrong sign, factor or index, a transposed operand) fails it:
 * exact harmonic solutions G(x, p) - G(x, q) are reproduced, with the exact
   multipliers (net source strength per island) - pins E, F, D and evaluation;
 * spectral convergence of the trapezoidal rule (Sec. 5);
+* a point vortex in the ocean of one circular island (Sec. 6, Example 2) against its
+  closed form by a planar image;
 * the unbordered operator has exactly M - 1 null vectors of the form
   sum c_k zeta_k with sum c_k area_k = 0 (Sec. 4.1), the bordered one none;
 * rotation invariance of the solution under the choice of pole (Sec. 3);
@@ -230,6 +232,29 @@ def test_island_constant_rows_from_orientation_and_winding(oracle, reverse):
 
 
 # ---- the bordered system ------------------------------------------------------
+
+def test_point_vortex_in_cap_ocean_by_planar_image(oracle):
+    """Sec. 6, Example 2, on a geometry with a closed form: one circular island around the
+    north pole is |xi| > R = cot(r0/2) in the plane, the ocean the disk |xi| < R.  For a
+    vortex at nu, psi = Gamma (G(., v) - H) with H the harmonic function on the disk equal
+    to G(., v) on |xi| = R: with |x - v|^2 = 4 |xi - nu|^2 / ((1 + |xi|^2)(1 + |nu|^2)) and,
+    on the circle, |xi - nu| = |nu| |xi - nu*| / R (nu* = R^2 / conj(nu), outside the disk),
+    H = (1/4pi) [log 2 - log 4 - log|xi - nu*|^2 - log(|nu|^2/R^2) + log(1 + R^2) + log(1 + |nu|^2)]."""
+    r0, gam = 0.6, 1.7
+    g = wl.star_caps(3, 1, 256, r0=[r0], amp=[0.0], kfreq=[2])
+    th, ph = r0 + 0.9, 0.4
+    v = np.array([[np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)]])
+    t = wl.targets_off_islands(g, 64, seed=7)
+    psi = oracle.point_vortices(g, v, [gam], t)
+    R = 1.0 / np.tan(r0 / 2)
+    xi_t = t[:, 0] / (1 - t[:, 2]) + 1j * t[:, 1] / (1 - t[:, 2])
+    nu = (v[0, 0] + 1j * v[0, 1]) / (1 - v[0, 2])
+    nus = R * R / np.conj(nu)
+    H = (np.log(2.0) - np.log(4.0) - np.log(np.abs(xi_t - nus) ** 2) - np.log(np.abs(nu) ** 2 / R ** 2)
+         + np.log(1 + R * R) + np.log(1 + np.abs(nu) ** 2)) / (4 * np.pi)
+    exact = gam * (oracle.green_sum(t, v, [1.0]) - H)
+    assert np.all(np.abs(xi_t) < R)  # the targets lie in the ocean
+    assert max_rel(psi, exact) < 1e-10
 
 def _solve_error(oracle, g, src, gam, T=64):
     data = oracle.green_sum(g.x, src, gam)
