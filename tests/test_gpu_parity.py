@@ -226,6 +226,25 @@ def _solve_check(g, src, gam, exact=True, **opt):
     return its, err
 
 
+def test_solve_bench_configuration_c3_matches_exact_solution():
+    """The bench's workload and launch configuration (1024 star caps x 1024 nodes,
+    N = 1,048,576; FP32 inner solves with FP64 refinement to 1e-10; default options)
+    against the exact Green's-pair solution at the bench's 256 targets."""
+    g = wl.star_caps(3, 1024, 1024)
+    src, gam, _ = wl.pair_sources(g, 0, 1)
+    data = oracle.green_sum(g.x, src, gam)
+    p = plan_for(g, tol=1e-10, precision=L.LBF_PRECISION_FP32_REFINE)
+    sig, a = zeros(g.N), zeros(g.M)
+    rc, its, rr = L.lbf_gmres_solve(p, dev(data), sig, a)
+    assert rc == L.LBF_OK and rr <= 1e-10
+    assert L.lbf_solve_stats(p)["refine_steps"] <= 4
+    tg = wl.targets_off_islands(g, 256, seed=17)
+    u = zeros(256)
+    L.lbf_evaluate(p, sig, a, dev(tg), u)
+    uex = oracle.green_sum(tg, src, gam)
+    assert np.max(np.abs(host(u) - uex)) / np.max(np.abs(uex)) < SOLVE_TOL
+
+
 def test_solve_c1_direct():
     g = wl.config_geometry("C1")
     src, gam, _ = wl.pair_sources(g, 0)
