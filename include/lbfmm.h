@@ -216,12 +216,20 @@ int lbf_evaluate_transpose(lbf_plan *plan, int64_t T, const double *targets, con
  *   dL/dxi_j = d/dxi_j (ubar^T C z) - lam^T (dA/dxi_j) z,   A^T lam = C^T ubar,
  * for the solution z = [sigma; a] of lbf_gmres_solve, ubar = dL/du at the targets
  * and lam from lbf_gmres_solve_transpose (r = C^T ubar from lbf_evaluate_transpose).
- * dL/dg_j = 2 lam_j needs no call.  sigma (N), a (M), lam (N + M), ubar (T),
+ * (dL/dg comes from lbf_gradient_data.)  sigma (N), a (M), lam (N + M), ubar (T),
  * targets (T x 3), grad (N x 2 out): device, caller order.  Asynchronous, FP64;
  * LBF_EWORKSPACE when the basis region holds fewer than 12 N doubles. */
 int lbf_gradient_nodes(lbf_plan *plan, const double *sigma, const double *a, const double *lam,
                        int64_t T, const double *targets, const double *ubar, double *grad,
                        lbf_stream_t stream);
+
+/* Gradient of a target functional with respect to the Dirichlet data g: the data
+ * enter the bordered system (Eq. matrix_eqns) only through its right-hand side
+ * [2 g; 0] (the doubled scaling of Eq. disc_sphere), so dL/dg_j = 2 lam_j with lam
+ * the adjoint solution of lbf_gmres_solve_transpose (A^T lam = C^T ubar).
+ *   lam : N + M (device, caller order; only the first N entries are read)
+ *   grad_g : N (device out, caller order).  Asynchronous. */
+int lbf_gradient_data(lbf_plan *plan, const double *lam, double *grad_g, lbf_stream_t stream);
 
 /* Batched solves of independent geometries: many instances of the bordered system
  * of Sec. 5, each with nrhs right-hand sides (the paper solves one instance at a

@@ -3,7 +3,8 @@
 forward:  planar plan from the nodes xi (N x 2; xi' and xi'' fixed), the bordered
           solve A [sigma; a] = [2 g; 0] (Sec. 5) and u at the targets (Eq. u_multi);
 backward: [sbar; abar] = C^T ubar, the adjoint solve A^T lam = C^T ubar (transposed
-          FMM inside GMRES), dL/dg = 2 lam_sigma and dL/dxi from lbf_gradient_nodes.
+          FMM inside GMRES), dL/dg from lbf_gradient_data and dL/dxi from
+          lbf_gradient_nodes.
 Every step runs in the CUDA library; this module only moves tensors.
 """
 from __future__ import annotations
@@ -44,7 +45,10 @@ class SolveEvaluate(torch.autograd.Function):
         rc, _, _ = L.lbf_gmres_solve_transpose(plan, r, lam)
         if rc != L.LBF_OK:
             raise L.LbfError(rc, "lbf_gmres_solve_transpose")
-        grad_g = 2.0 * lam[:N] if ctx.needs_input_grad[0] else None
+        grad_g = None
+        if ctx.needs_input_grad[0]:
+            grad_g = torch.empty(N, dtype=torch.float64, device=ub.device)
+            L.lbf_gradient_data(plan, lam, grad_g)
         grad_xi = None
         if ctx.needs_input_grad[1]:
             grad_xi = torch.empty((N, 2), dtype=torch.float64, device=ub.device)

@@ -197,7 +197,23 @@ Rot3 plan_rot(const lbf_plan *pl)
     return R;
 }
 
+// dL/dg_j = 2 lam_j: the Dirichlet data enter the bordered system only through its
+// doubled right-hand side [2 g; 0] (Eq. disc_sphere), so the adjoint of b -> z carries
+// the factor 2 onto the node part of lam (caller order in and out)
+__global__ void k_grad_data(int64_t N, const double *__restrict__ lam, double *__restrict__ gg)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < N) gg[j] = 2.0 * lam[j];
+}
+
 }  // namespace
+
+int lbf_gradient_data_impl(lbf_plan *pl, const double *lam, double *grad_g, cudaStream_t s)
+{
+    if (pl->N > 0) LBF_LAUNCH(k_grad_data, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, lam, grad_g);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
 
 int lbf_evaluate_transpose_impl(lbf_plan *pl, int64_t T, const double *t, const double *ub,
                                 double *sbar, double *abar, cudaStream_t s)

@@ -596,6 +596,12 @@ int lbf_gradient_nodes(lbf_plan *pl, const double *sigma, const double *a, const
     return lbf_gradient_nodes_impl(pl, sigma, a, lam, T, targets, ubar, grad, (cudaStream_t)stream);
 }
 
+int lbf_gradient_data(lbf_plan *pl, const double *lam, double *grad_g, lbf_stream_t stream)
+{
+    if (!pl || !lam || !grad_g) return LBF_EINVAL;
+    return lbf_gradient_data_impl(pl, lam, grad_g, (cudaStream_t)stream);
+}
+
 int lbf_solve_stats(const lbf_plan *pl, int64_t stats[4])
 {
     if (!pl || !stats) return LBF_EINVAL;

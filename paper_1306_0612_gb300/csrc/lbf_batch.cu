@@ -26,14 +26,14 @@ int run_item(lbf_batch_item &it, const lbf_options &opt_all, cudaStream_t s)
     }
     const int64_t N = pl->N;
     int worst = LBF_OK;
-    for (int r = 0; r < it.nrhs; r++) {
+    for (int r = 0; r < it.nrhs && worst >= 0; r++) {
         int its = 0;
         double rr = 0.0;
         rc = lbf_gmres_solve(pl, it.g + r * N, it.sigma + r * N, it.a ? it.a + (int64_t)r * it.M : nullptr,
                              nullptr, &its, &rr, (lbf_stream_t)s);
         if (rc < 0) {
-            lbf_plan_destroy(pl);
-            return rc;
+            worst = rc;
+            break;
         }
         if (rc == LBF_NOCONV) worst = LBF_NOCONV;
         it.iters += its;
@@ -45,13 +45,12 @@ int run_item(lbf_batch_item &it, const lbf_options &opt_all, cudaStream_t s)
         if (it.T > 0 && it.u) {
             rc = lbf_evaluate(pl, it.sigma + r * N, it.a ? it.a + (int64_t)r * it.M : nullptr, it.T,
                               it.targets, it.u + r * it.T, (lbf_stream_t)s);
-            if (rc) {
-                lbf_plan_destroy(pl);
-                return rc;
-            }
+            if (rc) worst = rc;
         }
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) worst = LBF_ECUDA;
+    // every path: the item's kernels finish before its plan (and the caller's view of
+    // its workspace) is released
+    if (cudaStreamSynchronize(s) != cudaSuccess && worst >= 0) worst = LBF_ECUDA;
     lbf_plan_destroy(pl);
     return worst;
 }

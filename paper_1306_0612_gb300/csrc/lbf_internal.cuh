@@ -283,6 +283,7 @@ int lbf_evaluate_transpose_impl(lbf_plan *pl, int64_t T, const double *t, const 
 int lbf_gradient_nodes_impl(lbf_plan *pl, const double *sigma, const double *a, const double *lam,
                             int64_t T, const double *t, const double *ub, double *grad,
                             cudaStream_t s);
+int lbf_gradient_data_impl(lbf_plan *pl, const double *lam, double *grad_g, cudaStream_t s);
 int lbf_permute_in(lbf_plan *pl, const double *in_caller, double *out_sorted, int with_a,
                    cudaStream_t s);
 int lbf_permute_out(lbf_plan *pl, const double *in_sorted, double *out_caller, int with_a,

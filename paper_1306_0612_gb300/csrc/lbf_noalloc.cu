@@ -144,7 +144,10 @@ extern "C" int lbf_evaluate_noalloc(int64_t N, const double *xi, const double *w
     double *scr = nullptr;
     int rc = na_scratch(&scr);
     if (rc) return rc;
-    // the reduction counter must start at zero whatever an earlier call left behind
+    // the last block of every call that ran to completion leaves the reduction counter at
+    // zero; this reset only recovers a counter left behind by a launch that never
+    // completed (an aborted context).  It does not make overlapping calls safe:
+    // serialise them.
     unsigned *count = (unsigned *)(scr + 2 * (int64_t)LBF_NOALLOC_MAX_NODES + kNaBlocks + 1);
     LBF_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
     int nb = (int)std::min<int64_t>(lbf_cdiv(N, 256), kNaBlocks);

@@ -107,6 +107,7 @@ def load():
                                         C.c_int]),
             "lbf_evaluate_transpose": (C.c_int, [_P, i64, _P, _P, _P, _P, _P]),
             "lbf_gradient_nodes": (C.c_int, [_P, _P, _P, _P, i64, _P, _P, _P, _P]),
+            "lbf_gradient_data": (C.c_int, [_P, _P, _P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
             "lbf_launch_count": (i64, []),
         }
@@ -125,7 +126,7 @@ def exported_symbols():
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
             "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
-            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
+            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
             "lbf_launch_count"]
 
 
@@ -322,6 +323,12 @@ def lbf_gradient_nodes(plan: Plan, sigma: torch.Tensor, a: torch.Tensor, lam: to
            "lbf_gradient_nodes")
 
 
+def lbf_gradient_data(plan: Plan, lam: torch.Tensor, grad_g: torch.Tensor, stream=None):
+    _check(load().lbf_gradient_data(plan.handle, _dptr(lam, plan.N + plan.M, "lam"),
+                                    _dptr(grad_g, plan.N, "grad_g"), _stream(stream)),
+           "lbf_gradient_data")
+
+
 def lbf_batch_run(instances, opt=None, nworkers=8):
     """Solve many independent instances (native scheduler, one CUDA stream per worker).
 
@@ -467,13 +474,26 @@ def lbf_evaluate_noalloc(xi: torch.Tensor, weight: torch.Tensor, sigma: torch.Te
                          a: torch.Tensor | None, centres: torch.Tensor | None,
                          targets: torch.Tensor, u: torch.Tensor, stream=None, N: int | None = None):
     """Off-curve evaluation without any device allocation (static scratch in the
-    library; N <= LBF_NOALLOC_MAX_NODES; overlapping calls race)."""
+    library; N <= LBF_NOALLOC_MAX_NODES; overlapping calls race).  Every array is
+    checked against N, M and T before the call.  N defaults to sigma's length; a
+    larger N is accepted only beyond LBF_NOALLOC_MAX_NODES, where the library
+    rejects the call before it reads any array."""
     N = sigma.numel() if N is None else int(N)
+    if N > sigma.numel() and N <= LBF_NOALLOC_MAX_NODES:
+        raise ValueError(f"N = {N} exceeds the {sigma.numel()} densities passed")
+    checked = N <= LBF_NOALLOC_MAX_NODES
     M = 0 if a is None else a.numel()
+    if (a is None) != (centres is None):
+        raise ValueError("a and centres go together")
     T = targets.numel() // 3
-    _check(load().lbf_evaluate_noalloc(N, _dptr(xi), _dptr(weight), _dptr(sigma), M, _dptr(a),
-                                       _dptr(centres), T, _dptr(targets), _dptr(u),
-                                       _stream(stream)), "lbf_evaluate_noalloc")
+    if targets.numel() != 3 * T:
+        raise ValueError("targets: need T x 3 entries")
+    _check(load().lbf_evaluate_noalloc(
+        N, _dptr(xi, 2 * N if checked else None, "xi"),
+        _dptr(weight, 2 * N if checked else None, "weight"),
+        _dptr(sigma, N if checked else None, "sigma"), M, _dptr(a, M, "a"),
+        _dptr(centres, 3 * M, "centres"), T, _dptr(targets, 3 * T, "targets"),
+        _dptr(u, T, "u"), _stream(stream)), "lbf_evaluate_noalloc")
 
 
 def lbf_sync_status(plan: Plan, stream=None) -> int:

@@ -25,7 +25,11 @@ a wrong sign, factor or index, a transposed operand) fails it:
   sum c_k zeta_k with sum c_k area_k = 0 (Sec. 4.1), the bordered one none;
 * rotation invariance of the solution under the choice of pole (Sec. 3);
 * the reference quadtree: a hand-derived example and brute-force invariants,
-  and completeness of the U/V/W/X lists.
+  and completeness of the U/V/W/X lists;
+* the stereographic projection (Sec. 3) at points whose images are known in closed
+  form: the south pole, the equator, and a point at colatitude theta;
+* the row-by-row matvec (the oracle's direct O(N^2) product, which the GPU parity
+  tests sample) equals the dense bordered matrix times the vector, on a ragged case.
 """
 import json
 import os
@@ -77,7 +81,49 @@ def test_green_special_values(oracle):
     assert abs(oracle.green(z, w) - np.log(2) / (4 * np.pi)) < 1e-15
 
 
+# ---- stereographic projection ---------------------------------------------------
+
+def test_projection_closed_forms(oracle):
+    """xi = (x1 + i x2)/(1 - x3) (Sec. 3), projecting from the north pole: the south
+    pole maps to 0; a point at colatitude theta and longitude phi maps to
+    cot(theta/2) e^{i phi}, so the equator goes to the unit circle at its own
+    longitude.  Dividing by 1 + x3 moves the south pole to infinity and inverts the
+    radii; swapping x1 and x2 reflects the angles about the diagonal."""
+    th = np.array([0.05, 0.3, 1.0, np.pi / 2, 2.2, 3.0, 3.1])
+    ph = np.array([0.1, 2.0, -1.3, 0.7, 4.0, 5.5, -2.9])
+    x = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    xi = oracle.project(np.vstack([x, [[0.0, 0.0, -1.0]]]))
+    assert np.all(xi[-1] == 0.0)
+    z = xi[:-1, 0] + 1j * xi[:-1, 1]
+    want = np.exp(1j * ph) / np.tan(th / 2)
+    assert np.max(np.abs(z - want) / np.abs(want)) < 1e-13  # 1 - cos(theta) rounds near the pole
+    eq = np.isclose(th, np.pi / 2)
+    assert abs(abs(z[eq][0]) - 1.0) < 1e-15
+    assert abs(np.angle(z[eq][0]) - 0.7) < 1e-15
+
+
 # ---- the double-layer operator --------------------------------------------------
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_apply_rows_equal_dense_matrix_product(oracle, op):
+    """The row-by-row matvec (every column of a row, node columns then multiplier
+    columns for op 0; the density block I + 2K for op 1) equals the dense bordered
+    matrix of Eq. (matrix_eqns) times the vector, on islands of 17, 23 and 30 nodes:
+    node rows, the constraint rows of Eq. (disc_constr) and the row of Eq. (sum_ak)."""
+    g = wl.star_caps(21, 3, [17, 23, 30], r0=[0.4, 0.3, 0.25], amp=[0.2, 0.1, 0.25],
+                     kfreq=[5, 3, 4])
+    A = oracle.matrix(g)
+    N, n = g.N, g.N + g.M
+    v = np.random.default_rng(3).standard_normal(n if op == 0 else N)
+    ref = A @ v if op == 0 else A[:N, :N] @ v
+    rows = np.arange(len(ref))[::-1].copy()       # any row order
+    out = oracle.apply_rows(g, v, rows, op=op)
+    assert np.max(np.abs(out - ref[rows])) < 1e-13 * np.max(np.abs(ref))
+    # a subset of rows, each computed alone
+    sub = np.array([0, 16, 17, 39, 69] + ([N, N + 1, N + 2] if op == 0 else []))
+    assert np.max(np.abs(oracle.apply_rows(g, v, sub, op=op) - ref[sub])) < 1e-13 * np.max(np.abs(ref))
+    assert np.allclose(oracle.apply(g, v, op), ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
+
 
 def test_cap_area_closed_form():
     # circular cap: area = 2 pi (1 - cos r0)
