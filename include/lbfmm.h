@@ -91,7 +91,19 @@ typedef struct lbf_options {
     int fmm64;            /* arithmetic of the accurate (double) FMM operator: 0 double,
                              1 double-float (pairs of floats, ~48-bit significands; this
                              GPU issues float 64 times faster than double) */
+    int schur;            /* how the preconditioner applies S^-1 (S = D - F E, Sec. 5, Eq.
+                             matrix_eqns_c): LBF_SCHUR_AUTO, LBF_SCHUR_GJ or LBF_SCHUR_LU */
 } lbf_options;
+
+/* schur: LBF_SCHUR_GJ forms S^-1 by Gauss-Jordan elimination in double (2 M^3 flops on
+ * the double pipe; S^-1 to about cond(S) 2^-52) and applies it as a matrix-vector
+ * product; LBF_SCHUR_LU factors S = P^T L U in double-float arithmetic on the float pipes
+ * (M^3 / 3 multiply-adds; about cond(S) 2^-46) and applies S^-1 by two triangular solves.
+ * Either is a preconditioner: the GMRES solution meets tol whichever is used.
+ * LBF_SCHUR_AUTO takes GJ for M <= 1024 and LU above. */
+#define LBF_SCHUR_AUTO 0
+#define LBF_SCHUR_GJ 1
+#define LBF_SCHUR_LU 2
 
 /* precision of gmres_solve:
  *   FP64:        every operator application in double;
@@ -329,7 +341,12 @@ int lbf_border_counts(const lbf_plan *plan, int64_t counts[6], lbf_stream_t stre
 #define LBF_STAGE_GEOMETRY 10 /* projection, quadtree, interaction lists, gather */
 #define LBF_STAGE_BORDER 11   /* multiplier-potential lists and the Schur complement */
 #define LBF_STAGE_INVERSE 12  /* Gauss-Jordan inverse of the Schur complement */
-#define LBF_KERNEL_COUNT 13
+/* the double-float LU of the Schur complement (schur = LBF_SCHUR_LU) */
+#define LBF_KERNEL_LU_PANEL 13  /* panel elimination with the pivot search (per panel) */
+#define LBF_KERNEL_LU_UPDATE 14 /* interchanges, U12 = L11^-1 A12, diagonal-block inverses */
+#define LBF_KERNEL_LU_GEMM 15   /* trailing update A22 -= L21 U12 */
+#define LBF_KERNEL_LU_SOLVE 16  /* the two triangular solves of each S^-1 application */
+#define LBF_KERNEL_COUNT 17
 int lbf_profile_enable(int on);
 int lbf_profile_reset(void);
 int lbf_profile_read(int kernel, int64_t *launches /* host out */, double *total_ms /* host out */);

@@ -37,7 +37,8 @@ bool valid(const lbf_options &o)
            (o.border == 0 || o.border == 1) &&
            (o.precision == LBF_PRECISION_FP64 || o.precision == LBF_PRECISION_FP32_REFINE) &&
            o.p32 >= 4 && o.p32 + 1 <= 32 && o.inner_tol > 0 && o.inner_tol < 1 &&
-           o.max_refine >= 1 && o.graphs >= -1 && o.graphs <= 1 && (o.fmm64 == 0 || o.fmm64 == 1);
+           o.max_refine >= 1 && o.graphs >= -1 && o.graphs <= 1 && (o.fmm64 == 0 || o.fmm64 == 1) &&
+           o.schur >= LBF_SCHUR_AUTO && o.schur <= LBF_SCHUR_LU;
 }
 
 // host tables of the translation operators (scaled expansions, see lbf_fmm.cu)
@@ -168,7 +169,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     pl->bsig = A.get<double>(4);
     pl->red = A.get<double>(1024);
     pl->red_count = A.get<unsigned>(4);
-    pl->dev_status = A.get<int>(1);
+    pl->dev_status = A.get<int>(2);  // [0] error bits, [1] poll limit of device waits (0: default)
     pl->fvec = A.get<double>(M);
     pl->yvec = A.get<double>(M);
     pl->tin = A.get<double>(n);
@@ -213,6 +214,17 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
         B.nu = A.get<double2>((int64_t)M * B.P);
         B.sums = A.get<double>(4);
         pl->Sinv = A.get<double>((int64_t)M * M);
+        pl->lu = o.schur == LBF_SCHUR_LU || (o.schur == LBF_SCHUR_AUTO && M > 1024);
+        if (pl->lu) {
+            pl->lu_piv = A.get<int>(M);
+            pl->lu_perm = A.get<int>(M);
+            pl->lu_z = A.get<float2>(M);
+            pl->lu_sync = A.get<unsigned>(lbf_lu_sync_words(M));
+            pl->lu_dinv = A.get<float2>(lbf_lu_dinv_entries(M));
+            pl->lu_S = A.get<double>((int64_t)M * M);
+            pl->lu_r = A.get<double>(M);
+            pl->lu_z2 = A.get<float2>(M);
+        }
     }
     int m = o.restart;
     pl->ldv = (n + 31) / 32 * 32;
@@ -240,7 +252,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     add(sizeof(int32_t) * nk);     // perm_alt
     int64_t iscr = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     add(sizeof(int32_t) * iscr);   // integer scratch (scans, histograms, flags)
-    add(sizeof(double) * lbf_gj_scratch_doubles(M));  // Gauss-Jordan pivot rows and partials
+    add(std::max(sizeof(double) * lbf_gj_scratch_doubles(M), lbf_lu_scratch_bytes()));  // the inverse's or the factorisation's
     size_t big = std::max(vbytes, tmp);
     pl->region = (char *)A.take(big);
     pl->region_bytes = big;
@@ -278,7 +290,7 @@ Temps temps(lbf_plan *pl, char *region, int64_t N, int M, int64_t cap)
     int64_t nunits = lbf_cdiv(N, 1024);
     t.iscr_len = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     t.iscr = (int32_t *)take(sizeof(int32_t) * t.iscr_len);
-    t.gj = (double *)take(sizeof(double) * lbf_gj_scratch_doubles(M));
+    t.gj = (double *)take(std::max(sizeof(double) * lbf_gj_scratch_doubles(M), lbf_lu_scratch_bytes()));
     return t;
 }
 }  // namespace
@@ -303,6 +315,7 @@ int lbf_default_options(lbf_options *o)
     o->max_refine = 20;
     o->graphs = -1;
     o->fmm64 = 1;
+    o->schur = LBF_SCHUR_AUTO;
     return LBF_OK;
 }
 
@@ -448,7 +461,7 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
     if (pl->upcnt) CK(cudaMemsetAsync(pl->upcnt, 0, sizeof(int32_t) * cap, s));
     if (pl->pull) CK(cudaMemsetAsync(pl->pull, 0, sizeof(uint32_t) * (2 * cap + 4), s));
     CK(cudaMemcpyAsync(pl->tab_tpow, tpow.data(), sizeof(double2) * tpow.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(pl->dev_status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(pl->dev_status, 0, 2 * sizeof(int), s));
     CK(cudaMemsetAsync(pl->red_count, 0, 4 * sizeof(unsigned), s));
     CK(cudaMemsetAsync(pl->bsig, 0, 4 * sizeof(double), s));
     // plan-creation temporaries overlay the region of the GMRES basis

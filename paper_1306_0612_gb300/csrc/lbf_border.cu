@@ -29,6 +29,7 @@
 
 #include "lbf_df64.cuh"
 #include "lbf_internal.cuh"
+#include "lbf_sync.cuh"
 
 namespace {
 
@@ -633,8 +634,9 @@ __global__ void k_mp_chain(int64_t nbox, int P, const int32_t *__restrict__ pare
             const int p = parent[b];
             if (lane == 0) {
                 unsigned spins = 0;
+                const unsigned lim = wait_limit(status, kChainSpins);
                 while (*(volatile unsigned *)&done[p] != epoch + 1u)
-                    if (++spins > kChainSpins) {
+                    if (++spins > lim) {
                         atomicOr(status, LBF_DEV_TIMEOUT);
                         break;
                     }

@@ -17,6 +17,7 @@
 
 #include "lbf_df64.cuh"
 #include "lbf_internal.cuh"
+#include "lbf_sync.cuh"
 
 namespace fmm {
 
@@ -567,8 +568,9 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     auto wait_for = [&](const unsigned *flag) {
         if (lane == 0) {
             unsigned spins = 0;
+            const unsigned lim = wait_limit(status, kPullSpins);
             while (*(volatile const unsigned *)flag != epoch + 1u)
-                if (++spins > kPullSpins) {
+                if (++spins > lim) {
                     atomicOr(status, LBF_DEV_TIMEOUT);
                     break;
                 }

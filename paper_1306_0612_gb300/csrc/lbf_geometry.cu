@@ -3,6 +3,7 @@
 #include <utility>
 
 #include "lbf_internal.cuh"
+#include "lbf_sync.cuh"
 
 namespace {
 
@@ -139,43 +140,8 @@ __global__ void k_rotate_centres(int M, const double *__restrict__ c, Rot R, dou
 // (cooperative launch), and each wait gives up after kBarrierSpins polls, setting
 // status bit LBF_DEV_TIMEOUT, so the kernel always ends.
 
-constexpr unsigned kBarrierSpins = 1u << 22;
 constexpr int kGjThreads = 512;
 constexpr int kGjMaxBlocks = 1024;
-
-struct GridBarrier {
-    unsigned count, gen;
-};
-
-__device__ bool grid_barrier(GridBarrier *bar, unsigned nb, int *status)
-{
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned *vgen = &bar->gen;
-        const unsigned g = *vgen;
-        __threadfence();
-        if (atomicAdd(&bar->count, 1u) == nb - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            unsigned it = 0;
-            while (*vgen == g) {
-                if (++it > kBarrierSpins) {
-                    atomicOr(status, LBF_DEV_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        if (*(volatile int *)status & LBF_DEV_TIMEOUT) ok = 0;
-    }
-    __syncthreads();
-    return ok != 0;
-}
 
 // Magnitudes are compared as the bit patterns of |x| (for doubles that are not NaN the
 // order of |x| is the unsigned order of its bits), so the pivot searches issue integer
@@ -519,8 +485,9 @@ __device__ bool gj_wait(unsigned *done, unsigned target, int *status)
     if (threadIdx.x == 0) {
         ok = 1;
         unsigned it = 0;
+        const unsigned lim = wait_limit(status, kBarrierSpins);
         while (*(volatile unsigned *)done < target)
-            if (++it > kBarrierSpins) {
+            if (++it > lim) {
                 atomicOr(status, LBF_DEV_TIMEOUT);
                 ok = 0;
                 break;
@@ -754,6 +721,12 @@ int lbf_border_start(lbf_plan *pl, cudaStream_t s0, const double2 *xi_o, double 
     // Schur entries summed directly (at most M^2 - M of them)
     int rc = lbf_schur_build(pl, s, xi_o, S, (int32_t *)scratch, 2 * (int64_t)M * M);
     if (rc) return rc;
+    if (pl->lu) {  // many islands: LU factors in double-float instead of the inverse
+        if ((rc = lbf_schur_lu_factor(pl, s, scratch))) return rc;
+        lbf_prof_mark(LBF_STAGE_INVERSE, 0, s);
+        LBF_CUDA(cudaEventRecord(pl->fork[1], s));
+        return LBF_OK;
+    }
     int dev = 0, nsm = 0, per_sm = 0, coop = 0;
     LBF_CUDA(cudaGetDevice(&dev));
     LBF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -172,7 +172,17 @@ struct lbf_plan {
     unsigned int *red_count = nullptr;
     // border
     Border bd;                  // E y by island expansions (E itself is never formed)
-    double *Sinv = nullptr;     // M x M inverse Schur complement
+    double *Sinv = nullptr;     // M x M inverse Schur complement, or (lu) its LU factors
+    int lu = 0;                 // S^-1 by the double-float LU factors (lbf_schur_lu.cu)
+    int *lu_piv = nullptr, *lu_perm = nullptr;  // row interchanges, final row order (M each)
+    float2 *lu_z = nullptr;     // M-vector of the triangular solves (double-float)
+    unsigned *lu_sync = nullptr;  // ticket, finished blocks, epoch, row-block flags
+    float2 *lu_dinv = nullptr;    // inverses of the 64 x 64 diagonal blocks of L and U
+    double *lu_S = nullptr;       // S itself (double), for the refinement step of accurate applies
+    double *lu_r = nullptr;       // M: that step's residual
+    float2 *lu_z2 = nullptr;      // M: its correction
+    int lu_fast = 0;              // 1 while an Arnoldi step applies the operator: S^-1 from the
+                                  // factors alone (every other application refines once)
     double *fvec = nullptr, *yvec = nullptr;  // M-vectors
     // generic N+M vectors for lbf_apply / gmres
     double *tin = nullptr, *tout = nullptr;
@@ -218,6 +228,13 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, int32_t *work, int64_t work_l
                      const SortBufs &sb);
 void lbf_border_end(lbf_plan *pl);     // releases the side stream and events
 size_t lbf_gj_scratch_doubles(int M);  // scratch of lbf_border_start
+// ---- LU of the Schur complement (lbf_schur_lu.cu) ---------------------------------
+size_t lbf_lu_scratch_bytes();
+int lbf_lu_sync_words(int M);
+int64_t lbf_lu_dinv_entries(int M);
+int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch);
+int lbf_schur_lu_apply(lbf_plan *pl, const double *f, double alpha, double *y, int trans,
+                       const int *gate, cudaStream_t s, int accurate);
 // ---- multiplier potential (lbf_border.cu) -------------------------------------
 // S = D - F E into G (M x M) from the planar nodes and centres alone; work holds the
 // list of entries summed directly

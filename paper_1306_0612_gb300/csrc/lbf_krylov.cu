@@ -509,6 +509,7 @@ static int island_sums(lbf_plan *pl, const double *u, double scale, double *out,
 static int small_gemv(lbf_plan *pl, const double *f, double alpha, double *y, const int *gate,
                       cudaStream_t s)
 {
+    if (pl->lu) return lbf_schur_lu_apply(pl, f, alpha, y, 0, gate, s, !pl->lu_fast);
     LBF_LAUNCH(k_small_gemv, lbf_cdiv((int64_t)pl->M * 32, 256), 256, 0, s, pl->M, pl->Sinv, f,
                alpha, y, gate);
     LBF_CHECK_LAUNCH();
@@ -527,6 +528,7 @@ static int island_scatter(lbf_plan *pl, const double *x, const double *mu, doubl
 static int small_gemv_t(lbf_plan *pl, const double *f, double alpha, double *y, const int *gate,
                         cudaStream_t s)
 {
+    if (pl->lu) return lbf_schur_lu_apply(pl, f, alpha, y, 1, gate, s, !pl->lu_fast);
     LBF_LAUNCH(k_small_gemv_t, lbf_cdiv(pl->M, 128), 128, 0, s, pl->M, pl->Sinv, f, alpha, y, gate);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
@@ -657,7 +659,9 @@ static int arnoldi_step_t(lbf_plan *pl, int opc, int prec, int k, bool from_stat
         }
         vj = pl->vstep;
     }
+    pl->lu_fast = 1;  // Arnoldi steps: S^-1 without its refinement step
     int rc = lbf_apply_op_sorted(pl, opc, vj, w, &pl->gs->go, s, prec);
+    pl->lu_fast = 0;
     if (rc) return rc;
     for (int mode = 0; mode < 3; mode++)
         LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi<T>, nblk, 256, smem, s, n, V, ldv, w, wt, pl->gpart,

@@ -1,0 +1,705 @@
+// The Schur complement S = D - F E of the border (Sec. 5, Eq. matrix_eqns_c) for many
+// islands: LU factorisation with partial pivoting in double-float arithmetic, and the
+// action of S^-1 (and S^-T) by triangular solves.
+//
+// Why not the inverse: the preconditioner needs S^-1 once per GMRES iteration, and
+// the Gauss-Jordan inverse costs 2 M^3 flops on this GPU's narrow double pipe (11.5 s
+// at M = 16384).  Why not float: S is a first-kind (log-kernel) system between the
+// islands, and its condition number grows with M (about 4e5 at M = 256, 3e7 at
+// M = 1024, 2e8 at M = 4096 for the star-cap family), beyond what a float
+// factorisation can refine.  So the factorisation runs in double-float (pairs of
+// floats, ~48-bit significands) on the float pipes, which issue 64 times faster than
+// the double pipe: M^3 / 3 multiply-adds instead of the inverse's M^3.  The
+// preconditioner only has to be close to P^-1: GMRES solves the bordered system to
+// its own tolerance whatever the rounding of S^-1 (which is about cond(S) 2^-46).
+//
+// Layout: the factors overwrite S in place, each entry stored as (hi, lo) floats in the
+// 8 bytes of its double: L strictly below the diagonal (unit diagonal implied), U on
+// and above it.  piv[k] = the row interchanged with row k at step k (row interchanges
+// in the order of the steps, as in LAPACK's getrf); perm[i] = the original row that
+// ends at position i, so P S = L U with (P f)_i = f_perm[i].
+//
+// Per panel of kLuNb columns [k0, k0 + w):
+//   k_lu_panel (cooperative launch): the panel's elimination over the rows >= k0 with
+//              the pivot search; each block keeps its share of the panel's rows in
+//              shared memory; one grid barrier per column, at which every block
+//              publishes its best candidate row (and the owner of row k its row), so
+//              the interchange needs no second barrier;
+//   k_lu_swap: the panel's interchanges applied to every column outside it;
+//   k_lu_trsm: U12 = L11^-1 A12 (the panel's rows to the right of it);
+//   k_lu_gemm: A22 -= L21 U12 (the trailing matrix, 64 x 64 tiles).
+// A pivot at or below M 2^-50 max|S_ij| reports a singular S (status bit 4); every
+// later kernel of the factorisation then returns at once.
+#include <algorithm>
+
+#include "lbf_df64.cuh"
+#include "lbf_internal.cuh"
+#include "lbf_sync.cuh"
+
+namespace {
+
+constexpr int kLuNb = 64;          // panel width
+constexpr int kLuThreads = 256;
+constexpr int kLuTs = 64;          // row block of the triangular solves, GEMM tile
+constexpr int kLuPad = 65;         // shared-memory row stride of 64-wide tiles
+constexpr unsigned kLuSpins = 1u << 24;
+constexpr int kLuMaxPanelBlocks = 1024;
+constexpr size_t kLuSmemCap = 200 * 1024;
+
+__device__ __forceinline__ df64 ld(float2 v) { return df64(v.x, v.y, 0); }
+__device__ __forceinline__ float2 pk(df64 v) { return make_float2(v.hi, v.lo); }
+__device__ __forceinline__ unsigned mag_key(float2 v) { return __float_as_uint(v.x) & 0x7fffffffu; }
+constexpr unsigned kFInf = 0x7f800000u;
+
+__device__ __forceinline__ bool lu_failed(const int *status)
+{
+    return (*(const volatile int *)status & 4) != 0;
+}
+
+// S (double) -> (hi, lo) floats in the same 8 bytes, and max |S_ij| as a bit key
+__global__ void k_lu_convert(int64_t n, double *S, unsigned *amax)
+{
+    unsigned best = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = S[i];
+        const float hi = (float)d;
+        const float lo = (float)(d - (double)hi);
+        ((float2 *)S)[i] = make_float2(hi, lo);
+        best = max(best, __float_as_uint(hi) & 0x7fffffffu);
+    }
+    __shared__ unsigned wb[32];
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) wb[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) best = max(best, wb[k]);
+        atomicMax(amax, best);
+    }
+}
+
+// The panel [k0, k0 + w) over rows [k0, M).  Block b owns rows [k0 + b rpb, ...).
+__global__ void __launch_bounds__(kLuThreads)
+k_lu_panel(int M, int k0, int w, int rpb, float2 *A, int *piv, const unsigned *amax,
+           unsigned *ckey, int *crow, float2 *cval, float2 *rjval, GridBarrier *bar, int *status)
+{
+    if (lu_failed(status)) return;  // same value in every block: set by an earlier launch
+    extern __shared__ __align__(16) float2 lsm[];
+    float2 *tile = lsm;                        // rpb x kLuNb
+    float2 *lcol = lsm + (size_t)rpb * kLuNb;  // rpb
+    __shared__ float2 pv[kLuNb], rj[kLuNb];
+    __shared__ unsigned sk[kLuThreads / 32];
+    __shared__ int si[kLuThreads / 32], sq[kLuThreads / 32];
+    __shared__ int s_row, s_wb, s_sing;
+    const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int r0 = k0 + b * rpb, r1 = min(M, r0 + rpb), nr = max(0, r1 - r0);
+    for (int e = tid; e < nr * w; e += blockDim.x) {
+        const int i = e / w, c = e % w;
+        tile[i * kLuNb + c] = A[(int64_t)(r0 + i) * M + k0 + c];
+    }
+    const unsigned tiny = __float_as_uint(__uint_as_float(*amax) * (float)M * 0x1p-50f);
+    __syncthreads();
+    for (int c = 0; c < w; c++) {
+        const int j = k0 + c, par = c & 1;
+        // this block's candidate: the largest |entry| of column c on its rows >= j
+        unsigned key = 0;
+        int row = INT_MAX;
+        for (int i = tid; i < nr; i += blockDim.x) {
+            const int gi = r0 + i;
+            if (gi < j) continue;
+            const unsigned kk = mag_key(tile[i * kLuNb + c]);
+            if (row == INT_MAX || kk > key || (kk == key && gi < row)) { key = kk; row = gi; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned k2 = __shfl_xor_sync(0xffffffffu, key, o);
+            const int r2 = __shfl_xor_sync(0xffffffffu, row, o);
+            if (r2 != INT_MAX && (row == INT_MAX || k2 > key || (k2 == key && r2 < row))) { key = k2; row = r2; }
+        }
+        if (lane == 0) { sk[wid] = key; si[wid] = row; }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned bk = 0;
+            int br = INT_MAX;
+            for (int q = 0; q < kLuThreads / 32; q++)
+                if (si[q] != INT_MAX && (br == INT_MAX || sk[q] > bk || (sk[q] == bk && si[q] < br))) {
+                    bk = sk[q];
+                    br = si[q];
+                }
+            ckey[par * nb + b] = bk;
+            crow[par * nb + b] = br;
+            s_row = br;
+        }
+        __syncthreads();
+        {
+            const int cr = s_row;
+            if (cr != INT_MAX && tid < w) cval[((size_t)par * nb + b) * kLuNb + tid] = tile[(cr - r0) * kLuNb + tid];
+            if (j >= r0 && j < r1 && tid < w) rjval[par * kLuNb + tid] = tile[(j - r0) * kLuNb + tid];
+        }
+        if (!grid_barrier(bar, nb, status)) return;
+        {
+            // the winner over the blocks' candidates: a thread per candidate, then the
+            // block's (max key, smallest row) reduction
+            unsigned bk = 0;
+            int br = INT_MAX, bq = -1;
+            for (int q = tid; q < nb; q += blockDim.x) {
+                const int rr = __ldcg(&crow[par * nb + q]);
+                if (rr == INT_MAX) continue;
+                const unsigned kk = __ldcg(&ckey[par * nb + q]);
+                if (bq < 0 || kk > bk || (kk == bk && rr < br)) { bk = kk; br = rr; bq = q; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+                const int r2 = __shfl_xor_sync(0xffffffffu, br, o);
+                const int q2 = __shfl_xor_sync(0xffffffffu, bq, o);
+                if (q2 >= 0 && (bq < 0 || k2 > bk || (k2 == bk && r2 < br))) { bk = k2; br = r2; bq = q2; }
+            }
+            __syncthreads();  // sk, si reused
+            if (lane == 0) { sk[wid] = bk; si[wid] = br; sq[wid] = bq; }
+            __syncthreads();
+            if (tid == 0) {
+                bk = 0;
+                br = INT_MAX;
+                bq = -1;
+                for (int q = 0; q < kLuThreads / 32; q++)
+                    if (sq[q] >= 0 && (bq < 0 || sk[q] > bk || (sk[q] == bk && si[q] < br))) {
+                        bk = sk[q];
+                        br = si[q];
+                        bq = sq[q];
+                    }
+                s_row = bq < 0 ? j : br;
+                s_wb = bq;
+                s_sing = bq < 0 || bk <= tiny || bk > kFInf;
+                if (b == 0) piv[j] = s_row;
+            }
+        }
+        __syncthreads();
+        if (s_sing) {
+            if (b == 0 && tid == 0) atomicOr(status, 4);
+            break;  // every block takes the same branch
+        }
+        const int p = s_row, wb = s_wb;
+        if (tid < w) {
+            pv[tid] = __ldcg(&cval[((size_t)par * nb + wb) * kLuNb + tid]);
+            rj[tid] = __ldcg(&rjval[par * kLuNb + tid]);
+        }
+        __syncthreads();
+        // the interchange of rows j and p, within the panel
+        if (j >= r0 && j < r1 && tid < w) tile[(j - r0) * kLuNb + tid] = pv[tid];
+        if (p != j && p >= r0 && p < r1 && tid < w) tile[(p - r0) * kLuNb + tid] = rj[tid];
+        __syncthreads();
+        const df64 invp = df_rcp(ld(pv[c]));
+        for (int i = tid; i < nr; i += blockDim.x) {
+            if (r0 + i <= j) continue;
+            const float2 l = pk(ld(tile[i * kLuNb + c]) * invp);
+            tile[i * kLuNb + c] = l;
+            lcol[i] = l;
+        }
+        __syncthreads();
+        const int nc = w - c - 1;
+        for (int e = tid; e < nr * nc; e += blockDim.x) {
+            const int i = e / nc, cc = c + 1 + e % nc;
+            if (r0 + i <= j) continue;
+            tile[i * kLuNb + cc] = pk(df_fma(-ld(lcol[i]), ld(pv[cc]), ld(tile[i * kLuNb + cc])));
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nr * w; e += blockDim.x) {
+        const int i = e / w, c = e % w;
+        A[(int64_t)(r0 + i) * M + k0 + c] = tile[i * kLuNb + c];
+    }
+}
+
+// the panel's interchanges, in order, on every column outside the panel
+__global__ void k_lu_swap(int M, int k0, int w, float2 *A, const int *piv, const int *status)
+{
+    if (lu_failed(status)) return;
+    __shared__ int sp[kLuNb];
+    if (threadIdx.x < w) sp[threadIdx.x] = piv[k0 + threadIdx.x];
+    __syncthreads();
+    const int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (col >= M || (col >= k0 && col < k0 + w)) return;
+    for (int c = 0; c < w; c++) {
+        const int p = sp[c], j = k0 + c;
+        if (p == j) continue;
+        const float2 a = A[(int64_t)j * M + col], q = A[(int64_t)p * M + col];
+        A[(int64_t)j * M + col] = q;
+        A[(int64_t)p * M + col] = a;
+    }
+}
+
+// U12 = L11^-1 A12 on 64 columns per block (column-oriented forward substitution)
+__global__ void __launch_bounds__(kLuThreads)
+k_lu_trsm(int M, int k0, int w, float2 *A, const int *status)
+{
+    if (lu_failed(status)) return;
+    extern __shared__ __align__(16) float2 tsm[];
+    float2 *Ls = tsm;                    // w x kLuPad
+    float2 *Xs = tsm + kLuNb * kLuPad;   // w x kLuPad
+    const int c0 = k0 + w + blockIdx.x * kLuTs, nc = min(kLuTs, M - c0);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+        const int r = e / w, t = e % w;
+        Ls[r * kLuPad + t] = A[(int64_t)(k0 + r) * M + k0 + t];
+    }
+    for (int e = tid; e < w * kLuTs; e += blockDim.x) {
+        const int r = e / kLuTs, cc = e % kLuTs;
+        if (cc < nc) Xs[r * kLuPad + cc] = A[(int64_t)(k0 + r) * M + c0 + cc];
+    }
+    __syncthreads();
+    for (int t = 0; t < w - 1; t++) {
+        const int cnt = (w - 1 - t) * nc;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const int r = t + 1 + e / nc, cc = e % nc;
+            Xs[r * kLuPad + cc] = pk(df_fma(-ld(Ls[r * kLuPad + t]), ld(Xs[t * kLuPad + cc]), ld(Xs[r * kLuPad + cc])));
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < w * kLuTs; e += blockDim.x) {
+        const int r = e / kLuTs, cc = e % kLuTs;
+        if (cc < nc) A[(int64_t)(k0 + r) * M + c0 + cc] = Xs[r * kLuPad + cc];
+    }
+}
+
+// A22 -= L21 U12: one 64 x 64 tile of A22 per block, each thread a 4 x 4 patch, the
+// panel's K <= 64 columns staged in shared memory (L21 transposed)
+__global__ void __launch_bounds__(kLuThreads)
+k_lu_gemm(int M, int k0, int w, float2 *A, const int *status)
+{
+    if (lu_failed(status)) return;
+    extern __shared__ __align__(16) float2 gsm2[];
+    float2 *As = gsm2;                    // As[k * kLuPad + r] = L21[r][k]
+    float2 *Bs = gsm2 + kLuNb * kLuPad;   // Bs[k * kLuTs + c] = U12[k][c]
+    const int k1 = k0 + w;
+    const int i0 = k1 + blockIdx.y * kLuTs, j0 = k1 + blockIdx.x * kLuTs;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int e = tid; e < kLuTs * w; e += blockDim.x) {
+        const int r = e / w, k = e % w, gi = i0 + r;
+        As[k * kLuPad + r] = gi < M ? A[(int64_t)gi * M + k0 + k] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < w * kLuTs; e += blockDim.x) {
+        const int k = e / kLuTs, c = e % kLuTs, gj = j0 + c;
+        Bs[k * kLuTs + c] = gj < M ? A[(int64_t)(k0 + k) * M + gj] : make_float2(0.f, 0.f);
+    }
+    df64 acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int gi = i0 + ty * 4 + u;
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            const int gj = j0 + tx * 4 + v;
+            acc[u][v] = (gi < M && gj < M) ? ld(A[(int64_t)gi * M + gj]) : df64(0.f);
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < w; k++) {
+        df64 a[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) a[u] = -ld(As[k * kLuPad + ty * 4 + u]);
+#pragma unroll
+        for (int v = 0; v < 4; v++) bv[v] = ld(Bs[k * kLuTs + tx * 4 + v]);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) acc[u][v] = df_fma(a[u], bv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int gi = i0 + ty * 4 + u;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            const int gj = j0 + tx * 4 + v;
+            if (gj < M) A[(int64_t)gi * M + gj] = pk(acc[u][v]);
+        }
+    }
+}
+
+// Inverses of the diagonal blocks of L (unit lower) and U (upper), one kLuTs x kLuTs
+// block per CUDA block, by substitution against the identity (columns in parallel);
+// a short last block is padded with the identity.  dinv: [2][nB][kLuTs][kLuTs],
+// L's inverses first.  The triangular solves then take each diagonal block as one
+// matrix-vector product instead of kLuTs dependent steps.
+__global__ void __launch_bounds__(kLuThreads)
+k_lu_diaginv(int M, const float2 *__restrict__ A, float2 *__restrict__ dinv, const int *status)
+{
+    if (lu_failed(status)) return;
+    extern __shared__ __align__(16) float2 dsm[];
+    float2 *Ts = dsm;                    // the factor's diagonal block
+    float2 *X = dsm + kLuTs * kLuPad;    // its inverse
+    const int b = blockIdx.x, rb = b * kLuTs, nr = min(kLuTs, M - rb), tid = threadIdx.x;
+    const int nB = gridDim.x;
+    for (int which = 0; which < 2; which++) {  // 0: L, 1: U
+        for (int e = tid; e < kLuTs * kLuTs; e += blockDim.x) {
+            const int r = e >> 6, c = e & 63;
+            float2 v = make_float2(r == c ? 1.f : 0.f, 0.f);
+            if (r < nr && c < nr && (which == 0 ? c < r : c >= r)) v = A[(int64_t)(rb + r) * M + rb + c];
+            Ts[r * kLuPad + c] = v;
+            X[r * kLuPad + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
+        }
+        __syncthreads();
+        if (which == 0) {
+            for (int t = 0; t < kLuTs - 1; t++) {  // rows below t lose L[r][t] times row t
+                for (int e = tid; e < (kLuTs - 1 - t) * kLuTs; e += blockDim.x) {
+                    const int r = t + 1 + (e >> 6), c = e & 63;
+                    X[r * kLuPad + c] = pk(df_fma(-ld(Ts[r * kLuPad + t]), ld(X[t * kLuPad + c]), ld(X[r * kLuPad + c])));
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int t = kLuTs - 1; t >= 0; t--) {  // row t divided by U[t][t], then rows above
+                const df64 ip = df_rcp(ld(Ts[t * kLuPad + t]));
+                if (tid < kLuTs) X[t * kLuPad + tid] = pk(ld(X[t * kLuPad + tid]) * ip);
+                __syncthreads();
+                for (int e = tid; e < t * kLuTs; e += blockDim.x) {
+                    const int r = e >> 6, c = e & 63;
+                    X[r * kLuPad + c] = pk(df_fma(-ld(Ts[r * kLuPad + t]), ld(X[t * kLuPad + c]), ld(X[r * kLuPad + c])));
+                }
+                __syncthreads();
+            }
+        }
+        float2 *out = dinv + ((size_t)which * nB + b) * kLuTs * kLuTs;
+        for (int e = tid; e < kLuTs * kLuTs; e += blockDim.x) out[e] = X[(e >> 6) * kLuPad + (e & 63)];
+        __syncthreads();
+    }
+}
+
+// perm from the interchanges (one block; in shared memory when it fits)
+__global__ void k_lu_perm(int M, const int *piv, int *perm, int in_shared)
+{
+    extern __shared__ int ps[];
+    int *p = in_shared ? ps : perm;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) p[i] = i;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < M; k++) {
+            const int q = piv[k];
+            if (q != k && q >= 0 && q < M) {
+                const int t = p[k];
+                p[k] = p[q];
+                p[q] = t;
+            }
+        }
+    __syncthreads();
+    if (in_shared)
+        for (int i = threadIdx.x; i < M; i += blockDim.x) perm[i] = p[i];
+}
+
+__device__ __forceinline__ bool gate_shut(const int *gate) { return gate && *gate == 0; }
+
+// z = P f (forward) or z = f (transposed), as double-float
+__global__ void k_lu_gather(int M, const int *__restrict__ perm, const double *__restrict__ f,
+                            float2 *__restrict__ z, int trans, const int *gate)
+{
+    if (gate_shut(gate)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) z[i] = pk(df64(trans ? f[i] : f[perm[i]]));
+}
+
+// y = alpha z (forward) or y = alpha P^T z (transposed)
+__global__ void k_lu_scatter(int M, const int *__restrict__ perm, const float2 *__restrict__ z,
+                             double alpha, double *__restrict__ y, int trans, const int *gate)
+{
+    if (gate_shut(gate)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double v = alpha * ((double)z[i].x + (double)z[i].y);
+    y[trans ? perm[i] : i] = v;
+}
+
+// Triangular solve T x = x (in place, double-float), T from the factors:
+//   mode 0: L (unit lower)   mode 1: U (upper)   mode 2: U^T (lower)   mode 3: L^T (unit upper).
+// Row blocks of kLuTs rows are taken from a ticket counter in solve order (increasing
+// for lower, decreasing for upper).  A block first prefetches its diagonal block's
+// inverse (shared memory) and the off-diagonal tile it will need last (registers),
+// then waits (bounded) for each block it depends on, in solve order, subtracting that
+// block's part as it arrives, and finally multiplies by the diagonal inverse and
+// publishes its rows by a flag word.  Every block it waits for took its ticket
+// earlier and is running, so every wait ends.
+// sw: [0] ticket, [1] finished blocks, [2] epoch, then one flag per row block; the last
+// block to finish resets the counters and advances the epoch.
+__global__ void __launch_bounds__(kLuThreads)
+k_lu_trsv(int M, int mode, const float2 *__restrict__ A, const float2 *__restrict__ dinv,
+          float2 *x, unsigned *sw, int *status, const int *gate)
+{
+    if (gate_shut(gate)) return;
+    extern __shared__ __align__(16) float2 vsm[];
+    float2 *T = vsm;                      // kLuTs x kLuPad: the diagonal block's inverse (as T)
+    float2 *part = vsm + kLuTs * kLuPad;  // 4 x kLuTs partial sums
+    __shared__ float2 xs[kLuTs], rv[kLuTs];
+    __shared__ unsigned s_t, s_epoch;
+    const bool lower = mode == 0 || mode == 2, trans = mode >= 2;
+    const int nB = (M + kLuTs - 1) / kLuTs, tid = threadIdx.x;
+    unsigned *flag = sw + 3;
+    if (tid == 0) s_epoch = *(volatile unsigned *)&sw[2];
+    __syncthreads();
+    const unsigned epoch = s_epoch;
+    // this thread's (row, quarter) of a tile product
+    const int r = trans ? (tid & 63) : (tid >> 2), q = trans ? (tid >> 6) : (tid & 3);
+    for (;;) {
+        if (tid == 0) s_t = atomicAdd(&sw[0], 1u);
+        __syncthreads();
+        const unsigned t = s_t;
+        __syncthreads();
+        if (t >= (unsigned)nB) break;
+        const int b = lower ? (int)t : nB - 1 - (int)t;
+        const int rb = b * kLuTs, nr = min(kLuTs, M - rb);
+        // the diagonal block's inverse: L^-1 (mode 0), U^-1 (1), U^-T (2), L^-T (3)
+        {
+            const float2 *D = dinv + ((size_t)((mode == 1 || mode == 2) ? 1 : 0) * nB + b) * kLuTs * kLuTs;
+            for (int e = tid; e < kLuTs * kLuTs; e += blockDim.x) {
+                const int rr = e >> 6, cc = e & 63;
+                T[(trans ? cc : rr) * kLuPad + (trans ? rr : cc)] = D[e];
+            }
+        }
+        const int nj = lower ? b : nB - 1 - b;
+        // prefetch of the last off-diagonal tile (the one on the critical path)
+        float2 pre[16];
+        if (nj > 0) {
+            const int j = lower ? b - 1 : b + 1, cb = j * kLuTs, nc = min(kLuTs, M - cb);
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const int c = q * 16 + k;
+                pre[k] = make_float2(0.f, 0.f);
+                if (r < nr && c < nc)
+                    pre[k] = trans ? A[(int64_t)(cb + c) * M + rb + r] : A[(int64_t)(rb + r) * M + cb + c];
+            }
+        }
+        df64 accp(0.f);
+        for (int jj = 0; jj < nj; jj++) {
+            const int j = lower ? jj : nB - 1 - jj;
+            block_wait_flag(&flag[j], epoch + 1u, status, kLuSpins);
+            const int cb = j * kLuTs, nc = min(kLuTs, M - cb);
+            if (tid < nc) xs[tid] = __ldcg(&x[cb + tid]);
+            __syncthreads();
+            if (r < nr) {
+                if (jj == nj - 1) {
+#pragma unroll
+                    for (int k = 0; k < 16; k++)
+                        if (q * 16 + k < nc) accp = df_fma(ld(pre[k]), ld(xs[q * 16 + k]), accp);
+                } else {
+                    const int c1 = min(nc, q * 16 + 16);
+                    if (!trans) {
+                        const float2 *row = A + (int64_t)(rb + r) * M + cb;
+                        for (int c = q * 16; c < c1; c++) accp = df_fma(ld(row[c]), ld(xs[c]), accp);
+                    } else {
+                        for (int c = q * 16; c < c1; c++)
+                            accp = df_fma(ld(A[(int64_t)(cb + c) * M + rb + r]), ld(xs[c]), accp);
+                    }
+                }
+            }
+            __syncthreads();  // xs is refilled next
+        }
+        part[q * kLuTs + r] = pk(accp);
+        __syncthreads();
+        if (tid < kLuTs) {
+            df64 v(0.f);
+            if (tid < nr)
+                v = ld(__ldcg(&x[rb + tid])) - (((ld(part[tid]) + ld(part[kLuTs + tid])) +
+                                                 ld(part[2 * kLuTs + tid])) + ld(part[3 * kLuTs + tid]));
+            rv[tid] = pk(v);
+        }
+        __syncthreads();
+        {
+            df64 a(0.f);
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const int c = q * 16 + k;
+                a = df_fma(ld(T[r * kLuPad + c]), ld(rv[c]), a);
+            }
+            part[q * kLuTs + r] = pk(a);
+        }
+        __syncthreads();
+        if (tid < nr)
+            x[rb + tid] = pk(((ld(part[tid]) + ld(part[kLuTs + tid])) + ld(part[2 * kLuTs + tid])) +
+                             ld(part[3 * kLuTs + tid]));
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(&flag[b], epoch + 1u);
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&sw[1], 1u) == gridDim.x - 1) {
+            sw[0] = 0u;
+            sw[1] = 0u;
+            __threadfence();
+            atomicExch(&sw[2], epoch + 1u);
+        }
+    }
+}
+
+// r = f - S z_nat (forward) or r = f - S^T z_nat (transposed) in double, where z holds
+// the double-float solve in the triangular solves' order (z_nat = z forward; z_nat[perm[k]]
+// = z[k] transposed): the residual of one refinement step against the double S.
+__global__ void k_lu_resid(int M, const double *__restrict__ S, const int *__restrict__ perm,
+                           const float2 *__restrict__ z, const double *__restrict__ f,
+                           double *__restrict__ r, int trans, const int *gate)
+{
+    if (gate_shut(gate)) return;
+    if (!trans) {  // a warp per row
+        const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+        if (i >= M) return;
+        double acc = 0.0;
+        for (int m = lane; m < M; m += 32) acc = fma(S[(int64_t)i * M + m], (double)z[m].x + (double)z[m].y, acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) r[i] = f[i] - acc;
+    } else {  // a thread per column of S, coalesced over the rows
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= M) return;
+        double acc = 0.0;
+        for (int k = 0; k < M; k++) acc = fma(S[(int64_t)perm[k] * M + i], (double)z[k].x + (double)z[k].y, acc);
+        r[i] = f[i] - acc;
+    }
+}
+
+// y = alpha (z0 + z1), both in the solves' order (see k_lu_scatter)
+__global__ void k_lu_scatter2(int M, const int *__restrict__ perm, const float2 *__restrict__ z0,
+                              const float2 *__restrict__ z1, double alpha, double *__restrict__ y,
+                              int trans, const int *gate)
+{
+    if (gate_shut(gate)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const df64 v = ld(z0[i]) + ld(z1[i]);
+    y[trans ? perm[i] : i] = alpha * ((double)v.hi + (double)v.lo);
+}
+
+}  // namespace
+
+// Scratch of the factorisation (plan time): the panel candidates and the grid barrier.
+size_t lbf_lu_scratch_bytes()
+{
+    return 256 + sizeof(unsigned) * 2 * kLuMaxPanelBlocks + sizeof(int) * 2 * kLuMaxPanelBlocks +
+           sizeof(float2) * 2 * (size_t)kLuMaxPanelBlocks * kLuNb + sizeof(float2) * 2 * kLuNb +
+           sizeof(GridBarrier) + 1024;
+}
+
+int lbf_lu_sync_words(int M) { return 3 + (M + kLuTs - 1) / kLuTs; }
+
+int64_t lbf_lu_dinv_entries(int M) { return 2 * (int64_t)((M + kLuTs - 1) / kLuTs) * kLuTs * kLuTs; }
+
+// S (double, M x M, in pl->Sinv) -> its LU factors in place (double-float), pl->lu_piv,
+// pl->lu_perm; on stream s.  scratch: lbf_lu_scratch_bytes() bytes of device memory.
+int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
+{
+    const int M = pl->M;
+    float2 *A = (float2 *)pl->Sinv;
+    char *p = (char *)scratch;
+    auto take = [&](size_t b) {
+        void *r = p;
+        p += (b + 255) & ~size_t(255);
+        return r;
+    };
+    unsigned *amax = (unsigned *)take(sizeof(unsigned));
+    unsigned *ckey = (unsigned *)take(sizeof(unsigned) * 2 * kLuMaxPanelBlocks);
+    int *crow = (int *)take(sizeof(int) * 2 * kLuMaxPanelBlocks);
+    float2 *cval = (float2 *)take(sizeof(float2) * 2 * (size_t)kLuMaxPanelBlocks * kLuNb);
+    float2 *rjval = (float2 *)take(sizeof(float2) * 2 * kLuNb);
+    GridBarrier *bar = (GridBarrier *)take(sizeof(GridBarrier));
+    int *status = pl->dev_status;
+    LBF_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), s));
+    LBF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+    LBF_CUDA(cudaMemsetAsync(pl->lu_sync, 0, sizeof(unsigned) * lbf_lu_sync_words(M), s));
+    const int64_t n2 = (int64_t)M * M;
+    LBF_CUDA(cudaMemcpyAsync(pl->lu_S, pl->Sinv, sizeof(double) * (size_t)n2, cudaMemcpyDeviceToDevice, s));
+    LBF_LAUNCH(k_lu_convert, (int)std::min<int64_t>(lbf_cdiv(n2, 256), 152 * 16), 256, 0, s, n2,
+               pl->Sinv, amax);
+    LBF_CHECK_LAUNCH();
+    int dev = 0, nsm = 0, coop = 0;
+    LBF_CUDA(cudaGetDevice(&dev));
+    LBF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    LBF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return LBF_ECUDA;
+    const size_t tile_smem = sizeof(float2) * 2 * kLuNb * kLuPad;
+    LBF_CUDA(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmemCap));
+    LBF_CUDA(cudaFuncSetAttribute(k_lu_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+    LBF_CUDA(cudaFuncSetAttribute(k_lu_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+    for (int k0 = 0; k0 < M; k0 += kLuNb) {
+        const int w = std::min(kLuNb, M - k0);
+        const int rows = M - k0;
+        int nblk = std::max(1, std::min(nsm, (rows + 31) / 32));
+        int rpb = (rows + nblk - 1) / nblk;
+        size_t smem = sizeof(float2) * ((size_t)rpb * kLuNb + rpb);
+        if (smem > kLuSmemCap) return LBF_EINVAL;  // M above ~60,000
+        int per_sm = 0;
+        LBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_panel, kLuThreads, smem));
+        if (per_sm < 1) return LBF_ECUDA;
+        nblk = std::min(nblk, std::min(kLuMaxPanelBlocks, per_sm * nsm));
+        rpb = (rows + nblk - 1) / nblk;
+        smem = sizeof(float2) * ((size_t)rpb * kLuNb + rpb);
+        int kk0 = k0, ww = w, rr = rpb;
+        void *args[] = {(void *)&M, &kk0, &ww, &rr, &A, &pl->lu_piv, &amax, &ckey, &crow, &cval,
+                        &rjval, &bar, &status};
+        lbf_prof_mark(LBF_KERNEL_LU_PANEL, 1, s);
+        LBF_CUDA(cudaLaunchCooperativeKernel((const void *)k_lu_panel, dim3(nblk), dim3(kLuThreads), args,
+                                             smem, s));
+        g_lbf_launches.fetch_add(1, std::memory_order_relaxed);
+        lbf_prof_mark(LBF_KERNEL_LU_PANEL, 0, s);
+        LBF_LAUNCH_P(LBF_KERNEL_LU_UPDATE, k_lu_swap, lbf_cdiv(M, 256), 256, 0, s, M, k0, w, A, pl->lu_piv,
+                     status);
+        const int rest = M - k0 - w;
+        if (rest > 0) {
+            const int nt = (rest + kLuTs - 1) / kLuTs;
+            LBF_LAUNCH_P(LBF_KERNEL_LU_UPDATE, k_lu_trsm, nt, kLuThreads, tile_smem, s, M, k0, w, A, status);
+            LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_lu_gemm, dim3(nt, nt), kLuThreads, tile_smem, s, M, k0, w, A,
+                         status);
+        }
+        LBF_CHECK_LAUNCH();
+    }
+    {
+        const int nB = (M + kLuTs - 1) / kLuTs;
+        LBF_CUDA(cudaFuncSetAttribute(k_lu_diaginv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+        LBF_LAUNCH_P(LBF_KERNEL_LU_UPDATE, k_lu_diaginv, nB, kLuThreads, tile_smem, s, M, A, pl->lu_dinv, status);
+        LBF_CHECK_LAUNCH();
+    }
+    const bool sh = (size_t)M * sizeof(int) <= kLuSmemCap;
+    if (sh) LBF_CUDA(cudaFuncSetAttribute(k_lu_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmemCap));
+    LBF_LAUNCH(k_lu_perm, 1, 256, sh ? sizeof(int) * (size_t)M : 0, s, M, pl->lu_piv, pl->lu_perm, sh ? 1 : 0);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+// y = alpha S^-1 f (trans = 0) or y = alpha S^-T f (trans = 1), M-vectors (double),
+// through the factors of lbf_schur_lu_factor.  accurate: one step of iterative
+// refinement against the double S kept by the plan (z = z0 + LU^-1 (f - S z0)), which
+// brings the rounding of the double-float solves (about cond(S) 2^-46) down to that of a
+// double solve; the refinement's FP64 residuals use it, so their preconditioned residual
+// has the same floor as with the double inverse.
+int lbf_schur_lu_apply(lbf_plan *pl, const double *f, double alpha, double *y, int trans,
+                       const int *gate, cudaStream_t s, int accurate)
+{
+    const int M = pl->M;
+    const size_t smem = sizeof(float2) * (kLuTs * kLuPad + 4 * kLuTs);  // < 48 KB
+    const int nB = (M + kLuTs - 1) / kLuTs;
+    const int grid = std::min(nB, 2 * std::max(1, pl->nsm));
+    const float2 *A = (const float2 *)pl->Sinv;
+    auto solve = [&](const double *rhs, float2 *z) -> int {
+        LBF_LAUNCH(k_lu_gather, lbf_cdiv(M, 256), 256, 0, s, M, pl->lu_perm, rhs, z, trans, gate);
+        LBF_LAUNCH_P(LBF_KERNEL_LU_SOLVE, k_lu_trsv, grid, kLuThreads, smem, s, M, trans ? 2 : 0, A,
+                     pl->lu_dinv, z, pl->lu_sync, pl->dev_status, gate);
+        LBF_LAUNCH_P(LBF_KERNEL_LU_SOLVE, k_lu_trsv, grid, kLuThreads, smem, s, M, trans ? 3 : 1, A,
+                     pl->lu_dinv, z, pl->lu_sync, pl->dev_status, gate);
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    };
+    int rc = solve(f, pl->lu_z);
+    if (rc) return rc;
+    if (!accurate) {
+        LBF_LAUNCH(k_lu_scatter, lbf_cdiv(M, 256), 256, 0, s, M, pl->lu_perm, pl->lu_z, alpha, y, trans,
+                   gate);
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    }
+    if (trans) LBF_LAUNCH(k_lu_resid, lbf_cdiv(M, 128), 128, 0, s, M, pl->lu_S, pl->lu_perm, pl->lu_z, f,
+                          pl->lu_r, 1, gate);
+    else LBF_LAUNCH(k_lu_resid, lbf_cdiv((int64_t)M * 32, 256), 256, 0, s, M, pl->lu_S, pl->lu_perm,
+                    pl->lu_z, f, pl->lu_r, 0, gate);
+    LBF_CHECK_LAUNCH();
+    if ((rc = solve(pl->lu_r, pl->lu_z2))) return rc;
+    LBF_LAUNCH(k_lu_scatter2, lbf_cdiv(M, 256), 256, 0, s, M, pl->lu_perm, pl->lu_z, pl->lu_z2, alpha, y,
+               trans, gate);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}

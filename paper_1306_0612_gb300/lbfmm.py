@@ -36,6 +36,9 @@ LBF_OP_FP32 = 16
 LBF_OP_TRANSPOSE = 32
 LBF_PRECISION_FP64 = 0
 LBF_PRECISION_FP32_REFINE = 1
+LBF_SCHUR_AUTO = 0
+LBF_SCHUR_GJ = 1
+LBF_SCHUR_LU = 2
 
 
 class lbf_options(C.Structure):
@@ -43,7 +46,7 @@ class lbf_options(C.Structure):
                 ("leaf_size", C.c_int), ("max_depth", C.c_int), ("matvec", C.c_int),
                 ("border", C.c_int), ("box_capacity", C.c_int64), ("precision", C.c_int),
                 ("p32", C.c_int), ("inner_tol", C.c_double), ("max_refine", C.c_int),
-                ("graphs", C.c_int), ("fmm64", C.c_int)]
+                ("graphs", C.c_int), ("fmm64", C.c_int), ("schur", C.c_int)]
 
 
 class lbf_batch_item(C.Structure):
@@ -435,7 +438,8 @@ def lbf_list_export(plan: Plan, kind: int, stream=None):
 LBF_KERNEL_UP, LBF_KERNEL_DOWN, LBF_KERNEL_LEAF = 0, 1, 2
 LBF_KERNEL_DIRECT, LBF_KERNEL_ARNOLDI, LBF_KERNEL_ESUM = 3, 4, 5
 KERNEL_NAMES = ["up", "down", "leaf", "direct", "arnoldi", "esum", "up32", "down32", "leaf32",
-                "esum32", "plan_geometry", "plan_border", "plan_inverse"]
+                "esum32", "plan_geometry", "plan_border", "plan_inverse", "lu_panel", "lu_update",
+                "lu_gemm", "lu_solve"]
 
 
 def lbf_plan_counts(plan: Plan, stream=None) -> dict:
