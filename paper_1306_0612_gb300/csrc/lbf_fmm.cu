@@ -736,3 +736,22 @@ int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p, c
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
+
+namespace {
+__global__ void k_selftest_rcp(int64_t n, const double *__restrict__ a, double *__restrict__ out,
+                               int variant)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = variant == 0 ? fmm::rcp(a[i]) : fmm::rcp_near(a[i]);
+}
+}  // namespace
+
+extern "C" int lbf_selftest_rcp(int variant, int64_t n, const double *a, double *out,
+                                lbf_stream_t stream)
+{
+    if ((variant != 0 && variant != 1) || n < 0 || (n > 0 && (!a || !out))) return LBF_EINVAL;
+    if (n == 0) return LBF_OK;
+    LBF_LAUNCH(k_selftest_rcp, lbf_cdiv(n, 256), 256, 0, (cudaStream_t)stream, n, a, out, variant);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}

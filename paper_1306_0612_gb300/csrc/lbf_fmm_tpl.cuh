@@ -68,9 +68,34 @@ __device__ __forceinline__ double rcp(double a)
 __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
 __device__ __forceinline__ df64 rcp(df64 a) { return df_rcp(a); }
 
+// 1/a in double for a positive normal a in [2^-126, 2^126] (the near field's squared
+// distances in units of a leaf half-width, the far-field arguments of M2P and P2L), with
+// no instruction on the double pipe but the Newton steps: the float seed is a with its
+// exponent rebiased and its mantissa cut to 20 bits, built with integer operations
+// (relative error < 2^-20), the float reciprocal approximation of that, widened back by
+// integer operations, then two Newton-Raphson steps x <- x + x (1 - a x) (the error
+// squares at each: ~2^-40, then below the rounding of the last step).  On this GPU the
+// double pipe is the bound of every double FMM kernel; a conversion instruction would
+// occupy it like an arithmetic one.
+__device__ __forceinline__ double rcp_near(double a)
+{
+    const int hi = __double2hiint(a);
+    const float af = __int_as_float((hi - (896 << 20)) << 3);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(af));
+    const unsigned yb = __float_as_uint(yf);
+    double x = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+    double e = fma(-a, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-a, x, 1.0);
+    return fma(x, e, x);
+}
+
 template <typename R> __device__ __forceinline__ cx<R> crcp(cx<R> a)
 {
-    R d = rcp(a.x * a.x + a.y * a.y);
+    R d;
+    if constexpr (std::is_same<R, double>::value) d = rcp_near(fma(a.x, a.x, a.y * a.y));
+    else d = rcp(a.x * a.x + a.y * a.y);
     return cx<R>{a.x * d, -a.y * d};
 }
 
@@ -807,10 +832,15 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                     // the target itself (the only source at distance 0) adds nothing: with a
                     // tiny shift of |dz|^2 its term is 0 x (finite), so the forward and
                     // transposed rows need no test; the derivative rows (|dz|^-4) test
-                    const R d2 = fm(dr, dr, di * di);
                     R ir2;
-                    if constexpr (MODE == kLeafDeriv) ir2 = positive(d2) ? rcp(d2) : R(0.0f);
-                    else ir2 = rcp(d2 + tiny_sq<R>());
+                    if constexpr (MODE == kLeafDeriv) {
+                        const R d2 = fm(dr, dr, di * di);
+                        ir2 = positive(d2) ? rcp(d2) : R(0.0f);
+                    } else if constexpr (std::is_same<R, double>::value) {
+                        ir2 = rcp_near(fma(dr, dr, fma(di, di, tiny_sq<R>())));
+                    } else {
+                        ir2 = rcp(fm(dr, dr, di * di) + tiny_sq<R>());
+                    }
                     if constexpr (MODE == kLeafForward) {
                         accI = fm(fm(qq.y, dr, -qq.x * di), ir2, accI);
                     } else if constexpr (MODE == kLeafTranspose) {

@@ -112,6 +112,7 @@ def load():
             "lbf_gradient_nodes": (C.c_int, [_P, _P, _P, _P, i64, _P, _P, _P, _P]),
             "lbf_gradient_data": (C.c_int, [_P, _P, _P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
+            "lbf_selftest_rcp": (C.c_int, [C.c_int, i64, _P, _P, _P]),
             "lbf_launch_count": (i64, []),
         }
         for name, (res, args) in sig.items():
@@ -129,7 +130,7 @@ def exported_symbols():
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
             "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
-            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status",
+            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp",
             "lbf_launch_count"]
 
 
@@ -498,6 +499,12 @@ def lbf_evaluate_noalloc(xi: torch.Tensor, weight: torch.Tensor, sigma: torch.Te
         _dptr(sigma, N if checked else None, "sigma"), M, _dptr(a, M, "a"),
         _dptr(centres, 3 * M, "centres"), T, _dptr(targets, 3 * T, "targets"),
         _dptr(u, T, "u"), _stream(stream)), "lbf_evaluate_noalloc")
+
+
+def lbf_selftest_rcp(variant: int, a: torch.Tensor, out: torch.Tensor, stream=None):
+    n = a.numel()
+    _check(load().lbf_selftest_rcp(int(variant), n, _dptr(a, n, "a"), _dptr(out, n, "out"),
+                                   _stream(stream)), "lbf_selftest_rcp")
 
 
 def lbf_sync_status(plan: Plan, stream=None) -> int:
