@@ -93,6 +93,8 @@ typedef struct lbf_options {
                              GPU issues float 64 times faster than double) */
     int schur;            /* how the preconditioner applies S^-1 (S = D - F E, Sec. 5, Eq.
                              matrix_eqns_c): LBF_SCHUR_AUTO, LBF_SCHUR_GJ or LBF_SCHUR_LU */
+    int p2p_warps;        /* near-field tile: warps (leaves) per block of the leaf pass,
+                             1..8 (0: 4) */
 } lbf_options;
 
 /* schur: LBF_SCHUR_GJ forms S^-1 by Gauss-Jordan elimination in double (2 M^3 flops on
@@ -274,6 +276,26 @@ typedef struct lbf_batch_item {
 } lbf_batch_item;
 int lbf_batch_run(int nitems, lbf_batch_item *items, const lbf_options *opt, int nworkers);
 
+/* Autotuner of the FMM's free parameters for one geometry (the paper fixes neither
+ * the expansion order nor the leaf size; Sec. 6 gives only the FMM tolerance):
+ * timed trials of the density operator (I + 2K) sigma on a seeded density, against a
+ * reference at order 44.  For each leaf size in {32, 48, 64} the order p rises from 16
+ * until the relative l2 error is at most target / 4; the fastest such (p, leaf) is
+ * kept, then the near-field tile (p2p_warps 2, 4, 8).  Trial plans are built without
+ * the border, one at a time, in the caller's workspace.
+ *   geometry and pole_rotation: as lbf_plan_create (device arrays; rotation host/NULL)
+ *   base: options to start from (precision, fmm64, ...: kept in *best)
+ *   target: the largest acceptable rel-l2 error of the operator
+ *   workspace, bytes: device memory; with workspace = NULL only *bytes_needed is set
+ *   best: host out, base with p, leaf_size and p2p_warps chosen
+ *   table, table_len: host out (nullable), every trial as JSON text
+ * Synchronous.  LBF_NOCONV (soft) when no trial met the target (best = base). */
+int lbf_autotune(int M, const int64_t *island_ptr, const double *x, const double *dx,
+                 const double *d2x, const double *centres, const double *pole_rotation,
+                 const lbf_options *base, double target, void *workspace, size_t bytes,
+                 size_t *bytes_needed, lbf_options *best, char *table, size_t table_len,
+                 lbf_stream_t stream);
+
 /* Work of the plan's last lbf_gmres_solve (host out): stats[0] Arnoldi steps,
  * [1] FP64 operator applications, [2] FP32 operator applications,
  * [3] refinement steps (0 for LBF_PRECISION_FP64). */
@@ -332,7 +354,8 @@ int lbf_border_counts(const lbf_plan *plan, int64_t counts[6], lbf_stream_t stre
 #define LBF_KERNEL_LEAF 2   /* L2P + M2P + P2P + combine */
 #define LBF_KERNEL_DIRECT 3
 #define LBF_KERNEL_ARNOLDI 4
-#define LBF_KERNEL_ESUM 5   /* multiplier potential E y at the nodes: L2P + direct centres */
+#define LBF_KERNEL_ESUM 5   /* multiplier potential E y: P2L, L2L and L2P + direct centres
+                               (float: the evaluation at the nodes only) */
 #define LBF_KERNEL_UP32 6   /* the three FMM passes of the float operator */
 #define LBF_KERNEL_DOWN32 7
 #define LBF_KERNEL_LEAF32 8

@@ -38,7 +38,8 @@ bool valid(const lbf_options &o)
            (o.precision == LBF_PRECISION_FP64 || o.precision == LBF_PRECISION_FP32_REFINE) &&
            o.p32 >= 4 && o.p32 + 1 <= 32 && o.inner_tol > 0 && o.inner_tol < 1 &&
            o.max_refine >= 1 && o.graphs >= -1 && o.graphs <= 1 && (o.fmm64 == 0 || o.fmm64 == 1) &&
-           o.schur >= LBF_SCHUR_AUTO && o.schur <= LBF_SCHUR_LU;
+           o.schur >= LBF_SCHUR_AUTO && o.schur <= LBF_SCHUR_LU && o.p2p_warps >= 0 &&
+           o.p2p_warps <= 8;
 }
 
 // host tables of the translation operators (scaled expansions, see lbf_fmm.cu)
@@ -178,6 +179,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     if (o.border) {
         Border &B = pl->bd;
         B.P = 36;   // (sqrt2/3)^36 / 36 ~ 1e-13 worst-case truncation of P2L + L2P
+        B.Pe = 32;  // the accurate E y: (sqrt2/3)^32 / 32 ~ 1e-12, one coefficient per lane
         B.P32 = 16;
         B.pair_cap = (int64_t)M * 27 * (o.max_depth + 1);
         B.leaf_of = A.get<int32_t>(N);
@@ -316,6 +318,7 @@ int lbf_default_options(lbf_options *o)
     o->graphs = -1;
     o->fmm64 = 1;
     o->schur = LBF_SCHUR_AUTO;
+    o->p2p_warps = 0;
     return LBF_OK;
 }
 

@@ -524,10 +524,11 @@ __global__ void k_mp_p2l(int64_t nbox, int P, int M, const int32_t *__restrict__
             pw = zmul(pw, tau);
         }
         __syncwarp();
+        const int nin = min(32, ptr[b + 1] - base);  // the chunk's centres (often a few)
         for (int l = lane; l < P; l += 32) {
             if (l == 0) continue;
             cz<R> s{0, 0};
-            for (int k = 0; k < 32; k++) { s.x += T[l * 32 + k].x; s.y += T[l * 32 + k].y; }
+            for (int k = 0; k < nin; k++) { s.x += T[l * 32 + k].x; s.y += T[l * 32 + k].y; }
             if (l < 32) { a0.x += s.x; a0.y += s.y; }
             else { a1.x += s.x; a1.y += s.y; }
         }
@@ -1024,15 +1025,15 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
                      B.partial);
     } else if (pl->udf) {
         // the accurate operator in double-float (P2L terms formed in double)
-        int P = B.P;
+        int P = B.Pe;
         size_t smem = sizeof(cz<df64>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH(k_mp_p2l<df64>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<df64>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
                    (cz<df64> *)B.loc, B.sums, gate);
         if (pl->pull) {  // the L2L chain in one launch
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH(k_mp_chain<df64>, grid, 32 * cw, l2l_smem<df64>(P, cw), s, T.nbox, P, T.parent,
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<df64>, grid, 32 * cw, l2l_smem<df64>(P, cw), s, T.nbox, P, T.parent,
                        T.level, T.ix, T.iy, (const df64 *)pl->tabdf_binom,
                        (const cz<df64> *)pl->tabdf_dshift, (cz<df64> *)B.loc, pl->pull,
                        pl->dev_status, gate);
@@ -1055,15 +1056,15 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
                      out, gate, T.parent, (const float2 *)nullptr, 0, (const cz<df64> *)pl->udf,
                      B.nodebase, B.partial);
     } else {
-        int P = B.P;
+        int P = B.Pe;
         size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH(k_mp_p2l<double>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
-                   B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
-                   (cz<double> *)B.loc, B.sums, gate);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<double>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox,
+                     P, M, B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
+                     (cz<double> *)B.loc, B.sums, gate);
         if (pl->pull) {  // the L2L chain in one launch
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH(k_mp_chain<double>, grid, 32 * cw, l2l_smem<double>(P, cw), s, T.nbox, P,
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<double>, grid, 32 * cw, l2l_smem<double>(P, cw), s, T.nbox, P,
                        T.parent, T.level, T.ix, T.iy, pl->tab_binom,
                        (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, pl->pull,
                        pl->dev_status, gate);
@@ -1125,7 +1126,7 @@ extern "C" int lbf_border_counts(const lbf_plan *pl, int64_t counts[6], lbf_stre
     counts[1] = (int64_t)h[0];
     counts[2] = B.nglob_h;
     counts[3] = (int64_t)h[1];
-    counts[4] = B.P;
+    counts[4] = B.Pe;
     counts[5] = B.P32;
     return LBF_OK;
 }

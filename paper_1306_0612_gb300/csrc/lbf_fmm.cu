@@ -287,8 +287,9 @@ constexpr double kEvalSep = 4.25;  // >= 3 sqrt(2): |(xi - c)/(t - c)| <= 1/3 in
 constexpr int kEvalFront = 2048;   // frontier capacity per warp (per level)
 constexpr int kEvalWarps = 4;
 
+template <typename R>
 __global__ void k_evaluate_tree(int64_t N, int M, const double2 *__restrict__ xi,
-                                const double2 *__restrict__ q, const cx<df64> *__restrict__ mp,
+                                const double2 *__restrict__ q, const cx<R> *__restrict__ mp,
                                 int P, const int32_t *__restrict__ level,
                                 const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
                                 const int32_t *__restrict__ child0,
@@ -331,10 +332,10 @@ __global__ void k_evaluate_tree(int64_t N, int M, const double2 *__restrict__ xi
                     const double dx = zx - cxd, dy = zy - cyd;
                     if (b != 0 && dx * dx + dy * dy >= kEvalSep * kEvalSep * r * r) {
                         // M2P: Phi(t) = (1/r) sum_k a_k rho^(k+1), rho = r/(t - c); q/(xi - t) = -Phi
-                        const double id = 1.0 / (dx * dx + dy * dy);
-                        const cx<df64> rho{df64(r * dx * id), df64(-r * dy * id)};
-                        const cx<df64> *ak = mp + (int64_t)b * P;
-                        cx<df64> ps = ak[P - 1];
+                        const double id = fmm::rcp_near(dx * dx + dy * dy);
+                        const cx<R> rho{R(r * dx * id), R(-r * dy * id)};
+                        const cx<R> *ak = mp + (int64_t)b * P;
+                        cx<R> ps = ak[P - 1];
                         for (int k = P - 2; k >= 0; k--) ps = fmm::cfma(ps, rho, ak[k]);
                         ps = fmm::cmul(ps, rho);
                         const double ir = 1.0 / r;
@@ -344,7 +345,8 @@ __global__ void k_evaluate_tree(int64_t N, int M, const double2 *__restrict__ xi
                         for (int j = bg[b]; j < en[b]; j++) {
                             const double dr = xi[j].x - zx, di = xi[j].y - zy;
                             const double2 qq = q[j];
-                            const double id = 1.0 / (dr * dr + di * di);
+                            const double d2 = fma(dr, dr, di * di);
+                            const double id = d2 > 0x1p-120 ? fmm::rcp_near(d2) : 1.0 / d2;
                             accr += (qq.x * dr + qq.y * di) * id;
                             acci += (qq.y * dr - qq.x * di) * id;
                         }
@@ -541,8 +543,9 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
             }
         }
     }
-    LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, fmm::kLeafWarps),
-                 32 * fmm::kLeafWarps, 0, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
+    const int lw = pl->opt.p2p_warps > 0 ? pl->opt.p2p_warps : fmm::kLeafWarps;
+    LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, lw), 32 * lw,
+                 sizeof(fmm::LeafSrc<R>) * fmm::kSrcChunk * lw, s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
                  sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf, walk ? 0 : 1,
                  split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
@@ -566,9 +569,22 @@ int lbf_fmm_init_attrs()
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_up<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
-    LBF_CUDA(cudaFuncSetAttribute(k_evaluate_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LBF_CUDA(cudaFuncSetAttribute(k_evaluate_tree<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(int32_t) * 2 * kEvalFront * kEvalWarps)));
+    LBF_CUDA(cudaFuncSetAttribute(k_evaluate_tree<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(int32_t) * 2 * kEvalFront * kEvalWarps)));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
+    // the leaf pass: up to 8 warps of staged near-field sources
+    const int leaf_cap = (int)(8 * fmm::kSrcChunk * sizeof(fmm::LeafSrc<double>));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<double, fmm::kLeafForward>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<double, fmm::kLeafTranspose>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<double, fmm::kLeafDeriv>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<df64, fmm::kLeafForward>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<df64, fmm::kLeafTranspose>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<df64, fmm::kLeafDeriv>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafForward>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafTranspose>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
+    LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<float, fmm::kLeafDeriv>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
     return LBF_OK;
 }
 
@@ -711,9 +727,29 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
                    (const cx<df64> *)pl->tabdf_dshift, pl->xi, (const cx<df64> *)pl->udf,
                    (const cx<df64> *)pl->qdf, (cx<df64> *)pl->mpole, pl->upcnt,
                    (const int *)nullptr);
-        LBF_LAUNCH(k_evaluate_tree, lbf_cdiv(T, kEvalWarps), 32 * kEvalWarps,
+        LBF_LAUNCH(k_evaluate_tree<df64>, lbf_cdiv(T, kEvalWarps), 32 * kEvalWarps,
                    sizeof(int32_t) * 2 * kEvalFront * kEvalWarps, s, pl->N, pl->M, pl->xi, pl->q,
                    (const cx<df64> *)pl->mpole, P, Tr.level, Tr.ix, Tr.iy, Tr.child0, Tr.nchild,
+                   Tr.begin, Tr.end, g, pl->bsig, a, pl->centres, T, t, pl->has_rot, pl->rot_d, u,
+                   pl->dev_status);
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    }
+    if (pl->opt.matvec == LBF_MATVEC_FMM && T > 0) {
+        // native double: double charges and multipoles, the same tree walk
+        int rc = prep(pl, sigma_sorted, Arith::F64, true, nullptr, s);
+        if (rc) return rc;
+        Tree &Tr = pl->tree;
+        BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L)};
+        const int P = pl->P, wpb = 2;
+        LBF_LAUNCH(fmm::k_up<double>, lbf_cdiv(Tr.nleaf, wpb), 32 * wpb, up_smem<double>(P, wpb), s,
+                   Tr.nleaf, Tr.leaves, Tr.level, Tr.ix, Tr.iy, Tr.begin, Tr.end, Tr.parent,
+                   Tr.child0, Tr.nchild, g, P, pl->tab_binom, (const cx<double> *)pl->tab_dshift,
+                   pl->xi, (const cx<double> *)nullptr, (const cx<double> *)pl->q,
+                   (cx<double> *)pl->mpole, pl->upcnt, (const int *)nullptr);
+        LBF_LAUNCH(k_evaluate_tree<double>, lbf_cdiv(T, kEvalWarps), 32 * kEvalWarps,
+                   sizeof(int32_t) * 2 * kEvalFront * kEvalWarps, s, pl->N, pl->M, pl->xi, pl->q,
+                   (const cx<double> *)pl->mpole, P, Tr.level, Tr.ix, Tr.iy, Tr.child0, Tr.nchild,
                    Tr.begin, Tr.end, g, pl->bsig, a, pl->centres, T, t, pl->has_rot, pl->rot_d, u,
                    pl->dev_status);
         LBF_CHECK_LAUNCH();

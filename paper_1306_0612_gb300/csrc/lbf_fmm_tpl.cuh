@@ -659,7 +659,7 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
     }
 }
 
-constexpr int kLeafWarps = 4;
+constexpr int kLeafWarps = 4;  // default warps per block of the leaf kernel
 constexpr int kSrcChunk = 256;
 
 template <typename R> struct LeafSrc {
@@ -711,9 +711,12 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
 {
     if (gate_closed(gate)) return;
     constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
-    __shared__ LeafSrc<R> ss[kLeafWarps][kSrcChunk];  // (position in units of r, charge)
+    // per warp, kSrcChunk staged sources (position in units of r, charge); the warps per
+    // block (the near-field tile) is a launch parameter
+    extern __shared__ __align__(16) unsigned char leaf_sm[];
+    LeafSrc<R>(*ss)[kSrcChunk] = (LeafSrc<R>(*)[kSrcChunk])leaf_sm;
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t t = blockIdx.x * (int64_t)kLeafWarps + wid;
+    int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
     if (t >= nleaf) return;
     const int b = leaves[t];
     const int lt = level[b], tx = ix[b], ty = iy[b];

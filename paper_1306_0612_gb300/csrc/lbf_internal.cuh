@@ -84,7 +84,9 @@ struct Tree {
 // Multiplier potential E y on the node quadtree, Schur complement from island
 // moments (lbf_border.cu).
 struct Border {
-    int P = 0, P32 = 0;              // expansion terms (double, float)
+    int P = 0, P32 = 0;              // expansion terms (double, float) of the island moments,
+                                     // the transposed and derivative potentials, the float E y
+    int Pe = 0;                      // expansion terms of the accurate E y (P2L, L2L, L2P)
     int64_t pair_cap = 0, n_p2l = 0, n_near = 0;
     // direct centres in chunks of 32 per leaf, a warp each: chunk -> (leaf, chunk index),
     // per node the first of its partial sums (one per chunk of its leaf)

@@ -46,7 +46,8 @@ class lbf_options(C.Structure):
                 ("leaf_size", C.c_int), ("max_depth", C.c_int), ("matvec", C.c_int),
                 ("border", C.c_int), ("box_capacity", C.c_int64), ("precision", C.c_int),
                 ("p32", C.c_int), ("inner_tol", C.c_double), ("max_refine", C.c_int),
-                ("graphs", C.c_int), ("fmm64", C.c_int), ("schur", C.c_int)]
+                ("graphs", C.c_int), ("fmm64", C.c_int), ("schur", C.c_int),
+                ("p2p_warps", C.c_int)]
 
 
 class lbf_batch_item(C.Structure):
@@ -113,6 +114,9 @@ def load():
             "lbf_gradient_data": (C.c_int, [_P, _P, _P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
             "lbf_selftest_rcp": (C.c_int, [C.c_int, i64, _P, _P, _P]),
+            "lbf_autotune": (C.c_int, [C.c_int, _P, _P, _P, _P, _P, _P, C.POINTER(lbf_options),
+                                       C.c_double, _P, C.c_size_t, C.POINTER(C.c_size_t),
+                                       C.POINTER(lbf_options), C.c_char_p, C.c_size_t, _P]),
             "lbf_launch_count": (i64, []),
         }
         for name, (res, args) in sig.items():
@@ -130,7 +134,7 @@ def exported_symbols():
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
             "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
-            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp",
+            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp", "lbf_autotune",
             "lbf_launch_count"]
 
 
@@ -499,6 +503,34 @@ def lbf_evaluate_noalloc(xi: torch.Tensor, weight: torch.Tensor, sigma: torch.Te
         _dptr(sigma, N if checked else None, "sigma"), M, _dptr(a, M, "a"),
         _dptr(centres, 3 * M, "centres"), T, _dptr(targets, 3 * T, "targets"),
         _dptr(u, T, "u"), _stream(stream)), "lbf_evaluate_noalloc")
+
+
+def lbf_autotune(island_ptr, x, dx, d2x, centres, target: float, opt=None, pole_rotation=None,
+                 stream=None):
+    """(options with p, leaf_size and p2p_warps chosen for this geometry, trial table)
+    from the library's timed trials (synchronous; the workspace is a torch tensor)."""
+    import json
+
+    lib = load()
+    opt = opt or lbf_default_options()
+    ptr = np.ascontiguousarray(island_ptr, dtype=np.int64)
+    M, N = len(ptr) - 1, int(ptr[-1])
+    rot = None if pole_rotation is None else np.ascontiguousarray(pole_rotation, dtype=np.float64)
+    need = C.c_size_t(0)
+    best = lbf_options()
+    _check(lib.lbf_autotune(M, ptr.ctypes.data_as(_P), None, None, None, None, None, C.byref(opt),
+                            float(target), None, 0, C.byref(need), C.byref(best), None, 0,
+                            _stream(stream)), "lbf_autotune")
+    ws = torch.empty(int(need.value), dtype=torch.uint8, device=x.device)
+    buf = C.create_string_buffer(1 << 16)
+    rc = lib.lbf_autotune(M, ptr.ctypes.data_as(_P), _dptr(x, 3 * N, "x"), _dptr(dx, 3 * N, "dx"),
+                          _dptr(d2x, 3 * N, "d2x"), _dptr(centres, 3 * M, "centres"),
+                          None if rot is None else rot.ctypes.data_as(_P), C.byref(opt),
+                          float(target), C.c_void_p(ws.data_ptr()), int(need.value), C.byref(need),
+                          C.byref(best), buf, len(buf), _stream(stream))
+    _check(rc, "lbf_autotune")
+    del ws
+    return best, json.loads(buf.value.decode())
 
 
 def lbf_selftest_rcp(variant: int, a: torch.Tensor, out: torch.Tensor, stream=None):
