@@ -409,6 +409,23 @@ int lbf_evaluate_noalloc(int64_t N, const double *xi, const double *weight, cons
  * a, out: n doubles (device).  Asynchronous. */
 int lbf_selftest_rcp(int variant, int64_t n, const double *a, double *out, lbf_stream_t stream);
 
+/* Failure injection, for tests of the bounded device waits (every wait polls a bounded
+ * number of times, then records LBF_ETIMEOUT in the plan's status word and lets its
+ * kernel finish, so the context stays usable):
+ *   LBF_INJECT_CHAIN (plan given): the plan's waits give up after `polls` polls, and the
+ *     next accurate operator application's one-launch L2L chain (the downward pass)
+ *     skips the boxes of levels 0-2 in its second phase, so the parent waits of their
+ *     children run out; lbf_sync_status then returns LBF_ETIMEOUT;
+ *   LBF_INJECT_BARRIER (plan NULL): the next lbf_plan_create on this thread gives its
+ *     waits `polls` polls and starts the grid barrier of the Schur complement's inverse
+ *     (or factorisation) already past its count, so it never opens; that creation
+ *     returns LBF_ETIMEOUT.
+ * Synchronous.  lbf_debug_clear resets a plan's status word and poll limit. */
+#define LBF_INJECT_CHAIN 1
+#define LBF_INJECT_BARRIER 2
+int lbf_debug_inject(lbf_plan *plan, int what, unsigned polls, lbf_stream_t stream);
+int lbf_debug_clear(lbf_plan *plan, lbf_stream_t stream);
+
 /* Wait for the stream and return the first device-side error recorded by
  * this plan's kernels (LBF_OK if none).  Synchronous. */
 int lbf_sync_status(lbf_plan *plan, lbf_stream_t stream);

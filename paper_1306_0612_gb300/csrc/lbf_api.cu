@@ -297,6 +297,17 @@ Temps temps(lbf_plan *pl, char *region, int64_t N, int M, int64_t cap)
 }
 }  // namespace
 
+LbfInject &lbf_inject_state()
+{
+    static thread_local LbfInject st;
+    return st;
+}
+
+void lbf_inject_barrier(unsigned *count, cudaStream_t s)
+{
+    if (lbf_inject_state().barrier) cudaMemsetAsync(count, 0xff, sizeof(unsigned), s);
+}
+
 extern "C" {
 
 int lbf_default_options(lbf_options *o)
@@ -465,6 +476,11 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
     if (pl->pull) CK(cudaMemsetAsync(pl->pull, 0, sizeof(uint32_t) * (2 * cap + 4), s));
     CK(cudaMemcpyAsync(pl->tab_tpow, tpow.data(), sizeof(double2) * tpow.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(pl->dev_status, 0, 2 * sizeof(int), s));
+    if (lbf_inject_state().barrier) {  // a test's injection: this plan's poll limit
+        const int lim = (int)lbf_inject_state().polls;
+        CK(cudaMemcpyAsync(pl->dev_status + 1, &lim, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
     CK(cudaMemsetAsync(pl->red_count, 0, 4 * sizeof(unsigned), s));
     CK(cudaMemsetAsync(pl->bsig, 0, 4 * sizeof(double), s));
     // plan-creation temporaries overlay the region of the GMRES basis
@@ -511,8 +527,10 @@ int lbf_plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const dou
                     const double *pole_rotation, const lbf_options *opt, void *workspace,
                     size_t bytes, int64_t *box_needed, lbf_stream_t stream)
 {
-    return plan_create(plan, M, island_ptr, x, dx, d2x, centres, pole_rotation, 0, opt, workspace,
-                       bytes, box_needed, stream);
+    const int rc = plan_create(plan, M, island_ptr, x, dx, d2x, centres, pole_rotation, 0, opt,
+                               workspace, bytes, box_needed, stream);
+    lbf_inject_state() = LbfInject{};  // a pending injection applies to one plan creation
+    return rc;
 }
 
 int lbf_plan_create_planar(lbf_plan **plan, int M, const int64_t *island_ptr, const double *xi,
@@ -520,8 +538,10 @@ int lbf_plan_create_planar(lbf_plan **plan, int M, const int64_t *island_ptr, co
                            const lbf_options *opt, void *workspace, size_t bytes,
                            int64_t *box_needed, lbf_stream_t stream)
 {
-    return plan_create(plan, M, island_ptr, xi, dxi, d2xi, centres, nullptr, 1, opt, workspace,
-                       bytes, box_needed, stream);
+    const int rc = plan_create(plan, M, island_ptr, xi, dxi, d2xi, centres, nullptr, 1, opt,
+                               workspace, bytes, box_needed, stream);
+    lbf_inject_state() = LbfInject{};
+    return rc;
 }
 
 int lbf_plan_destroy(lbf_plan *pl)
@@ -658,5 +678,36 @@ int lbf_sync_status(lbf_plan *pl, lbf_stream_t stream)
 }
 
 int64_t lbf_launch_count(void) { return g_lbf_launches.load(); }
+
+int lbf_debug_inject(lbf_plan *pl, int what, unsigned polls, lbf_stream_t stream)
+{
+    if (polls == 0 || polls > (1u << 30)) return LBF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (what == LBF_INJECT_BARRIER) {
+        if (pl) return LBF_EINVAL;
+        lbf_inject_state() = LbfInject{1, polls};
+        return LBF_OK;
+    }
+    if (what != LBF_INJECT_CHAIN || !pl) return LBF_EINVAL;
+    if (!pl->pull || pl->opt.matvec != LBF_MATVEC_FMM || pl->tree.nlev <= 3) return LBF_ENOTBUILT;
+    // the poll limit, and the second phase of the next chain starting at the first box of
+    // level 3: levels 0..2 are never marked done in that epoch, so their children's
+    // parent waits run out; the chain's last warp resets the counters as always
+    const int lim = (int)polls;
+    const unsigned first = (unsigned)pl->tree.lev_start[3];
+    LBF_CUDA(cudaMemcpyAsync(pl->dev_status + 1, &lim, sizeof(int), cudaMemcpyHostToDevice, s));
+    LBF_CUDA(cudaMemcpyAsync(pl->pull + 3, &first, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+    LBF_CUDA(cudaStreamSynchronize(s));
+    return LBF_OK;
+}
+
+int lbf_debug_clear(lbf_plan *pl, lbf_stream_t stream)
+{
+    if (!pl) return LBF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    LBF_CUDA(cudaMemsetAsync(pl->dev_status, 0, 2 * sizeof(int), s));
+    LBF_CUDA(cudaStreamSynchronize(s));
+    return LBF_OK;
+}
 
 }  // extern "C"

@@ -760,6 +760,7 @@ int lbf_border_start(lbf_plan *pl, cudaStream_t s0, const double2 *xi_o, double 
     unsigned *done = (unsigned *)(perm + M);                     // 1
     GridBarrier *bar = (GridBarrier *)(done + 2);
     LBF_CUDA(cudaMemsetAsync(done, 0, 2 * sizeof(unsigned) + sizeof(GridBarrier), s));
+    lbf_inject_barrier(&bar->count, s);
     LBF_LAUNCH(k_gj_init, lbf_cdiv(M, 256), 256, 0, s, M, pivrow);
     // round q reads A_q and writes A_(q+1); start so that the result lands in S1
     const int rounds = (M + kGjPanel - 1) / kGjPanel;

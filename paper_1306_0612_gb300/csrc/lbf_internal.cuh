@@ -209,6 +209,18 @@ struct lbf_plan {
     cudaEvent_t fork[2] = {nullptr, nullptr};
 };
 
+// ---- failure injection for tests (lbf_debug_inject) ------------------------------
+// A barrier injection is consumed by the next plan creation on the calling thread:
+// its poll limit goes into the plan's status block, and the grid barrier of the Schur
+// complement's inverse or factorisation starts pre-arrived so that it never opens.
+struct LbfInject {
+    int barrier = 0;
+    unsigned polls = 0;
+};
+LbfInject &lbf_inject_state();  // this thread's pending injection
+// the barrier word of a grid barrier, to pre-arrive it when an injection is pending
+void lbf_inject_barrier(unsigned *count, cudaStream_t s);
+
 // ---- layout ------------------------------------------------------------------
 void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &opt, int64_t box_cap);
 

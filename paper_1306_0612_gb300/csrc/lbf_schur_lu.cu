@@ -28,8 +28,9 @@
 //   k_lu_swap: the panel's interchanges applied to every column outside it;
 //   k_lu_trsm: U12 = L11^-1 A12 (the panel's rows to the right of it);
 //   k_lu_gemm: A22 -= L21 U12 (the trailing matrix, 64 x 64 tiles).
-// A pivot at or below M 2^-50 max|S_ij| reports a singular S (status bit 4); every
-// later kernel of the factorisation then returns at once.
+// A pivot at or below M 2^-50 max|S_ij| reports a singular S (status bit 4), a grid
+// barrier that gave up a time-out; every later kernel of the factorisation then returns
+// at once.
 #include <algorithm>
 
 #include "lbf_df64.cuh"
@@ -53,7 +54,7 @@ constexpr unsigned kFInf = 0x7f800000u;
 
 __device__ __forceinline__ bool lu_failed(const int *status)
 {
-    return (*(const volatile int *)status & 4) != 0;
+    return (*(const volatile int *)status & (4 | LBF_DEV_TIMEOUT)) != 0;
 }
 
 // S (double) -> (hi, lo) floats in the same 8 bytes, and max |S_ij| as a bit key
@@ -601,6 +602,7 @@ int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
     int *status = pl->dev_status;
     LBF_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), s));
     LBF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+    lbf_inject_barrier(&bar->count, s);
     LBF_CUDA(cudaMemsetAsync(pl->lu_sync, 0, sizeof(unsigned) * lbf_lu_sync_words(M), s));
     const int64_t n2 = (int64_t)M * M;
     LBF_CUDA(cudaMemcpyAsync(pl->lu_S, pl->Sinv, sizeof(double) * (size_t)n2, cudaMemcpyDeviceToDevice, s));

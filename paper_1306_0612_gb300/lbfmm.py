@@ -114,6 +114,8 @@ def load():
             "lbf_gradient_data": (C.c_int, [_P, _P, _P, _P]),
             "lbf_sync_status": (C.c_int, [_P, _P]),
             "lbf_selftest_rcp": (C.c_int, [C.c_int, i64, _P, _P, _P]),
+            "lbf_debug_inject": (C.c_int, [_P, C.c_int, C.c_uint, _P]),
+            "lbf_debug_clear": (C.c_int, [_P, _P]),
             "lbf_autotune": (C.c_int, [C.c_int, _P, _P, _P, _P, _P, _P, C.POINTER(lbf_options),
                                        C.c_double, _P, C.c_size_t, C.POINTER(C.c_size_t),
                                        C.POINTER(lbf_options), C.c_char_p, C.c_size_t, _P]),
@@ -134,7 +136,7 @@ def exported_symbols():
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
             "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
-            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp", "lbf_autotune",
+            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp", "lbf_autotune", "lbf_debug_inject", "lbf_debug_clear",
             "lbf_launch_count"]
 
 
@@ -537,6 +539,19 @@ def lbf_selftest_rcp(variant: int, a: torch.Tensor, out: torch.Tensor, stream=No
     n = a.numel()
     _check(load().lbf_selftest_rcp(int(variant), n, _dptr(a, n, "a"), _dptr(out, n, "out"),
                                    _stream(stream)), "lbf_selftest_rcp")
+
+
+LBF_INJECT_CHAIN = 1
+LBF_INJECT_BARRIER = 2
+
+
+def lbf_debug_inject(plan, what: int, polls: int, stream=None):
+    _check(load().lbf_debug_inject(None if plan is None else plan.handle, int(what), int(polls),
+                                   _stream(stream)), "lbf_debug_inject")
+
+
+def lbf_debug_clear(plan: Plan, stream=None):
+    _check(load().lbf_debug_clear(plan.handle, _stream(stream)), "lbf_debug_clear")
 
 
 def lbf_sync_status(plan: Plan, stream=None) -> int:
