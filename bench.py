@@ -663,6 +663,41 @@ def run_extras(args, L, dev, stream):
                          "node positions, 256 islands x 512 nodes (N=131072), FP64, tol 1e-10",
                  "forward_backward_ms": gms}
 
+    # the paper's table shapes on elliptical islands (Sec. 6, Examples 1 and 3): GMRES
+    # iterations, plan ("CPU Prec") and solve time, and the error at 75 points against the
+    # exact data (1/2) sum Re 1/(xi - xi_k), for growing nodes per island
+    def ellipse_row(M, n, precond):
+        g = wl.ellipse_islands(1 if M == 15 else M, M, n)
+        x = t(g.x)
+        data = torch.empty(g.N, dtype=torch.float64, device=dev)
+        L.lbf_dipole_sum(x, t(g.centres[1:]), data)
+        tg = t(wl.targets_off_islands(g, 75, seed=2))
+        ue = torch.empty(75, dtype=torch.float64, device=dev)
+        L.lbf_dipole_sum(tg, t(g.centres[1:]), ue)
+        opt = L.lbf_default_options(tol=1e-11, fmm64=0, precond=precond)
+        t0 = time.perf_counter()
+        plan = L.lbf_plan_create(g.island_ptr, x, t(g.dx), t(g.d2x), t(g.centres), opt=opt)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sig = torch.empty(g.N, dtype=torch.float64, device=dev)
+        a = torch.empty(g.M, dtype=torch.float64, device=dev)
+        rc, its, rr = L.lbf_gmres_solve(plan, data, sig, a)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        u = torch.empty(75, dtype=torch.float64, device=dev)
+        L.lbf_evaluate(plan, sig, a, tg, u)
+        err = float((u - ue).abs().max() / ue.abs().max())
+        return {"N": n, "iterations": its, "status": rc, "plan_ms": 1e3 * (t1 - t0),
+                "solve_ms": 1e3 * (t2 - t1), "error": err}
+
+    ex1 = {"preconditioned": [ellipse_row(15, n, 1) for n in (32, 64, 128, 256, 512)],
+           "unpreconditioned": [ellipse_row(15, n, 0) for n in (32, 64, 128, 256, 512)]}
+    ex3 = {str(M): [ellipse_row(M, n, 1) for n in (128, 256, 512, 1024, 2048)] for M in (98, 200, 407)}
+    out["ellipse_tables"] = {"what": "elliptical islands on a Fibonacci lattice with random axes, "
+                                     "exact data (1/2) sum Re 1/(xi - xi_k), GMRES tol 1e-11, FP64, "
+                                     "error at 75 points",
+                             "example1_M15": ex1, "example3": ex3}
+
     # C4: batched uneven solves against the plain FP64 loop, every 16th instance
     insts = wl.batch_instances(seed=4, count=512, nrhs=16)[::16]
     T4 = 32

@@ -95,6 +95,9 @@ typedef struct lbf_options {
                              matrix_eqns_c): LBF_SCHUR_AUTO, LBF_SCHUR_GJ or LBF_SCHUR_LU */
     int p2p_warps;        /* near-field tile: warps (leaves) per block of the leaf pass,
                              1..8 (0: 4) */
+    int precond;          /* 1: GMRES on P^-1 A (Eq. matrix_eqns_c); 0: on A itself, the
+                             unpreconditioned comparison of Sec. 6, Example 1 (the stopping
+                             test is then on ||[2g; 0] - A x||) */
 } lbf_options;
 
 /* schur: LBF_SCHUR_GJ forms S^-1 by Gauss-Jordan elimination in double (2 M^3 flops on
@@ -197,7 +200,7 @@ int lbf_geometry_out(const lbf_plan *plan, double *xi, double *normal, double *w
 int lbf_apply(lbf_plan *plan, int op, const double *in, double *out, lbf_stream_t stream);
 
 /* Solve [[I+K, E],[F, D]] [sigma; a] = [2 g; 0] with restarted GMRES on the
- * left-preconditioned system (Eq. matrix_eqns_c).  g: N boundary values
+ * left-preconditioned system (Eq. matrix_eqns_c; opt.precond = 0: on the system itself).  g: N boundary values
  * (device); sigma (N), a (M): device out; x0: initial guess [sigma; a] (N+M,
  * device, nullable = zero).  iters, rel_res: host out (nullable): iterations
  * done and the final preconditioned relative residual.  Synchronous.
@@ -312,6 +315,30 @@ int lbf_evaluate(lbf_plan *plan, const double *sigma, const double *a, int64_t T
  * (Sec. 6, Example 2).  t: T x 3, p: S x 3, gamma: S, out: T (device). */
 int lbf_green_sum(int64_t T, const double *t, int64_t S, const double *p, const double *gamma,
                   double *out, lbf_stream_t stream);
+
+/* out_q = (1/2) sum_s Re 1 / (xi(t_q) - xi(p_s)), xi the stereographic image (Sec. 3):
+ * the exact solution of Sec. 6, Examples 1 and 3 (Eq. exact_bcs), harmonic in the plane
+ * away from the xi(p_s) and hence Laplace-Beltrami harmonic on the sphere.  A source at the
+ * north pole (xi = infinity) adds nothing.  t: T x 3, p: S x 3, out: T (device), in the
+ * frame whose north pole is the projection pole. */
+int lbf_dipole_sum(int64_t T, const double *t, int64_t S, const double *p, double *out,
+                   lbf_stream_t stream);
+
+/* Point vortices in the ocean (Sec. 6, Example 2): the stream function
+ * psi = psi* + sum_s gamma_s G(., v_s) with psi = 0 on every curve, where the regular
+ * part psi* solves the Dirichlet problem with data -sum_s gamma_s G(x, v_s) on the curves
+ * (composed in the library: that data from the plan's nodes, lbf_gmres_solve, then
+ * lbf_evaluate plus the vortices' own term at the targets).
+ *   vortices : S x 3 points on the sphere in the ocean (device, caller's frame)
+ *   gamma    : S strengths (device)
+ *   targets  : T x 3 off-curve points (device, caller's frame); u: T (device out)
+ *   sigma, a : N and M (device out): the density and multipliers of psi*; sigma also
+ *              holds the data while the solve reads it
+ *   iters, rel_res : host out (nullable), as lbf_gmres_solve.
+ * Synchronous (the solve is); LBF_NOCONV (soft) when GMRES reached maxit. */
+int lbf_point_vortices(lbf_plan *plan, int64_t S, const double *vortices, const double *gamma,
+                       int64_t T, const double *targets, double *u, double *sigma, double *a,
+                       int *iters, double *rel_res, lbf_stream_t stream);
 
 /* The quadtree of a plan (Sec. 6, Example 3), for inspection and tests
  * (device out, synchronous, all nullable):

@@ -158,6 +158,19 @@ def point_vortices(g, vortices, gamma, targets, A=None) -> np.ndarray:
     return evaluate(g, sigma, a, targets) + green_sum(targets, vortices, gamma)
 
 
+def dipole_data(points, sources) -> np.ndarray:
+    """psi = (1/2) sum_k Re 1/(xi - xi_k) at each point (Sec. 6, Eq. exact_bcs: the exact
+    solution of Examples 1 and 3), xi and xi_k the stereographic images (Sec. 3) of the
+    point and of each source; a source at the north pole (xi_k infinite) adds nothing."""
+    xi = project(points)
+    z = xi[:, 0] + 1j * xi[:, 1]
+    src = _f64(sources)
+    fin = src[:, 2] < 1.0
+    xk = project(src[fin])
+    zk = xk[:, 0] + 1j * xk[:, 1]
+    return 0.5 * np.real(1.0 / (z[:, None] - zk[None, :])).sum(axis=1)
+
+
 def project(x) -> np.ndarray:
     """Stereographic projection xi = (x1 + i x2)/(1 - x3) (Sec. 3), as an N x 2 array."""
     x = _f64(x)

@@ -39,7 +39,7 @@ bool valid(const lbf_options &o)
            o.p32 >= 4 && o.p32 + 1 <= 32 && o.inner_tol > 0 && o.inner_tol < 1 &&
            o.max_refine >= 1 && o.graphs >= -1 && o.graphs <= 1 && (o.fmm64 == 0 || o.fmm64 == 1) &&
            o.schur >= LBF_SCHUR_AUTO && o.schur <= LBF_SCHUR_LU && o.p2p_warps >= 0 &&
-           o.p2p_warps <= 8;
+           o.p2p_warps <= 8 && (o.precond == 0 || o.precond == 1);
 }
 
 // host tables of the translation operators (scaled expansions, see lbf_fmm.cu)
@@ -330,6 +330,7 @@ int lbf_default_options(lbf_options *o)
     o->fmm64 = 1;
     o->schur = LBF_SCHUR_AUTO;
     o->p2p_warps = 0;
+    o->precond = 1;
     return LBF_OK;
 }
 

@@ -774,6 +774,71 @@ int lbf_green_sum_impl(int64_t T, const double *t, int64_t S, const double *p, c
 }
 
 namespace {
+// The Dirichlet data of point vortices in the ocean (Sec. 6, Example 2): the regular part
+// psi* of psi = psi* + sum_s Gamma_s G(., v_s) takes g = -sum_s Gamma_s G(x_j, v_s) on the
+// curves.  x_j comes back from its planar image in the plan's frame,
+// x = (2 Re xi, 2 Im xi, |xi|^2 - 1) / (|xi|^2 + 1), and the vortices are rotated into
+// that frame; g is written in the caller's node order.
+__global__ void k_vortex_data(int64_t N, const double2 *__restrict__ xi,
+                              const int32_t *__restrict__ perm, int64_t S,
+                              const double *__restrict__ v, const double *__restrict__ gam,
+                              int rot_on, const double *__restrict__ rot, double *__restrict__ g)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double2 z = xi[i];
+    const double r2 = z.x * z.x + z.y * z.y, id = 1.0 / (r2 + 1.0);
+    const double x0 = 2.0 * z.x * id, x1 = 2.0 * z.y * id, x2 = (r2 - 1.0) * id;
+    double sum = 0.0;
+    for (int64_t k = 0; k < S; k++) {
+        double p0 = v[3 * k], p1 = v[3 * k + 1], p2 = v[3 * k + 2];
+        if (rot_on) {
+            const double a = rot[0] * p0 + rot[1] * p1 + rot[2] * p2;
+            const double b = rot[3] * p0 + rot[4] * p1 + rot[5] * p2;
+            const double c = rot[6] * p0 + rot[7] * p1 + rot[8] * p2;
+            p0 = a; p1 = b; p2 = c;
+        }
+        const double d0 = x0 - p0, d1 = x1 - p1, d2 = x2 - p2;
+        sum += gam[k] * (1.0 / (4.0 * LBF_PI)) * log(2.0 / (d0 * d0 + d1 * d1 + d2 * d2));
+    }
+    g[perm[i]] = -sum;
+}
+
+// u_t += sum_s Gamma_s G(t, v_s) (the singular part, in the caller's frame)
+__global__ void k_green_add(int64_t T, const double *__restrict__ t, int64_t S,
+                            const double *__restrict__ p, const double *__restrict__ gm,
+                            double *__restrict__ u)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    const double x0 = t[3 * q], x1 = t[3 * q + 1], x2 = t[3 * q + 2];
+    double sum = 0.0;
+    for (int64_t k = 0; k < S; k++) {
+        const double d0 = x0 - p[3 * k], d1 = x1 - p[3 * k + 1], d2 = x2 - p[3 * k + 2];
+        sum += gm[k] * (1.0 / (4.0 * LBF_PI)) * log(2.0 / (d0 * d0 + d1 * d1 + d2 * d2));
+    }
+    u[q] += sum;
+}
+
+// out_q = (1/2) sum_s Re 1/(xi_q - xi_s), xi = (x1 + i x2)/(1 - x3); a source at the pole
+// (1 - x3 <= 0) adds nothing
+__global__ void k_dipole_sum(int64_t T, const double *__restrict__ t, int64_t S,
+                             const double *__restrict__ p, double *__restrict__ out)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    const double w = 1.0 - t[3 * q + 2];
+    const double zx = t[3 * q] / w, zy = t[3 * q + 1] / w;
+    double sum = 0.0;
+    for (int64_t k = 0; k < S; k++) {
+        const double wk = 1.0 - p[3 * k + 2];
+        if (!(wk > 0.0)) continue;
+        const double dx = zx - p[3 * k] / wk, dy = zy - p[3 * k + 1] / wk;
+        sum += dx / (dx * dx + dy * dy);
+    }
+    out[q] = 0.5 * sum;
+}
+
 __global__ void k_selftest_rcp(int64_t n, const double *__restrict__ a, double *__restrict__ out,
                                int variant)
 {
@@ -788,6 +853,40 @@ extern "C" int lbf_selftest_rcp(int variant, int64_t n, const double *a, double 
     if ((variant != 0 && variant != 1) || n < 0 || (n > 0 && (!a || !out))) return LBF_EINVAL;
     if (n == 0) return LBF_OK;
     LBF_LAUNCH(k_selftest_rcp, lbf_cdiv(n, 256), 256, 0, (cudaStream_t)stream, n, a, out, variant);
+    LBF_CHECK_LAUNCH();
+    return LBF_OK;
+}
+
+extern "C" int lbf_point_vortices(lbf_plan *pl, int64_t S, const double *vortices,
+                                  const double *gamma, int64_t T, const double *targets, double *u,
+                                  double *sigma, double *a, int *iters, double *rel_res,
+                                  lbf_stream_t stream)
+{
+    if (!pl || S < 1 || !vortices || !gamma || T < 0 || (T > 0 && (!targets || !u)) || !sigma || !a)
+        return LBF_EINVAL;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the data into sigma (caller order), then the solve reads it before writing sigma
+    LBF_LAUNCH(k_vortex_data, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, pl->xi, pl->perm, S, vortices,
+               gamma, pl->has_rot, pl->rot_d, sigma);
+    LBF_CHECK_LAUNCH();
+    const int rc = lbf_gmres_impl(pl, sigma, sigma, a, nullptr, iters, rel_res, s, 0);
+    if (rc < 0) return rc;
+    if (T > 0) {
+        const int re = lbf_evaluate(pl, sigma, a, T, targets, u, stream);
+        if (re) return re;
+        LBF_LAUNCH(k_green_add, lbf_cdiv(T, 128), 128, 0, s, T, targets, S, vortices, gamma, u);
+        LBF_CHECK_LAUNCH();
+    }
+    return rc;
+}
+
+extern "C" int lbf_dipole_sum(int64_t T, const double *t, int64_t S, const double *p, double *out,
+                              lbf_stream_t stream)
+{
+    if (T < 0 || S < 0 || (T > 0 && (!t || !out)) || (S > 0 && !p)) return LBF_EINVAL;
+    if (T == 0) return LBF_OK;
+    LBF_LAUNCH(k_dipole_sum, lbf_cdiv(T, 128), 128, 0, (cudaStream_t)stream, T, t, S, p, out);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }

@@ -686,6 +686,7 @@ static cudaGraphExec_t step_graph(lbf_plan *pl, int opc, int prec, cudaStream_t 
 {
     const int g = pl->opt.graphs;
     if (g == 0 || (g < 0 && pl->N > (1 << 18)) || s == nullptr || !pl->vstep) return nullptr;
+    if (!(opc & LBF_OP_PRECONDITIONED)) return nullptr;  // the graphs hold the preconditioned step
     const int pi = prec == LBF_PREC_FP32 ? 1 : 0, ti = (opc & LBF_OP_TRANSPOSE) ? 1 : 0;
     if (pl->gexec[pi][ti]) return pl->gexec[pi][ti];
     cudaGraph_t graph = nullptr;
@@ -822,9 +823,19 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
     int64_t N = pl->N, n = pl->n;
     int rc;
     double *b = pl->gb, *x = pl->gx;
-    const int opc = LBF_OP_PRECONDITIONED | (transpose ? LBF_OP_TRANSPOSE : 0);
+    const bool pc = pl->opt.precond != 0;
+    const int opc = (pc ? LBF_OP_PRECONDITIONED : LBF_OP_FULL) | (transpose ? LBF_OP_TRANSPOSE : 0);
     for (auto &v : pl->stats) v = 0;
-    if (transpose) {
+    if (!pc) {
+        // without the preconditioner (the comparison of Sec. 6, Example 1): b = [2 g; 0]
+        // (or r for the adjoint), in sorted order
+        if ((rc = lbf_permute_in(pl, g, b, transpose ? 1 : 0, s))) return rc;
+        if (!transpose) {
+            LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, b);
+            LBF_CUDA(cudaMemsetAsync(b + N, 0, sizeof(double) * pl->M, s));
+            LBF_CHECK_LAUNCH();
+        }
+    } else if (transpose) {
         // b = P^-T r
         if ((rc = lbf_permute_in(pl, g, pl->tin, 1, s))) return rc;
         if ((rc = lbf_precondition_rhs_t(pl, pl->tin, b, s))) return rc;

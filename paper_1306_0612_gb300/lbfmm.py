@@ -47,7 +47,7 @@ class lbf_options(C.Structure):
                 ("border", C.c_int), ("box_capacity", C.c_int64), ("precision", C.c_int),
                 ("p32", C.c_int), ("inner_tol", C.c_double), ("max_refine", C.c_int),
                 ("graphs", C.c_int), ("fmm64", C.c_int), ("schur", C.c_int),
-                ("p2p_warps", C.c_int)]
+                ("p2p_warps", C.c_int), ("precond", C.c_int)]
 
 
 class lbf_batch_item(C.Structure):
@@ -116,6 +116,8 @@ def load():
             "lbf_selftest_rcp": (C.c_int, [C.c_int, i64, _P, _P, _P]),
             "lbf_debug_inject": (C.c_int, [_P, C.c_int, C.c_uint, _P]),
             "lbf_debug_clear": (C.c_int, [_P, _P]),
+            "lbf_point_vortices": (C.c_int, [_P, i64, _P, _P, i64, _P, _P, _P, _P, _P, _P, _P]),
+            "lbf_dipole_sum": (C.c_int, [i64, _P, i64, _P, _P, _P]),
             "lbf_autotune": (C.c_int, [C.c_int, _P, _P, _P, _P, _P, _P, C.POINTER(lbf_options),
                                        C.c_double, _P, C.c_size_t, C.POINTER(C.c_size_t),
                                        C.POINTER(lbf_options), C.c_char_p, C.c_size_t, _P]),
@@ -136,7 +138,7 @@ def exported_symbols():
             "lbf_gmres_solve", "lbf_evaluate", "lbf_green_sum", "lbf_tree_export",
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
             "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
-            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp", "lbf_autotune", "lbf_debug_inject", "lbf_debug_clear",
+            "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp", "lbf_autotune", "lbf_debug_inject", "lbf_debug_clear", "lbf_point_vortices", "lbf_dipole_sum",
             "lbf_launch_count"]
 
 
@@ -404,6 +406,27 @@ def lbf_batch_run(instances, opt=None, nworkers=8):
     for q in todo:
         raise LbfError(LBF_EWORKSPACE, f"lbf_batch_run item {q}")
     return results
+
+
+def lbf_point_vortices(plan: Plan, vortices: torch.Tensor, gamma: torch.Tensor,
+                       targets: torch.Tensor, u: torch.Tensor, sigma: torch.Tensor,
+                       a: torch.Tensor, stream=None):
+    """psi at the targets for point vortices in the ocean with psi = 0 on the curves
+    (Sec. 6, Example 2).  Returns (status, iterations, relative residual)."""
+    S, T = vortices.numel() // 3, targets.numel() // 3
+    it, rr = C.c_int(0), C.c_double(0.0)
+    rc = load().lbf_point_vortices(plan.handle, S, _dptr(vortices, 3 * S, "vortices"),
+                                   _dptr(gamma, S, "gamma"), T, _dptr(targets, 3 * T, "targets"),
+                                   _dptr(u, T, "u"), _dptr(sigma, plan.N, "sigma"),
+                                   _dptr(a, plan.M, "a"), C.byref(it), C.byref(rr), _stream(stream))
+    _check(rc, "lbf_point_vortices")
+    return rc, it.value, rr.value
+
+
+def lbf_dipole_sum(t: torch.Tensor, p: torch.Tensor, out: torch.Tensor, stream=None):
+    T, S = t.numel() // 3, p.numel() // 3
+    _check(load().lbf_dipole_sum(T, _dptr(t, 3 * T, "t"), S, _dptr(p, 3 * S, "p"),
+                                 _dptr(out, T, "out"), _stream(stream)), "lbf_dipole_sum")
 
 
 def lbf_green_sum(t: torch.Tensor, p: torch.Tensor, gamma: torch.Tensor, out: torch.Tensor,

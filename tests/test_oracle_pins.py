@@ -29,7 +29,10 @@ a wrong sign, factor or index, a transposed operand) fails it:
 * the stereographic projection (Sec. 3) at points whose images are known in closed
   form: the south pole, the equator, and a point at colatitude theta;
 * the row-by-row matvec (the oracle's direct O(N^2) product, which the GPU parity
-  tests sample) equals the dense bordered matrix times the vector, on a ragged case.
+  tests sample) equals the dense bordered matrix times the vector, on a ragged case;
+* the exact data of the paper's first and third examples, (1/2) sum Re 1/(xi - xi_k), is
+  Laplace-Beltrami harmonic and has its closed-form value at the south pole, and the
+  bordered solve reproduces it off the curves of an elliptical-island geometry.
 """
 import json
 import os
@@ -477,3 +480,44 @@ def test_interaction_lists_cover_every_pair_once(oracle):
         for w in lst["W"][b]:
             assert b in lst["X"][w]
     assert sum(len(v) for v in lst["V"]) > 0 and sum(len(w) for w in lst["W"]) > 0
+
+
+# ---- the elliptical islands of the first and third examples ------------------------------
+
+def test_dipole_data_is_harmonic_with_known_values(oracle):
+    """(1/2) sum_k Re 1/(xi - xi_k) (Sec. 6, Eq. exact_bcs): Delta_S psi = 0 away from the
+    sources (central differences of the spherical-coordinate operator), and at the south
+    pole (xi = 0) psi = (1/2) sum_k Re(-1/xi_k)."""
+    src = np.array([[0.3, -0.4, 0.5], [-0.6, 0.1, -0.2]])
+    src /= np.linalg.norm(src, axis=1)[:, None]
+
+    def psi(th, ph):
+        x = np.array([[np.cos(ph) * np.sin(th), np.sin(ph) * np.sin(th), np.cos(th)]])
+        return oracle.dipole_data(x, src)[0]
+
+    th, ph, e = 2.2, 0.9, 1e-4
+    f0 = psi(th, ph)
+    d2ph = (psi(th, ph + e) - 2 * f0 + psi(th, ph - e)) / e ** 2
+    fth = lambda t: np.sin(t) * (psi(t + e / 2, ph) - psi(t - e / 2, ph)) / e
+    dth = (fth(th + e / 2) - fth(th - e / 2)) / e
+    assert abs(d2ph / np.sin(th) ** 2 + dth / np.sin(th)) < 1e-5 * abs(f0)
+    xk = (src[:, 0] + 1j * src[:, 1]) / (1 - src[:, 2])
+    sp = oracle.dipole_data(np.array([[0.0, 0.0, -1.0]]), src)[0]
+    assert abs(sp - 0.5 * np.sum(np.real(-1.0 / xk))) < 1e-15 * np.sum(np.abs(1 / xk))
+    # a source at the north pole adds nothing
+    both = np.vstack([src, [[0.0, 0.0, 1.0]]])
+    assert oracle.dipole_data(np.array([[0.5, 0.5, 0.0]]) / np.sqrt(0.5), both)[0] == \
+        oracle.dipole_data(np.array([[0.5, 0.5, 0.0]]) / np.sqrt(0.5), src)[0]
+
+
+def test_ellipse_islands_exact_solution(oracle):
+    """Fifteen elliptical islands (the first example's M): the dense solve reproduces the
+    exact solution off the curves, with zero multipliers (no net source in any island)."""
+    g = wl.ellipse_islands(1, 15, 128)
+    data = oracle.dipole_data(g.x, g.centres[1:])
+    sig, a = oracle.solve(g, data)
+    t = wl.targets_off_islands(g, 75, seed=2)
+    u = oracle.evaluate(g, sig, a, t)
+    ue = oracle.dipole_data(t, g.centres[1:])
+    assert max_rel(u, ue) < 1e-8
+    assert np.max(np.abs(a)) < 1e-9 * np.max(np.abs(sig))

@@ -16,4 +16,6 @@ from .star_caps import (  # noqa: F401
     apply_rotation,
     rotated,
     batch_instances,
+    ellipse_islands,
+    fibonacci_centres,
 )

@@ -45,6 +45,28 @@ class Geometry:
     e1: np.ndarray  # (M, 3) frames (after rotation)
     e2: np.ndarray
     rotation: np.ndarray = field(default_factory=lambda: np.eye(3))
+    # "star": r(t) = r0 (1 + amp cos(kfreq t)); "ellipse": semi-axes (axes[:, 0], axes[:, 1])
+    # with the major axis at angle axes[:, 2] from e1
+    shape: str = "star"
+    axes: np.ndarray | None = None
+
+    def radius(self, k: int, t):
+        """The island's geodesic radius r(t) about its centre."""
+        if self.shape == "ellipse":
+            a, b, ph = self.axes[k]
+            u = np.asarray(t) - ph
+            return a * b / np.sqrt((b * np.cos(u)) ** 2 + (a * np.sin(u)) ** 2)
+        return self.r0[k] * (1.0 + self.amp[k] * np.cos(self.kfreq[k] * np.asarray(t)))
+
+    def rmax(self, k: int) -> float:
+        if self.shape == "ellipse":
+            return float(max(self.axes[k, 0], self.axes[k, 1]))
+        return float(self.r0[k] * (1.0 + self.amp[k]))
+
+    def rmin(self, k: int) -> float:
+        if self.shape == "ellipse":
+            return float(min(self.axes[k, 0], self.axes[k, 1]))
+        return float(self.r0[k] * (1.0 - self.amp[k]))
 
     @property
     def N(self) -> int:
@@ -177,7 +199,8 @@ def rotated(g: Geometry, R: np.ndarray) -> Geometry:
                     dx=apply_rotation(R, g.dx), d2x=apply_rotation(R, g.d2x),
                     centres=apply_rotation(R, g.centres), r0=g.r0.copy(), amp=g.amp.copy(),
                     kfreq=g.kfreq.copy(), e1=apply_rotation(R, g.e1), e2=apply_rotation(R, g.e2),
-                    rotation=R @ g.rotation)
+                    rotation=R @ g.rotation, shape=g.shape,
+                    axes=None if g.axes is None else g.axes.copy())
 
 
 def _point_at(g: Geometry, k: int, rho: float, t: float) -> np.ndarray:
@@ -195,13 +218,13 @@ def pair_sources(g: Geometry, k_plus: int = 0, k_minus: int | None = None, frac:
     """
     if k_minus is None or k_minus == k_plus:
         k = k_plus
-        rmin = g.r0[k] * (1.0 - g.amp[k])
+        rmin = g.rmin(k)
         p = g.centres[k].copy()
         q = _point_at(g, k, frac * rmin, 0.0)
         return np.stack([p, q]), np.array([1.0, -1.0]), np.array([k, k])
     pts = []
     for k in (k_plus, k_minus):
-        rmin = g.r0[k] * (1.0 - g.amp[k])
+        rmin = g.rmin(k)
         pts.append(_point_at(g, k, frac * rmin, 0.0))
     return np.stack(pts), np.array([1.0, -1.0]), np.array([k_plus, k_minus])
 
@@ -215,7 +238,7 @@ def random_pair_sources(g: Geometry, rng: np.random.Generator):
         ks = tuple(int(v) for v in rng.choice(g.M, size=2, replace=False))
     pts = []
     for k in ks:
-        rmin = g.r0[k] * (1.0 - g.amp[k])
+        rmin = g.rmin(k)
         pts.append(_point_at(g, k, rng.uniform(0.1, 0.8) * rmin, rng.uniform(0, TWO_PI)))
     return np.stack(pts), np.array([1.0, -1.0]), np.array(ks)
 
@@ -226,11 +249,11 @@ def _inside_island(g: Geometry, y: np.ndarray) -> np.ndarray:
     for k in range(g.M):
         c, e1, e2 = g.centres[k], g.e1[k], g.e2[k]
         rho = np.arccos(np.clip(y @ c, -1.0, 1.0))
-        near = rho < g.r0[k] * (1.0 + g.amp[k]) + 1e-12
+        near = rho < g.rmax(k) + 1e-12
         if not near.any():
             continue
         t = np.arctan2(y[near] @ e2, y[near] @ e1)
-        r = g.r0[k] * (1.0 + g.amp[k] * np.cos(g.kfreq[k] * t))
+        r = g.radius(k, t)
         inside[np.flatnonzero(near)[rho[near] < r]] = True
     return inside
 
@@ -260,6 +283,81 @@ def targets_off_islands(g: Geometry, T: int, seed: int, clearance: float = 5.0) 
             if len(out) == T:
                 break
     return np.ascontiguousarray(np.array(out))
+
+
+def _ellipse_curve(c, e1, e2, a, b, ph, n):
+    """The curve of geodesic radius r(t) = a b / sqrt(b^2 cos^2 u + a^2 sin^2 u), u = t - ph
+    (an ellipse with semi-axes a, b in geodesic polar coordinates), with its analytic
+    t-derivatives."""
+    t = TWO_PI * np.arange(n) / n
+    u = t - ph
+    D = (b * np.cos(u)) ** 2 + (a * np.sin(u)) ** 2
+    D1 = (a * a - b * b) * np.sin(2.0 * u)
+    D2 = 2.0 * (a * a - b * b) * np.cos(2.0 * u)
+    r = a * b * D ** -0.5
+    rp = -0.5 * a * b * D ** -1.5 * D1
+    rpp = a * b * (0.75 * D ** -2.5 * D1 ** 2 - 0.5 * D ** -1.5 * D2)
+    ct, st = np.cos(t)[:, None], np.sin(t)[:, None]
+    uu = ct * e1 + st * e2
+    vv = -st * e1 + ct * e2
+    cr, sr = np.cos(r)[:, None], np.sin(r)[:, None]
+    rp_, rpp_ = rp[:, None], rpp[:, None]
+    C = c[None, :]
+    x = cr * C + sr * uu
+    dx = -rp_ * sr * C + rp_ * cr * uu + sr * vv
+    d2x = (-rpp_ * sr - rp_ ** 2 * cr) * C + (rpp_ * cr - rp_ ** 2 * sr - sr) * uu + 2.0 * rp_ * cr * vv
+    return x, dx, d2x
+
+
+def fibonacci_centres(M: int) -> np.ndarray:
+    """M points spread regularly over the sphere (a Fibonacci lattice)."""
+    i = np.arange(M) + 0.5
+    z = 1.0 - 2.0 * i / M
+    phi = np.pi * (3.0 - np.sqrt(5.0)) * np.arange(M)
+    rxy = np.sqrt(np.clip(1.0 - z * z, 0.0, None))
+    return np.stack([rxy * np.cos(phi), rxy * np.sin(phi), z], axis=1)
+
+
+def ellipse_islands(seed: int, M: int, nodes, *, pole: str | None = "first") -> Geometry:
+    """M elliptical islands spread regularly over the sphere with random semi-axes and
+    orientations (the shape of the paper's first and third examples, whose exact axes are
+    not given): centres on a Fibonacci lattice, semi-axes a, b ~ U[0.15, 0.38] d and
+    orientation ~ U[0, pi), d the lattice's smallest angular spacing, so that every pair
+    keeps the star-cap family's clearance (angle >= 1.2 (R_i + R_j))."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    centres = fibonacci_centres(M)
+    if M > 1:
+        dd, _ = cKDTree(centres).query(centres, k=2)
+        d = 2.0 * np.arcsin(np.clip(dd[:, 1].min() / 2.0, 0.0, 1.0))
+    else:
+        d = 1.0
+    axes = np.empty((M, 3))
+    for k in range(M):
+        axes[k, 0] = rng.uniform(0.15, 0.38) * d
+        axes[k, 1] = rng.uniform(0.15, 0.38) * d
+        axes[k, 2] = rng.uniform(0.0, np.pi)
+    nodes = np.broadcast_to(np.asarray(nodes, dtype=np.int64), (M,)).copy()
+    ptr = np.zeros(M + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum(nodes)
+    N = int(ptr[-1])
+    x, dx, d2x = np.empty((N, 3)), np.empty((N, 3)), np.empty((N, 3))
+    E1, E2 = np.empty((M, 3)), np.empty((M, 3))
+    for k in range(M):
+        e1, e2 = _frame(centres[k])
+        E1[k], E2[k] = e1, e2
+        a_, b_ = ptr[k], ptr[k + 1]
+        x[a_:b_], dx[a_:b_], d2x[a_:b_] = _ellipse_curve(centres[k], e1, e2, *axes[k], int(nodes[k]))
+    rmax = axes[:, :2].max(axis=1)
+    g = Geometry(M=M, island_ptr=ptr, x=x, dx=dx, d2x=d2x, centres=centres.copy(),
+                 r0=rmax, amp=np.zeros(M), kfreq=np.zeros(M, dtype=np.int64), e1=E1, e2=E2,
+                 shape="ellipse", axes=axes)
+    if pole == "first":
+        g = rotated(g, rotation_to_pole(centres[0]))
+    elif pole is not None:
+        raise ValueError(pole)
+    return g
 
 
 def random_density(N: int, seed: int) -> np.ndarray:
