@@ -79,6 +79,9 @@ def parse():
                     help="skip the autotuner (p, leaf size and near-field tile at their defaults)")
     ap.add_argument("--tune-target", type=float, default=1e-10,
                     help="the autotuner's bound on the operator's rel-l2 error")
+    ap.add_argument("--warps", type=int, default=None, help="near-field tile (warps per block)")
+    ap.add_argument("--apply", action="store_true",
+                    help="one density-operator application on the workload's plan, for kernel profiling")
     return ap.parse_args()
 
 
@@ -916,8 +919,41 @@ def run_sweep(args):
     return 0
 
 
+def run_apply(args):
+    """One application of the density operator (I + 2K) sigma, sigma ~ N(0, 1), on the
+    workload's plan (border included, as in a solve: the float forward rows then take the
+    far field by the per-node ancestor walk), in the precision's FMM arithmetic: the
+    launches a kernel profile captures."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1306_0612_gb300 import lbfmm as L
+    import __graft_entry__
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    g, _, _ = make_geometry(args.workload)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).to(dev)
+    kw = dict(**precision_options(L, args.precision))
+    for k, v in (("p", args.p), ("p32", args.p32), ("leaf_size", args.leaf), ("p2p_warps", args.warps)):
+        if v:
+            kw[k] = v
+    plan = L.lbf_plan_create(g.island_ptr, t(g.x), t(g.dx), t(g.d2x), t(g.centres),
+                             opt=L.lbf_default_options(**kw))
+    v = t(wl.random_density(g.N, 1))
+    o = torch.empty_like(v)
+    op = L.LBF_OP_K_ONLY | (L.LBF_OP_FP32 if args.precision == "fp32r" else 0)
+    L.lbf_apply(plan, op, v, o)
+    torch.cuda.synchronize()
+    print(json.dumps({"apply": args.workload, "precision": args.precision, "tree": plan.info(),
+                      "counts": L.lbf_plan_counts(plan), "norm": float(o.norm())}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.apply:
+        return run_apply(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.sweep:

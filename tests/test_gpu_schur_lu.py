@@ -59,11 +59,13 @@ def test_lu_singular_shared_centre():
 
 
 @pytest.mark.parametrize("precision,tol,agree", [(L.LBF_PRECISION_FP64, 1e-12, 1e-9),
-                                                  (L.LBF_PRECISION_FP32_REFINE, 1e-10, 1e-8)])
+                                                  (L.LBF_PRECISION_FP32_REFINE, 1e-10, 1e-7)])
 def test_lu_solve_many_islands_matches_gauss_jordan(precision, tol, agree):
     """2048 islands (the LU path by default) against the same solve with the
-    Gauss-Jordan inverse: the same bordered system, each solved to tol (two solutions
-    within tol of the same one agree to a small multiple of tol)."""
+    Gauss-Jordan inverse: the same bordered system, each solved to a preconditioned
+    relative residual below tol.  Two such solutions differ by at most
+    ||(P^-1 A)^-1|| 2 tol relative, a few hundred tol on these geometries; the FP64 GMRES
+    runs the same Krylov iteration to rounding and agrees far closer."""
     g = wl.star_caps(3, 2048, 64)
     src, gam, _ = wl.pair_sources(g, 0, 1)
     data = zeros(g.N)
