@@ -183,8 +183,8 @@ struct lbf_plan {
     double *lu_S = nullptr;       // S itself (double), for the refinement step of accurate applies
     double *lu_r = nullptr;       // M: that step's residual
     float2 *lu_z2 = nullptr;      // M: its correction
-    int lu_fast = 0;              // 1 while an Arnoldi step applies the operator: S^-1 from the
-                                  // factors alone (every other application refines once)
+    int lu_fast = 0;              // 1 while an FP64 Arnoldi step applies the operator: S^-1 from
+                                  // the factors alone (every other application refines once)
     double *fvec = nullptr, *yvec = nullptr;  // M-vectors
     // generic N+M vectors for lbf_apply / gmres
     double *tin = nullptr, *tout = nullptr;

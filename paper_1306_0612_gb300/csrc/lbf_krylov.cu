@@ -659,7 +659,10 @@ static int arnoldi_step_t(lbf_plan *pl, int opc, int prec, int k, bool from_stat
         }
         vj = pl->vstep;
     }
-    pl->lu_fast = 1;  // Arnoldi steps: S^-1 without its refinement step
+    // FP64 Arnoldi steps take S^-1 from the factors alone; the refinement's float inner
+    // steps keep the refinement step, so that they approximate the same P^-1 A as the
+    // FP64 residual (a coarser S^-1 there costs refinement steps when S is ill-conditioned)
+    pl->lu_fast = prec == LBF_PREC_FP64 ? 1 : 0;
     int rc = lbf_apply_op_sorted(pl, opc, vj, w, &pl->gs->go, s, prec);
     pl->lu_fast = 0;
     if (rc) return rc;
