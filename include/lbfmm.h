@@ -426,13 +426,14 @@ int lbf_evaluate_noalloc(int64_t N, const double *xi, const double *weight, cons
 
 /* The double reciprocals of the operator's sums, exposed for tests against IEEE
  * division.  Every near-field pair of Sec. 5's discretised double layer needs
- * 1/|xi_j - xi_i|^2; the library forms it by Newton-Raphson iteration
- * x <- x + x (1 - a x) from a single-precision seed, two steps:
- *   variant 0: the general form, seeded by the float reciprocal of (float)a; outside
- *              [1e-30, 1e30] it falls back to the division operator;
+ * 1/|xi_j - xi_i|^2; the library refines a single-precision seed x with e = 1 - a x:
+ *   variant 0: the general form, seeded by the float reciprocal of (float)a, two
+ *              Newton-Raphson steps x <- x + x e; outside [1e-30, 1e30] it falls back
+ *              to the division operator;
  *   variant 1: the near-field and far-field form, for a in [2^-126, 2^126] only: the
  *              seed is built from a's bits by integer operations (no conversion
- *              instruction on the double pipe).
+ *              instruction on the double pipe), then one third-order step
+ *              x <- x + x (e + e^2).
  * a, out: n doubles (device).  Asynchronous. */
 int lbf_selftest_rcp(int variant, int64_t n, const double *a, double *out, lbf_stream_t stream);
 

@@ -70,13 +70,15 @@ __device__ __forceinline__ df64 rcp(df64 a) { return df_rcp(a); }
 
 // 1/a in double for a positive normal a in [2^-126, 2^126] (the near field's squared
 // distances in units of a leaf half-width, the far-field arguments of M2P and P2L), with
-// no instruction on the double pipe but the Newton steps: the float seed is a with its
+// no instruction on the double pipe but the refinement: the float seed is a with its
 // exponent rebiased and its mantissa cut to 20 bits, built with integer operations
 // (relative error < 2^-20), the float reciprocal approximation of that, widened back by
-// integer operations, then two Newton-Raphson steps x <- x + x (1 - a x) (the error
-// squares at each: ~2^-40, then below the rounding of the last step).  On this GPU the
-// double pipe is the bound of every double FMM kernel; a conversion instruction would
-// occupy it like an arithmetic one.
+// integer operations, then one third-order step of the series 1/a = x/(1 - e) =
+// x (1 + e + e^2 + ...), e = 1 - a x: x <- x + x (e + e^2), three fused multiply-adds
+// (the dropped terms are ~e^3 < 2^-59, below the rounding of the last one; two
+// Newton-Raphson steps would take four).  On this GPU the double pipe is the bound of
+// every double FMM kernel; a conversion instruction would occupy it like an arithmetic
+// one.
 __device__ __forceinline__ double rcp_near(double a)
 {
     const int hi = __double2hiint(a);
@@ -84,11 +86,9 @@ __device__ __forceinline__ double rcp_near(double a)
     float yf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(af));
     const unsigned yb = __float_as_uint(yf);
-    double x = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
-    double e = fma(-a, x, 1.0);
-    x = fma(x, e, x);
-    e = fma(-a, x, 1.0);
-    return fma(x, e, x);
+    const double x = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+    const double e = fma(-a, x, 1.0);
+    return fma(x, fma(e, e, e), x);
 }
 
 template <typename R> __device__ __forceinline__ cx<R> crcp(cx<R> a)
@@ -451,6 +451,57 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         accF0.x += __shfl_down_sync(0xffffffffu, accF0.x, 16);
         accF0.y += __shfl_down_sync(0xffffffffu, accF0.y, 16);
         if (lane >= 16) accF0 = mk<R>(0, 0);
+    } else if (std::is_same<R, double>::value && nv[b] >= 4) {
+        // Native double, four or more V-list boxes: a masked lane occupies the double pipe
+        // like an active one, so the nv x P (box, coefficient) slots run flattened, 32 at a
+        // time, instead of a box at a time on P of the 32 lanes.  The scaled multipoles
+        // t^k a_k of all the boxes go to shared memory first; slot (v, l) forms
+        // sum_k C(k+l, l) t_v^k a_{v,k} and adds (-1)^l t_v^(l+1) times it into the
+        // coefficient l of a per-warp accumulator.  Lanes i and i + P of a round hold the
+        // same l (P >= 17 here, so no third): they add in two steps, so every coefficient
+        // takes its boxes in list order, the same operations in the same order as the
+        // box-at-a-time loop.
+        const int nvb = nv[b];
+        int vs = 0, vo = 0;
+        if (lane < nvb) {
+            vs = vlist[b * 27 + lane];
+            vo = (bx - ix[vs] + 3) * 7 + (by - iy[vs] + 3);
+        }
+        const int ns = nvb * P;
+        cx<R> *Af = T;  // nv x P scaled multipoles (T holds 32 P)
+        for (int s0 = 0; s0 < ns; s0 += 32) {
+            const int sl = s0 + lane, v = sl / P, k = sl - v * P;
+            const int src = __shfl_sync(0xffffffffu, vs, v & 31);
+            const int o = __shfl_sync(0xffffffffu, vo, v & 31);
+            if (sl < ns)
+                Af[sl] = cmul(mp[(int64_t)src * P + k], tpow[(size_t)o * (LBF_MAX_TERMS + 1) + k]);
+        }
+        for (int l = lane; l < P; l += 32) A[l] = mk<R>(0, 0);
+        __syncwarp();
+        for (int s0 = 0; s0 < ns; s0 += 32) {
+            const int sl = s0 + lane, v = sl / P, l = sl - v * P;
+            const int o = __shfl_sync(0xffffffffu, vo, v & 31);
+            const bool on = sl < ns;
+            cx<R> sa = mk<R>(0, 0);
+            if (on) {
+                const cx<R> *av = Af + v * P;
+                for (int k = 0; k < P; k++) {
+                    const cx<R> a = av[k];
+                    const R c = Cm[k * P + l];
+                    sa.x = fm(c, a.x, sa.x);
+                    sa.y = fm(c, a.y, sa.y);
+                }
+            }
+            cx<R> f = on ? tpow[(size_t)o * (LBF_MAX_TERMS + 1) + l + 1] : mk<R>(0, 0);
+            if (l & 1) { f.x = -f.x; f.y = -f.y; }
+            if (on && lane < P) A[l] = cfma(f, sa, A[l]);
+            __syncwarp();
+            if (on && lane >= P) A[l] = cfma(f, sa, A[l]);
+            __syncwarp();
+        }
+        if (l0 < P) accF0 = A[l0];
+        if (l1 < P) accF1 = A[l1];
+        __syncwarp();
     } else {
         // V-list records loaded once (a lane per entry); with P <= 32 the next box's
         // coefficients are fetched one step ahead
@@ -522,7 +573,51 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         xr_b = bg[xr_s];
         xr_e = en[xr_s];
     }
-    for (int xq = 0; xq < nxb; xq++) {
+    if constexpr (std::is_same<R, double>::value) {
+        // native double: the X-list boxes' nodes (all taken relative to this box's centre
+        // in double) run as one list, 32 at a time, so short source boxes share a round
+        const int xn = lane < nxb ? xr_e - xr_b : 0;
+        int inc = xn;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const int nxt = __shfl_sync(0xffffffffu, inc, 31), xoff = inc - xn;
+        if (nxt > 0) need_centre();
+        for (int base = 0; base < nxt; base += 32) {
+            const int gi = base + lane;
+            int j = -1;
+            for (int xq = 0; xq < nxb; xq++) {
+                const int o = __shfl_sync(0xffffffffu, xoff, xq);
+                const int n = __shfl_sync(0xffffffffu, xn, xq);
+                const int b0 = __shfl_sync(0xffffffffu, xr_b, xq);
+                if (gi >= o && gi < o + n) j = b0 + gi - o;
+            }
+            cx<R> tau = mk<R>(0, 0), term = mk<R>(0, 0);
+            if (j >= 0) {
+                const double2 z = xi[j];
+                tau = crcp(mk<R>((R)((cxd - z.x) * ir), (R)((cyd - z.y) * ir)));
+                term = cmul(q[j], tau);  // l = 0
+            }
+            for (int l = 0; l < P; l++) {
+                T[l * 32 + lane] = (l & 1) ? mk<R>(-term.x, -term.y) : term;
+                term = cmul(term, tau);
+            }
+            __syncwarp();
+            for (int l = lane; l < P; l += 32) {
+                cx<R> sm = mk<R>(0, 0);
+                for (int m = 0; m < 32; m++) {
+                    cx<R> v = T[l * 32 + m];
+                    sm.x += v.x;
+                    sm.y += v.y;
+                }
+                if (l < 32) { accF0.x += sm.x; accF0.y += sm.y; }
+                else { accF1.x += sm.x; accF1.y += sm.y; }
+            }
+            __syncwarp();
+        }
+    }
+    for (int xq = 0; xq < (std::is_same<R, double>::value ? 0 : nxb); xq++) {
         const int ls = __shfl_sync(0xffffffffu, xr_l, xq);
         const int sx_ = __shfl_sync(0xffffffffu, xr_x, xq), sy_ = __shfl_sync(0xffffffffu, xr_y, xq);
         const int sbg = __shfl_sync(0xffffffffu, xr_b, xq), sen = __shfl_sync(0xffffffffu, xr_e, xq);
@@ -661,10 +756,16 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
 
 constexpr int kLeafWarps = 4;  // default warps per block of the leaf kernel
 constexpr int kSrcChunk = 256;
+constexpr int kLeafExtra = 64 * 16;  // per warp: 32 target positions, 32 pairs of partial sums
 
 template <typename R> struct LeafSrc {
     cx<R> z, q;
 };
+// dynamic shared memory of the leaf kernel for lw warps per block
+template <typename R> constexpr size_t leaf_smem(int lw)
+{
+    return (size_t)lw * (kSrcChunk * sizeof(LeafSrc<R>) + kLeafExtra);
+}
 __device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
 __device__ __forceinline__ bool positive(double x) { return x > 0.0; }
 __device__ __forceinline__ bool positive(df64 x) { return x.hi > 0.0f; }
@@ -716,6 +817,12 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
     extern __shared__ __align__(16) unsigned char leaf_sm[];
     LeafSrc<R>(*ss)[kSrcChunk] = (LeafSrc<R>(*)[kSrcChunk])leaf_sm;
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the double forward rows split the near field's (target, source) pairs evenly over
+    // the lanes (below); the others give each target 32/TP lanes
+    constexpr bool kFlat = std::is_same<R, double>::value && MODE == kLeafForward;
+    double2 *tz = (double2 *)(leaf_sm + (blockDim.x >> 5) * kSrcChunk * sizeof(LeafSrc<R>)) +
+                  (size_t)wid * 64;
+    double2 *part = tz + 32;
     int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
     if (t >= nleaf) return;
     const int b = leaves[t];
@@ -824,7 +931,61 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         R accI = 0;
         cx<R> acc = mk<R>(0, 0);
         int fill = 0;
+        if constexpr (kFlat) {
+            if (act) tz[lane] = make_double2((double)u.x, (double)u.y);
+        }
+        // Double forward rows: a masked lane occupies the double pipe like an active one,
+        // so the nt x fill (target, source) pairs of a staged chunk, target-major, are
+        // cut into 32 runs of W = ceil(nt fill / 32); a run spans at most two targets
+        // (W <= fill), and each target then sums the partial sums of the runs that
+        // cover it, in lane order (a fixed order: the result does not depend on timing).
+        auto process_flat = [&]() {
+            __syncwarp();
+            const int tot = nt * fill, W = (tot + 31) >> 5;
+            const int a0 = min(lane * W, tot), a1 = min(a0 + W, tot);
+            // one loop of a1 - a0 steps (the same for all but the last runs); a run that
+            // reaches the end of its first target moves on to the next one inside it, so
+            // the warp does not execute the two targets' parts one after the other
+            double p = 0.0, pfirst = 0.0;
+            bool second = false;
+            {
+                const int t = a0 < tot ? a0 / fill : 0;
+                int m = a0 - t * fill;
+                double2 z = tz[t];
+#pragma unroll 4
+                for (int k = a0; k < a1; k++, m++) {
+                    if (m == fill) {
+                        pfirst = p;
+                        p = 0.0;
+                        m = 0;
+                        z = tz[t + 1];
+                        second = true;
+                    }
+                    const LeafSrc<R> sm = ss[wid][m];
+                    const double dr = (double)sm.z.x - z.x, di = (double)sm.z.y - z.y;
+                    const double ir2 = rcp_near(fma(dr, dr, fma(di, di, 1e-30)));
+                    p = fma(fma((double)sm.q.y, dr, -(double)sm.q.x * di), ir2, p);
+                }
+            }
+            part[lane] = second ? make_double2(pfirst, p) : make_double2(p, 0.0);
+            __syncwarp();
+            if (lane < nt) {
+                const int lo = (lane * fill) / W, hi = ((lane + 1) * fill - 1) / W;
+                double sum = 0.0;
+                for (int L = lo; L <= hi; L++) {
+                    const double2 pv = part[L];
+                    sum += (L * W) / fill == lane ? pv.x : pv.y;  // the run's first target?
+                }
+                accI += (R)sum;
+            }
+            __syncwarp();
+            fill = 0;
+        };
         auto process = [&]() {
+            if constexpr (kFlat) {
+                process_flat();
+                return;
+            }
             __syncwarp();
             if (pact) {
 #pragma unroll 4
@@ -902,10 +1063,12 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             }
         }
         if (fill > 0) process();
-        for (int o = TP; o < 32; o <<= 1) {  // sum the source groups of each target
-            accI += __shfl_xor_sync(0xffffffffu, accI, o);
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        if constexpr (!kFlat) {
+            for (int o = TP; o < 32; o <<= 1) {  // sum the source groups of each target
+                accI += __shfl_xor_sync(0xffffffffu, accI, o);
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
         }
         if (act) {
             if constexpr (MODE == kLeafForward) {

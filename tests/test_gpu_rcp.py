@@ -1,4 +1,5 @@
-"""The library's double reciprocals (Newton-Raphson from a single-precision seed, used
+"""The library's double reciprocals (a single-precision seed refined by Newton-Raphson
+steps, or by one third-order step in the near-field form, used
 for 1/|xi_j - xi_i|^2 at every near pair of the discretised double layer, Sec. 5, and
 for the far-field conversions) against IEEE division on the host, over a log-spaced
 sweep with random mantissas: within 2 units in the last place of double."""
