@@ -487,7 +487,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
               cudaStream_t s, bool split = false)
 {
     Tree &T = pl->tree;
-    BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
+    BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L), 1.0 / T.L};
     const int P = a.P;
     const cx<R> *q = (const cx<R> *)a.q;
     cx<R> *mp = (cx<R> *)a.mp, *loc = (cx<R> *)a.loc;
@@ -673,7 +673,7 @@ int lbf_multipoles(lbf_plan *pl, const double *x, int P, double2 *mp, const int 
     int rc = prep(pl, x, Arith::F64, false, gate, s);
     if (rc) return rc;
     Tree &T = pl->tree;
-    BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
+    BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L), 1.0 / T.L};
     const int wpb = 2;
     LBF_LAUNCH(fmm::k_up<double>, lbf_cdiv(T.nleaf, wpb), 32 * wpb, up_smem<double>(P, wpb), s,
                T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin, T.end, T.parent, T.child0,
@@ -698,7 +698,7 @@ int lbf_fmm_prepare(lbf_plan *pl, cudaStream_t s)
     }
     if (!pl->u32 && !pl->udf) return LBF_OK;
     Tree &T = pl->tree;
-    fmm::BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L)};
+    fmm::BoxGeo g{T.xmin, T.ymin, T.L, (float)(1.0 / T.L), df64(1.0 / T.L), 1.0 / T.L};
     LBF_LAUNCH(k_local_coords, lbf_cdiv(T.nleaf, 8), 256, 0, s, T.nleaf, T.leaves, T.level, T.ix,
                T.iy, T.begin, T.end, g, pl->xi, pl->u32, (cx<df64> *)pl->udf);
     if (pl->anc)
@@ -719,7 +719,7 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
                    (const int *)nullptr, (const int32_t *)nullptr, (const double *)nullptr);
         LBF_CHECK_LAUNCH();
         Tree &Tr = pl->tree;
-        BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L)};
+        BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L), 1.0 / Tr.L};
         const int P = pl->P, wpb = 2;
         LBF_LAUNCH(fmm::k_up<df64>, lbf_cdiv(Tr.nleaf, wpb), 32 * wpb, up_smem<df64>(P, wpb), s,
                    Tr.nleaf, Tr.leaves, Tr.level, Tr.ix, Tr.iy, Tr.begin, Tr.end, Tr.parent,
@@ -740,7 +740,7 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
         int rc = prep(pl, sigma_sorted, Arith::F64, true, nullptr, s);
         if (rc) return rc;
         Tree &Tr = pl->tree;
-        BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L)};
+        BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L), 1.0 / Tr.L};
         const int P = pl->P, wpb = 2;
         LBF_LAUNCH(fmm::k_up<double>, lbf_cdiv(Tr.nleaf, wpb), 32 * wpb, up_smem<double>(P, wpb), s,
                    Tr.nleaf, Tr.leaves, Tr.level, Tr.ix, Tr.iy, Tr.begin, Tr.end, Tr.parent,

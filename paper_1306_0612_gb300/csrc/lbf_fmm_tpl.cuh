@@ -111,6 +111,7 @@ struct BoxGeo {
     double xmin, ymin, L;
     float invLf;  // 1/L rounded to float: 1/r of a level-l box is invLf 2^(l+1)
     df64 invLd;   // 1/L as a double-float
+    double invL;  // 1/L in double
 };
 
 __device__ __forceinline__ void box_centre(const BoxGeo &g, int l, int ix, int iy, double &cx_,
@@ -122,6 +123,12 @@ __device__ __forceinline__ void box_centre(const BoxGeo &g, int l, int ix, int i
     cy_ = g.ymin + (iy + 0.5) * w;
 }
 
+// The centre of a level-l box and 1/r, its half-width's reciprocal, with few instructions
+// on the double pipe: ix + 1/2 from the integer's bits (2^52 + ix less 2^52 - 1/2, exact),
+// the width L 2^-l and 1/r = (1/L) 2^(l+1) by exact power-of-two products (the same values
+// as box_centre and 1.0 / r).
+__device__ __forceinline__ void box_centre_ir(const BoxGeo &g, int l, int ix, int iy,
+                                              double &cx_, double &cy_, double &ir);
 // 2^e from the exponent bits (|e| well inside the normal range)
 template <typename R> __device__ __forceinline__ R pow2(int e);
 template <> __device__ __forceinline__ float pow2<float>(int e) { return __int_as_float((127 + e) << 23); }
@@ -130,6 +137,17 @@ template <> __device__ __forceinline__ double pow2<double>(int e)
     return __longlong_as_double((long long)(1023 + e) << 52);
 }
 template <> __device__ __forceinline__ df64 pow2<df64>(int e) { return df64(pow2<float>(e)); }
+
+__device__ __forceinline__ void box_centre_ir(const BoxGeo &g, int l, int ix, int iy,
+                                              double &cx_, double &cy_, double &ir)
+{
+    const double w = g.L * pow2<double>(-l);
+    const double hx = __hiloint2double(0x43300000, ix) - 4503599627370495.5;
+    const double hy = __hiloint2double(0x43300000, iy) - 4503599627370495.5;
+    cx_ = fma(hx, w, g.xmin);
+    cy_ = fma(hy, w, g.ymin);
+    ir = g.invL * pow2<double>(l + 1);
+}
 
 // 1/r of a level-l box in R without double arithmetic (float, double-float)
 template <typename R> __device__ __forceinline__ R inv_half_width(const BoxGeo &g, int l);
@@ -245,9 +263,10 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
                 term = cmul(term, z);
             }
             __syncwarp();
+            const int nin = min(32, en[b] - base);  // the chunk's nodes (the rest add 0)
             for (int k = lane; k < P; k += 32) {
                 cx<R> s = mk<R>(0, 0);
-                for (int m = 0; m < 32; m++) {
+                for (int m = 0; m < nin; m++) {
                     cx<R> v = T[k * 32 + m];
                     s.x += v.x;
                     s.y += v.y;
@@ -604,9 +623,10 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                 term = cmul(term, tau);
             }
             __syncwarp();
+            const int nin = min(32, nxt - base);
             for (int l = lane; l < P; l += 32) {
                 cx<R> sm = mk<R>(0, 0);
-                for (int m = 0; m < 32; m++) {
+                for (int m = 0; m < nin; m++) {
                     cx<R> v = T[l * 32 + m];
                     sm.x += v.x;
                     sm.y += v.y;
@@ -659,9 +679,10 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                 term = cmul(term, tau);
             }
             __syncwarp();
+            const int nin = min(32, sen - base);
             for (int l = lane; l < P; l += 32) {
                 cx<R> sm = mk<R>(0, 0);
-                for (int m = 0; m < 32; m++) {
+                for (int m = 0; m < nin; m++) {
                     cx<R> v = T[l * 32 + m];
                     sm.x += v.x;
                     sm.y += v.y;
@@ -861,6 +882,8 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                 double2 zi = xi[i];
                 u = mk<R>((zi.x - cxd) * ir, (zi.y - cyd) * ir);
             }
+            // (the double forward rows take their far field below, flattened)
+            if constexpr (!kFlat) {
             if constexpr (MODE == kLeafDeriv) {
                 // d/dz sum_l b_l ((z - c)/r)^l = (1/r) sum_{l>=1} l b_l u^(l-1)
                 cx<R> d = mk<R>((R)(P - 1) * lb[P - 1].x, (R)(P - 1) * lb[P - 1].y);
@@ -923,6 +946,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                     phi.y += ps.y * isr;
                 }
             }
+            }
         }
         // near field, in units of r: sum over sources of q conj(dz)/|dz|^2 (Im part only
         // in the forward mode) or q conj(dz)^2/|dz|^4, dz = xi_s - z
@@ -931,8 +955,46 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         R accI = 0;
         cx<R> acc = mk<R>(0, 0);
         int fill = 0;
+        double phiI = 0.0;  // the double forward rows: Im of the far field at target lane
         if constexpr (kFlat) {
             if (act) tz[lane] = make_double2((double)u.x, (double)u.y);
+            __syncwarp();
+            // Far field as nt x (1 + |W(b)|) items, 32 at a time, source-major (the lanes of a
+            // round mostly share one expansion): item (0, t) is the L2P of the leaf's own
+            // local expansion at target t, item (s, t) the M2P of the s-th W-list box.  Both
+            // are a Horner sum of P terms at a point x, times a factor w: x = w = 1 for the
+            // L2P; x = rho = r_s/(z - c_s) and w = rho/r_s for the M2P.  Each target then
+            // adds its items of the round in item order.
+            const int wb = wptr[b], nit = nt * (wptr[b + 1] - wb + (l2p ? 1 : 0));
+            const int s_off = l2p ? 0 : 1;
+            for (int i0 = 0; i0 < nit; i0 += 32) {
+                const int it = min(i0 + lane, nit - 1);
+                const int sq = it / nt + s_off, t = it - (sq - s_off) * nt;
+                const cx<double> *cf;
+                cx<double> x, w;
+                if (sq == 0) {
+                    cf = (const cx<double> *)lb;
+                    x = mk<double>(tz[t].x, tz[t].y);
+                    w = mk<double>(1.0, 0.0);
+                } else {
+                    const int sb = widx[wb + sq - 1];
+                    double sxd, syd, sir;
+                    box_centre_ir(g, level[sb], ix[sb], iy[sb], sxd, syd, sir);
+                    const double2 zi = xi[tb + t];
+                    x = crcp(mk<double>((zi.x - sxd) * sir, (zi.y - syd) * sir));
+                    w = mk<double>(x.x * sir, x.y * sir);
+                    cf = (const cx<double> *)mp + (int64_t)sb * P;
+                }
+                cx<double> h = cf[P - 1];
+                for (int l = P - 2; l >= 0; l--) h = cfma(h, x, cf[l]);
+                part[lane].x = fma(w.x, h.y, w.y * h.x);  // Im(w h)
+                __syncwarp();
+                if (lane < nt) {
+                    for (int L = (lane - i0 % nt + nt) % nt; L < 32 && i0 + L < nit; L += nt)
+                        phiI += part[L].x;
+                }
+                __syncwarp();
+            }
         }
         // Double forward rows: a masked lane occupies the double pipe like an active one,
         // so the nt x fill (target, source) pairs of a staged chunk, target-major, are
@@ -1072,7 +1134,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         }
         if (act) {
             if constexpr (MODE == kLeafForward) {
-                double c = (double)(-phi.y) + (double)(accI * irr);
+                double c = (double)(-(kFlat ? (R)phiI : phi.y)) + (double)(accI * irr);
                 // with island means m split off (isl given): the sums saw sigma - m; the
                 // means' rows are a_k m_k + 2 n m_(enclosing island) (the beta . m part is
                 // in bsig, formed from sigma)
