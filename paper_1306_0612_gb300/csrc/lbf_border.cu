@@ -572,15 +572,23 @@ __global__ void k_mp_l2l(int64_t ls, int64_t le, int P, const int32_t *__restric
     const int l0 = lane, l1 = lane + 32;
     const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
     cz<R> s0{0, 0}, s1{0, 0};
-    for (int k = 0; k < P; k++) {
-        cz<R> a = A[k];
-        R c0 = Cd[k * P + lc0];
-        s0.x = fmr(c0, a.x, s0.x);
-        s0.y = fmr(c0, a.y, s0.y);
-        if (l1 < P) {
-            R c1 = Cd[k * P + lc1];
+    // the second coefficient's sum only when P > 32: a test inside the loop leaves
+    // predicated-off multiply-adds that still occupy the double pipe
+    if (P > 32) {
+        for (int k = 0; k < P; k++) {
+            const cz<R> a = A[k];
+            const R c0 = Cd[k * P + lc0], c1 = Cd[k * P + lc1];
+            s0.x = fmr(c0, a.x, s0.x);
+            s0.y = fmr(c0, a.y, s0.y);
             s1.x = fmr(c1, a.x, s1.x);
             s1.y = fmr(c1, a.y, s1.y);
+        }
+    } else {
+        for (int k = 0; k < P; k++) {
+            const cz<R> a = A[k];
+            const R c0 = Cd[k * P + lc0];
+            s0.x = fmr(c0, a.x, s0.x);
+            s0.y = fmr(c0, a.y, s0.y);
         }
     }
     if (l0 < P) {
@@ -653,15 +661,23 @@ __global__ void k_mp_chain(int64_t nbox, int P, const int32_t *__restrict__ pare
             }
             __syncwarp();
             cz<R> s0{0, 0}, s1{0, 0};
-            for (int k = 0; k < P; k++) {
-                const cz<R> a = A[k];
-                const R c0 = Cd[k * P + lc0];
-                s0.x = fmr(c0, a.x, s0.x);
-                s0.y = fmr(c0, a.y, s0.y);
-                if (l1 < P) {
-                    const R c1 = Cd[k * P + lc1];
+            // the second coefficient's sum only when P > 32: a test inside the loop leaves
+            // predicated-off multiply-adds that still occupy the double pipe
+            if (P > 32) {
+                for (int k = 0; k < P; k++) {
+                    const cz<R> a = A[k];
+                    const R c0 = Cd[k * P + lc0], c1 = Cd[k * P + lc1];
+                    s0.x = fmr(c0, a.x, s0.x);
+                    s0.y = fmr(c0, a.y, s0.y);
                     s1.x = fmr(c1, a.x, s1.x);
                     s1.y = fmr(c1, a.y, s1.y);
+                }
+            } else {
+                for (int k = 0; k < P; k++) {
+                    const cz<R> a = A[k];
+                    const R c0 = Cd[k * P + lc0];
+                    s0.x = fmr(c0, a.x, s0.x);
+                    s0.y = fmr(c0, a.y, s0.y);
                 }
             }
             if (l0 < P) {

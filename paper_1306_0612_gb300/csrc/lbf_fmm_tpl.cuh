@@ -210,6 +210,35 @@ template <typename R> __device__ __forceinline__ const cx<R> *d2inv(const cx<R> 
     return dtab + (size_t)(4 + c) * (LBF_MAX_TERMS + 1);
 }
 
+// s0 = sum_k C[k P + lc0] A[k], and s1 the same for lc1 when a lane holds two coefficients
+// (two = P > 32, the same in every lane).  The test sits outside the loop: inside it the
+// compiler predicates the second sum's multiply-adds, and an instruction whose lanes are all
+// predicated off still takes its issue slots on the double pipe.
+template <typename R>
+__device__ __forceinline__ void coef_sums(const cx<R> *A, const R *C, int P, int lc0, int lc1,
+                                          bool two, cx<R> &s0, cx<R> &s1)
+{
+    s0 = mk<R>(0, 0);
+    s1 = mk<R>(0, 0);
+    if (two) {
+        for (int k = 0; k < P; k++) {
+            const cx<R> a = A[k];
+            const R c0 = C[k * P + lc0], c1 = C[k * P + lc1];
+            s0.x = fm(c0, a.x, s0.x);
+            s0.y = fm(c0, a.y, s0.y);
+            s1.x = fm(c1, a.x, s1.x);
+            s1.y = fm(c1, a.y, s1.y);
+        }
+    } else {
+        for (int k = 0; k < P; k++) {
+            const cx<R> a = A[k];
+            const R c0 = C[k * P + lc0];
+            s0.x = fm(c0, a.x, s0.x);
+            s0.y = fm(c0, a.y, s0.y);
+        }
+    }
+}
+
 // Upward pass in one launch (see lbf_fmm.cu): P2M per leaf, then M2M by the warp
 // that completes a box's last child:  a_l = d^l sum_{k<=l} C(l,k) (2d)^-k a'_k.
 template <typename R>
@@ -306,18 +335,8 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
                 A[k] = cmul(a, inv[k]);
             }
             __syncwarp();
-            cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
-            for (int k = 0; k < P; k++) {
-                cx<R> a = A[k];
-                R c0 = Cl[k * P + lc0];
-                s0.x = fm(c0, a.x, s0.x);
-                s0.y = fm(c0, a.y, s0.y);
-                if (l1 < P) {
-                    R c1 = Cl[k * P + lc1];
-                    s1.x = fm(c1, a.x, s1.x);
-                    s1.y = fm(c1, a.y, s1.y);
-                }
-            }
+            cx<R> s0, s1;
+            coef_sums(A, Cl, P, lc0, lc1, P > 32, s0, s1);
             const cx<R> *dp = dpow(dtab, d);
             acc0 = cfma(dp[l0], s0, acc0);
             if (l1 < P) acc1 = cfma(dp[l1], s1, acc1);
@@ -404,18 +423,8 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         const cx<R> *dp = dpow(dtab, d);
         for (int k = lane; k < P; k += 32) A[k] = cmul(ldcg_cx(&loc[(int64_t)p * P + k]), dp[k]);
         __syncwarp();
-        cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
-        for (int k = 0; k < P; k++) {
-            cx<R> a = A[k];
-            R c0 = Cd[k * P + lc0];
-            s0.x = fm(c0, a.x, s0.x);
-            s0.y = fm(c0, a.y, s0.y);
-            if (l1 < P) {
-                R c1 = Cd[k * P + lc1];
-                s1.x = fm(c1, a.x, s1.x);
-                s1.y = fm(c1, a.y, s1.y);
-            }
-        }
+        cx<R> s0, s1;
+        coef_sums(A, Cd, P, lc0, lc1, P > 32, s0, s1);
         const cx<R> *inv = d2inv(dtab, d);
         accL0 = cmul(inv[l0], s0);
         if (l1 < P) accL1 = cmul(inv[l1], s1);
@@ -546,18 +555,8 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
                 for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
             }
             __syncwarp();
-            cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
-            for (int k = 0; k < P; k++) {
-                cx<R> a = A[k];
-                R c0 = Cm[k * P + lc0];
-                s0.x = fm(c0, a.x, s0.x);
-                s0.y = fm(c0, a.y, s0.y);
-                if (l1 < P) {
-                    R c1 = Cm[k * P + lc1];
-                    s1.x = fm(c1, a.x, s1.x);
-                    s1.y = fm(c1, a.y, s1.y);
-                }
-            }
+            cx<R> s0, s1;
+            coef_sums(A, Cm, P, lc0, lc1, P > 32, s0, s1);
             cx<R> f0 = tp[l0 + 1];
             if (l0 & 1) { f0.x = -f0.x; f0.y = -f0.y; }
             accF0 = cfma(f0, s0, accF0);
@@ -737,18 +736,8 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
             const cx<R> *dp = dpow(dtab, d);
             for (int k = lane; k < P; k += 32) A[k] = cmul(ldcg_cx(&loc[(int64_t)p * P + k]), dp[k]);
             __syncwarp();
-            cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
-            for (int k = 0; k < P; k++) {
-                cx<R> a = A[k];
-                R c0 = Cd[k * P + lc0];
-                s0.x = fm(c0, a.x, s0.x);
-                s0.y = fm(c0, a.y, s0.y);
-                if (l1 < P) {
-                    R c1 = Cd[k * P + lc1];
-                    s1.x = fm(c1, a.x, s1.x);
-                    s1.y = fm(c1, a.y, s1.y);
-                }
-            }
+            cx<R> s0, s1;
+            coef_sums(A, Cd, P, lc0, lc1, P > 32, s0, s1);
             const cx<R> *inv = d2inv(dtab, d);
             if (l0 < P) {
                 const cx<R> own = ldcg_cx(&loc[b * P + l0]);
