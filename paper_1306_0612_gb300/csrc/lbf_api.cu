@@ -254,7 +254,7 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     add(sizeof(int32_t) * nk);     // perm_alt
     int64_t iscr = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     add(sizeof(int32_t) * iscr);   // integer scratch (scans, histograms, flags)
-    add(std::max(sizeof(double) * lbf_gj_scratch_doubles(M), lbf_lu_scratch_bytes()));  // the inverse's or the factorisation's
+    add(std::max(sizeof(double) * lbf_gj_scratch_doubles(M), lbf_lu_scratch_bytes(M)));  // the inverse's or the factorisation's
     size_t big = std::max(vbytes, tmp);
     pl->region = (char *)A.take(big);
     pl->region_bytes = big;
@@ -292,7 +292,7 @@ Temps temps(lbf_plan *pl, char *region, int64_t N, int M, int64_t cap)
     int64_t nunits = lbf_cdiv(N, 1024);
     t.iscr_len = std::max<int64_t>(256 * nunits + 4096, 4 * cap + 4096) + 6 * (int64_t)M + N / 512 + 8192;
     t.iscr = (int32_t *)take(sizeof(int32_t) * t.iscr_len);
-    t.gj = (double *)take(std::max(sizeof(double) * lbf_gj_scratch_doubles(M), lbf_lu_scratch_bytes()));
+    t.gj = (double *)take(std::max(sizeof(double) * lbf_gj_scratch_doubles(M), lbf_lu_scratch_bytes(M)));
     return t;
 }
 }  // namespace

@@ -243,7 +243,7 @@ int lbf_border_build(lbf_plan *pl, cudaStream_t s, int32_t *work, int64_t work_l
 void lbf_border_end(lbf_plan *pl);     // releases the side stream and events
 size_t lbf_gj_scratch_doubles(int M);  // scratch of lbf_border_start
 // ---- LU of the Schur complement (lbf_schur_lu.cu) ---------------------------------
-size_t lbf_lu_scratch_bytes();
+size_t lbf_lu_scratch_bytes(int M);
 int lbf_lu_sync_words(int M);
 int64_t lbf_lu_dinv_entries(int M);
 int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch);

@@ -8,8 +8,11 @@
 // islands, and its condition number grows with M (about 4e5 at M = 256, 3e7 at
 // M = 1024, 2e8 at M = 4096 for the star-cap family), beyond what a float
 // factorisation can refine.  So the factorisation runs in double-float (pairs of
-// floats, ~48-bit significands) on the float pipes, which issue 64 times faster than
-// the double pipe: M^3 / 3 multiply-adds instead of the inverse's M^3.  The
+// floats, ~48-bit significands): the panels, the triangular solves and the combination
+// of the trailing update's partial products on the float pipes, which issue 64 times
+// faster than the double pipe, and the trailing update's products, almost all of its
+// M^3 / 3 multiply-adds (the inverse would take M^3), on the tensor cores through an
+// exact split of the operands into bf16 slices.  The
 // preconditioner only has to be close to P^-1: GMRES solves the bordered system to
 // its own tolerance whatever the rounding of S^-1 (which is about cond(S) 2^-46).
 //
@@ -27,11 +30,14 @@
 //              the interchange needs no second barrier;
 //   k_lu_swap: the panel's interchanges applied to every column outside it;
 //   k_lu_trsm: U12 = L11^-1 A12 (the panel's rows to the right of it);
-//   k_lu_gemm: A22 -= L21 U12 (the trailing matrix, 64 x 64 tiles).
+//   k_oz_slice_rows, k_oz_slice_cols, k_lu_gemm_tc: A22 -= L21 U12 (the trailing
+//              matrix) on the tensor cores, by an exact split of the double-float
+//              operands into bf16 integer slices (below).
 // A pivot at or below M 2^-50 max|S_ij| reports a singular S (status bit 4), a grid
 // barrier that gave up a time-out; every later kernel of the factorisation then returns
 // at once.
 #include <algorithm>
+#include <cuda_bf16.h>
 
 #include "lbf_df64.cuh"
 #include "lbf_internal.cuh"
@@ -264,81 +270,326 @@ k_lu_trsm(int M, int k0, int w, float2 *A, const int *status)
     }
 }
 
-// A22 -= L21 U12: one 64 x 64 tile of A22 per block, each thread a 4 x 4 patch, the
-// panel's K <= 64 columns staged in shared memory (L21 transposed)
-template <bool FULL>  // FULL: a whole panel (w = kLuNb), the inner loop without bounds
-__global__ void __launch_bounds__(kLuThreads)
-k_lu_gemm(int M, int k0, int w, float2 *A, const int *status)
+// ---- the trailing update on the tensor cores --------------------------------------
+// A22 -= L21 U12 with K = w <= 64, the operands in double-float (~48-bit significands).
+// The bf16 tensor-core products reach that precision by an exact split (Ozaki's scheme):
+// each row i of L21 is scaled by 2^-e_i (|l_ik| 2^-e_i < 1, e_i from the row's largest
+// entry), each column j of U12 by 2^-f_j, and the scaled values are cut into kOzS slices
+// of 8 bits, x = sum_s v_s 2^(-8(s+1)), v_s a rounded integer (|v_0| <= 256, later
+// |v_s| <= 128), exact in bf16.  A product of two slices is an integer below 2^16 and a
+// sum of 64 of them, over the (s, t) with s + t = d, stays below 2^24: exact in the
+// float accumulators of the MMA.  The update is then
+//   (L21 U12)_ij = 2^(e_i + f_j) sum_d 2^(-8(d+2)) P_d,ij,  P_d = sum_{s+t=d} L_s U_t^T,
+// with the pairs s + t > kOzD dropped (below 2^-48 of the row-times-column scale), and
+// each tile combines its kOzD + 1 accumulators in double-float.
+constexpr int kOzS = 6;              // slices per operand
+constexpr int kOzD = 5;              // slice pairs with s + t <= kOzD
+constexpr int kTcM = 128, kTcN = 64; // tile of A22 per CTA: 128 rows x 64 columns
+constexpr int kTcLBytes = kTcM * kLuNb * 2;  // one bf16 slice of a 128-row block
+constexpr int kTcUBytes = kTcN * kLuNb * 2;  // one bf16 slice of a 64-column block
+constexpr int kTcSmem = kOzS * (kTcLBytes + kTcUBytes);
+// instruction descriptor of tcgen05.mma kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N = 64, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+// element (r, k) of a K-major operand tile without swizzle, in bf16 units: 8 x 8 core
+// matrices of 8 rows x 16 bytes, the 8 K-adjacent cores of an 8-row group 128 bytes
+// apart (the descriptor's leading-dimension offset), the 8-row groups 1024 bytes apart
+// (its stride-dimension offset)
+__device__ __forceinline__ int core_off(int r, int k)
+{
+    return ((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor (no swizzle): start address, leading- and
+// stride-dimension byte offsets (all in 16-byte units), descriptor version 1
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred P1;\n mbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+                 " selp.b32 %0, 1, 0, P1;\n}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes, one lane per thread
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t u[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+                   "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]),
+                   "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(u[i]);
+}
+
+// 2^x as a float, 0 below the normal range (x above 127 does not occur: the entries
+// of S and its factors are far below 2^100)
+__device__ __forceinline__ float pow2f(int x)
+{
+    return x < -126 ? 0.f : __int_as_float((min(x, 127) + 127) << 23);
+}
+
+// the exponent e with max < 2^e <= 2 max (0 for max = 0)
+__device__ __forceinline__ int exp_above(float mx)
+{
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    return e;
+}
+
+// kOzS slices of the eight values x[0..7] (each scaled to |x| < 1), packed as bf16 into
+// out[s] (16 bytes: one row of a core matrix)
+__device__ __forceinline__ void oz_split8(df64 (&x)[8], uint4 (&out)[kOzS])
+{
+#pragma unroll
+    for (int sl = 0; sl < kOzS; sl++) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const float th = x[i].hi * 256.f, tl = x[i].lo * 256.f;
+            const float v = rintf(th);
+            df_two_sum(th - v, tl, x[i].hi, x[i].lo);  // th - v is exact
+            const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+            if (i & 1) w[i >> 1] |= b << 16;
+            else w[i >> 1] = b;
+        }
+        out[sl] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Slices of L21 = A[k1.., k0 .. k0 + w) (k1 = k0 + w), rows in 128-row blocks: 8 threads
+// a row, 8 columns each; Limg[rb][s] is the shared-memory image of slice s of block rb,
+// el[rr] the exponent of row k1 + rr.  Rows past M and columns past w give zeros.
+__global__ void __launch_bounds__(256)
+k_oz_slice_rows(int M, int k0, int w, const float2 *A, uint4 *Limg, int *el, const int *status)
 {
     if (lu_failed(status)) return;
-    extern __shared__ __align__(16) float2 gsm2[];
-    float2 *As = gsm2;                    // As[k * kLuPad + r] = L21[r][k]
-    float2 *Bs = gsm2 + kLuNb * kLuPad;   // Bs[k * kLuTs + c] = U12[k][c]
-    const int k1 = k0 + w;
-    const int i0 = k1 + blockIdx.y * kLuTs, j0 = k1 + blockIdx.x * kLuTs;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    for (int e = tid; e < kLuTs * w; e += blockDim.x) {
-        const int r = e / w, k = e % w, gi = i0 + r;
-        As[k * kLuPad + r] = gi < M ? A[(int64_t)gi * M + k0 + k] : make_float2(0.f, 0.f);
-    }
-    for (int e = tid; e < w * kLuTs; e += blockDim.x) {
-        const int k = e / kLuTs, c = e % kLuTs, gj = j0 + c;
-        Bs[k * kLuTs + c] = gj < M ? A[(int64_t)(k0 + k) * M + gj] : make_float2(0.f, 0.f);
-    }
-    df64 acc[4][4];
+    const int t = threadIdx.x, kg = t & 7;
+    const int rr = blockIdx.x * 32 + (t >> 3), row = k0 + w + rr;
+    df64 x[8];
+    unsigned key = 0;
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-        const int gi = i0 + ty * 4 + u;
+    for (int i = 0; i < 8; i++) {
+        const int k = kg * 8 + i;
+        const float2 v = (row < M && k < w) ? A[(int64_t)row * M + k0 + k] : make_float2(0.f, 0.f);
+        x[i] = df64(v.x, v.y, 0);
+        key = max(key, __float_as_uint(v.x) & 0x7fffffffu);
+    }
+    key = max(key, __shfl_xor_sync(0xffffffffu, key, 1));
+    key = max(key, __shfl_xor_sync(0xffffffffu, key, 2));
+    key = max(key, __shfl_xor_sync(0xffffffffu, key, 4));
+    const int e = exp_above(__uint_as_float(key));
+    const float sc = pow2f(-e);
 #pragma unroll
-        for (int v = 0; v < 4; v++) {
-            const int gj = j0 + tx * 4 + v;
-            acc[u][v] = (gi < M && gj < M) ? ld(A[(int64_t)gi * M + gj]) : df64(0.f);
+    for (int i = 0; i < 8; i++) x[i] = df_ldexp(x[i], sc);
+    uint4 out[kOzS];
+    oz_split8(x, out);
+    const int rb = rr >> 7, r = rr & 127;
+#pragma unroll
+    for (int sl = 0; sl < kOzS; sl++)
+        Limg[((size_t)(rb * kOzS + sl) * kTcLBytes + 2 * core_off(r, kg * 8)) / 16] = out[sl];
+    if (kg == 0) el[rr] = e;
+}
+
+// Slices of U12 = A[k0 .. k0 + w, k1 ..), columns in 64-column blocks: a block of 512
+// threads per column block, (column, 8 rows of K) per thread; Uimg[cb][s] as above,
+// eu[cc] the exponent of column k1 + cc.
+__global__ void __launch_bounds__(512)
+k_oz_slice_cols(int M, int k0, int w, const float2 *A, uint4 *Uimg, int *eu, const int *status)
+{
+    if (lu_failed(status)) return;
+    __shared__ unsigned red[8][kTcN];
+    const int t = threadIdx.x, jl = t & (kTcN - 1), kg = t >> 6;
+    const int cb = blockIdx.x, col = k0 + w + cb * kTcN + jl;
+    df64 x[8];
+    unsigned key = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int k = kg * 8 + i;
+        const float2 v = (col < M && k < w) ? A[(int64_t)(k0 + k) * M + col] : make_float2(0.f, 0.f);
+        x[i] = df64(v.x, v.y, 0);
+        key = max(key, __float_as_uint(v.x) & 0x7fffffffu);
+    }
+    red[kg][jl] = key;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; q++) key = max(key, red[q][jl]);
+    const int e = exp_above(__uint_as_float(key));
+    const float sc = pow2f(-e);
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = df_ldexp(x[i], sc);
+    uint4 out[kOzS];
+    oz_split8(x, out);
+#pragma unroll
+    for (int sl = 0; sl < kOzS; sl++)
+        Uimg[((size_t)(cb * kOzS + sl) * kTcUBytes + 2 * core_off(jl, kg * 8)) / 16] = out[sl];
+    if (kg == 0) eu[cb * kTcN + jl] = e;
+}
+
+// One 128 x 64 tile of A22 per CTA (8 warps).  One thread copies the row block's and
+// column block's slice images into shared memory with two bulk asynchronous copies and,
+// once they have landed (an mbarrier counting their bytes), issues the
+// 4 (kOzD + 1)(kOzD + 2)/2 MMAs (K = 16 each) into kOzD + 1 accumulators of 64 TMEM
+// columns; their completion is signalled on a second mbarrier.  Each thread then takes
+// 32 columns of one row of the tile from TMEM (warp q reads lanes 32 (q mod 4) ...,
+// columns 32 (q / 4) ...), combines the accumulators in double-float and subtracts the
+// product from A22.  Every wait is bounded: past the limit the CTA records a time-out,
+// waits once more (bounded) for its copies and MMAs, frees its TMEM and returns.
+constexpr int kTcThreads = 256;
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, unsigned lim)
+{
+    for (unsigned spins = 0; spins < lim; spins++)
+        if (mbar_test(mb, 0)) return true;
+    return false;
+}
+
+__global__ void __launch_bounds__(kTcThreads)
+k_lu_gemm_tc(int M, int k1, const uint4 *Limg, const uint4 *Uimg, const int *el, const int *eu,
+             float2 *A, int *status)
+{
+    if (lu_failed(status)) return;
+    extern __shared__ __align__(128) uint4 gsm_tc[];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) unsigned long long bar_ld, bar_mma;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rb = blockIdx.y, cb = blockIdx.x;
+    uint4 *sL = gsm_tc, *sU = gsm_tc + kOzS * kTcLBytes / 16;
+    const uint32_t mld = smem_u32(&bar_ld), mmm = smem_u32(&bar_mma);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mld), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mmm), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const unsigned lim = wait_limit(status, kLuSpins);
+    bool ok = true;
+    if (tid == 0) {
+        const uint32_t aL = smem_u32(sL), aU = smem_u32(sU);
+        const uint4 *gL = Limg + (size_t)rb * (kOzS * kTcLBytes / 16);
+        const uint4 *gU = Uimg + (size_t)cb * (kOzS * kTcUBytes / 16);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(mld), "r"(kTcSmem) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(aL), "l"(gL), "r"(kOzS * kTcLBytes), "r"(mld) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(aU), "l"(gU), "r"(kOzS * kTcUBytes), "r"(mld) : "memory");
+        ok = mbar_wait(mld, lim);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // descriptors of the slices' first K step; a K step of 16 advances the start
+            // address by 256 bytes, a slice by kTcLBytes or kTcUBytes (the address field
+            // counts 16-byte units)
+            const uint64_t dL = tc_desc(aL), dU = tc_desc(aU);
+#pragma unroll
+            for (int d = 0; d <= kOzD; d++)
+#pragma unroll
+                for (int sl = 0; sl <= d; sl++)
+#pragma unroll
+                    for (int j = 0; j < kLuNb / 16; j++)
+                        tc_mma(tmem + (uint32_t)(d * kTcN), dL + (uint64_t)((sl * kTcLBytes + j * 256) >> 4),
+                               dU + (uint64_t)(((d - sl) * kTcUBytes + j * 256) >> 4), (sl > 0 || j > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(mmm) : "memory");
+        } else {
+            atomicOr(status, LBF_DEV_TIMEOUT);
+            mbar_wait(mld, lim);  // the copies still in flight
+        }
+    }
+    if (tid == 0 && ok && !mbar_wait(mmm, lim)) {
+        ok = false;
+        atomicOr(status, LBF_DEV_TIMEOUT);
+        mbar_wait(mmm, lim);
+    }
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // 1. TMEM -> the products V_ij = sum_d P_d 2^(-8d) (times the row's scale) in
+    //    double-float, thread = row, into shared memory (the operands' space is free now)
+    const int quarter = warp & 3, half = warp >> 2;
+    const int rl = quarter * 32 + lane, i = k1 + rb * kTcM + rl;
+    const float ri = ok && i < M ? pow2f(el[rb * kTcM + rl] - 16) : 0.f;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    float2 *vt = (float2 *)gsm_tc;  // [kTcM][kTcN + 1]: V of row r, column c
+    constexpr int kVs = kTcN + 1;
+    for (int c = 0; c < 32; c += 16) {
+        float acc[kOzD + 1][16];
+#pragma unroll
+        for (int d = 0; d <= kOzD; d++) tc_ld16(trow + (uint32_t)(d * kTcN + c), acc[d]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            float h = acc[kOzD][q], l = 0.f;  // from the smallest term up
+#pragma unroll
+            for (int d = kOzD - 1; d >= 0; d--) {
+                float e2;
+                df_two_sum(acc[d][q], h * 0x1p-8f, h, e2);
+                l = e2 + l * 0x1p-8f;
+            }
+            const df64 v = df_fast(h, l);
+            vt[rl * kVs + half * 32 + c + q] = make_float2(v.hi * ri, v.lo * ri);
         }
     }
     __syncthreads();
-    // each product joins the sum by an error-free two-sum of the high parts; the low
-    // parts (the products' exact errors and the two-sums' errors) add into the low word,
-    // renormalised every 8 steps (12 float operations per multiply-add instead of 15)
-    for (int k0 = 0; k0 < w; k0 += 8) {
+    // 2. A22 -= V 2^f_j, lanes on consecutive columns of a row; all of a thread's loads
+    //    are issued before its stores (a store could alias a later load, so the compiler
+    //    would not move the loads up on its own)
+    if (ok) {
+        constexpr int kRows = kTcM * kTcN / kTcThreads;  // 32 rows per thread
+        const int jl = tid & (kTcN - 1), j = k1 + cb * kTcN + jl, r0 = tid >> 6;
+        const float cj = j < M ? pow2f(eu[cb * kTcN + jl]) : 0.f;
+        const int nrow = min(kTcM, M - (k1 + rb * kTcM));
+        float2 *ap = A + (int64_t)(k1 + rb * kTcM) * M + j;
+        const int64_t rs = (int64_t)(kTcThreads / kTcN) * M;
+        if (j < M) {
+            float2 av[kRows];
 #pragma unroll
-        for (int kk = 0; kk < 8; kk++) {
-            const int k = k0 + kk;
-            if (!FULL && k >= w) break;
-            df64 a[4], bv[4];
+            for (int q = 0; q < kRows; q++)
+                av[q] = r0 + 4 * q < nrow ? ap[r0 * (int64_t)M + q * rs] : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < 4; u++) a[u] = -ld(As[k * kLuPad + ty * 4 + u]);
-#pragma unroll
-            for (int v = 0; v < 4; v++) bv[v] = ld(Bs[k * kLuTs + tx * 4 + v]);
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-#pragma unroll
-                for (int v = 0; v < 4; v++) {
-                    const float p = __fmul_rn(a[u].hi, bv[v].hi);
-                    float e = __fmaf_rn(a[u].hi, bv[v].hi, -p);
-                    e = __fmaf_rn(a[u].hi, bv[v].lo, e);
-                    e = __fmaf_rn(a[u].lo, bv[v].hi, e);
-                    float sh, se;
-                    df_two_sum(acc[u][v].hi, p, sh, se);
-                    acc[u][v].hi = sh;
-                    acc[u][v].lo = __fadd_rn(acc[u][v].lo, __fadd_rn(se, e));
-                }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-#pragma unroll
-            for (int v = 0; v < 4; v++) acc[u][v] = df_fast(acc[u][v].hi, acc[u][v].lo);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-        const int gi = i0 + ty * 4 + u;
-        if (gi >= M) continue;
-#pragma unroll
-        for (int v = 0; v < 4; v++) {
-            const int gj = j0 + tx * 4 + v;
-            if (gj < M) A[(int64_t)gi * M + gj] = pk(acc[u][v]);
+            for (int q = 0; q < kRows; q++) {
+                const int r = r0 + 4 * q;
+                if (r >= nrow) break;
+                const float2 v = vt[r * kVs + jl];
+                const df64 res = df64(av[q].x, av[q].y, 0) - df64(v.x * cj, v.y * cj, 0);
+                ap[r0 * (int64_t)M + q * rs] = make_float2(res.hi, res.lo);
+            }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512) : "memory");
 }
+
 
 // Inverses of the diagonal blocks of L (unit lower) and U (upper), one kLuTs x kLuTs
 // block per CUDA block, by substitution against the identity (columns in parallel);
@@ -592,11 +843,17 @@ __global__ void k_lu_scatter2(int M, const int *__restrict__ perm, const float2 
 }  // namespace
 
 // Scratch of the factorisation (plan time): the panel candidates and the grid barrier.
-size_t lbf_lu_scratch_bytes()
+// row and column blocks of the trailing update's slice images for an M x M matrix
+static int64_t oz_row_blocks(int M) { return (M + kTcM - 1) / kTcM; }
+static int64_t oz_col_blocks(int M) { return (M + kTcN - 1) / kTcN; }
+
+size_t lbf_lu_scratch_bytes(int M)
 {
     return 256 + sizeof(unsigned) * 2 * kLuMaxPanelBlocks + sizeof(int) * 2 * kLuMaxPanelBlocks +
            sizeof(float2) * 2 * (size_t)kLuMaxPanelBlocks * kLuNb + sizeof(float2) * 2 * kLuNb +
-           sizeof(GridBarrier) + 1024;
+           sizeof(GridBarrier) + (size_t)oz_row_blocks(M) * kOzS * kTcLBytes +
+           (size_t)oz_col_blocks(M) * kOzS * kTcUBytes + sizeof(int) * (size_t)(oz_row_blocks(M) * kTcM) +
+           sizeof(int) * (size_t)(oz_col_blocks(M) * kTcN) + 8 * 256;
 }
 
 int lbf_lu_sync_words(int M) { return 3 + (M + kLuTs - 1) / kLuTs; }
@@ -604,7 +861,7 @@ int lbf_lu_sync_words(int M) { return 3 + (M + kLuTs - 1) / kLuTs; }
 int64_t lbf_lu_dinv_entries(int M) { return 2 * (int64_t)((M + kLuTs - 1) / kLuTs) * kLuTs * kLuTs; }
 
 // S (double, M x M, in pl->Sinv) -> its LU factors in place (double-float), pl->lu_piv,
-// pl->lu_perm; on stream s.  scratch: lbf_lu_scratch_bytes() bytes of device memory.
+// pl->lu_perm; on stream s.  scratch: lbf_lu_scratch_bytes(M) bytes of device memory.
 int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
 {
     const int M = pl->M;
@@ -621,6 +878,10 @@ int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
     float2 *cval = (float2 *)take(sizeof(float2) * 2 * (size_t)kLuMaxPanelBlocks * kLuNb);
     float2 *rjval = (float2 *)take(sizeof(float2) * 2 * kLuNb);
     GridBarrier *bar = (GridBarrier *)take(sizeof(GridBarrier));
+    uint4 *Limg = (uint4 *)take((size_t)oz_row_blocks(M) * kOzS * kTcLBytes);
+    uint4 *Uimg = (uint4 *)take((size_t)oz_col_blocks(M) * kOzS * kTcUBytes);
+    int *el = (int *)take(sizeof(int) * (size_t)(oz_row_blocks(M) * kTcM));
+    int *eu = (int *)take(sizeof(int) * (size_t)(oz_col_blocks(M) * kTcN));
     int *status = pl->dev_status;
     LBF_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), s));
     LBF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
@@ -639,8 +900,7 @@ int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
     const size_t tile_smem = sizeof(float2) * 2 * kLuNb * kLuPad;
     LBF_CUDA(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(k_lu_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
-    LBF_CUDA(cudaFuncSetAttribute(k_lu_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
-    LBF_CUDA(cudaFuncSetAttribute(k_lu_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+    LBF_CUDA(cudaFuncSetAttribute(k_lu_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
     for (int k0 = 0; k0 < M; k0 += kLuNb) {
         const int w = std::min(kLuNb, M - k0);
         const int rows = M - k0;
@@ -668,12 +928,13 @@ int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
         if (rest > 0) {
             const int nt = (rest + kLuTs - 1) / kLuTs;
             LBF_LAUNCH_P(LBF_KERNEL_LU_UPDATE, k_lu_trsm, nt, kLuThreads, tile_smem, s, M, k0, w, A, status);
-            if (w == kLuNb)
-                LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_lu_gemm<true>, dim3(nt, nt), kLuThreads, tile_smem, s, M,
-                             k0, w, A, status);
-            else
-                LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_lu_gemm<false>, dim3(nt, nt), kLuThreads, tile_smem, s, M,
-                             k0, w, A, status);
+            const int nrb = (rest + kTcM - 1) / kTcM, ncb = (rest + kTcN - 1) / kTcN;
+            LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_oz_slice_rows, nrb * (kTcM / 32), 256, 0, s, M, k0, w, A,
+                         Limg, el, status);
+            LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_oz_slice_cols, ncb, 512, 0, s, M, k0, w, A, Uimg, eu,
+                         status);
+            LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_lu_gemm_tc, dim3(ncb, nrb), kTcThreads, kTcSmem, s, M, k0 + w, Limg,
+                         Uimg, el, eu, A, status);
         }
         LBF_CHECK_LAUNCH();
     }
