@@ -226,31 +226,42 @@ def run_reference(args):
 
 # ---- our arm ---------------------------------------------------------------------------
 
+# the sources that decide the FMM passes' memory traffic (their kernels, launch shapes,
+# tree and lists); the DRAM bytes of profiles/traffic.json are keyed to them
+FMM_SOURCES = ("lbf_fmm_tpl.cuh", "lbf_fmm.cu", "lbf_tree.cu", "lbf_border.cu", "lbf_df64.cuh",
+               "lbf_internal.cuh")
+
+
 def src_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1306_0612_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in FMM_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def kernel_work(name, c, bc, P, P32, N):
     """(algorithmic work of one operator application, unit) per the FMM's
-    operation counts: 11 flops per near pair, 8(p+1) per node for P2M and L2P and
-    per (node, box) for M2P/P2L, 8(p+1)^2 per translation, 10 per node to combine.
-    Multiplier potential: 8 flops per local-expansion term evaluated at a node
-    (one expansion per node in double, one per ancestor level >= 2 in float),
-    8 per (node, centre) pair summed directly (log counted as one flop, like the
-    division of P2P), 10 per node to combine."""
+    operation counts, Q = p + 1 terms: 11 flops per near pair, 8Q per node for P2M and
+    L2P and per (node, box) for M2P/P2L, 10 per node to combine; a translation in the
+    binomial factorisation the kernels use: the real binomial matrix on the complex
+    coefficients (4 flops an entry) between two diagonal complex scalings (6Q and 8Q),
+    so 4Q^2 + 14Q for M2L and 2Q(Q+1) + 14Q for M2M and L2L, whose binomial matrix is
+    triangular.  Multiplier potential: 8 flops per local-expansion term evaluated at a
+    node (one expansion per node in double, one per ancestor level >= 2 in float), 8 per
+    (node, centre) pair summed directly (log counted as one flop, like the division of
+    P2P), 10 per node to combine."""
     f32 = name.endswith("32")
     base = name[:-2] if f32 else name
     Q = P32 if f32 else P
+    m2l = 4 * Q * Q + 14 * Q
+    tri = 2 * Q * (Q + 1) + 14 * Q
     if base == "leaf":
         return 11 * c["p2p_pairs"] + 8 * Q * N + 8 * Q * c["w_pairs"] + 10 * N, "TFLOP/s"
     if base == "down":
-        return 8 * Q * Q * (c["m2l"] + c["l2l"]) + 8 * Q * c["x_pairs"], "TFLOP/s"
+        return m2l * c["m2l"] + tri * c["l2l"] + 8 * Q * c["x_pairs"], "TFLOP/s"
     if base == "up":
-        return 8 * Q * N + 8 * Q * Q * c["m2m"], "TFLOP/s"
+        return 8 * Q * N + tri * c["m2m"], "TFLOP/s"
     if base == "direct":
         return 11 * N * (N - 1), "TFLOP/s"
     if base == "esum" and bc:
@@ -258,7 +269,7 @@ def kernel_work(name, c, bc, P, P32, N):
             terms = 8 * bc["terms32"] * bc["walk_expansions"]
         else:  # P2L per (box, centre) pair, L2L per box, L2P per node
             Pe = bc["terms"]
-            terms = 8 * Pe * bc["p2l_pairs"] + 8 * Pe * Pe * c["l2l"] + 8 * Pe * N
+            terms = 8 * Pe * bc["p2l_pairs"] + (2 * Pe * (Pe + 1) + 14 * Pe) * c["l2l"] + 8 * Pe * N
         return (terms + 8 * bc["direct_pairs"] + 8 * bc["global_centres"] * N + 10 * N,
                 "TFLOP/s")
     return None, None
@@ -349,14 +360,16 @@ def traced(L, fn):
     return prof
 
 
-def traffic_for(kernel):
+def traffic_for(kernel, p, leaf):
+    """DRAM bytes per launch of an FMM pass from the ncu captures in profiles/traffic.json,
+    for the same kernel sources, expansion order and leaf size; else None."""
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tp):
         return None
     tj = json.load(open(tp))
     if tj.get("src_hash") != src_hash():
         return None
-    return tj.get("kernels", {}).get(kernel, {}).get("bytes_per_launch")
+    return tj.get("kernels", {}).get(f"{kernel}@p{p}/leaf{leaf}", {}).get("bytes_per_launch")
 
 
 def roofline_of(L, prof, plan, opt, g, n64, n32, fmm64):
@@ -385,7 +398,8 @@ def roofline_of(L, prof, plan, opt, g, n64, n32, fmm64):
                       f"ceiling is {FP32_PEAK_TFLOPS / DF64_FLOPS_PER_FLOP:.2f} TFLOP/s of double flops")
     ach = rate / 1e12
     return ({"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": unit,
-             "frac": ach / peak, "traffic": traffic_for(dom + ("_df64" if fmm64 and not f32 else "")),
+             "frac": ach / peak,
+             "traffic": traffic_for(dom + ("_df64" if fmm64 and not f32 else ""), info["p"], opt.leaf_size),
              "peak_source": src_p, "work_per_launch": work, "ms_per_launch": per_launch_ms},
             counts, bcounts, info)
 

@@ -83,3 +83,27 @@ def test_lu_solve_many_islands_matches_gauss_jordan(precision, tol, agree):
     assert rel_l2(a_lu, a_gj) < agree
     if precision == L.LBF_PRECISION_FP64:  # the same Krylov iteration to rounding
         assert abs(it_lu - it_gj) <= 2
+
+
+@pytest.mark.parametrize("M,nodes", [(1100, 32), (2500, 128)])
+def test_preconditioner_reproduces_multiplier_only_vectors(M, nodes):
+    """P = [[I, E], [F, D]] agrees with A = [[I + 2K, E], [F, D]] on vectors [0; y], so
+    P^-1 A [0; y] = [0; y] whatever S = D - F E is: the factors of S (the LU's trailing
+    updates on the tensor cores included) are checked through S^-1 S y = y at sizes beyond
+    the dense oracle.  Any S^-1 in double carries about cond(S) eps of S y's rounding (up
+    to ~1e-8 here), so the LU path (one refinement step against the double S) is held to
+    ten times the Gauss-Jordan inverse's own deviation, and both to 1e-6."""
+    g = wl.star_caps(7, M, nodes)
+    y = np.random.default_rng(11).standard_normal(M)
+    v = np.concatenate([np.zeros(g.N), y])
+    err, sig = {}, {}
+    for schur in (L.LBF_SCHUR_LU, L.LBF_SCHUR_GJ):
+        p = plan_for(g, schur=schur)
+        out = zeros(g.N + g.M)
+        L.lbf_apply(p, L.LBF_OP_PRECONDITIONED, dev(v), out)
+        o = host(out)
+        err[schur] = np.linalg.norm(o[g.N:] - y) / np.linalg.norm(y)
+        sig[schur] = np.linalg.norm(o[:g.N]) / np.sqrt(g.N) / (np.linalg.norm(y) / np.sqrt(M))
+    assert err[L.LBF_SCHUR_GJ] < 1e-6 and sig[L.LBF_SCHUR_GJ] < 1e-6, (err, sig)
+    assert err[L.LBF_SCHUR_LU] < max(1e-9, 10 * err[L.LBF_SCHUR_GJ]), err
+    assert sig[L.LBF_SCHUR_LU] < max(1e-9, 10 * sig[L.LBF_SCHUR_GJ]), sig
