@@ -226,10 +226,10 @@ def run_reference(args):
 
 # ---- our arm ---------------------------------------------------------------------------
 
-# the sources that decide the FMM passes' memory traffic (their kernels, launch shapes,
-# tree and lists); the DRAM bytes of profiles/traffic.json are keyed to them
-FMM_SOURCES = ("lbf_fmm_tpl.cuh", "lbf_fmm.cu", "lbf_tree.cu", "lbf_border.cu", "lbf_df64.cuh",
-               "lbf_internal.cuh")
+# the sources that decide the memory traffic of the FMM passes (up, down, leaf: their
+# kernels, launch shapes, tree and lists); the DRAM bytes of profiles/traffic.json are
+# keyed to them
+FMM_SOURCES = ("lbf_fmm_tpl.cuh", "lbf_fmm.cu", "lbf_tree.cu", "lbf_df64.cuh", "lbf_internal.cuh")
 
 
 def src_hash():

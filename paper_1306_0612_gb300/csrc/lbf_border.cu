@@ -518,13 +518,44 @@ __global__ void k_mp_p2l(int64_t nbox, int P, int M, const int32_t *__restrict__
             }
             ym = (R)y[m];
         }
-        cz<R> pw{ym * tau.x, ym * tau.y};  // y tau^l, l = 1
-        for (int l = 1; l < P; l++) {
-            T[l * 32 + lane] = pw;
-            pw = zmul(pw, tau);
+        const int nin = min(32, ptr[b + 1] - base);  // the chunk's centres (often a few)
+        bool grouped = false;
+        if constexpr (std::is_same<R, double>::value) grouped = nin <= 16 && P <= 33;
+        if (grouped) {
+            // few centres (most boxes): G lanes per centre (the largest power of two with
+            // nin G <= 32), lane g of a centre forming the powers l = g L + 1 .. (g + 1) L,
+            // L = 32 / G.  Its first power comes from tau^L (log2 L squarings) and an
+            // exclusive product of tau^L over the group's lanes below it (log2 G steps):
+            // about 7 + L complex products a lane instead of P - 1 with most lanes idle.
+            int G = 2;
+            while (G * 2 * nin <= 32) G *= 2;
+            const int L = 32 / G, c = lane / G, g = lane % G, cl = c < nin ? c : 0;
+            const cz<R> tc{__shfl_sync(0xffffffffu, tau.x, cl), __shfl_sync(0xffffffffu, tau.y, cl)};
+            const R yc = __shfl_sync(0xffffffffu, ym, cl);
+            cz<R> tl = tc;
+            for (int q = 1; q < L; q <<= 1) tl = zmul(tl, tl);
+            cz<R> x = g == 0 ? cz<R>{(R)1, (R)0} : tl;  // tau^(g L) after the scan
+            if constexpr (std::is_same<R, double>::value) {
+                for (int d = 1; d < G; d <<= 1) {
+                    const cz<R> y2{__shfl_up_sync(0xffffffffu, x.x, d, G),
+                                   __shfl_up_sync(0xffffffffu, x.y, d, G)};
+                    if (g >= d) x = zmul(x, y2);
+                }
+            }
+            cz<R> pw = zmul(x, cz<R>{yc * tc.x, yc * tc.y});  // y tau^(g L + 1)
+            for (int q = 0; q < L; q++) {
+                const int l = g * L + 1 + q;
+                if (l < P && c < nin) T[l * 32 + c] = pw;
+                pw = zmul(pw, tc);
+            }
+        } else {
+            cz<R> pw{ym * tau.x, ym * tau.y};  // y tau^l, l = 1
+            for (int l = 1; l < P; l++) {
+                T[l * 32 + lane] = pw;
+                pw = zmul(pw, tau);
+            }
         }
         __syncwarp();
-        const int nin = min(32, ptr[b + 1] - base);  // the chunk's centres (often a few)
         for (int l = lane; l < P; l += 32) {
             if (l == 0) continue;
             cz<R> s{0, 0};
