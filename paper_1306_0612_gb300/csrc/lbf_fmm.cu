@@ -545,7 +545,7 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     }
     const int lw = pl->opt.p2p_warps > 0 ? pl->opt.p2p_warps : fmm::kLeafWarps;
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, lw), 32 * lw,
-                 fmm::leaf_smem<R>(lw), s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
+                 (fmm::leaf_smem<R, MODE>(lw)), s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
                  sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf, walk ? 0 : 1,
                  split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
@@ -575,7 +575,7 @@ int lbf_fmm_init_attrs()
                                   (int)(sizeof(int32_t) * 2 * kEvalFront * kEvalWarps)));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_down<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     // the leaf pass: up to 8 warps of staged near-field sources
-    const int leaf_cap = (int)fmm::leaf_smem<df64>(8);
+    const int leaf_cap = (int)fmm::leaf_smem<double, fmm::kLeafForward>(8);
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<double, fmm::kLeafForward>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<double, fmm::kLeafTranspose>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));
     LBF_CUDA(cudaFuncSetAttribute(fmm::k_leaf<double, fmm::kLeafDeriv>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_cap));

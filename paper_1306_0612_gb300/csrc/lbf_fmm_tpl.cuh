@@ -354,8 +354,12 @@ constexpr unsigned kGrab = 1;
 // Downward pass for one level (see lbf_fmm.cu): L2L + M2L (V) + P2L (X).
 // P2L lanes take source nodes and run the power recurrence; their terms go
 // through shared memory and lanes then take coefficients and sum in node order.
+// Registers are held for three resident blocks of up to 8 warps per SM in float (a
+// latency-bound pass) and two in double and double-float (whose shared memory allows two).
+template <typename R> constexpr int kDownMinBlocks = std::is_same<R, float>::value ? 3 : 2;
 template <typename R>
-__global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level,
+__global__ void __launch_bounds__(256, kDownMinBlocks<R>)
+k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level,
                        const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
                        const int32_t *__restrict__ parent, const int32_t *__restrict__ vlist,
                        const int32_t *__restrict__ nv, const int32_t *__restrict__ xlist,
@@ -479,93 +483,100 @@ __global__ void k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level
         accF0.x += __shfl_down_sync(0xffffffffu, accF0.x, 16);
         accF0.y += __shfl_down_sync(0xffffffffu, accF0.y, 16);
         if (lane >= 16) accF0 = mk<R>(0, 0);
-    } else if (std::is_same<R, double>::value && nv[b] >= 4) {
-        // Native double, four or more V-list boxes: a masked lane occupies the double pipe
-        // like an active one, so the nv x P (box, coefficient) slots run flattened, 32 at a
-        // time, instead of a box at a time on P of the 32 lanes.  The scaled multipoles
-        // t^k a_k of all the boxes go to shared memory first; slot (v, l) forms
-        // sum_k C(k+l, l) t_v^k a_{v,k} and adds (-1)^l t_v^(l+1) times it into the
-        // coefficient l of a per-warp accumulator.  Lanes i and i + P of a round hold the
-        // same l (P >= 17 here, so no third): they add in two steps, so every coefficient
-        // takes its boxes in list order, the same operations in the same order as the
-        // box-at-a-time loop.
-        const int nvb = nv[b];
-        int vs = 0, vo = 0;
-        if (lane < nvb) {
-            vs = vlist[b * 27 + lane];
-            vo = (bx - ix[vs] + 3) * 7 + (by - iy[vs] + 3);
-        }
-        const int ns = nvb * P;
-        cx<R> *Af = T;  // nv x P scaled multipoles (T holds 32 P)
-        for (int s0 = 0; s0 < ns; s0 += 32) {
-            const int sl = s0 + lane, v = sl / P, k = sl - v * P;
-            const int src = __shfl_sync(0xffffffffu, vs, v & 31);
-            const int o = __shfl_sync(0xffffffffu, vo, v & 31);
-            if (sl < ns)
-                Af[sl] = cmul(mp[(int64_t)src * P + k], tpow[(size_t)o * (LBF_MAX_TERMS + 1) + k]);
-        }
-        for (int l = lane; l < P; l += 32) A[l] = mk<R>(0, 0);
-        __syncwarp();
-        for (int s0 = 0; s0 < ns; s0 += 32) {
-            const int sl = s0 + lane, v = sl / P, l = sl - v * P;
-            const int o = __shfl_sync(0xffffffffu, vo, v & 31);
-            const bool on = sl < ns;
-            cx<R> sa = mk<R>(0, 0);
-            if (on) {
-                const cx<R> *av = Af + v * P;
-                for (int k = 0; k < P; k++) {
-                    const cx<R> a = av[k];
-                    const R c = Cm[k * P + l];
-                    sa.x = fm(c, a.x, sa.x);
-                    sa.y = fm(c, a.y, sa.y);
-                }
-            }
-            cx<R> f = on ? tpow[(size_t)o * (LBF_MAX_TERMS + 1) + l + 1] : mk<R>(0, 0);
-            if (l & 1) { f.x = -f.x; f.y = -f.y; }
-            if (on && lane < P) A[l] = cfma(f, sa, A[l]);
-            __syncwarp();
-            if (on && lane >= P) A[l] = cfma(f, sa, A[l]);
-            __syncwarp();
-        }
-        if (l0 < P) accF0 = A[l0];
-        if (l1 < P) accF1 = A[l1];
-        __syncwarp();
     } else {
-        // V-list records loaded once (a lane per entry); with P <= 32 the next box's
-        // coefficients are fetched one step ahead
-        const int nvb = nv[b];
-        int vs = 0, vo = 0;
-        if (lane < nvb) {
-            vs = vlist[b * 27 + lane];
-            vo = (bx - ix[vs] + 3) * 7 + (by - iy[vs] + 3);
+        bool done = false;
+        if constexpr (std::is_same<R, double>::value) {
+            if (nv[b] >= 4) {
+                done = true;
+                // Native double, four or more V-list boxes: a masked lane occupies the double pipe
+                // like an active one, so the nv x P (box, coefficient) slots run flattened, 32 at a
+                // time, instead of a box at a time on P of the 32 lanes.  The scaled multipoles
+                // t^k a_k of all the boxes go to shared memory first; slot (v, l) forms
+                // sum_k C(k+l, l) t_v^k a_{v,k} and adds (-1)^l t_v^(l+1) times it into the
+                // coefficient l of a per-warp accumulator.  Lanes i and i + P of a round hold the
+                // same l (P >= 17 here, so no third): they add in two steps, so every coefficient
+                // takes its boxes in list order, the same operations in the same order as the
+                // box-at-a-time loop.
+                const int nvb = nv[b];
+                int vs = 0, vo = 0;
+                if (lane < nvb) {
+                    vs = vlist[b * 27 + lane];
+                    vo = (bx - ix[vs] + 3) * 7 + (by - iy[vs] + 3);
+                }
+                const int ns = nvb * P;
+                cx<R> *Af = T;  // nv x P scaled multipoles (T holds 32 P)
+                for (int s0 = 0; s0 < ns; s0 += 32) {
+                    const int sl = s0 + lane, v = sl / P, k = sl - v * P;
+                    const int src = __shfl_sync(0xffffffffu, vs, v & 31);
+                    const int o = __shfl_sync(0xffffffffu, vo, v & 31);
+                    if (sl < ns)
+                        Af[sl] = cmul(mp[(int64_t)src * P + k], tpow[(size_t)o * (LBF_MAX_TERMS + 1) + k]);
+                }
+                for (int l = lane; l < P; l += 32) A[l] = mk<R>(0, 0);
+                __syncwarp();
+                for (int s0 = 0; s0 < ns; s0 += 32) {
+                    const int sl = s0 + lane, v = sl / P, l = sl - v * P;
+                    const int o = __shfl_sync(0xffffffffu, vo, v & 31);
+                    const bool on = sl < ns;
+                    cx<R> sa = mk<R>(0, 0);
+                    if (on) {
+                        const cx<R> *av = Af + v * P;
+                        for (int k = 0; k < P; k++) {
+                            const cx<R> a = av[k];
+                            const R c = Cm[k * P + l];
+                            sa.x = fm(c, a.x, sa.x);
+                            sa.y = fm(c, a.y, sa.y);
+                        }
+                    }
+                    cx<R> f = on ? tpow[(size_t)o * (LBF_MAX_TERMS + 1) + l + 1] : mk<R>(0, 0);
+                    if (l & 1) { f.x = -f.x; f.y = -f.y; }
+                    if (on && lane < P) A[l] = cfma(f, sa, A[l]);
+                    __syncwarp();
+                    if (on && lane >= P) A[l] = cfma(f, sa, A[l]);
+                    __syncwarp();
+                }
+                if (l0 < P) accF0 = A[l0];
+                if (l1 < P) accF1 = A[l1];
+                __syncwarp();
+            }
         }
-        cx<R> mnext = mk<R>(0, 0);
-        const int sfirst = __shfl_sync(0xffffffffu, vs, 0);
-        if (P <= 32 && nvb > 0 && lane < P) mnext = mp[(int64_t)sfirst * P + lane];
-        for (int vq = 0; vq < nvb; vq++) {
-            const int s = __shfl_sync(0xffffffffu, vs, vq);
-            const int o = __shfl_sync(0xffffffffu, vo, vq);
-            const int sn = __shfl_sync(0xffffffffu, vs, (vq + 1) & 31);
-            const cx<R> *tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
-            if (P <= 32) {
-                const cx<R> mcur = mnext;
-                if (vq + 1 < nvb && lane < P) mnext = mp[(int64_t)sn * P + lane];
-                if (lane < P) A[lane] = cmul(mcur, tp[lane]);
-            } else {
-                for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
+        if (!done) {
+            // V-list records loaded once (a lane per entry); with P <= 32 the next box's
+            // coefficients are fetched one step ahead
+            const int nvb = nv[b];
+            int vs = 0, vo = 0;
+            if (lane < nvb) {
+                vs = vlist[b * 27 + lane];
+                vo = (bx - ix[vs] + 3) * 7 + (by - iy[vs] + 3);
             }
-            __syncwarp();
-            cx<R> s0, s1;
-            coef_sums(A, Cm, P, lc0, lc1, P > 32, s0, s1);
-            cx<R> f0 = tp[l0 + 1];
-            if (l0 & 1) { f0.x = -f0.x; f0.y = -f0.y; }
-            accF0 = cfma(f0, s0, accF0);
-            if (l1 < P) {
-                cx<R> f1 = tp[l1 + 1];
-                if (l1 & 1) { f1.x = -f1.x; f1.y = -f1.y; }
-                accF1 = cfma(f1, s1, accF1);
+            cx<R> mnext = mk<R>(0, 0);
+            const int sfirst = __shfl_sync(0xffffffffu, vs, 0);
+            if (P <= 32 && nvb > 0 && lane < P) mnext = mp[(int64_t)sfirst * P + lane];
+            for (int vq = 0; vq < nvb; vq++) {
+                const int s = __shfl_sync(0xffffffffu, vs, vq);
+                const int o = __shfl_sync(0xffffffffu, vo, vq);
+                const int sn = __shfl_sync(0xffffffffu, vs, (vq + 1) & 31);
+                const cx<R> *tp = tpow + (size_t)o * (LBF_MAX_TERMS + 1);
+                if (P <= 32) {
+                    const cx<R> mcur = mnext;
+                    if (vq + 1 < nvb && lane < P) mnext = mp[(int64_t)sn * P + lane];
+                    if (lane < P) A[lane] = cmul(mcur, tp[lane]);
+                } else {
+                    for (int k = lane; k < P; k += 32) A[k] = cmul(mp[(int64_t)s * P + k], tp[k]);
+                }
+                __syncwarp();
+                cx<R> s0, s1;
+                coef_sums(A, Cm, P, lc0, lc1, P > 32, s0, s1);
+                cx<R> f0 = tp[l0 + 1];
+                if (l0 & 1) { f0.x = -f0.x; f0.y = -f0.y; }
+                accF0 = cfma(f0, s0, accF0);
+                if (l1 < P) {
+                    cx<R> f1 = tp[l1 + 1];
+                    if (l1 & 1) { f1.x = -f1.x; f1.y = -f1.y; }
+                    accF1 = cfma(f1, s1, accF1);
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
     // P2L: (-1)^l sum_j q_j tau_j^(l+1), tau_j = r / (c - xi_j)  (times 1/r below)
@@ -772,9 +783,10 @@ template <typename R> struct LeafSrc {
     cx<R> z, q;
 };
 // dynamic shared memory of the leaf kernel for lw warps per block
-template <typename R> constexpr size_t leaf_smem(int lw)
+template <typename R, int MODE> constexpr size_t leaf_smem(int lw)
 {
-    return (size_t)lw * (kSrcChunk * sizeof(LeafSrc<R>) + kLeafExtra);
+    return (size_t)lw * (kSrcChunk * sizeof(LeafSrc<R>) +
+                         (std::is_same<R, double>::value && MODE == 0 ? kLeafExtra : 0));
 }
 __device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
 __device__ __forceinline__ bool positive(double x) { return x > 0.0; }
