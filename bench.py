@@ -399,7 +399,8 @@ def roofline_of(L, prof, plan, opt, g, n64, n32, fmm64):
     ach = rate / 1e12
     return ({"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": unit,
              "frac": ach / peak,
-             "traffic": traffic_for(dom + ("_df64" if fmm64 and not f32 else ""), info["p"], opt.leaf_size),
+             "traffic": traffic_for(dom + ("_df64" if fmm64 and not f32 else ""),
+                                    opt.p32 if f32 else info["p"], opt.leaf_size),
              "peak_source": src_p, "work_per_launch": work, "ms_per_launch": per_launch_ms},
             counts, bcounts, info)
 
