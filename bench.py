@@ -392,7 +392,8 @@ def roofline_of(L, prof, plan, opt, g, n64, n32, fmm64):
         peak, src_p = FP32_PEAK_TFLOPS, "FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
     else:
         peak = FP64_PEAK_TFLOPS
-        src_p = "nominal FP64 of the recipe table (MEASURED_PEAKS.json has HBM and bf16 only)"
+        src_p = ("nominal FP64: 152 SMs x 2 double multiply-adds per clock x 2.07 GHz (no measured "
+                 "FP64 peak is available)")
         if fmm64 and dom in ("up", "down", "leaf"):
             src_p += ("; this kernel runs double-float arithmetic on the FP32 pipes, whose own "
                       f"ceiling is {FP32_PEAK_TFLOPS / DF64_FLOPS_PER_FLOP:.2f} TFLOP/s of double flops")
