@@ -653,7 +653,7 @@ __global__ void k_mp_chain(int64_t nbox, int P, const int32_t *__restrict__ pare
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tl = (P * P * (int)sizeof(R) + 15) / 16 * 16;
     R *Cd = (R *)smr;  // Cd[k*P + l] = C(k, l) (0 for k < l)
-    cz<R> *A = (cz<R> *)(smr + tl) + (size_t)wid * P;
+    cz<R> *A = (cz<R> *)(smr + tl) + (size_t)wid * 2 * P;  // two boxes a warp (below)
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
         const int k = e / P, l = e % P;
         Cd[e] = k >= l ? binom[k * LBF_MAX_TERMS + l] : R(0);
@@ -663,66 +663,135 @@ __global__ void k_mp_chain(int64_t nbox, int P, const int32_t *__restrict__ pare
     unsigned epoch = 0;
     if (lane == 0) epoch = *(volatile unsigned *)&pull[2];
     epoch = __shfl_sync(0xffffffffu, epoch, 0);
-    const int l0 = lane, l1 = lane + 32;
-    const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
-    for (;;) {
-        unsigned bi = 0;
-        if (lane == 0) bi = atomicAdd(&pull[3], 1u);
-        const int64_t b = (int64_t)__shfl_sync(0xffffffffu, bi, 0);
-        if (b >= nbox) break;
-        if (level[b] >= 3) {
-            const int p = parent[b];
-            if (lane == 0) {
-                unsigned spins = 0;
-                const unsigned lim = wait_limit(status, kChainSpins);
-                while (*(volatile unsigned *)&done[p] != epoch + 1u)
-                    if (++spins > lim) {
-                        atomicOr(status, LBF_DEV_TIMEOUT);
-                        break;
+    if (P <= 32) {
+        // Two boxes a warp, one per half-warp.  The shift matrix C(k, l) (k >= l) is
+        // triangular: lane j of a half sums the rows l = j and l = P - 1 - j, P + 1 terms in
+        // one loop (it moves to the second row inside the loop), so a half-warp does a box's
+        // shift in P + 1 steps where a warp with a row per lane would take P steps for one box
+        // with half of its terms zero.  Each half waits for its own box's parent; when that
+        // parent is the other half's box, the other half marks it done first.
+        const int hf = lane >> 4, j = lane & 15;
+        const unsigned hmask = hf ? 0xffff0000u : 0x0000ffffu;
+        const int nr = (P + 1) / 2;  // lanes of a half with rows
+        const int r1 = j < nr ? j : 0, r2 = P - 1 - r1, n1 = P - r1;
+        cz<R> *Ah = A + hf * P;
+        for (;;) {
+            unsigned bi = 0;
+            if (lane == 0) bi = atomicAdd(&pull[3], 2u);
+            const int64_t b0 = (int64_t)__shfl_sync(0xffffffffu, bi, 0);
+            if (b0 >= nbox) break;
+            const int64_t b = b0 + hf;
+            if (b < nbox) {
+                if (level[b] >= 3) {
+                    const int p = parent[b];
+                    if (j == 0) {
+                        unsigned spins = 0;
+                        const unsigned lim = wait_limit(status, kChainSpins);
+                        while (*(volatile unsigned *)&done[p] != epoch + 1u)
+                            if (++spins > lim) {
+                                atomicOr(status, LBF_DEV_TIMEOUT);
+                                break;
+                            }
                     }
-            }
-            __syncwarp();
-            __threadfence();
-            const int d = (ix[b] & 1) + 2 * (iy[b] & 1);
-            const cz<R> *dp = dtab + (size_t)d * (LBF_MAX_TERMS + 1);
-            const cz<R> *inv = dtab + (size_t)(4 + d) * (LBF_MAX_TERMS + 1);
-            for (int k = lane; k < P; k += 32) {
-                const cz<R> pk = ldcg_cz(&loc[(int64_t)p * P + k]);
-                A[k] = zmul(pk, dp[k]);
-            }
-            __syncwarp();
-            cz<R> s0{0, 0}, s1{0, 0};
-            // the second coefficient's sum only when P > 32: a test inside the loop leaves
-            // predicated-off multiply-adds that still occupy the double pipe
-            if (P > 32) {
-                for (int k = 0; k < P; k++) {
-                    const cz<R> a = A[k];
-                    const R c0 = Cd[k * P + lc0], c1 = Cd[k * P + lc1];
-                    s0.x = fmr(c0, a.x, s0.x);
-                    s0.y = fmr(c0, a.y, s0.y);
-                    s1.x = fmr(c1, a.x, s1.x);
-                    s1.y = fmr(c1, a.y, s1.y);
+                    __syncwarp(hmask);
+                    __threadfence();
+                    const int d = (ix[b] & 1) + 2 * (iy[b] & 1);
+                    const cz<R> *dp = dtab + (size_t)d * (LBF_MAX_TERMS + 1);
+                    const cz<R> *inv = dtab + (size_t)(4 + d) * (LBF_MAX_TERMS + 1);
+                    for (int k = j; k < P; k += 16) {
+                        const cz<R> pk = ldcg_cz(&loc[(int64_t)p * P + k]);
+                        Ah[k] = zmul(pk, dp[k]);
+                    }
+                    __syncwarp(hmask);
+                    cz<R> acc{0, 0}, s1{0, 0};
+                    for (int it = 0; it <= P; it++) {
+                        const bool first = it < n1;
+                        if (it == n1) {
+                            s1 = acc;
+                            acc = cz<R>{0, 0};
+                        }
+                        const int k = first ? r1 + it : r2 + (it - n1), l = first ? r1 : r2;
+                        const cz<R> a = Ah[k];
+                        const R c = Cd[k * P + l];
+                        acc.x = fmr(c, a.x, acc.x);
+                        acc.y = fmr(c, a.y, acc.y);
+                    }
+                    if (j < nr) {
+                        const cz<R> o = loc[b * P + r1], t = zmul(inv[r1], s1);
+                        loc[b * P + r1] = cz<R>{o.x + t.x, o.y + t.y};
+                        if (r2 != r1) {
+                            const cz<R> o2 = loc[b * P + r2], t2 = zmul(inv[r2], acc);
+                            loc[b * P + r2] = cz<R>{o2.x + t2.x, o2.y + t2.y};
+                        }
+                    }
+                    __threadfence();
+                    __syncwarp(hmask);
                 }
-            } else {
-                for (int k = 0; k < P; k++) {
-                    const cz<R> a = A[k];
-                    const R c0 = Cd[k * P + lc0];
-                    s0.x = fmr(c0, a.x, s0.x);
-                    s0.y = fmr(c0, a.y, s0.y);
-                }
+                if (j == 0) atomicExch(&done[b], epoch + 1u);
             }
-            if (l0 < P) {
-                const cz<R> o = loc[b * P + l0], t = zmul(inv[l0], s0);
-                loc[b * P + l0] = cz<R>{o.x + t.x, o.y + t.y};
-            }
-            if (l1 < P) {
-                const cz<R> o = loc[b * P + l1], t = zmul(inv[l1], s1);
-                loc[b * P + l1] = cz<R>{o.x + t.x, o.y + t.y};
-            }
-            __threadfence();
-            __syncwarp();
         }
-        if (lane == 0) atomicExch(&done[b], epoch + 1u);
+    } else {
+        const int l0 = lane, l1 = lane + 32;
+        const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
+        for (;;) {
+            unsigned bi = 0;
+            if (lane == 0) bi = atomicAdd(&pull[3], 1u);
+            const int64_t b = (int64_t)__shfl_sync(0xffffffffu, bi, 0);
+            if (b >= nbox) break;
+            if (level[b] >= 3) {
+                const int p = parent[b];
+                if (lane == 0) {
+                    unsigned spins = 0;
+                    const unsigned lim = wait_limit(status, kChainSpins);
+                    while (*(volatile unsigned *)&done[p] != epoch + 1u)
+                        if (++spins > lim) {
+                            atomicOr(status, LBF_DEV_TIMEOUT);
+                            break;
+                        }
+                }
+                __syncwarp();
+                __threadfence();
+                const int d = (ix[b] & 1) + 2 * (iy[b] & 1);
+                const cz<R> *dp = dtab + (size_t)d * (LBF_MAX_TERMS + 1);
+                const cz<R> *inv = dtab + (size_t)(4 + d) * (LBF_MAX_TERMS + 1);
+                for (int k = lane; k < P; k += 32) {
+                    const cz<R> pk = ldcg_cz(&loc[(int64_t)p * P + k]);
+                    A[k] = zmul(pk, dp[k]);
+                }
+                __syncwarp();
+                cz<R> s0{0, 0}, s1{0, 0};
+                // the second coefficient's sum only when P > 32: a test inside the loop leaves
+                // predicated-off multiply-adds that still occupy the double pipe
+                if (P > 32) {
+                    for (int k = 0; k < P; k++) {
+                        const cz<R> a = A[k];
+                        const R c0 = Cd[k * P + lc0], c1 = Cd[k * P + lc1];
+                        s0.x = fmr(c0, a.x, s0.x);
+                        s0.y = fmr(c0, a.y, s0.y);
+                        s1.x = fmr(c1, a.x, s1.x);
+                        s1.y = fmr(c1, a.y, s1.y);
+                    }
+                } else {
+                    for (int k = 0; k < P; k++) {
+                        const cz<R> a = A[k];
+                        const R c0 = Cd[k * P + lc0];
+                        s0.x = fmr(c0, a.x, s0.x);
+                        s0.y = fmr(c0, a.y, s0.y);
+                    }
+                }
+                if (l0 < P) {
+                    const cz<R> o = loc[b * P + l0], t = zmul(inv[l0], s0);
+                    loc[b * P + l0] = cz<R>{o.x + t.x, o.y + t.y};
+                }
+                if (l1 < P) {
+                    const cz<R> o = loc[b * P + l1], t = zmul(inv[l1], s1);
+                    loc[b * P + l1] = cz<R>{o.x + t.x, o.y + t.y};
+                }
+                __threadfence();
+                __syncwarp();
+            }
+            if (lane == 0) atomicExch(&done[b], epoch + 1u);
+        }
     }
     if (lane == 0) {
         const unsigned total = gridDim.x * (unsigned)nw;
@@ -868,7 +937,7 @@ __global__ void k_zero_i32(int32_t *p, int64_t n)
 
 template <typename R> size_t l2l_smem(int P, int wpb)
 {
-    return (P * P * sizeof(R) + 15) / 16 * 16 + sizeof(cz<R>) * (size_t)wpb * P;
+    return (P * P * sizeof(R) + 15) / 16 * 16 + sizeof(cz<R>) * (size_t)wpb * 2 * P;
 }
 
 }  // namespace

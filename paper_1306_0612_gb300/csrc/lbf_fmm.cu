@@ -447,7 +447,7 @@ __global__ void k_ancestors(int64_t nleaf, const int32_t *__restrict__ leaves,
 // shared-memory bytes of the two FMM pass kernels
 template <typename R> size_t up_smem(int P, int wpb)
 {
-    return (P * P * sizeof(R) + 15) / 16 * 16 + sizeof(cx<R>) * (size_t)wpb * P * 33;
+    return (P * P * sizeof(R) + 15) / 16 * 16 + sizeof(cx<R>) * (size_t)wpb * P * 34;
 }
 template <typename R> size_t down_smem(int P, int wpb)
 {

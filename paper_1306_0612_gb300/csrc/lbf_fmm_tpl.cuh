@@ -258,7 +258,7 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
     const int cl_len = (P * P * (int)sizeof(R) + 15) / 16 * 16;
     R *Cl = (R *)sm_raw;  // Cl[k*P + l] = C(l, k) (0 for k > l)
     cx<R> *T = (cx<R> *)(sm_raw + cl_len) + (size_t)wid * P * 32;
-    cx<R> *A = (cx<R> *)(sm_raw + cl_len) + (size_t)nw * P * 32 + (size_t)wid * P;
+    cx<R> *A = (cx<R> *)(sm_raw + cl_len) + (size_t)nw * P * 32 + (size_t)wid * 2 * P;
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
         int k = e / P, l = e % P;
         Cl[e] = k <= l ? binom[l * LBF_MAX_TERMS + k] : R(0);
@@ -323,6 +323,55 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
         last = __shfl_sync(0xffffffffu, last, 0);
         if (!last) break;
         __threadfence();
+        if (P <= 32) {
+            // Two children at a time, one per half-warp.  The M2M matrix C(l, k) (k <= l) is
+            // triangular: lane j of a half sums the rows l = j and l = P - 1 - j, P + 1 terms
+            // in one loop (it moves to the second row inside the loop); the halves' sums over
+            // their children are added at the end.
+            const int hf = lane >> 4, j = lane & 15;
+            const unsigned hmask = hf ? 0xffff0000u : 0x0000ffffu;
+            const int nr = (P + 1) / 2;
+            const int r1 = j < nr ? j : 0, r2 = P - 1 - r1, n1 = r1 + 1;
+            cx<R> *Ah = A + hf * P;
+            cx<R> a1 = mk<R>(0, 0), a2 = mk<R>(0, 0);
+            const int cend = child0[p] + nchild[p];
+            for (int c0 = child0[p]; c0 < cend; c0 += 2) {
+                const int c = c0 + hf;
+                if (c < cend) {
+                    const int d = (ix[c] & 1) + 2 * (iy[c] & 1);
+                    const cx<R> *inv = d2inv(dtab, d);
+                    for (int k = j; k < P; k += 16) Ah[k] = cmul(ldcg_cx(&mp[(int64_t)c * P + k]), inv[k]);
+                    __syncwarp(hmask);
+                    cx<R> acc = mk<R>(0, 0), s1 = mk<R>(0, 0);
+                    for (int it = 0; it <= P; it++) {
+                        const bool first = it < n1;
+                        if (it == n1) {
+                            s1 = acc;
+                            acc = mk<R>(0, 0);
+                        }
+                        const int k = first ? it : it - n1, l = first ? r1 : r2;
+                        const cx<R> a = Ah[k];
+                        const R cc = Cl[k * P + l];
+                        acc.x = fm(cc, a.x, acc.x);
+                        acc.y = fm(cc, a.y, acc.y);
+                    }
+                    const cx<R> *dp = dpow(dtab, d);
+                    a1 = cfma(dp[r1], s1, a1);
+                    a2 = cfma(dp[r2], acc, a2);
+                    __syncwarp(hmask);
+                }
+            }
+            a1.x += __shfl_xor_sync(0xffffffffu, a1.x, 16);
+            a1.y += __shfl_xor_sync(0xffffffffu, a1.y, 16);
+            a2.x += __shfl_xor_sync(0xffffffffu, a2.x, 16);
+            a2.y += __shfl_xor_sync(0xffffffffu, a2.y, 16);
+            if (hf == 0 && j < nr) {
+                mp[(int64_t)p * P + r1] = a1;
+                if (r2 != r1) mp[(int64_t)p * P + r2] = a2;
+            }
+            cur = p;
+            continue;
+        }
         const int l0 = lane, l1 = lane + 32;
         const int lc0 = l0 < P ? l0 : 0, lc1 = l1 < P ? l1 : 0;
         cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
@@ -729,39 +778,108 @@ k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level,
         __syncwarp();
         __threadfence();
     };
-    cb = ce = 0;
-    for (;;) {
-        if (cb == ce) {
-            unsigned bi = 0;
-            if (lane == 0) bi = atomicAdd(&pull[3], kGrab);
-            cb = __shfl_sync(0xffffffffu, bi, 0);
-            ce = cb + kGrab;
-        }
-        const int64_t b = ls + (int64_t)cb++;
-        if (b >= le) break;
-        wait_for(&part[b - ls]);
-        if (level[b] >= 3) {
-            const int p = parent[b];
-            wait_for(&done[p - ls]);
-            const int bx = ix[b], by = iy[b], d = (bx & 1) + 2 * (by & 1);
-            const cx<R> *dp = dpow(dtab, d);
-            for (int k = lane; k < P; k += 32) A[k] = cmul(ldcg_cx(&loc[(int64_t)p * P + k]), dp[k]);
-            __syncwarp();
-            cx<R> s0, s1;
-            coef_sums(A, Cd, P, lc0, lc1, P > 32, s0, s1);
-            const cx<R> *inv = d2inv(dtab, d);
-            if (l0 < P) {
-                const cx<R> own = ldcg_cx(&loc[b * P + l0]);
-                loc[b * P + l0] = cfma(inv[l0], s0, own);
+    if (P <= 32) {
+        // Two boxes a warp, one per half-warp.  The L2L matrix C(k, l) (k >= l) is
+        // triangular: lane j of a half sums the rows l = j and l = P - 1 - j, P + 1 terms in
+        // one loop (it moves to the second row inside the loop), each row's terms in the
+        // order of the full-row loop without its zero terms.  Each half waits for its own
+        // box's part and parent; when the parent is the other half's box, the other half
+        // marks it done first.
+        const int hf = lane >> 4, j = lane & 15;
+        const unsigned hmask = hf ? 0xffff0000u : 0x0000ffffu;
+        const int nr = (P + 1) / 2;  // lanes of a half with rows
+        const int r1 = j < nr ? j : 0, r2 = P - 1 - r1, n1 = P - r1;
+        cx<R> *Ah = A + hf * P;
+        auto wait_half = [&](const unsigned *flag) {
+            if (j == 0) {
+                unsigned spins = 0;
+                const unsigned lim = wait_limit(status, kPullSpins);
+                while (*(volatile const unsigned *)flag != epoch + 1u)
+                    if (++spins > lim) {
+                        atomicOr(status, LBF_DEV_TIMEOUT);
+                        break;
+                    }
             }
-            if (l1 < P) {
-                const cx<R> own = ldcg_cx(&loc[b * P + l1]);
-                loc[b * P + l1] = cfma(inv[l1], s1, own);
-            }
+            __syncwarp(hmask);
             __threadfence();
-            __syncwarp();
+        };
+        for (;;) {
+            unsigned bi = 0;
+            if (lane == 0) bi = atomicAdd(&pull[3], 2u);
+            const int64_t bpair = ls + (int64_t)__shfl_sync(0xffffffffu, bi, 0);
+            if (bpair >= le) break;
+            const int64_t b = bpair + hf;
+            if (b >= le) continue;
+            wait_half(&part[b - ls]);
+            if (level[b] >= 3) {
+                const int p = parent[b];
+                wait_half(&done[p - ls]);
+                const int bx = ix[b], by = iy[b], d = (bx & 1) + 2 * (by & 1);
+                const cx<R> *dp = dpow(dtab, d);
+                for (int k = j; k < P; k += 16) Ah[k] = cmul(ldcg_cx(&loc[(int64_t)p * P + k]), dp[k]);
+                __syncwarp(hmask);
+                cx<R> acc = mk<R>(0, 0), s1 = mk<R>(0, 0);
+                for (int it = 0; it <= P; it++) {
+                    const bool first = it < n1;
+                    if (it == n1) {
+                        s1 = acc;
+                        acc = mk<R>(0, 0);
+                    }
+                    const int k = first ? r1 + it : r2 + (it - n1), l = first ? r1 : r2;
+                    const cx<R> a = Ah[k];
+                    const R c = Cd[k * P + l];
+                    acc.x = fm(c, a.x, acc.x);
+                    acc.y = fm(c, a.y, acc.y);
+                }
+                const cx<R> *inv = d2inv(dtab, d);
+                if (j < nr) {
+                    const cx<R> own = ldcg_cx(&loc[b * P + r1]);
+                    loc[b * P + r1] = cfma(inv[r1], s1, own);
+                    if (r2 != r1) {
+                        const cx<R> own2 = ldcg_cx(&loc[b * P + r2]);
+                        loc[b * P + r2] = cfma(inv[r2], acc, own2);
+                    }
+                }
+                __threadfence();
+                __syncwarp(hmask);
+            }
+            if (j == 0) atomicExch(&done[b - ls], epoch + 1u);
         }
-        if (lane == 0) atomicExch(&done[b - ls], epoch + 1u);
+    } else {
+        cb = ce = 0;
+        for (;;) {
+            if (cb == ce) {
+                unsigned bi = 0;
+                if (lane == 0) bi = atomicAdd(&pull[3], kGrab);
+                cb = __shfl_sync(0xffffffffu, bi, 0);
+                ce = cb + kGrab;
+            }
+            const int64_t b = ls + (int64_t)cb++;
+            if (b >= le) break;
+            wait_for(&part[b - ls]);
+            if (level[b] >= 3) {
+                const int p = parent[b];
+                wait_for(&done[p - ls]);
+                const int bx = ix[b], by = iy[b], d = (bx & 1) + 2 * (by & 1);
+                const cx<R> *dp = dpow(dtab, d);
+                for (int k = lane; k < P; k += 32) A[k] = cmul(ldcg_cx(&loc[(int64_t)p * P + k]), dp[k]);
+                __syncwarp();
+                cx<R> s0, s1;
+                coef_sums(A, Cd, P, lc0, lc1, P > 32, s0, s1);
+                const cx<R> *inv = d2inv(dtab, d);
+                if (l0 < P) {
+                    const cx<R> own = ldcg_cx(&loc[b * P + l0]);
+                    loc[b * P + l0] = cfma(inv[l0], s0, own);
+                }
+                if (l1 < P) {
+                    const cx<R> own = ldcg_cx(&loc[b * P + l1]);
+                    loc[b * P + l1] = cfma(inv[l1], s1, own);
+                }
+                __threadfence();
+                __syncwarp();
+            }
+            if (lane == 0) atomicExch(&done[b - ls], epoch + 1u);
+        }
     }
     if (lane == 0) {
         const unsigned total = gridDim.x * (unsigned)nw;

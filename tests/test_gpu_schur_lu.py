@@ -58,14 +58,17 @@ def test_lu_singular_shared_centre():
     assert e.value.status == L.LBF_ESINGULAR
 
 
-@pytest.mark.parametrize("precision,tol,agree", [(L.LBF_PRECISION_FP64, 1e-12, 1e-9),
+@pytest.mark.parametrize("precision,tol,agree", [(L.LBF_PRECISION_FP64, 1e-12, 1e-8),
                                                   (L.LBF_PRECISION_FP32_REFINE, 1e-10, 1e-7)])
 def test_lu_solve_many_islands_matches_gauss_jordan(precision, tol, agree):
     """2048 islands (the LU path by default) against the same solve with the
     Gauss-Jordan inverse: the same bordered system, each solved to a preconditioned
-    relative residual below tol.  Two such solutions differ by at most
-    ||(P^-1 A)^-1|| 2 tol relative, a few hundred tol on these geometries; the FP64 GMRES
-    runs the same Krylov iteration to rounding and agrees far closer."""
+    relative residual below tol.  The preconditioned operator is applied as
+    x + P^-1 [2K sigma; 0], so a solve meets the system whose Schur block is the inverse
+    of the S^-1 it applies: the Gauss-Jordan path's double S^-1, unrefined, carries about
+    cond(S) 2^-53 (cond(S) ~ 1e8 at 2048 star caps, so ~1e-8), the LU path's refined one
+    less; the two solutions agree to that, whatever tol (1e-12 and 1e-13 give the same
+    difference)."""
     g = wl.star_caps(3, 2048, 64)
     src, gam, _ = wl.pair_sources(g, 0, 1)
     data = zeros(g.N)
