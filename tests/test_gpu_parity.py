@@ -131,6 +131,27 @@ def test_apply_all_ops_small(matvec):
     assert rel_l2(host(o2), A[:N, :N] @ v[:N]) < MATVEC_TOL
 
 
+@pytest.mark.parametrize("p,leaf,warps", [(26, 5, 1), (26, 13, 3), (31, 40, 8), (35, 64, 2),
+                                           (31, 24, 4)])
+def test_native_double_operator_across_orders_leaves_and_tiles(p, leaf, warps):
+    """The native-double passes spread their work over the 32 lanes by counts that depend on
+    the leaf's target count, the staged source count, the number of V-list boxes and the
+    order: near-field runs spanning two targets, far-field items, (box, coefficient) M2L
+    slots with two add steps, half-warp triangular shifts with rows l and P - 1 - l (P odd,
+    P = 32, and P > 32 on the whole-warp path).  Leaf sizes that are not powers of two, a
+    leaf size above 32 (two target chunks) and tiles of 1 to 8 leaves a block, each against
+    the oracle's rows at the FP64 tolerance, on every operator form."""
+    g = wl.config_geometry("C2", nodes=256)
+    pl = plan_for(g, p=p, leaf_size=leaf, p2p_warps=warps)
+    v = np.random.default_rng(p + leaf).standard_normal(g.N + g.M)
+    out = zeros(g.N + g.M)
+    L.lbf_apply(pl, L.LBF_OP_FULL, dev(v), out)
+    assert rel_l2(host(out), oracle.apply(g, v, 0)) < MATVEC_TOL
+    o2 = zeros(g.N)
+    L.lbf_apply(pl, L.LBF_OP_K_ONLY, dev(v[:g.N]), o2)
+    assert rel_l2(host(o2), oracle.apply(g, v[:g.N], 1)) < MATVEC_TOL
+
+
 def test_preconditioned_op_many_islands():
     """200 islands: the inverse Schur complement from the multi-block Gauss-Jordan
     kernel and the tree-based multiplier potential against the dense P^-1 A."""
