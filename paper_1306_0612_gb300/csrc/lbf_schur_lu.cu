@@ -447,140 +447,204 @@ k_oz_slice_cols(int M, int k0, int w, const float2 *A, uint4 *Uimg, int *eu, con
     if (kg == 0) eu[cb * kTcN + jl] = e;
 }
 
-// One 128 x 64 tile of A22 per CTA (8 warps).  One thread copies the row block's and
-// column block's slice images into shared memory with two bulk asynchronous copies and,
-// once they have landed (an mbarrier counting their bytes), issues the
-// 4 (kOzD + 1)(kOzD + 2)/2 MMAs (K = 16 each) into kOzD + 1 accumulators of 64 TMEM
-// columns; their completion is signalled on a second mbarrier.  Each thread then takes
-// 32 columns of one row of the tile from TMEM (warp q reads lanes 32 (q mod 4) ...,
-// columns 32 (q / 4) ...), combines the accumulators in double-float and subtracts the
-// product from A22.  Every wait is bounded: past the limit the CTA records a time-out,
-// waits once more (bounded) for its copies and MMAs, frees its TMEM and returns.
-constexpr int kTcThreads = 256;
+// The trailing update as a persistent kernel, one CTA per SM taking work items of up to
+// kTcChunk column blocks of one 128-row block (items c, c + grid, c + 2 grid, ... for CTA
+// c, so every thread knows the sequence).  Warp 8 produces: one thread loads an item's
+// row-block slices once (96 KB) and, per 128 x 64 tile, the column block's slices (48 KB)
+// with bulk asynchronous copies, then issues the tile's 84 MMAs (21 slice pairs x 4 K
+// steps of 16) into six TMEM accumulators of 64 columns and commits them.  Warps 0-7
+// consume: per tile they read the accumulators (warp q: TMEM lanes 32 (q mod 4) ...,
+// columns 32 (q / 4) ...), combine them in double-float, tell the producer that TMEM is
+// free, stage the tile in shared memory and subtract it from A22 with coalesced loads and
+// stores — while the producer already loads and multiplies the next tile.  mbarriers:
+// row-block slices landed, column-block slices landed, MMAs done (the column buffer and
+// TMEM are then free to reuse), accumulators read (8 arrivals).  Every wait is bounded; a
+// wait that gives up records a time-out, and each side stops at its next tile (the
+// consumers decide together, after a barrier of theirs); the CTA then frees its TMEM.
+constexpr int kTcChunk = 8;                 // column blocks per work item
+constexpr int kTcConsumers = 256;           // warps 0-7
+constexpr int kTcThreads = kTcConsumers + 32;
+constexpr int kTcVs = kTcN + 1;             // row stride of the staged tile (float2)
+constexpr int kTcSmemAll = kTcSmem + kTcM * kTcVs * 8;
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, unsigned lim)
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, unsigned lim)
 {
     for (unsigned spins = 0; spins < lim; spins++)
-        if (mbar_test(mb, 0)) return true;
+        if (mbar_test(mb, parity)) return true;
     return false;
 }
 
-__global__ void __launch_bounds__(kTcThreads)
-k_lu_gemm_tc(int M, int k1, const uint4 *Limg, const uint4 *Uimg, const int *el, const int *eu,
-             float2 *A, int *status)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, int bytes, uint32_t mb)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mb) : "memory");
+}
+
+__device__ __forceinline__ void consumers_sync()
+{
+    asm volatile("bar.sync 1, %0;" :: "r"(kTcConsumers) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_lu_gemm_tc(int M, int k1, int nrb, int ncb, const uint4 *Limg, const uint4 *Uimg, const int *el,
+             const int *eu, float2 *A, int *status)
 {
     if (lu_failed(status)) return;
     extern __shared__ __align__(128) uint4 gsm_tc[];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) unsigned long long bar_ld, bar_mma;
+    __shared__ __align__(8) unsigned long long bar_l, bar_u, bar_mma, bar_free;
+    __shared__ int s_abort, s_stop;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rb = blockIdx.y, cb = blockIdx.x;
     uint4 *sL = gsm_tc, *sU = gsm_tc + kOzS * kTcLBytes / 16;
-    const uint32_t mld = smem_u32(&bar_ld), mmm = smem_u32(&bar_mma);
+    float2 *vt = (float2 *)(gsm_tc + kTcSmem / 16);  // [kTcM][kTcVs]: the tile's products
+    const uint32_t ml = smem_u32(&bar_l), mu = smem_u32(&bar_u), mm = smem_u32(&bar_mma),
+                   mf = smem_u32(&bar_free);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(&tmem_base)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mld), "r"(1) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mmm), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(ml), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mu), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mm), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mf), "r"(kTcConsumers / 32) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     const unsigned lim = wait_limit(status, kLuSpins);
-    bool ok = true;
-    if (tid == 0) {
-        const uint32_t aL = smem_u32(sL), aU = smem_u32(sU);
-        const uint4 *gL = Limg + (size_t)rb * (kOzS * kTcLBytes / 16);
-        const uint4 *gU = Uimg + (size_t)cb * (kOzS * kTcUBytes / 16);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     :: "r"(mld), "r"(kTcSmem) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(aL), "l"(gL), "r"(kOzS * kTcLBytes), "r"(mld) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(aU), "l"(gU), "r"(kOzS * kTcUBytes), "r"(mld) : "memory");
-        ok = mbar_wait(mld, lim);
-        if (ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // descriptors of the slices' first K step; a K step of 16 advances the start
-            // address by 256 bytes, a slice by kTcLBytes or kTcUBytes (the address field
-            // counts 16-byte units)
-            const uint64_t dL = tc_desc(aL), dU = tc_desc(aU);
-#pragma unroll
-            for (int d = 0; d <= kOzD; d++)
-#pragma unroll
-                for (int sl = 0; sl <= d; sl++)
-#pragma unroll
-                    for (int j = 0; j < kLuNb / 16; j++)
-                        tc_mma(tmem + (uint32_t)(d * kTcN), dL + (uint64_t)((sl * kTcLBytes + j * 256) >> 4),
-                               dU + (uint64_t)(((d - sl) * kTcUBytes + j * 256) >> 4), (sl > 0 || j > 0) ? 1u : 0u);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(mmm) : "memory");
-        } else {
-            atomicOr(status, LBF_DEV_TIMEOUT);
-            mbar_wait(mld, lim);  // the copies still in flight
-        }
-    }
-    if (tid == 0 && ok && !mbar_wait(mmm, lim)) {
-        ok = false;
+    const int q = (ncb + kTcChunk - 1) / kTcChunk, nitems = nrb * q;
+    auto give_up = [&]() {
         atomicOr(status, LBF_DEV_TIMEOUT);
-        mbar_wait(mmm, lim);
-    }
-    ok = __syncthreads_and(ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // 1. TMEM -> the products V_ij = sum_d P_d 2^(-8d) (times the row's scale) in
-    //    double-float, thread = row, into shared memory (the operands' space is free now)
-    const int quarter = warp & 3, half = warp >> 2;
-    const int rl = quarter * 32 + lane, i = k1 + rb * kTcM + rl;
-    const float ri = ok && i < M ? pow2f(el[rb * kTcM + rl] - 16) : 0.f;
-    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
-    float2 *vt = (float2 *)gsm_tc;  // [kTcM][kTcN + 1]: V of row r, column c
-    constexpr int kVs = kTcN + 1;
-    for (int c = 0; c < 32; c += 16) {
-        float acc[kOzD + 1][16];
+        *(volatile int *)&s_abort = 1;
+    };
+    if (warp == kTcConsumers / 32) {
+        // ---- producer ----
+        if (lane == 0) {
+            const uint32_t aL = smem_u32(sL), aU = smem_u32(sU);
+            const uint64_t dL = tc_desc(aL), dU = tc_desc(aU);
+            unsigned t = 0, nl = 0;
+            int prev_rb = -1;
+            bool ok = true;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int rb = item / q, c0 = (item % q) * kTcChunk, c1 = min(ncb, c0 + kTcChunk);
+                if (rb != prev_rb) {
+                    // the row-block buffer is read until the last tile's MMAs are done
+                    if (t > 0 && !(ok = mbar_wait(mm, (t - 1) & 1, lim))) break;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 :: "r"(ml), "r"(kOzS * kTcLBytes) : "memory");
+                    bulk_g2s(aL, (const char *)Limg + (size_t)rb * kOzS * kTcLBytes, kOzS * kTcLBytes, ml);
+                    if (!(ok = mbar_wait(ml, nl & 1, lim))) break;
+                    nl++;
+                    prev_rb = rb;
+                }
+                for (int cb = c0; cb < c1 && ok; cb++, t++) {
+                    if (t > 0 && !(ok = mbar_wait(mm, (t - 1) & 1, lim))) break;  // column buffer free
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 :: "r"(mu), "r"(kOzS * kTcUBytes) : "memory");
+                    bulk_g2s(aU, (const char *)Uimg + (size_t)cb * kOzS * kTcUBytes, kOzS * kTcUBytes, mu);
+                    if (!(ok = mbar_wait(mu, t & 1, lim))) break;
+                    if (t > 0 && !(ok = mbar_wait(mf, (t - 1) & 1, lim))) break;  // TMEM read
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int d = 0; d <= kOzD; d++) tc_ld16(trow + (uint32_t)(d * kTcN + c), acc[d]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    for (int d = 0; d <= kOzD; d++)
 #pragma unroll
-        for (int q = 0; q < 16; q++) {
-            float h = acc[kOzD][q], l = 0.f;  // from the smallest term up
+                        for (int sl = 0; sl <= d; sl++)
 #pragma unroll
-            for (int d = kOzD - 1; d >= 0; d--) {
-                float e2;
-                df_two_sum(acc[d][q], h * 0x1p-8f, h, e2);
-                l = e2 + l * 0x1p-8f;
+                            for (int jk = 0; jk < kLuNb / 16; jk++)
+                                tc_mma(tmem + (uint32_t)(d * kTcN),
+                                       dL + (uint64_t)((sl * kTcLBytes + jk * 256) >> 4),
+                                       dU + (uint64_t)(((d - sl) * kTcUBytes + jk * 256) >> 4),
+                                       (sl > 0 || jk > 0) ? 1u : 0u);
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(mm) : "memory");
+                }
             }
-            const df64 v = df_fast(h, l);
-            vt[rl * kVs + half * 32 + c + q] = make_float2(v.hi * ri, v.lo * ri);
+            if (!ok) {
+                give_up();
+                // copies or MMAs still in flight finish before the CTA lets go of its memory
+                mbar_wait(mm, (t - 1) & 1, lim);
+            } else if (t > 0) {
+                mbar_wait(mm, (t - 1) & 1, lim);
+            }
         }
-    }
-    __syncthreads();
-    // 2. A22 -= V 2^f_j, lanes on consecutive columns of a row; all of a thread's loads
-    //    are issued before its stores (a store could alias a later load, so the compiler
-    //    would not move the loads up on its own)
-    if (ok) {
-        constexpr int kRows = kTcM * kTcN / kTcThreads;  // 32 rows per thread
-        const int jl = tid & (kTcN - 1), j = k1 + cb * kTcN + jl, r0 = tid >> 6;
-        const float cj = j < M ? pow2f(eu[cb * kTcN + jl]) : 0.f;
-        const int nrow = min(kTcM, M - (k1 + rb * kTcM));
-        float2 *ap = A + (int64_t)(k1 + rb * kTcM) * M + j;
-        const int64_t rs = (int64_t)(kTcThreads / kTcN) * M;
-        if (j < M) {
-            float2 av[kRows];
+    } else {
+        // ---- consumers ----
+        const int quarter = warp & 3, half = warp >> 2, rl = quarter * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+        unsigned t = 0;
+        bool stop = false;
+        for (int item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
+            const int rb = item / q, c0 = (item % q) * kTcChunk, c1 = min(ncb, c0 + kTcChunk);
+            const int i = k1 + rb * kTcM + rl;
+            const float ri = i < M ? pow2f(el[rb * kTcM + rl] - 16) : 0.f;
+            for (int cb = c0; cb < c1; cb++, t++) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(mm, t & 1, lim);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok && lane == 0) give_up();
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // 1. TMEM -> V_ij = sum_d P_d 2^(-8d) (times the row's scale), double-float
+                float2 v[32];
 #pragma unroll
-            for (int q = 0; q < kRows; q++)
-                av[q] = r0 + 4 * q < nrow ? ap[r0 * (int64_t)M + q * rs] : make_float2(0.f, 0.f);
+                for (int c = 0; c < 32; c += 16) {
+                    float acc[kOzD + 1][16];
 #pragma unroll
-            for (int q = 0; q < kRows; q++) {
-                const int r = r0 + 4 * q;
-                if (r >= nrow) break;
-                const float2 v = vt[r * kVs + jl];
-                const df64 res = df64(av[q].x, av[q].y, 0) - df64(v.x * cj, v.y * cj, 0);
-                ap[r0 * (int64_t)M + q * rs] = make_float2(res.hi, res.lo);
+                    for (int d = 0; d <= kOzD; d++) tc_ld16(trow + (uint32_t)(d * kTcN + c), acc[d]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int qq = 0; qq < 16; qq++) {
+                        float h = acc[kOzD][qq], l = 0.f;  // from the smallest term up
+#pragma unroll
+                        for (int d = kOzD - 1; d >= 0; d--) {
+                            float e2;
+                            df_two_sum(acc[d][qq], h * 0x1p-8f, h, e2);
+                            l = e2 + l * 0x1p-8f;
+                        }
+                        const df64 vv = df_fast(h, l);
+                        v[c + qq] = make_float2(vv.hi * ri, vv.lo * ri);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mf) : "memory");
+                // 2. the previous tile's update is done everywhere: stage this one.  Whether to
+                //    stop is read by one thread before the barrier and by all after it, so every
+                //    consumer takes the same branch (the flag itself may change at any time)
+                if (tid == 0) s_stop = *(volatile int *)&s_abort;
+                consumers_sync();
+                stop = s_stop != 0;
+                if (stop) break;
+#pragma unroll
+                for (int c = 0; c < 32; c++) vt[rl * kTcVs + half * 32 + c] = v[c];
+                consumers_sync();
+                // 3. A22 -= V 2^f_j, lanes on consecutive columns of a row; all of a thread's
+                //    loads before its stores (a store could alias a later load)
+                constexpr int kStep = kTcConsumers / kTcN, kRows = kTcM / kStep;
+                const int jl = tid % kTcN, j = k1 + cb * kTcN + jl, r0 = tid / kTcN;
+                const float cj = j < M ? pow2f(eu[cb * kTcN + jl]) : 0.f;
+                const int nrow = min(kTcM, M - (k1 + rb * kTcM));
+                float2 *ap = A + (int64_t)(k1 + rb * kTcM) * M + j;
+                const int64_t rs = (int64_t)kStep * M;
+                if (j < M) {
+                    float2 av[kRows];
+#pragma unroll
+                    for (int qq = 0; qq < kRows; qq++)
+                        av[qq] = r0 + kStep * qq < nrow ? ap[r0 * (int64_t)M + qq * rs] : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int qq = 0; qq < kRows; qq++) {
+                        const int r = r0 + kStep * qq;
+                        if (r >= nrow) break;
+                        const float2 w2 = vt[r * kTcVs + jl];
+                        const df64 res = df64(av[qq].x, av[qq].y, 0) - df64(w2.x * cj, w2.y * cj, 0);
+                        ap[r0 * (int64_t)M + qq * rs] = make_float2(res.hi, res.lo);
+                    }
+                }
             }
         }
     }
@@ -900,7 +964,7 @@ int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
     const size_t tile_smem = sizeof(float2) * 2 * kLuNb * kLuPad;
     LBF_CUDA(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLuSmemCap));
     LBF_CUDA(cudaFuncSetAttribute(k_lu_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
-    LBF_CUDA(cudaFuncSetAttribute(k_lu_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    LBF_CUDA(cudaFuncSetAttribute(k_lu_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAll));
     for (int k0 = 0; k0 < M; k0 += kLuNb) {
         const int w = std::min(kLuNb, M - k0);
         const int rows = M - k0;
@@ -933,8 +997,9 @@ int lbf_schur_lu_factor(lbf_plan *pl, cudaStream_t s, void *scratch)
                          Limg, el, status);
             LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_oz_slice_cols, ncb, 512, 0, s, M, k0, w, A, Uimg, eu,
                          status);
-            LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_lu_gemm_tc, dim3(ncb, nrb), kTcThreads, kTcSmem, s, M, k0 + w, Limg,
-                         Uimg, el, eu, A, status);
+            const int items = nrb * ((ncb + kTcChunk - 1) / kTcChunk);
+            LBF_LAUNCH_P(LBF_KERNEL_LU_GEMM, k_lu_gemm_tc, std::min(items, nsm), kTcThreads, kTcSmemAll, s, M,
+                         k0 + w, nrb, ncb, Limg, Uimg, el, eu, A, status);
         }
         LBF_CHECK_LAUNCH();
     }
