@@ -748,6 +748,14 @@ def run_extras(args, L, dev, stream):
     dtb = time.perf_counter() - t0
     eb = errs(res)
     ol = L.lbf_default_options(tol=args.tol, fmm64=0)
+    # the FP64 operator with each instance's right-hand sides in lockstep
+    L.lbf_batch_run(inst[:4], opt=ol, nworkers=args.workers, lockstep=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    resk = L.lbf_batch_run(inst, opt=ol, nworkers=args.workers, lockstep=True)
+    torch.cuda.synchronize()
+    dtk = time.perf_counter() - t0
+    ek = errs(resk)
     t0 = time.perf_counter()
     le = []
     for ins in inst:
@@ -767,6 +775,8 @@ def run_extras(args, L, dev, stream):
                          f"tol {args.tol:g}, {T4} targets each",
                  "batched_fp32r_solves_per_s": nsolve / dtb, "batched_fp32r_s": dtb,
                  "batched_solution_err_max": eb,
+                 "batched_fp64_lockstep_solves_per_s": nsolve / dtk, "batched_fp64_lockstep_s": dtk,
+                 "batched_fp64_lockstep_err_max": ek,
                  "loop_fp64_solves_per_s": nsolve / dtl, "loop_fp64_s": dtl,
                  "loop_solution_err_max": float(np.max(le)),
                  "speedup": dtl / dtb}
@@ -812,12 +822,12 @@ def run_batch(args):
             e.extend(d.tolist())
         return float(np.max(e)), float(np.median(e))
 
-    def batched(precision, sub):
+    def batched(precision, sub, lockstep=False):
         kw = dict(inner_tol=args.inner_tol) if args.inner_tol else {}
         opt = L.lbf_default_options(tol=args.tol, precision=precision, fmm64=0, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = L.lbf_batch_run(sub, opt=opt, nworkers=args.workers)
+        res = L.lbf_batch_run(sub, opt=opt, nworkers=args.workers, lockstep=lockstep)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         st = [r["status"] for r in res]
@@ -828,6 +838,9 @@ def run_batch(args):
     e32 = err(res32, inst)
     dt64b, res64b, st64b = batched(L.LBF_PRECISION_FP64, inst)
     e64b = err(res64b, inst)
+    batched(L.LBF_PRECISION_FP64, inst[:args.workers], lockstep=True)
+    dt64k, res64k, st64k = batched(L.LBF_PRECISION_FP64, inst, lockstep=True)
+    e64k = err(res64k, inst)
     opt64 = L.lbf_default_options(tol=args.tol, fmm64=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -862,7 +875,13 @@ def run_batch(args):
                               "fp64_applies": sum(r["fp64_applies"] for r in res32)},
             "batched_fp64": {"wall_s": dt64b, "solves_per_s": nsolve / dt64b,
                              "statuses_ok": st64b.count(0), "solution_err_max": e64b[0],
-                             "solution_err_median": e64b[1]},
+                             "solution_err_median": e64b[1],
+                             "note": "each instance's right-hand sides one after another"},
+            "batched_fp64_lockstep": {"wall_s": dt64k, "solves_per_s": nsolve / dt64k,
+                                      "statuses_ok": st64k.count(0), "solution_err_max": e64k[0],
+                                      "solution_err_median": e64k[1],
+                                      "note": "each instance's 16 right-hand sides in lockstep "
+                                              "(lbf_gmres_solve_many)"},
             "loop_fp64": {"instances": len(inst), "solves": nloop, "wall_s": dtl,
                           "solves_per_s": loop_rate, "solution_err_max": float(np.max(loop_err)),
                           "note": "plain FP64 loop over every instance on one stream"},

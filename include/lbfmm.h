@@ -208,6 +208,30 @@ int lbf_apply(lbf_plan *plan, int op, const double *in, double *out, lbf_stream_
 int lbf_gmres_solve(lbf_plan *plan, const double *g, double *sigma, double *a, const double *x0,
                     int *iters, double *rel_res, lbf_stream_t stream);
 
+/* Several right-hand sides of one geometry (the system of Sec. 5, Eq. matrix_eqns, with
+ * the options of lbf_gmres_solve), solved together: their GMRES iterations advance in
+ * lockstep, groups of up to 16, and every launch of an Arnoldi step, restart or
+ * operator application covers the whole group (one CUDA block row per right-hand side,
+ * each gated by its own GMRES state), the step replayed from one CUDA graph per group
+ * when graphs are on.  Each right-hand side runs the kernels and fixed-order reductions
+ * of lbf_gmres_solve on its own buffers, so sigma, a, iters and rel_res equal those of
+ * nrhs separate lbf_gmres_solve calls bit for bit; a right-hand side that converges
+ * stops while the others go on.  Plans built for FP32_REFINE or whose S^-1 is applied
+ * by LU factors (LBF_SCHUR_LU, or M > 1024 with LBF_SCHUR_AUTO) solve the right-hand
+ * sides one after another with lbf_gmres_solve (workspace 0).
+ *   g: device, nrhs x N, caller order (right-hand side r at g + r N)
+ *   sigma: device out, nrhs x N; a: device out, nrhs x M (nullable)
+ *   iters, rel_res: host out, nrhs each (nullable)
+ *   work, bytes: device memory, 256-byte aligned, of at least lbf_gmres_workspace_many
+ *   bytes (the buffers of each right-hand side of a group: charges, expansions,
+ *   Krylov basis; the caller owns it and may reuse it after the call)
+ * Synchronous.  LBF_EWORKSPACE when work is short, LBF_NOCONV (soft) when some
+ * right-hand side reached maxit. */
+int lbf_gmres_workspace_many(const lbf_plan *plan, int nrhs, size_t *bytes /* host out */);
+int lbf_gmres_solve_many(lbf_plan *plan, int nrhs, const double *g, double *sigma, double *a,
+                         int *iters, double *rel_res, void *work, size_t bytes,
+                         lbf_stream_t stream);
+
 /* The adjoint system (Sec. 5, the bordered Eq. matrix_eqns transposed): solve
  * A^T lam = r by GMRES on P^-T A^T (left preconditioning with P^T, the same
  * tolerance, restart, precision and refinement options as lbf_gmres_solve).
@@ -252,9 +276,10 @@ int lbf_gradient_data(lbf_plan *plan, const double *lam, double *grad_g, lbf_str
  * of Sec. 5, each with nrhs right-hand sides (the paper solves one instance at a
  * time; this is an interface of the library).  nworkers host threads, each with its
  * own CUDA stream, take the items largest first (nodes x right-hand sides); per
- * item: a plan (lbf_plan_create, no pole rotation), for every right-hand side
- * lbf_gmres_solve with opt and, when T > 0 and u != NULL, lbf_evaluate at the
- * targets; then the plan is destroyed.  Synchronous.  Returns LBF_EINVAL for a bad
+ * item: a plan (lbf_plan_create, no pole rotation); the right-hand sides solved with
+ * opt by lbf_gmres_solve_many when the item's workspace has room for it after the
+ * plan's (lbf_batch_workspace_size), else by lbf_gmres_solve one after another; when
+ * T > 0 and u != NULL, lbf_evaluate at the targets; then the plan is destroyed.  Synchronous.  Returns LBF_EINVAL for a bad
  * item, LBF_ECUDA if a worker could not start; each item's own outcome is in its
  * status (LBF_EWORKSPACE with box_capacity_needed set when its workspace was short). */
 typedef struct lbf_batch_item {
@@ -278,6 +303,13 @@ typedef struct lbf_batch_item {
     int64_t box_capacity_needed;            /* see lbf_plan_create */
 } lbf_batch_item;
 int lbf_batch_run(int nitems, lbf_batch_item *items, const lbf_options *opt, int nworkers);
+/* Workspace of one batch item whose right-hand sides are solved in lockstep
+ * (lbf_gmres_solve_many) by lbf_batch_run: the plan's bytes (lbf_workspace_size),
+ * rounded up to 256, then lbf_gmres_workspace_many's for nrhs right-hand sides (none
+ * where those are solved one after another).  An item whose workspace holds less
+ * solves its right-hand sides one after another.  Host call, no GPU work. */
+int lbf_batch_workspace_size(int M, const int64_t *island_ptr, const lbf_options *opt, int nrhs,
+                             size_t *bytes /* host out */);
 
 /* Autotuner of the FMM's free parameters for one geometry (the paper fixes neither
  * the expansion order nor the leaf size; Sec. 6 gives only the FMM tolerance):

@@ -5,6 +5,7 @@
 #include <complex>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "lbf_internal.cuh"
@@ -261,6 +262,100 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     pl->V = o.border ? (double *)pl->region : nullptr;
 }
 
+// The buffers one right-hand side's solve writes, in the sizes lbf_layout gives them
+// (which of them exist follows the options, as there), carved from A for a plan view of
+// lbf_gmres_solve_many: each right-hand side has its own copy, while the geometry, the
+// tree, the lists, the tables and S^-1 stay the plan's.  pl needs only the sizes that
+// lbf_layout sets (it may have been laid out without memory).
+static void layout_rhs(const lbf_plan *pl, lbf_plan *v, Arena &A)
+{
+    const lbf_options &o = pl->opt;
+    const int64_t N = pl->N, n = pl->n, cap = pl->tree.cap;
+    const int M = pl->M, P = pl->P, m = o.restart;
+    const Border &B = pl->bd;
+    const bool fmm = o.matvec == LBF_MATVEC_FMM, f32 = o.precision == LBF_PRECISION_FP32_REFINE;
+    v->q = A.get<double2>(N);
+    v->mpole = fmm ? A.get<double2>(cap * P) : nullptr;
+    v->local = fmm ? A.get<double2>(cap * P) : nullptr;
+    v->upcnt = fmm || o.border ? A.get<int32_t>(cap) : nullptr;
+    v->pull = fmm || o.border ? A.get<uint32_t>(2 * cap + 4) : nullptr;
+    v->qdf = fmm && o.fmm64 ? (void *)A.get<double2>(N) : nullptr;
+    v->q32 = f32 ? A.get<float2>(N) : nullptr;
+    v->mpole32 = f32 && fmm ? A.get<float2>(cap * (o.p32 + 1)) : nullptr;
+    v->local32 = f32 && fmm ? A.get<float2>(cap * (o.p32 + 1)) : nullptr;
+    v->imean = f32 ? A.get<double>((int64_t)M + 8) : nullptr;
+    v->gr = f32 && o.border ? A.get<double>(n) : nullptr;
+    v->gd = f32 && o.border ? A.get<double>(n) : nullptr;
+    v->v = A.get<double>(N);
+    v->bsig = A.get<double>(4);
+    v->red = A.get<double>(1024);
+    v->red_count = A.get<unsigned>(4);
+    v->fvec = A.get<double>(M);
+    v->yvec = A.get<double>(M);
+    v->tin = A.get<double>(n);
+    v->tout = A.get<double>(n);
+    v->vstep = o.border ? A.get<double>(n) : nullptr;
+    v->bd.partial = o.border ? A.get<double>(B.partial_cap) : nullptr;
+    v->bd.loc = o.border ? A.get<double2>(cap * B.P) : nullptr;
+    v->bd.loc32 = o.border && f32 ? A.get<float2>(cap * B.P32) : nullptr;
+    v->bd.sums = o.border ? A.get<double>(4) : nullptr;
+    v->H = A.get<double>((int64_t)(m + 1) * m + 2 * (m + 1) + 2 * m + 2 * (m + 1) + m);
+    v->gw = A.get<double>(n);
+    v->gx = A.get<double>(n);
+    v->gb = A.get<double>(n);
+    v->gpart = A.get<double>((int64_t)pl->mdot_blocks * (m + 2));
+    v->gs = (GmresState *)A.take(sizeof(GmresStateBytes));
+    v->V = A.get<double>(pl->ldv * (m + 1));
+    v->region = (char *)v->V;
+    v->region_bytes = sizeof(double) * (size_t)pl->ldv * (m + 1);
+}
+
+// A view of plan pl over R right-hand sides whose buffers fill work (R slabs of equal
+// size, then 3 R device states for the host's reads); *need = the bytes it takes.
+// work == nullptr only sizes it.
+int lbf_many_view(const lbf_plan *pl, int R, void *work, size_t bytes, lbf_plan *view,
+                  size_t *need)
+{
+    lbf_plan v = *pl;
+    Arena A;
+    layout_rhs(pl, &v, A);  // sizes only
+    const size_t slab = (A.off + 255) & ~size_t(255);
+    const size_t total = slab * (size_t)R + 3 * (size_t)R * sizeof(GmresStateBytes);
+    if (need) *need = total;
+    if (!work || !view) return LBF_OK;
+    if (bytes < total) return LBF_EWORKSPACE;
+    Arena W;
+    W.base = (char *)work;
+    W.cap = slab;
+    layout_rhs(pl, &v, W);
+    if (W.overflow) return LBF_EWORKSPACE;
+    v.nrhs = R;
+    v.slab = (int64_t)slab;
+    for (auto &row : v.gexec)
+        for (auto &g : row) g = nullptr;  // the view captures its own step graph
+    *view = v;
+    return LBF_OK;
+}
+
+// The view's right-hand side r alone (one right-hand side, its own buffers)
+lbf_plan lbf_view_at(const lbf_plan &v, int r)
+{
+    lbf_plan o = v;
+    const int64_t off = (int64_t)r * v.slab;
+    auto mv = [&](auto *&p) {
+        using P = std::remove_reference_t<decltype(p)>;
+        if (p) p = (P)((char *)p + off);
+    };
+    mv(o.q); mv(o.mpole); mv(o.local); mv(o.upcnt); mv(o.pull); mv(o.qdf); mv(o.q32);
+    mv(o.mpole32); mv(o.local32); mv(o.imean); mv(o.gr); mv(o.gd); mv(o.v); mv(o.bsig);
+    mv(o.red); mv(o.red_count); mv(o.fvec); mv(o.yvec); mv(o.tin); mv(o.tout); mv(o.vstep);
+    mv(o.bd.partial); mv(o.bd.loc); mv(o.bd.loc32); mv(o.bd.sums); mv(o.H); mv(o.gw);
+    mv(o.gx); mv(o.gb); mv(o.gpart); mv(o.gs); mv(o.V); mv(o.region);
+    o.nrhs = 1;
+    o.slab = 0;
+    return o;
+}
+
 namespace {
 struct Temps {
     double2 *xi_o, *w_o;
@@ -375,6 +470,33 @@ int lbf_workspace_size(int M, const int64_t *island_ptr, const lbf_options *opt,
     return LBF_OK;
 }
 
+int lbf_batch_workspace_size(int M, const int64_t *island_ptr, const lbf_options *opt, int nrhs,
+                             size_t *bytes)
+{
+    if (nrhs < 1) return LBF_EINVAL;
+    size_t pb = 0;
+    int rc = lbf_workspace_size(M, island_ptr, opt, &pb);
+    if (rc) return rc;
+    *bytes = pb;
+    const bool lu = opt->schur == LBF_SCHUR_LU || (opt->schur == LBF_SCHUR_AUTO && M > 1024);
+    if (nrhs < 2 || opt->precision != LBF_PRECISION_FP64 || !opt->border || lu) return LBF_OK;
+    const int64_t N = island_ptr[M];
+    lbf_plan tmp;
+    tmp.N = N;
+    tmp.M = M;
+    tmp.n = N + M;
+    tmp.opt = *opt;
+    tmp.P = opt->p + 1;
+    tmp.arena.base = nullptr;
+    tmp.arena.cap = ~size_t(0);
+    lbf_layout(&tmp, N, M, *opt, box_capacity_estimate(N, *opt));
+    size_t need = 0;
+    if ((rc = lbf_many_view(&tmp, std::min(nrhs, LBF_LOCKSTEP_MAX), nullptr, 0, nullptr, &need)))
+        return rc;
+    *bytes = ((pb + 255) & ~size_t(255)) + need;
+    return LBF_OK;
+}
+
 static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const double *x,
                        const double *dx, const double *d2x, const double *centres,
                        const double *pole_rotation, int planar, const lbf_options *opt,
@@ -423,7 +545,7 @@ static int plan_create(lbf_plan **plan, int M, const int64_t *island_ptr, const 
         return code;
     };
     if (cudaHostAlloc((void **)&pl->host_status, 64, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&pl->host_scalars, 256, cudaHostAllocDefault) != cudaSuccess)
+        cudaHostAlloc((void **)&pl->host_scalars, 64 * (4 + 3 * LBF_LOCKSTEP_MAX), cudaHostAllocDefault) != cudaSuccess)
         return fail(LBF_ECUDA);
     for (auto &e : pl->ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LBF_ECUDA);
@@ -603,6 +725,27 @@ int lbf_gmres_solve(lbf_plan *pl, const double *g, double *sigma, double *a, con
     if (!pl || !g || !sigma) return LBF_EINVAL;
     if (!pl->opt.border) return LBF_ENOTBUILT;
     return lbf_gmres_impl(pl, g, sigma, a, x0, iters, rel_res, (cudaStream_t)stream, 0);
+}
+
+int lbf_gmres_workspace_many(const lbf_plan *pl, int nrhs, size_t *bytes)
+{
+    if (!pl || nrhs < 1 || !bytes) return LBF_EINVAL;
+    *bytes = 0;
+    if (pl->lu || pl->opt.precision != LBF_PRECISION_FP64 || !pl->opt.border) return LBF_OK;
+    return lbf_many_view(pl, std::min(nrhs, LBF_LOCKSTEP_MAX), nullptr, 0, nullptr, bytes);
+}
+
+int lbf_gmres_solve_many(lbf_plan *pl, int nrhs, const double *g, double *sigma, double *a,
+                         int *iters, double *rel_res, void *work, size_t bytes, lbf_stream_t stream)
+{
+    if (!pl || nrhs < 1 || !g || !sigma) return LBF_EINVAL;
+    if (!pl->opt.border) return LBF_ENOTBUILT;
+    size_t need = 0;
+    int rc = lbf_gmres_workspace_many(pl, nrhs, &need);
+    if (rc) return rc;
+    if (need > 0 && (!work || bytes < need || ((uintptr_t)work & 255))) return LBF_EWORKSPACE;
+    return lbf_gmres_many_impl(pl, nrhs, g, sigma, a, iters, rel_res, work, bytes,
+                               (cudaStream_t)stream);
 }
 
 int lbf_gmres_solve_transpose(lbf_plan *pl, const double *r, double *lam, const double *x0,

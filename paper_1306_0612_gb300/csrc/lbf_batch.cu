@@ -26,7 +26,38 @@ int run_item(lbf_batch_item &it, const lbf_options &opt_all, cudaStream_t s)
     }
     const int64_t N = pl->N;
     int worst = LBF_OK;
-    for (int r = 0; r < it.nrhs && worst >= 0; r++) {
+    // the right-hand sides in lockstep when the item's workspace holds their buffers
+    // after the plan's (lbf_batch_workspace_size)
+    size_t pbytes = 0, mbytes = 0;
+    lbf_workspace_size(it.M, it.island_ptr, &opt, &pbytes);
+    pbytes = (pbytes + 255) & ~size_t(255);
+    const bool lock = it.nrhs > 1 && lbf_gmres_workspace_many(pl, it.nrhs, &mbytes) == LBF_OK &&
+                      mbytes > 0 && it.bytes >= pbytes + mbytes;
+    if (lock) {
+        std::vector<int> its(it.nrhs, 0);
+        std::vector<double> rr(it.nrhs, 0.0);
+        rc = lbf_gmres_solve_many(pl, it.nrhs, it.g, it.sigma, it.a, its.data(), rr.data(),
+                                  (char *)it.workspace + pbytes, it.bytes - pbytes, (lbf_stream_t)s);
+        if (rc < 0) {
+            worst = rc;
+        } else {
+            if (rc == LBF_NOCONV) worst = LBF_NOCONV;
+            for (int r = 0; r < it.nrhs; r++) {
+                it.iters += its[r];
+                it.max_rel_res = std::max(it.max_rel_res, rr[r]);
+            }
+            int64_t st[4];
+            lbf_solve_stats(pl, st);
+            it.fp64_applies += st[1];
+            it.fp32_applies += st[2];
+            for (int r = 0; r < it.nrhs && it.T > 0 && it.u && worst >= 0; r++) {
+                rc = lbf_evaluate(pl, it.sigma + r * N, it.a ? it.a + (int64_t)r * it.M : nullptr,
+                                  it.T, it.targets, it.u + r * it.T, (lbf_stream_t)s);
+                if (rc) worst = rc;
+            }
+        }
+    }
+    for (int r = 0; r < it.nrhs && worst >= 0 && !lock; r++) {
         int its = 0;
         double rr = 0.0;
         rc = lbf_gmres_solve(pl, it.g + r * N, it.sigma + r * N, it.a ? it.a + (int64_t)r * it.M : nullptr,

@@ -470,8 +470,10 @@ __global__ void k_mp_p2l(int64_t nbox, int P, int M, const int32_t *__restrict__
                          const int32_t *__restrict__ ix, const int32_t *__restrict__ iy, Geo g,
                          const double2 *__restrict__ xc, const int32_t *__restrict__ kind,
                          const double *__restrict__ lam, const double *__restrict__ y,
-                         cz<R> *__restrict__ loc, double *__restrict__ sums, const int *gate)
+                         cz<R> *__restrict__ loc, double *__restrict__ sums, const int *gate,
+                         int64_t slab)
 {
+    lbf_rhs(slab, y, loc, sums, gate);
     if (gate && *gate == 0) return;
     extern __shared__ __align__(16) unsigned char smr[];
     int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -578,8 +580,9 @@ template <typename R>
 __global__ void k_mp_l2l(int64_t ls, int64_t le, int P, const int32_t *__restrict__ parent,
                          const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
                          const R *__restrict__ binom, const cz<R> *__restrict__ dtab,
-                         cz<R> *__restrict__ loc, const int *gate)
+                         cz<R> *__restrict__ loc, const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, loc, gate);
     if (gate && *gate == 0) return;
     extern __shared__ __align__(16) unsigned char smr[];
     const int nw = blockDim.x >> 5;
@@ -645,8 +648,9 @@ __global__ void k_mp_chain(int64_t nbox, int P, const int32_t *__restrict__ pare
                            const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
                            const int32_t *__restrict__ iy, const R *__restrict__ binom,
                            const cz<R> *__restrict__ dtab, cz<R> *loc, unsigned *pull, int *status,
-                           const int *gate)
+                           const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, loc, pull, gate);
     if (gate && *gate == 0) return;
     extern __shared__ __align__(16) unsigned char smr[];
     const int nw = blockDim.x >> 5;
@@ -815,8 +819,9 @@ __global__ void k_mp_near(int64_t nchunks, const int32_t *__restrict__ cleaf,
                           const int32_t *__restrict__ en, const double2 *__restrict__ xi,
                           const double2 *__restrict__ xc, const double *__restrict__ y,
                           const int32_t *__restrict__ nodebase, double *__restrict__ partial,
-                          const int *gate)
+                          const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, y, partial, gate);
     if (gate && *gate == 0) return;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -852,8 +857,10 @@ __global__ void k_mp_eval(int64_t N, int P, const double2 *__restrict__ xi,
                           double *__restrict__ out, const int *gate,
                           const int32_t *__restrict__ parent, const float2 *__restrict__ u32,
                           int walk, const cz<R> *__restrict__ uloc,
-                          const int32_t *__restrict__ nodebase, const double *__restrict__ partial)
+                          const int32_t *__restrict__ nodebase, const double *__restrict__ partial,
+                          int64_t slab)
 {
+    lbf_rhs(slab, loc, y, sums, x, v, out, gate, partial);
     if (gate && *gate == 0) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -1115,93 +1122,93 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
     if (f32) {
         int P = B.P32;
         size_t smem = sizeof(cz<float>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH(k_mp_p2l<float>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
+        LBF_LAUNCH(k_mp_p2l<float>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s, T.nbox, P, M,
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
-                   (cz<float> *)B.loc32, B.sums, gate);
+                   (cz<float> *)B.loc32, B.sums, gate, pl->slab);
         // float: the evaluation walks each node's ancestors (cheaper here than the L2L
         // chain, which is serial along each path while the walk is parallel over nodes)
         const bool chain = false;
         if (chain) {
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_chain<float>, grid, 32 * cw, l2l_smem<float>(P, cw), s,
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_chain<float>, lbf_grid(pl, grid), 32 * cw, l2l_smem<float>(P, cw), s,
                          T.nbox, P, T.parent, T.level, T.ix, T.iy, pl->tab32_binom,
                          (const cz<float> *)pl->tab32_dshift, (cz<float> *)B.loc32, pl->pull,
-                         pl->dev_status, gate);
+                         pl->dev_status, gate, pl->slab);
         }
         if (B.nchunks)
-            LBF_LAUNCH(k_mp_near<float>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks, B.chunk_leaf,
+            LBF_LAUNCH(k_mp_near<float>, lbf_grid(pl, lbf_cdiv(B.nchunks, 8)), 256, 0, s, B.nchunks, B.chunk_leaf,
                        B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi, B.xc, y,
-                       B.nodebase, B.partial, gate);
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_eval<float>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
+                       B.nodebase, B.partial, gate, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_eval<float>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N, P,
                      pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<float> *)B.loc32,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
                      out, gate, pl->anc, pl->u32, chain ? 0 : 1,
                      chain ? (const cz<float> *)pl->u32 : (const cz<float> *)nullptr, B.nodebase,
-                     B.partial);
+                     B.partial, pl->slab);
     } else if (pl->udf) {
         // the accurate operator in double-float (P2L terms formed in double)
         int P = B.Pe;
         size_t smem = sizeof(cz<df64>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<df64>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M,
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<df64>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s, T.nbox, P, M,
                    B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
-                   (cz<df64> *)B.loc, B.sums, gate);
+                   (cz<df64> *)B.loc, B.sums, gate, pl->slab);
         if (pl->pull) {  // the L2L chain in one launch
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<df64>, grid, 32 * cw, l2l_smem<df64>(P, cw), s, T.nbox, P, T.parent,
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<df64>, lbf_grid(pl, grid), 32 * cw, l2l_smem<df64>(P, cw), s, T.nbox, P, T.parent,
                        T.level, T.ix, T.iy, (const df64 *)pl->tabdf_binom,
                        (const cz<df64> *)pl->tabdf_dshift, (cz<df64> *)B.loc, pl->pull,
-                       pl->dev_status, gate);
+                       pl->dev_status, gate, pl->slab);
         } else {
             for (int l = 3; l < T.nlev; l++) {
                 int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
                 if (le <= ls) continue;
-                LBF_LAUNCH(k_mp_l2l<df64>, lbf_cdiv(le - ls, 8), 256, l2l_smem<df64>(P, 8), s, ls, le,
+                LBF_LAUNCH(k_mp_l2l<df64>, lbf_grid(pl, lbf_cdiv(le - ls, 8)), 256, l2l_smem<df64>(P, 8), s, ls, le,
                            P, T.parent, T.ix, T.iy, (const df64 *)pl->tabdf_binom,
-                           (const cz<df64> *)pl->tabdf_dshift, (cz<df64> *)B.loc, gate);
+                           (const cz<df64> *)pl->tabdf_dshift, (cz<df64> *)B.loc, gate, pl->slab);
             }
         }
         if (B.nchunks)
-            LBF_LAUNCH(k_mp_near<double>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks,
+            LBF_LAUNCH(k_mp_near<double>, lbf_grid(pl, lbf_cdiv(B.nchunks, 8)), 256, 0, s, B.nchunks,
                        B.chunk_leaf, B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi,
-                       B.xc, y, B.nodebase, B.partial, gate);
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<df64>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
+                       B.xc, y, B.nodebase, B.partial, gate, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<df64>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N, P,
                      pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<df64> *)B.loc,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
                      out, gate, T.parent, (const float2 *)nullptr, 0, (const cz<df64> *)pl->udf,
-                     B.nodebase, B.partial);
+                     B.nodebase, B.partial, pl->slab);
     } else {
         int P = B.Pe;
         size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<double>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox,
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<double>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s, T.nbox,
                      P, M, B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
-                     (cz<double> *)B.loc, B.sums, gate);
+                     (cz<double> *)B.loc, B.sums, gate, pl->slab);
         if (pl->pull) {  // the L2L chain in one launch
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<double>, grid, 32 * cw, l2l_smem<double>(P, cw), s, T.nbox, P,
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<double>, lbf_grid(pl, grid), 32 * cw, l2l_smem<double>(P, cw), s, T.nbox, P,
                        T.parent, T.level, T.ix, T.iy, pl->tab_binom,
                        (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, pl->pull,
-                       pl->dev_status, gate);
+                       pl->dev_status, gate, pl->slab);
         } else {
             for (int l = 3; l < T.nlev; l++) {
                 int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
                 if (le <= ls) continue;
-                LBF_LAUNCH(k_mp_l2l<double>, lbf_cdiv(le - ls, 8), 256, l2l_smem<double>(P, 8), s, ls,
+                LBF_LAUNCH(k_mp_l2l<double>, lbf_grid(pl, lbf_cdiv(le - ls, 8)), 256, l2l_smem<double>(P, 8), s, ls,
                            le, P, T.parent, T.ix, T.iy, pl->tab_binom,
-                           (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, gate);
+                           (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, gate, pl->slab);
             }
         }
         if (B.nchunks)
-            LBF_LAUNCH(k_mp_near<double>, lbf_cdiv(B.nchunks, 8), 256, 0, s, B.nchunks,
+            LBF_LAUNCH(k_mp_near<double>, lbf_grid(pl, lbf_cdiv(B.nchunks, 8)), 256, 0, s, B.nchunks,
                        B.chunk_leaf, B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi,
-                       B.xc, y, B.nodebase, B.partial, gate);
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<double>, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N,
+                       B.xc, y, B.nodebase, B.partial, gate, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<double>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N,
                      P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<double> *)B.loc,
                      B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
                      out, gate, T.parent, (const float2 *)nullptr, 0, (const cz<double> *)nullptr,
-                     B.nodebase, B.partial);
+                     B.nodebase, B.partial, pl->slab);
     }
     LBF_CHECK_LAUNCH();
     return LBF_OK;
@@ -1390,13 +1397,13 @@ int lbf_mp_gradient(lbf_plan *pl, const double *y, double2 *out, cudaStream_t s)
     size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
     LBF_LAUNCH(k_mp_p2l<double>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, T.nbox, P, M, B.p2l_ptr,
                B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y, (cz<double> *)B.loc,
-               B.sums, (const int *)nullptr);
+               B.sums, (const int *)nullptr, (int64_t)0);
     for (int l = 3; l < T.nlev; l++) {
         int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
         if (le <= ls) continue;
         LBF_LAUNCH(k_mp_l2l<double>, lbf_cdiv(le - ls, 8), 256, l2l_smem<double>(P, 8), s, ls, le,
                    P, T.parent, T.ix, T.iy, pl->tab_binom, (const cz<double> *)pl->tab_dshift,
-                   (cz<double> *)B.loc, (const int *)nullptr);
+                   (cz<double> *)B.loc, (const int *)nullptr, (int64_t)0);
     }
     LBF_LAUNCH(k_mp_grad, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P, pl->xi, B.leaf_of, T.level,
                T.ix, T.iy, g, (const cz<double> *)B.loc, B.near_ptr, B.near_src, B.glob,

@@ -39,8 +39,10 @@ __global__ void k_prep(int64_t N, const double *__restrict__ sigma, const double
                        float2 *__restrict__ q32, cx<df64> *__restrict__ qdf,
                        double *__restrict__ part, unsigned *__restrict__ count,
                        double *__restrict__ out, const int *gate,
-                       const int32_t *__restrict__ isl, const double *__restrict__ mean)
+                       const int32_t *__restrict__ isl, const double *__restrict__ mean,
+                       int64_t slab)
 {
+    lbf_rhs(slab, sigma, q, q32, qdf, part, count, out, gate, mean);
     if (fmm::gate_closed(gate)) return;
     __shared__ double sh[32];
     __shared__ bool last;
@@ -167,8 +169,9 @@ __global__ void k_island_modes_end(double *__restrict__ scal, unsigned *__restri
 // (0 where the split is off)
 __global__ void k_island_means(int M, const int64_t *__restrict__ ptr, const int32_t *__restrict__ rank,
                                const double *__restrict__ sigma, double *__restrict__ mean,
-                               const int *gate)
+                               const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, sigma, mean, gate);
     if (fmm::gate_closed(gate)) return;
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -186,8 +189,10 @@ template <int MODE>
 __global__ void k_direct(int64_t N, const double2 *__restrict__ xi, const double2 *__restrict__ q,
                          const double *__restrict__ sigma, const double *__restrict__ dself,
                          const double2 *__restrict__ w, const double *__restrict__ beta,
-                         const double *__restrict__ bsig, double *__restrict__ v, const int *gate)
+                         const double *__restrict__ bsig, double *__restrict__ v, const int *gate,
+                         int64_t slab)
 {
+    lbf_rhs(slab, q, sigma, bsig, v, gate);
     if (fmm::gate_closed(gate)) return;
     __shared__ double2 sx[256], sq[256];
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -502,10 +507,10 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
     const int kid_leaf = dbl ? LBF_KERNEL_LEAF : LBF_KERNEL_LEAF32;
     {
         const int wpb = 2;
-        LBF_LAUNCH_P(kid_up, fmm::k_up<R>, lbf_cdiv(T.nleaf, wpb), 32 * wpb,
+        LBF_LAUNCH_P(kid_up, fmm::k_up<R>, lbf_grid(pl, lbf_cdiv(T.nleaf, wpb)), 32 * wpb,
                      up_smem<R>(P, wpb), s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                      T.end, T.parent, T.child0, T.nchild, g, P, binom, dsh, pl->xi, uloc, q,
-                     mp, pl->upcnt, gate);
+                     mp, pl->upcnt, gate, pl->slab);
         LBF_CHECK_LAUNCH();
     }
     // float forward rows: no chain, the far field comes from the per-node walk below
@@ -519,42 +524,42 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
         const int wpb = down_warps<R>(P);
         const size_t smem = down_smem<R>(P, wpb);
         if (walk) {  // every box's own M2L + P2L, a warp per box, no chain
-            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(T.nbox, wpb), 32 * wpb, smem, s, (int64_t)0,
-                         T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin,
-                         T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate, 0,
-                         (unsigned *)nullptr, pl->dev_status, udf);
+            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s,
+                         (int64_t)0, T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist,
+                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate,
+                         0, (unsigned *)nullptr, pl->dev_status, udf, pl->slab);
             LBF_CHECK_LAUNCH();
         } else if (pl->pull) {
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, wpb), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, grid, 32 * wpb, smem, s, (int64_t)0, T.nbox,
-                         T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin, T.end,
-                         g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate, 2, pl->pull,
-                         pl->dev_status, udf);
+            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_grid(pl, grid), 32 * wpb, smem, s, (int64_t)0,
+                         T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx, T.begin,
+                         T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate, 2, pl->pull,
+                         pl->dev_status, udf, pl->slab);
             LBF_CHECK_LAUNCH();
         } else {
             for (int l = 0; l < T.nlev; l++) {
                 int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
                 if (le <= ls) continue;
-                LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_cdiv(le - ls, wpb), 32 * wpb, smem, s,
-                             ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist, T.nx,
-                             T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc,
-                             gate, 1, (unsigned *)nullptr, pl->dev_status, udf);
+                LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_grid(pl, lbf_cdiv(le - ls, wpb)), 32 * wpb,
+                             smem, s, ls, le, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist,
+                             T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc,
+                             gate, 1, (unsigned *)nullptr, pl->dev_status, udf, pl->slab);
                 LBF_CHECK_LAUNCH();
             }
         }
     }
     const int lw = pl->opt.p2p_warps > 0 ? pl->opt.p2p_warps : fmm::kLeafWarps;
-    LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_cdiv(T.nleaf, lw), 32 * lw,
+    LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_grid(pl, lbf_cdiv(T.nleaf, lw)), 32 * lw,
                  (fmm::leaf_smem<R, MODE>(lw)), s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
                  T.end, T.u_ptr, T.u_idx, T.w_ptr, T.w_idx, g, P, pl->xi, uloc, q, mp, loc,
                  sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf, walk ? 0 : 1,
                  split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
                  split ? (const double *)pl->imean : (const double *)nullptr,
-                 split ? (const double *)pl->iacoef : (const double *)nullptr, pl->M);
+                 split ? (const double *)pl->iacoef : (const double *)nullptr, pl->M, pl->slab);
     if (walk) {
-        LBF_LAUNCH_P(kid_leaf, fmm::k_l2p_walk, lbf_cdiv(pl->N, 256), 256, 0, s, pl->N, P,
-                     pl->bd.leaf_of, T.level, T.ix, T.iy, pl->anc, (const float2 *)uloc,
-                     (const cx<float> *)loc, v, gate);
+        LBF_LAUNCH_P(kid_leaf, fmm::k_l2p_walk, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N,
+                     P, pl->bd.leaf_of, T.level, T.ix, T.iy, pl->anc, (const float2 *)uloc,
+                     (const cx<float> *)loc, v, gate, pl->slab);
     }
     LBF_CHECK_LAUNCH();
     return LBF_OK;
@@ -600,15 +605,15 @@ static int prep(lbf_plan *pl, const double *sigma, Arith ar, bool weighted, cons
 {
     int nb = (int)std::min<int64_t>(lbf_cdiv(pl->N, 256), 1024);
     if (split)
-        LBF_LAUNCH(k_island_means, lbf_cdiv((int64_t)pl->M * 32, 256), 256, 0, s, pl->M,
-                   pl->island_ptr, pl->rank, sigma, pl->imean, gate);
-    LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma, weighted ? pl->w : (const double2 *)nullptr,
+        LBF_LAUNCH(k_island_means, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s,
+                   pl->M, pl->island_ptr, pl->rank, sigma, pl->imean, gate, pl->slab);
+    LBF_LAUNCH(k_prep, lbf_grid(pl, nb), 256, 0, s, pl->N, sigma, weighted ? pl->w : (const double2 *)nullptr,
                weighted ? pl->beta : (const double *)nullptr,
                ar == Arith::F64 ? pl->q : (double2 *)nullptr,
                ar == Arith::F32 ? pl->q32 : (float2 *)nullptr,
                ar == Arith::DF64 ? (cx<df64> *)pl->qdf : (cx<df64> *)nullptr, pl->red,
                pl->red_count, pl->bsig, gate, split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
-               split ? (const double *)pl->imean : (const double *)nullptr);
+               split ? (const double *)pl->imean : (const double *)nullptr, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -629,8 +634,8 @@ static int apply_mode(lbf_plan *pl, const double *sigma, double *v, const int *g
     if (rc) return rc;
     int64_t N = pl->N;
     if (pl->opt.matvec == LBF_MATVEC_DIRECT) {
-        LBF_LAUNCH_P(LBF_KERNEL_DIRECT, k_direct<MODE>, lbf_cdiv(N, 256), 256, 0, s, N, pl->xi,
-                     pl->q, sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate);
+        LBF_LAUNCH_P(LBF_KERNEL_DIRECT, k_direct<MODE>, lbf_grid(pl, lbf_cdiv(N, 256)), 256, 0, s, N,
+                     pl->xi, pl->q, sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, pl->slab);
         LBF_CHECK_LAUNCH();
         return LBF_OK;
     }
@@ -679,7 +684,7 @@ int lbf_multipoles(lbf_plan *pl, const double *x, int P, double2 *mp, const int 
                T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin, T.end, T.parent, T.child0,
                T.nchild, g, P, pl->tab_binom, (const cx<double> *)pl->tab_dshift, pl->xi,
                (const cx<double> *)nullptr, (const cx<double> *)pl->q, (cx<double> *)mp,
-               pl->upcnt, gate);
+               pl->upcnt, gate, (int64_t)0);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -716,7 +721,7 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
         int nb = (int)std::min<int64_t>(lbf_cdiv(pl->N, 256), 1024);
         LBF_LAUNCH(k_prep, nb, 256, 0, s, pl->N, sigma_sorted, pl->w, pl->beta, pl->q,
                    (float2 *)nullptr, (cx<df64> *)pl->qdf, pl->red, pl->red_count, pl->bsig,
-                   (const int *)nullptr, (const int32_t *)nullptr, (const double *)nullptr);
+                   (const int *)nullptr, (const int32_t *)nullptr, (const double *)nullptr, (int64_t)0);
         LBF_CHECK_LAUNCH();
         Tree &Tr = pl->tree;
         BoxGeo g{Tr.xmin, Tr.ymin, Tr.L, (float)(1.0 / Tr.L), df64(1.0 / Tr.L), 1.0 / Tr.L};
@@ -726,7 +731,7 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
                    Tr.child0, Tr.nchild, g, P, (const df64 *)pl->tabdf_binom,
                    (const cx<df64> *)pl->tabdf_dshift, pl->xi, (const cx<df64> *)pl->udf,
                    (const cx<df64> *)pl->qdf, (cx<df64> *)pl->mpole, pl->upcnt,
-                   (const int *)nullptr);
+                   (const int *)nullptr, (int64_t)0);
         LBF_LAUNCH(k_evaluate_tree<df64>, lbf_cdiv(T, kEvalWarps), 32 * kEvalWarps,
                    sizeof(int32_t) * 2 * kEvalFront * kEvalWarps, s, pl->N, pl->M, pl->xi, pl->q,
                    (const cx<df64> *)pl->mpole, P, Tr.level, Tr.ix, Tr.iy, Tr.child0, Tr.nchild,
@@ -746,7 +751,7 @@ int lbf_evaluate_impl(lbf_plan *pl, const double *sigma_sorted, const double *a,
                    Tr.nleaf, Tr.leaves, Tr.level, Tr.ix, Tr.iy, Tr.begin, Tr.end, Tr.parent,
                    Tr.child0, Tr.nchild, g, P, pl->tab_binom, (const cx<double> *)pl->tab_dshift,
                    pl->xi, (const cx<double> *)nullptr, (const cx<double> *)pl->q,
-                   (cx<double> *)pl->mpole, pl->upcnt, (const int *)nullptr);
+                   (cx<double> *)pl->mpole, pl->upcnt, (const int *)nullptr, (int64_t)0);
         LBF_LAUNCH(k_evaluate_tree<double>, lbf_cdiv(T, kEvalWarps), 32 * kEvalWarps,
                    sizeof(int32_t) * 2 * kEvalFront * kEvalWarps, s, pl->N, pl->M, pl->xi, pl->q,
                    (const cx<double> *)pl->mpole, P, Tr.level, Tr.ix, Tr.iy, Tr.child0, Tr.nchild,

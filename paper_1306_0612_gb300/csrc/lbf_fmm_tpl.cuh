@@ -249,8 +249,10 @@ __global__ void k_up(int64_t nleaf, const int32_t *__restrict__ leaves,
                      const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
                      BoxGeo g, int P, const R *__restrict__ binom, const cx<R> *__restrict__ dtab,
                      const double2 *__restrict__ xi, const cx<R> *__restrict__ uloc,
-                     const cx<R> *__restrict__ q, cx<R> *mp, int *cnt, const int *gate)
+                     const cx<R> *__restrict__ q, cx<R> *mp, int *cnt, const int *gate,
+                     int64_t slab)
 {
+    lbf_rhs(slab, q, mp, cnt, gate);
     if (gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int nw = blockDim.x >> 5;
@@ -418,8 +420,10 @@ k_down(int64_t ls, int64_t le, const int32_t *__restrict__ level,
                        const cx<R> *__restrict__ dtab, const double2 *__restrict__ xi,
                        const cx<R> *__restrict__ uloc, const cx<R> *__restrict__ q,
                        const cx<R> *__restrict__ mp, cx<R> *__restrict__ loc, const int *gate,
-                       int with_l2l, unsigned *pull, int *status, const cx<df64> *__restrict__ udf)
+                       int with_l2l, unsigned *pull, int *status, const cx<df64> *__restrict__ udf,
+                       int64_t slab)
 {
+    lbf_rhs(slab, q, mp, loc, gate, pull);
     if (gate_closed(gate)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int nw = blockDim.x >> 5;
@@ -948,8 +952,9 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const double *__restrict__ beta, const double *__restrict__ bsig,
                        double *__restrict__ v, const int *gate, const cx<df64> *__restrict__ udf,
                        int l2p, const int32_t *__restrict__ isl, const double *__restrict__ imean,
-                       const double *__restrict__ iacoef, int M)
+                       const double *__restrict__ iacoef, int M, int64_t slab)
 {
+    lbf_rhs(slab, q, mp, loc, sigma, bsig, v, gate, imean);
     if (gate_closed(gate)) return;
     constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
     // per warp, kSrcChunk staged sources (position in units of r, charge); the warps per
@@ -1293,8 +1298,9 @@ __global__ void k_l2p_walk(int64_t N, int P, const int32_t *__restrict__ leaf_of
                            const int32_t *__restrict__ level, const int32_t *__restrict__ ix,
                            const int32_t *__restrict__ iy, const int32_t *__restrict__ anc,
                            const float2 *__restrict__ u32, const cx<float> *__restrict__ loc,
-                           double *__restrict__ v, const int *gate)
+                           double *__restrict__ v, const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, loc, v, gate);
     if (gate_closed(gate)) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;

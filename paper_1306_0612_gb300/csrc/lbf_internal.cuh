@@ -207,7 +207,29 @@ struct lbf_plan {
     // tree build), and its fork and join events
     cudaStream_t side = nullptr;
     cudaEvent_t fork[2] = {nullptr, nullptr};
+    // Right-hand sides advanced together (lbf_gmres_solve_many): a launch on a plan view
+    // with nrhs > 1 covers all of them, blockIdx.y = the right-hand side, whose buffers
+    // sit blockIdx.y * slab bytes after those the view points at (1 and 0 on a plan).
+    int nrhs = 1;
+    int64_t slab = 0;
 };
+
+// grid of a launch over the plan's right-hand sides
+static inline dim3 lbf_grid(const lbf_plan *pl, int64_t gx)
+{
+    return dim3((unsigned)gx, (unsigned)pl->nrhs, 1u);
+}
+
+#ifdef __CUDACC__
+// Moves each per-right-hand-side pointer of a kernel to right-hand side blockIdx.y
+// (null pointers stay null; slab 0 leaves them as they are).
+template <class... Ts> __device__ __forceinline__ void lbf_rhs(int64_t slab, Ts &...p)
+{
+    if (slab == 0) return;
+    const int64_t o = (int64_t)blockIdx.y * slab;
+    ((p = p ? (Ts)((const char *)p + o) : p), ...);
+}
+#endif
 
 // ---- failure injection for tests (lbf_debug_inject) ------------------------------
 // A barrier injection is consumed by the next plan creation on the calling thread:
@@ -307,6 +329,13 @@ int lbf_precondition_rhs(lbf_plan *pl, const double *g2_sorted, double *out, cud
 int lbf_precondition_rhs_t(lbf_plan *pl, const double *r_sorted, double *out, cudaStream_t s);
 int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, const double *x0,
                    int *iters, double *rel_res, cudaStream_t s, int transpose);
+// lockstep right-hand sides (lbf_gmres_solve_many)
+#define LBF_LOCKSTEP_MAX 16  // right-hand sides of one lockstep group
+int lbf_many_view(const lbf_plan *pl, int R, void *work, size_t bytes, lbf_plan *view,
+                  size_t *need);
+lbf_plan lbf_view_at(const lbf_plan &v, int r);
+int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, double *a,
+                        int *iters, double *rel_res, void *work, size_t bytes, cudaStream_t s);
 int lbf_dot(lbf_plan *pl, const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
 // ---- adjoint (lbf_adjoint.cu) ---------------------------------------------------------
 int lbf_evaluate_transpose_impl(lbf_plan *pl, int64_t T, const double *t, const double *ub,

@@ -62,8 +62,9 @@ __global__ void k_permute_out(int64_t N, int M, const int32_t *__restrict__ perm
 // fixed order (caller order within the island).  Row M-1 of F is zero.
 __global__ void k_island_sums(int M, const int64_t *__restrict__ ptr, const int32_t *__restrict__ rank,
                               const double *__restrict__ u, double scale, double *__restrict__ out,
-                              const int *gate)
+                              const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, u, out, gate);
     if (gate_closed(gate)) return;
     int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (r >= M) return;
@@ -76,8 +77,9 @@ __global__ void k_island_sums(int M, const int64_t *__restrict__ ptr, const int3
 
 // y = alpha S^-1 f (one warp per row)
 __global__ void k_small_gemv(int M, const double *__restrict__ A, const double *__restrict__ f,
-                             double alpha, double *__restrict__ y, const int *gate)
+                             double alpha, double *__restrict__ y, const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, f, y, gate);
     if (gate_closed(gate)) return;
     int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (r >= M) return;
@@ -88,8 +90,9 @@ __global__ void k_small_gemv(int M, const double *__restrict__ A, const double *
 }
 
 __global__ void k_add(int64_t n, const double *__restrict__ x, const double *__restrict__ v,
-                      double *__restrict__ out, const int *gate)
+                      double *__restrict__ out, const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, x, v, out, gate);
     if (gate_closed(gate)) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = x[i] + v[i];
@@ -99,8 +102,9 @@ __global__ void k_add(int64_t n, const double *__restrict__ x, const double *__r
 //   mode 0 (A x):      out_r = f_r (r < M-1), out_{M-1} = sum_m a_m
 //   mode 1 (P^-1 A x): out_m = a_m - y_m
 __global__ void k_arows(int M, int mode, const double *__restrict__ a, const double *__restrict__ f,
-                        double *__restrict__ out, const int *gate)
+                        double *__restrict__ out, const int *gate, int64_t slab)
 {
+    lbf_rhs(slab, a, f, out, gate);
     if (gate_closed(gate)) return;
     int m = threadIdx.x;
     if (mode == 0) {
@@ -160,8 +164,9 @@ __global__ void k_add_last(int M, const double *__restrict__ c, double *__restri
 // the Arnoldi input v_j of the current step (j from the device state) into a fixed buffer
 template <typename T>
 __global__ void k_copy_vj(int64_t n, const T *__restrict__ V, int64_t ldv,
-                          const GmresState *__restrict__ st, double *__restrict__ out)
+                          const GmresState *__restrict__ st, double *__restrict__ out, int64_t slab)
 {
+    lbf_rhs(slab, V, st, out);
     if (st->go == 0) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (double)V[(int64_t)st->j * ldv + i];
@@ -205,8 +210,9 @@ __device__ bool finish_block(unsigned *count)
 template <typename T>
 __global__ void k_arnoldi(int64_t n, const T *__restrict__ V, int64_t ldv, const double *w,
                           T *wt, double *part, unsigned *count, double *hbuf, double *H,
-                          double *cs, double *sn, double *gv, GmresState *st, int mode)
+                          double *cs, double *sn, double *gv, GmresState *st, int mode, int64_t slab)
 {
+    lbf_rhs(slab, V, w, wt, part, count, hbuf, H, cs, sn, gv, st);
     if (st->go == 0) return;
     extern __shared__ double sh[];
     int m = st->m;
@@ -310,8 +316,9 @@ __global__ void k_arnoldi(int64_t n, const T *__restrict__ V, int64_t ldv, const
 // V[j] = w * inv (j = st->j after the Arnoldi step)
 template <typename T>
 __global__ void k_scale_next(int64_t n, const T *__restrict__ w, T *V, int64_t ldv,
-                             const GmresState *st)
+                             const GmresState *st, int64_t slab)
 {
+    lbf_rhs(slab, w, V, st);
     if (st->go == 0) return;
     int j = st->j;
     const T inv = (T)st->inv;
@@ -322,8 +329,9 @@ __global__ void k_scale_next(int64_t n, const T *__restrict__ w, T *V, int64_t l
 }
 
 // end of a cycle: y = H^-1 g (upper triangular, j columns), x += V y
-__global__ void k_solve_y(const double *H, const double *gv, double *y, GmresState *st)
+__global__ void k_solve_y(const double *H, const double *gv, double *y, GmresState *st, int64_t slab)
 {
+    lbf_rhs(slab, H, gv, y, st);
     if (threadIdx.x != 0) return;
     int m = st->m, j = st->j;
     for (int i = j - 1; i >= 0; i--) {
@@ -335,8 +343,9 @@ __global__ void k_solve_y(const double *H, const double *gv, double *y, GmresSta
 
 template <typename T>
 __global__ void k_xupdate(int64_t n, const T *__restrict__ V, int64_t ldv,
-                          const double *__restrict__ y, const GmresState *st, double *x)
+                          const double *__restrict__ y, const GmresState *st, double *x, int64_t slab)
 {
+    lbf_rhs(slab, V, y, st, x);
     int j = st->j;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -352,8 +361,15 @@ __global__ void k_xupdate(int64_t n, const T *__restrict__ V, int64_t ldv,
 template <typename T>
 __global__ void k_restart(int64_t n, const double *__restrict__ b, const double *__restrict__ Ax,
                           T *V, double *part, unsigned *count, double *gv, GmresState *st,
-                          int init, const double *__restrict__ bn)
+                          int init, const double *__restrict__ bn, int64_t slab)
 {
+    lbf_rhs(slab, b, Ax, V, part, count, gv, st, bn);
+    // a restart of a system that has finished (the others of a lockstep solve go on)
+    // leaves it as it is, with no columns left to add to its solution
+    if (!init && (st->converged || st->it >= st->maxit)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->j = 0;
+        return;
+    }
     __shared__ double wsum[32];
     double nrm = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -393,8 +409,9 @@ __global__ void k_restart(int64_t n, const double *__restrict__ b, const double 
 }
 
 template <typename T>
-__global__ void k_scale_first(int64_t n, T *V, const GmresState *st)
+__global__ void k_scale_first(int64_t n, T *V, const GmresState *st, int64_t slab)
 {
+    lbf_rhs(slab, V, st);
     const T inv = (T)st->inv;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -404,8 +421,9 @@ __global__ void k_scale_first(int64_t n, T *V, const GmresState *st)
 // ||v|| with a fixed-order reduction: block partials, then the last block to finish
 // sums them (strided, then by warps) and resets the counter
 __global__ void k_norm2(int64_t n, const double *__restrict__ v, double *part, unsigned *count,
-                        double *out)
+                        double *out, int64_t slab)
 {
+    lbf_rhs(slab, v, part, count, out);
     __shared__ double wsum[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double s = 0.0;
@@ -435,35 +453,40 @@ __global__ void k_norm2(int64_t n, const double *__restrict__ v, double *part, u
     }
 }
 
-__global__ void k_init_state(GmresState *st, int m, int maxit, double tol)
+__global__ void k_init_state(GmresState *st, int m, int maxit, double tol, int64_t slab)
 {
+    lbf_rhs(slab, st);
     st->go = 0; st->j = 0; st->it = 0; st->converged = 0;
     st->m = m; st->maxit = maxit; st->tol = tol;
     st->bnorm = 0; st->beta = 0; st->resid = 0; st->inv = 0;
 }
 
-__global__ void k_scale(int64_t n, double alpha, double *p)
+__global__ void k_scale(int64_t n, double alpha, double *p, int64_t slab)
 {
+    lbf_rhs(slab, p);
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) p[i] *= alpha;
 }
 
 // out = alpha x + beta y (out may alias x or y)
 __global__ void k_axpby(int64_t n, double alpha, const double *x, double beta, const double *y,
-                        double *out)
+                        double *out, int64_t slab)
 {
+    lbf_rhs(slab, x, y, out);
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = alpha * x[i] + beta * y[i];
 }
 
-__global__ void k_widen(int64_t n, const float *__restrict__ in, double *__restrict__ out)
+__global__ void k_widen(int64_t n, const float *__restrict__ in, double *__restrict__ out, int64_t slab)
 {
+    lbf_rhs(slab, in, out);
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (double)in[i];
 }
 
-__global__ void k_fill(double *p, int64_t n, double v)
+__global__ void k_fill(double *p, int64_t n, double v, int64_t slab)
 {
+    lbf_rhs(slab, p);
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
 }
@@ -500,8 +523,8 @@ static int esum(lbf_plan *pl, const double *x, const double *v, const double *c,
 static int island_sums(lbf_plan *pl, const double *u, double scale, double *out, const int *gate,
                        cudaStream_t s)
 {
-    LBF_LAUNCH(k_island_sums, lbf_cdiv((int64_t)pl->M * 32, 256), 256, 0, s, pl->M, pl->island_ptr,
-               pl->rank, u, scale, out, gate);
+    LBF_LAUNCH(k_island_sums, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s, pl->M, pl->island_ptr,
+               pl->rank, u, scale, out, gate, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -510,8 +533,8 @@ static int small_gemv(lbf_plan *pl, const double *f, double alpha, double *y, co
                       cudaStream_t s)
 {
     if (pl->lu) return lbf_schur_lu_apply(pl, f, alpha, y, 0, gate, s, !pl->lu_fast);
-    LBF_LAUNCH(k_small_gemv, lbf_cdiv((int64_t)pl->M * 32, 256), 256, 0, s, pl->M, pl->Sinv, f,
-               alpha, y, gate);
+    LBF_LAUNCH(k_small_gemv, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s, pl->M, pl->Sinv, f,
+               alpha, y, gate, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -546,7 +569,7 @@ static int apply_op_transposed(lbf_plan *pl, int op, const double *in, double *o
     int M = pl->M;
     int rc = lbf_apply_KT(pl, in, pl->v, gate, s, prec);
     if (rc) return rc;
-    LBF_LAUNCH(k_add, lbf_cdiv(N, 256), 256, 0, s, N, in, pl->v, out, gate);
+    LBF_LAUNCH(k_add, lbf_grid(pl, lbf_cdiv(N, 256)), 256, 0, s, N, in, pl->v, out, gate, pl->slab);
     LBF_CHECK_LAUNCH();
     if (op == LBF_OP_K_ONLY) return LBF_OK;
     if (!pl->opt.border) return LBF_ENOTBUILT;
@@ -560,7 +583,7 @@ static int apply_op_transposed(lbf_plan *pl, int op, const double *in, double *o
     if ((rc = lbf_mp_apply_transpose(pl, pl->v, 1.0, nullptr, pl->fvec, gate, s))) return rc;
     if ((rc = small_gemv_t(pl, pl->fvec, -1.0, pl->yvec, gate, s))) return rc;
     if ((rc = island_scatter(pl, out, pl->yvec, -1.0, out, gate, s))) return rc;
-    LBF_LAUNCH(k_add, lbf_cdiv(M, 128), 128, 0, s, M, in + N, pl->yvec, out + N, gate);
+    LBF_LAUNCH(k_add, lbf_grid(pl, lbf_cdiv(M, 128)), 128, 0, s, M, in + N, pl->yvec, out + N, gate, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -584,7 +607,7 @@ int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, con
     int rc = lbf_apply_K(pl, in, pl->v, gate, s, prec);
     if (rc) return rc;
     if (op == LBF_OP_K_ONLY) {
-        LBF_LAUNCH(k_add, lbf_cdiv(N, 256), 256, 0, s, N, in, pl->v, out, gate);
+        LBF_LAUNCH(k_add, lbf_grid(pl, lbf_cdiv(N, 256)), 256, 0, s, N, in, pl->v, out, gate, pl->slab);
         LBF_CHECK_LAUNCH();
         return LBF_OK;
     }
@@ -592,7 +615,7 @@ int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, con
     if (op == LBF_OP_FULL) {
         if ((rc = island_sums(pl, in, 1.0, pl->fvec, gate, s))) return rc;
         if ((rc = esum(pl, in, pl->v, in + N, 1.0, out, gate, s))) return rc;
-        LBF_LAUNCH(k_arows, 1, 256, 0, s, M, 0, in + N, pl->fvec, out + N, gate);
+        LBF_LAUNCH(k_arows, lbf_grid(pl, 1), 256, 0, s, M, 0, in + N, pl->fvec, out + N, gate, pl->slab);
         LBF_CHECK_LAUNCH();
         return LBF_OK;
     }
@@ -600,7 +623,7 @@ int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, con
     if ((rc = island_sums(pl, pl->v, 1.0, pl->fvec, gate, s))) return rc;
     if ((rc = small_gemv(pl, pl->fvec, 1.0, pl->yvec, gate, s))) return rc;
     if ((rc = esum(pl, in, pl->v, pl->yvec, 1.0, out, gate, s, prec))) return rc;
-    LBF_LAUNCH(k_arows, 1, 256, 0, s, M, 1, in + N, pl->yvec, out + N, gate);
+    LBF_LAUNCH(k_arows, lbf_grid(pl, 1), 256, 0, s, M, 1, in + N, pl->yvec, out + N, gate, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -652,10 +675,10 @@ static int arnoldi_step_t(lbf_plan *pl, int opc, int prec, int k, bool from_stat
         // the operator reads v_j in double: from the device's j (graph-replayable), or a
         // float basis vector widened
         if (from_state) {
-            LBF_LAUNCH(k_copy_vj<T>, lbf_cdiv(n, 256), 256, 0, s, n, V, ldv, pl->gs, pl->vstep);
+            LBF_LAUNCH(k_copy_vj<T>, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, V, ldv, pl->gs, pl->vstep, pl->slab);
         } else {
-            LBF_LAUNCH(k_widen, lbf_cdiv(n, 256), 256, 0, s, n, (const float *)(V + (int64_t)k * ldv),
-                       pl->vstep);
+            LBF_LAUNCH(k_widen, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, (const float *)(V + (int64_t)k * ldv),
+                       pl->vstep, pl->slab);
         }
         vj = pl->vstep;
     }
@@ -667,9 +690,9 @@ static int arnoldi_step_t(lbf_plan *pl, int opc, int prec, int k, bool from_stat
     pl->lu_fast = 0;
     if (rc) return rc;
     for (int mode = 0; mode < 3; mode++)
-        LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi<T>, nblk, 256, smem, s, n, V, ldv, w, wt, pl->gpart,
-                     count, hbuf, pl->H, cs, sn, gv, pl->gs, mode);
-    LBF_LAUNCH(k_scale_next<T>, nblk, 256, 0, s, n, wt, V, ldv, pl->gs);
+        LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi<T>, lbf_grid(pl, nblk), 256, smem, s, n, V, ldv, w, wt, pl->gpart,
+                     count, hbuf, pl->H, cs, sn, gv, pl->gs, mode, pl->slab);
+    LBF_LAUNCH(k_scale_next<T>, lbf_grid(pl, nblk), 256, 0, s, n, wt, V, ldv, pl->gs, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -729,7 +752,7 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
     double *cs = hbuf + 2 * (m + 1), *sn = cs + m, *gv = sn + m, *y = gv + (m + 1);
     unsigned *count = pl->red_count + 1;
     int64_t *applies = prec == LBF_PREC_FP32 ? &pl->stats[2] : &pl->stats[1];
-    LBF_LAUNCH(k_init_state, 1, 1, 0, s, pl->gs, m, maxit, tol);
+    LBF_LAUNCH(k_init_state, lbf_grid(pl, 1), 1, 0, s, pl->gs, m, maxit, tol, pl->slab);
     LBF_CHECK_LAUNCH();
     const double *Ax = nullptr;
     if (x_given) {
@@ -737,19 +760,19 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
         (*applies)++;
         Ax = w;
     } else {
-        LBF_LAUNCH(k_fill, lbf_cdiv(n, 256), 256, 0, s, x, n, 0.0);
+        LBF_LAUNCH(k_fill, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, x, n, 0.0, pl->slab);
         LBF_CHECK_LAUNCH();
     }
     const bool f32 = prec == LBF_PREC_FP32;
     float *V32 = basis32(pl);
     if (f32) {
-        LBF_LAUNCH(k_restart<float>, nblk, 256, 0, s, n, b, Ax, V32, pl->gpart, count, gv, pl->gs, 1,
-                   bnorm_dev);
-        LBF_LAUNCH(k_scale_first<float>, nblk, 256, 0, s, n, V32, pl->gs);
+        LBF_LAUNCH(k_restart<float>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V32, pl->gpart, count, gv, pl->gs, 1,
+                   bnorm_dev, pl->slab);
+        LBF_LAUNCH(k_scale_first<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, pl->gs, pl->slab);
     } else {
-        LBF_LAUNCH(k_restart<double>, nblk, 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1,
-                   bnorm_dev);
-        LBF_LAUNCH(k_scale_first<double>, nblk, 256, 0, s, n, V, pl->gs);
+        LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1,
+                   bnorm_dev, pl->slab);
+        LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
     }
     LBF_CHECK_LAUNCH();
     cudaGraphExec_t sg = step_graph(pl, opc, prec, s);
@@ -789,9 +812,9 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
             LBF_CUDA(cudaEventRecord(pl->ev[slot], s));
         }
         // cycle end: x += V y
-        LBF_LAUNCH(k_solve_y, 1, 32, 0, s, pl->H, gv, y, pl->gs);
-        if (f32) LBF_LAUNCH(k_xupdate<float>, nblk, 256, 0, s, n, V32, ldv, y, pl->gs, x);
-        else LBF_LAUNCH(k_xupdate<double>, nblk, 256, 0, s, n, V, ldv, y, pl->gs, x);
+        LBF_LAUNCH(k_solve_y, lbf_grid(pl, 1), 32, 0, s, pl->H, gv, y, pl->gs, pl->slab);
+        if (f32) LBF_LAUNCH(k_xupdate<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, ldv, y, pl->gs, x, pl->slab);
+        else LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x, pl->slab);
         LBF_CHECK_LAUNCH();
         if ((rc = read_state(pl, &hs, s))) return rc;
         if (hs.converged || hs.it >= hs.maxit) break;
@@ -799,13 +822,13 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
         if ((rc = lbf_apply_op_sorted(pl, opc, x, w, nullptr, s, prec))) return rc;
         (*applies)++;
         if (f32) {
-            LBF_LAUNCH(k_restart<float>, nblk, 256, 0, s, n, b, w, V32, pl->gpart, count, gv, pl->gs, 0,
-                       bnorm_dev);
-            LBF_LAUNCH(k_scale_first<float>, nblk, 256, 0, s, n, V32, pl->gs);
+            LBF_LAUNCH(k_restart<float>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V32, pl->gpart, count, gv, pl->gs, 0,
+                       bnorm_dev, pl->slab);
+            LBF_LAUNCH(k_scale_first<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, pl->gs, pl->slab);
         } else {
-            LBF_LAUNCH(k_restart<double>, nblk, 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0,
-                       bnorm_dev);
-            LBF_LAUNCH(k_scale_first<double>, nblk, 256, 0, s, n, V, pl->gs);
+            LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0,
+                       bnorm_dev, pl->slab);
+            LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
         }
         LBF_CHECK_LAUNCH();
     }
@@ -834,7 +857,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         // (or r for the adjoint), in sorted order
         if ((rc = lbf_permute_in(pl, g, b, transpose ? 1 : 0, s))) return rc;
         if (!transpose) {
-            LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, b);
+            LBF_LAUNCH(k_scale, lbf_grid(pl, lbf_cdiv(N, 256)), 256, 0, s, N, 2.0, b, pl->slab);
             LBF_CUDA(cudaMemsetAsync(b + N, 0, sizeof(double) * pl->M, s));
             LBF_CHECK_LAUNCH();
         }
@@ -846,12 +869,12 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         // b = P^-1 [2 g; 0] in sorted order (tin holds the permuted data), with the
         // doubled right-hand side 2 g of Eq. disc_sphere
         if ((rc = lbf_permute_in(pl, g, pl->tin, 0, s))) return rc;
-        LBF_LAUNCH(k_scale, lbf_cdiv(N, 256), 256, 0, s, N, 2.0, pl->tin);
+        LBF_LAUNCH(k_scale, lbf_grid(pl, lbf_cdiv(N, 256)), 256, 0, s, N, 2.0, pl->tin, pl->slab);
         LBF_CHECK_LAUNCH();
         if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
     }
     double *bn = pl->bsig + 1, *rn = pl->bsig + 2;
-    LBF_LAUNCH(k_norm2, pl->mdot_blocks, 256, 0, s, n, b, pl->gpart, pl->red_count + 2, bn);
+    LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, b, pl->gpart, pl->red_count + 2, bn, pl->slab);
     LBF_CHECK_LAUNCH();
     if (x0 && (rc = lbf_permute_in(pl, x0, x, 1, s))) return rc;
     GmresState hs{};
@@ -869,7 +892,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         // iterative refinement: FP64 residual, FP32-operator GMRES correction
         double *r = pl->gr, *d = pl->gd;
         if (!x0) {
-            LBF_LAUNCH(k_fill, lbf_cdiv(n, 256), 256, 0, s, x, n, 0.0);
+            LBF_LAUNCH(k_fill, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, x, n, 0.0, pl->slab);
             LBF_CHECK_LAUNCH();
         }
         double hb[3];
@@ -881,10 +904,10 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
                                               LBF_PREC_FP64)))
                     return rc;
                 pl->stats[1]++;
-                LBF_LAUNCH(k_axpby, lbf_cdiv(n, 256), 256, 0, s, n, 1.0, b, -1.0, pl->gw, r);
+                LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, b, -1.0, pl->gw, r, pl->slab);
                 LBF_CHECK_LAUNCH();
             }
-            LBF_LAUNCH(k_norm2, pl->mdot_blocks, 256, 0, s, n, r, pl->gpart, pl->red_count + 2, rn);
+            LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, r, pl->gpart, pl->red_count + 2, rn, pl->slab);
             LBF_CHECK_LAUNCH();
             LBF_CUDA(cudaMemcpyAsync(hb, pl->bsig, sizeof(hb), cudaMemcpyDeviceToHost, s));
             LBF_CUDA(cudaStreamSynchronize(s));
@@ -896,7 +919,7 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
                                  LBF_PREC_FP32, s, &hs)))
                 return rc;
             its += hs.it;
-            LBF_LAUNCH(k_axpby, lbf_cdiv(n, 256), 256, 0, s, n, 1.0, x, 1.0, d, x);
+            LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, x, 1.0, d, x, pl->slab);
             LBF_CHECK_LAUNCH();
         }
     }
@@ -914,3 +937,220 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
 
 int lbf_gmres_kernels_smem(int m) { return (int)(sizeof(double) * (kRowsPerChunk + 2 * (m + 2))); }
 int lbf_gmres_blocks() { return kDotBlocks; }
+
+// ---- right-hand sides in lockstep -----------------------------------------------------
+
+static_assert(sizeof(GmresState) <= 64, "GMRES state: 64-byte host slots");
+
+namespace {
+
+// the states of the view's right-hand sides, packed (a thread each)
+__global__ void k_gather_states(const GmresState *st, int64_t slab, int nrhs, GmresState *out)
+{
+    const int r = threadIdx.x;
+    if (r < nrhs) out[r] = *(const GmresState *)((const char *)st + (int64_t)r * slab);
+}
+
+// before a restart's operator application: the right-hand sides still iterating
+// pass their gate again (the others stay closed)
+__global__ void k_reopen(GmresState *st, int64_t slab)
+{
+    lbf_rhs(slab, st);
+    if (!st->converged && st->it < st->maxit) st->go = 1;
+}
+
+inline bool finished(const GmresState &h) { return h.converged || h.it >= h.maxit; }
+
+}  // namespace
+
+// The view's states into pinned host slot k (0: read now; 1, 2: the chunk checks),
+// staged in device slot k of dst (3 R states after the slabs).
+static int stage_states(lbf_plan *v, GmresState *dst, int k, cudaStream_t s)
+{
+    const int R = v->nrhs;
+    LBF_LAUNCH(k_gather_states, 1, 32, 0, s, v->gs, v->slab, R, dst + (int64_t)k * R);
+    LBF_CHECK_LAUNCH();
+    LBF_CUDA(cudaMemcpyAsync((char *)v->host_scalars + 256 + (size_t)64 * R * k, dst + (int64_t)k * R,
+                             sizeof(GmresState) * R, cudaMemcpyDeviceToHost, s));
+    return LBF_OK;
+}
+static const GmresState *host_states(lbf_plan *v, int k)
+{
+    return (const GmresState *)((char *)v->host_scalars + 256 + (size_t)64 * v->nrhs * k);
+}
+
+// GMRES from x = 0 on every right-hand side of view v (FP64 operator), b and its norm
+// in the view's buffers: gmres_core's steps, each launch covering all right-hand sides
+// and gated per right-hand side by its own state.  A right-hand side that finishes
+// stops (its gate closes, its restarts are skipped, and later cycle ends add nothing
+// to its x), so its iterates are those of a solve on its own.
+static int gmres_core_many(lbf_plan *pl, int opc, double tol, int maxit, GmresState *dst,
+                           cudaStream_t s, GmresState *out)
+{
+    const int R = pl->nrhs;
+    int64_t n = pl->n;
+    int m = pl->opt.restart;
+    int rc;
+    double *w = pl->gw, *V = pl->V, *x = pl->gx, *b = pl->gb;
+    int64_t ldv = pl->ldv;
+    int nblk = pl->mdot_blocks;
+    double *hbuf = pl->H + (int64_t)(m + 1) * m;
+    double *cs = hbuf + 2 * (m + 1), *sn = cs + m, *gv = sn + m, *y = gv + (m + 1);
+    unsigned *count = pl->red_count + 1;
+    const double *bn = pl->bsig + 1;
+    LBF_LAUNCH(k_init_state, lbf_grid(pl, 1), 1, 0, s, pl->gs, m, maxit, tol, pl->slab);
+    LBF_LAUNCH(k_fill, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, x, n, 0.0, pl->slab);
+    LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, (const double *)nullptr, V,
+               pl->gpart, count, gv, pl->gs, 1, bn, pl->slab);
+    LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
+    LBF_CHECK_LAUNCH();
+    cudaGraphExec_t sg = step_graph(pl, opc, LBF_PREC_FP64, s);
+    const int64_t sg_nodes = pl->gnodes[0][0];
+    auto read_all = [&]() -> int {
+        int e = stage_states(pl, dst, 0, s);
+        if (e) return e;
+        LBF_CUDA(cudaStreamSynchronize(s));
+        return LBF_OK;
+    };
+    int64_t restarts = 0;
+    for (;;) {
+        if ((rc = read_all())) return rc;
+        const GmresState *hs = host_states(pl, 0);
+        int it_act = -1;
+        for (int r = 0; r < R; r++)
+            if (hs[r].go) it_act = std::max(it_act, hs[r].it);
+        if (it_act < 0) break;
+        const int steps = std::min(m, maxit - it_act);
+        const int chunk = 4;
+        for (int c = 0, k0 = 0; k0 < steps; c++) {
+            const int slot = 1 + (c & 1);
+            if (c >= 2) {  // the states recorded after chunk c-2
+                LBF_CUDA(cudaEventSynchronize(pl->ev[c & 1]));
+                const GmresState *chk = host_states(pl, slot);
+                bool any = false;
+                for (int r = 0; r < R; r++) any = any || chk[r].go;
+                if (!any) break;
+            }
+            const int k1 = std::min(steps, k0 + chunk);
+            for (int k = k0; k < k1; k++) {
+                if (sg) {
+                    LBF_CUDA(cudaGraphLaunch(sg, s));
+                    g_lbf_launches.fetch_add(sg_nodes, std::memory_order_relaxed);
+                } else if ((rc = arnoldi_step(pl, opc, LBF_PREC_FP64, k, false, s))) {
+                    return rc;
+                }
+            }
+            k0 = k1;
+            if ((rc = stage_states(pl, dst, slot, s))) return rc;
+            LBF_CUDA(cudaEventRecord(pl->ev[c & 1], s));
+        }
+        // cycle end: x += V y on every right-hand side (none for those finished earlier)
+        LBF_LAUNCH(k_solve_y, lbf_grid(pl, 1), 32, 0, s, pl->H, gv, y, pl->gs, pl->slab);
+        LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x, pl->slab);
+        LBF_CHECK_LAUNCH();
+        if ((rc = read_all())) return rc;
+        hs = host_states(pl, 0);
+        int open = 0;
+        for (int r = 0; r < R; r++) open += finished(hs[r]) ? 0 : 1;
+        if (open == 0) break;
+        // restart the unfinished ones from their true preconditioned residual
+        LBF_LAUNCH(k_reopen, lbf_grid(pl, 1), 1, 0, s, pl->gs, pl->slab);
+        LBF_CHECK_LAUNCH();
+        if ((rc = lbf_apply_op_sorted(pl, opc, x, w, &pl->gs->go, s, LBF_PREC_FP64))) return rc;
+        restarts += open;
+        LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V, pl->gpart, count, gv,
+                   pl->gs, 0, bn, pl->slab);
+        LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
+        LBF_CHECK_LAUNCH();
+    }
+    if ((rc = read_all())) return rc;
+    const GmresState *hs = host_states(pl, 0);
+    for (int r = 0; r < R; r++) {
+        out[r] = hs[r];
+        pl->stats[0] += hs[r].it;
+        pl->stats[1] += hs[r].it;
+    }
+    pl->stats[1] += restarts;
+    return LBF_OK;
+}
+
+// nrhs right-hand sides of one plan, in lockstep groups of up to LBF_LOCKSTEP_MAX; the
+// plans whose S^-1 is applied by LU factors, and those built for FP32_REFINE, solve them
+// one after another (lbf_gmres_impl).
+int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, double *a,
+                        int *iters, double *rel_res, void *work, size_t bytes, cudaStream_t s)
+{
+    const int64_t N = pl->N;
+    const int M = pl->M;
+    int worst = LBF_OK;
+    for (auto &v : pl->stats) v = 0;
+    if (pl->lu || pl->opt.precision != LBF_PRECISION_FP64) {
+        int64_t st[4] = {0, 0, 0, 0};
+        for (int r = 0; r < nrhs; r++) {
+            int its = 0;
+            double rr = 0.0;
+            int rc = lbf_gmres_impl(pl, g + r * N, sigma + r * N, a ? a + (int64_t)r * M : nullptr,
+                                    nullptr, &its, &rr, s, 0);
+            if (rc < 0) return rc;
+            if (rc == LBF_NOCONV) worst = LBF_NOCONV;
+            for (int k = 0; k < 4; k++) st[k] += pl->stats[k];
+            if (iters) iters[r] = its;
+            if (rel_res) rel_res[r] = rr;
+        }
+        for (int k = 0; k < 4; k++) pl->stats[k] = st[k];
+        return worst;
+    }
+    const bool pc = pl->opt.precond != 0;
+    const int opc = pc ? LBF_OP_PRECONDITIONED : LBF_OP_FULL;
+    for (int r0 = 0; r0 < nrhs; r0 += LBF_LOCKSTEP_MAX) {
+        const int R = std::min(LBF_LOCKSTEP_MAX, nrhs - r0);
+        lbf_plan v;
+        size_t need = 0;
+        int rc = lbf_many_view(pl, R, work, bytes, &v, &need);
+        if (rc) return rc;
+        GmresState *dst = (GmresState *)((char *)work + (size_t)v.slab * R);
+        LBF_CUDA(cudaMemsetAsync(work, 0, (size_t)v.slab * R, s));
+        if (pl->imean)  // the island-mean constants of the float split, per right-hand side
+            for (int r = 0; r < R; r++)
+                LBF_CUDA(cudaMemcpyAsync(lbf_view_at(v, r).imean + M, pl->imean + M, sizeof(double) * 8,
+                                         cudaMemcpyDeviceToDevice, s));
+        // b = P^-1 [2 g; 0] (or [2 g; 0] without the preconditioner) and ||b||
+        for (int r = 0; r < R; r++) {
+            lbf_plan vr = lbf_view_at(v, r);
+            if ((rc = lbf_permute_in(&vr, g + (int64_t)(r0 + r) * N, pc ? vr.tin : vr.gb, 0, s))) return rc;
+        }
+        LBF_LAUNCH(k_scale, lbf_grid(&v, lbf_cdiv(N, 256)), 256, 0, s, N, 2.0, pc ? v.tin : v.gb, v.slab);
+        LBF_CHECK_LAUNCH();
+        if (pc) {
+            if ((rc = lbf_precondition_rhs(&v, v.tin, v.gb, s))) return rc;
+        } else {
+            LBF_LAUNCH(k_fill, lbf_grid(&v, lbf_cdiv(M, 256)), 256, 0, s, v.gb + N, (int64_t)M, 0.0, v.slab);
+            LBF_CHECK_LAUNCH();
+        }
+        LBF_LAUNCH(k_norm2, lbf_grid(&v, v.mdot_blocks), 256, 0, s, v.n, v.gb, v.gpart, v.red_count + 2,
+                   v.bsig + 1, v.slab);
+        LBF_CHECK_LAUNCH();
+        GmresState hs[LBF_LOCKSTEP_MAX];
+        for (auto &k : v.stats) k = 0;
+        rc = gmres_core_many(&v, opc, pl->opt.tol, pl->opt.maxit, dst, s, hs);
+        for (auto &row : v.gexec)
+            for (auto &ge : row)
+                if (ge) cudaGraphExecDestroy(ge);
+        if (rc) return rc;
+        for (int k = 0; k < 4; k++) pl->stats[k] += v.stats[k];
+        for (int r = 0; r < R; r++) {
+            lbf_plan vr = lbf_view_at(v, r);
+            LBF_LAUNCH(k_permute_out, lbf_cdiv(N, 256), 256, 0, s, N, M, pl->perm, vr.gx,
+                       sigma + (int64_t)(r0 + r) * N, 0);
+            LBF_CHECK_LAUNCH();
+            if (a)
+                LBF_CUDA(cudaMemcpyAsync(a + (int64_t)(r0 + r) * M, vr.gx + N, sizeof(double) * M,
+                                         cudaMemcpyDeviceToDevice, s));
+            if (!hs[r].converged) worst = LBF_NOCONV;
+            if (iters) iters[r0 + r] = hs[r].it;
+            if (rel_res) rel_res[r0 + r] = hs[r].bnorm > 0 ? hs[r].resid / hs[r].bnorm : 0.0;
+        }
+        LBF_CUDA(cudaStreamSynchronize(s));
+    }
+    return worst;
+}

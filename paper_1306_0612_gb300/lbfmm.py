@@ -122,6 +122,10 @@ def load():
                                        C.c_double, _P, C.c_size_t, C.POINTER(C.c_size_t),
                                        C.POINTER(lbf_options), C.c_char_p, C.c_size_t, _P]),
             "lbf_launch_count": (i64, []),
+            "lbf_gmres_workspace_many": (C.c_int, [_P, C.c_int, C.POINTER(C.c_size_t)]),
+            "lbf_gmres_solve_many": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
+            "lbf_batch_workspace_size": (C.c_int, [C.c_int, _P, C.POINTER(lbf_options), C.c_int,
+                                                   C.POINTER(C.c_size_t)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -139,7 +143,8 @@ def exported_symbols():
             "lbf_list_export", "lbf_plan_counts", "lbf_border_counts", "lbf_profile_enable",
             "lbf_profile_reset", "lbf_profile_read", "lbf_gmres_solve_transpose",
             "lbf_evaluate_transpose", "lbf_gradient_nodes", "lbf_gradient_data", "lbf_batch_run", "lbf_evaluate_noalloc", "lbf_solve_stats", "lbf_sync_status", "lbf_selftest_rcp", "lbf_autotune", "lbf_debug_inject", "lbf_debug_clear", "lbf_point_vortices", "lbf_dipole_sum",
-            "lbf_launch_count"]
+            "lbf_launch_count", "lbf_gmres_workspace_many", "lbf_gmres_solve_many",
+            "lbf_batch_workspace_size"]
 
 
 def lbf_status_string(status: int) -> str:
@@ -186,6 +191,14 @@ def lbf_workspace_size(island_ptr: np.ndarray, opt: lbf_options) -> int:
     _check(load().lbf_workspace_size(len(ptr) - 1, ptr.ctypes.data_as(_P), C.byref(opt),
                                      C.byref(out)), "lbf_workspace_size")
     return int(out.value)
+
+
+def lbf_batch_workspace_size(island_ptr: np.ndarray, opt: lbf_options, nrhs: int) -> int:
+    ptr = np.ascontiguousarray(island_ptr, dtype=np.int64)
+    n = C.c_size_t(0)
+    _check(load().lbf_batch_workspace_size(len(ptr) - 1, ptr.ctypes.data, C.byref(opt), int(nrhs),
+                                           C.byref(n)), "lbf_batch_workspace_size")
+    return n.value
 
 
 class Plan:
@@ -296,6 +309,34 @@ def lbf_gmres_solve(plan: Plan, g: torch.Tensor, sigma: torch.Tensor, a: torch.T
     return rc, it.value, rr.value
 
 
+def lbf_gmres_workspace_many(plan: Plan, nrhs: int) -> int:
+    n = C.c_size_t(0)
+    _check(load().lbf_gmres_workspace_many(plan.handle, int(nrhs), C.byref(n)), "lbf_gmres_workspace_many")
+    return n.value
+
+
+def lbf_gmres_solve_many(plan: Plan, g: torch.Tensor, sigma: torch.Tensor,
+                         a: torch.Tensor | None = None, work: torch.Tensor | None = None,
+                         stream=None):
+    """g: nrhs x N (device).  Returns (status, iterations per rhs, relative residual per rhs)."""
+    nrhs = g.numel() // plan.N
+    if nrhs < 1 or g.numel() != nrhs * plan.N:
+        raise ValueError("g must hold nrhs x N values")
+    need = lbf_gmres_workspace_many(plan, nrhs)
+    if work is None and need > 0:
+        work = torch.empty(need, dtype=torch.uint8, device=g.device)
+    its = (C.c_int * nrhs)()
+    rr = (C.c_double * nrhs)()
+    rc = load().lbf_gmres_solve_many(plan.handle, nrhs, _dptr(g, nrhs * plan.N, "g"),
+                                     _dptr(sigma, nrhs * plan.N, "sigma"),
+                                     _dptr(a, nrhs * plan.M, "a"), its, rr,
+                                     None if work is None else work.data_ptr(),
+                                     0 if work is None else work.numel() * work.element_size(),
+                                     _stream(stream))
+    _check(rc, "lbf_gmres_solve_many")
+    return rc, list(its), list(rr)
+
+
 def lbf_evaluate(plan: Plan, sigma: torch.Tensor, a: torch.Tensor | None, targets: torch.Tensor,
                  u: torch.Tensor, stream=None):
     T = targets.numel() // 3
@@ -341,14 +382,16 @@ def lbf_gradient_data(plan: Plan, lam: torch.Tensor, grad_g: torch.Tensor, strea
            "lbf_gradient_data")
 
 
-def lbf_batch_run(instances, opt=None, nworkers=8):
+def lbf_batch_run(instances, opt=None, nworkers=8, lockstep=True):
     """Solve many independent instances (native scheduler, one CUDA stream per worker).
 
     instances: list of dicts with keys island_ptr (host int64, M + 1), x, dx, d2x,
     centres (CUDA float64), g (nrhs x N), and optionally targets (T x 3).  Returns a
     list of dicts with sigma (nrhs x N), a (nrhs x M), u (nrhs x T or None) and the
     item's status, iters, fp64_applies, fp32_applies, max_rel_res.  Instances whose
-    quadtree outgrew the workspace estimate are rerun with the size they reported."""
+    quadtree outgrew the workspace estimate are rerun with the size they reported.
+    lockstep: size each workspace for lbf_gmres_solve_many (lbf_batch_workspace_size), so
+    that an instance's right-hand sides advance together; else one after another."""
     lib = load()
     opt = opt or lbf_default_options()
     n = len(instances)
@@ -366,11 +409,11 @@ def lbf_batch_run(instances, opt=None, nworkers=8):
             M, N = len(ptr) - 1, int(ptr[-1])
             o = lbf_options.from_buffer_copy(opt)
             o.box_capacity = caps[q]
-            nbytes = lbf_workspace_size(ptr, o)
-            dev = ins["x"].device
-            ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
             g = ins["g"].reshape(-1)
             nrhs = g.numel() // N
+            nbytes = lbf_batch_workspace_size(ptr, o, nrhs) if lockstep else lbf_workspace_size(ptr, o)
+            dev = ins["x"].device
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
             sigma = torch.empty(nrhs * N, dtype=torch.float64, device=dev)
             a = torch.empty(nrhs * M, dtype=torch.float64, device=dev)
             t = ins.get("targets")

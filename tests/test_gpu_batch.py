@@ -47,3 +47,103 @@ def test_batch_matches_single_solves_and_oracle(precision):
             assert np.array_equal(host(r["u"][k]), host(u))
             z = np.linalg.solve(A, np.concatenate([2 * ins["data"][k], np.zeros(g.M)]))
             assert rel_l2(host(sig), z[:g.N]) < 1e-9
+
+
+# ---- right-hand sides of one geometry in lockstep (lbf_gmres_solve_many) ------------------
+
+def _lockstep_case(M, nodes, nrhs, seed):
+    """A star-cap geometry and nrhs right-hand sides of mixed difficulty: Green's-pair
+    data (the paper's exact solutions), seeded noise (needs more iterations), and one zero
+    right-hand side (converged at the start)."""
+    g = wl.star_caps(seed, M, nodes)
+    rng = np.random.default_rng(seed + 1)
+    rows = []
+    for k in range(nrhs):
+        if k == 2:
+            rows.append(np.zeros(g.N))
+        elif k % 3 == 1:
+            rows.append(rng.standard_normal(g.N))
+        else:
+            p, gam, _ = wl.random_pair_sources(g, rng)
+            rows.append(oracle.green_sum(g.x, p, gam))
+    return g, np.stack(rows)
+
+
+def _separate(p, g, data):
+    out = []
+    for k in range(data.shape[0]):
+        sig, a = zeros(g.N), zeros(g.M)
+        rc, its, rr = L.lbf_gmres_solve(p, dev(data[k]), sig, a)
+        out.append((rc, its, rr, host(sig), host(a)))
+    return out
+
+
+@pytest.mark.parametrize("M,nodes,nrhs,restart,graphs,matvec", [
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM),     # graph-replayed steps, one cycle
+    (5, 120, 4, 6, 1, L.LBF_MATVEC_FMM),     # restarts every 6 steps
+    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM),    # two lockstep groups (16 + 2)
+    (3, 100, 3, 50, 0, L.LBF_MATVEC_FMM),    # steps launched one by one
+    (1, 256, 3, 50, 1, L.LBF_MATVEC_DIRECT), # one island, direct sums
+])
+def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec):
+    g, data = _lockstep_case(M, nodes, nrhs, seed=70 + M)
+    p = plan_for(g, tol=1e-12, restart=restart, graphs=graphs, matvec=matvec)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        sig, a = zeros(nrhs * g.N), zeros(nrhs * g.M)
+        rc, its, rr = L.lbf_gmres_solve_many(p, dev(data), sig, a, stream=s)
+        s.synchronize()
+        ref = _separate(p, g, data)
+    assert rc == L.LBF_OK
+    assert its[2] == 0 and rr[2] == 0.0  # the zero right-hand side
+    assert len(set(its)) > 1  # the right-hand sides stopped at different steps
+    for k, (rck, itk, rrk, sk, ak) in enumerate(ref):
+        assert rck == L.LBF_OK
+        assert its[k] == itk and rr[k] == rrk
+        assert np.array_equal(host(sig)[k * g.N:(k + 1) * g.N], sk)
+        assert np.array_equal(host(a)[k * g.M:(k + 1) * g.M], ak)
+
+
+def test_lockstep_matches_oracle_dense_solve():
+    g, data = _lockstep_case(5, 88, 6, seed=91)
+    p = plan_for(g, tol=1e-12)
+    sig, a = zeros(6 * g.N), zeros(6 * g.M)
+    rc, its, rr = L.lbf_gmres_solve_many(p, dev(data), sig, a)
+    assert rc == L.LBF_OK and max(rr) <= 1e-12
+    A = oracle.matrix(g)
+    for k in range(6):
+        z = np.linalg.solve(A, np.concatenate([2 * data[k], np.zeros(g.M)]))
+        if k == 2:
+            assert not np.any(host(sig)[k * g.N:(k + 1) * g.N])
+            continue
+        assert rel_l2(host(sig)[k * g.N:(k + 1) * g.N], z[:g.N]) < 1e-9
+        assert rel_l2(host(a)[k * g.M:(k + 1) * g.M], z[g.N:]) < 1e-9
+
+
+def test_lockstep_short_workspace_and_sequential_plans():
+    g, data = _lockstep_case(4, 64, 3, seed=93)
+    p = plan_for(g, tol=1e-12)
+    need = L.lbf_gmres_workspace_many(p, 3)
+    assert need > 0
+    short = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(L.LbfError):
+        L.lbf_gmres_solve_many(p, dev(data), zeros(3 * g.N), zeros(3 * g.M), work=short)
+    # an FP32-refinement plan takes no lockstep workspace and solves one after another
+    q = plan_for(g, tol=1e-12, precision=L.LBF_PRECISION_FP32_REFINE)
+    assert L.lbf_gmres_workspace_many(q, 3) == 0
+    sig, a = zeros(3 * g.N), zeros(3 * g.M)
+    rc, its, rr = L.lbf_gmres_solve_many(q, dev(data), sig, a)
+    for k, (rck, itk, rrk, sk, ak) in enumerate(_separate(q, g, data)):
+        assert its[k] == itk and np.array_equal(host(sig)[k * g.N:(k + 1) * g.N], sk)
+
+
+def test_batch_lockstep_equals_batch_one_after_another():
+    inst = _instances(count=6, nrhs=5)
+    opt = L.lbf_default_options(tol=1e-12)
+    lock = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=True)
+    seq = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=False)
+    for a, b in zip(lock, seq):
+        assert a["status"] == b["status"] == L.LBF_OK
+        assert a["iters"] == b["iters"] and a["fp64_applies"] == b["fp64_applies"]
+        assert torch.equal(a["sigma"], b["sigma"]) and torch.equal(a["a"], b["a"])
+        assert torch.equal(a["u"], b["u"])
