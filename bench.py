@@ -747,6 +747,10 @@ def run_extras(args, L, dev, stream):
     torch.cuda.synchronize()
     dtb = time.perf_counter() - t0
     eb = errs(res)
+    t0 = time.perf_counter()
+    L.lbf_batch_run(inst, opt=ob, nworkers=args.workers, lockstep=False)
+    torch.cuda.synchronize()
+    dts = time.perf_counter() - t0
     ol = L.lbf_default_options(tol=args.tol, fmm64=0)
     # the FP64 operator with each instance's right-hand sides in lockstep
     L.lbf_batch_run(inst[:4], opt=ol, nworkers=args.workers, lockstep=True)
@@ -774,6 +778,7 @@ def run_extras(args, L, dev, stream):
                          f"64-1024 nodes per island) x 16 right-hand sides = {nsolve} solves to "
                          f"tol {args.tol:g}, {T4} targets each",
                  "batched_fp32r_solves_per_s": nsolve / dtb, "batched_fp32r_s": dtb,
+                 "batched_fp32r_one_after_another_solves_per_s": nsolve / dts,
                  "batched_solution_err_max": eb,
                  "batched_fp64_lockstep_solves_per_s": nsolve / dtk, "batched_fp64_lockstep_s": dtk,
                  "batched_fp64_lockstep_err_max": ek,
@@ -833,9 +838,11 @@ def run_batch(args):
         st = [r["status"] for r in res]
         return dt, res, st
 
-    batched(L.LBF_PRECISION_FP32_REFINE, inst[:args.workers])
-    dt32, res32, st32 = batched(L.LBF_PRECISION_FP32_REFINE, inst)
+    batched(L.LBF_PRECISION_FP32_REFINE, inst[:args.workers], lockstep=True)
+    dt32, res32, st32 = batched(L.LBF_PRECISION_FP32_REFINE, inst, lockstep=True)
     e32 = err(res32, inst)
+    dt32s, res32s, st32s = batched(L.LBF_PRECISION_FP32_REFINE, inst)
+    e32s = err(res32s, inst)
     dt64b, res64b, st64b = batched(L.LBF_PRECISION_FP64, inst)
     e64b = err(res64b, inst)
     batched(L.LBF_PRECISION_FP64, inst[:args.workers], lockstep=True)
@@ -872,7 +879,12 @@ def run_batch(args):
                               "statuses_ok": st32.count(0), "solution_err_max": e32[0],
                               "solution_err_median": e32[1],
                               "fp32_applies": sum(r["fp32_applies"] for r in res32),
-                              "fp64_applies": sum(r["fp64_applies"] for r in res32)},
+                              "fp64_applies": sum(r["fp64_applies"] for r in res32),
+                              "note": "each instance's 16 right-hand sides in lockstep "
+                                      "(lbf_gmres_solve_many)"},
+            "batched_fp32r_one_after_another": {"wall_s": dt32s, "solves_per_s": nsolve / dt32s,
+                                                "statuses_ok": st32s.count(0),
+                                                "solution_err_max": e32s[0]},
             "batched_fp64": {"wall_s": dt64b, "solves_per_s": nsolve / dt64b,
                              "statuses_ok": st64b.count(0), "solution_err_max": e64b[0],
                              "solution_err_median": e64b[1],

@@ -479,7 +479,7 @@ int lbf_batch_workspace_size(int M, const int64_t *island_ptr, const lbf_options
     if (rc) return rc;
     *bytes = pb;
     const bool lu = opt->schur == LBF_SCHUR_LU || (opt->schur == LBF_SCHUR_AUTO && M > 1024);
-    if (nrhs < 2 || opt->precision != LBF_PRECISION_FP64 || !opt->border || lu) return LBF_OK;
+    if (nrhs < 2 || !opt->border || lu) return LBF_OK;
     const int64_t N = island_ptr[M];
     lbf_plan tmp;
     tmp.N = N;
@@ -731,7 +731,7 @@ int lbf_gmres_workspace_many(const lbf_plan *pl, int nrhs, size_t *bytes)
 {
     if (!pl || nrhs < 1 || !bytes) return LBF_EINVAL;
     *bytes = 0;
-    if (pl->lu || pl->opt.precision != LBF_PRECISION_FP64 || !pl->opt.border) return LBF_OK;
+    if (pl->lu || !pl->opt.border) return LBF_OK;
     return lbf_many_view(pl, std::min(nrhs, LBF_LOCKSTEP_MAX), nullptr, 0, nullptr, bytes);
 }
 

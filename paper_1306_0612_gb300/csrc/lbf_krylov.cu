@@ -944,11 +944,33 @@ static_assert(sizeof(GmresState) <= 64, "GMRES state: 64-byte host slots");
 
 namespace {
 
+struct RhsInts {  // one value per right-hand side of a lockstep group, passed by value
+    int v[LBF_LOCKSTEP_MAX];
+};
+
 // the states of the view's right-hand sides, packed (a thread each)
 __global__ void k_gather_states(const GmresState *st, int64_t slab, int nrhs, GmresState *out)
 {
     const int r = threadIdx.x;
     if (r < nrhs) out[r] = *(const GmresState *)((const char *)st + (int64_t)r * slab);
+}
+
+// k_init_state with each right-hand side's own iteration limit (0: it takes no step)
+__global__ void k_init_states(GmresState *st, int m, RhsInts maxit, double tol, int64_t slab)
+{
+    const int mx = maxit.v[blockIdx.y];
+    lbf_rhs(slab, st);
+    st->go = 0; st->j = 0; st->it = 0; st->converged = 0;
+    st->m = m; st->maxit = mx; st->tol = tol;
+    st->bnorm = 0; st->beta = 0; st->resid = 0; st->inv = 0;
+}
+
+// the gates of the next launches: open for the right-hand sides marked in on
+__global__ void k_set_gates(GmresState *st, RhsInts on, int64_t slab)
+{
+    const int g = on.v[blockIdx.y];
+    lbf_rhs(slab, st);
+    st->go = g;
 }
 
 // before a restart's operator application: the right-hand sides still iterating
@@ -979,33 +1001,52 @@ static const GmresState *host_states(lbf_plan *v, int k)
     return (const GmresState *)((char *)v->host_scalars + 256 + (size_t)64 * v->nrhs * k);
 }
 
-// GMRES from x = 0 on every right-hand side of view v (FP64 operator), b and its norm
-// in the view's buffers: gmres_core's steps, each launch covering all right-hand sides
-// and gated per right-hand side by its own state.  A right-hand side that finishes
-// stops (its gate closes, its restarts are skipped, and later cycle ends add nothing
-// to its x), so its iterates are those of a solve on its own.
-static int gmres_core_many(lbf_plan *pl, int opc, double tol, int maxit, GmresState *dst,
+// gmres_core on every right-hand side of view v from x = 0: b, ||b|| (bn) and x are the
+// first right-hand side's (the others' follow at the view's stride), maxit[r] the
+// iteration limit of right-hand side r (0: none).  Each launch covers all right-hand
+// sides and is gated per right-hand side by its own state; one that finishes stops (its
+// gate closes, its restarts are skipped, and later cycle ends add nothing to its x), so
+// its iterates are those of gmres_core on it alone.
+static int gmres_core_many(lbf_plan *pl, int opc, int prec, const double *b, const double *bn,
+                           double *x, double tol, const int *maxit, GmresState *dst,
                            cudaStream_t s, GmresState *out)
 {
     const int R = pl->nrhs;
     int64_t n = pl->n;
     int m = pl->opt.restart;
     int rc;
-    double *w = pl->gw, *V = pl->V, *x = pl->gx, *b = pl->gb;
+    double *w = pl->gw, *V = pl->V;
     int64_t ldv = pl->ldv;
     int nblk = pl->mdot_blocks;
     double *hbuf = pl->H + (int64_t)(m + 1) * m;
     double *cs = hbuf + 2 * (m + 1), *sn = cs + m, *gv = sn + m, *y = gv + (m + 1);
     unsigned *count = pl->red_count + 1;
-    const double *bn = pl->bsig + 1;
-    LBF_LAUNCH(k_init_state, lbf_grid(pl, 1), 1, 0, s, pl->gs, m, maxit, tol, pl->slab);
+    const bool f32 = prec == LBF_PREC_FP32;
+    float *V32 = basis32(pl);
+    RhsInts mx{};
+    int mmax = 0;
+    for (int r = 0; r < R; r++) {
+        mx.v[r] = maxit[r];
+        mmax = std::max(mmax, maxit[r]);
+    }
+    LBF_LAUNCH(k_init_states, lbf_grid(pl, 1), 1, 0, s, pl->gs, m, mx, tol, pl->slab);
     LBF_LAUNCH(k_fill, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, x, n, 0.0, pl->slab);
-    LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, (const double *)nullptr, V,
-               pl->gpart, count, gv, pl->gs, 1, bn, pl->slab);
-    LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
-    LBF_CHECK_LAUNCH();
-    cudaGraphExec_t sg = step_graph(pl, opc, LBF_PREC_FP64, s);
-    const int64_t sg_nodes = pl->gnodes[0][0];
+    auto restart = [&](const double *Ax, int init) -> int {
+        if (f32) {
+            LBF_LAUNCH(k_restart<float>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V32, pl->gpart, count,
+                       gv, pl->gs, init, bn, pl->slab);
+            LBF_LAUNCH(k_scale_first<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, pl->gs, pl->slab);
+        } else {
+            LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V, pl->gpart, count,
+                       gv, pl->gs, init, bn, pl->slab);
+            LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
+        }
+        LBF_CHECK_LAUNCH();
+        return LBF_OK;
+    };
+    if ((rc = restart(nullptr, 1))) return rc;
+    cudaGraphExec_t sg = step_graph(pl, opc, prec, s);
+    const int64_t sg_nodes = pl->gnodes[f32 ? 1 : 0][0];
     auto read_all = [&]() -> int {
         int e = stage_states(pl, dst, 0, s);
         if (e) return e;
@@ -1020,7 +1061,7 @@ static int gmres_core_many(lbf_plan *pl, int opc, double tol, int maxit, GmresSt
         for (int r = 0; r < R; r++)
             if (hs[r].go) it_act = std::max(it_act, hs[r].it);
         if (it_act < 0) break;
-        const int steps = std::min(m, maxit - it_act);
+        const int steps = std::min(m, mmax - it_act);
         const int chunk = 4;
         for (int c = 0, k0 = 0; k0 < steps; c++) {
             const int slot = 1 + (c & 1);
@@ -1036,7 +1077,7 @@ static int gmres_core_many(lbf_plan *pl, int opc, double tol, int maxit, GmresSt
                 if (sg) {
                     LBF_CUDA(cudaGraphLaunch(sg, s));
                     g_lbf_launches.fetch_add(sg_nodes, std::memory_order_relaxed);
-                } else if ((rc = arnoldi_step(pl, opc, LBF_PREC_FP64, k, false, s))) {
+                } else if ((rc = arnoldi_step(pl, opc, prec, k, false, s))) {
                     return rc;
                 }
             }
@@ -1046,7 +1087,10 @@ static int gmres_core_many(lbf_plan *pl, int opc, double tol, int maxit, GmresSt
         }
         // cycle end: x += V y on every right-hand side (none for those finished earlier)
         LBF_LAUNCH(k_solve_y, lbf_grid(pl, 1), 32, 0, s, pl->H, gv, y, pl->gs, pl->slab);
-        LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x, pl->slab);
+        if (f32)
+            LBF_LAUNCH(k_xupdate<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, ldv, y, pl->gs, x, pl->slab);
+        else
+            LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x, pl->slab);
         LBF_CHECK_LAUNCH();
         if ((rc = read_all())) return rc;
         hs = host_states(pl, 0);
@@ -1056,27 +1100,107 @@ static int gmres_core_many(lbf_plan *pl, int opc, double tol, int maxit, GmresSt
         // restart the unfinished ones from their true preconditioned residual
         LBF_LAUNCH(k_reopen, lbf_grid(pl, 1), 1, 0, s, pl->gs, pl->slab);
         LBF_CHECK_LAUNCH();
-        if ((rc = lbf_apply_op_sorted(pl, opc, x, w, &pl->gs->go, s, LBF_PREC_FP64))) return rc;
+        if ((rc = lbf_apply_op_sorted(pl, opc, x, w, &pl->gs->go, s, prec))) return rc;
         restarts += open;
-        LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V, pl->gpart, count, gv,
-                   pl->gs, 0, bn, pl->slab);
-        LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
-        LBF_CHECK_LAUNCH();
+        if ((rc = restart(w, 0))) return rc;
     }
     if ((rc = read_all())) return rc;
     const GmresState *hs = host_states(pl, 0);
+    int64_t its = 0;
     for (int r = 0; r < R; r++) {
         out[r] = hs[r];
-        pl->stats[0] += hs[r].it;
-        pl->stats[1] += hs[r].it;
+        its += hs[r].it;
     }
-    pl->stats[1] += restarts;
+    pl->stats[0] += its;
+    pl->stats[f32 ? 2 : 1] += its + restarts;
+    return LBF_OK;
+}
+
+// GMRES-IR of lbf_gmres_impl on every right-hand side of view v (b, ||b|| in the view's
+// buffers): a refinement round forms the FP64 residuals of the right-hand sides still
+// open, stops those that meet tol or their limits, and runs the float inner solves of
+// the others together.
+static int refine_many(lbf_plan *pl, int opc, GmresState *dst, cudaStream_t s, int *its_out,
+                       double *rel_out, int *conv_out)
+{
+    const int R = pl->nrhs;
+    const int64_t n = pl->n;
+    double *x = pl->gx, *b = pl->gb, *r = pl->gr, *d = pl->gd;
+    const double *bn = pl->bsig + 1;
+    double *rn = pl->bsig + 2;
+    int rc;
+    int its[LBF_LOCKSTEP_MAX] = {0};
+    bool open[LBF_LOCKSTEP_MAX];
+    for (int q = 0; q < R; q++) {
+        open[q] = true;
+        conv_out[q] = 0;
+        rel_out[q] = 0.0;
+    }
+    LBF_LAUNCH(k_fill, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, x, n, 0.0, pl->slab);
+    LBF_CHECK_LAUNCH();
+    double *hb = (double *)((char *)pl->host_scalars + 256);  // R x (||b||, ||r||) after the reads
+    for (int k = 0;; k++) {
+        RhsInts on{};
+        int nopen = 0;
+        for (int q = 0; q < R; q++) {
+            on.v[q] = open[q] ? 1 : 0;
+            nopen += on.v[q];
+        }
+        if (nopen == 0) break;
+        if (k == 0) {
+            for (int q = 0; q < R; q++)
+                LBF_CUDA(cudaMemcpyAsync(r + q * (pl->slab / 8), b + q * (pl->slab / 8), sizeof(double) * n,
+                                         cudaMemcpyDeviceToDevice, s));
+        } else {
+            LBF_LAUNCH(k_set_gates, lbf_grid(pl, 1), 1, 0, s, pl->gs, on, pl->slab);
+            LBF_CHECK_LAUNCH();
+            if ((rc = lbf_apply_op_sorted(pl, opc, x, pl->gw, &pl->gs->go, s, LBF_PREC_FP64))) return rc;
+            pl->stats[1] += nopen;
+            LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, b, -1.0, pl->gw, r,
+                       pl->slab);
+            LBF_CHECK_LAUNCH();
+        }
+        LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, r, pl->gpart, pl->red_count + 2,
+                   rn, pl->slab);
+        LBF_CHECK_LAUNCH();
+        for (int q = 0; q < R; q++)
+            LBF_CUDA(cudaMemcpyAsync(hb + 2 * q, (const char *)bn + q * pl->slab, sizeof(double) * 2,
+                                     cudaMemcpyDeviceToHost, s));
+        LBF_CUDA(cudaStreamSynchronize(s));
+        int lim[LBF_LOCKSTEP_MAX] = {0};
+        int nin = 0;
+        for (int q = 0; q < R; q++) {
+            if (!open[q]) continue;
+            const double rel = hb[2 * q] > 0 ? hb[2 * q + 1] / hb[2 * q] : 0.0;
+            rel_out[q] = rel;
+            if (rel <= pl->opt.tol) {
+                conv_out[q] = 1;
+                open[q] = false;
+                continue;
+            }
+            if (k >= pl->opt.max_refine || its[q] >= pl->opt.maxit) {
+                open[q] = false;
+                continue;
+            }
+            lim[q] = pl->opt.maxit - its[q];
+            nin++;
+            pl->stats[3]++;
+        }
+        if (nin == 0) break;
+        GmresState hs[LBF_LOCKSTEP_MAX];
+        if ((rc = gmres_core_many(pl, opc, LBF_PREC_FP32, r, rn, d, pl->opt.inner_tol, lim, dst, s, hs)))
+            return rc;
+        for (int q = 0; q < R; q++) its[q] += lim[q] > 0 ? hs[q].it : 0;
+        // x += d (d = 0 on the right-hand sides without an inner solve)
+        LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, x, 1.0, d, x, pl->slab);
+        LBF_CHECK_LAUNCH();
+    }
+    for (int q = 0; q < R; q++) its_out[q] = its[q];
     return LBF_OK;
 }
 
 // nrhs right-hand sides of one plan, in lockstep groups of up to LBF_LOCKSTEP_MAX; the
-// plans whose S^-1 is applied by LU factors, and those built for FP32_REFINE, solve them
-// one after another (lbf_gmres_impl).
+// plans whose S^-1 is applied by LU factors solve them one after another (lbf_gmres_impl).
 int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, double *a,
                         int *iters, double *rel_res, void *work, size_t bytes, cudaStream_t s)
 {
@@ -1084,7 +1208,7 @@ int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, 
     const int M = pl->M;
     int worst = LBF_OK;
     for (auto &v : pl->stats) v = 0;
-    if (pl->lu || pl->opt.precision != LBF_PRECISION_FP64) {
+    if (pl->lu) {
         int64_t st[4] = {0, 0, 0, 0};
         for (int r = 0; r < nrhs; r++) {
             int its = 0;
@@ -1102,6 +1226,7 @@ int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, 
     }
     const bool pc = pl->opt.precond != 0;
     const int opc = pc ? LBF_OP_PRECONDITIONED : LBF_OP_FULL;
+    const bool ir = pl->opt.precision != LBF_PRECISION_FP64 && pl->q32;
     for (int r0 = 0; r0 < nrhs; r0 += LBF_LOCKSTEP_MAX) {
         const int R = std::min(LBF_LOCKSTEP_MAX, nrhs - r0);
         lbf_plan v;
@@ -1130,9 +1255,23 @@ int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, 
         LBF_LAUNCH(k_norm2, lbf_grid(&v, v.mdot_blocks), 256, 0, s, v.n, v.gb, v.gpart, v.red_count + 2,
                    v.bsig + 1, v.slab);
         LBF_CHECK_LAUNCH();
-        GmresState hs[LBF_LOCKSTEP_MAX];
         for (auto &k : v.stats) k = 0;
-        rc = gmres_core_many(&v, opc, pl->opt.tol, pl->opt.maxit, dst, s, hs);
+        int its[LBF_LOCKSTEP_MAX], conv[LBF_LOCKSTEP_MAX];
+        double rel[LBF_LOCKSTEP_MAX];
+        if (ir) {
+            rc = refine_many(&v, opc, dst, s, its, rel, conv);
+        } else {
+            GmresState hs[LBF_LOCKSTEP_MAX];
+            int lim[LBF_LOCKSTEP_MAX];
+            for (int r = 0; r < R; r++) lim[r] = pl->opt.maxit;
+            rc = gmres_core_many(&v, opc, LBF_PREC_FP64, v.gb, v.bsig + 1, v.gx, pl->opt.tol, lim, dst, s,
+                                 hs);
+            for (int r = 0; r < R; r++) {
+                its[r] = hs[r].it;
+                conv[r] = hs[r].converged;
+                rel[r] = hs[r].bnorm > 0 ? hs[r].resid / hs[r].bnorm : 0.0;
+            }
+        }
         for (auto &row : v.gexec)
             for (auto &ge : row)
                 if (ge) cudaGraphExecDestroy(ge);
@@ -1146,9 +1285,9 @@ int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, 
             if (a)
                 LBF_CUDA(cudaMemcpyAsync(a + (int64_t)(r0 + r) * M, vr.gx + N, sizeof(double) * M,
                                          cudaMemcpyDeviceToDevice, s));
-            if (!hs[r].converged) worst = LBF_NOCONV;
-            if (iters) iters[r0 + r] = hs[r].it;
-            if (rel_res) rel_res[r0 + r] = hs[r].bnorm > 0 ? hs[r].resid / hs[r].bnorm : 0.0;
+            if (!conv[r]) worst = LBF_NOCONV;
+            if (iters) iters[r0 + r] = its[r];
+            if (rel_res) rel_res[r0 + r] = rel[r];
         }
         LBF_CUDA(cudaStreamSynchronize(s));
     }

@@ -78,16 +78,21 @@ def _separate(p, g, data):
     return out
 
 
-@pytest.mark.parametrize("M,nodes,nrhs,restart,graphs,matvec", [
-    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM),     # graph-replayed steps, one cycle
-    (5, 120, 4, 6, 1, L.LBF_MATVEC_FMM),     # restarts every 6 steps
-    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM),    # two lockstep groups (16 + 2)
-    (3, 100, 3, 50, 0, L.LBF_MATVEC_FMM),    # steps launched one by one
-    (1, 256, 3, 50, 1, L.LBF_MATVEC_DIRECT), # one island, direct sums
+FP64, IR = L.LBF_PRECISION_FP64, L.LBF_PRECISION_FP32_REFINE
+
+
+@pytest.mark.parametrize("M,nodes,nrhs,restart,graphs,matvec,precision", [
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, FP64),     # graph-replayed steps, one cycle
+    (5, 120, 4, 6, 1, L.LBF_MATVEC_FMM, FP64),     # restarts every 6 steps
+    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM, FP64),    # two lockstep groups (16 + 2)
+    (3, 100, 3, 50, 0, L.LBF_MATVEC_FMM, FP64),    # steps launched one by one
+    (1, 256, 3, 50, 1, L.LBF_MATVEC_DIRECT, FP64), # one island, direct sums
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, IR),       # refinement: FP64 residuals, float inner solves
+    (5, 120, 7, 8, 0, L.LBF_MATVEC_FMM, IR),       # refinement with inner restarts, no graphs
 ])
-def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec):
+def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec, precision):
     g, data = _lockstep_case(M, nodes, nrhs, seed=70 + M)
-    p = plan_for(g, tol=1e-12, restart=restart, graphs=graphs, matvec=matvec)
+    p = plan_for(g, tol=1e-12, restart=restart, graphs=graphs, matvec=matvec, precision=precision)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         sig, a = zeros(nrhs * g.N), zeros(nrhs * g.M)
@@ -128,8 +133,10 @@ def test_lockstep_short_workspace_and_sequential_plans():
     short = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(L.LbfError):
         L.lbf_gmres_solve_many(p, dev(data), zeros(3 * g.N), zeros(3 * g.M), work=short)
-    # an FP32-refinement plan takes no lockstep workspace and solves one after another
-    q = plan_for(g, tol=1e-12, precision=L.LBF_PRECISION_FP32_REFINE)
+    # a plan that applies S^-1 by LU factors takes no lockstep workspace and solves the
+    # right-hand sides one after another
+    g, data = _lockstep_case(67, 12, 3, seed=95)
+    q = plan_for(g, tol=1e-12, leaf_size=8, schur=L.LBF_SCHUR_LU)
     assert L.lbf_gmres_workspace_many(q, 3) == 0
     sig, a = zeros(3 * g.N), zeros(3 * g.M)
     rc, its, rr = L.lbf_gmres_solve_many(q, dev(data), sig, a)
@@ -137,13 +144,15 @@ def test_lockstep_short_workspace_and_sequential_plans():
         assert its[k] == itk and np.array_equal(host(sig)[k * g.N:(k + 1) * g.N], sk)
 
 
-def test_batch_lockstep_equals_batch_one_after_another():
+@pytest.mark.parametrize("precision", [FP64, IR])
+def test_batch_lockstep_equals_batch_one_after_another(precision):
     inst = _instances(count=6, nrhs=5)
-    opt = L.lbf_default_options(tol=1e-12)
+    opt = L.lbf_default_options(tol=1e-12, precision=precision)
     lock = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=True)
     seq = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=False)
     for a, b in zip(lock, seq):
         assert a["status"] == b["status"] == L.LBF_OK
         assert a["iters"] == b["iters"] and a["fp64_applies"] == b["fp64_applies"]
+        assert a["fp32_applies"] == b["fp32_applies"]
         assert torch.equal(a["sigma"], b["sigma"]) and torch.equal(a["a"], b["a"])
         assert torch.equal(a["u"], b["u"])
