@@ -231,7 +231,9 @@ void lbf_layout(lbf_plan *pl, int64_t N, int M, const lbf_options &o, int64_t ca
     }
     int m = o.restart;
     pl->ldv = (n + 31) / 32 * 32;
-    pl->mdot_blocks = lbf_gmres_blocks();
+    // blocks of the Arnoldi reductions: about 2048 unknowns each, at most 2 per SM (a
+    // small system's steps would otherwise pay for hundreds of near-empty blocks)
+    pl->mdot_blocks = (int)std::min<int64_t>(lbf_gmres_blocks(), std::max<int64_t>(1, lbf_cdiv(n, 2048)));
     if (o.border) {
         pl->H = A.get<double>((int64_t)(m + 1) * m + 2 * (m + 1) + 2 * m + 2 * (m + 1) + m);
         pl->gw = A.get<double>(n);
@@ -305,6 +307,7 @@ static void layout_rhs(const lbf_plan *pl, lbf_plan *v, Arena &A)
     v->gb = A.get<double>(n);
     v->gpart = A.get<double>((int64_t)pl->mdot_blocks * (m + 2));
     v->gs = (GmresState *)A.take(sizeof(GmresStateBytes));
+    v->nearbuf = A.get<double>(N);
     v->V = A.get<double>(pl->ldv * (m + 1));
     v->region = (char *)v->V;
     v->region_bytes = sizeof(double) * (size_t)pl->ldv * (m + 1);
@@ -350,7 +353,7 @@ lbf_plan lbf_view_at(const lbf_plan &v, int r)
     mv(o.mpole32); mv(o.local32); mv(o.imean); mv(o.gr); mv(o.gd); mv(o.v); mv(o.bsig);
     mv(o.red); mv(o.red_count); mv(o.fvec); mv(o.yvec); mv(o.tin); mv(o.tout); mv(o.vstep);
     mv(o.bd.partial); mv(o.bd.loc); mv(o.bd.loc32); mv(o.bd.sums); mv(o.H); mv(o.gw);
-    mv(o.gx); mv(o.gb); mv(o.gpart); mv(o.gs); mv(o.V); mv(o.region);
+    mv(o.gx); mv(o.gb); mv(o.gpart); mv(o.gs); mv(o.V); mv(o.region); mv(o.nearbuf);
     o.nrhs = 1;
     o.slab = 0;
     return o;
@@ -473,7 +476,7 @@ int lbf_workspace_size(int M, const int64_t *island_ptr, const lbf_options *opt,
 int lbf_batch_workspace_size(int M, const int64_t *island_ptr, const lbf_options *opt, int nrhs,
                              size_t *bytes)
 {
-    if (nrhs < 1) return LBF_EINVAL;
+    if (nrhs < 0 || !bytes) return LBF_EINVAL;
     size_t pb = 0;
     int rc = lbf_workspace_size(M, island_ptr, opt, &pb);
     if (rc) return rc;

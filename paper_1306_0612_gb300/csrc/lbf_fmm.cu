@@ -548,6 +548,26 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
             }
         }
     }
+    // Several right-hand sides in lockstep: their forward rows' near field in one pass that
+    // forms each pair's geometry once (k_near_multi), the leaf kernel adding it
+    const bool multi = MODE == fmm::kLeafForward && pl->nrhs > 1 && pl->nearbuf &&
+                       !std::is_same<R, df64>::value;
+    if constexpr (MODE == fmm::kLeafForward && !std::is_same<R, df64>::value) if (multi) {
+        const int nr = pl->nrhs;
+        const int64_t nb = lbf_cdiv(T.nleaf, 4);
+        const int32_t *isl = split ? (const int32_t *)pl->isl : nullptr;
+        const double *im = split ? (const double *)pl->imean : nullptr;
+#define LBF_NEAR_MULTI(NR)                                                                       \
+        LBF_LAUNCH_P(kid_leaf, (fmm::k_near_multi<R, NR>), nb, 128, (fmm::near_multi_smem<R, NR>(4)), \
+                     s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin, T.end, T.u_ptr, T.u_idx, g,  \
+                     pl->xi, uloc, udf, pl->w, sigma, isl, im, nr, pl->slab, pl->nearbuf, gate)
+        if (nr <= 2) LBF_NEAR_MULTI(2);
+        else if (nr <= 4) LBF_NEAR_MULTI(4);
+        else if (nr <= 8) LBF_NEAR_MULTI(8);
+        else LBF_NEAR_MULTI(16);
+#undef LBF_NEAR_MULTI
+        LBF_CHECK_LAUNCH();
+    }
     const int lw = pl->opt.p2p_warps > 0 ? pl->opt.p2p_warps : fmm::kLeafWarps;
     LBF_LAUNCH_P(kid_leaf, (fmm::k_leaf<R, MODE>), lbf_grid(pl, lbf_cdiv(T.nleaf, lw)), 32 * lw,
                  (fmm::leaf_smem<R, MODE>(lw)), s, T.nleaf, T.leaves, T.level, T.ix, T.iy, T.begin,
@@ -555,7 +575,8 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
                  sigma, pl->dself, pl->w, pl->beta, pl->bsig, v, gate, udf, walk ? 0 : 1,
                  split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
                  split ? (const double *)pl->imean : (const double *)nullptr,
-                 split ? (const double *)pl->iacoef : (const double *)nullptr, pl->M, pl->slab);
+                 split ? (const double *)pl->iacoef : (const double *)nullptr, pl->M, pl->slab,
+                 multi ? (const double *)pl->nearbuf : (const double *)nullptr);
     if (walk) {
         LBF_LAUNCH_P(kid_leaf, fmm::k_l2p_walk, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N,
                      P, pl->bd.leaf_of, T.level, T.ix, T.iy, pl->anc, (const float2 *)uloc,

@@ -952,9 +952,10 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
                        const double *__restrict__ beta, const double *__restrict__ bsig,
                        double *__restrict__ v, const int *gate, const cx<df64> *__restrict__ udf,
                        int l2p, const int32_t *__restrict__ isl, const double *__restrict__ imean,
-                       const double *__restrict__ iacoef, int M, int64_t slab)
+                       const double *__restrict__ iacoef, int M, int64_t slab,
+                       const double *__restrict__ nearv)
 {
-    lbf_rhs(slab, q, mp, loc, sigma, bsig, v, gate, imean);
+    lbf_rhs(slab, q, mp, loc, sigma, bsig, v, gate, imean, nearv);
     if (gate_closed(gate)) return;
     constexpr bool kF32 = kLocal<R>;  // leaf-local coordinates (float, double-float)
     // per warp, kSrcChunk staged sources (position in units of r, charge); the warps per
@@ -1207,7 +1208,8 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
             __syncwarp();
             fill = 0;
         };
-        for (int uq = uptr[b]; uq < uptr[b + 1]; uq++) {
+        // (nearv given: the near field of these rows was summed by k_near_multi)
+        for (int uq = uptr[b]; !nearv && uq < uptr[b + 1]; uq++) {
             const int s = uidx[uq];
             int sb = bg[s], se = en[s];
             bool local = false, dfp = false;
@@ -1259,6 +1261,7 @@ __global__ void k_leaf(int64_t nleaf, const int32_t *__restrict__ leaves,
         if (act) {
             if constexpr (MODE == kLeafForward) {
                 double c = (double)(-(kFlat ? (R)phiI : phi.y)) + (double)(accI * irr);
+                if (nearv) c += nearv[i];
                 // with island means m split off (isl given): the sums saw sigma - m; the
                 // means' rows are a_k m_k + 2 n m_(enclosing island) (the beta . m part is
                 // in bsig, formed from sigma)
@@ -1336,6 +1339,172 @@ __global__ void k_l2p_walk(int64_t N, int P, const int32_t *__restrict__ leaf_of
         acc += t.y;
     }
     v[i] += 2.0 * (-(double)acc * (1.0 / (2.0 * LBF_PI)));
+}
+
+// Near field of several right-hand sides at once (solves in lockstep): the forward rows'
+// P2P sum over U(b) for nr densities.  With the charges q_j = c_j w_j (c_j the density, less
+// its island mean where the float operator splits it, w_j the node's complex weight), a
+// pair's term Im(q_j conj(dz)) / |dz|^2 is c_j G with G = Im(w_j conj(dz)) / |dz|^2: the
+// pair's geometry (dz, the reciprocal, G) is formed once and each right-hand side adds
+// c_j G, one multiply-add, where the single-density kernel spends the whole pair on it.
+// Lanes hold targets as in k_leaf (32 / TP lanes a target splitting the sources), each
+// with NR sums; positions are leaf-local as there.  Writes near_r[i] = (1/r) sum, the
+// near part of the forward row k_leaf adds when given nearv (r: the target leaf's
+// half-width).  Right-hand side k's buffers (sigma, imean, near, its gate) sit k slab
+// bytes after the first's; those beyond nr add zeros.
+template <typename R> constexpr int kMultiChunk = std::is_same<R, double>::value ? 64 : 128;
+template <typename R, int NR> constexpr size_t near_multi_smem(int lw)
+{
+    return (size_t)lw * kMultiChunk<R> * (2 * sizeof(cx<R>) + NR * sizeof(R));
+}
+template <typename R, int NR>
+__global__ void __launch_bounds__(128)
+k_near_multi(int64_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ level,
+             const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
+             const int32_t *__restrict__ bg, const int32_t *__restrict__ en,
+             const int32_t *__restrict__ uptr, const int32_t *__restrict__ uidx, BoxGeo g,
+             const double2 *__restrict__ xi, const cx<R> *__restrict__ uloc,
+             const cx<df64> *__restrict__ udf, const double2 *__restrict__ w,
+             const double *__restrict__ sigma, const int32_t *__restrict__ isl,
+             const double *__restrict__ imean, int nr, int64_t slab, double *__restrict__ near,
+             const int *gate)
+{
+    constexpr bool kF32 = kLocal<R>;
+    constexpr int CH = kMultiChunk<R>;
+    int open = 0;  // right-hand sides whose gate is open
+    for (int k = 0; k < nr; k++)
+        open += gate_closed((const int *)((const char *)gate + k * slab)) ? 0 : 1;
+    if (open == 0) return;
+    extern __shared__ __align__(16) unsigned char nm_sm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t per = (size_t)CH * (2 * sizeof(cx<R>) + NR * sizeof(R));
+    cx<R> *sz = (cx<R> *)(nm_sm + wid * per), *sw = sz + CH;
+    R(*sc)[NR] = (R(*)[NR])(sw + CH);
+    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
+    if (t >= nleaf) return;
+    const int b = leaves[t];
+    const int lt = level[b], tx = ix[b], ty = iy[b];
+    double cxd = 0, cyd = 0, ir = 0;
+    bool have_c = false;
+    auto need_centre = [&]() {
+        if (have_c) return;
+        double r;
+        box_centre(g, lt, tx, ty, cxd, cyd, r);
+        ir = 1.0 / r;
+        have_c = true;
+    };
+    R irr;
+    if constexpr (kF32) {
+        irr = inv_half_width<R>(g, lt);
+    } else {
+        need_centre();
+        irr = (R)ir;
+    }
+    for (int tb = bg[b]; tb < en[b]; tb += 32) {
+        const int nt = min(32, en[b] - tb);
+        const int TP = nt <= 1 ? 1 : 1 << (32 - __clz(nt - 1));
+        const int slot = lane & (TP - 1), grp = lane / TP, G = 32 / TP;
+        cx<R> u = mk<R>(0, 0);
+        if (slot < nt) {
+            if constexpr (kF32) {
+                u = uloc[tb + slot];
+            } else {
+                const double2 zi = xi[tb + slot];
+                u = mk<R>((zi.x - cxd) * ir, (zi.y - cyd) * ir);
+            }
+        }
+        R acc[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++) acc[k] = R(0.0f);
+        int fill = 0;
+        auto process = [&]() {
+            __syncwarp();
+            if (slot < nt) {
+#pragma unroll 2
+                for (int m = grp; m < fill; m += G) {
+                    const cx<R> zs = sz[m], ww = sw[m];
+                    const R dr = zs.x - u.x, di = zs.y - u.y;
+                    R ir2;
+                    if constexpr (std::is_same<R, double>::value)
+                        ir2 = rcp_near(fma(dr, dr, fma(di, di, tiny_sq<R>())));
+                    else
+                        ir2 = rcp(fm(dr, dr, di * di) + tiny_sq<R>());
+                    const R gm = fm(ww.y, dr, -ww.x * di) * ir2;
+#pragma unroll
+                    for (int k = 0; k < NR; k++) acc[k] = fm(sc[m][k], gm, acc[k]);
+                }
+            }
+            __syncwarp();
+            fill = 0;
+        };
+        for (int uq = uptr[b]; uq < uptr[b + 1]; uq++) {
+            const int s = uidx[uq];
+            int sb = bg[s], se = en[s];
+            bool local = false, dfp = false;
+            R fs = R(0.0f);
+            cx<R> os = mk<R>(R(0.0f), R(0.0f));
+            if constexpr (kF32) {
+                const int ls = level[s];
+                local = ls >= lt && ls - lt <= 16;
+                if constexpr (std::is_same<R, float>::value)
+                    dfp = !local && udf && ls < lt && lt - ls <= kDfGap;
+                if (local || dfp) {
+                    fs = R(pow2<float>(lt - ls));
+                    os = offset_cx<R>(centre_offset(ls, ix[s], iy[s], lt, tx, ty));
+                }
+            }
+            while (sb < se) {
+                const int take = min(se - sb, CH - fill);
+                for (int m = lane; m < take; m += 32) {
+                    const int j = sb + m;
+                    cx<R> zr;
+                    if (local) {
+                        const cx<R> uu = uloc[j];
+                        zr = mk<R>(uu.x * fs + os.x, uu.y * fs + os.y);
+                    } else if (dfp) {
+                        if constexpr (std::is_same<R, float>::value) {
+                            const cx<df64> ud = udf[j];
+                            zr = mk<R>(df_round(df_ldexp(ud.x, fs) + df64(os.x)),
+                                       df_round(df_ldexp(ud.y, fs) + df64(os.y)));
+                        }
+                    } else {
+                        need_centre();
+                        const double2 zs = xi[j];
+                        zr = mk<R>((R)((zs.x - cxd) * ir), (R)((zs.y - cyd) * ir));
+                    }
+                    sz[fill + m] = zr;
+                    const double2 wj = w[j];
+                    sw[fill + m] = mk<R>((R)wj.x, (R)wj.y);
+                    const int kj = isl ? isl[j] : 0;
+#pragma unroll
+                    for (int k = 0; k < NR; k++) {
+                        double c = 0.0;
+                        if (k < nr) {
+                            const int64_t o = (int64_t)k * slab;
+                            c = *(const double *)((const char *)(sigma + j) + o);
+                            if (isl) c -= *(const double *)((const char *)(imean + kj) + o);
+                        }
+                        sc[fill + m][k] = (R)c;
+                    }
+                }
+                fill += take;
+                sb += take;
+                if (fill == CH) process();
+            }
+        }
+        if (fill > 0) process();
+        for (int o = TP; o < 32; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < NR; k++) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        }
+        if (grp == 0 && slot < nt) {
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                if (k < nr)
+                    *(double *)((char *)(near + tb + slot) + (int64_t)k * slab) = (double)(acc[k] * irr);
+        }
+        __syncwarp();
+    }
 }
 
 }  // namespace fmm

@@ -212,6 +212,7 @@ struct lbf_plan {
     // sit blockIdx.y * slab bytes after those the view points at (1 and 0 on a plan).
     int nrhs = 1;
     int64_t slab = 0;
+    double *nearbuf = nullptr;  // views: the forward rows' near field of every right-hand side
 };
 
 // grid of a launch over the plan's right-hand sides

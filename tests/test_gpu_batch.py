@@ -31,7 +31,7 @@ def _instances(count=7, nrhs=3):
 def test_batch_matches_single_solves_and_oracle(precision):
     inst = _instances()
     opt = L.lbf_default_options(tol=1e-12, precision=precision)
-    res = L.lbf_batch_run(inst, opt=opt, nworkers=4)
+    res = L.lbf_batch_run(inst, opt=opt, nworkers=4, lockstep=False)
     for ins, r in zip(inst, res):
         g = ins["geom"]
         assert r["status"] == L.LBF_OK and r["max_rel_res"] <= 1e-12
@@ -69,6 +69,10 @@ def _lockstep_case(M, nodes, nrhs, seed):
     return g, np.stack(rows)
 
 
+def _rows(t, k, n):
+    return host(t)[k * n:(k + 1) * n]
+
+
 def _separate(p, g, data):
     out = []
     for k in range(data.shape[0]):
@@ -91,6 +95,13 @@ FP64, IR = L.LBF_PRECISION_FP64, L.LBF_PRECISION_FP32_REFINE
     (5, 120, 7, 8, 0, L.LBF_MATVEC_FMM, IR),       # refinement with inner restarts, no graphs
 ])
 def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec, precision):
+    """Each right-hand side of a lockstep solve runs the kernels of a solve on its own,
+    except the FMM's near field, which the lockstep group sums in one pass sharing each
+    pair's geometry (k_near_multi: c (w x dz) / |dz|^2 formed as c times the pair's
+    factor instead of (c w) x dz, a different rounding).  So the direct-sum plans agree
+    bit for bit, and the FMM plans to the solver's tolerance: iterations within 2 and
+    solutions within 1e-9 (tol 1e-12 on the preconditioned residual, the refinement's
+    included: its FP64 residual decides when it stops)."""
     g, data = _lockstep_case(M, nodes, nrhs, seed=70 + M)
     p = plan_for(g, tol=1e-12, restart=restart, graphs=graphs, matvec=matvec, precision=precision)
     s = torch.cuda.Stream()
@@ -102,16 +113,23 @@ def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec
     assert rc == L.LBF_OK
     assert its[2] == 0 and rr[2] == 0.0  # the zero right-hand side
     assert len(set(its)) > 1  # the right-hand sides stopped at different steps
+    exact = matvec == L.LBF_MATVEC_DIRECT
     for k, (rck, itk, rrk, sk, ak) in enumerate(ref):
-        assert rck == L.LBF_OK
-        assert its[k] == itk and rr[k] == rrk
-        assert np.array_equal(host(sig)[k * g.N:(k + 1) * g.N], sk)
-        assert np.array_equal(host(a)[k * g.M:(k + 1) * g.M], ak)
+        assert rck == L.LBF_OK and rr[k] <= 1e-12
+        if exact:
+            assert its[k] == itk and rr[k] == rrk
+            assert np.array_equal(_rows(sig, k, g.N), sk)
+            assert np.array_equal(_rows(a, k, g.M), ak)
+        elif k != 2:
+            assert abs(its[k] - itk) <= 2
+            assert rel_l2(_rows(sig, k, g.N), sk) < 1e-9
+            assert rel_l2(_rows(a, k, g.M), ak) < 1e-9
 
 
-def test_lockstep_matches_oracle_dense_solve():
+@pytest.mark.parametrize("precision", [FP64, IR])
+def test_lockstep_matches_oracle_dense_solve(precision):
     g, data = _lockstep_case(5, 88, 6, seed=91)
-    p = plan_for(g, tol=1e-12)
+    p = plan_for(g, tol=1e-12, precision=precision)
     sig, a = zeros(6 * g.N), zeros(6 * g.M)
     rc, its, rr = L.lbf_gmres_solve_many(p, dev(data), sig, a)
     assert rc == L.LBF_OK and max(rr) <= 1e-12
@@ -141,18 +159,22 @@ def test_lockstep_short_workspace_and_sequential_plans():
     sig, a = zeros(3 * g.N), zeros(3 * g.M)
     rc, its, rr = L.lbf_gmres_solve_many(q, dev(data), sig, a)
     for k, (rck, itk, rrk, sk, ak) in enumerate(_separate(q, g, data)):
-        assert its[k] == itk and np.array_equal(host(sig)[k * g.N:(k + 1) * g.N], sk)
+        assert its[k] == itk and np.array_equal(_rows(sig, k, g.N), sk)
 
 
 @pytest.mark.parametrize("precision", [FP64, IR])
-def test_batch_lockstep_equals_batch_one_after_another(precision):
+def test_batch_lockstep_matches_oracle(precision):
+    """The batch runner's lockstep solves (the default) against the oracle's dense solve
+    and the evaluation at the targets against the one-after-another runs."""
     inst = _instances(count=6, nrhs=5)
     opt = L.lbf_default_options(tol=1e-12, precision=precision)
     lock = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=True)
     seq = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=False)
-    for a, b in zip(lock, seq):
-        assert a["status"] == b["status"] == L.LBF_OK
-        assert a["iters"] == b["iters"] and a["fp64_applies"] == b["fp64_applies"]
-        assert a["fp32_applies"] == b["fp32_applies"]
-        assert torch.equal(a["sigma"], b["sigma"]) and torch.equal(a["a"], b["a"])
-        assert torch.equal(a["u"], b["u"])
+    for ins, a, b in zip(inst, lock, seq):
+        g = ins["geom"]
+        assert a["status"] == b["status"] == L.LBF_OK and a["max_rel_res"] <= 1e-12
+        A = oracle.matrix(g)
+        for k in range(ins["data"].shape[0]):
+            z = np.linalg.solve(A, np.concatenate([2 * ins["data"][k], np.zeros(g.M)]))
+            assert rel_l2(host(a["sigma"][k]), z[:g.N]) < 1e-9
+            assert rel_l2(host(a["u"][k]), host(b["u"][k])) < 1e-9
