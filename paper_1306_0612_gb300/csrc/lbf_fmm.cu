@@ -548,13 +548,16 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
             }
         }
     }
-    // Several right-hand sides in lockstep: their forward rows' near field in one pass that
-    // forms each pair's geometry once (k_near_multi), the leaf kernel adding it
+    // Several right-hand sides in lockstep: the double forward rows' near field in one pass
+    // that forms each pair's geometry once (k_near_multi), the leaf kernel adding it.  (The
+    // float operator keeps a leaf pass per right-hand side: its pairs are cheap on the
+    // float pipes, and one warp per leaf for all right-hand sides left too few warps to
+    // hide the latency of a small system: measured slower.)
     const bool multi = MODE == fmm::kLeafForward && pl->nrhs > 1 && pl->nearbuf &&
-                       !std::is_same<R, df64>::value;
-    if constexpr (MODE == fmm::kLeafForward && !std::is_same<R, df64>::value) if (multi) {
+                       std::is_same<R, double>::value;
+    if constexpr (MODE == fmm::kLeafForward && std::is_same<R, double>::value) if (multi) {
         const int nr = pl->nrhs;
-        const int64_t nb = lbf_cdiv(T.nleaf, 4);
+        const int64_t nb = lbf_cdiv(2 * T.nleaf, 4);  // two warps a leaf
         const int32_t *isl = split ? (const int32_t *)pl->isl : nullptr;
         const double *im = split ? (const double *)pl->imean : nullptr;
 #define LBF_NEAR_MULTI(NR)                                                                       \

@@ -1348,7 +1348,9 @@ __global__ void k_l2p_walk(int64_t N, int P, const int32_t *__restrict__ leaf_of
 // pair's geometry (dz, the reciprocal, G) is formed once and each right-hand side adds
 // c_j G, one multiply-add, where the single-density kernel spends the whole pair on it.
 // Lanes hold targets as in k_leaf (32 / TP lanes a target splitting the sources), each
-// with NR sums; positions are leaf-local as there.  Writes near_r[i] = (1/r) sum, the
+// with NR sums; positions are leaf-local as there.  Two warps share a leaf, taking its
+// chunks of 32 targets in turn (warp 2 t + c: chunks c, c + 2, ...), so a small system
+// still has a warp per chunk of most leaves.  Writes near_r[i] = (1/r) sum, the
 // near part of the forward row k_leaf adds when given nearv (r: the target leaf's
 // half-width).  Right-hand side k's buffers (sigma, imean, near, its gate) sit k slab
 // bytes after the first's; those beyond nr add zeros.
@@ -1380,9 +1382,9 @@ k_near_multi(int64_t nleaf, const int32_t *__restrict__ leaves, const int32_t *_
     const size_t per = (size_t)CH * (2 * sizeof(cx<R>) + NR * sizeof(R));
     cx<R> *sz = (cx<R> *)(nm_sm + wid * per), *sw = sz + CH;
     R(*sc)[NR] = (R(*)[NR])(sw + CH);
-    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
-    if (t >= nleaf) return;
-    const int b = leaves[t];
+    const int64_t wt = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid;
+    if (wt >= 2 * nleaf) return;
+    const int b = leaves[wt >> 1];
     const int lt = level[b], tx = ix[b], ty = iy[b];
     double cxd = 0, cyd = 0, ir = 0;
     bool have_c = false;
@@ -1400,7 +1402,7 @@ k_near_multi(int64_t nleaf, const int32_t *__restrict__ leaves, const int32_t *_
         need_centre();
         irr = (R)ir;
     }
-    for (int tb = bg[b]; tb < en[b]; tb += 32) {
+    for (int tb = bg[b] + 32 * (int)(wt & 1); tb < en[b]; tb += 64) {
         const int nt = min(32, en[b] - tb);
         const int TP = nt <= 1 ? 1 : 1 << (32 - __clz(nt - 1));
         const int slot = lane & (TP - 1), grp = lane / TP, G = 32 / TP;

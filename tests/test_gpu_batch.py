@@ -85,16 +85,17 @@ def _separate(p, g, data):
 FP64, IR = L.LBF_PRECISION_FP64, L.LBF_PRECISION_FP32_REFINE
 
 
-@pytest.mark.parametrize("M,nodes,nrhs,restart,graphs,matvec,precision", [
-    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, FP64),     # graph-replayed steps, one cycle
-    (5, 120, 4, 6, 1, L.LBF_MATVEC_FMM, FP64),     # restarts every 6 steps
-    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM, FP64),    # two lockstep groups (16 + 2)
-    (3, 100, 3, 50, 0, L.LBF_MATVEC_FMM, FP64),    # steps launched one by one
-    (1, 256, 3, 50, 1, L.LBF_MATVEC_DIRECT, FP64), # one island, direct sums
-    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, IR),       # refinement: FP64 residuals, float inner solves
-    (5, 120, 7, 8, 0, L.LBF_MATVEC_FMM, IR),       # refinement with inner restarts, no graphs
+@pytest.mark.parametrize("M,nodes,nrhs,restart,graphs,matvec,precision,depth", [
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, FP64, 30),     # graph-replayed steps, one cycle
+    (5, 120, 4, 6, 1, L.LBF_MATVEC_FMM, FP64, 30),     # restarts every 6 steps
+    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM, FP64, 30),    # two lockstep groups (16 + 2)
+    (3, 100, 3, 50, 0, L.LBF_MATVEC_FMM, FP64, 30),    # steps launched one by one
+    (4, 150, 6, 50, 1, L.LBF_MATVEC_FMM, FP64, 3),     # depth cap: leaves of well over 64 nodes
+    (1, 256, 3, 50, 1, L.LBF_MATVEC_DIRECT, FP64, 30), # one island, direct sums
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, IR, 30),       # refinement: FP64 residuals, float inner solves
+    (5, 120, 7, 8, 0, L.LBF_MATVEC_FMM, IR, 30),       # refinement with inner restarts, no graphs
 ])
-def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec, precision):
+def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec, precision, depth):
     """Each right-hand side of a lockstep solve runs the kernels of a solve on its own,
     except the FMM's near field, which the lockstep group sums in one pass sharing each
     pair's geometry (k_near_multi: c (w x dz) / |dz|^2 formed as c times the pair's
@@ -103,7 +104,8 @@ def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec
     solutions within 1e-9 (tol 1e-12 on the preconditioned residual, the refinement's
     included: its FP64 residual decides when it stops)."""
     g, data = _lockstep_case(M, nodes, nrhs, seed=70 + M)
-    p = plan_for(g, tol=1e-12, restart=restart, graphs=graphs, matvec=matvec, precision=precision)
+    p = plan_for(g, tol=1e-12, restart=restart, graphs=graphs, matvec=matvec, precision=precision,
+                 max_depth=depth)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         sig, a = zeros(nrhs * g.N), zeros(nrhs * g.M)
