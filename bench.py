@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["C4"])
     ap.add_argument("--instances", type=int, default=512, help="C4: independent geometries")
     ap.add_argument("--workers", type=int, default=16, help="C4: scheduler threads/streams")
+    ap.add_argument("--arms", default="all",
+                    help="C4: comma list of fp32r, fp32r_seq, fp64, fp64_lockstep, loop (default all)")
     ap.add_argument("--sweep", action="store_true",
                     help="C3 matvec sweep: one line per island count (K_ONLY operator)")
     ap.add_argument("--sweep-m", default="64,128,256,1024,2048,4096,8192,16384")
@@ -791,9 +793,10 @@ def run_extras(args, L, dev, stream):
 def run_batch(args):
     """C4: independent geometries of uneven size (1-64 islands, 64-1024 nodes per
     island, log-uniform), 16 Green's-pair right-hand sides each, solved to 1e-10 and
-    evaluated at off-curve targets.  Batched arm: the native scheduler (worker streams,
-    FP32 FMM with FP64 refinement).  Baseline arm: the plain FP64 loop over all
-    instances on one stream (plan, 16 solves, evaluations)."""
+    evaluated at off-curve targets.  Batched arms: the native scheduler (worker streams),
+    FP32 FMM with FP64 refinement or FP64, each instance's right-hand sides in lockstep
+    (lbf_gmres_solve_many) or one after another.  Baseline arm: the plain FP64 loop over
+    all instances on one stream (plan, 16 solves, evaluations).  --arms picks a subset."""
     import numpy as np
     import torch
     import workloads as wl
@@ -838,66 +841,59 @@ def run_batch(args):
         st = [r["status"] for r in res]
         return dt, res, st
 
-    batched(L.LBF_PRECISION_FP32_REFINE, inst[:args.workers], lockstep=True)
-    dt32, res32, st32 = batched(L.LBF_PRECISION_FP32_REFINE, inst, lockstep=True)
-    e32 = err(res32, inst)
-    dt32s, res32s, st32s = batched(L.LBF_PRECISION_FP32_REFINE, inst)
-    e32s = err(res32s, inst)
-    dt64b, res64b, st64b = batched(L.LBF_PRECISION_FP64, inst)
-    e64b = err(res64b, inst)
-    batched(L.LBF_PRECISION_FP64, inst[:args.workers], lockstep=True)
-    dt64k, res64k, st64k = batched(L.LBF_PRECISION_FP64, inst, lockstep=True)
-    e64k = err(res64k, inst)
-    opt64 = L.lbf_default_options(tol=args.tol, fmm64=0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    nloop = 0
-    loop_err = []
-    for ins in inst:
-        plan = L.lbf_plan_create(ins["island_ptr"], ins["x"], ins["dx"], ins["d2x"], ins["centres"],
-                                 opt=opt64)
-        sig = torch.empty(ins["N"], dtype=torch.float64, device=dev)
-        a = torch.empty(ins["M"], dtype=torch.float64, device=dev)
-        u = torch.empty(T, dtype=torch.float64, device=dev)
-        for k in range(ins["g"].shape[0]):
-            L.lbf_gmres_solve(plan, ins["g"][k], sig, a)
-            L.lbf_evaluate(plan, sig, a, ins["targets"], u)
-            loop_err.append(float((u - ins["uex"][k]).abs().max() / ins["uex"][k].abs().max()))
-            nloop += 1
-        del plan
-    torch.cuda.synchronize()
-    dtl = time.perf_counter() - t0
-    loop_rate = nloop / dtl
+    arms = set(args.arms.split(",")) if args.arms != "all" else {"fp32r", "fp32r_seq", "fp64",
+                                                                  "fp64_lockstep", "loop"}
     line = {"metric": "batched uneven solves: solves per second (plan + GMRES to 1e-10 + evaluation)",
-            "value": nsolve / dt32, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
-            "data": "synthetic",
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": f"C4: {len(inst)} star-cap geometries, 1-64 islands, 64-1024 nodes "
                                    f"per island (log-uniform), 16 Green's-pair right-hand sides each, "
                                    f"{T} targets", "instances": len(inst), "solves": nsolve,
-                       "nodes": nodes, "workers": args.workers, "tol": args.tol},
-            "batched_fp32r": {"wall_s": dt32, "solves_per_s": nsolve / dt32,
-                              "statuses_ok": st32.count(0), "solution_err_max": e32[0],
-                              "solution_err_median": e32[1],
-                              "fp32_applies": sum(r["fp32_applies"] for r in res32),
-                              "fp64_applies": sum(r["fp64_applies"] for r in res32),
-                              "note": "each instance's 16 right-hand sides in lockstep "
-                                      "(lbf_gmres_solve_many)"},
-            "batched_fp32r_one_after_another": {"wall_s": dt32s, "solves_per_s": nsolve / dt32s,
-                                                "statuses_ok": st32s.count(0),
-                                                "solution_err_max": e32s[0]},
-            "batched_fp64": {"wall_s": dt64b, "solves_per_s": nsolve / dt64b,
-                             "statuses_ok": st64b.count(0), "solution_err_max": e64b[0],
-                             "solution_err_median": e64b[1],
-                             "note": "each instance's right-hand sides one after another"},
-            "batched_fp64_lockstep": {"wall_s": dt64k, "solves_per_s": nsolve / dt64k,
-                                      "statuses_ok": st64k.count(0), "solution_err_max": e64k[0],
-                                      "solution_err_median": e64k[1],
-                                      "note": "each instance's 16 right-hand sides in lockstep "
-                                              "(lbf_gmres_solve_many)"},
-            "loop_fp64": {"instances": len(inst), "solves": nloop, "wall_s": dtl,
-                          "solves_per_s": loop_rate, "solution_err_max": float(np.max(loop_err)),
-                          "note": "plain FP64 loop over every instance on one stream"},
-            "speedup_vs_loop_fp64": (nsolve / dt32) / loop_rate}
+                       "nodes": nodes, "workers": args.workers, "tol": args.tol}}
+    arm_defs = [("fp32r", "batched_fp32r", L.LBF_PRECISION_FP32_REFINE, True,
+                 "each instance's 16 right-hand sides in lockstep (lbf_gmres_solve_many)"),
+                ("fp32r_seq", "batched_fp32r_one_after_another", L.LBF_PRECISION_FP32_REFINE, False,
+                 "each instance's right-hand sides one after another"),
+                ("fp64", "batched_fp64", L.LBF_PRECISION_FP64, False,
+                 "each instance's right-hand sides one after another"),
+                ("fp64_lockstep", "batched_fp64_lockstep", L.LBF_PRECISION_FP64, True,
+                 "each instance's 16 right-hand sides in lockstep (lbf_gmres_solve_many)")]
+    for key, name, prec, lock, note in arm_defs:
+        if key not in arms:
+            continue
+        batched(prec, inst[:args.workers], lockstep=lock)  # warm-up
+        dt, res, st = batched(prec, inst, lockstep=lock)
+        e = err(res, inst)
+        line[name] = {"wall_s": dt, "solves_per_s": nsolve / dt, "statuses_ok": st.count(0),
+                      "solution_err_max": e[0], "solution_err_median": e[1],
+                      "fp32_applies": sum(r["fp32_applies"] for r in res),
+                      "fp64_applies": sum(r["fp64_applies"] for r in res), "note": note}
+        if "value" not in line:
+            line["value"] = nsolve / dt
+    if "loop" in arms:
+        opt64 = L.lbf_default_options(tol=args.tol, fmm64=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nloop = 0
+        loop_err = []
+        for ins in inst:
+            plan = L.lbf_plan_create(ins["island_ptr"], ins["x"], ins["dx"], ins["d2x"], ins["centres"],
+                                     opt=opt64)
+            sig = torch.empty(ins["N"], dtype=torch.float64, device=dev)
+            a = torch.empty(ins["M"], dtype=torch.float64, device=dev)
+            u = torch.empty(T, dtype=torch.float64, device=dev)
+            for k in range(ins["g"].shape[0]):
+                L.lbf_gmres_solve(plan, ins["g"][k], sig, a)
+                L.lbf_evaluate(plan, sig, a, ins["targets"], u)
+                loop_err.append(float((u - ins["uex"][k]).abs().max() / ins["uex"][k].abs().max()))
+                nloop += 1
+            del plan
+        torch.cuda.synchronize()
+        dtl = time.perf_counter() - t0
+        line["loop_fp64"] = {"instances": len(inst), "solves": nloop, "wall_s": dtl,
+                             "solves_per_s": nloop / dtl, "solution_err_max": float(np.max(loop_err)),
+                             "note": "plain FP64 loop over every instance on one stream"}
+        if "value" in line:
+            line["speedup_vs_loop_fp64"] = line["value"] / (nloop / dtl)
     print(json.dumps(line))
     return 0
 
