@@ -318,8 +318,10 @@ int lbf_batch_workspace_size(int M, const int64_t *island_ptr, const lbf_options
  * timed trials of the density operator (I + 2K) sigma on a seeded density, against a
  * reference at order 44.  For each leaf size in {32, 48, 64} the order p rises from 16
  * until the relative l2 error is at most target / 4; the fastest such (p, leaf) is
- * kept, then the near-field tile (p2p_warps 2, 4, 8).  Trial plans are built without
- * the border, one at a time, in the caller's workspace.
+ * kept, then the near-field tile (p2p_warps 2, 4, 8).  A trial's time is its accurate
+ * application's, plus, when base asks for FP32_REFINE, 10 times its float application's
+ * (about the float applications per FP64 residual of a refinement solve).  Trial plans
+ * are built without the border, one at a time, in the caller's workspace.
  *   geometry and pole_rotation: as lbf_plan_create (device arrays; rotation host/NULL)
  *   base: options to start from (precision, fmm64, ...: kept in *best)
  *   target: the largest acceptable rel-l2 error of the operator

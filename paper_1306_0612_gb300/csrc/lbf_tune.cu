@@ -8,6 +8,11 @@
 //      reference is at most target / 4 (the first such p is the cheapest at that leaf
 //      size: a higher order only adds work), then time it (median of 3 after a warm-up);
 //   3. for the fastest (p, leaf), the near-field tile of 2, 4 and 8 warps, timed.
+// A trial's time is what a solve spends on the operator: the double (or double-float)
+// application, plus, for FP32_REFINE options, kFloatPerDouble times the float one (the
+// refinement's inner solves apply the float operator about ten times per FP64 residual:
+// 41 to 4 on the 16,384-island benchmark, 239,211 to 24,578 on the 512 batched
+// geometries), so the leaf size and tile suit the operator the solve mostly runs.
 // Every trial plan is built without the border (the border does not depend on these
 // parameters) in the caller's workspace, one at a time.
 #include <algorithm>
@@ -73,10 +78,11 @@ __global__ void k_tune_err(int64_t n, const double *a, const double *b, double *
 }
 
 constexpr int kErrBlocks = 304;
+constexpr double kFloatPerDouble = 10.0;
 
 struct Trial {
     int p, leaf, warps;
-    double err, ms;
+    double err, ms, ms64, ms32;
     int status;
 };
 
@@ -127,7 +133,7 @@ extern "C" int lbf_autotune(int M, const int64_t *island_ptr, const double *x, c
     std::vector<Trial> trials;
     // one trial: plan, apply, error against the reference (when it exists), time
     auto run = [&](int p, int leaf, int warps, bool as_ref, bool time_it, Trial &t) -> int {
-        t = Trial{p, leaf, warps, -1.0, -1.0, 0};
+        t = Trial{p, leaf, warps, -1.0, -1.0, -1.0, -1.0, 0};
         lbf_options q = o;
         q.p = p;
         q.leaf_size = leaf;
@@ -150,11 +156,12 @@ extern "C" int lbf_autotune(int M, const int64_t *island_ptr, const double *x, c
                 rc = LBF_ECUDA;
             t.err = h;
         }
-        if (!rc && time_it) {
+        // median of 3 timed applications of op after a warm-up
+        auto time_op = [&](int op, double &ms_out) {
             std::vector<float> ts;
             for (int r = 0; r < 4 && !rc; r++) {
                 if (cudaEventRecord(e0, s) != cudaSuccess) rc = LBF_ECUDA;
-                if (!rc) rc = lbf_apply(pl, LBF_OP_K_ONLY, sig, out, stream);
+                if (!rc) rc = lbf_apply(pl, op, sig, out, stream);
                 if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
                     rc = LBF_ECUDA;
                 float ms = 0.f;
@@ -163,7 +170,15 @@ extern "C" int lbf_autotune(int M, const int64_t *island_ptr, const double *x, c
             }
             if (!rc) {
                 std::sort(ts.begin(), ts.end());
-                t.ms = ts[ts.size() / 2];
+                ms_out = ts[ts.size() / 2];
+            }
+        };
+        if (!rc && time_it) {
+            time_op(LBF_OP_K_ONLY, t.ms64);
+            t.ms = t.ms64;
+            if (!rc && o.precision == LBF_PRECISION_FP32_REFINE) {
+                time_op(LBF_OP_K_ONLY | LBF_OP_FP32, t.ms32);
+                if (!rc) t.ms = t.ms64 + kFloatPerDouble * t.ms32;
             }
         }
         int rs = lbf_sync_status(pl, stream);
@@ -214,8 +229,11 @@ extern "C" int lbf_autotune(int M, const int64_t *island_ptr, const double *x, c
         char buf[256];
         for (size_t i = 0; i < trials.size(); i++) {
             const Trial &t = trials[i];
-            snprintf(buf, sizeof(buf), "%s{\"p\": %d, \"leaf\": %d, \"warps\": %d, \"err\": %.3e, \"ms\": %.4f, \"status\": %d}",
-                     i ? ", " : "", t.p, t.leaf, t.warps ? t.warps : 4, t.err, t.ms, t.status);
+            snprintf(buf, sizeof(buf),
+                     "%s{\"p\": %d, \"leaf\": %d, \"warps\": %d, \"err\": %.3e, \"ms\": %.4f, "
+                     "\"ms64\": %.4f, \"ms32\": %.4f, \"status\": %d}",
+                     i ? ", " : "", t.p, t.leaf, t.warps ? t.warps : 4, t.err, t.ms, t.ms64, t.ms32,
+                     t.status);
             js += buf;
         }
         snprintf(buf, sizeof(buf), "], \"best\": {\"p\": %d, \"leaf\": %d, \"warps\": %d, \"ms\": %.4f}}",
