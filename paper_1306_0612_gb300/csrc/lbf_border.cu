@@ -1122,8 +1122,8 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
     if (f32) {
         int P = B.P32;
         size_t smem = sizeof(cz<float>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH(k_mp_p2l<float>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s, T.nbox, P, M,
-                   B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
+        LBF_LAUNCH(k_mp_p2l<float>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s, T.nbox,
+                   P, M, B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
                    (cz<float> *)B.loc32, B.sums, gate, pl->slab);
         // float: the evaluation walks each node's ancestors (cheaper here than the L2L
         // chain, which is serial along each path while the walk is parallel over nodes)
@@ -1131,84 +1131,86 @@ int lbf_mp_apply(lbf_plan *pl, const double *y, const double *x, const double *v
         if (chain) {
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_chain<float>, lbf_grid(pl, grid), 32 * cw, l2l_smem<float>(P, cw), s,
-                         T.nbox, P, T.parent, T.level, T.ix, T.iy, pl->tab32_binom,
-                         (const cz<float> *)pl->tab32_dshift, (cz<float> *)B.loc32, pl->pull,
-                         pl->dev_status, gate, pl->slab);
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_chain<float>, lbf_grid(pl, grid), 32 * cw,
+                         l2l_smem<float>(P, cw), s, T.nbox, P, T.parent, T.level, T.ix, T.iy,
+                         pl->tab32_binom, (const cz<float> *)pl->tab32_dshift, (cz<float> *)B.loc32,
+                         pl->pull, pl->dev_status, gate, pl->slab);
         }
         if (B.nchunks)
-            LBF_LAUNCH(k_mp_near<float>, lbf_grid(pl, lbf_cdiv(B.nchunks, 8)), 256, 0, s, B.nchunks, B.chunk_leaf,
-                       B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi, B.xc, y,
-                       B.nodebase, B.partial, gate, pl->slab);
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_eval<float>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N, P,
-                     pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<float> *)B.loc32,
-                     B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, pl->anc, pl->u32, chain ? 0 : 1,
+            LBF_LAUNCH(k_mp_near<float>, lbf_grid(pl, lbf_cdiv(B.nchunks, 8)), 256, 0, s, B.nchunks,
+                       B.chunk_leaf, B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi,
+                       B.xc, y, B.nodebase, B.partial, gate, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM32, k_mp_eval<float>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256,
+                     0, s, pl->N, P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g,
+                     (const cz<float> *)B.loc32, B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y,
+                     B.ell, B.sums, x, v, sc, out, gate, pl->anc, pl->u32, chain ? 0 : 1,
                      chain ? (const cz<float> *)pl->u32 : (const cz<float> *)nullptr, B.nodebase,
                      B.partial, pl->slab);
     } else if (pl->udf) {
         // the accurate operator in double-float (P2L terms formed in double)
         int P = B.Pe;
         size_t smem = sizeof(cz<df64>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<df64>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s, T.nbox, P, M,
-                   B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
-                   (cz<df64> *)B.loc, B.sums, gate, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<df64>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb,
+                     smem, s, T.nbox, P, M, B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc,
+                     B.kind, B.lam, y, (cz<df64> *)B.loc, B.sums, gate, pl->slab);
         if (pl->pull) {  // the L2L chain in one launch
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<df64>, lbf_grid(pl, grid), 32 * cw, l2l_smem<df64>(P, cw), s, T.nbox, P, T.parent,
-                       T.level, T.ix, T.iy, (const df64 *)pl->tabdf_binom,
-                       (const cz<df64> *)pl->tabdf_dshift, (cz<df64> *)B.loc, pl->pull,
-                       pl->dev_status, gate, pl->slab);
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<df64>, lbf_grid(pl, grid), 32 * cw,
+                         l2l_smem<df64>(P, cw), s, T.nbox, P, T.parent, T.level, T.ix, T.iy,
+                         (const df64 *)pl->tabdf_binom, (const cz<df64> *)pl->tabdf_dshift,
+                         (cz<df64> *)B.loc, pl->pull, pl->dev_status, gate, pl->slab);
         } else {
             for (int l = 3; l < T.nlev; l++) {
                 int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
                 if (le <= ls) continue;
-                LBF_LAUNCH(k_mp_l2l<df64>, lbf_grid(pl, lbf_cdiv(le - ls, 8)), 256, l2l_smem<df64>(P, 8), s, ls, le,
-                           P, T.parent, T.ix, T.iy, (const df64 *)pl->tabdf_binom,
-                           (const cz<df64> *)pl->tabdf_dshift, (cz<df64> *)B.loc, gate, pl->slab);
+                LBF_LAUNCH(k_mp_l2l<df64>, lbf_grid(pl, lbf_cdiv(le - ls, 8)), 256,
+                           l2l_smem<df64>(P, 8), s, ls, le, P, T.parent, T.ix, T.iy,
+                           (const df64 *)pl->tabdf_binom, (const cz<df64> *)pl->tabdf_dshift,
+                           (cz<df64> *)B.loc, gate, pl->slab);
             }
         }
         if (B.nchunks)
             LBF_LAUNCH(k_mp_near<double>, lbf_grid(pl, lbf_cdiv(B.nchunks, 8)), 256, 0, s, B.nchunks,
                        B.chunk_leaf, B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi,
                        B.xc, y, B.nodebase, B.partial, gate, pl->slab);
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<df64>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N, P,
-                     pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<df64> *)B.loc,
-                     B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, T.parent, (const float2 *)nullptr, 0, (const cz<df64> *)pl->udf,
-                     B.nodebase, B.partial, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<df64>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0,
+                     s, pl->N, P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g,
+                     (const cz<df64> *)B.loc, B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y,
+                     B.ell, B.sums, x, v, sc, out, gate, T.parent, (const float2 *)nullptr, 0,
+                     (const cz<df64> *)pl->udf, B.nodebase, B.partial, pl->slab);
     } else {
         int P = B.Pe;
         size_t smem = sizeof(cz<double>) * (size_t)wpb * P * 32;
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<double>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s, T.nbox,
-                     P, M, B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g, B.xc, B.kind, B.lam, y,
-                     (cz<double> *)B.loc, B.sums, gate, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_p2l<double>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)),
+                     32 * wpb, smem, s, T.nbox, P, M, B.p2l_ptr, B.p2l_src, T.level, T.ix, T.iy, g,
+                     B.xc, B.kind, B.lam, y, (cz<double> *)B.loc, B.sums, gate, pl->slab);
         if (pl->pull) {  // the L2L chain in one launch
             const int cw = 8;
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, cw), 4 * (int64_t)std::max(pl->nsm, 1));
-            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<double>, lbf_grid(pl, grid), 32 * cw, l2l_smem<double>(P, cw), s, T.nbox, P,
-                       T.parent, T.level, T.ix, T.iy, pl->tab_binom,
-                       (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, pl->pull,
-                       pl->dev_status, gate, pl->slab);
+            LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_chain<double>, lbf_grid(pl, grid), 32 * cw,
+                         l2l_smem<double>(P, cw), s, T.nbox, P, T.parent, T.level, T.ix, T.iy,
+                         pl->tab_binom, (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc,
+                         pl->pull, pl->dev_status, gate, pl->slab);
         } else {
             for (int l = 3; l < T.nlev; l++) {
                 int64_t ls = T.lev_start[l], le = T.lev_start[l + 1];
                 if (le <= ls) continue;
-                LBF_LAUNCH(k_mp_l2l<double>, lbf_grid(pl, lbf_cdiv(le - ls, 8)), 256, l2l_smem<double>(P, 8), s, ls,
-                           le, P, T.parent, T.ix, T.iy, pl->tab_binom,
-                           (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc, gate, pl->slab);
+                LBF_LAUNCH(k_mp_l2l<double>, lbf_grid(pl, lbf_cdiv(le - ls, 8)), 256,
+                           l2l_smem<double>(P, 8), s, ls, le, P, T.parent, T.ix, T.iy,
+                           pl->tab_binom, (const cz<double> *)pl->tab_dshift, (cz<double> *)B.loc,
+                           gate, pl->slab);
             }
         }
         if (B.nchunks)
             LBF_LAUNCH(k_mp_near<double>, lbf_grid(pl, lbf_cdiv(B.nchunks, 8)), 256, 0, s, B.nchunks,
                        B.chunk_leaf, B.chunk_k, B.near_ptr, B.near_src, T.begin, T.end, pl->xi,
                        B.xc, y, B.nodebase, B.partial, gate, pl->slab);
-        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<double>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0, s, pl->N,
-                     P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g, (const cz<double> *)B.loc,
-                     B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y, B.ell, B.sums, x, v, sc,
-                     out, gate, T.parent, (const float2 *)nullptr, 0, (const cz<double> *)nullptr,
-                     B.nodebase, B.partial, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ESUM, k_mp_eval<double>, lbf_grid(pl, lbf_cdiv(pl->N, 256)), 256, 0,
+                     s, pl->N, P, pl->xi, B.leaf_of, T.level, T.ix, T.iy, g,
+                     (const cz<double> *)B.loc, B.near_ptr, B.near_src, B.glob, B.nglob_h, B.xc, y,
+                     B.ell, B.sums, x, v, sc, out, gate, T.parent, (const float2 *)nullptr, 0,
+                     (const cz<double> *)nullptr, B.nodebase, B.partial, pl->slab);
     }
     LBF_CHECK_LAUNCH();
     return LBF_OK;

@@ -524,10 +524,10 @@ int fmm_apply(lbf_plan *pl, const FmmArrays &a, const double *sigma, double *v, 
         const int wpb = down_warps<R>(P);
         const size_t smem = down_smem<R>(P, wpb);
         if (walk) {  // every box's own M2L + P2L, a warp per box, no chain
-            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb, smem, s,
-                         (int64_t)0, T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv, T.xlist,
-                         T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp, loc, gate,
-                         0, (unsigned *)nullptr, pl->dev_status, udf, pl->slab);
+            LBF_LAUNCH_P(kid_down, fmm::k_down<R>, lbf_grid(pl, lbf_cdiv(T.nbox, wpb)), 32 * wpb,
+                         smem, s, (int64_t)0, T.nbox, T.level, T.ix, T.iy, T.parent, T.vlist, T.nv,
+                         T.xlist, T.nx, T.begin, T.end, g, P, binom, tpow, dsh, pl->xi, uloc, q, mp,
+                         loc, gate, 0, (unsigned *)nullptr, pl->dev_status, udf, pl->slab);
             LBF_CHECK_LAUNCH();
         } else if (pl->pull) {
             const int64_t grid = std::min<int64_t>(lbf_cdiv(T.nbox, wpb), 4 * (int64_t)std::max(pl->nsm, 1));
@@ -631,12 +631,14 @@ static int prep(lbf_plan *pl, const double *sigma, Arith ar, bool weighted, cons
     if (split)
         LBF_LAUNCH(k_island_means, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s,
                    pl->M, pl->island_ptr, pl->rank, sigma, pl->imean, gate, pl->slab);
-    LBF_LAUNCH(k_prep, lbf_grid(pl, nb), 256, 0, s, pl->N, sigma, weighted ? pl->w : (const double2 *)nullptr,
+    LBF_LAUNCH(k_prep, lbf_grid(pl, nb), 256, 0, s, pl->N, sigma,
+               weighted ? pl->w : (const double2 *)nullptr,
                weighted ? pl->beta : (const double *)nullptr,
                ar == Arith::F64 ? pl->q : (double2 *)nullptr,
                ar == Arith::F32 ? pl->q32 : (float2 *)nullptr,
                ar == Arith::DF64 ? (cx<df64> *)pl->qdf : (cx<df64> *)nullptr, pl->red,
-               pl->red_count, pl->bsig, gate, split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
+               pl->red_count, pl->bsig, gate,
+               split ? (const int32_t *)pl->isl : (const int32_t *)nullptr,
                split ? (const double *)pl->imean : (const double *)nullptr, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;

@@ -523,8 +523,8 @@ static int esum(lbf_plan *pl, const double *x, const double *v, const double *c,
 static int island_sums(lbf_plan *pl, const double *u, double scale, double *out, const int *gate,
                        cudaStream_t s)
 {
-    LBF_LAUNCH(k_island_sums, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s, pl->M, pl->island_ptr,
-               pl->rank, u, scale, out, gate, pl->slab);
+    LBF_LAUNCH(k_island_sums, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s, pl->M,
+               pl->island_ptr, pl->rank, u, scale, out, gate, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -533,8 +533,8 @@ static int small_gemv(lbf_plan *pl, const double *f, double alpha, double *y, co
                       cudaStream_t s)
 {
     if (pl->lu) return lbf_schur_lu_apply(pl, f, alpha, y, 0, gate, s, !pl->lu_fast);
-    LBF_LAUNCH(k_small_gemv, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s, pl->M, pl->Sinv, f,
-               alpha, y, gate, pl->slab);
+    LBF_LAUNCH(k_small_gemv, lbf_grid(pl, lbf_cdiv((int64_t)pl->M * 32, 256)), 256, 0, s, pl->M,
+               pl->Sinv, f, alpha, y, gate, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -583,7 +583,8 @@ static int apply_op_transposed(lbf_plan *pl, int op, const double *in, double *o
     if ((rc = lbf_mp_apply_transpose(pl, pl->v, 1.0, nullptr, pl->fvec, gate, s))) return rc;
     if ((rc = small_gemv_t(pl, pl->fvec, -1.0, pl->yvec, gate, s))) return rc;
     if ((rc = island_scatter(pl, out, pl->yvec, -1.0, out, gate, s))) return rc;
-    LBF_LAUNCH(k_add, lbf_grid(pl, lbf_cdiv(M, 128)), 128, 0, s, M, in + N, pl->yvec, out + N, gate, pl->slab);
+    LBF_LAUNCH(k_add, lbf_grid(pl, lbf_cdiv(M, 128)), 128, 0, s, M, in + N, pl->yvec, out + N, gate,
+               pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
 }
@@ -615,7 +616,8 @@ int lbf_apply_op_sorted(lbf_plan *pl, int op, const double *in, double *out, con
     if (op == LBF_OP_FULL) {
         if ((rc = island_sums(pl, in, 1.0, pl->fvec, gate, s))) return rc;
         if ((rc = esum(pl, in, pl->v, in + N, 1.0, out, gate, s))) return rc;
-        LBF_LAUNCH(k_arows, lbf_grid(pl, 1), 256, 0, s, M, 0, in + N, pl->fvec, out + N, gate, pl->slab);
+        LBF_LAUNCH(k_arows, lbf_grid(pl, 1), 256, 0, s, M, 0, in + N, pl->fvec, out + N, gate,
+                   pl->slab);
         LBF_CHECK_LAUNCH();
         return LBF_OK;
     }
@@ -675,10 +677,11 @@ static int arnoldi_step_t(lbf_plan *pl, int opc, int prec, int k, bool from_stat
         // the operator reads v_j in double: from the device's j (graph-replayable), or a
         // float basis vector widened
         if (from_state) {
-            LBF_LAUNCH(k_copy_vj<T>, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, V, ldv, pl->gs, pl->vstep, pl->slab);
-        } else {
-            LBF_LAUNCH(k_widen, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, (const float *)(V + (int64_t)k * ldv),
+            LBF_LAUNCH(k_copy_vj<T>, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, V, ldv, pl->gs,
                        pl->vstep, pl->slab);
+        } else {
+            LBF_LAUNCH(k_widen, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n,
+                       (const float *)(V + (int64_t)k * ldv), pl->vstep, pl->slab);
         }
         vj = pl->vstep;
     }
@@ -690,8 +693,8 @@ static int arnoldi_step_t(lbf_plan *pl, int opc, int prec, int k, bool from_stat
     pl->lu_fast = 0;
     if (rc) return rc;
     for (int mode = 0; mode < 3; mode++)
-        LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi<T>, lbf_grid(pl, nblk), 256, smem, s, n, V, ldv, w, wt, pl->gpart,
-                     count, hbuf, pl->H, cs, sn, gv, pl->gs, mode, pl->slab);
+        LBF_LAUNCH_P(LBF_KERNEL_ARNOLDI, k_arnoldi<T>, lbf_grid(pl, nblk), 256, smem, s, n, V, ldv,
+                     w, wt, pl->gpart, count, hbuf, pl->H, cs, sn, gv, pl->gs, mode, pl->slab);
     LBF_LAUNCH(k_scale_next<T>, lbf_grid(pl, nblk), 256, 0, s, n, wt, V, ldv, pl->gs, pl->slab);
     LBF_CHECK_LAUNCH();
     return LBF_OK;
@@ -766,12 +769,12 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
     const bool f32 = prec == LBF_PREC_FP32;
     float *V32 = basis32(pl);
     if (f32) {
-        LBF_LAUNCH(k_restart<float>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V32, pl->gpart, count, gv, pl->gs, 1,
-                   bnorm_dev, pl->slab);
+        LBF_LAUNCH(k_restart<float>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V32, pl->gpart, count,
+                   gv, pl->gs, 1, bnorm_dev, pl->slab);
         LBF_LAUNCH(k_scale_first<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, pl->gs, pl->slab);
     } else {
-        LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V, pl->gpart, count, gv, pl->gs, 1,
-                   bnorm_dev, pl->slab);
+        LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, Ax, V, pl->gpart, count,
+                   gv, pl->gs, 1, bnorm_dev, pl->slab);
         LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
     }
     LBF_CHECK_LAUNCH();
@@ -813,8 +816,10 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
         }
         // cycle end: x += V y
         LBF_LAUNCH(k_solve_y, lbf_grid(pl, 1), 32, 0, s, pl->H, gv, y, pl->gs, pl->slab);
-        if (f32) LBF_LAUNCH(k_xupdate<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, ldv, y, pl->gs, x, pl->slab);
-        else LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x, pl->slab);
+        if (f32) LBF_LAUNCH(k_xupdate<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, ldv, y, pl->gs,
+                            x, pl->slab);
+        else LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x,
+                        pl->slab);
         LBF_CHECK_LAUNCH();
         if ((rc = read_state(pl, &hs, s))) return rc;
         if (hs.converged || hs.it >= hs.maxit) break;
@@ -822,12 +827,12 @@ static int gmres_core(lbf_plan *pl, int opc, const double *b, const double *bnor
         if ((rc = lbf_apply_op_sorted(pl, opc, x, w, nullptr, s, prec))) return rc;
         (*applies)++;
         if (f32) {
-            LBF_LAUNCH(k_restart<float>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V32, pl->gpart, count, gv, pl->gs, 0,
-                       bnorm_dev, pl->slab);
+            LBF_LAUNCH(k_restart<float>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V32, pl->gpart,
+                       count, gv, pl->gs, 0, bnorm_dev, pl->slab);
             LBF_LAUNCH(k_scale_first<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, pl->gs, pl->slab);
         } else {
-            LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V, pl->gpart, count, gv, pl->gs, 0,
-                       bnorm_dev, pl->slab);
+            LBF_LAUNCH(k_restart<double>, lbf_grid(pl, nblk), 256, 0, s, n, b, w, V, pl->gpart,
+                       count, gv, pl->gs, 0, bnorm_dev, pl->slab);
             LBF_LAUNCH(k_scale_first<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, pl->gs, pl->slab);
         }
         LBF_CHECK_LAUNCH();
@@ -874,7 +879,8 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
         if ((rc = lbf_precondition_rhs(pl, pl->tin, b, s))) return rc;
     }
     double *bn = pl->bsig + 1, *rn = pl->bsig + 2;
-    LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, b, pl->gpart, pl->red_count + 2, bn, pl->slab);
+    LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, b, pl->gpart,
+               pl->red_count + 2, bn, pl->slab);
     LBF_CHECK_LAUNCH();
     if (x0 && (rc = lbf_permute_in(pl, x0, x, 1, s))) return rc;
     GmresState hs{};
@@ -904,10 +910,12 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
                                               LBF_PREC_FP64)))
                     return rc;
                 pl->stats[1]++;
-                LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, b, -1.0, pl->gw, r, pl->slab);
+                LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, b, -1.0,
+                           pl->gw, r, pl->slab);
                 LBF_CHECK_LAUNCH();
             }
-            LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, r, pl->gpart, pl->red_count + 2, rn, pl->slab);
+            LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, r, pl->gpart,
+                       pl->red_count + 2, rn, pl->slab);
             LBF_CHECK_LAUNCH();
             LBF_CUDA(cudaMemcpyAsync(hb, pl->bsig, sizeof(hb), cudaMemcpyDeviceToHost, s));
             LBF_CUDA(cudaStreamSynchronize(s));
@@ -919,7 +927,8 @@ int lbf_gmres_impl(lbf_plan *pl, const double *g, double *sigma, double *a, cons
                                  LBF_PREC_FP32, s, &hs)))
                 return rc;
             its += hs.it;
-            LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, x, 1.0, d, x, pl->slab);
+            LBF_LAUNCH(k_axpby, lbf_grid(pl, lbf_cdiv(n, 256)), 256, 0, s, n, 1.0, x, 1.0, d, x,
+                       pl->slab);
             LBF_CHECK_LAUNCH();
         }
     }
@@ -1088,9 +1097,11 @@ static int gmres_core_many(lbf_plan *pl, int opc, int prec, const double *b, con
         // cycle end: x += V y on every right-hand side (none for those finished earlier)
         LBF_LAUNCH(k_solve_y, lbf_grid(pl, 1), 32, 0, s, pl->H, gv, y, pl->gs, pl->slab);
         if (f32)
-            LBF_LAUNCH(k_xupdate<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, ldv, y, pl->gs, x, pl->slab);
+            LBF_LAUNCH(k_xupdate<float>, lbf_grid(pl, nblk), 256, 0, s, n, V32, ldv, y, pl->gs, x,
+                       pl->slab);
         else
-            LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x, pl->slab);
+            LBF_LAUNCH(k_xupdate<double>, lbf_grid(pl, nblk), 256, 0, s, n, V, ldv, y, pl->gs, x,
+                       pl->slab);
         LBF_CHECK_LAUNCH();
         if ((rc = read_all())) return rc;
         hs = host_states(pl, 0);
@@ -1160,8 +1171,8 @@ static int refine_many(lbf_plan *pl, int opc, GmresState *dst, cudaStream_t s, i
                        pl->slab);
             LBF_CHECK_LAUNCH();
         }
-        LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, r, pl->gpart, pl->red_count + 2,
-                   rn, pl->slab);
+        LBF_LAUNCH(k_norm2, lbf_grid(pl, pl->mdot_blocks), 256, 0, s, n, r, pl->gpart,
+                   pl->red_count + 2, rn, pl->slab);
         LBF_CHECK_LAUNCH();
         for (int q = 0; q < R; q++)
             LBF_CUDA(cudaMemcpyAsync(hb + 2 * q, (const char *)bn + q * pl->slab, sizeof(double) * 2,
@@ -1244,12 +1255,14 @@ int lbf_gmres_many_impl(lbf_plan *pl, int nrhs, const double *g, double *sigma, 
             lbf_plan vr = lbf_view_at(v, r);
             if ((rc = lbf_permute_in(&vr, g + (int64_t)(r0 + r) * N, pc ? vr.tin : vr.gb, 0, s))) return rc;
         }
-        LBF_LAUNCH(k_scale, lbf_grid(&v, lbf_cdiv(N, 256)), 256, 0, s, N, 2.0, pc ? v.tin : v.gb, v.slab);
+        LBF_LAUNCH(k_scale, lbf_grid(&v, lbf_cdiv(N, 256)), 256, 0, s, N, 2.0, pc ? v.tin : v.gb,
+                   v.slab);
         LBF_CHECK_LAUNCH();
         if (pc) {
             if ((rc = lbf_precondition_rhs(&v, v.tin, v.gb, s))) return rc;
         } else {
-            LBF_LAUNCH(k_fill, lbf_grid(&v, lbf_cdiv(M, 256)), 256, 0, s, v.gb + N, (int64_t)M, 0.0, v.slab);
+            LBF_LAUNCH(k_fill, lbf_grid(&v, lbf_cdiv(M, 256)), 256, 0, s, v.gb + N, (int64_t)M, 0.0,
+                       v.slab);
             LBF_CHECK_LAUNCH();
         }
         LBF_LAUNCH(k_norm2, lbf_grid(&v, v.mdot_blocks), 256, 0, s, v.n, v.gb, v.gpart, v.red_count + 2,
