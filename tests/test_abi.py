@@ -75,3 +75,30 @@ def test_status_strings(lib):
     assert lib.lbf_status_string(0) == "ok"
     assert "pole" in lib.lbf_status_string(lib.LBF_EPOLE)
     assert lib.lbf_status_string(12345) == "unknown status"
+
+
+def test_batch_workspace_size_host_only(lib):
+    """A batch item's workspace: the plan's bytes (rounded up to 256), then the lockstep
+    slabs of its right-hand sides (lbf_gmres_solve_many), which grow with their number up
+    to one group of 16 and are absent where right-hand sides run one after another (a
+    single one, no border, or S^-1 by LU factors)."""
+    ptr = np.array([0, 300, 700, 1000], dtype=np.int64)
+    o = lib.lbf_default_options()
+    plan = lib.lbf_workspace_size(ptr, o)
+    rnd = (plan + 255) // 256 * 256
+    assert lib.lbf_batch_workspace_size(ptr, o, 0) == plan
+    assert lib.lbf_batch_workspace_size(ptr, o, 1) == plan
+    b2, b8, b16 = (lib.lbf_batch_workspace_size(ptr, o, r) for r in (2, 8, 16))
+    # each right-hand side's slab holds at least its Krylov basis ((restart + 1) x n doubles)
+    n = int(ptr[-1]) + len(ptr) - 1
+    states = 3 * 128  # per right-hand side: three staged GMRES states for the host's reads
+    slab = (b16 - rnd - 16 * states) // 16
+    assert (b16 - rnd - 16 * states) % (16 * 256) == 0 and slab >= 8 * 51 * n
+    assert b2 - rnd == 2 * (slab + states) and b8 - rnd == 8 * (slab + states)
+    assert lib.lbf_batch_workspace_size(ptr, o, 40) == b16  # groups of 16 reuse one workspace
+    ir = lib.lbf_default_options(precision=lib.LBF_PRECISION_FP32_REFINE)
+    assert lib.lbf_batch_workspace_size(ptr, ir, 4) > (lib.lbf_workspace_size(ptr, ir) + 255) // 256 * 256
+    for opt in (lib.lbf_default_options(schur=lib.LBF_SCHUR_LU), lib.lbf_default_options(border=0)):
+        assert lib.lbf_batch_workspace_size(ptr, opt, 16) == lib.lbf_workspace_size(ptr, opt)
+    with pytest.raises(lib.LbfError):
+        lib.lbf_batch_workspace_size(ptr, o, -1)
