@@ -1373,8 +1373,8 @@ k_near_multi(int64_t nleaf, const int32_t *__restrict__ leaves, const int32_t *_
 {
     constexpr bool kF32 = kLocal<R>;
     constexpr int CH = kMultiChunk<R>;
-    int open = 0;  // right-hand sides whose gate is open
-    for (int k = 0; k < nr; k++)
+    int open = gate ? 0 : nr;  // right-hand sides whose gate is open (no gate: all)
+    for (int k = 0; gate && k < nr; k++)
         open += gate_closed((const int *)((const char *)gate + k * slab)) ? 0 : 1;
     if (open == 0) return;
     extern __shared__ __align__(16) unsigned char nm_sm[];
