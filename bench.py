@@ -231,6 +231,12 @@ def run_reference(args):
 # the sources that decide the memory traffic of the FMM passes (up, down, leaf: their
 # kernels, launch shapes, tree and lists); the DRAM bytes of profiles/traffic.json are
 # keyed to them
+# inner tolerance of the batched refinement: on 128 of the 512 geometries, 1e-5 needs two
+# refinement rounds where 3e-4 (the library's default) needs three, with fewer float applies
+# too (51,663 and 4,174 FP64 against 58,486 and 6,133): 1.41 s against 1.64 s; 1e-4 and 3e-5
+# were slower (1.71, 1.91 s: more float applies, the same rounds)
+C4_INNER_TOL = 1e-5
+
 FMM_SOURCES = ("lbf_fmm_tpl.cuh", "lbf_fmm.cu", "lbf_tree.cu", "lbf_df64.cuh", "lbf_internal.cuh")
 
 
@@ -741,7 +747,8 @@ def run_extras(args, L, dev, stream):
             e.extend(((r["u"] - ins["uex"]).abs().amax(dim=1) / ins["uex"].abs().amax(dim=1)).tolist())
         return float(np.max(e))
 
-    ob = L.lbf_default_options(tol=args.tol, precision=L.LBF_PRECISION_FP32_REFINE, fmm64=0)
+    ob = L.lbf_default_options(tol=args.tol, precision=L.LBF_PRECISION_FP32_REFINE, fmm64=0,
+                               inner_tol=C4_INNER_TOL)
     L.lbf_batch_run(inst[:4], opt=ob, nworkers=args.workers)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -831,7 +838,7 @@ def run_batch(args):
         return float(np.max(e)), float(np.median(e))
 
     def batched(precision, sub, lockstep=False):
-        kw = dict(inner_tol=args.inner_tol) if args.inner_tol else {}
+        kw = dict(inner_tol=args.inner_tol or C4_INNER_TOL)
         opt = L.lbf_default_options(tol=args.tol, precision=precision, fmm64=0, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
