@@ -85,17 +85,23 @@ def _separate(p, g, data):
 FP64, IR = L.LBF_PRECISION_FP64, L.LBF_PRECISION_FP32_REFINE
 
 
-@pytest.mark.parametrize("M,nodes,nrhs,restart,graphs,matvec,precision,depth", [
-    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, FP64, 30),     # graph-replayed steps, one cycle
-    (5, 120, 4, 6, 1, L.LBF_MATVEC_FMM, FP64, 30),     # restarts every 6 steps
-    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM, FP64, 30),    # two lockstep groups (16 + 2)
-    (3, 100, 3, 50, 0, L.LBF_MATVEC_FMM, FP64, 30),    # steps launched one by one
-    (4, 150, 6, 50, 1, L.LBF_MATVEC_FMM, FP64, 3),     # depth cap: leaves of well over 64 nodes
-    (1, 256, 3, 50, 1, L.LBF_MATVEC_DIRECT, FP64, 30), # one island, direct sums
-    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, IR, 30),       # refinement: FP64 residuals, float inner solves
-    (5, 120, 7, 8, 0, L.LBF_MATVEC_FMM, IR, 30),       # refinement with inner restarts, no graphs
+# fmm64 0: the accurate operator in native double (its lockstep near field is k_near_multi);
+# 1: in double-float (a leaf pass per right-hand side)
+@pytest.mark.parametrize("M,nodes,nrhs,restart,graphs,matvec,precision,depth,fmm64", [
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, FP64, 30, 0),     # graph-replayed steps, one cycle
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, FP64, 30, 1),     # the same, double-float operator
+    (5, 120, 4, 6, 1, L.LBF_MATVEC_FMM, FP64, 30, 0),     # restarts every 6 steps
+    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM, FP64, 30, 0),    # two lockstep groups (16 + 2)
+    (4, 80, 18, 50, 1, L.LBF_MATVEC_FMM, FP64, 30, 1),
+    (3, 100, 3, 50, 0, L.LBF_MATVEC_FMM, FP64, 30, 0),    # steps launched one by one
+    (4, 150, 6, 50, 1, L.LBF_MATVEC_FMM, FP64, 3, 0),     # depth cap: leaves of well over 64 nodes
+    (1, 256, 3, 50, 1, L.LBF_MATVEC_DIRECT, FP64, 30, 0), # one island, direct sums
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, IR, 30, 0),       # refinement: FP64 residuals, float inner solves
+    (6, 96, 5, 50, 1, L.LBF_MATVEC_FMM, IR, 30, 1),
+    (5, 120, 7, 8, 0, L.LBF_MATVEC_FMM, IR, 30, 0),       # refinement with inner restarts, no graphs
 ])
-def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec, precision, depth):
+def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec, precision, depth,
+                                         fmm64):
     """Each right-hand side of a lockstep solve runs the kernels of a solve on its own,
     except the FMM's near field, which the lockstep group sums in one pass sharing each
     pair's geometry (k_near_multi: c (w x dz) / |dz|^2 formed as c times the pair's
@@ -105,7 +111,7 @@ def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec
     included: its FP64 residual decides when it stops)."""
     g, data = _lockstep_case(M, nodes, nrhs, seed=70 + M)
     p = plan_for(g, tol=1e-12, restart=restart, graphs=graphs, matvec=matvec, precision=precision,
-                 max_depth=depth)
+                 max_depth=depth, fmm64=fmm64)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         sig, a = zeros(nrhs * g.N), zeros(nrhs * g.M)
@@ -128,10 +134,10 @@ def test_lockstep_equals_separate_solves(M, nodes, nrhs, restart, graphs, matvec
             assert rel_l2(_rows(a, k, g.M), ak) < 1e-9
 
 
-@pytest.mark.parametrize("precision", [FP64, IR])
-def test_lockstep_matches_oracle_dense_solve(precision):
+@pytest.mark.parametrize("precision,fmm64", [(FP64, 0), (FP64, 1), (IR, 0)])
+def test_lockstep_matches_oracle_dense_solve(precision, fmm64):
     g, data = _lockstep_case(5, 88, 6, seed=91)
-    p = plan_for(g, tol=1e-12, precision=precision)
+    p = plan_for(g, tol=1e-12, precision=precision, fmm64=fmm64)
     sig, a = zeros(6 * g.N), zeros(6 * g.M)
     rc, its, rr = L.lbf_gmres_solve_many(p, dev(data), sig, a)
     assert rc == L.LBF_OK and max(rr) <= 1e-12
@@ -164,12 +170,12 @@ def test_lockstep_short_workspace_and_sequential_plans():
         assert its[k] == itk and np.array_equal(_rows(sig, k, g.N), sk)
 
 
-@pytest.mark.parametrize("precision", [FP64, IR])
-def test_batch_lockstep_matches_oracle(precision):
+@pytest.mark.parametrize("precision,fmm64", [(FP64, 0), (FP64, 1), (IR, 0)])
+def test_batch_lockstep_matches_oracle(precision, fmm64):
     """The batch runner's lockstep solves (the default) against the oracle's dense solve
     and the evaluation at the targets against the one-after-another runs."""
     inst = _instances(count=6, nrhs=5)
-    opt = L.lbf_default_options(tol=1e-12, precision=precision)
+    opt = L.lbf_default_options(tol=1e-12, precision=precision, fmm64=fmm64)
     lock = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=True)
     seq = L.lbf_batch_run(inst, opt=opt, nworkers=3, lockstep=False)
     for ins, a, b in zip(inst, lock, seq):
