@@ -216,11 +216,14 @@ int lbf_gmres_solve(lbf_plan *plan, const double *g, double *sigma, double *a, c
  * when graphs are on; with FP32_REFINE every refinement round forms the FP64 residuals
  * of the open right-hand sides together and runs their float inner solves in lockstep.
  * Each right-hand side runs the kernels and fixed-order reductions of lbf_gmres_solve on
- * its own buffers, so sigma, a, iters and rel_res equal those of nrhs separate
- * lbf_gmres_solve calls bit for bit; a right-hand side that converges stops while the
- * others go on.  Plans whose S^-1 is applied by LU factors (LBF_SCHUR_LU, or M > 1024
- * with LBF_SCHUR_AUTO) solve the right-hand sides one after another with lbf_gmres_solve
- * (workspace 0).
+ * its own buffers, except the near field of the native-double FMM operator (fmm64 = 0),
+ * which one pass forms for the whole group, a pair's geometry once for all densities (a
+ * different rounding: results agree with separate solves to the solver's tolerance).
+ * With direct sums, the double-float operator, or the float one alone, sigma, a, iters
+ * and rel_res equal those of nrhs separate lbf_gmres_solve calls bit for bit.  A
+ * right-hand side that converges stops while the others go on.  Plans whose S^-1 is
+ * applied by LU factors (LBF_SCHUR_LU, or M > 1024 with LBF_SCHUR_AUTO) solve the
+ * right-hand sides one after another with lbf_gmres_solve (workspace 0).
  *   g: device, nrhs x N, caller order (right-hand side r at g + r N)
  *   sigma: device out, nrhs x N; a: device out, nrhs x M (nullable)
  *   iters, rel_res: host out, nrhs each (nullable)

@@ -1015,7 +1015,8 @@ static const GmresState *host_states(lbf_plan *v, int k)
 // iteration limit of right-hand side r (0: none).  Each launch covers all right-hand
 // sides and is gated per right-hand side by its own state; one that finishes stops (its
 // gate closes, its restarts are skipped, and later cycle ends add nothing to its x), so
-// its iterates are those of gmres_core on it alone.
+// its iterates are those of gmres_core on it alone (up to the rounding of the group's
+// near field, when the native-double operator forms it in one pass).
 static int gmres_core_many(lbf_plan *pl, int opc, int prec, const double *b, const double *bn,
                            double *x, double tol, const int *maxit, GmresState *dst,
                            cudaStream_t s, GmresState *out)
