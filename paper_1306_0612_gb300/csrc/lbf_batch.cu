@@ -29,9 +29,9 @@ int run_item(lbf_batch_item &it, const lbf_options &opt_all, cudaStream_t s)
     // the right-hand sides in lockstep when the item's workspace holds their buffers
     // after the plan's (lbf_batch_workspace_size)
     size_t pbytes = 0, mbytes = 0;
-    lbf_workspace_size(it.M, it.island_ptr, &opt, &pbytes);
+    const bool sized = lbf_workspace_size(it.M, it.island_ptr, &opt, &pbytes) == LBF_OK;
     pbytes = (pbytes + 255) & ~size_t(255);
-    const bool lock = it.nrhs > 1 && lbf_gmres_workspace_many(pl, it.nrhs, &mbytes) == LBF_OK &&
+    const bool lock = sized && it.nrhs > 1 && lbf_gmres_workspace_many(pl, it.nrhs, &mbytes) == LBF_OK &&
                       mbytes > 0 && it.bytes >= pbytes + mbytes;
     if (lock) {
         std::vector<int> its(it.nrhs, 0);
