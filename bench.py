@@ -684,7 +684,7 @@ def run_extras(args, L, dev, stream):
         u = AG.solve_evaluate(gt, xt, d1t, d2t, cen, tg, g.island_ptr, o5)
         loss = (u ** 2).mean()
         loss.backward()
-        return float(loss)
+        return float(loss.detach())
 
     grad_step()
     gms = timed(grad_step, stream, 3)[0] / 3
