@@ -285,6 +285,35 @@ def kernel_work(name, c, bc, P, P32, N):
     return None, None
 
 
+def peak_fractions(line):
+    """The FMM matvec's and the whole GMRES solve's algorithmic FP64 rate against the
+    roofline's FP64 peak (native-double runs): the operator's work by kernel_work (upward,
+    downward and leaf passes; the solve adds each preconditioned application's multiplier
+    potential E y) over the measured apply and solve times.  The Arnoldi steps, the
+    preconditioner's S^-1 and the vector work count as no work, so the solve's fraction is
+    a lower bound.  None when the line lacks what it needs."""
+    try:
+        s, rf = line["solve"], line["roofline"]
+        c, bc, N = s["counts"], s["border_counts"], s["counts"]["N"]
+        P = s["tree"]["p"] + 1
+        if rf.get("unit") != "TFLOP/s" or not line["matvec"].get("fp64"):
+            return None
+        w = {k: kernel_work(k, c, bc, P, 0, N)[0] for k in ("up", "down", "leaf", "esum")}
+        k_apply = w["up"] + w["down"] + w["leaf"]
+        mv_ms = line["matvec"]["fp64"]["ms"]
+        work = s["fp64_applies"] * (k_apply + (w["esum"] or 0))
+        peak = rf["peak"]
+
+        def rate(flop, ms):
+            a = flop / (ms * 1e-3) / 1e12
+            return {"gflop": flop / 1e9, "ms": ms, "achieved": a, "frac": a / peak}
+
+        return {"unit": "TFLOP/s", "peak": peak, "peak_source": rf.get("peak_source"),
+                "matvec": rate(k_apply, mv_ms), "solve": rate(work, s["solve_ms"])}
+    except (KeyError, TypeError, AttributeError, ZeroDivisionError):
+        return None
+
+
 def aggregate(ms, units, world, device):
     """Whole-job numbers of one timed region over the ranks: the slowest rank's time and
     the units every rank processed (each rank runs its own replica)."""
@@ -606,6 +635,8 @@ def run_ours(args):
                 "kernel_launches": {k: v["launches"] for k, v in prof.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks}
+        if args.precision == "fp64":
+            line["peak_fractions"] = peak_fractions(line)
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
