@@ -292,7 +292,9 @@ typedef struct lbf_batch_item {
     int M;                                  /* islands */
     const int64_t *island_ptr;              /* host, M + 1 */
     const double *x, *dx, *d2x, *centres;   /* device, as lbf_plan_create */
-    void *workspace;                        /* device, >= lbf_workspace_size(M, island_ptr, opt) */
+    void *workspace;                        /* device, >= lbf_workspace_size(M, island_ptr, opt);
+                                               lbf_batch_workspace_size(..., nrhs) bytes for the
+                                               right-hand sides in lockstep */
     size_t bytes;
     int nrhs;                               /* right-hand sides */
     const double *g;                        /* device, nrhs x N: right-hand side r at g + r N */
